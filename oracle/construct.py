@@ -1,0 +1,250 @@
+"""Numeric setup of the oracle: Algorithm 1 step by step (test infrastructure).
+
+For each level l (Algorithm 1), while l < L_max - 1 and n_l > n_coarse:
+
+  1. aggregation: the level-0 aggregates are an input; on coarse levels the
+     block graph (one node per previous-level aggregate, an edge where a row
+     of G touches both) is aggregated with standard passes and every coarse
+     dof of a block follows its block (the paper leaves the coarse rule
+     open; this reading keeps the cycle independent of the basis chosen
+     inside each block);
+  2. overlapping subdomains and Boolean PoU (Section 2.2, Eq. pou2);
+  3. smoother blocks A_i = A_l(Omega_i, Omega_i) and their Cholesky factors
+     (Section 2.2; the factors are applied by triangular solves);
+  4. SPSD splitting A~_i = sum_{rows in nz_i} g^T g / M (Lemma);
+  5. reduced generalized eigenproblem on omega_i (Eq. gevp-S):
+     A_ww u = lambda S~ u with S~ the Schur complement of A~_i onto omega_i;
+     solved as S~ u = mu A_ww u, mu = 1/lambda ascending, so the largest
+     lambda come first;
+  6. selection: all lambda > thresh, at most max(1, floor(|omega_i|/c_l))
+     (Section 3.4); Z_i normalised so Z_i^T A_ww Z_i = I and the entry of
+     largest magnitude of each column is positive;
+  7. P_l = [R_{omega_1}^T Z_1 ... ] (Eq. mg-p), columns ordered by aggregate
+     then by ascending mu;
+  8. G_{l+1} = G_l P_l, A_{l+1} = G_{l+1}^T G_{l+1} (Section 3.1,
+     "Multilevel method").
+
+The coarsest level is factored densely (Cholesky).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from .structure import (
+    cleanup_aggregates,
+    multiplicity_and_nz,
+    overlapping_subdomains,
+    row_groups_from_csr,
+    structural_adjacency,
+    vanek_aggregation,
+)
+
+
+@dataclass
+class Level:
+    n: int
+    sups: list  # row-group supports of G_l
+    grams: list  # row-group outer-product sums of G_l
+    A: sp.csr_matrix  # A_l = G_l^T G_l (structural pattern kept)
+    agg: np.ndarray | None = None
+    nagg: int = 0
+    omega: list = field(default_factory=list)
+    gamma: list = field(default_factory=list)
+    Omega: list = field(default_factory=list)
+    M: np.ndarray | None = None
+    nz: list = field(default_factory=list)
+    touched: list = field(default_factory=list)
+    chol: list = field(default_factory=list)  # lower Cholesky factor of each A_i
+    mu: list = field(default_factory=list)  # all local eigenvalues mu (ascending)
+    Z: list = field(default_factory=list)  # selected, A_ww-orthonormal
+    k: np.ndarray | None = None
+    col0: np.ndarray | None = None  # first coarse column of each aggregate
+    P: sp.csr_matrix | None = None
+    Atil: list = field(default_factory=list)  # kept only when keep_local
+    S: list = field(default_factory=list)  # kept only when keep_local
+    Ai: list = field(default_factory=list)  # kept only when keep_local
+
+
+@dataclass
+class Hierarchy:
+    levels: list
+    coarse_chol: np.ndarray  # lower Cholesky factor of the coarsest A_L
+    params: dict
+
+
+def assemble_A(sups, grams, n):
+    """A = sum_g embed(H_g): the structural pattern of G^T G is kept."""
+    rows, cols, vals = [], [], []
+    for s, H in zip(sups, grams):
+        rows.append(np.repeat(s, s.shape[0]))
+        cols.append(np.tile(s, s.shape[0]))
+        vals.append(H.ravel())
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    A = A.tocsr()
+    A.sum_duplicates()
+    A.sort_indices()
+    return A
+
+
+def local_splitting(Omega_i, nz_i, sups, grams, M, n_scratch=None):
+    """A~_i of the Lemma: sum over rows in nz_i of g^T W g, embedded in Omega_i."""
+    m = Omega_i.shape[0]
+    loc = {int(j): t for t, j in enumerate(Omega_i)}
+    At = np.zeros((m, m))
+    for g in nz_i:
+        p = np.array([loc[int(j)] for j in sups[g]])
+        At[np.ix_(p, p)] += grams[g] / M[g]
+    return At
+
+
+def schur_complement(Atil, no, rtol):
+    """S~ of Eq. gevp-S: A~_ww - A~_wG (A~_GG)^+ A~_Gw.
+
+    Where A~_GG is singular (a Gamma node or direction that no row of nz_i
+    sees) the inverse is read as the pseudo-inverse, eigenvalues at or below
+    rtol * (largest eigenvalue) being treated as zero.
+    """
+    Aww = Atil[:no, :no]
+    if Atil.shape[0] == no:
+        S = Aww.copy()
+    else:
+        Awg = Atil[:no, no:]
+        Agg = Atil[no:, no:]
+        w, U = np.linalg.eigh(Agg)
+        keep = w > rtol * max(w.max(), 0.0) if w.size else w > 0
+        if not np.any(keep):
+            S = Aww.copy()
+        else:
+            Uk = U[:, keep]
+            T = Awg @ Uk
+            S = Aww - (T / w[keep]) @ T.T
+    return 0.5 * (S + S.T)
+
+
+def local_gep(S, Aww, cap, thresh):
+    """Reduced GEP (Eq. gevp-S) and the eigenvector selection of Section 3.4.
+
+    Solves S~ u = mu A_ww u (mu = 1/lambda, ascending).  Keeps the first
+    k = min(#{lambda > thresh}, cap) columns; mu <= 0 counts as lambda = inf.
+    Returns (mu_all, Z) with Z^T A_ww Z = I, largest-magnitude entry of each
+    column positive (first index on ties).
+    """
+    mu, V = sla.eigh(S, Aww)
+    if thresh > 0:
+        count = int(np.sum((mu <= 0) | (mu < 1.0 / thresh)))
+    else:
+        count = mu.shape[0]
+    k = min(count, cap)
+    Z = V[:, :k].copy()
+    for c in range(k):
+        j = int(np.argmax(np.abs(Z[:, c])))
+        if Z[j, c] < 0:
+            Z[:, c] = -Z[:, c]
+    return mu, Z
+
+
+def _block_aggregation(prev):
+    """Coarse aggregates on the block graph of the previous level."""
+    nb = prev.nagg
+    r, c = [], []
+    for t in prev.touched:
+        if t.shape[0] > 1:
+            r.append(np.repeat(t, t.shape[0]))
+            c.append(np.tile(t, t.shape[0]))
+    if r:
+        B = sp.csr_matrix((np.ones(sum(x.shape[0] for x in r), dtype=np.int8),
+                           (np.concatenate(r), np.concatenate(c))), shape=(nb, nb))
+        B.setdiag(0)
+        B.eliminate_zeros()
+    else:
+        B = sp.csr_matrix((nb, nb), dtype=np.int8)
+    B.sort_indices()
+    bagg, nagg = vanek_aggregation(B)
+    agg = np.repeat(bagg, prev.k)
+    return agg, nagg
+
+
+def _next_groups(level):
+    """Row groups of G_{l+1} = G_l P_l, merged by identical support.
+
+    A row g of G_l becomes g P_l; its support is the coarse columns of every
+    aggregate the row touches, and g^T g becomes P^T (g^T g) P restricted to
+    those columns.
+    """
+    P = level.P.tocsr()
+    merged = {}
+    for s, H, t in zip(level.sups, level.grams, level.touched):
+        cs = np.concatenate([np.arange(level.col0[a], level.col0[a] + level.k[a]) for a in t])
+        Pg = P[s][:, cs].toarray()
+        Hn = Pg.T @ H @ Pg
+        key = tuple(int(a) for a in t)
+        if key in merged:
+            merged[key][1][...] += Hn
+        else:
+            merged[key] = (cs.astype(np.int64), Hn)
+    keys = sorted(merged)
+    return [merged[k][0] for k in keys], [merged[k][1] for k in keys]
+
+
+def setup(rowptr, col, val, n, D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=2000, L_max=10,
+          thresh=0.1, schur_rtol=1e-12, keep_local=False):
+    """Build the multilevel hierarchy {A_l, G_l, P_l} of Algorithm 1."""
+    sups, grams = row_groups_from_csr(rowptr, col, val, n, D1)
+    A = assemble_A(sups, grams, n)
+    levels = []
+    cur = Level(n=n, sups=sups, grams=grams, A=A)
+    lvl = 0
+    agg0 = np.asarray(agg)
+    while lvl < L_max - 1 and cur.n > n_coarse:
+        adj = structural_adjacency(cur.sups, cur.n)
+        if lvl == 0:
+            cur.agg, cur.nagg = cleanup_aggregates(agg0, adj)
+        else:
+            cur.agg, cur.nagg = _block_aggregation(levels[-1])
+        cur.omega, cur.gamma, cur.Omega = overlapping_subdomains(cur.agg, cur.nagg, adj, overlap)
+        cur.M, cur.nz, cur.touched = multiplicity_and_nz(cur.sups, cur.agg, cur.nagg)
+        c = c_min[min(lvl, len(c_min) - 1)]
+        ks = np.zeros(cur.nagg, dtype=np.int64)
+        Acsr = cur.A
+        for i in range(cur.nagg):
+            om, Om = cur.omega[i], cur.Omega[i]
+            no = om.shape[0]
+            Ai = Acsr[Om][:, Om].toarray()
+            L = np.linalg.cholesky(Ai)  # raises LinAlgError when A_i is not SPD
+            cur.chol.append(L)
+            At = local_splitting(Om, cur.nz[i], cur.sups, cur.grams, cur.M)
+            S = schur_complement(At, no, schur_rtol)
+            mu, Z = local_gep(S, Ai[:no, :no], max(1, no // c), thresh)
+            cur.mu.append(mu)
+            cur.Z.append(Z)
+            ks[i] = Z.shape[1]
+            if keep_local:
+                cur.Atil.append(At)
+                cur.S.append(S)
+                cur.Ai.append(Ai)
+        cur.k = ks
+        cur.col0 = np.zeros(cur.nagg + 1, dtype=np.int64)
+        np.cumsum(ks, out=cur.col0[1:])
+        nc = int(cur.col0[-1])
+        r, cc, v = [], [], []
+        for i in range(cur.nagg):
+            Z = cur.Z[i]
+            r.append(np.repeat(cur.omega[i], Z.shape[1]))
+            cc.append(np.tile(np.arange(cur.col0[i], cur.col0[i + 1]), Z.shape[0]))
+            v.append(Z.ravel())
+        cur.P = sp.csr_matrix((np.concatenate(v), (np.concatenate(r), np.concatenate(cc))), shape=(cur.n, nc))
+        cur.P.sort_indices()
+        levels.append(cur)
+        nsups, ngrams = _next_groups(cur)
+        cur = Level(n=nc, sups=nsups, grams=ngrams, A=assemble_A(nsups, ngrams, nc))
+        lvl += 1
+    levels.append(cur)
+    AL = cur.A.toarray()
+    coarse = np.linalg.cholesky(AL)
+    params = dict(overlap=overlap, c_min=tuple(c_min), n_coarse=n_coarse, L_max=L_max, thresh=thresh,
+                  schur_rtol=schur_rtol)
+    return Hierarchy(levels=levels, coarse_chol=coarse, params=params)
