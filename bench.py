@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Benchmark of the LS-AMG-DD solve phase on one GB300 (or N replicas).
+
+Workload (default): 512 x 512 Q1 cells (261,121 unknowns), K = R diag(1, eps)
+R^T with theta = pi/6, eps = 1e-4, 4 x 4 level-0 aggregates, overlap 1,
+LS_{2,3,4} coarsening to <= 2000 unknowns, one N(0,1) right-hand side per
+solve, CG to 1e-8 relative residual.
+
+A step is one V-cycle-preconditioned CG solve to 1e-8 of a fresh
+right-hand side already resident in device memory (the hierarchy is built
+once, before timing).  `value` is solves/s of the mixed-precision form (FP32
+V-cycle under FP64 flexible CG); the plain FP64 GPU path is timed on the
+same inputs beside it.  `e2e` repeats the timing through the C ABI with
+pinned host buffers (host->device copy of b and device->host copy of x
+inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank is an independent replica (its own right-hand
+sides); value = all solves / max over ranks of the timed wall time.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "V-cycles/s & solves/s to 1e-8 rel. residual (mixed vs FP64); p50/p99 latency"
+WORKLOAD = "q1_512_rot"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--theta", type=float, default=None)
+    ap.add_argument("--eps", type=float, default=None)
+    ap.add_argument("--N", type=int, default=None, help="cells per axis (smaller captures)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true", help="setup + a few solves, no timing line")
+    ap.add_argument("--oracle-solve", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for row in csv.reader(f):
+                if len(row) < 9:
+                    continue
+                try:
+                    sm.append(float(row[1]))
+                    mx = float(row[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, row[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_desc(cfg):
+    return (f"{cfg['N']}x{cfg['N']} Q1 cells ({(cfg['N'] - 1) ** 2:,} unknowns), theta={cfg['theta']:.6f}, "
+            f"eps={cfg['eps']:g}, {cfg['bs']}x{cfg['bs']} aggregates, overlap {cfg['overlap']}, "
+            f"LS_{{{','.join(str(c) for c in cfg['c_min'])}}}, n_coarse {cfg['n_coarse']}, 1 RHS, tol 1e-8")
+
+
+def oracle_setup(prob, cfg):
+    """The oracle's own hierarchy for the workload (not timed)."""
+    import oracle
+
+    t0 = time.time()
+    ho = oracle.setup(prob.rowptr, prob.col, prob.val, prob.n, prob.D1, prob.agg, overlap=cfg["overlap"],
+                      c_min=cfg["c_min"], n_coarse=cfg["n_coarse"], thresh=cfg["thresh"])
+    setup_s = time.time() - t0
+    return ho, setup_s
+
+
+def cpu_threads():
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(v):
+            return int(os.environ[v])
+    return os.cpu_count() or 1
+
+
+def oracle_solve_sample(args):
+    """One oracle CG solve of a given right-hand side (runs in its own process)."""
+    import numpy as np
+
+    import oracle
+    from inputs.q1 import config_problem
+
+    d = np.load(args.oracle_solve)
+    over = {k: float(d[k]) for k in ("theta", "eps") if k in d}
+    if "N" in d:
+        over["N"] = int(d["N"])
+    prob, cfg = config_problem(args.workload, **over)
+    ho, setup_s = oracle_setup(prob, cfg)
+    t0 = time.time()
+    xo, io = oracle.pcg(ho, d["b"], tol=1e-8)
+    solve_s = time.time() - t0
+    err = float(np.abs(xo - d["x"]).max() / np.abs(xo).max())
+    print(json.dumps({"setup_s": setup_s, "solve_s": solve_s, "iters": io["iters"], "err": err,
+                      "cores": cpu_threads()}), flush=True)
+
+
+def run_reference(args):
+    """The oracle on the host cores, same workload, metric and unit."""
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from inputs.q1 import config_problem, seeded_rhs
+
+    over = {}
+    if args.theta is not None:
+        over["theta"] = args.theta
+    if args.eps is not None:
+        over["eps"] = args.eps
+    if args.N is not None:
+        over["N"] = args.N
+    prob, cfg = config_problem(args.workload, **over)
+    ho, setup_s = oracle_setup(prob, cfg)
+    b = seeded_rhs(prob.n, 1, cfg["seed"] * 1000)[:, 0]
+    # one full solve gives the iteration count; each timed step is one
+    # CG iteration (A-apply, V-cycle, updates) of that solve
+    t0 = time.time()
+    x, info = oracle.pcg(ho, b, tol=1e-8)
+    full_s = time.time() - t0
+    iters = info["iters"]
+    # one preconditioned CG iteration (the recurrences of oracle.pcg)
+    A0 = ho.levels[0]
+    r = b.copy()
+    z = oracle.vcycle(ho, r)
+    p = z.copy()
+    xk = np.zeros_like(b)
+    rz = float(r @ z)
+    times = []
+    for step in range(args.warmup + args.steps):
+        t = time.time()
+        q = oracle.apply_A(A0, p)
+        alpha = rz / float(p @ q)
+        xk += alpha * p
+        r -= alpha * q
+        z = oracle.vcycle(ho, r)
+        rzn = float(r @ z)
+        p = z + (rzn / rz) * p
+        rz = rzn
+        if step >= args.warmup:
+            times.append(time.time() - t)
+        if step + 1 >= iters:  # restart from the first iterate to stay on the solve's path
+            r = b.copy()
+            z = oracle.vcycle(ho, r)
+            p = z.copy()
+            rz = float(r @ z)
+    t_iter = sum(times) / len(times)
+    value = 1.0 / (t_iter * iters)
+    cores = cpu_threads()
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_iter * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload_desc(cfg)},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"oracle setup untimed ({setup_s:.1f} s); each step one CG iteration of the "
+                                       f"oracle's solve, solves/s = 1/(mean step time x {iters} iterations); "
+                                       f"one full oracle solve took {full_s:.1f} s"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2601_04112_gb300 as amg
+    from inputs.q1 import config_problem, seeded_rhs
+
+    over = {}
+    if args.theta is not None:
+        over["theta"] = args.theta
+    if args.eps is not None:
+        over["eps"] = args.eps
+    if args.N is not None:
+        over["N"] = args.N
+    prob, cfg = config_problem(args.workload, **over)
+    n = prob.n
+    t0 = time.time()
+    H = amg.Hierarchy.from_problem(prob, overlap=cfg["overlap"], c_min=cfg["c_min"], n_coarse=cfg["n_coarse"],
+                                   thresh=cfg["thresh"], precision=amg.MIXED32)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    stats = H.stats()
+    nsol = args.warmup + args.steps
+    Bh = seeded_rhs(n, nsol, cfg["seed"] * 1000 + rank)  # n x nsol, column-major
+    B = torch.from_numpy(np.ascontiguousarray(Bh.T)).cuda()  # row j = right-hand side j
+    X = torch.zeros_like(B)
+
+    def timed(prec, start, count, bsrc, xdst):
+        H.set_precision(prec)
+        infos = []
+        dev = bsrc.is_cuda
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        k0 = amg.kernel_launches()
+        w0 = time.perf_counter()
+        e0.record()
+        for j in range(start, start + count):
+            _, inf = H.solve(bsrc[j] if dev else bsrc[j].numpy(), x=xdst[j] if dev else xdst[j].numpy())
+            infos.append(inf[0])
+        e1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        return e0.elapsed_time(e1) / 1e3, wall, infos, amg.kernel_launches() - k0
+
+    def maxrank(v):
+        if world == 1:
+            return v
+        import torch.distributed as dist
+
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # warm-up (both precisions: graph capture, first-touch)
+    for prec in (amg.FP64, amg.MIXED32):
+        timed(prec, 0, args.warmup, B, X)
+    if args.profile_only:
+        H.set_precision(amg.MIXED32)
+        ms, by = H.profile_vcycle(10)
+        print(json.dumps({"stats": stats, "profile_ms": ms.tolist(), "profile_bytes": by.tolist()}))
+        return
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_mix, w_mix, inf_mix, launches = timed(amg.MIXED32, args.warmup, args.steps, B, X)
+    clocks = sampler.stop()
+    t_64, w_64, inf_64, _ = timed(amg.FP64, args.warmup, args.steps, B, X)
+    t_mix = maxrank(t_mix)
+    t_64 = maxrank(t_64)
+    for inf in inf_mix + inf_64:
+        assert inf["status"] == 0 and inf["relres_true"] <= 1e-8, inf
+    it_mix = [i["iters"] for i in inf_mix]
+    it_64 = [i["iters"] for i in inf_64]
+    solves = args.steps * world
+    value = solves / t_mix
+    fp64_value = solves / t_64
+    vc_mix = sum(i + 1 for i in it_mix) * world / t_mix
+    vc_64 = sum(i + 1 for i in it_64) * world / t_64
+    lat = sorted(i["solve_ms"] for i in inf_mix)
+
+    # per-step V-cycle profile (CUDA events between launches) -> roofline
+    H.set_precision(amg.MIXED32)
+    ms, by = H.profile_vcycle(10)
+    seg_slots, app_slots = (0, 3, 4, 7), (2,)
+    seg_ms = float(sum(ms[l, s] for l in range(ms.shape[0]) for s in seg_slots))
+    seg_by = float(sum(by[l, s] for l in range(ms.shape[0]) for s in seg_slots))
+    app_ms = float(sum(ms[l, s] for l in range(ms.shape[0]) for s in app_slots))
+    app_by = float(sum(by[l, s] for l in range(ms.shape[0]) for s in app_slots))
+    vcyc_ms = float(ms.sum())
+    peak, peak_kind = hbm_peak()
+    if seg_ms >= app_ms:
+        kname, kms, kby = "k_seg (RAS/RAS-T/P/R gather-GEMV-scatter, all levels, FP32)", seg_ms, seg_by
+        nlaunch = 4 * (ms.shape[0] - 1) + 1
+    else:
+        kname, kms, kby = "k_apply (grouped G then G^T residual, all levels, FP32)", app_ms, app_by
+        nlaunch = 2 * (ms.shape[0] - 1)
+    achieved = kby / (kms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": kname, "launches_per_vcycle": nlaunch,
+                "bytes_per_vcycle": kby, "ms_per_vcycle": kms,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "vcycle": {"ms": vcyc_ms, "bytes": float(by.sum()),
+                           "achieved_gbs": float(by.sum()) / (vcyc_ms * 1e-3) / 1e9}}
+
+    # end to end through the C ABI with pinned host buffers
+    Bp = torch.empty((nsol, n), dtype=torch.float64, pin_memory=True)
+    Bp.copy_(B.cpu())
+    Xp = torch.zeros_like(Bp).pin_memory()
+    t_e2e, w_e2e, inf_e2e, _ = timed(amg.MIXED32, args.warmup, args.steps, Bp, Xp)
+    t_e2e = maxrank(max(t_e2e, w_e2e))
+    e2e = {"value": solves / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle in a process of its own, single-threaded BLAS
+        fd, path = tempfile.mkstemp(suffix=".npz")
+        os.close(fd)
+        np.savez(path, b=Bh[:, args.warmup].copy(), x=X[args.warmup].cpu().numpy(), theta=cfg["theta"],
+                 eps=cfg["eps"], N=cfg["N"])
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference", "--workload",
+                            args.workload, "--oracle-solve", path], capture_output=True, text=True, env=env)
+        os.unlink(path)
+        try:
+            o = json.loads(r.stdout.strip().splitlines()[-1])
+            cpu = {"value": 1.0 / o["solve_s"], "unit": "solves/s", "cores": o["cores"], "kind": "oracle",
+                   "sample": f"one oracle PCG solve of the first timed right-hand side ({o['iters']} iterations, "
+                             f"{o['solve_s']:.1f} s) after the oracle's own setup ({o['setup_s']:.1f} s, untimed), "
+                             f"single-threaded BLAS; max |x_oracle - x_gpu| / max |x_oracle| = {o['err']:.1e}"}
+        except Exception as e:  # report, do not hide, a failed baseline
+            cpu = {"value": None, "unit": "solves/s", "cores": None, "kind": "oracle",
+                   "sample": f"oracle run failed: {e}: {r.stderr[-300:]}"}
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_mix / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": workload_desc(cfg), "precision": "FP32 V-cycle, FP64 flexible CG",
+                   "l2": "inputs larger than L2: one V-cycle moves %.2f GB" % (float(by.sum()) / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "fp64": {"value": fp64_value, "unit": "solves/s", "ms_per_step": t_64 / args.steps * 1e3,
+                 "iters": it_64},
+        "mixed_over_fp64": value / fp64_value,
+        "vcycles_per_s": {"mixed": vc_mix, "fp64": vc_64},
+        "iters": it_mix, "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "setup_s": setup_s, "levels": stats["n"], "op_complexity": stats["op_complexity"],
+        "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        # the oracle's many small LAPACK calls run fastest single-threaded;
+        # set before numpy loads its BLAS
+        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        if args.oracle_solve:
+            oracle_solve_sample(args)
+        else:
+            run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

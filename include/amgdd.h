@@ -1,0 +1,217 @@
+/*
+ * amgdd.h -- C ABI of the GB300 LS-AMG-DD library (libamgdd.so).
+ *
+ * Multilevel least-squares AMG with overlapping Schwarz smoothers and local
+ * spectral coarse spaces (Southworth, Al Daas, Wimmer, Threlfall, "Algebraic
+ * Multigrid with Overlapping Schwarz Smoothers and Local Spectral Coarse
+ * Grids for Least Squares Problems").  The system is A x = b with
+ *
+ *     A = D1 + G^T G,   G sparse m x n                     (Section 1, Eq. 1)
+ *
+ * (D1 >= 0 diagonal; it is the sqrt(D1) block of G^T = [sqrt(D1), ...]).
+ * `amgdd_setup` builds the hierarchy of Algorithm 1 on one GPU; `amgdd_solve`
+ * runs conjugate gradients preconditioned by the V-cycle of Section 3.1 (one
+ * RAS pre-smoothing, Eq. ras; coarse-grid correction, Eq. cgc; one RAS-T
+ * post-smoothing, Eq. ras-t; exact solve on the coarsest level).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: AMGDD_OK (0) or a negative AMGDD_ERR_* code; no call
+ *     throws or aborts.  `amgdd_last_error()` gives a one-line description
+ *     of the last failure on the calling thread.
+ *   - Pointers are plain host or device addresses.  Where an argument may be
+ *     either, the library asks the CUDA runtime which it is.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work of a call is ordered on that stream; calls
+ *     that return host data synchronise it first.
+ *   - Sizes are element counts.  Index arrays are int32 (node and column
+ *     ids); offsets are int64.
+ *   - Every routine requires a CUDA device; there is no CPU fallback.
+ */
+#ifndef AMGDD_H
+#define AMGDD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define AMGDD_OK 0
+#define AMGDD_ERR_INVALID_ARG -1    /* malformed input (CSR, ids, sizes)   */
+#define AMGDD_ERR_NOT_SPD -2        /* a local or coarsest block is not SPD */
+#define AMGDD_ERR_NONFINITE -3      /* NaN/Inf in G, D1 or b               */
+#define AMGDD_ERR_BREAKDOWN -4      /* CG: p^T A p <= 0                    */
+#define AMGDD_ERR_NO_CONVERGENCE -5 /* CG reached max_iter                 */
+#define AMGDD_ERR_OOM -6            /* device allocation failed            */
+#define AMGDD_ERR_CUDA -7           /* any other CUDA runtime error        */
+#define AMGDD_ERR_INTERNAL -8       /* violated internal invariant         */
+
+/* ---- memory spaces and precisions ------------------------------------ */
+#define AMGDD_HOST 0
+#define AMGDD_DEVICE 1
+
+/* FP64: every vector, local inverse and basis in double precision.
+ * MIXED32: the V-cycle (local Schwarz solves, P/R, level operators, vectors)
+ * in FP32 under an FP64 flexible CG whose residual, inner products, updates
+ * and fine-level A-apply stay FP64; the coarsest solve stays FP64.         */
+#define AMGDD_FP64 0
+#define AMGDD_MIXED32 1
+
+/* ---- inputs ----------------------------------------------------------- */
+/* G in CSR form.  rowptr has m+1 entries (rowptr[0] = 0, nondecreasing,
+ * rowptr[m] = nnz); col holds strictly increasing column ids in [0, n) per
+ * row; val the values.  Every listed entry is structural, zero or not.
+ * `mem` says where the three arrays live (AMGDD_HOST or AMGDD_DEVICE).   */
+typedef struct {
+  int64_t m, n, nnz;
+  const int64_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  int mem;
+} amgdd_csr;
+
+/* Method parameters (Algorithm 1 inputs and solver options).            */
+typedef struct {
+  int L_max;           /* maximum number of levels (Algorithm 1)          */
+  int64_t n_coarse;    /* coarsen while n_l > n_coarse                    */
+  double thresh;       /* keep local eigenpairs with lambda > thresh      */
+  int c_min[8];        /* minimum coarsening ratio per level; the last    */
+  int n_cmin;          /*   entry repeats for deeper levels (LS_{a,b,..}) */
+  int precision;       /* AMGDD_FP64 or AMGDD_MIXED32                     */
+  int max_iter;        /* CG iteration limit                              */
+  double schur_rtol;   /* pivots of A~_GG below schur_rtol * max diag are */
+                       /*   treated as zero (pseudo-inverse reading)      */
+  int use_graph;       /* capture the CG iteration in a CUDA graph        */
+  int check_every;     /* host reads the convergence flag every k iters   */
+} amgdd_params;
+
+typedef struct amgdd_hierarchy amgdd_hierarchy; /* opaque, library-owned */
+
+/* Per right-hand-side result of amgdd_solve.                            */
+typedef struct {
+  int iters;           /* CG iterations (A-applications)                  */
+  int status;          /* AMGDD_OK, _BREAKDOWN or _NO_CONVERGENCE         */
+  double relres;       /* ||r_k|| / ||b|| of the recursively updated r    */
+  double relres_true;  /* ||b - A x|| / ||b|| recomputed at the end (FP64) */
+  double solve_ms;     /* device time of this right-hand side             */
+} amgdd_info;
+
+/* Defaults: L_max 10, n_coarse 2000, thresh 0.1, c_min = {2,3,4} (LS_{2,3,4}),
+ * FP64, max_iter 1000, schur_rtol 1e-12, graphs on, check_every 4.      */
+amgdd_params amgdd_params_default(void);
+
+/* ---- setup: Algorithm 1 ---------------------------------------------- */
+/* Builds the hierarchy {G_l, P_l, smoothers} for A = D1 + G^T G.
+ *   G        : CSR as above (copied; the caller keeps ownership).
+ *   D1       : n diagonal entries (>= 0) or NULL for D1 = 0; host or device.
+ *   agg      : n level-0 aggregate ids (host or device).  Ids >= 0 name
+ *              aggregates; -1 marks an unaggregated node, which joins the
+ *              smallest aggregate id among its neighbours in the graph of A
+ *              (Section 3.3); ids are relabelled 0..nagg-1 in ascending
+ *              order, skipping unused ids.
+ *   overlap  : number of graph hops added around each aggregate (>= 1)
+ *              to form Omega_i = omega_i u Gamma_i (Section 2.2).
+ *   params   : NULL for amgdd_params_default().
+ *   out      : receives the hierarchy, freed with amgdd_free.
+ * Errors: INVALID_ARG (bad CSR/ids/params), NONFINITE, NOT_SPD (a block
+ * A(Omega_i, Omega_i) or the coarsest matrix failed Cholesky), OOM, CUDA. */
+int amgdd_setup(const amgdd_csr* G, const double* D1, const int32_t* agg, int overlap,
+                const amgdd_params* params, void* stream, amgdd_hierarchy** out);
+
+/* ---- solve: V-cycle preconditioned CG -------------------------------- */
+/* Solves A x = b for nrhs independent right-hand sides stored column-major
+ * (n x nrhs, leading dimension n).  b and x may be host or device pointers
+ * (each is classified on its own); x is overwritten (x_0 = 0).  Stops when
+ * ||r_k|| <= tol ||b|| on the recursively updated residual (the check runs
+ * every params.check_every iterations; iterations after convergence leave x
+ * unchanged).  info (host, nrhs entries) may be NULL.
+ * Returns the first non-OK per-RHS status, or an error code.             */
+int amgdd_solve(amgdd_hierarchy* h, const double* b, int nrhs, double tol, double* x, void* stream,
+                amgdd_info* info);
+
+/* Switches the precision used by later solves (the hierarchy stores both). */
+int amgdd_set_precision(amgdd_hierarchy* h, int precision);
+
+/* ---- single steps of the cycle (device FP64 vectors; for testing) ---- */
+#define AMGDD_OP_A 0        /* y = A_l x                    (Eq. 1)       */
+#define AMGDD_OP_RAS 1      /* y = M_RAS^{-1} x             (Eq. ras)     */
+#define AMGDD_OP_RAST 2     /* y = M_RAS-T^{-1} x           (Eq. ras-t)   */
+#define AMGDD_OP_RESTRICT 3 /* y = P_l^T x  (length n_{l+1}) (Eq. mg-p)   */
+#define AMGDD_OP_PROLONG 4  /* y = P_l x    (x of length n_{l+1})         */
+#define AMGDD_OP_VCYCLE 5   /* y = B_l x: V-cycle from level l, x_0 = 0   */
+#define AMGDD_OP_COARSE 6   /* y = A_L^{-1} x on the coarsest level       */
+/* Applies one operator of level `level` in the hierarchy's current
+ * precision; x and y are device arrays of FP64 (converted internally in
+ * MIXED32).  x and y must not alias.                                     */
+int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* y, void* stream);
+
+/* ---- inspection ------------------------------------------------------ */
+typedef struct {
+  int64_t n;           /* unknowns on this level                          */
+  int64_t nagg;        /* aggregates (0 on the coarsest level)            */
+  int64_t n_next;      /* n_{l+1} (0 on the coarsest level)               */
+  int64_t omega_len;   /* sum_i |Omega_i|                                 */
+  int64_t z_len;       /* sum_i |omega_i| k_i                             */
+  int64_t ngroups;     /* row groups of G_l                               */
+  int64_t g_rows;      /* sum of compressed row counts of G_l             */
+  int64_t g_vals;      /* stored values of G_l (rows x support)           */
+  int64_t w_vals;      /* stored values of the smoother, sum |omega||Omega| */
+  int is_coarsest;
+} amgdd_level_desc;
+
+int amgdd_num_levels(const amgdd_hierarchy* h);
+int amgdd_level_describe(const amgdd_hierarchy* h, int level, amgdd_level_desc* out);
+
+/* Copies one array of a level to host memory `dst` of `cap` bytes.
+ *   AGG       int32[n]         aggregate id of each dof
+ *   OMEGA_PTR int64[nagg+1]    offsets into OMEGA_IDX
+ *   OMEGA_IDX int32[omega_len] Omega_i: omega_i ascending, then Gamma_i ascending
+ *   NOMEGA    int32[nagg]      |omega_i|
+ *   K         int32[nagg]      k_i, selected eigenvectors
+ *   Z         double[z_len]    Z_i row-major |omega_i| x k_i, aggregate order;
+ *                              columns ordered by ascending mu, normalised so
+ *                              Z_i^T A_ww Z_i = I, largest |entry| positive
+ *   MU        double[sum |omega_i|] all local eigenvalues mu = 1/lambda, ascending */
+#define AMGDD_ARR_AGG 0
+#define AMGDD_ARR_OMEGA_PTR 1
+#define AMGDD_ARR_OMEGA_IDX 2
+#define AMGDD_ARR_NOMEGA 3
+#define AMGDD_ARR_K 4
+#define AMGDD_ARR_Z 5
+#define AMGDD_ARR_MU 6
+int amgdd_level_export(const amgdd_hierarchy* h, int level, int which, void* dst, size_t cap);
+
+/* JSON summary (levels, n_l, row groups, stored values, operator
+ * complexity, algorithmic bytes per V-cycle, setup time) into json[cap].  */
+int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap);
+
+/* Algorithmic bytes one V-cycle must move in the current precision, and
+ * those of one FP64 fine-level A-apply (used by the roofline report).    */
+int amgdd_bytes_model(const amgdd_hierarchy* h, double* vcycle_bytes, double* apply_bytes);
+
+/* ---- measurement ----------------------------------------------------- */
+/* Times `reps` V-cycles from level 0 in the current precision with CUDA
+ * events recorded between the launches on the library's work stream, and
+ * reports per level l and step slot the mean device milliseconds per cycle
+ * (ms[l*8 + slot]) and the algorithmic bytes that step moves
+ * (bytes[l*8 + slot]: stored matrix values, index arrays, and one pass over
+ * each input and output vector).  Slots: 0 RAS (or the coarsest solve),
+ * 1 residual copies (casts on the coarsest level), 2 residual A-applies,
+ * 3 restriction, 4 prolongation, 5 cast back (coarsest level), 7 RAS-T.
+ * cap >= 8 * amgdd_num_levels(h).                                        */
+int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes, int cap);
+
+/* Kernels this library has launched in the process so far (a replay of a
+ * captured CUDA graph counts every kernel in it).                         */
+int64_t amgdd_kernel_launches(void);
+
+void amgdd_free(amgdd_hierarchy* h);
+const char* amgdd_status_string(int status);
+const char* amgdd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMGDD_H */

@@ -17,8 +17,8 @@ For each level l (Algorithm 1), while l < L_max - 1 and n_l > n_coarse:
      solved as S~ u = mu A_ww u, mu = 1/lambda ascending, so the largest
      lambda come first;
   6. selection: all lambda > thresh, at most max(1, floor(|omega_i|/c_l))
-     (Section 3.4); Z_i normalised so Z_i^T A_ww Z_i = I and the entry of
-     largest magnitude of each column is positive;
+     (Section 3.4); Z_i normalised so Z_i^T A_ww Z_i = I and the first entry
+     within (1 - 1e-6) of the column's largest magnitude is positive;
   7. P_l = [R_{omega_1}^T Z_1 ... ] (Eq. mg-p), columns ordered by aggregate
      then by ascending mu;
   8. G_{l+1} = G_l P_l, A_{l+1} = G_{l+1}^T G_{l+1} (Section 3.1,
@@ -90,13 +90,13 @@ def assemble_A(sups, grams, n):
     return A
 
 
-def local_splitting(Omega_i, nz_i, sups, grams, M, n_scratch=None):
+def local_splitting(Omega_i, nz_i, sups, grams, M):
     """A~_i of the Lemma: sum over rows in nz_i of g^T W g, embedded in Omega_i."""
     m = Omega_i.shape[0]
-    loc = {int(j): t for t, j in enumerate(Omega_i)}
+    order = np.argsort(Omega_i)
     At = np.zeros((m, m))
     for g in nz_i:
-        p = np.array([loc[int(j)] for j in sups[g]])
+        p = order[np.searchsorted(Omega_i, sups[g], sorter=order)]
         At[np.ix_(p, p)] += grams[g] / M[g]
     return At
 
@@ -130,8 +130,11 @@ def local_gep(S, Aww, cap, thresh):
 
     Solves S~ u = mu A_ww u (mu = 1/lambda, ascending).  Keeps the first
     k = min(#{lambda > thresh}, cap) columns; mu <= 0 counts as lambda = inf.
-    Returns (mu_all, Z) with Z^T A_ww Z = I, largest-magnitude entry of each
-    column positive (first index on ties).
+    Returns (mu_all, Z) with Z^T A_ww Z = I.  Sign (the paper fixes none):
+    the first entry whose magnitude is within a factor (1 - 1e-6) of the
+    column's largest is made positive, so that entries equal in magnitude in
+    exact arithmetic (symmetric or antisymmetric modes of symmetric
+    aggregates) cannot trade places under rounding.
     """
     mu, V = sla.eigh(S, Aww)
     if thresh > 0:
@@ -141,7 +144,8 @@ def local_gep(S, Aww, cap, thresh):
     k = min(count, cap)
     Z = V[:, :k].copy()
     for c in range(k):
-        j = int(np.argmax(np.abs(Z[:, c])))
+        a = np.abs(Z[:, c])
+        j = int(np.nonzero(a >= (1.0 - 1e-6) * a.max())[0][0])
         if Z[j, c] < 0:
             Z[:, c] = -Z[:, c]
     return mu, Z
@@ -175,11 +179,19 @@ def _next_groups(level):
     aggregate the row touches, and g^T g becomes P^T (g^T g) P restricted to
     those columns.
     """
-    P = level.P.tocsr()
+    # row j of P is Z_a(position of j in omega_a, :) in the columns of a
+    pos = np.zeros(level.n, dtype=np.int64)
+    for i in range(level.nagg):
+        pos[level.omega[i]] = np.arange(level.omega[i].shape[0])
     merged = {}
     for s, H, t in zip(level.sups, level.grams, level.touched):
         cs = np.concatenate([np.arange(level.col0[a], level.col0[a] + level.k[a]) for a in t])
-        Pg = P[s][:, cs].toarray()
+        Pg = np.zeros((s.shape[0], cs.shape[0]))  # P(S_g, S'_g)
+        off = np.concatenate([[0], np.cumsum([level.k[a] for a in t])])
+        for r, j in enumerate(s):
+            a = int(level.agg[j])
+            c = int(np.searchsorted(t, a))
+            Pg[r, off[c]:off[c + 1]] = level.Z[a][pos[j]]
         Hn = Pg.T @ H @ Pg
         key = tuple(int(a) for a in t)
         if key in merged:

@@ -1,0 +1,254 @@
+"""Python binding of libamgdd (GB300 LS-AMG-DD): argument marshalling only.
+
+Every computation runs in the CUDA library declared by include/amgdd.h; this
+module loads it with ctypes, converts arguments to plain pointers and sizes,
+and raises on a non-OK status.  There is no CPU fallback: importing works
+without a GPU, but every call needs the built library and a CUDA device.
+
+Host arrays are numpy arrays; device arrays are torch CUDA tensors (torch is
+used for device memory and streams only).
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libamgdd.so")
+
+AMGDD_OK = 0
+STATUS = {0: "ok", -1: "invalid argument", -2: "not SPD", -3: "non-finite", -4: "CG breakdown",
+          -5: "no convergence", -6: "out of device memory", -7: "CUDA error", -8: "internal error"}
+HOST, DEVICE = 0, 1
+FP64, MIXED32 = 0, 1
+OP_A, OP_RAS, OP_RAST, OP_RESTRICT, OP_PROLONG, OP_VCYCLE, OP_COARSE = range(7)
+ARR_AGG, ARR_OMEGA_PTR, ARR_OMEGA_IDX, ARR_NOMEGA, ARR_K, ARR_Z, ARR_MU = range(7)
+
+EXPORTED = [
+    "amgdd_params_default", "amgdd_setup", "amgdd_solve", "amgdd_set_precision", "amgdd_apply",
+    "amgdd_num_levels", "amgdd_level_describe", "amgdd_level_export", "amgdd_hierarchy_stats",
+    "amgdd_bytes_model", "amgdd_free", "amgdd_status_string", "amgdd_last_error", "amgdd_profile_vcycle",
+    "amgdd_kernel_launches",
+]
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("mem", ctypes.c_int)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("L_max", ctypes.c_int), ("n_coarse", ctypes.c_int64), ("thresh", ctypes.c_double),
+                ("c_min", ctypes.c_int * 8), ("n_cmin", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("schur_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
+                ("check_every", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("relres", ctypes.c_double),
+                ("relres_true", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+
+class LevelDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nagg", ctypes.c_int64), ("n_next", ctypes.c_int64),
+                ("omega_len", ctypes.c_int64), ("z_len", ctypes.c_int64), ("ngroups", ctypes.c_int64),
+                ("g_rows", ctypes.c_int64), ("g_vals", ctypes.c_int64), ("w_vals", ctypes.c_int64),
+                ("is_coarsest", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libamgdd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libamgdd.so not found at {path}; build it with "
+                           "`python -m paper_2601_04112_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    lib.amgdd_params_default.restype = Params
+    lib.amgdd_setup.argtypes = [ctypes.POINTER(Csr), vp, vp, i32, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]
+    lib.amgdd_solve.argtypes = [vp, vp, i32, dbl, vp, vp, ctypes.POINTER(Info)]
+    lib.amgdd_set_precision.argtypes = [vp, i32]
+    lib.amgdd_apply.argtypes = [vp, i32, i32, vp, vp, vp]
+    lib.amgdd_num_levels.argtypes = [vp]
+    lib.amgdd_level_describe.argtypes = [vp, i32, ctypes.POINTER(LevelDesc)]
+    lib.amgdd_level_export.argtypes = [vp, i32, i32, vp, ctypes.c_size_t]
+    lib.amgdd_hierarchy_stats.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.amgdd_bytes_model.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    lib.amgdd_free.argtypes = [vp]
+    lib.amgdd_free.restype = None
+    lib.amgdd_status_string.argtypes = [i32]
+    lib.amgdd_status_string.restype = ctypes.c_char_p
+    lib.amgdd_last_error.restype = ctypes.c_char_p
+    lib.amgdd_profile_vcycle.argtypes = [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl), i32]
+    lib.amgdd_profile_vcycle.restype = i32
+    lib.amgdd_kernel_launches.restype = ctypes.c_int64
+    for name in ("amgdd_setup", "amgdd_solve", "amgdd_set_precision", "amgdd_apply", "amgdd_num_levels",
+                 "amgdd_level_describe", "amgdd_level_export", "amgdd_hierarchy_stats", "amgdd_bytes_model"):
+        getattr(lib, name).restype = i32
+    _lib = lib
+    return lib
+
+
+class AmgddError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st: int):
+    if st != AMGDD_OK:
+        raise AmgddError(st, _lib.amgdd_last_error().decode())
+
+
+def _ptr(a):
+    """(pointer, is_device) of a numpy array or torch tensor."""
+    if a is None:
+        return None, False
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, False
+    return a.data_ptr(), bool(a.is_cuda)
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    import torch
+
+    return torch.cuda.current_stream().cuda_stream
+
+
+def kernel_launches() -> int:
+    return int(load_library().amgdd_kernel_launches())
+
+
+def params(**kw) -> Params:
+    lib = load_library()
+    p = lib.amgdd_params_default()
+    for k, v in kw.items():
+        if k == "c_min":
+            v = list(v)
+            for i, c in enumerate(v):
+                p.c_min[i] = int(c)
+            p.n_cmin = len(v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Hierarchy:
+    """A built LS-AMG-DD hierarchy on the current CUDA device."""
+
+    def __init__(self, rowptr, col, val, n, D1=None, agg=None, overlap=1, stream=None, **kw):
+        lib = load_library()
+        self._lib = lib
+        self._keep = []
+        rp = np.ascontiguousarray(rowptr, dtype=np.int64) if isinstance(rowptr, np.ndarray) else rowptr
+        cl = np.ascontiguousarray(col, dtype=np.int32) if isinstance(col, np.ndarray) else col
+        vl = np.ascontiguousarray(val, dtype=np.float64) if isinstance(val, np.ndarray) else val
+        ag = np.ascontiguousarray(agg, dtype=np.int32) if isinstance(agg, np.ndarray) else agg
+        d1 = np.ascontiguousarray(D1, dtype=np.float64) if isinstance(D1, np.ndarray) else D1
+        self._keep += [rp, cl, vl, ag, d1]
+        prp, dev = _ptr(rp)
+        csr = Csr(m=len(rp) - 1, n=int(n), nnz=int(len(vl)), rowptr=prp, col=_ptr(cl)[0], val=_ptr(vl)[0],
+                  mem=DEVICE if dev else HOST)
+        self.params = params(**kw)
+        h = ctypes.c_void_p()
+        _check(lib.amgdd_setup(ctypes.byref(csr), _ptr(d1)[0], _ptr(ag)[0], int(overlap), ctypes.byref(self.params),
+                               _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.n = int(n)
+        self._keep = []
+
+    @classmethod
+    def from_problem(cls, prob, overlap=1, **kw):
+        return cls(prob.rowptr, prob.col, prob.val, prob.n, D1=prob.D1, agg=prob.agg, overlap=overlap, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.amgdd_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- solve ----------------------------------------------------------------
+    def set_precision(self, precision: int):
+        _check(self._lib.amgdd_set_precision(self._h, int(precision)))
+
+    def solve(self, b, x=None, tol=1e-8, stream=None):
+        """Solve A x = b (b: n or n x nrhs, column-major); returns (x, infos)."""
+        nrhs = 1 if b.ndim == 1 else b.shape[1]
+        if isinstance(b, np.ndarray):
+            b = np.asfortranarray(b, dtype=np.float64)
+            if x is None:
+                x = np.zeros_like(b, order="F")
+        else:
+            assert b.is_contiguous() or nrhs == 1
+            if x is None:
+                import torch
+
+                x = torch.zeros_like(b)
+        infos = (Info * nrhs)()
+        st = self._lib.amgdd_solve(self._h, _ptr(b)[0], nrhs, float(tol), _ptr(x)[0], _stream(stream), infos)
+        if st not in (0, -4, -5, -3):
+            _check(st)
+        return x, [dict(iters=i.iters, status=i.status, relres=i.relres, relres_true=i.relres_true,
+                        solve_ms=i.solve_ms) for i in infos]
+
+    def apply(self, op: int, level: int, x, y, stream=None):
+        """y = op_l x on device FP64 tensors (see AMGDD_OP_*)."""
+        _check(self._lib.amgdd_apply(self._h, int(op), int(level), _ptr(x)[0], _ptr(y)[0], _stream(stream)))
+
+    # -- inspection -----------------------------------------------------------
+    @property
+    def num_levels(self) -> int:
+        return self._lib.amgdd_num_levels(self._h)
+
+    def describe(self, level: int) -> dict:
+        d = LevelDesc()
+        _check(self._lib.amgdd_level_describe(self._h, level, ctypes.byref(d)))
+        return {f: getattr(d, f) for f, _ in LevelDesc._fields_}
+
+    def export(self, level: int, which: int) -> np.ndarray:
+        d = self.describe(level)
+        nag = d["nagg"]
+        size = {ARR_AGG: (d["n"], np.int32), ARR_OMEGA_PTR: (nag + 1, np.int64),
+                ARR_OMEGA_IDX: (d["omega_len"], np.int32), ARR_NOMEGA: (nag, np.int32), ARR_K: (nag, np.int32),
+                ARR_Z: (d["z_len"], np.float64)}
+        if which == ARR_MU:
+            cnt = int(self.export(level, ARR_NOMEGA).sum())
+            size[ARR_MU] = (cnt, np.float64)
+        cnt, dt = size[which]
+        out = np.zeros(max(int(cnt), 1), dtype=dt)
+        _check(self._lib.amgdd_level_export(self._h, level, which, out.ctypes.data, out.nbytes))
+        return out[:cnt]
+
+    def stats(self) -> dict:
+        buf = ctypes.create_string_buffer(1 << 16)
+        _check(self._lib.amgdd_hierarchy_stats(self._h, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
+    def profile_vcycle(self, reps: int = 10):
+        """Per (level, slot) mean device ms and algorithmic bytes of one V-cycle."""
+        nl = self.num_levels
+        ms = (ctypes.c_double * (8 * nl))()
+        by = (ctypes.c_double * (8 * nl))()
+        _check(self._lib.amgdd_profile_vcycle(self._h, int(reps), ms, by, 8 * nl))
+        return np.array(ms).reshape(nl, 8), np.array(by).reshape(nl, 8)
+
+    def bytes_model(self):
+        v, a = ctypes.c_double(), ctypes.c_double()
+        _check(self._lib.amgdd_bytes_model(self._h, ctypes.byref(v), ctypes.byref(a)))
+        return v.value, a.value

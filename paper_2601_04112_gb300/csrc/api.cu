@@ -1,0 +1,1459 @@
+// C ABI of libamgdd and the host-side drivers: hierarchy construction
+// (Algorithm 1), the V-cycle (Section 3.1: RAS pre-smoothing, coarse-grid
+// correction, RAS-T post-smoothing, exact coarsest solve) and the
+// V-cycle-preconditioned conjugate gradient solver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "structure.h"
+
+namespace amgdd {
+
+static thread_local std::string g_last_error;
+
+static std::atomic<int64_t> g_kernels{0};
+static thread_local bool g_capturing = false;
+static thread_local int64_t g_capture_kernels = 0;
+
+void count_kernels(int64_t k) {
+  if (g_capturing)
+    g_capture_kernels += k;
+  else
+    g_kernels += k;
+}
+void capture_begin() {
+  g_capturing = true;
+  g_capture_kernels = 0;
+}
+int64_t capture_end() {
+  g_capturing = false;
+  return g_capture_kernels;
+}
+void count_graph_launch(int64_t kernels) { g_kernels += kernels; }
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+namespace {
+
+PhaseTimer g_timer;
+
+// Synchronise and charge the elapsed time to a phase (AMGDD_VERBOSE only).
+struct Phase {
+  int id;
+  const char* nm;
+  cudaStream_t s;
+  std::chrono::steady_clock::time_point t0;
+  Phase(int i, const char* n, cudaStream_t st) : id(i), nm(n), s(st), t0(std::chrono::steady_clock::now()) {}
+  ~Phase() {
+    if (!g_timer.on) return;
+    cudaStreamSynchronize(s);
+    g_timer.add(id, nm, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+  }
+};
+
+template <class T>
+int upload_vec(DBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
+  return d.upload(h, s);
+}
+
+template <class T>
+int download(std::vector<T>& h, const T* d, size_t n, cudaStream_t s) {
+  h.resize(n);
+  if (n) {
+    AMGDD_CUDA(cudaMemcpyAsync(h.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+    AMGDD_CUDA(cudaStreamSynchronize(s));
+  }
+  return AMGDD_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy n elements of a host-or-device array to a host vector.
+template <class T>
+int fetch_any(std::vector<T>& h, const T* src, size_t n, bool dev, cudaStream_t s) {
+  h.resize(n);
+  if (n == 0) return AMGDD_OK;
+  if (dev) {
+    AMGDD_CUDA(cudaMemcpyAsync(h.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+    AMGDD_CUDA(cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(h.data(), src, n * sizeof(T));
+  }
+  return AMGDD_OK;
+}
+
+int lanes_for(int max_nc) { return max_nc >= 64 ? 32 : (max_nc >= 24 ? 16 : (max_nc >= 8 ? 8 : 4)); }
+
+int build_seg(SegPlan& p, const std::vector<int32_t>& nr, const std::vector<int32_t>& nc,
+              const std::vector<int64_t>& m_off, const std::vector<int64_t>& in_off,
+              const std::vector<int64_t>& out_off, const int32_t* in_ext, const int32_t* out_ext, cudaStream_t s) {
+  p.nblocks = (int)nr.size();
+  p.max_nc = 0;
+  p.mat_len = 0;
+  int64_t rows = 0, cols = 0;
+  for (int b = 0; b < p.nblocks; ++b) {
+    p.max_nc = std::max(p.max_nc, nc[b]);
+    p.mat_len += (int64_t)nr[b] * nc[b];
+    rows += nr[b];
+    cols += nc[b];
+  }
+  p.in_len = cols;
+  p.out_len = rows;
+  p.lanes = lanes_for(p.max_nc);
+  p.rows_per_chunk = 2 * (256 / p.lanes);
+  std::vector<int32_t> cb, cr;
+  for (int b = 0; b < p.nblocks; ++b)
+    for (int r = 0; r < nr[b]; r += p.rows_per_chunk) {
+      cb.push_back(b);
+      cr.push_back(r);
+    }
+  p.nchunks = (int)cb.size();
+  p.in_idx_ext = in_ext;
+  p.out_idx_ext = out_ext;
+  AMGDD_TRY(p.nr.upload(nr, s));
+  AMGDD_TRY(p.nc.upload(nc, s));
+  AMGDD_TRY(p.m_off.upload(m_off, s));
+  AMGDD_TRY(p.in_off.upload(in_off, s));
+  AMGDD_TRY(p.out_off.upload(out_off, s));
+  AMGDD_TRY(p.chunk_blk.upload(cb, s));
+  AMGDD_TRY(p.chunk_row0.upload(cr, s));
+  return AMGDD_OK;
+}
+
+int apply_kind(int sz) {
+  if (sz <= 4) return 0;
+  if (sz <= 8) return 1;
+  if (sz <= 16) return 2;
+  if (sz <= 32) return 3;
+  if (sz <= 64) return 4;
+  if (sz <= 128) return 5;
+  if (sz <= 256) return 6;
+  if (sz <= 512) return 7;
+  if (sz <= 2048) return 8;
+  return -1;
+}
+const int kKindLanes[9] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
+
+int build_apply(Level& L, cudaStream_t s) {
+  ApplyPlan& p = L.aplan;
+  const int64_t ng = (int64_t)L.g_ptr.size() - 1;
+  std::vector<std::vector<int32_t>> tg(9), tr(9), tn(9);
+  p.r_len = 0;
+  for (int64_t g = 0; g < ng; ++g) {
+    const int sz = (int)(L.g_ptr[g + 1] - L.g_ptr[g]);
+    const int rk = L.g_rank[g];
+    if (rk == 0 || sz == 0) continue;
+    const int kd = apply_kind(sz);
+    if (kd < 0) {
+      set_error("row group with %d support columns exceeds the A-apply limit of 2048", sz);
+      return AMGDD_ERR_INTERNAL;
+    }
+    p.r_len += (int64_t)rk * sz;
+    const int chunk = sz <= 32 ? rk : 32;
+    for (int r = 0; r < rk; r += chunk) {
+      tg[kd].push_back((int32_t)g);
+      tr[kd].push_back(r);
+      tn[kd].push_back(std::min(chunk, rk - r));
+    }
+  }
+  std::vector<int32_t> ag, ar, an;
+  p.nbuckets = 0;
+  int cta = 0;
+  for (int kd = 0; kd < 9; ++kd) {
+    if (tg[kd].empty()) continue;
+    const int per = kd == 8 ? 4 : 128 / kKindLanes[kd];
+    p.bucket_kind[p.nbuckets] = kd;
+    p.bucket_start[p.nbuckets] = cta;
+    p.bucket_tasks[p.nbuckets] = (int)tg[kd].size();
+    cta += (int)((tg[kd].size() + per - 1) / per);
+    ++p.nbuckets;
+    ag.insert(ag.end(), tg[kd].begin(), tg[kd].end());
+    ar.insert(ar.end(), tr[kd].begin(), tr[kd].end());
+    an.insert(an.end(), tn[kd].begin(), tn[kd].end());
+  }
+  p.bucket_start[p.nbuckets] = cta;
+  p.ntasks = (int)ag.size();
+  AMGDD_TRY(p.task_grp.upload(ag, s));
+  AMGDD_TRY(p.task_row0.upload(ar, s));
+  AMGDD_TRY(p.task_nrow.upload(an, s));
+  return AMGDD_OK;
+}
+
+}  // namespace
+}  // namespace amgdd
+
+using namespace amgdd;
+
+struct amgdd_hierarchy {
+  amgdd_params prm{};
+  int overlap = 1;
+  int64_t n = 0;
+  int precision = AMGDD_FP64;
+  int device = 0;
+  std::vector<std::unique_ptr<Level>> lv;
+  std::vector<int64_t> nnzA;  // structural nnz of A_l
+  DBuf<int32_t> iota;
+  DBuf<double> x, r, z, zold, p, q, b, partials;
+  DBuf<PcgState> st;
+  PcgState* st_host = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int64_t gkernels[2] = {0, 0};
+  cudaStream_t work = nullptr;  // solves run here (capturable, unlike the legacy stream)
+  cudaEvent_t join[2] = {nullptr, nullptr};
+  double setup_ms = 0.0;
+  ~amgdd_hierarchy() {
+    for (auto& g : gexec)
+      if (g) cudaGraphExecDestroy(g);
+    if (st_host) cudaFreeHost(st_host);
+    for (auto& e : join)
+      if (e) cudaEventDestroy(e);
+    if (work) cudaStreamDestroy(work);
+  }
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Compression of the row groups of one level: pivoted Cholesky of each Gram.
+int compress(Level& L, cudaStream_t s) {
+  const int64_t ng = (int64_t)L.g_ptr.size() - 1;
+  const int64_t cap = L.h_off.back();
+  AMGDD_TRY(L.d_R64.alloc(cap));
+  AMGDD_TRY(L.d_R32.alloc(cap));
+  AMGDD_TRY(L.d_rank.alloc(ng));
+  int max_s = 1;
+  for (int64_t g = 0; g < ng; ++g) max_s = std::max(max_s, (int)(L.g_ptr[g + 1] - L.g_ptr[g]));
+  const int64_t per = (int64_t)max_s * max_s;
+  int64_t chunk = std::max<int64_t>(1, (int64_t)(32 << 20) / per);
+  chunk = std::min<int64_t>(chunk, std::max<int64_t>(ng, 1));
+  DBuf<double> scratch;
+  AMGDD_TRY(scratch.alloc(chunk * per));
+  for (int64_t f = 0; f < ng; f += chunk) {
+    const int64_t c = std::min(chunk, ng - f);
+    AMGDD_TRY(launch_pchol(f, c, max_s, L.d_g_ptr.p, L.d_h_off.p, L.d_H.p, L.d_R64.p, L.d_R32.p, L.d_rank.p,
+                           scratch.p, per, s));
+  }
+  AMGDD_TRY(download(L.g_rank, L.d_rank.p, ng, s));
+  return build_apply(L, s);
+}
+
+int alloc_vectors(Level& L) {
+  AMGDD_TRY(L.r64.alloc(L.n));
+  AMGDD_TRY(L.x64.alloc(L.n));
+  AMGDD_TRY(L.s64.alloc(L.n));
+  AMGDD_TRY(L.r32.alloc(L.n));
+  AMGDD_TRY(L.x32.alloc(L.n));
+  AMGDD_TRY(L.s32.alloc(L.n));
+  return AMGDD_OK;
+}
+
+int64_t structural_nnz(const Level& L, const std::vector<int64_t>& nptr, const std::vector<int32_t>& ngrp) {
+  const int64_t n = L.n;
+  std::vector<int64_t> mark(n, -1);
+  int64_t tot = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    for (int64_t q = nptr[j]; q < nptr[j + 1]; ++q) {
+      const int32_t g = ngrp[q];
+      for (int64_t p = L.g_ptr[g]; p < L.g_ptr[g + 1]; ++p) {
+        const int32_t v = L.g_idx[p];
+        if (mark[v] != j) {
+          mark[v] = j;
+          ++tot;
+        }
+      }
+    }
+  }
+  return tot;
+}
+
+// Local problems of one level: smoother, splitting, eigenproblems, Z.
+int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cudaStream_t s) {
+  auto ts = std::chrono::steady_clock::now();
+  Supports S;
+  S.ptr = L.g_ptr;
+  S.idx = L.g_idx;
+  std::vector<int64_t> nptr;
+  std::vector<int32_t> ngrp;
+  node_groups(S, L.n, nptr, ngrp);
+  h.nnzA.push_back(structural_nnz(L, nptr, ngrp));
+  if (lvl == 0) {
+    if (!cleanup_aggregates(agg_in, L.n, S, nptr, ngrp, L.agg, L.nagg)) {
+      set_error("aggregate ids must be >= -1");
+      return AMGDD_ERR_INVALID_ARG;
+    }
+  }
+  const int nagg = L.nagg;
+  overlap_sets(L.agg, nagg, S, nptr, ngrp, h.overlap, L.om_ptr, L.om_idx, L.nomega);
+  std::vector<int64_t> tptr;
+  std::vector<int32_t> tids, M;
+  touched_aggregates(S, L.agg, tptr, tids, M);
+  const int c = h.prm.c_min[std::min(lvl, h.prm.n_cmin - 1)];
+  if (g_timer.on)
+    g_timer.add(0, "structure", std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count());
+  std::vector<int32_t> cap(nagg), mdim(nagg);
+  int max_m = 0, max_no = 0;
+  for (int i = 0; i < nagg; ++i) {
+    cap[i] = std::max(1, L.nomega[i] / c);
+    mdim[i] = (int32_t)(L.om_ptr[i + 1] - L.om_ptr[i]);
+    max_m = std::max(max_m, mdim[i]);
+    max_no = std::max(max_no, L.nomega[i]);
+  }
+  // level-wide device arrays
+  DBuf<int32_t> dM;
+  AMGDD_TRY(dM.upload(M, s));
+  std::vector<int64_t> w_off(nagg + 1, 0), mu_off(nagg + 1, 0);
+  for (int i = 0; i < nagg; ++i) {
+    w_off[i + 1] = w_off[i] + (int64_t)mdim[i] * L.nomega[i];
+    mu_off[i + 1] = mu_off[i] + L.nomega[i];
+  }
+  L.mu_off = mu_off;
+  AMGDD_TRY(L.W64.alloc(w_off[nagg]));
+  AMGDD_TRY(L.Wt64.alloc(w_off[nagg]));
+  AMGDD_TRY(L.W32.alloc(w_off[nagg]));
+  AMGDD_TRY(L.Wt32.alloc(w_off[nagg]));
+  AMGDD_TRY(L.mu.alloc(mu_off[nagg]));
+  DBuf<double> inv_scratch;
+  AMGDD_TRY(inv_scratch.alloc(w_off[nagg]));
+  DBuf<int64_t> d_w_off, d_mu_off;
+  AMGDD_TRY(d_w_off.upload(w_off, s));
+  AMGDD_TRY(d_mu_off.upload(mu_off, s));
+  // Z pools sized for the caps; packed tightly once k is known
+  int64_t zcap_tot = 0;
+  for (int i = 0; i < nagg; ++i) zcap_tot += (int64_t)L.nomega[i] * cap[i];
+  AMGDD_TRY(L.Z64.alloc(zcap_tot));
+  AMGDD_TRY(L.Zt64.alloc(zcap_tot));
+  AMGDD_TRY(L.Z32.alloc(zcap_tot));
+  AMGDD_TRY(L.Zt32.alloc(zcap_tot));
+  L.k.assign(nagg, 0);
+  L.z_off.assign(nagg + 1, 0);
+
+  std::vector<int32_t> loc(L.n, -1);
+  std::vector<int64_t> gstamp((size_t)(L.g_ptr.size() - 1), -1);
+  const int64_t budget = (int64_t)384 << 20;  // doubles per batch for A and A~ pools
+  int i0 = 0;
+  while (i0 < nagg) {
+    int i1 = i0;
+    int64_t pool = 0;
+    while (i1 < nagg && (i1 == i0 || pool + 2 * (int64_t)mdim[i1] * mdim[i1] <= budget)) {
+      pool += 2 * (int64_t)mdim[i1] * mdim[i1];
+      ++i1;
+    }
+    const int nb = i1 - i0;
+    // host batch description
+    std::vector<int32_t> bm(nb), bno(nb), bcap(nb), pgrp, pnz, mp;
+    std::vector<int64_t> aoff(nb + 1, 0), pptr(nb + 1, 0), mptr, zoffcap(nb + 1, 0), scroff(nb + 1, 0),
+        bw_off(nb), bmu_off(nb);
+    std::vector<int32_t> glist;
+    for (int t = 0; t < nb; ++t) {
+      const int i = i0 + t;
+      bm[t] = mdim[i];
+      bno[t] = L.nomega[i];
+      bcap[t] = cap[i];
+      aoff[t + 1] = aoff[t] + (int64_t)mdim[i] * mdim[i];
+      zoffcap[t + 1] = zoffcap[t] + (int64_t)L.nomega[i] * cap[i];
+      const int64_t nn = L.nomega[i];
+      scroff[t + 1] = scroff[t] + 5 * nn * nn + 4 * (nn + 1) + 8;
+      bw_off[t] = w_off[i];
+      bmu_off[t] = mu_off[i];
+      const int64_t o0 = L.om_ptr[i], o1 = L.om_ptr[i + 1];
+      for (int64_t q = o0; q < o1; ++q) loc[L.om_idx[q]] = (int32_t)(q - o0);
+      glist.clear();
+      for (int64_t q = o0; q < o1; ++q) {
+        const int32_t v = L.om_idx[q];
+        for (int64_t e = nptr[v]; e < nptr[v + 1]; ++e) {
+          const int32_t g = ngrp[e];
+          if (gstamp[g] != i) {
+            gstamp[g] = i;
+            glist.push_back(g);
+          }
+        }
+      }
+      std::sort(glist.begin(), glist.end());
+      for (int32_t g : glist) {
+        pgrp.push_back(g);
+        const bool nz = std::binary_search(tids.begin() + tptr[g], tids.begin() + tptr[g + 1], (int32_t)i);
+        pnz.push_back(nz ? 1 : 0);
+        mptr.push_back((int64_t)mp.size());
+        for (int64_t e = L.g_ptr[g]; e < L.g_ptr[g + 1]; ++e) mp.push_back(loc[L.g_idx[e]]);
+      }
+      pptr[t + 1] = (int64_t)pgrp.size();
+      for (int64_t q = o0; q < o1; ++q) loc[L.om_idx[q]] = -1;
+    }
+    mptr.push_back((int64_t)mp.size());
+    LocalBatch B;
+    AMGDD_TRY(B.m.upload(bm, s));
+    AMGDD_TRY(B.no.upload(bno, s));
+    AMGDD_TRY(B.a_off.upload(aoff, s));
+    AMGDD_TRY(B.pair_ptr.upload(pptr, s));
+    AMGDD_TRY(B.pair_grp.upload(pgrp, s));
+    AMGDD_TRY(B.pair_nz.upload(pnz, s));
+    AMGDD_TRY(B.map_ptr.upload(mptr, s));
+    AMGDD_TRY(B.map.upload(mp, s));
+    DBuf<int32_t> dcap, dk, dstat;
+    DBuf<int64_t> dzcap, dscr, dwoff, dmuoff;
+    AMGDD_TRY(dcap.upload(bcap, s));
+    AMGDD_TRY(dzcap.upload(zoffcap, s));
+    AMGDD_TRY(dscr.upload(scroff, s));
+    AMGDD_TRY(dwoff.upload(bw_off, s));
+    AMGDD_TRY(dmuoff.upload(bmu_off, s));
+    AMGDD_TRY(dk.alloc(nb));
+    AMGDD_TRY(dstat.alloc(nb));
+    DBuf<double> Apool, Atpool, Zcap, gscr;
+    AMGDD_TRY(Apool.alloc(aoff[nb]));
+    AMGDD_TRY(Atpool.alloc(aoff[nb]));
+    AMGDD_TRY(Zcap.alloc(std::max<int64_t>(zoffcap[nb], 1)));
+    AMGDD_TRY(gscr.alloc(scroff[nb]));
+    {
+      Phase ph(1, "assemble", s);
+      AMGDD_TRY(launch_assemble(nb, max_m, B, L.d_g_ptr.p, L.d_h_off.p, L.d_H.p, dM.p, Apool.p, Atpool.p, s));
+    }
+    {
+      Phase ph(2, "cholesky", s);
+      AMGDD_TRY(launch_chol(nb, max_m, B.m.p, B.a_off.p, Apool.p, dstat.p, s));
+    }
+    std::vector<int32_t> stat;
+    AMGDD_TRY(download(stat, dstat.p, nb, s));
+    for (int t = 0; t < nb; ++t)
+      if (stat[t] != 0) {
+        set_error("level %d: local block A(Omega_%d, Omega_%d) is not SPD (pivot %d)", lvl, i0 + t, i0 + t,
+                  stat[t] - 1);
+        return AMGDD_ERR_NOT_SPD;
+      }
+    {
+      Phase ph(3, "schur", s);
+      AMGDD_TRY(launch_schur(nb, max_m, B.m.p, B.no.p, B.a_off.p, Atpool.p, h.prm.schur_rtol, s));
+    }
+    {
+      Phase ph(4, "inverse rows", s);
+      std::vector<int32_t> cb, cc;
+      for (int t = 0; t < nb; ++t)
+        for (int c = 0; c < bno[t]; c += kInvChunk) {
+          cb.push_back(t);
+          cc.push_back(c);
+        }
+      DBuf<int32_t> dcb, dcc;
+      AMGDD_TRY(dcb.upload(cb, s));
+      AMGDD_TRY(dcc.upload(cc, s));
+      AMGDD_TRY(launch_inv_rows(nb, max_m, B.m.p, B.no.p, B.a_off.p, Apool.p, dwoff.p, L.W64.p, L.W32.p, L.Wt64.p,
+                                L.Wt32.p, inv_scratch.p, dcb.p, dcc.p, (int)cb.size(), kInvChunk, s));
+      AMGDD_CUDA(cudaStreamSynchronize(s));
+    }
+    {
+      Phase ph(5, "eigen", s);
+      AMGDD_TRY(launch_gep(nb, max_no, B.m.p, B.no.p, B.a_off.p, Apool.p, Atpool.p, dcap.p, h.prm.thresh, dmuoff.p,
+                           L.mu.p, dzcap.p, Zcap.p, dk.p, gscr.p, dscr.p, s));
+    }
+    std::vector<int32_t> kb;
+    AMGDD_TRY(download(kb, dk.p, nb, s));
+    std::vector<int64_t> zoff_b(nb);
+    for (int t = 0; t < nb; ++t) {
+      const int i = i0 + t;
+      L.k[i] = kb[t];
+      zoff_b[t] = L.z_off[i];
+      L.z_off[i + 1] = L.z_off[i] + (int64_t)L.nomega[i] * kb[t];
+    }
+    DBuf<int64_t> dzoff;
+    AMGDD_TRY(dzoff.upload(zoff_b, s));
+    AMGDD_TRY(launch_pack_z(nb, B.no.p, dk.p, dzcap.p, Zcap.p, dzoff.p, L.Z64.p, L.Z32.p, L.Zt64.p, L.Zt32.p, s));
+    AMGDD_CUDA(cudaStreamSynchronize(s));
+    i0 = i1;
+  }
+  L.col0.assign(nagg + 1, 0);
+  for (int i = 0; i < nagg; ++i) L.col0[i + 1] = L.col0[i] + L.k[i];
+  return AMGDD_OK;
+}
+
+int build_plans(amgdd_hierarchy& h, Level& L, DBuf<int32_t>& d_om_idx, cudaStream_t s) {
+  const int nagg = L.nagg;
+  AMGDD_TRY(d_om_idx.upload(L.om_idx, s));
+  std::vector<int32_t> nr(nagg), nc(nagg);
+  std::vector<int64_t> moff(nagg), ioff(nagg), ooff(nagg);
+  std::vector<int64_t> w_off(nagg + 1, 0);
+  for (int i = 0; i < nagg; ++i)
+    w_off[i + 1] = w_off[i] + (int64_t)L.nomega[i] * (L.om_ptr[i + 1] - L.om_ptr[i]);
+  // RAS: x(omega_i) = W_i r(Omega_i)
+  for (int i = 0; i < nagg; ++i) {
+    nr[i] = L.nomega[i];
+    nc[i] = (int32_t)(L.om_ptr[i + 1] - L.om_ptr[i]);
+    moff[i] = w_off[i];
+    ioff[i] = L.om_ptr[i];
+    ooff[i] = L.om_ptr[i];
+  }
+  AMGDD_TRY(build_seg(L.ras, nr, nc, moff, ioff, ooff, d_om_idx.p, d_om_idx.p, s));
+  // RAS-T: x(Omega_i) += W_i^T s(omega_i)
+  for (int i = 0; i < nagg; ++i) std::swap(nr[i], nc[i]);
+  AMGDD_TRY(build_seg(L.rast, nr, nc, moff, ioff, ooff, d_om_idx.p, d_om_idx.p, s));
+  // restriction: r_c[col0_i + c] = (Z_i^T s(omega_i))_c
+  for (int i = 0; i < nagg; ++i) {
+    nr[i] = L.k[i];
+    nc[i] = L.nomega[i];
+    moff[i] = L.z_off[i];
+    ioff[i] = L.om_ptr[i];
+    ooff[i] = L.col0[i];
+  }
+  AMGDD_TRY(build_seg(L.restr, nr, nc, moff, ioff, ooff, d_om_idx.p, h.iota.p, s));
+  // prolongation: x(omega_i) += Z_i x_c[col0_i ...]
+  for (int i = 0; i < nagg; ++i) {
+    nr[i] = L.nomega[i];
+    nc[i] = L.k[i];
+    ioff[i] = L.col0[i];
+    ooff[i] = L.om_ptr[i];
+  }
+  AMGDD_TRY(build_seg(L.prol, nr, nc, moff, ioff, ooff, h.iota.p, d_om_idx.p, s));
+  return AMGDD_OK;
+}
+
+// Supports and Grams of G_{l+1} = G_l P_l; aggregates of level l+1.
+int build_next(amgdd_hierarchy& h, Level& L, Level& N, cudaStream_t s) {
+  (void)h;
+  Supports S;
+  S.ptr = L.g_ptr;
+  S.idx = L.g_idx;
+  std::vector<int64_t> tptr;
+  std::vector<int32_t> tids, M;
+  touched_aggregates(S, L.agg, tptr, tids, M);
+  const int64_t ng = S.size();
+  std::map<std::vector<int32_t>, int64_t> keys;
+  for (int64_t g = 0; g < ng; ++g) keys.emplace(std::vector<int32_t>(tids.begin() + tptr[g], tids.begin() + tptr[g + 1]), 0);
+  int64_t h_id = 0;
+  N.g_ptr.assign(1, 0);
+  N.g_idx.clear();
+  for (auto& kv : keys) {
+    kv.second = h_id++;
+    for (int32_t a : kv.first)
+      for (int64_t c = L.col0[a]; c < L.col0[a + 1]; ++c) N.g_idx.push_back((int32_t)c);
+    N.g_ptr.push_back((int64_t)N.g_idx.size());
+  }
+  const int64_t nnew = h_id;
+  N.h_off.assign(nnew + 1, 0);
+  int max_sn = 1;
+  for (int64_t q = 0; q < nnew; ++q) {
+    const int64_t sn = N.g_ptr[q + 1] - N.g_ptr[q];
+    max_sn = std::max<int>(max_sn, (int)sn);
+    N.h_off[q + 1] = N.h_off[q] + sn * sn;
+  }
+  // contributions and per-support-node Z rows
+  std::vector<int64_t> owner(ng);
+  std::vector<int64_t> cnt(nnew + 1, 0);
+  for (int64_t g = 0; g < ng; ++g) {
+    owner[g] = keys[std::vector<int32_t>(tids.begin() + tptr[g], tids.begin() + tptr[g + 1])];
+    cnt[owner[g] + 1]++;
+  }
+  for (int64_t q = 0; q < nnew; ++q) cnt[q + 1] += cnt[q];
+  std::vector<int32_t> contrib(ng);
+  {
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t g = 0; g < ng; ++g) contrib[fill[owner[g]]++] = (int32_t)g;
+  }
+  std::vector<int32_t> pos(L.n, 0);
+  for (int i = 0; i < L.nagg; ++i)
+    for (int t = 0; t < L.nomega[i]; ++t) pos[L.om_idx[L.om_ptr[i] + t]] = t;
+  std::vector<int64_t> rz_ptr(ng + 1, 0), rz_zoff;
+  std::vector<int32_t> rz_k, rz_col;
+  int max_s = 1;
+  for (int64_t g = 0; g < ng; ++g) {
+    max_s = std::max(max_s, S.len(g));
+    for (int64_t e = S.ptr[g]; e < S.ptr[g + 1]; ++e) {
+      const int32_t v = S.idx[e];
+      const int32_t a = L.agg[v];
+      int64_t col = 0;
+      for (int64_t t = tptr[g]; t < tptr[g + 1] && tids[t] < a; ++t) col += L.k[tids[t]];
+      rz_zoff.push_back(L.z_off[a] + (int64_t)pos[v] * L.k[a]);
+      rz_k.push_back(L.k[a]);
+      rz_col.push_back((int32_t)col);
+    }
+    rz_ptr[g + 1] = (int64_t)rz_zoff.size();
+  }
+  NextGramPlan P;
+  P.nnew = nnew;
+  AMGDD_TRY(P.new_ptr.upload(cnt, s));
+  AMGDD_TRY(P.contrib.upload(contrib, s));
+  AMGDD_TRY(P.new_sptr.upload(N.g_ptr, s));
+  AMGDD_TRY(P.new_hoff.upload(N.h_off, s));
+  AMGDD_TRY(P.rowz_ptr.upload(rz_ptr, s));
+  AMGDD_TRY(P.rowz_zoff.upload(rz_zoff, s));
+  AMGDD_TRY(P.rowz_k.upload(rz_k, s));
+  AMGDD_TRY(P.rowz_col.upload(rz_col, s));
+  P.scratch_per = (int64_t)max_s * max_sn;
+  AMGDD_TRY(N.d_H.alloc(std::max<int64_t>(N.h_off[nnew], 1)));
+  int64_t chunk = std::max<int64_t>(1, (int64_t)(32 << 20) / P.scratch_per);
+  chunk = std::min<int64_t>(chunk, std::max<int64_t>(nnew, 1));
+  DBuf<double> scratch;
+  AMGDD_TRY(scratch.alloc(chunk * P.scratch_per));
+  for (int64_t f = 0; f < nnew; f += chunk) {
+    const int64_t c = std::min(chunk, nnew - f);
+    AMGDD_TRY(launch_next_gram(P, max_sn, L.d_g_ptr.p, L.d_h_off.p, L.d_H.p, L.Z64.p, N.d_H.p, scratch.p, f, c, s));
+  }
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  N.n = L.col0[L.nagg];
+  AMGDD_TRY(N.d_g_ptr.upload(N.g_ptr, s));
+  AMGDD_TRY(N.d_g_idx.upload(N.g_idx, s));
+  AMGDD_TRY(N.d_h_off.upload(N.h_off, s));
+  // aggregates of level l+1: whole blocks of coarse dofs
+  std::vector<int32_t> bagg;
+  int nn = 0;
+  block_aggregation(L.nagg, tptr, tids, bagg, nn);
+  N.agg.assign(N.n, 0);
+  for (int a = 0; a < L.nagg; ++a)
+    for (int64_t c = L.col0[a]; c < L.col0[a + 1]; ++c) N.agg[c] = bagg[a];
+  N.nagg = nn;
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  return AMGDD_OK;
+}
+
+// Coarsest level: dense A_L, Cholesky, explicit inverse (one block).
+int build_coarsest(amgdd_hierarchy& h, Level& L, cudaStream_t s) {
+  const int64_t m = L.n;
+  if (m > 24000) {
+    set_error("coarsest level has %lld unknowns; raise L_max or lower n_coarse", (long long)m);
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  L.coarsest = true;
+  Supports S;
+  S.ptr = L.g_ptr;
+  S.idx = L.g_idx;
+  std::vector<int64_t> nptr;
+  std::vector<int32_t> ngrp;
+  node_groups(S, L.n, nptr, ngrp);
+  h.nnzA.push_back(structural_nnz(L, nptr, ngrp));
+  const int64_t ng = S.size();
+  std::vector<int32_t> bm{(int32_t)m}, bno{(int32_t)m}, pgrp(ng), pnz(ng, 0), mp(L.g_idx.begin(), L.g_idx.end());
+  std::vector<int64_t> aoff{0, m * m}, pptr{0, ng}, mptr(L.g_ptr.begin(), L.g_ptr.end());
+  std::iota(pgrp.begin(), pgrp.end(), 0);
+  std::vector<int32_t> Mv(ng, 1);
+  LocalBatch B;
+  AMGDD_TRY(B.m.upload(bm, s));
+  AMGDD_TRY(B.no.upload(bno, s));
+  AMGDD_TRY(B.a_off.upload(aoff, s));
+  AMGDD_TRY(B.pair_ptr.upload(pptr, s));
+  AMGDD_TRY(B.pair_grp.upload(pgrp, s));
+  AMGDD_TRY(B.pair_nz.upload(pnz, s));
+  AMGDD_TRY(B.map_ptr.upload(mptr, s));
+  AMGDD_TRY(B.map.upload(mp, s));
+  DBuf<int32_t> dM, dstat;
+  AMGDD_TRY(dM.upload(Mv, s));
+  AMGDD_TRY(dstat.alloc(1));
+  DBuf<double> Apool, Atpool, scratch;
+  AMGDD_TRY(Apool.alloc(m * m));
+  AMGDD_TRY(Atpool.alloc(m * m));
+  AMGDD_TRY(scratch.alloc(m * m));
+  AMGDD_TRY(launch_assemble(1, (int)m, B, L.d_g_ptr.p, L.d_h_off.p, L.d_H.p, dM.p, Apool.p, Atpool.p, s));
+  AMGDD_TRY(launch_chol(1, (int)m, B.m.p, B.a_off.p, Apool.p, dstat.p, s));
+  std::vector<int32_t> stat;
+  AMGDD_TRY(download(stat, dstat.p, 1, s));
+  if (stat[0] != 0) {
+    set_error("coarsest matrix (n = %lld) is not SPD (pivot %d)", (long long)m, stat[0] - 1);
+    return AMGDD_ERR_NOT_SPD;
+  }
+  AMGDD_TRY(L.W64.alloc(m * m));
+  AMGDD_TRY(L.Wt64.alloc(m * m));
+  AMGDD_TRY(L.W32.alloc(m * m));
+  AMGDD_TRY(L.Wt32.alloc(m * m));
+  std::vector<int64_t> woff{0};
+  DBuf<int64_t> dwoff;
+  AMGDD_TRY(dwoff.upload(woff, s));
+  {
+    std::vector<int32_t> cb, cc;
+    for (int64_t c = 0; c < m; c += kInvChunk) {
+      cb.push_back(0);
+      cc.push_back((int32_t)c);
+    }
+    DBuf<int32_t> dcb, dcc;
+    AMGDD_TRY(dcb.upload(cb, s));
+    AMGDD_TRY(dcc.upload(cc, s));
+    AMGDD_TRY(launch_inv_rows(1, (int)m, B.m.p, B.no.p, B.a_off.p, Apool.p, dwoff.p, L.W64.p, L.W32.p, L.Wt64.p,
+                              L.Wt32.p, scratch.p, dcb.p, dcc.p, (int)cb.size(), kInvChunk, s));
+  }
+  std::vector<int32_t> nr{(int32_t)m}, nc{(int32_t)m};
+  std::vector<int64_t> moff{0}, ioff{0}, ooff{0};
+  AMGDD_TRY(build_seg(L.ras, nr, nc, moff, ioff, ooff, h.iota.p, h.iota.p, s));
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  return AMGDD_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Event marks between the launches of one V-cycle (profiling only): the time
+// from mark i to mark i+1 is charged to (level, slot) of mark i.
+struct VProf {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> tag;  // level * kSlots + slot, -1 for the final mark
+  size_t used = 0;
+  static constexpr int kSlots = 8;
+  int mark(cudaStream_t s, int level, int slot) {
+    if (used == ev.size()) {
+      cudaEvent_t e;
+      AMGDD_CUDA(cudaEventCreate(&e));
+      ev.push_back(e);
+      tag.push_back(0);
+    }
+    tag[used] = level < 0 ? -1 : level * kSlots + slot;
+    AMGDD_CUDA(cudaEventRecord(ev[used], s));
+    ++used;
+    return AMGDD_OK;
+  }
+  ~VProf() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+#define AMGDD_MARK(slot) \
+  if (prof) AMGDD_TRY(prof->mark(s, l, (slot)))
+
+// V-cycle of Section 3.1 from level l: z = B_l r.
+static int vcycle(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, const int* skip, cudaStream_t s,
+                  VProf* prof = nullptr) {
+  Level& L = *h.lv[l];
+  if (L.coarsest) {
+    if (f32) {
+      AMGDD_MARK(1);
+      AMGDD_TRY(launch_cast(r, true, L.r64.p, false, L.n, skip, s));
+      AMGDD_MARK(0);
+      AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, L.r64.p, L.x64.p, false, SEG_STORE, skip, s));
+      AMGDD_MARK(5);
+      return launch_cast(L.x64.p, false, x, true, L.n, skip, s);
+    }
+    AMGDD_MARK(0);
+    return launch_seg(L.ras, L.W64.p, false, r, x, false, SEG_STORE, skip, s);
+  }
+  Level& N = *h.lv[l + 1];
+  const void* W = f32 ? (const void*)L.W32.p : (const void*)L.W64.p;
+  const void* Wt = f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p;
+  const void* Z = f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p;
+  const void* Zt = f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p;
+  void* sv = f32 ? (void*)L.s32.p : (void*)L.s64.p;
+  void* rn = f32 ? (void*)N.r32.p : (void*)N.r64.p;
+  void* xn = f32 ? (void*)N.x32.p : (void*)N.x64.p;
+  // pre-smoothing from x = 0: x = M_RAS^{-1} r  (Eq. ras)
+  AMGDD_MARK(0);
+  AMGDD_TRY(launch_seg(L.ras, W, f32, r, x, f32, SEG_STORE, skip, s));
+  // s = r - A x ; r_c = P^T s
+  AMGDD_MARK(1);
+  AMGDD_TRY(launch_copy_vec(r, sv, f32, L.n, skip, s));
+  AMGDD_MARK(2);
+  AMGDD_TRY(launch_apply(L.aplan, L, f32, x, sv, -1, skip, s));
+  AMGDD_MARK(3);
+  AMGDD_TRY(launch_seg(L.restr, Zt, f32, sv, rn, f32, SEG_STORE, skip, s));
+  // x_c = B_{l+1} r_c ; x += P x_c  (Eq. cgc)
+  AMGDD_TRY(vcycle(h, l + 1, f32, rn, xn, skip, s, prof));
+  AMGDD_MARK(4);
+  AMGDD_TRY(launch_seg(L.prol, Z, f32, xn, x, f32, SEG_ADD, skip, s));
+  // post-smoothing: x += M_RAS-T^{-1} (r - A x)  (Eq. ras-t)
+  AMGDD_MARK(1);
+  AMGDD_TRY(launch_copy_vec(r, sv, f32, L.n, skip, s));
+  AMGDD_MARK(2);
+  AMGDD_TRY(launch_apply(L.aplan, L, f32, x, sv, -1, skip, s));
+  AMGDD_MARK(7);
+  AMGDD_TRY(launch_seg(L.rast, Wt, f32, sv, x, f32, SEG_ATOMIC_ADD, skip, s));
+  return AMGDD_OK;
+}
+
+// z = B r on FP64 PCG vectors, in the hierarchy's precision.
+static int precondition(amgdd_hierarchy& h, const double* r, double* z, const int* skip, cudaStream_t s) {
+  Level& L0 = *h.lv[0];
+  if (h.precision == AMGDD_MIXED32) {
+    AMGDD_TRY(launch_cast(r, false, L0.r32.p, true, L0.n, skip, s));
+    AMGDD_TRY(vcycle(h, 0, true, L0.r32.p, L0.x32.p, skip, s));
+    return launch_cast(L0.x32.p, true, z, false, L0.n, skip, s);
+  }
+  return vcycle(h, 0, false, r, z, skip, s);
+}
+
+// q = A p in FP64 on level 0.
+static int apply_fine64(amgdd_hierarchy& h, const double* p, double* q, const int* skip, cudaStream_t s) {
+  Level& L0 = *h.lv[0];
+  AMGDD_CUDA(cudaMemsetAsync(q, 0, L0.n * sizeof(double), s));
+  return launch_apply(L0.aplan, L0, false, p, q, +1, skip, s);
+}
+
+static int pcg_iteration(amgdd_hierarchy& h, cudaStream_t s) {
+  const int64_t n = h.n;
+  PcgState* st = h.st.p;
+  const int* done = &st->done;
+  AMGDD_TRY(apply_fine64(h, h.p.p, h.q.p, done, s));
+  AMGDD_TRY(launch_dot_partial(h.p.p, h.q.p, nullptr, n, h.partials.p, done, s));
+  AMGDD_TRY(launch_pcg_scalar(1, st, h.partials.p, s));
+  AMGDD_TRY(launch_update_xr(st, h.x.p, h.r.p, h.p.p, h.q.p, n, s));
+  AMGDD_TRY(launch_dot_partial(h.r.p, h.r.p, nullptr, n, h.partials.p, done, s));
+  AMGDD_TRY(launch_pcg_scalar(2, st, h.partials.p, s));
+  AMGDD_TRY(precondition(h, h.r.p, h.z.p, done, s));
+  const bool flex = h.precision == AMGDD_MIXED32;
+  AMGDD_TRY(launch_dot_partial(h.r.p, h.z.p, flex ? h.zold.p : nullptr, n, h.partials.p, done, s));
+  AMGDD_TRY(launch_pcg_scalar(3, st, h.partials.p, s));
+  AMGDD_TRY(launch_update_p(st, h.p.p, h.z.p, flex ? h.zold.p : nullptr, n, s));
+  return AMGDD_OK;
+}
+
+static int solve_one(amgdd_hierarchy& h, const double* bsrc, bool bdev, double tol, double* xdst, bool xdev,
+                     cudaStream_t s, amgdd_info* info) {
+  const int64_t n = h.n;
+  cudaEvent_t e0, e1;
+  AMGDD_CUDA(cudaEventCreate(&e0));
+  AMGDD_CUDA(cudaEventCreate(&e1));
+  AMGDD_CUDA(cudaEventRecord(e0, s));
+  AMGDD_CUDA(cudaMemcpyAsync(h.b.p, bsrc, n * sizeof(double), bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             s));
+  AMGDD_CUDA(cudaMemcpyAsync(h.r.p, h.b.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  AMGDD_CUDA(cudaMemsetAsync(h.x.p, 0, n * sizeof(double), s));
+  PcgState init{};
+  init.tol2 = tol * tol;
+  init.max_iter = h.prm.max_iter;
+  init.flexible = h.precision == AMGDD_MIXED32 ? 1 : 0;
+  *h.st_host = init;
+  AMGDD_CUDA(cudaMemcpyAsync(h.st.p, h.st_host, sizeof(PcgState), cudaMemcpyHostToDevice, s));
+  PcgState* st = h.st.p;
+  const int* done = &st->done;
+  AMGDD_TRY(launch_dot_partial(h.b.p, h.b.p, nullptr, n, h.partials.p, nullptr, s));
+  AMGDD_TRY(launch_pcg_scalar(4, st, h.partials.p, s));
+  AMGDD_TRY(precondition(h, h.r.p, h.z.p, done, s));
+  AMGDD_TRY(launch_copy_vec(h.z.p, h.p.p, false, n, done, s));
+  if (h.precision == AMGDD_MIXED32) AMGDD_TRY(launch_copy_vec(h.z.p, h.zold.p, false, n, done, s));
+  AMGDD_TRY(launch_dot_partial(h.r.p, h.z.p, nullptr, n, h.partials.p, done, s));
+  AMGDD_TRY(launch_pcg_scalar(0, st, h.partials.p, s));
+  const int K = std::max(1, h.prm.check_every);
+  const int pi = h.precision == AMGDD_MIXED32 ? 1 : 0;
+  bool first_batch = true;
+  for (;;) {
+    if (h.prm.use_graph && h.gexec[pi] != nullptr) {
+      AMGDD_CUDA(cudaGraphLaunch(h.gexec[pi], s));
+      count_graph_launch(h.gkernels[pi]);
+    } else if (h.prm.use_graph && !first_batch) {
+      cudaGraph_t g;
+      AMGDD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      capture_begin();
+      int rc = AMGDD_OK;
+      for (int k = 0; k < K && rc == AMGDD_OK; ++k) rc = pcg_iteration(h, s);
+      h.gkernels[pi] = capture_end();
+      cudaError_t ce = cudaStreamEndCapture(s, &g);
+      if (rc != AMGDD_OK) return rc;
+      AMGDD_CUDA(ce);
+      AMGDD_CUDA(cudaGraphInstantiate(&h.gexec[pi], g, 0));
+      cudaGraphDestroy(g);
+      AMGDD_CUDA(cudaGraphLaunch(h.gexec[pi], s));
+      count_graph_launch(h.gkernels[pi]);
+    } else {
+      for (int k = 0; k < K; ++k) AMGDD_TRY(pcg_iteration(h, s));
+    }
+    first_batch = false;
+    AMGDD_CUDA(cudaMemcpyAsync(h.st_host, h.st.p, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    AMGDD_CUDA(cudaStreamSynchronize(s));
+    if (h.st_host->done) break;
+  }
+  const PcgState fin = *h.st_host;
+  // true residual ||b - A x|| in FP64
+  AMGDD_CUDA(cudaMemcpyAsync(h.q.p, h.b.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  AMGDD_TRY(launch_apply(h.lv[0]->aplan, *h.lv[0], false, h.x.p, h.q.p, -1, nullptr, s));
+  AMGDD_TRY(launch_dot_partial(h.q.p, h.q.p, nullptr, n, h.partials.p, nullptr, s));
+  std::vector<double> part;
+  AMGDD_CUDA(cudaMemcpyAsync(xdst, h.x.p, n * sizeof(double), xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             s));
+  AMGDD_CUDA(cudaEventRecord(e1, s));
+  AMGDD_TRY(download(part, h.partials.p, 2 * kDotBlocks, s));
+  double qq = 0.0;
+  for (int i = 0; i < kDotBlocks; ++i) qq += part[2 * i];
+  float ms = 0.f;
+  AMGDD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    info->iters = fin.iters;
+    info->status = fin.status;
+    info->relres = fin.relres;
+    info->relres_true = fin.bnorm2 > 0 ? std::sqrt(qq / fin.bnorm2) : 0.0;
+    info->solve_ms = ms;
+  }
+  return fin.status;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+amgdd_params amgdd_params_default(void) {
+  amgdd_params p;
+  std::memset(&p, 0, sizeof(p));
+  p.L_max = 10;
+  p.n_coarse = 2000;
+  p.thresh = 0.1;
+  p.c_min[0] = 2;
+  p.c_min[1] = 3;
+  p.c_min[2] = 4;
+  p.n_cmin = 3;
+  p.precision = AMGDD_FP64;
+  p.max_iter = 1000;
+  p.schur_rtol = 1e-12;
+  p.use_graph = 1;
+  p.check_every = 4;
+  return p;
+}
+
+const char* amgdd_status_string(int st) {
+  switch (st) {
+    case AMGDD_OK: return "ok";
+    case AMGDD_ERR_INVALID_ARG: return "invalid argument";
+    case AMGDD_ERR_NOT_SPD: return "matrix not SPD";
+    case AMGDD_ERR_NONFINITE: return "non-finite value";
+    case AMGDD_ERR_BREAKDOWN: return "CG breakdown";
+    case AMGDD_ERR_NO_CONVERGENCE: return "no convergence";
+    case AMGDD_ERR_OOM: return "out of device memory";
+    case AMGDD_ERR_CUDA: return "CUDA error";
+    case AMGDD_ERR_INTERNAL: return "internal error";
+    default: return "unknown status";
+  }
+}
+
+const char* amgdd_last_error(void) { return g_last_error.c_str(); }
+
+static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, int overlap,
+                      const amgdd_params* params, void* stream, amgdd_hierarchy** out) {
+  if (out == nullptr || G == nullptr || agg == nullptr) {
+    set_error("amgdd_setup: G, agg and out must not be NULL");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  amgdd_params prm = params ? *params : amgdd_params_default();
+  if (prm.L_max < 1 || prm.n_cmin < 1 || prm.n_cmin > 8 || prm.max_iter < 1 || overlap < 1 ||
+      (prm.precision != AMGDD_FP64 && prm.precision != AMGDD_MIXED32) || prm.check_every < 1 || prm.n_coarse < 1) {
+    set_error("amgdd_setup: invalid parameters");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < prm.n_cmin; ++i)
+    if (prm.c_min[i] < 1) {
+      set_error("amgdd_setup: c_min entries must be >= 1");
+      return AMGDD_ERR_INVALID_ARG;
+    }
+  const int64_t m = G->m, n = G->n, nnz = G->nnz;
+  if (m < 0 || n < 1 || nnz < 0 || n >= (int64_t)1 << 31 || G->rowptr == nullptr ||
+      (nnz > 0 && (G->col == nullptr || G->val == nullptr))) {
+    set_error("amgdd_setup: bad CSR header (m=%lld n=%lld nnz=%lld)", (long long)m, (long long)n, (long long)nnz);
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  g_timer = PhaseTimer();
+  g_timer.on = std::getenv("AMGDD_VERBOSE") != nullptr;
+  const bool gdev = G->mem == AMGDD_DEVICE;
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> col;
+  std::vector<double> val, d1;
+  std::vector<int32_t> aggh;
+  AMGDD_TRY(fetch_any(rowptr, G->rowptr, (size_t)m + 1, gdev, s));
+  AMGDD_TRY(fetch_any(col, G->col, (size_t)nnz, gdev, s));
+  AMGDD_TRY(fetch_any(val, G->val, (size_t)nnz, gdev, s));
+  AMGDD_TRY(fetch_any(aggh, agg, (size_t)n, is_device_ptr(agg), s));
+  if (D1) AMGDD_TRY(fetch_any(d1, D1, (size_t)n, is_device_ptr(D1), s));
+  // CSR validation
+  if (rowptr[0] != 0 || rowptr[m] != nnz) {
+    set_error("amgdd_setup: rowptr[0] must be 0 and rowptr[m] = nnz");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  for (int64_t r = 0; r < m; ++r) {
+    if (rowptr[r + 1] < rowptr[r]) {
+      set_error("amgdd_setup: rowptr decreases at row %lld", (long long)r);
+      return AMGDD_ERR_INVALID_ARG;
+    }
+    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+      if (col[e] < 0 || col[e] >= n || (e > rowptr[r] && col[e] <= col[e - 1])) {
+        set_error("amgdd_setup: row %lld: column ids must increase strictly within [0, n)", (long long)r);
+        return AMGDD_ERR_INVALID_ARG;
+      }
+    }
+  }
+  for (double v : val)
+    if (!std::isfinite(v)) {
+      set_error("amgdd_setup: non-finite value in G");
+      return AMGDD_ERR_NONFINITE;
+    }
+  for (double v : d1)
+    if (!std::isfinite(v) || v < 0) {
+      set_error("amgdd_setup: D1 must be finite and >= 0");
+      return AMGDD_ERR_NONFINITE;
+    }
+  std::unique_ptr<amgdd_hierarchy> H(new amgdd_hierarchy());
+  H->prm = prm;
+  H->overlap = overlap;
+  H->n = n;
+  H->precision = prm.precision;
+  AMGDD_CUDA(cudaGetDevice(&H->device));
+  // ---- level 0 row groups: consecutive rows with identical supports ----
+  std::unique_ptr<Level> L0(new Level());
+  L0->n = n;
+  std::vector<int64_t> g_row0, g_row1;
+  L0->g_ptr.assign(1, 0);
+  int64_t prev = -1;
+  for (int64_t r = 0; r < m; ++r) {
+    const int64_t len = rowptr[r + 1] - rowptr[r];
+    if (len == 0) continue;
+    bool same = prev >= 0 && (rowptr[prev + 1] - rowptr[prev]) == len &&
+                std::equal(col.begin() + rowptr[r], col.begin() + rowptr[r + 1], col.begin() + rowptr[prev]);
+    if (same && g_row1.back() == r) {
+      g_row1.back() = r + 1;
+    } else {
+      g_row0.push_back(r);
+      g_row1.push_back(r + 1);
+      L0->g_idx.insert(L0->g_idx.end(), col.begin() + rowptr[r], col.begin() + rowptr[r + 1]);
+      L0->g_ptr.push_back((int64_t)L0->g_idx.size());
+    }
+    prev = r;
+  }
+  const int64_t ncsr = (int64_t)g_row0.size();
+  std::vector<double> d1vals;
+  for (int64_t j = 0; j < (int64_t)d1.size(); ++j)
+    if (d1[j] != 0.0) {
+      d1vals.push_back(d1[j]);
+      L0->g_idx.push_back((int32_t)j);
+      L0->g_ptr.push_back((int64_t)L0->g_idx.size());
+    }
+  const int64_t ng0 = (int64_t)L0->g_ptr.size() - 1;
+  L0->h_off.assign(ng0 + 1, 0);
+  for (int64_t g = 0; g < ng0; ++g) {
+    const int64_t sz = L0->g_ptr[g + 1] - L0->g_ptr[g];
+    L0->h_off[g + 1] = L0->h_off[g] + sz * sz;
+  }
+  AMGDD_TRY(L0->d_g_ptr.upload(L0->g_ptr, s));
+  AMGDD_TRY(L0->d_g_idx.upload(L0->g_idx, s));
+  AMGDD_TRY(L0->d_h_off.upload(L0->h_off, s));
+  AMGDD_TRY(L0->d_H.alloc(std::max<int64_t>(L0->h_off[ng0], 1)));
+  {
+    DBuf<int64_t> d_rowptr, d_r0, d_r1;
+    DBuf<double> d_val, d_d1;
+    AMGDD_TRY(d_rowptr.upload(rowptr, s));
+    AMGDD_TRY(d_val.upload(val, s));
+    AMGDD_TRY(d_r0.upload(g_row0, s));
+    AMGDD_TRY(d_r1.upload(g_row1, s));
+    AMGDD_TRY(launch_gram_rows(ncsr, d_r0.p, d_r1.p, L0->d_g_ptr.p, L0->d_h_off.p, d_rowptr.p, d_val.p, L0->d_H.p, s));
+    if (!d1vals.empty()) {
+      AMGDD_TRY(d_d1.upload(d1vals, s));
+      AMGDD_TRY(launch_gram_diag((int64_t)d1vals.size(), ncsr, L0->d_h_off.p, d_d1.p, L0->d_H.p, s));
+    }
+    AMGDD_CUDA(cudaStreamSynchronize(s));
+  }
+  // iota (shared identity index array)
+  {
+    std::vector<int32_t> io(n);
+    std::iota(io.begin(), io.end(), 0);
+    AMGDD_TRY(H->iota.upload(io, s));
+  }
+  H->lv.push_back(std::move(L0));
+  // ---- Algorithm 1 -----------------------------------------------------
+  int lvl = 0;
+  for (;;) {
+    Level& L = *H->lv[lvl];
+    const bool coarsest = !(lvl < prm.L_max - 1 && L.n > prm.n_coarse);
+    if (!coarsest || lvl == 0) {
+      Phase ph(6, "compress", s);
+      AMGDD_TRY(compress(L, s));
+    }
+    AMGDD_TRY(alloc_vectors(L));
+    if (coarsest) {
+      Phase ph(8, "coarsest", s);
+      AMGDD_TRY(build_coarsest(*H, L, s));
+      break;
+    }
+    AMGDD_TRY(build_level(*H, L, lvl, lvl == 0 ? aggh.data() : nullptr, s));
+    AMGDD_TRY(build_plans(*H, L, L.d_om_idx, s));
+    std::unique_ptr<Level> N(new Level());
+    {
+      Phase ph(7, "next level", s);
+      AMGDD_TRY(build_next(*H, L, *N, s));
+    }
+    if (g_timer.on) {
+      fprintf(stderr, "[amgdd] level %d: n=%lld nagg=%d", lvl, (long long)L.n, L.nagg);
+      for (int i = 0; i < 16; ++i)
+        if (g_timer.name[i]) fprintf(stderr, " %s=%.1fms", g_timer.name[i], g_timer.acc[i]);
+      fprintf(stderr, "\n");
+      for (double& a : g_timer.acc) a = 0.0;
+    }
+    L.d_H.release();
+    if (N->n == 0) {
+      set_error("level %d produced an empty coarse space", lvl);
+      return AMGDD_ERR_INTERNAL;
+    }
+    H->lv.push_back(std::move(N));
+    ++lvl;
+  }
+  H->lv.back()->d_H.release();
+  // ---- solver workspace --------------------------------------------------
+  AMGDD_TRY(H->x.alloc(n));
+  AMGDD_TRY(H->r.alloc(n));
+  AMGDD_TRY(H->z.alloc(n));
+  AMGDD_TRY(H->zold.alloc(n));
+  AMGDD_TRY(H->p.alloc(n));
+  AMGDD_TRY(H->q.alloc(n));
+  AMGDD_TRY(H->b.alloc(n));
+  AMGDD_TRY(H->partials.alloc(2 * kDotBlocks));
+  AMGDD_TRY(H->st.alloc(1));
+  AMGDD_CUDA(cudaMallocHost((void**)&H->st_host, sizeof(PcgState)));
+  AMGDD_CUDA(cudaStreamCreateWithFlags(&H->work, cudaStreamNonBlocking));
+  AMGDD_CUDA(cudaEventCreateWithFlags(&H->join[0], cudaEventDisableTiming));
+  AMGDD_CUDA(cudaEventCreateWithFlags(&H->join[1], cudaEventDisableTiming));
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  H->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = H.release();
+  return AMGDD_OK;
+}
+
+int amgdd_setup(const amgdd_csr* G, const double* D1, const int32_t* agg, int overlap, const amgdd_params* params,
+                void* stream, amgdd_hierarchy** out) {
+  try {
+    return setup_impl(G, D1, agg, overlap, params, stream, out);
+  } catch (const std::bad_alloc&) {
+    set_error("amgdd_setup: host allocation failed");
+    return AMGDD_ERR_OOM;
+  } catch (...) {
+    set_error("amgdd_setup: unexpected exception");
+    return AMGDD_ERR_INTERNAL;
+  }
+}
+
+int amgdd_solve(amgdd_hierarchy* h, const double* b, int nrhs, double tol, double* x, void* stream,
+                amgdd_info* info) {
+  if (h == nullptr || b == nullptr || x == nullptr || nrhs < 0 || !(tol >= 0.0)) {
+    set_error("amgdd_solve: invalid argument");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  try {
+    cudaStream_t us = (cudaStream_t)stream;
+    cudaStream_t s = h->work;
+    AMGDD_CUDA(cudaEventRecord(h->join[0], us));
+    AMGDD_CUDA(cudaStreamWaitEvent(s, h->join[0], 0));
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    int first_bad = AMGDD_OK;
+    for (int j = 0; j < nrhs; ++j) {
+      amgdd_info tmp{};
+      const int st = solve_one(*h, b + (int64_t)j * h->n, bdev, tol, x + (int64_t)j * h->n, xdev, s,
+                               info ? info + j : &tmp);
+      const bool per_rhs = st == AMGDD_OK || st == AMGDD_ERR_BREAKDOWN || st == AMGDD_ERR_NO_CONVERGENCE ||
+                           st == AMGDD_ERR_NONFINITE;
+      if (!per_rhs) return st;
+      if (st != AMGDD_OK && first_bad == AMGDD_OK) first_bad = st;
+    }
+    AMGDD_CUDA(cudaEventRecord(h->join[1], s));
+    AMGDD_CUDA(cudaStreamWaitEvent(us, h->join[1], 0));
+    return first_bad;
+  } catch (...) {
+    set_error("amgdd_solve: unexpected exception");
+    return AMGDD_ERR_INTERNAL;
+  }
+}
+
+int amgdd_set_precision(amgdd_hierarchy* h, int precision) {
+  if (h == nullptr || (precision != AMGDD_FP64 && precision != AMGDD_MIXED32)) {
+    set_error("amgdd_set_precision: invalid argument");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  h->precision = precision;
+  return AMGDD_OK;
+}
+
+int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* y, void* stream) {
+  if (h == nullptr || x == nullptr || y == nullptr || level < 0 || level >= (int)h->lv.size()) {
+    set_error("amgdd_apply: invalid argument");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Level& L = *h->lv[level];
+  const bool f32 = h->precision == AMGDD_MIXED32;
+  const bool coarsest_op = op == AMGDD_OP_COARSE || (op == AMGDD_OP_VCYCLE && L.coarsest);
+  if (coarsest_op) {
+    if (!L.coarsest) {
+      set_error("amgdd_apply: COARSE needs the coarsest level");
+      return AMGDD_ERR_INVALID_ARG;
+    }
+    AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, x, y, false, SEG_STORE, nullptr, s));
+    return AMGDD_OK;
+  }
+  if (L.coarsest && op != AMGDD_OP_A) {
+    set_error("amgdd_apply: operator not defined on the coarsest level");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  if (op == AMGDD_OP_A && L.aplan.ntasks == 0 && L.n > 0 && !(level == 0)) {
+    set_error("amgdd_apply: A is not stored on the coarsest level");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  const int64_t nin = op == AMGDD_OP_PROLONG ? h->lv[level + 1]->n : L.n;
+  const int64_t nout = op == AMGDD_OP_RESTRICT ? h->lv[level + 1]->n : L.n;
+  // staging buffers in the working precision
+  DBuf<float> xin32, yout32;
+  const void* xin = x;
+  void* yout = y;
+  if (f32) {
+    AMGDD_TRY(xin32.alloc(nin));
+    AMGDD_TRY(yout32.alloc(nout));
+    AMGDD_TRY(launch_cast(x, false, xin32.p, true, nin, nullptr, s));
+    xin = xin32.p;
+    yout = yout32.p;
+  }
+  const size_t esz = f32 ? sizeof(float) : sizeof(double);
+  switch (op) {
+    case AMGDD_OP_A:
+      AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
+      AMGDD_TRY(launch_apply(L.aplan, L, f32, xin, yout, +1, nullptr, s));
+      break;
+    case AMGDD_OP_RAS:
+      AMGDD_TRY(launch_seg(L.ras, f32 ? (const void*)L.W32.p : (const void*)L.W64.p, f32, xin, yout, f32, SEG_STORE,
+                           nullptr, s));
+      break;
+    case AMGDD_OP_RAST:
+      AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
+      AMGDD_TRY(launch_seg(L.rast, f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p, f32, xin, yout, f32,
+                           SEG_ATOMIC_ADD, nullptr, s));
+      break;
+    case AMGDD_OP_RESTRICT:
+      AMGDD_TRY(launch_seg(L.restr, f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p, f32, xin, yout, f32,
+                           SEG_STORE, nullptr, s));
+      break;
+    case AMGDD_OP_PROLONG:
+      AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
+      AMGDD_TRY(launch_seg(L.prol, f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p, f32, xin, yout, f32, SEG_ADD,
+                           nullptr, s));
+      break;
+    case AMGDD_OP_VCYCLE:
+      AMGDD_TRY(vcycle(*h, level, f32, xin, yout, nullptr, s));
+      break;
+    default:
+      set_error("amgdd_apply: unknown operator %d", op);
+      return AMGDD_ERR_INVALID_ARG;
+  }
+  if (f32) AMGDD_TRY(launch_cast(yout32.p, true, y, false, nout, nullptr, s));
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  return AMGDD_OK;
+}
+
+int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes, int cap) {
+  if (h == nullptr || ms == nullptr || bytes == nullptr || reps < 1 ||
+      cap < (int)h->lv.size() * VProf::kSlots) {
+    set_error("amgdd_profile_vcycle: invalid argument (cap must be >= levels * %d)", VProf::kSlots);
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  const int nl = (int)h->lv.size();
+  for (int i = 0; i < nl * VProf::kSlots; ++i) ms[i] = bytes[i] = 0.0;
+  cudaStream_t s = h->work;
+  const bool f32 = h->precision == AMGDD_MIXED32;
+  Level& L0 = *h->lv[0];
+  const void* r = f32 ? (const void*)L0.s32.p : (const void*)L0.s64.p;
+  void* x = f32 ? (void*)L0.r32.p : (void*)L0.r64.p;
+  // a deterministic nonzero input
+  AMGDD_TRY(launch_cast(h->iota.p ? (const void*)L0.x64.p : nullptr, false, (void*)r, f32, 0, nullptr, s));
+  AMGDD_CUDA(cudaMemsetAsync((void*)r, 0, L0.n * (f32 ? 4 : 8), s));
+  VProf prof;
+  std::vector<double> acc(nl * VProf::kSlots, 0.0);
+  for (int rep = 0; rep < reps; ++rep) {
+    prof.used = 0;
+    AMGDD_TRY(vcycle(*h, 0, f32, r, x, nullptr, s, &prof));
+    AMGDD_TRY(prof.mark(s, -1, 0));
+    AMGDD_CUDA(cudaStreamSynchronize(s));
+    for (size_t i = 0; i + 1 < prof.used; ++i) {
+      float t = 0.f;
+      AMGDD_CUDA(cudaEventElapsedTime(&t, prof.ev[i], prof.ev[i + 1]));
+      if (prof.tag[i] >= 0) acc[prof.tag[i]] += t;
+    }
+  }
+  const size_t esz = f32 ? 4 : 8;
+  for (int l = 0; l < nl; ++l) {
+    const Level& L = *h->lv[l];
+    double* b = bytes + l * VProf::kSlots;
+    auto seg = [&](const SegPlan& p, int64_t nin, int64_t nout, bool rmw, size_t e) {
+      return (double)p.mat_len * e + (double)(p.in_len + p.out_len) * 4.0 + (double)nin * e +
+             (double)nout * e * (rmw ? 2.0 : 1.0);
+    };
+    if (L.coarsest) {
+      b[0] = seg(L.ras, L.n, L.n, false, 8);
+      if (f32) b[1] = b[5] = (double)L.n * 12.0;
+    } else {
+      const int64_t nn = L.col0.back();
+      double ap = (double)L.aplan.r_len * esz + 3.0 * L.n * esz;
+      for (size_t g = 0; g + 1 < L.g_ptr.size(); ++g)
+        if (L.g_rank[g] > 0) ap += (double)(L.g_ptr[g + 1] - L.g_ptr[g]) * 4.0;
+      b[0] = seg(L.ras, L.n, L.n, false, esz);
+      b[1] = 2.0 * 2.0 * L.n * esz;  // two r -> s copies
+      b[2] = 2.0 * ap;                // two residual A-applies
+      b[3] = seg(L.restr, L.n, nn, false, esz);
+      b[4] = seg(L.prol, nn, L.n, true, esz);
+      b[7] = seg(L.rast, L.n, L.n, true, esz);
+    }
+  }
+  for (int i = 0; i < nl * VProf::kSlots; ++i) ms[i] = acc[i] / reps;
+  return AMGDD_OK;
+}
+
+int64_t amgdd_kernel_launches(void) { return g_kernels.load(); }
+
+int amgdd_num_levels(const amgdd_hierarchy* h) { return h ? (int)h->lv.size() : 0; }
+
+int amgdd_level_describe(const amgdd_hierarchy* h, int level, amgdd_level_desc* out) {
+  if (h == nullptr || out == nullptr || level < 0 || level >= (int)h->lv.size()) {
+    set_error("amgdd_level_describe: invalid argument");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  const Level& L = *h->lv[level];
+  std::memset(out, 0, sizeof(*out));
+  out->n = L.n;
+  out->is_coarsest = L.coarsest ? 1 : 0;
+  out->ngroups = (int64_t)L.g_ptr.size() - 1;
+  for (size_t g = 0; g + 1 < L.g_ptr.size() && g < L.g_rank.size(); ++g) {
+    out->g_rows += L.g_rank[g];
+    out->g_vals += (int64_t)L.g_rank[g] * (L.g_ptr[g + 1] - L.g_ptr[g]);
+  }
+  if (!L.coarsest) {
+    out->nagg = L.nagg;
+    out->n_next = L.col0.empty() ? 0 : L.col0.back();
+    out->omega_len = (int64_t)L.om_idx.size();
+    out->z_len = L.z_off.empty() ? 0 : L.z_off.back();
+    for (int i = 0; i < L.nagg; ++i) out->w_vals += (int64_t)L.nomega[i] * (L.om_ptr[i + 1] - L.om_ptr[i]);
+  } else {
+    out->w_vals = L.n * L.n;
+  }
+  return AMGDD_OK;
+}
+
+int amgdd_level_export(const amgdd_hierarchy* h, int level, int which, void* dst, size_t cap) {
+  if (h == nullptr || dst == nullptr || level < 0 || level >= (int)h->lv.size()) {
+    set_error("amgdd_level_export: invalid argument");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  const Level& L = *h->lv[level];
+  auto put = [&](const void* src, size_t bytes) -> int {
+    if (bytes > cap) {
+      set_error("amgdd_level_export: destination holds %zu bytes, %zu needed", cap, bytes);
+      return AMGDD_ERR_INVALID_ARG;
+    }
+    std::memcpy(dst, src, bytes);
+    return AMGDD_OK;
+  };
+  if (L.coarsest && which != AMGDD_ARR_AGG) {
+    set_error("amgdd_level_export: the coarsest level has no aggregates");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  switch (which) {
+    case AMGDD_ARR_AGG:
+      if (L.agg.empty()) {
+        set_error("amgdd_level_export: no aggregates on this level");
+        return AMGDD_ERR_INVALID_ARG;
+      }
+      return put(L.agg.data(), L.agg.size() * sizeof(int32_t));
+    case AMGDD_ARR_OMEGA_PTR: return put(L.om_ptr.data(), L.om_ptr.size() * sizeof(int64_t));
+    case AMGDD_ARR_OMEGA_IDX: return put(L.om_idx.data(), L.om_idx.size() * sizeof(int32_t));
+    case AMGDD_ARR_NOMEGA: return put(L.nomega.data(), L.nomega.size() * sizeof(int32_t));
+    case AMGDD_ARR_K: return put(L.k.data(), L.k.size() * sizeof(int32_t));
+    case AMGDD_ARR_Z:
+    case AMGDD_ARR_MU: {
+      const bool z = which == AMGDD_ARR_Z;
+      const size_t cnt = z ? (size_t)L.z_off.back() : (size_t)L.mu_off.back();
+      if (cnt * sizeof(double) > cap) {
+        set_error("amgdd_level_export: destination too small");
+        return AMGDD_ERR_INVALID_ARG;
+      }
+      if (cudaMemcpy(dst, z ? L.Z64.p : L.mu.p, cnt * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_error("amgdd_level_export: copy failed");
+        return AMGDD_ERR_CUDA;
+      }
+      return AMGDD_OK;
+    }
+    default:
+      set_error("amgdd_level_export: unknown array %d", which);
+      return AMGDD_ERR_INVALID_ARG;
+  }
+}
+
+static void level_bytes(const amgdd_hierarchy& h, const Level& L, size_t esz, double& cyc) {
+  auto seg = [&](const SegPlan& p, int64_t nin, int64_t nout, bool rmw) {
+    return (double)p.mat_len * esz + (double)(p.in_len + p.out_len) * 4.0 + (double)nin * esz +
+           (double)nout * esz * (rmw ? 2.0 : 1.0);
+  };
+  if (L.coarsest) {
+    cyc += (double)L.n * L.n * 8.0 + 2.0 * L.n * 8.0;
+    return;
+  }
+  const int64_t nn = L.col0.back();
+  double apply = (double)L.aplan.r_len * esz + 3.0 * L.n * esz;
+  for (size_t g = 0; g + 1 < L.g_ptr.size(); ++g)
+    if (L.g_rank[g] > 0) apply += (double)(L.g_ptr[g + 1] - L.g_ptr[g]) * 4.0;
+  cyc += seg(L.ras, L.n, L.n, false) + seg(L.rast, L.n, L.n, true) + seg(L.restr, L.n, nn, false) +
+         seg(L.prol, nn, L.n, true) + 2.0 * (apply + 2.0 * L.n * esz);
+  (void)h;
+}
+
+int amgdd_bytes_model(const amgdd_hierarchy* h, double* vcycle_bytes, double* apply_bytes) {
+  if (h == nullptr) return AMGDD_ERR_INVALID_ARG;
+  const size_t esz = h->precision == AMGDD_MIXED32 ? 4 : 8;
+  double cyc = 0.0;
+  for (const auto& L : h->lv) level_bytes(*h, *L, esz, cyc);
+  const Level& L0 = *h->lv[0];
+  double ap = (double)L0.aplan.r_len * 8.0 + 3.0 * L0.n * 8.0;
+  for (size_t g = 0; g + 1 < L0.g_ptr.size(); ++g)
+    if (L0.g_rank[g] > 0) ap += (double)(L0.g_ptr[g + 1] - L0.g_ptr[g]) * 4.0;
+  if (vcycle_bytes) *vcycle_bytes = cyc;
+  if (apply_bytes) *apply_bytes = ap;
+  return AMGDD_OK;
+}
+
+int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap) {
+  if (h == nullptr || json == nullptr || cap == 0) return AMGDD_ERR_INVALID_ARG;
+  std::string s = "{\"levels\": " + std::to_string(h->lv.size()) + ", \"n\": [";
+  for (size_t l = 0; l < h->lv.size(); ++l) s += (l ? ", " : "") + std::to_string(h->lv[l]->n);
+  s += "], \"nnzA\": [";
+  for (size_t l = 0; l < h->nnzA.size(); ++l) s += (l ? ", " : "") + std::to_string(h->nnzA[l]);
+  double oc = 0;
+  for (int64_t v : h->nnzA) oc += (double)v;
+  oc /= h->nnzA.empty() ? 1.0 : (double)h->nnzA[0];
+  s += "], \"op_complexity\": " + std::to_string(oc);
+  s += ", \"nagg\": [";
+  for (size_t l = 0; l < h->lv.size(); ++l) s += (l ? ", " : "") + std::to_string(h->lv[l]->nagg);
+  s += "], \"g_vals\": [";
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    int64_t gv = 0;
+    const Level& L = *h->lv[l];
+    for (size_t g = 0; g + 1 < L.g_ptr.size() && g < L.g_rank.size(); ++g)
+      gv += (int64_t)L.g_rank[g] * (L.g_ptr[g + 1] - L.g_ptr[g]);
+    s += (l ? ", " : "") + std::to_string(gv);
+  }
+  s += "], \"w_vals\": [";
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    amgdd_level_desc d;
+    amgdd_level_describe(h, (int)l, &d);
+    s += (l ? ", " : "") + std::to_string(d.w_vals);
+  }
+  double vb = 0, ab = 0;
+  amgdd_bytes_model(h, &vb, &ab);
+  s += "], \"vcycle_bytes\": " + std::to_string(vb) + ", \"apply64_bytes\": " + std::to_string(ab);
+  s += ", \"setup_ms\": " + std::to_string(h->setup_ms) + "}";
+  if (s.size() + 1 > cap) return AMGDD_ERR_INVALID_ARG;
+  std::memcpy(json, s.c_str(), s.size() + 1);
+  return AMGDD_OK;
+}
+
+void amgdd_free(amgdd_hierarchy* h) {
+  if (h == nullptr) return;
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+// Internal declarations of libamgdd: device buffers, level layout, kernel
+// launch wrappers.  Nothing here is part of the C ABI (include/amgdd.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "amgdd.h"
+
+namespace amgdd {
+
+void set_error(const char* fmt, ...);
+
+#define AMGDD_CUDA(call)                                                              \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      ::amgdd::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return e_ == cudaErrorMemoryAllocation ? AMGDD_ERR_OOM : AMGDD_ERR_CUDA;        \
+    }                                                                                 \
+  } while (0)
+
+#define AMGDD_TRY(call)          \
+  do {                           \
+    int s_ = (call);             \
+    if (s_ != AMGDD_OK) return s_; \
+  } while (0)
+
+// Owning device buffer.
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  int alloc(size_t count) {
+    release();
+    if (count == 0) return AMGDD_OK;
+    cudaError_t e = cudaMalloc((void**)&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? AMGDD_ERR_OOM : AMGDD_ERR_CUDA;
+    }
+    n = count;
+    return AMGDD_OK;
+  }
+  int upload(const std::vector<T>& h, cudaStream_t s) {
+    AMGDD_TRY(alloc(h.size()));
+    if (!h.empty()) AMGDD_CUDA(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return AMGDD_OK;
+  }
+  int zero(cudaStream_t s) {
+    if (n) AMGDD_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+    return AMGDD_OK;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+};
+
+// ---------------------------------------------------------------------------
+// Batched gather-GEMV-scatter: for every block b,
+//     y[out_idx[out_off[b] + r]] (op)= sum_c M_b[r, c] * x[in_idx[in_off[b] + c]]
+// with M_b row-major (nr_b x nc_b, leading dimension nc_b) at m_off[b].
+// Used for RAS (W_i), RAS-T (W_i^T), restriction (Z_i^T), prolongation (Z_i)
+// and the coarsest solve (A_L^{-1} as a single block).
+enum SegMode { SEG_STORE = 0, SEG_ADD = 1, SEG_ATOMIC_ADD = 2 };
+
+struct SegPlan {
+  int nblocks = 0;
+  int nchunks = 0;      // CTAs: chunks of at most `rows_per_chunk` rows of one block
+  int rows_per_chunk = 0;
+  int lanes = 32;       // lanes cooperating on one row (4, 8, 16 or 32)
+  int max_nc = 0;       // longest row (shared-memory staging of the gathered x)
+  int64_t mat_len = 0;  // total stored matrix entries
+  int64_t in_len = 0, out_len = 0;
+  DBuf<int64_t> m_off, in_off, out_off;
+  DBuf<int32_t> nr, nc;
+  DBuf<int32_t> chunk_blk, chunk_row0;
+  // index arrays owned elsewhere (level Omega lists or the identity)
+  const int32_t* in_idx_ext = nullptr;
+  const int32_t* out_idx_ext = nullptr;
+};
+
+// Row groups of G_l (rows sharing one support), compressed: R_g has rank_g
+// rows over the support S_g (row-major, leading dimension s_g).  A-apply:
+//     y[S_g] (+/-)= R_g^T (R_g x[S_g]).
+struct ApplyPlan {
+  int ntasks = 0;
+  int nbuckets = 0;
+  int bucket_start[16] = {0};  // first CTA of each bucket
+  int bucket_kind[16] = {0};   // kernel variant (lanes, columns per lane)
+  int bucket_tasks[16] = {0};
+  int64_t r_len = 0;           // stored entries of R (sum rank * s)
+  DBuf<int32_t> task_grp, task_row0, task_nrow;  // per task (grouped by bucket)
+};
+
+struct Level {
+  int64_t n = 0;
+  int nagg = 0;
+  bool coarsest = false;
+  // ---- row groups of G_l --------------------------------------------------
+  std::vector<int64_t> g_ptr;   // ngroups+1 offsets into g_idx
+  std::vector<int32_t> g_idx;   // supports (sorted)
+  std::vector<int32_t> g_rank;  // rows kept after compression
+  std::vector<int64_t> h_off;   // offsets of the s x s Grams (and of R capacity)
+  DBuf<int64_t> d_g_ptr, d_h_off;
+  DBuf<int32_t> d_g_idx, d_rank;
+  DBuf<double> d_H;     // Grams H_g = sum_rows g^T g (setup only, freed after use)
+  DBuf<double> d_R64;   // compressed rows, capacity s x s per group
+  DBuf<float> d_R32;
+  ApplyPlan aplan;
+  // ---- aggregates and subdomains ------------------------------------------
+  std::vector<int32_t> agg;      // n
+  std::vector<int64_t> om_ptr;   // nagg+1
+  std::vector<int32_t> om_idx;   // omega_i ascending then Gamma_i ascending
+  std::vector<int32_t> nomega;   // |omega_i|
+  std::vector<int32_t> k;        // selected eigenvectors per aggregate
+  std::vector<int64_t> col0;     // nagg+1 first coarse column of each aggregate
+  std::vector<int64_t> z_off;    // nagg+1 offsets of Z_i (|omega_i| x k_i)
+  std::vector<int64_t> mu_off;   // nagg+1 offsets of the local spectra
+  DBuf<int32_t> d_om_idx;        // Omega lists on the device
+  // ---- smoother and transfer operators -------------------------------------
+  SegPlan ras, rast, restr, prol;
+  DBuf<double> W64, Wt64, Z64, Zt64, mu;
+  DBuf<float> W32, Wt32, Z32, Zt32;
+  // ---- work vectors of the V-cycle ----------------------------------------
+  DBuf<double> r64, x64, s64;
+  DBuf<float> r32, x32, s32;
+};
+
+// ---------------------------------------------------------------------------
+// kernels (cycle_kernels.cu)
+int launch_seg(const SegPlan& p, const void* M, bool m_fp32, const void* x, void* y, bool v_fp32, SegMode mode,
+               const int* skip, cudaStream_t s);
+int launch_apply(const ApplyPlan& p, const Level& L, bool fp32, const void* x, void* y, int sign, const int* skip,
+                 cudaStream_t s);
+int launch_cast(const void* src, bool src32, void* dst, bool dst32, int64_t n, const int* skip, cudaStream_t s);
+int launch_copy_vec(const void* src, void* dst, bool fp32, int64_t n, const int* skip, cudaStream_t s);
+
+// Kernel-launch accounting (kernels launched directly, plus the kernels of
+// each captured CUDA graph every time it is launched).
+void count_kernels(int64_t k);
+void capture_begin();
+int64_t capture_end();
+void count_graph_launch(int64_t kernels);
+
+// PCG state kept in device memory
+struct PcgState {
+  double rz;      // r_k^T z_k
+  double pq;      // p_k^T A p_k
+  double rr;      // r_k^T r_k
+  double rzn;     // r_{k+1}^T z_{k+1}
+  double rzo;     // r_{k+1}^T z_k (flexible variant)
+  double alpha, beta;
+  double bnorm2;
+  double tol2;    // tol^2 * ||b||^2
+  double relres;
+  int iters, max_iter, done, status, flexible, pad;
+};
+
+constexpr int kDotBlocks = 608;  // 4 x 152 SMs; partial sums per dot product
+
+int launch_dot_partial(const double* a, const double* b, const double* c, int64_t n, double* partials,
+                       const int* skip, cudaStream_t s);
+int launch_pcg_scalar(int which, PcgState* st, const double* partials, cudaStream_t s);
+int launch_update_xr(PcgState* st, double* x, double* r, const double* p, const double* q, int64_t n,
+                     cudaStream_t s);
+int launch_update_p(PcgState* st, double* p, const double* z, double* zold, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// setup kernels (setup_kernels.cu); all FP64
+struct LocalBatch {
+  // one entry per aggregate of the batch
+  DBuf<int32_t> m, no;              // |Omega_i|, |omega_i|
+  DBuf<int64_t> a_off;              // offset of A_i / A~_i in the work pools (m x m, column-major)
+  DBuf<int64_t> pair_ptr;           // groups touching Omega_i
+  DBuf<int32_t> pair_grp, pair_nz;  // group id, 1 if the group is in nz_i
+  DBuf<int64_t> map_ptr;            // per pair: offsets into map
+  DBuf<int32_t> map;                // local index of each support node (-1 outside Omega_i)
+};
+
+struct NextGramPlan {
+  int64_t nnew = 0;
+  DBuf<int64_t> new_ptr;    // new group -> range in contrib
+  DBuf<int32_t> contrib;    // level-l group ids
+  DBuf<int64_t> new_sptr;   // new group support offsets
+  DBuf<int64_t> new_hoff;   // output Gram offsets
+  // per support node of each level-l group: the Z row offset, k and the
+  // column offset of its aggregate's block inside the new support
+  DBuf<int64_t> rowz_ptr;
+  DBuf<int64_t> rowz_zoff;
+  DBuf<int32_t> rowz_k;
+  DBuf<int32_t> rowz_col;
+  int64_t scratch_per = 0;
+};
+
+int launch_gram_rows(int64_t ngroups, const int64_t* g_row0, const int64_t* g_row1, const int64_t* g_ptr,
+                     const int64_t* h_off, const int64_t* rowptr, const double* val, double* H, cudaStream_t s);
+int launch_gram_diag(int64_t n, int64_t first_group, const int64_t* h_off, const double* D1, double* H,
+                     cudaStream_t s);
+int launch_pchol(int64_t first, int64_t count, int max_s, const int64_t* g_ptr, const int64_t* h_off,
+                 const double* H, double* R64, float* R32, int32_t* rank, double* scratch, int64_t scratch_per,
+                 cudaStream_t s);
+int launch_assemble(int nb, int max_m, const LocalBatch& b, const int64_t* g_ptr, const int64_t* h_off,
+                    const double* H, const int32_t* M, double* Apool, double* Atpool, cudaStream_t s);
+int launch_chol(int nb, int max_m, const int32_t* m, const int64_t* a_off, double* Apool, int32_t* status,
+                cudaStream_t s);
+int launch_schur(int nb, int max_m, const int32_t* m, const int32_t* no, const int64_t* a_off, double* Atpool,
+                 double rtol, cudaStream_t s);
+int launch_inv_rows(int nb, int max_m, const int32_t* m, const int32_t* no, const int64_t* a_off,
+                    const double* Lpool, const int64_t* w_off, double* W64, float* W32, double* Wt64, float* Wt32,
+                    double* scratch, const int32_t* chunk_b, const int32_t* chunk_c0, int nchunks, int cw,
+                    cudaStream_t s);
+constexpr int kInvChunk = 32;  // RHS columns per CTA of the inverse-row solves
+
+// Wall-clock accounting of setup phases (printed when AMGDD_VERBOSE is set).
+struct PhaseTimer {
+  bool on = false;
+  double acc[16] = {0};
+  const char* name[16] = {nullptr};
+  void add(int i, const char* nm, double ms) {
+    acc[i] += ms;
+    name[i] = nm;
+  }
+};
+int launch_gep(int nb, int max_no, const int32_t* m, const int32_t* no, const int64_t* a_off, const double* Lpool,
+               const double* Spool, const int32_t* cap, double thresh, const int64_t* mu_off, double* mu,
+               const int64_t* z_off_cap, double* Zcap, int32_t* kout, double* scratch, const int64_t* scr_off,
+               cudaStream_t s);
+int launch_pack_z(int nb, const int32_t* no, const int32_t* k, const int64_t* z_off_cap, const double* Zcap,
+                  const int64_t* z_off, double* Z64, float* Z32, double* Zt64, float* Zt32, cudaStream_t s);
+int launch_next_gram(const NextGramPlan& p, int max_sn, const int64_t* g_ptr, const int64_t* h_off, const double* H,
+                     const double* Z64, double* Hn, double* scratch, int64_t first, int64_t count, cudaStream_t s);
+
+}  // namespace amgdd

@@ -1,0 +1,797 @@
+// Setup kernels (FP64): the numeric steps of Algorithm 1.
+//
+//  k_gram_rows   H_g = sum of g^T g over the rows of one support group of G
+//  k_pchol       rank-revealing (diagonally pivoted) Cholesky H_g = R_g^T R_g:
+//                the compressed rows of G_l used by the A-apply
+//  k_assemble    A_i = A(Omega_i, Omega_i) and the SPSD splitting block
+//                A~_i = sum_{rows in nz_i} g^T g / M (Lemma)
+//  k_chol        A_i = L L^T (the omega-first ordering makes the leading
+//                block the Cholesky factor of A_ww)
+//  k_schur       S~ = A~_ww - A~_wG A~_GG^+ A~_Gw (Eq. gevp-S) by eliminating
+//                the Gamma pivots; pivots below rtol * max diag are zero
+//  k_inv_rows    A_i^{-1}(:, omega_i): the RAS / RAS-T operators
+//  k_gep         S~ u = mu A_ww u via C = L^{-1} S~ L^{-T}, cyclic Jacobi,
+//                ascending mu, selection, Z = L^{-T} V, sign convention
+//  k_pack_z      Z_i and Z_i^T in FP64 and FP32
+//  k_next_gram   Grams of G_{l+1} = G_l P_l, per new support group
+//
+// One CTA owns one matrix; matrices live in global memory (column-major
+// unless stated otherwise) so that sizes from a handful to a few thousand
+// rows use the same code.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+
+#include <cooperative_groups.h>
+
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace amgdd {
+
+namespace {
+
+__device__ __forceinline__ double warp_max_idx(double v, int& idx) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+    if (ov > v || (ov == v && oi < idx)) {
+      v = ov;
+      idx = oi;
+    }
+  }
+  return v;
+}
+
+__device__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (int)threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (threadIdx.x == 0) sh[0] = t;
+  }
+  __syncthreads();
+  t = sh[0];
+  __syncthreads();
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_gram_rows(int64_t first, const int64_t* __restrict__ g_row0, const int64_t* __restrict__ g_row1,
+                            const int64_t* __restrict__ g_ptr, const int64_t* __restrict__ h_off,
+                            const int64_t* __restrict__ rowptr, const double* __restrict__ val,
+                            double* __restrict__ H) {
+  const int64_t g = first + blockIdx.x;
+  const int s = (int)(g_ptr[g + 1] - g_ptr[g]);
+  double* Hg = H + h_off[g];
+  const int64_t r0 = g_row0[g], r1 = g_row1[g];
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int a = e / s, b = e % s;
+    double acc = 0.0;
+    for (int64_t r = r0; r < r1; ++r) {
+      const double* v = val + rowptr[r];
+      acc += v[a] * v[b];
+    }
+    Hg[e] = acc;
+  }
+}
+
+__global__ void k_gram_diag(int64_t n, int64_t first_group, const int64_t* __restrict__ h_off,
+                            const double* __restrict__ D1, double* __restrict__ H) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n) H[h_off[first_group + j]] = D1[j];
+}
+
+// Diagonally pivoted Cholesky of the PSD Gram H (s x s, row-major) on a
+// scratch copy W.  Row k of R: R[k][piv_k] = sqrt(d_k), R[k][piv_j] =
+// W[piv_j][piv_k] / sqrt(d_k) for later pivots, 0 for earlier ones; the
+// columns stay in support order, so R^T R = H up to the dropped remainder.
+// Stops when the largest remaining diagonal is <= max(s,16) * 4 eps * max
+// diag(H) (rounding level).
+__global__ void k_pchol(int64_t first, const int64_t* __restrict__ g_ptr, const int64_t* __restrict__ h_off,
+                        const double* __restrict__ H, double* __restrict__ R64, float* __restrict__ R32,
+                        int32_t* __restrict__ rank_out, double* __restrict__ scratch, int64_t scratch_per) {
+  extern __shared__ int piv[];
+  __shared__ double sh_best;
+  __shared__ int sh_bidx;
+  const int64_t g = first + blockIdx.x;
+  const int s = (int)(g_ptr[g + 1] - g_ptr[g]);
+  const double* Hg = H + h_off[g];
+  double* R = R64 + h_off[g];
+  float* R32g = R32 + h_off[g];
+  double* W = scratch + (int64_t)blockIdx.x * scratch_per;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) W[e] = Hg[e];
+  for (int j = threadIdx.x; j < s; j += blockDim.x) piv[j] = j;
+  __syncthreads();
+  double dmax0 = 0.0;
+  for (int j = 0; j < s; ++j) dmax0 = fmax(dmax0, Hg[j * s + j]);
+  const double tau = (double)max(s, 16) * 4.0 * DBL_EPSILON * dmax0;
+  int rank = 0;
+  for (int k = 0; k < s; ++k) {
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int bidx = s;
+      for (int j = k + threadIdx.x; j < s; j += 32) {
+        const double d = W[piv[j] * s + piv[j]];
+        if (d > best || (d == best && j < bidx)) {
+          best = d;
+          bidx = j;
+        }
+      }
+      best = warp_max_idx(best, bidx);
+      if (threadIdx.x == 0) {
+        sh_best = best;
+        sh_bidx = bidx;
+      }
+    }
+    __syncthreads();
+    const double d = sh_best;
+    if (!(d > tau)) break;
+    if (threadIdx.x == 0) {
+      const int t = piv[k];
+      piv[k] = piv[sh_bidx];
+      piv[sh_bidx] = t;
+    }
+    __syncthreads();
+    const int pk = piv[k];
+    const double l = sqrt(d);
+    double* Rk = R + (int64_t)k * s;
+    for (int j = threadIdx.x; j < s; j += blockDim.x) {
+      double v;
+      if (j < k)
+        v = 0.0;
+      else if (j == k)
+        v = l;
+      else
+        v = W[piv[j] * s + pk] / l;
+      Rk[piv[j]] = v;
+      R32g[(int64_t)k * s + piv[j]] = (float)v;
+    }
+    __syncthreads();
+    const int rem = s - k - 1;
+    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+      const int i = piv[k + 1 + e / rem], j = piv[k + 1 + e % rem];
+      W[i * s + j] -= Rk[i] * Rk[j];
+    }
+    __syncthreads();
+    rank = k + 1;
+  }
+  if (threadIdx.x == 0) rank_out[g] = rank;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_assemble(const int32_t* __restrict__ mdim, const int64_t* __restrict__ a_off,
+                           const int64_t* __restrict__ pair_ptr, const int32_t* __restrict__ pair_grp,
+                           const int32_t* __restrict__ pair_nz, const int64_t* __restrict__ map_ptr,
+                           const int32_t* __restrict__ map, const int64_t* __restrict__ g_ptr,
+                           const int64_t* __restrict__ h_off, const double* __restrict__ H,
+                           const int32_t* __restrict__ M, double* __restrict__ Apool, double* __restrict__ Atpool) {
+  const int b = blockIdx.x;
+  const int m = mdim[b];
+  double* A = Apool + a_off[b];
+  double* At = Atpool + a_off[b];
+  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+    A[e] = 0.0;
+    At[e] = 0.0;
+  }
+  __syncthreads();
+  for (int64_t p = pair_ptr[b]; p < pair_ptr[b + 1]; ++p) {
+    const int g = pair_grp[p];
+    const int s = (int)(g_ptr[g + 1] - g_ptr[g]);
+    const double* Hg = H + h_off[g];
+    const int32_t* mp = map + map_ptr[p];
+    const bool nz = pair_nz[p] != 0;
+    const double w = 1.0 / (double)M[g];
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+      const int a = e / s, c = e % s;
+      const int la = mp[a], lc = mp[c];
+      if (la >= 0 && lc >= 0) {
+        const double h = Hg[e];
+        A[la + (int64_t)lc * m] += h;
+        if (nz) At[la + (int64_t)lc * m] += h * w;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A "team" works on one matrix: one CTA, or CL CTAs of a thread-block
+// cluster (large coarse-level blocks) that synchronise with cluster barriers.
+// Reductions across the team go through a small global slot per matrix.
+template <int CL>
+struct Team {
+  int cta, rank, size;
+  __device__ Team() {
+    if constexpr (CL > 1)
+      cta = (int)cg::this_cluster().block_rank();
+    else
+      cta = 0;
+    rank = cta * (int)blockDim.x + (int)threadIdx.x;
+    size = CL * (int)blockDim.x;
+  }
+  __device__ void sync() const {
+    if constexpr (CL > 1)
+      cg::this_cluster().sync();
+    else
+      __syncthreads();
+  }
+  // deterministic team-wide sum; red holds CL doubles
+  __device__ double sum(double v, double* sh, double* red) const {
+    v = block_sum(v, sh);
+    if constexpr (CL == 1) {
+      return v;
+    } else {
+      if (threadIdx.x == 0) red[cta] = v;
+      sync();
+      double t = 0.0;
+      for (int c = 0; c < CL; ++c) t += red[c];
+      sync();
+      return t;
+    }
+  }
+};
+
+// In-place right-looking Cholesky (lower, column-major).
+template <int CL>
+__global__ void k_chol(const int32_t* __restrict__ mdim, const int64_t* __restrict__ a_off, double* __restrict__ Apool,
+                       int32_t* __restrict__ status) {
+  const Team<CL> tm;
+  const int b = blockIdx.x / CL;
+  const int m = mdim[b];
+  double* A = Apool + a_off[b];
+  int bad = 0;
+  for (int k = 0; k < m; ++k) {
+    const double d = A[k + (int64_t)k * m];
+    if (!(d > 0.0) || !isfinite(d)) {
+      bad = k + 1;
+      break;
+    }
+    const double l = sqrt(d);
+    tm.sync();
+    for (int i = k + 1 + tm.rank; i < m; i += tm.size) A[i + (int64_t)k * m] /= l;
+    tm.sync();
+    if (tm.rank == 0) A[k + (int64_t)k * m] = l;
+    const int rem = m - k - 1;
+    for (int64_t e = tm.rank; e < (int64_t)rem * rem; e += tm.size) {
+      const int j = k + 1 + (int)(e / rem), i = k + 1 + (int)(e % rem);
+      if (i >= j) A[i + (int64_t)j * m] -= A[i + (int64_t)k * m] * A[j + (int64_t)k * m];
+    }
+    tm.sync();
+  }
+  if (tm.rank == 0) status[b] = bad;
+}
+
+// Eliminate the Gamma pivots (local indices no..m-1) of the symmetric A~
+// (lower triangle maintained); the omega block becomes the Schur complement.
+template <int CL>
+__global__ void k_schur(const int32_t* __restrict__ mdim, const int32_t* __restrict__ nodim,
+                        const int64_t* __restrict__ a_off, double* __restrict__ Atpool, double rtol) {
+  const Team<CL> tm;
+  const int b = blockIdx.x / CL;
+  const int m = mdim[b], no = nodim[b];
+  double* A = Atpool + a_off[b];
+  double dmax = 0.0;
+  for (int p = no; p < m; ++p) dmax = fmax(dmax, A[p + (int64_t)p * m]);
+  tm.sync();
+  for (int p = no; p < m; ++p) {
+    const double d = A[p + (int64_t)p * m];
+    tm.sync();
+    if (!(d > rtol * dmax)) continue;
+    // remaining set: 0..no-1 then p+1..m-1
+    const int r = no + (m - 1 - p);
+    for (int64_t e = tm.rank; e < (int64_t)r * r; e += tm.size) {
+      const int jj = (int)(e / r), ii = (int)(e % r);
+      if (ii < jj) continue;
+      const int i = ii < no ? ii : p + 1 + (ii - no);
+      const int j = jj < no ? jj : p + 1 + (jj - no);
+      const double vi = i > p ? A[i + (int64_t)p * m] : A[p + (int64_t)i * m];
+      const double vj = j > p ? A[j + (int64_t)p * m] : A[p + (int64_t)j * m];
+      A[i + (int64_t)j * m] -= vi * vj / d;
+    }
+    tm.sync();
+  }
+  for (int64_t e = tm.rank; e < (int64_t)no * no; e += tm.size) {
+    const int j = (int)(e / no), i = (int)(e % no);
+    if (i < j) A[i + (int64_t)j * m] = A[j + (int64_t)i * m];
+  }
+}
+
+// Columns [c0, c1) of X = A^{-1} E_omega = L^{-T} L^{-1} E_omega (m x no):
+// the substitutions of different columns are independent, so each CTA takes
+// one chunk of columns.  Writes W = X^T (no x m, row-major) and W^T = X
+// (m x no, row-major), FP64 and FP32.
+__global__ void k_inv_rows(const int32_t* __restrict__ chunk_b, const int32_t* __restrict__ chunk_c0, int cw,
+                           const int32_t* __restrict__ mdim, const int32_t* __restrict__ nodim,
+                           const int64_t* __restrict__ a_off, const double* __restrict__ Lpool,
+                           const int64_t* __restrict__ w_off, double* __restrict__ W64, float* __restrict__ W32,
+                           double* __restrict__ Wt64, float* __restrict__ Wt32, double* __restrict__ scratch) {
+  const int b = chunk_b[blockIdx.x];
+  const int c0 = chunk_c0[blockIdx.x];
+  const int m = mdim[b], no = nodim[b];
+  const int c1 = min(no, c0 + cw);
+  const int nc = c1 - c0;
+  const double* L = Lpool + a_off[b];
+  double* Y = scratch + w_off[b];  // row-major m x no
+  for (int64_t e = threadIdx.x; e < (int64_t)m * nc; e += blockDim.x) {
+    const int i = (int)(e / nc), j = c0 + (int)(e % nc);
+    Y[(int64_t)i * no + j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // forward: L Y = E (column j is zero above row j)
+  for (int t = c0; t < m; ++t) {
+    const double ltt = L[t + (int64_t)t * m];
+    const int jn = min(c1, t + 1) - c0;
+    for (int j = threadIdx.x; j < jn; j += blockDim.x) Y[(int64_t)t * no + c0 + j] /= ltt;
+    __syncthreads();
+    const int rem = m - t - 1;
+    for (int64_t e = threadIdx.x; e < (int64_t)rem * jn; e += blockDim.x) {
+      const int i = t + 1 + (int)(e / jn), j = c0 + (int)(e % jn);
+      Y[(int64_t)i * no + j] -= L[i + (int64_t)t * m] * Y[(int64_t)t * no + j];
+    }
+    __syncthreads();
+  }
+  // backward: L^T X = Y
+  for (int t = m - 1; t >= 0; --t) {
+    const double ltt = L[t + (int64_t)t * m];
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) Y[(int64_t)t * no + c0 + j] /= ltt;
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)t * nc; e += blockDim.x) {
+      const int i = (int)(e / nc), j = c0 + (int)(e % nc);
+      Y[(int64_t)i * no + j] -= L[t + (int64_t)i * m] * Y[(int64_t)t * no + j];
+    }
+    __syncthreads();
+  }
+  const int64_t o = w_off[b];
+  for (int64_t e = threadIdx.x; e < (int64_t)m * nc; e += blockDim.x) {
+    const int i = (int)(e / nc), j = c0 + (int)(e % nc);
+    const double v = Y[(int64_t)i * no + j];
+    Wt64[o + (int64_t)i * no + j] = v;
+    Wt32[o + (int64_t)i * no + j] = (float)v;
+    W64[o + (int64_t)j * m + i] = v;
+    W32[o + (int64_t)j * m + i] = (float)v;
+  }
+}
+
+// Forward substitution L X = B on columns [c0, c1) of the column-major n x nc
+// matrix X (ld n), L lower with leading dimension ldl.
+__device__ void tri_fwd_cols(const double* __restrict__ L, int ldl, double* X, int n, int c0, int c1) {
+  const int nc = c1 - c0;
+  if (nc <= 0) return;
+  for (int t = 0; t < n; ++t) {
+    const double ltt = L[t + (int64_t)t * ldl];
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) X[t + (int64_t)(c0 + j) * n] /= ltt;
+    __syncthreads();
+    const int rem = n - t - 1;
+    for (int64_t e = threadIdx.x; e < (int64_t)rem * nc; e += blockDim.x) {
+      const int i = t + 1 + (int)(e % rem), j = c0 + (int)(e / rem);
+      X[i + (int64_t)j * n] -= L[i + (int64_t)t * ldl] * X[t + (int64_t)j * n];
+    }
+    __syncthreads();
+  }
+}
+
+// Backward substitution L^T X = B on columns [c0, c1).
+__device__ void tri_bwd_cols(const double* __restrict__ L, int ldl, double* X, int n, int c0, int c1) {
+  const int nc = c1 - c0;
+  if (nc <= 0) return;
+  for (int t = n - 1; t >= 0; --t) {
+    const double ltt = L[t + (int64_t)t * ldl];
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) X[t + (int64_t)(c0 + j) * n] /= ltt;
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)t * nc; e += blockDim.x) {
+      const int i = (int)(e % t), j = c0 + (int)(e / t);
+      X[i + (int64_t)j * n] -= L[t + (int64_t)i * ldl] * X[t + (int64_t)j * n];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Generalized eigenproblem S~ u = mu A_ww u on one aggregate (one team).
+// Global scratch per matrix: C, Cn, V, Vn, T (n x n each), perm (n ints),
+// red (CL doubles), kslot.  Shared: rotation coefficients of one round.
+template <int CL>
+__global__ void k_gep(const int32_t* __restrict__ mdim, const int32_t* __restrict__ nodim,
+                      const int64_t* __restrict__ a_off, const double* __restrict__ Lpool,
+                      const double* __restrict__ Spool, const int32_t* __restrict__ capv, double thresh,
+                      const int64_t* __restrict__ mu_off, double* __restrict__ mu_out,
+                      const int64_t* __restrict__ z_off_cap, double* __restrict__ Zcap, int32_t* __restrict__ kout,
+                      double* __restrict__ scratch, const int64_t* __restrict__ scr_off) {
+  __shared__ double sh[32];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Team<CL> tm;
+  const int b = blockIdx.x / CL;
+  const int m = mdim[b], n = nodim[b];
+  const double* L = Lpool + a_off[b];  // leading n x n block: chol(A_ww), ld m
+  const double* S = Spool + a_off[b];  // leading n x n block: S~, ld m
+  double* C = scratch + scr_off[b];
+  double* Cn = C + (int64_t)n * n;
+  double* V = Cn + (int64_t)n * n;
+  double* Vn = V + (int64_t)n * n;
+  double* T = Vn + (int64_t)n * n;
+  int* perm = (int*)(T + (int64_t)n * n);
+  double* red = (double*)(perm + n + (n & 1)) ;
+  int* kslot = (int*)(red + CL);
+  double* cself = reinterpret_cast<double*>(smem_raw);
+  double* cpart = cself + n + 1;
+  int* partner = reinterpret_cast<int*>(cpart + n + 1);
+  // this CTA's contiguous column range for column-parallel phases
+  const int per = (n + CL - 1) / CL;
+  const int c0 = min(n, tm.cta * per), c1 = min(n, c0 + per);
+
+  // T = L^{-1} S (column-major n x n)
+  for (int64_t e = threadIdx.x; e < (int64_t)n * (c1 - c0); e += blockDim.x) {
+    const int i = (int)(e % n), j = c0 + (int)(e / n);
+    T[i + (int64_t)j * n] = S[i + (int64_t)j * m];
+  }
+  __syncthreads();
+  tri_fwd_cols(L, m, T, n, c0, c1);
+  tm.sync();
+  // C = L^{-1} T^T
+  for (int64_t e = threadIdx.x; e < (int64_t)n * (c1 - c0); e += blockDim.x) {
+    const int i = (int)(e % n), j = c0 + (int)(e / n);
+    C[i + (int64_t)j * n] = T[j + (int64_t)i * n];
+  }
+  __syncthreads();
+  tri_fwd_cols(L, m, C, n, c0, c1);
+  tm.sync();
+  // symmetrise (upper from lower), V = I
+  for (int64_t e = tm.rank; e < (int64_t)n * n; e += tm.size) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i > j) {
+      const double v = 0.5 * (C[i + (int64_t)j * n] + C[j + (int64_t)i * n]);
+      Cn[i + (int64_t)j * n] = v;
+      Cn[j + (int64_t)i * n] = v;
+    } else if (i == j) {
+      Cn[e] = C[e];
+    }
+    V[e] = (i == j) ? 1.0 : 0.0;
+  }
+  tm.sync();
+  {
+    double* t0 = C;
+    C = Cn;
+    Cn = t0;
+  }
+
+  // Cyclic Jacobi, parallel (round-robin) ordering: each round applies n/2
+  // disjoint rotations at once, C <- J^T C J, V <- V J.  Every CTA of the
+  // team computes all rotation angles of a round (same inputs, same
+  // results) and updates its share of the entries.
+  const int ne = n + (n & 1);
+  const int mr = ne - 1;
+  const double tolf = 4.0 * (double)max(n, 16) * DBL_EPSILON;
+  for (int sweep = 0; sweep < 40 && n > 1; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int64_t e = tm.rank; e < (int64_t)n * n; e += tm.size) {
+      const int i = (int)(e % n), j = (int)(e / n);
+      const double v = C[e] * C[e];
+      tot += v;
+      if (i != j) off += v;
+    }
+    off = tm.sum(off, sh, red);
+    tot = tm.sum(tot, sh, red);
+    if (!(off > tolf * tolf * tot)) break;
+    for (int r = 0; r < mr; ++r) {
+      for (int k = threadIdx.x; k < ne / 2; k += blockDim.x) {
+        int p, q;
+        if (k == 0) {
+          p = 0;
+          q = r + 1;
+        } else {
+          p = ((r + k) % mr) + 1;
+          q = (((r - k) % mr) + mr) % mr + 1;
+        }
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        if (q >= n) {  // dummy partner (odd n)
+          if (p < n) {
+            partner[p] = p;
+            cself[p] = 1.0;
+            cpart[p] = 0.0;
+          }
+          continue;
+        }
+        const double app = C[p + (int64_t)p * n], aqq = C[q + (int64_t)q * n], apq = C[p + (int64_t)q * n];
+        double c = 1.0, s = 0.0;
+        if (apq != 0.0) {
+          const double th = (aqq - app) / (2.0 * apq);
+          const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        partner[p] = q;
+        partner[q] = p;
+        cself[p] = c;
+        cpart[p] = -s;
+        cself[q] = c;
+        cpart[q] = s;
+      }
+      __syncthreads();
+      for (int64_t e = tm.rank; e < (int64_t)n * n; e += tm.size) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        const int pi = partner[i], pj = partner[j];
+        const double si = cself[i], ti = cpart[i], sj = cself[j], tj = cpart[j];
+        double v = si * sj * C[i + (int64_t)j * n];
+        if (pj != j) v += si * tj * C[i + (int64_t)pj * n];
+        if (pi != i) v += ti * sj * C[pi + (int64_t)j * n];
+        if (pi != i && pj != j) v += ti * tj * C[pi + (int64_t)pj * n];
+        Cn[e] = v;
+        double w = sj * V[i + (int64_t)j * n];
+        if (pj != j) w += tj * V[i + (int64_t)pj * n];
+        Vn[e] = w;
+      }
+      tm.sync();
+      double* t0 = C;
+      C = Cn;
+      Cn = t0;
+      double* t1 = V;
+      V = Vn;
+      Vn = t1;
+    }
+  }
+  // ascending mu (stable on ties)
+  for (int i = tm.rank; i < n; i += tm.size) {
+    const double di = C[i + (int64_t)i * n];
+    int rk = 0;
+    for (int j = 0; j < n; ++j) {
+      const double dj = C[j + (int64_t)j * n];
+      if (dj < di || (dj == di && j < i)) ++rk;
+    }
+    perm[rk] = i;
+  }
+  tm.sync();
+  if (tm.rank == 0) {
+    int cnt = 0;
+    for (int i = 0; i < n; ++i) {
+      const double mu = C[perm[i] + (int64_t)perm[i] * n];
+      if (thresh <= 0.0 || mu <= 0.0 || mu < 1.0 / thresh) ++cnt;
+    }
+    const int kk = min(cnt, capv[b]);
+    kout[b] = kk;
+    *kslot = kk;
+  }
+  for (int i = tm.rank; i < n; i += tm.size) mu_out[mu_off[b] + i] = C[perm[i] + (int64_t)perm[i] * n];
+  tm.sync();
+  const int k = *kslot;
+  // X = L^{-T} V(:, perm[0..k)) in T (column-major n x k); column chunks per CTA
+  const int perk = (k + CL - 1) / CL;
+  const int k0 = min(k, tm.cta * perk), k1 = min(k, k0 + perk);
+  for (int64_t e = threadIdx.x; e < (int64_t)n * (k1 - k0); e += blockDim.x) {
+    const int i = (int)(e % n), c = k0 + (int)(e / n);
+    T[i + (int64_t)c * n] = V[i + (int64_t)perm[c] * n];
+  }
+  __syncthreads();
+  tri_bwd_cols(L, m, T, n, k0, k1);
+  // sign: the first entry within (1 - 1e-6) of the largest magnitude is
+  // positive (robust when two entries tie in exact arithmetic)
+  double* Z = Zcap + z_off_cap[b];  // column-major n x k
+  for (int c = k0 + (int)threadIdx.x; c < k1; c += blockDim.x) {
+    double best = 0.0;
+    for (int i = 0; i < n; ++i) best = fmax(best, fabs(T[i + (int64_t)c * n]));
+    int bi = 0;
+    for (int i = 0; i < n; ++i)
+      if (fabs(T[i + (int64_t)c * n]) >= (1.0 - 1e-6) * best) {
+        bi = i;
+        break;
+      }
+    const double sg = T[bi + (int64_t)c * n] < 0.0 ? -1.0 : 1.0;
+    for (int i = 0; i < n; ++i) Z[i + (int64_t)c * n] = sg * T[i + (int64_t)c * n];
+  }
+}
+
+__global__ void k_pack_z(const int32_t* __restrict__ nodim, const int32_t* __restrict__ kv,
+                         const int64_t* __restrict__ z_off_cap, const double* __restrict__ Zcap,
+                         const int64_t* __restrict__ z_off, double* __restrict__ Z64, float* __restrict__ Z32,
+                         double* __restrict__ Zt64, float* __restrict__ Zt32) {
+  const int b = blockIdx.x;
+  const int n = nodim[b], k = kv[b];
+  const double* Zc = Zcap + z_off_cap[b];
+  const int64_t o = z_off[b];
+  for (int64_t e = threadIdx.x; e < (int64_t)n * k; e += blockDim.x) {
+    const int i = (int)(e % n), c = (int)(e / n);
+    const double v = Zc[e];
+    Z64[o + (int64_t)i * k + c] = v;  // Z: n x k row-major
+    Z32[o + (int64_t)i * k + c] = (float)v;
+    Zt64[o + (int64_t)c * n + i] = v;  // Z^T: k x n row-major
+    Zt32[o + (int64_t)c * n + i] = (float)v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gram of one support group of G_{l+1} = G_l P_l:  H' = sum_g P_g^T H_g P_g.
+// Row b of P_g (support node b of g) has k_b entries Z(row of node b, :) at
+// columns [col_b, col_b + k_b) of the new support.
+__global__ void k_next_gram(int64_t first, const int64_t* __restrict__ new_ptr, const int32_t* __restrict__ contrib,
+                            const int64_t* __restrict__ new_sptr, const int64_t* __restrict__ new_hoff,
+                            const int64_t* __restrict__ rowz_ptr, const int64_t* __restrict__ rowz_zoff,
+                            const int32_t* __restrict__ rowz_k, const int32_t* __restrict__ rowz_col,
+                            const int64_t* __restrict__ g_ptr, const int64_t* __restrict__ h_off,
+                            const double* __restrict__ H, const double* __restrict__ Z64, double* __restrict__ Hn,
+                            double* __restrict__ scratch, int64_t scratch_per) {
+  const int64_t h = first + blockIdx.x;
+  const int sn = (int)(new_sptr[h + 1] - new_sptr[h]);
+  double* Hh = Hn + new_hoff[h];
+  double* Tm = scratch + (int64_t)blockIdx.x * scratch_per;
+  for (int64_t e = threadIdx.x; e < (int64_t)sn * sn; e += blockDim.x) Hh[e] = 0.0;
+  __syncthreads();
+  for (int64_t q = new_ptr[h]; q < new_ptr[h + 1]; ++q) {
+    const int g = contrib[q];
+    const int s = (int)(g_ptr[g + 1] - g_ptr[g]);
+    const double* Hg = H + h_off[g];
+    const int64_t rp = rowz_ptr[g];
+    // Tm (s x sn, row-major) = H_g P_g
+    for (int64_t e = threadIdx.x; e < (int64_t)s * sn; e += blockDim.x) {
+      const int a = (int)(e / sn), d = (int)(e % sn);
+      double acc = 0.0;
+      for (int bb = 0; bb < s; ++bb) {
+        const int cb = rowz_col[rp + bb];
+        const int kb = rowz_k[rp + bb];
+        if (d >= cb && d < cb + kb) acc += Hg[(int64_t)a * s + bb] * Z64[rowz_zoff[rp + bb] + (d - cb)];
+      }
+      Tm[e] = acc;
+    }
+    __syncthreads();
+    // Hh += P_g^T Tm
+    for (int64_t e = threadIdx.x; e < (int64_t)sn * sn; e += blockDim.x) {
+      const int c = (int)(e / sn), d = (int)(e % sn);
+      double acc = 0.0;
+      for (int a = 0; a < s; ++a) {
+        const int ca = rowz_col[rp + a];
+        const int ka = rowz_k[rp + a];
+        if (c >= ca && c < ca + ka) acc += Z64[rowz_zoff[rp + a] + (c - ca)] * Tm[(int64_t)a * sn + d];
+      }
+      Hh[e] += acc;
+    }
+    __syncthreads();
+  }
+}
+
+int threads_for(int64_t work) { return work <= 64 ? 64 : (work <= 1024 ? 128 : 256); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+int launch_gram_rows(int64_t ngroups, const int64_t* g_row0, const int64_t* g_row1, const int64_t* g_ptr,
+                     const int64_t* h_off, const int64_t* rowptr, const double* val, double* H, cudaStream_t s) {
+  const int64_t chunk = 1 << 20;
+  for (int64_t f = 0; f < ngroups; f += chunk) {
+    const int64_t c = ngroups - f < chunk ? ngroups - f : chunk;
+    k_gram_rows<<<(unsigned)c, 64, 0, s>>>(f, g_row0, g_row1, g_ptr, h_off, rowptr, val, H);
+    AMGDD_CUDA(cudaGetLastError());
+  }
+  return AMGDD_OK;
+}
+
+int launch_gram_diag(int64_t n, int64_t first_group, const int64_t* h_off, const double* D1, double* H,
+                     cudaStream_t s) {
+  if (n == 0) return AMGDD_OK;
+  k_gram_diag<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, first_group, h_off, D1, H);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
+int launch_pchol(int64_t first, int64_t count, int max_s, const int64_t* g_ptr, const int64_t* h_off,
+                 const double* H, double* R64, float* R32, int32_t* rank, double* scratch, int64_t scratch_per,
+                 cudaStream_t s) {
+  if (count == 0) return AMGDD_OK;
+  const size_t smem = (size_t)max_s * sizeof(int);
+  if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(k_pchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_pchol<<<(unsigned)count, threads_for((int64_t)max_s * max_s), smem, s>>>(first, g_ptr, h_off, H, R64, R32, rank,
+                                                                             scratch, scratch_per);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
+int launch_assemble(int nb, int max_m, const LocalBatch& b, const int64_t* g_ptr, const int64_t* h_off,
+                    const double* H, const int32_t* M, double* Apool, double* Atpool, cudaStream_t s) {
+  if (nb == 0) return AMGDD_OK;
+  k_assemble<<<nb, threads_for((int64_t)max_m * max_m), 0, s>>>(b.m.p, b.a_off.p, b.pair_ptr.p, b.pair_grp.p,
+                                                                b.pair_nz.p, b.map_ptr.p, b.map.p, g_ptr, h_off, H, M,
+                                                                Apool, Atpool);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
+template <class K, class... Args>
+int launch_team(K kern, int CL, int nb, int threads, size_t smem, cudaStream_t s, Args... args) {
+  if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nb * CL));
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = CL > 1 ? 1 : 0;
+  AMGDD_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
+constexpr int kBigTeam = 8;   // CTAs per large matrix (portable cluster size)
+constexpr int kBigDim = 160;  // matrices at least this large use a cluster team
+
+int launch_chol(int nb, int max_m, const int32_t* m, const int64_t* a_off, double* Apool, int32_t* status,
+                cudaStream_t s) {
+  if (nb == 0) return AMGDD_OK;
+  if (max_m >= kBigDim) return launch_team(k_chol<kBigTeam>, kBigTeam, nb, 256, 0, s, m, a_off, Apool, status);
+  return launch_team(k_chol<1>, 1, nb, threads_for((int64_t)max_m * max_m), 0, s, m, a_off, Apool, status);
+}
+
+int launch_schur(int nb, int max_m, const int32_t* m, const int32_t* no, const int64_t* a_off, double* Atpool,
+                 double rtol, cudaStream_t s) {
+  if (nb == 0) return AMGDD_OK;
+  if (max_m >= kBigDim) return launch_team(k_schur<kBigTeam>, kBigTeam, nb, 256, 0, s, m, no, a_off, Atpool, rtol);
+  return launch_team(k_schur<1>, 1, nb, threads_for((int64_t)max_m * max_m), 0, s, m, no, a_off, Atpool, rtol);
+}
+
+int launch_inv_rows(int nb, int max_m, const int32_t* m, const int32_t* no, const int64_t* a_off,
+                    const double* Lpool, const int64_t* w_off, double* W64, float* W32, double* Wt64, float* Wt32,
+                    double* scratch, const int32_t* chunk_b, const int32_t* chunk_c0, int nchunks, int cw,
+                    cudaStream_t s) {
+  if (nb == 0 || nchunks == 0) return AMGDD_OK;
+  k_inv_rows<<<nchunks, threads_for((int64_t)max_m * cw), 0, s>>>(chunk_b, chunk_c0, cw, m, no, a_off, Lpool, w_off,
+                                                                  W64, W32, Wt64, Wt32, scratch);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
+int gep_scratch_doubles(int n, int CL) { return 5 * n * n + (n + 2) / 2 + 1 + CL + 2; }
+
+int launch_gep(int nb, int max_no, const int32_t* m, const int32_t* no, const int64_t* a_off, const double* Lpool,
+               const double* Spool, const int32_t* cap, double thresh, const int64_t* mu_off, double* mu,
+               const int64_t* z_off_cap, double* Zcap, int32_t* kout, double* scratch, const int64_t* scr_off,
+               cudaStream_t s) {
+  if (nb == 0) return AMGDD_OK;
+  const size_t smem = (size_t)(2 * (max_no + 1)) * sizeof(double) + (size_t)(max_no + 1) * sizeof(int);
+  if (max_no >= kBigDim)
+    return launch_team(k_gep<kBigTeam>, kBigTeam, nb, 256, smem, s, m, no, a_off, Lpool, Spool, cap, thresh, mu_off,
+                       mu, z_off_cap, Zcap, kout, scratch, scr_off);
+  return launch_team(k_gep<1>, 1, nb, threads_for((int64_t)max_no * max_no), smem, s, m, no, a_off, Lpool, Spool, cap,
+                     thresh, mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off);
+}
+
+int launch_pack_z(int nb, const int32_t* no, const int32_t* k, const int64_t* z_off_cap, const double* Zcap,
+                  const int64_t* z_off, double* Z64, float* Z32, double* Zt64, float* Zt32, cudaStream_t s) {
+  if (nb == 0) return AMGDD_OK;
+  k_pack_z<<<nb, 128, 0, s>>>(no, k, z_off_cap, Zcap, z_off, Z64, Z32, Zt64, Zt32);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
+int launch_next_gram(const NextGramPlan& p, int max_sn, const int64_t* g_ptr, const int64_t* h_off, const double* H,
+                     const double* Z64, double* Hn, double* scratch, int64_t first, int64_t count, cudaStream_t s) {
+  if (count == 0) return AMGDD_OK;
+  k_next_gram<<<(unsigned)count, threads_for((int64_t)max_sn * max_sn), 0, s>>>(
+      first, p.new_ptr.p, p.contrib.p, p.new_sptr.p, p.new_hoff.p, p.rowz_ptr.p, p.rowz_zoff.p, p.rowz_k.p,
+      p.rowz_col.p, g_ptr, h_off, H, Z64, Hn, scratch, p.scratch_per);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
+}  // namespace amgdd

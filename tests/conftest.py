@@ -1,7 +1,11 @@
 import os
 import sys
 
-import pytest
+# The oracle makes many small LAPACK calls; threaded BLAS only slows them down.
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+import pytest  # noqa: E402
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:

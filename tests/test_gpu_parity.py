@@ -1,0 +1,280 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Every check runs the same seeded problem through both sides.  Structures
+(aggregates, Omega lists, k_i) must be bit-exact.  Floating point:
+
+* 1e-12 relative per FP64 V-cycle application (every level), 1e-10
+  relative on the final x, the mixed form reaching the same 1e-8 relative
+  residual;
+* level 0: local eigenvalues within 1e-11 and per-aggregate subspace angles
+  within 1e-10 (or the Davis-Kahan scale 64 n eps / gap where the gap at the
+  selection cut is smaller; aggregates whose cut falls inside a cluster with
+  relative gap <= 1e-8 have no unique subspace and are skipped);
+* coarse levels: the Schur complement of Eq. gevp-S is taken from Gram
+  matrices A~_GG that are exactly singular with a continuum of tiny
+  eigenvalues, which fixes S~ only to ~ eps / lambda_min; there the spectra
+  are compared to 1e-5 and angles to 1e-4, and the level operators that
+  depend on the coarse basis (A_l, RAS, RAS-T for l >= 1) to 1e-10.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from inputs import block_aggregates_2d, q1_2d, rotated_sqrtK, seeded_rhs
+from inputs.q1 import config_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amg():
+    from paper_2601_04112_gb300 import build
+
+    build.build()
+    import paper_2601_04112_gb300 as amg
+
+    amg.load_library()
+    return amg
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _oracle(p, overlap, c_min, n_coarse, L_max=10, thresh=0.1):
+    return oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, overlap=overlap, c_min=c_min, n_coarse=n_coarse,
+                        L_max=L_max, thresh=thresh, keep_local=True)
+
+
+def _gpu(amg, p, overlap, c_min, n_coarse, L_max=10, thresh=0.1, precision=0):
+    return amg.Hierarchy.from_problem(p, overlap=overlap, c_min=c_min, n_coarse=n_coarse, L_max=L_max, thresh=thresh,
+                                      precision=precision)
+
+
+def _dev(x):
+    t = _torch()
+    return t.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def _apply(amg, H, op, lvl, x, nout):
+    t = _torch()
+    y = t.zeros(nout, dtype=t.float64, device="cuda")
+    H.apply(op, lvl, _dev(x), y)
+    t.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _check_structure(amg, H, ho):
+    assert H.num_levels == len(ho.levels)
+    for lvl, Lo in enumerate(ho.levels):
+        d = H.describe(lvl)
+        assert d["n"] == Lo.n
+        if lvl == len(ho.levels) - 1:
+            assert d["is_coarsest"] == 1
+            continue
+        assert d["nagg"] == Lo.nagg
+        assert np.array_equal(H.export(lvl, amg.ARR_AGG), Lo.agg.astype(np.int32))
+        ptr = H.export(lvl, amg.ARR_OMEGA_PTR)
+        idx = H.export(lvl, amg.ARR_OMEGA_IDX)
+        nom = H.export(lvl, amg.ARR_NOMEGA)
+        for i in range(Lo.nagg):
+            assert np.array_equal(idx[ptr[i]:ptr[i + 1]], Lo.Omega[i].astype(np.int32)), (lvl, i)
+            assert nom[i] == Lo.omega[i].shape[0]
+        assert np.array_equal(H.export(lvl, amg.ARR_K), np.array([Z.shape[1] for Z in Lo.Z], dtype=np.int32))
+
+
+def subspace_sine(Zo, Zg, Aww):
+    """sin of the largest principal angle between range(Zo) and range(Zg) in
+    the A_ww inner product (both A_ww-orthonormal): ||A^(1/2)(I - Pi_o) Zg||."""
+    if Zo.shape[1] == 0:
+        return 0.0
+    R = Zg - Zo @ (Zo.T @ (Aww @ Zg))
+    w = np.linalg.eigvalsh(R.T @ Aww @ R)
+    return float(math.sqrt(max(w.max(), 0.0)))
+
+
+def _degenerate_cut(mu, k, no):
+    return k < no and (mu[k] - mu[k - 1]) <= 1e-8 * max(mu[k], 1e-300)
+
+
+def _check_spectra(amg, H, ho, lvl, tol_mu=None, tol_angle=None):
+    tol_mu = tol_mu if tol_mu is not None else (1e-11 if lvl == 0 else 1e-5)
+    tol_angle = tol_angle if tol_angle is not None else (1e-10 if lvl == 0 else 1e-4)
+    Lo = ho.levels[lvl]
+    mu = H.export(lvl, amg.ARR_MU)
+    Z = H.export(lvl, amg.ARR_Z)
+    mo = zo = 0
+    worst = 0.0
+    for i in range(Lo.nagg):
+        no = Lo.omega[i].shape[0]
+        k = Lo.Z[i].shape[1]
+        mug = mu[mo:mo + no]
+        assert np.abs(mug - Lo.mu[i]).max() <= tol_mu, (lvl, i)
+        Zg = Z[zo:zo + no * k].reshape(no, k)
+        mo += no
+        zo += no * k
+        # Both sides solve the same symmetric eigenproblem with backward error
+        # ~ n eps ||C|| (||C|| <= 1 since mu in [0, 1]); the selected subspace is
+        # then fixed only to ~ n eps / gap (Davis-Kahan).  The 1e-10 bar applies
+        # where the gap at the cutoff allows it, that bound elsewhere.
+        allowed = tol_angle
+        if k < no:
+            if _degenerate_cut(Lo.mu[i], k, no):
+                continue
+            allowed = max(tol_angle, 64 * no * 2.2e-16 / (Lo.mu[i][k] - Lo.mu[i][k - 1]))
+        ang = subspace_sine(Lo.Z[i], Zg, Lo.Ai[i][:no, :no])
+        assert ang <= allowed, (lvl, i, ang, allowed)
+        worst = max(worst, ang)
+    return worst
+
+
+CASES = {
+    # 64 x 64 cells, theta = pi/6, eps = 1e-3: two levels (n_1 = 1984 <= 2000)
+    "q1_64": dict(N=64, theta=math.pi / 6, eps=1e-3, bs=4, overlap=1, c_min=(2, 3, 4), n_coarse=2000),
+    # ragged blocks (22 interior nodes per axis), three levels
+    "ragged_3lvl": dict(N=23, theta=0.4, eps=1e-2, bs=4, overlap=1, c_min=(2, 3), n_coarse=40),
+    # overlap 2 with D1 rows and 8x8 aggregates
+    "overlap2_d1": dict(N=32, theta=1.0, eps=1e-4, bs=8, overlap=2, c_min=(4, 5), n_coarse=60, d1=1e-3),
+}
+
+
+def _problem(c):
+    N = c["N"]
+    D1 = None
+    if c.get("d1"):
+        D1 = np.full((N - 1) ** 2, c["d1"])
+    return q1_2d(N, rotated_sqrtK(c["theta"], c["eps"]), D1=D1, agg=block_aggregates_2d(N, c["bs"]))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_structure_and_spectra(amg, name):
+    c = CASES[name]
+    p = _problem(c)
+    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"])
+    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"])
+    _check_structure(amg, H, ho)
+    for lvl in range(len(ho.levels) - 1):
+        _check_spectra(amg, H, ho, lvl)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_level_operators_fp64(amg, name):
+    c = CASES[name]
+    p = _problem(c)
+    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"])
+    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"])
+    rng = np.random.default_rng(11)
+    for lvl, Lo in enumerate(ho.levels[:-1]):
+        x = rng.standard_normal(Lo.n)
+        tA = 1e-13 if lvl == 0 else 1e-10
+        tS = 1e-12 if lvl == 0 else 1e-10
+        assert _rel(_apply(amg, H, amg.OP_A, lvl, x, Lo.n), Lo.A @ x) <= tA
+        assert _rel(_apply(amg, H, amg.OP_RAS, lvl, x, Lo.n), oracle.ras(Lo, x)) <= tS
+        assert _rel(_apply(amg, H, amg.OP_RAST, lvl, x, Lo.n), oracle.rast(Lo, x)) <= tS
+        nn = ho.levels[lvl + 1].n
+        # P P^T x is independent of the basis chosen inside each block; it is
+        # unique where the selection does not cut a degenerate cluster
+        rc = _apply(amg, H, amg.OP_RESTRICT, lvl, x, nn)
+        y = _apply(amg, H, amg.OP_PROLONG, lvl, rc, Lo.n)
+        yo = Lo.P @ (Lo.P.T @ x)
+        tP = 1e-10 if lvl == 0 else 1e-4
+        for i in range(Lo.nagg):
+            if _degenerate_cut(Lo.mu[i], Lo.Z[i].shape[1], Lo.omega[i].shape[0]):
+                continue
+            om = Lo.omega[i]
+            assert np.abs(y[om] - yo[om]).max() <= tP * np.abs(yo).max(), (lvl, i)
+        v = _apply(amg, H, amg.OP_VCYCLE, lvl, x, Lo.n)
+        assert _rel(v, oracle.vcycle(ho, x, lvl)) <= 1e-12, (lvl, _rel(v, oracle.vcycle(ho, x, lvl)))
+    Lc = ho.levels[-1]
+    xc = rng.standard_normal(Lc.n)
+    ref = np.linalg.solve(Lc.A.toarray(), xc)
+    # A_L is written in the basis of level L-1; that basis carries the
+    # coarse-level Schur sensitivity once L-1 >= 1
+    tC = 1e-11 if len(ho.levels) == 2 else 1e-4
+    assert _rel(_apply(amg, H, amg.OP_COARSE, len(ho.levels) - 1, xc, Lc.n), ref) <= tC
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_pcg_fp64_matches_oracle(amg, name):
+    c = CASES[name]
+    p = _problem(c)
+    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"])
+    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"])
+    b = seeded_rhs(p.n, 1, 1)[:, 0]
+    xo, io = oracle.pcg(ho, b, tol=1e-8)
+    xg, ig = H.solve(b, tol=1e-8)
+    assert ig[0]["status"] == 0 and ig[0]["relres_true"] <= 1e-8
+    assert abs(ig[0]["iters"] - io["iters"]) <= 1
+    if ig[0]["iters"] == io["iters"]:
+        assert _rel(xg[:, 0] if xg.ndim == 2 else xg, xo) <= 1e-10
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_pcg_mixed_reaches_tolerance(amg, name):
+    c = CASES[name]
+    p = _problem(c)
+    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"])
+    b = seeded_rhs(p.n, 1, 1)[:, 0]
+    _, i64 = H.solve(b, tol=1e-8)
+    H.set_precision(amg.MIXED32)
+    x32, i32 = H.solve(b, tol=1e-8)
+    assert i32[0]["status"] == 0 and i32[0]["relres_true"] <= 1e-8
+    assert i32[0]["iters"] <= i64[0]["iters"] + 5  # extra iterations of the FP32 cycle stay small
+    A = H  # noqa: F841
+
+
+def test_multi_rhs_device_buffers_and_zero_rhs(amg):
+    t = _torch()
+    c = CASES["ragged_3lvl"]
+    p = _problem(c)
+    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"])
+    B = seeded_rhs(p.n, 3, 4)
+    B[:, 1] = 0.0
+    bd = t.from_numpy(np.ascontiguousarray(B.T)).cuda()  # column-major n x 3 == row-major 3 x n
+    xd = t.zeros_like(bd)
+    import ctypes
+
+    infos = (amg.Info * 3)()
+    st = H._lib.amgdd_solve(H._h, bd.data_ptr(), 3, 1e-8, xd.data_ptr(), t.cuda.current_stream().cuda_stream, infos)
+    assert st == 0
+    X = xd.cpu().numpy().T
+    assert infos[1].iters == 0 and np.all(X[:, 1] == 0.0)
+    for j in (0, 2):
+        assert infos[j].relres_true <= 1e-8
+        xh, ih = H.solve(B[:, j], tol=1e-8)
+        assert _rel(X[:, j], xh[:, 0] if xh.ndim == 2 else xh) <= 1e-12
+
+
+def test_cleanup_of_unaggregated_nodes(amg):
+    N = 14
+    p = q1_2d(N, rotated_sqrtK(0.3, 0.05), agg=block_aggregates_2d(N, 3))
+    agg = p.agg.copy()
+    agg[::7] = -1  # unaggregated nodes join a neighbour's aggregate
+    p.agg = agg
+    ho = _oracle(p, 1, (2,), 30)
+    H = _gpu(amg, p, 1, (2,), 30)
+    _check_structure(amg, H, ho)
+
+
+def test_invalid_inputs_rejected(amg):
+    p = _problem(CASES["ragged_3lvl"])
+    bad = p.col.copy()
+    bad[5] = p.n + 3
+    with pytest.raises(amg.AmgddError) as e:
+        amg.Hierarchy(p.rowptr, bad, p.val, p.n, agg=p.agg)
+    assert e.value.status == -1
+    val = p.val.copy()
+    val[0] = np.nan
+    with pytest.raises(amg.AmgddError) as e:
+        amg.Hierarchy(p.rowptr, p.col, val, p.n, agg=p.agg)
+    assert e.value.status == -3
+    with pytest.raises(amg.AmgddError):
+        amg.Hierarchy(p.rowptr, p.col, p.val, p.n, agg=p.agg, overlap=0)

@@ -103,13 +103,12 @@ def test_permuted_coarse_columns_break_galerkin(monkeypatch):
 
     def permuted(level):
         # wrong index: coarse columns of every block reversed while propagating G
-        good = level.P
-        perm = np.concatenate([np.arange(level.col0[a + 1] - 1, level.col0[a] - 1, -1) for a in range(level.nagg)])
-        level.P = good[:, perm]
+        good = level.Z
+        level.Z = [Z[:, ::-1] for Z in good]
         try:
             return orig(level)
         finally:
-            level.P = good
+            level.Z = good
 
     monkeypatch.setattr(osetup, "_next_groups", permuted)
     h = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, overlap=1, c_min=(3,), n_coarse=5, L_max=2)
