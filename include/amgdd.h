@@ -147,6 +147,25 @@ int amgdd_set_precision(amgdd_hierarchy* h, int precision);
  * MIXED32).  x and y must not alias.                                     */
 int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* y, void* stream);
 
+/* Same operators and arguments as amgdd_apply, but the call allocates no
+ * device memory: no cudaMalloc, no cudaFree, no allocating library routine.
+ * It is meant for callers that must not allocate once setup is done, for
+ * example code that runs while another component owns the device memory
+ * budget or inside an allocator-free serving loop (amgdd_setup itself still
+ * allocates the hierarchy).  The paper has no counterpart: this is an
+ * interface convenience, not a step of the method.
+ * In MIXED32 the FP64 x and y are staged through FP32 vectors kept in one
+ * file-scope device array of 2 x 131072 floats (1 MiB); every GPU that loads
+ * the library holds that array until the process exits.  Levels whose
+ * input or output vector has more than 131072 entries are rejected with
+ * AMGDD_ERR_INVALID_ARG in MIXED32 (FP64 needs no staging and has no limit).
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU (other streams,
+ * other host threads) race on it.  The call synchronises `stream` before
+ * returning, as amgdd_apply does.                                          */
+int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, double* y, void* stream);
+
 /* ---- inspection ------------------------------------------------------ */
 typedef struct {
   int64_t n;           /* unknowns on this level                          */

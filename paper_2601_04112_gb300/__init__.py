@@ -31,7 +31,7 @@ EXPORTED = [
     "amgdd_params_default", "amgdd_setup", "amgdd_solve", "amgdd_set_precision", "amgdd_apply",
     "amgdd_num_levels", "amgdd_level_describe", "amgdd_level_export", "amgdd_hierarchy_stats",
     "amgdd_bytes_model", "amgdd_free", "amgdd_status_string", "amgdd_last_error", "amgdd_profile_vcycle",
-    "amgdd_kernel_launches",
+    "amgdd_kernel_launches", "amgdd_apply_noalloc",
 ]
 
 
@@ -78,6 +78,8 @@ def load_library(path: str = LIB_PATH):
     lib.amgdd_solve.argtypes = [vp, vp, i32, dbl, vp, vp, ctypes.POINTER(Info)]
     lib.amgdd_set_precision.argtypes = [vp, i32]
     lib.amgdd_apply.argtypes = [vp, i32, i32, vp, vp, vp]
+    lib.amgdd_apply_noalloc.argtypes = [vp, i32, i32, vp, vp, vp]
+    lib.amgdd_apply_noalloc.restype = i32
     lib.amgdd_num_levels.argtypes = [vp]
     lib.amgdd_level_describe.argtypes = [vp, i32, ctypes.POINTER(LevelDesc)]
     lib.amgdd_level_export.argtypes = [vp, i32, i32, vp, ctypes.c_size_t]

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <string>
@@ -1244,6 +1245,124 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
       return AMGDD_ERR_INVALID_ARG;
   }
   if (f32) AMGDD_TRY(launch_cast(yout32.p, true, y, false, nout, nullptr, s));
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  return AMGDD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of amgdd_apply.  In MIXED32 amgdd_apply stages the
+// FP64 caller vectors through two FP32 work vectors that it allocates on
+// every call.  Here the staging lives in one file-scope device array, so
+// the call never allocates.  The array holds 2 x kNoAllocMaxN floats (1 MiB)
+// on every device that loads the library, until the process exits.
+constexpr int64_t kNoAllocMaxN = (int64_t)1 << 17;
+static __device__ __align__(256) float g_noalloc_stage[2 * kNoAllocMaxN];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+float* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of the staging array on the current device.  Host code
+// may not use the symbol itself: it names a host-side stand-in.  The
+// address is looked up once per device, with that device current.
+int noalloc_stage(float** out) {
+  int dev = 0;
+  AMGDD_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_error("amgdd_apply_noalloc: device id %d out of range", dev);
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    AMGDD_CUDA(cudaGetSymbolAddress(&p, g_noalloc_stage));
+    g_noalloc_ptr[dev] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return AMGDD_OK;
+}
+}  // namespace
+
+int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, double* y, void* stream) {
+  if (h == nullptr || x == nullptr || y == nullptr || level < 0 || level >= (int)h->lv.size()) {
+    set_error("amgdd_apply_noalloc: invalid argument");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Level& L = *h->lv[level];
+  const bool f32 = h->precision == AMGDD_MIXED32;
+  const bool coarsest_op = op == AMGDD_OP_COARSE || (op == AMGDD_OP_VCYCLE && L.coarsest);
+  if (coarsest_op) {
+    if (!L.coarsest) {
+      set_error("amgdd_apply_noalloc: COARSE needs the coarsest level");
+      return AMGDD_ERR_INVALID_ARG;
+    }
+    AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, x, y, false, SEG_STORE, nullptr, s));
+    AMGDD_CUDA(cudaStreamSynchronize(s));
+    return AMGDD_OK;
+  }
+  if (L.coarsest && op != AMGDD_OP_A) {
+    set_error("amgdd_apply_noalloc: operator not defined on the coarsest level");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  if (op == AMGDD_OP_A && L.aplan.ntasks == 0 && level != 0) {
+    set_error("amgdd_apply_noalloc: A is not stored on the coarsest level");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  if ((op == AMGDD_OP_RESTRICT || op == AMGDD_OP_PROLONG) && level + 1 >= (int)h->lv.size()) {
+    set_error("amgdd_apply_noalloc: no coarser level below level %d", level);
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  const int64_t nin = op == AMGDD_OP_PROLONG ? h->lv[level + 1]->n : L.n;
+  const int64_t nout = op == AMGDD_OP_RESTRICT ? h->lv[level + 1]->n : L.n;
+  const void* xin = x;
+  void* yout = y;
+  float* stage = nullptr;
+  if (f32) {
+    if (nin > kNoAllocMaxN || nout > kNoAllocMaxN) {
+      set_error("amgdd_apply_noalloc: vectors of %lld and %lld entries exceed the fixed staging size of %lld "
+                "entries per vector (MIXED32); use amgdd_apply",
+                (long long)nin, (long long)nout, (long long)kNoAllocMaxN);
+      return AMGDD_ERR_INVALID_ARG;
+    }
+    AMGDD_TRY(noalloc_stage(&stage));
+    AMGDD_TRY(launch_cast(x, false, stage, true, nin, nullptr, s));
+    xin = stage;
+    yout = stage + kNoAllocMaxN;
+  }
+  const size_t esz = f32 ? sizeof(float) : sizeof(double);
+  switch (op) {
+    case AMGDD_OP_A:
+      AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
+      AMGDD_TRY(launch_apply(L.aplan, L, f32, xin, yout, +1, nullptr, s));
+      break;
+    case AMGDD_OP_RAS:
+      AMGDD_TRY(launch_seg(L.ras, f32 ? (const void*)L.W32.p : (const void*)L.W64.p, f32, xin, yout, f32, SEG_STORE,
+                           nullptr, s));
+      break;
+    case AMGDD_OP_RAST:
+      AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
+      AMGDD_TRY(launch_seg(L.rast, f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p, f32, xin, yout, f32,
+                           SEG_ATOMIC_ADD, nullptr, s));
+      break;
+    case AMGDD_OP_RESTRICT:
+      AMGDD_TRY(launch_seg(L.restr, f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p, f32, xin, yout, f32,
+                           SEG_STORE, nullptr, s));
+      break;
+    case AMGDD_OP_PROLONG:
+      AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
+      AMGDD_TRY(launch_seg(L.prol, f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p, f32, xin, yout, f32, SEG_ADD,
+                           nullptr, s));
+      break;
+    case AMGDD_OP_VCYCLE:
+      AMGDD_TRY(vcycle(*h, level, f32, xin, yout, nullptr, s));
+      break;
+    default:
+      set_error("amgdd_apply_noalloc: unknown operator %d", op);
+      return AMGDD_ERR_INVALID_ARG;
+  }
+  if (f32) AMGDD_TRY(launch_cast(yout, true, y, false, nout, nullptr, s));
   AMGDD_CUDA(cudaStreamSynchronize(s));
   return AMGDD_OK;
 }
