@@ -351,6 +351,13 @@ def run_ours(args):
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
                 "vcycle": {"ms": vcyc_ms, "bytes": float(by.sum()),
                            "achieved_gbs": float(by.sum()) / (vcyc_ms * 1e-3) / 1e9}}
+    slot_names = {0: "ras_or_coarse", 1: "cast_in", 2: "residual_applies", 3: "restrict", 4: "prolong",
+                  5: "cast_out", 7: "rast"}
+    vprof = []
+    for l in range(ms.shape[0]):
+        vprof.append({slot_names[k]: [round(float(ms[l, k]) * 1e3, 1),
+                                      round(float(by[l, k]) / max(float(ms[l, k]) * 1e-3, 1e-12) / 1e9)]
+                      for k in slot_names if ms[l, k] > 0})
 
     # end to end through the C ABI with pinned host buffers
     Bp = torch.empty((nsol, n), dtype=torch.float64, pin_memory=True)
@@ -395,7 +402,8 @@ def run_ours(args):
         "vcycles_per_s": {"mixed": vc_mix, "fp64": vc_64},
         "iters": it_mix, "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "setup_s": setup_s, "levels": stats["n"], "op_complexity": stats["op_complexity"],
-        "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+        "roofline": roofline, "vcycle_profile_us_gbs": vprof,
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

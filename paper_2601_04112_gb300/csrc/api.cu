@@ -114,9 +114,12 @@ int fetch_any(std::vector<T>& h, const T* src, size_t n, bool dev, cudaStream_t 
 
 int lanes_for(int max_nc) { return max_nc >= 64 ? 32 : (max_nc >= 24 ? 16 : (max_nc >= 8 ? 8 : 4)); }
 
+// force: 0 picks the mode from the row length, 1 lanes-per-row chunks,
+// 2 row per lane (the caller then passes the transposed copy).
 int build_seg(SegPlan& p, const std::vector<int32_t>& nr, const std::vector<int32_t>& nc,
               const std::vector<int64_t>& m_off, const std::vector<int64_t>& in_off,
-              const std::vector<int64_t>& out_off, const int32_t* in_ext, const int32_t* out_ext, cudaStream_t s) {
+              const std::vector<int64_t>& out_off, const int32_t* in_ext, const int32_t* out_ext, cudaStream_t s,
+              int force = 0) {
   p.nblocks = (int)nr.size();
   p.max_nc = 0;
   p.mat_len = 0;
@@ -130,16 +133,48 @@ int build_seg(SegPlan& p, const std::vector<int32_t>& nr, const std::vector<int3
   p.in_len = cols;
   p.out_len = rows;
   p.lanes = lanes_for(p.max_nc);
-  p.rows_per_chunk = 2 * (256 / p.lanes);
-  std::vector<int32_t> cb, cr;
-  for (int b = 0; b < p.nblocks; ++b)
-    for (int r = 0; r < nr[b]; r += p.rows_per_chunk) {
-      cb.push_back(b);
-      cr.push_back(r);
-    }
-  p.nchunks = (int)cb.size();
+  // rows per CTA: enough CTAs to fill the GPU (8 per SM), at least one row
+  // per lane group
+  {
+    const int ngrp = 128 / p.lanes;
+    int64_t rpc = rows / (152 * 8);
+    rpc = std::max<int64_t>(ngrp, std::min<int64_t>(64, (rpc + ngrp - 1) / ngrp * ngrp));
+    p.rows_per_chunk = (int)rpc;
+  }
+  // 16-byte vector loads when every row starts aligned (FP32 and FP64 copies
+  // share offsets, so 4-element alignment serves both)
+  p.vec = p.nblocks > 0;
+  for (int b = 0; b < p.nblocks && p.vec; ++b)
+    if (nc[b] % 4 != 0 || m_off[b] % 4 != 0) p.vec = false;
   p.in_idx_ext = in_ext;
   p.out_idx_ext = out_ext;
+  // short rows: one lane per output row over the transposed copy
+  p.rows_mode = force == 2 || (force == 0 && p.max_nc <= 128);
+  if (p.rows_mode) {
+    int max_nr = 0;
+    for (int b = 0; b < p.nblocks; ++b) max_nr = std::max(max_nr, nr[b]);
+    p.kind = max_nr >= 24 ? 32 : (max_nr >= 12 ? 16 : 8);
+    std::vector<int32_t> tb, tr, tn;
+    for (int b = 0; b < p.nblocks; ++b) {
+      for (int r = 0; r < nr[b]; r += p.kind) {
+        tb.push_back(b);
+        tr.push_back(r);
+        tn.push_back(std::min(p.kind, nr[b] - r));
+      }
+    }
+    p.ntasks = (int)tb.size();
+    AMGDD_TRY(p.task_blk.upload(tb, s));
+    AMGDD_TRY(p.task_row0.upload(tr, s));
+    AMGDD_TRY(p.task_nrow.upload(tn, s));
+  }
+  std::vector<int32_t> cb, cr;
+  if (!p.rows_mode)
+    for (int b = 0; b < p.nblocks; ++b)
+      for (int r = 0; r < nr[b]; r += p.rows_per_chunk) {
+        cb.push_back(b);
+        cr.push_back(r);
+      }
+  p.nchunks = (int)cb.size();
   AMGDD_TRY(p.nr.upload(nr, s));
   AMGDD_TRY(p.nc.upload(nc, s));
   AMGDD_TRY(p.m_off.upload(m_off, s));
@@ -158,28 +193,41 @@ int apply_kind(int sz) {
   if (sz <= 64) return 4;
   if (sz <= 128) return 5;
   if (sz <= 256) return 6;
-  if (sz <= 512) return 7;
-  if (sz <= 2048) return 8;
-  return -1;
+  return 7;  // up to kApplyMaxS
 }
-const int kKindLanes[9] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
+const int kKindLanes[8] = {1, 8, 16, 32, 32, 32, 32, 32};
+constexpr int kApplyMaxS = 512;  // wider supports use the two-pass plans
+constexpr int kWideRows = 8;     // rows per task of the wide kinds
 
 int build_apply(Level& L, cudaStream_t s) {
   ApplyPlan& p = L.aplan;
   const int64_t ng = (int64_t)L.g_ptr.size() - 1;
-  std::vector<std::vector<int32_t>> tg(9), tr(9), tn(9);
+  std::vector<std::vector<int32_t>> tg(8), tr(8), tn(8);
   p.r_len = 0;
+  // wide supports: t = R_g x(S_g), then y(S_g) -= R_g^T t
+  std::vector<int32_t> n1, c1, n2, c2;
+  std::vector<int64_t> moff, in1, out1, in2, out2;
+  int64_t toff = 0;
   for (int64_t g = 0; g < ng; ++g) {
     const int sz = (int)(L.g_ptr[g + 1] - L.g_ptr[g]);
     const int rk = L.g_rank[g];
     if (rk == 0 || sz == 0) continue;
-    const int kd = apply_kind(sz);
-    if (kd < 0) {
-      set_error("row group with %d support columns exceeds the A-apply limit of 2048", sz);
-      return AMGDD_ERR_INTERNAL;
+    if (sz > kApplyMaxS) {
+      n1.push_back(rk);
+      c1.push_back(sz);
+      n2.push_back(sz);
+      c2.push_back(rk);
+      moff.push_back(L.h_off[g]);
+      in1.push_back(L.g_ptr[g]);
+      out1.push_back(toff);
+      in2.push_back(toff);
+      out2.push_back(L.g_ptr[g]);
+      toff += rk;
+      continue;
     }
+    const int kd = apply_kind(sz);
     p.r_len += (int64_t)rk * sz;
-    const int chunk = sz <= 32 ? rk : 32;
+    const int chunk = kd >= 4 ? kWideRows : rk;
     for (int r = 0; r < rk; r += chunk) {
       tg[kd].push_back((int32_t)g);
       tr[kd].push_back(r);
@@ -189,9 +237,9 @@ int build_apply(Level& L, cudaStream_t s) {
   std::vector<int32_t> ag, ar, an;
   p.nbuckets = 0;
   int cta = 0;
-  for (int kd = 0; kd < 9; ++kd) {
+  for (int kd = 0; kd < 8; ++kd) {
     if (tg[kd].empty()) continue;
-    const int per = kd == 8 ? 4 : 128 / kKindLanes[kd];
+    const int per = kd == 0 ? 128 : 128 / kKindLanes[kd];
     p.bucket_kind[p.nbuckets] = kd;
     p.bucket_start[p.nbuckets] = cta;
     p.bucket_tasks[p.nbuckets] = (int)tg[kd].size();
@@ -206,6 +254,16 @@ int build_apply(Level& L, cudaStream_t s) {
   AMGDD_TRY(p.task_grp.upload(ag, s));
   AMGDD_TRY(p.task_row0.upload(ar, s));
   AMGDD_TRY(p.task_nrow.upload(an, s));
+  L.t_len = toff;
+  if (toff > 0) {
+    std::vector<int32_t> io(toff);
+    std::iota(io.begin(), io.end(), 0);
+    AMGDD_TRY(L.d_tidx.upload(io, s));
+    AMGDD_TRY(L.t64.alloc(toff));
+    AMGDD_TRY(L.t32.alloc(toff));
+    AMGDD_TRY(build_seg(L.gt1, n1, c1, moff, in1, out1, L.d_g_idx.p, L.d_tidx.p, s, 1));
+    AMGDD_TRY(build_seg(L.gt2, n2, c2, moff, in2, out2, L.d_tidx.p, L.d_g_idx.p, s, 2));
+  }
   return AMGDD_OK;
 }
 
@@ -226,14 +284,16 @@ struct amgdd_hierarchy {
   DBuf<double> x, r, z, zold, p, q, b, partials;
   DBuf<PcgState> st;
   PcgState* st_host = nullptr;
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  int64_t gkernels[2] = {0, 0};
+  cudaGraphExec_t ginit[2] = {nullptr, nullptr}, gloop[2] = {nullptr, nullptr};
+  int64_t ginit_kernels[2] = {0, 0}, gloop_kernels[2] = {0, 0};
   cudaStream_t work = nullptr;  // solves run here (capturable, unlike the legacy stream)
   cudaEvent_t join[2] = {nullptr, nullptr};
   double setup_ms = 0.0;
   ~amgdd_hierarchy() {
-    for (auto& g : gexec)
-      if (g) cudaGraphExecDestroy(g);
+    for (int i = 0; i < 2; ++i) {
+      if (ginit[i]) cudaGraphExecDestroy(ginit[i]);
+      if (gloop[i]) cudaGraphExecDestroy(gloop[i]);
+    }
     if (st_host) cudaFreeHost(st_host);
     for (auto& e : join)
       if (e) cudaEventDestroy(e);
@@ -704,6 +764,25 @@ int build_coarsest(amgdd_hierarchy& h, Level& L, cudaStream_t s) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Algorithmic bytes: stored matrix values, index arrays, and one pass over
+// each input and output vector (two for read-modify-write outputs).
+static double seg_bytes(const SegPlan& p, int64_t nin, int64_t nout, bool rmw, size_t esz) {
+  return (double)p.mat_len * esz + (double)(p.in_len + p.out_len) * 4.0 + (double)nin * esz +
+         (double)nout * esz * (rmw ? 2.0 : 1.0);
+}
+
+// One A-apply (residual form y -= A x) of level L.
+static double apply_bytes(const Level& L, size_t esz) {
+  double b = (double)L.aplan.r_len * esz + 3.0 * L.n * esz;
+  for (size_t g = 0; g + 1 < L.g_ptr.size() && g < L.g_rank.size(); ++g) {
+    const int64_t sz = L.g_ptr[g + 1] - L.g_ptr[g];
+    if (L.g_rank[g] > 0 && sz <= 512) b += (double)sz * 4.0;
+  }
+  if (L.t_len > 0) b += seg_bytes(L.gt1, 0, L.t_len, false, esz) + seg_bytes(L.gt2, L.t_len, 0, false, esz);
+  return b;
+}
+
+// ---------------------------------------------------------------------------
 // Event marks between the launches of one V-cycle (profiling only): the time
 // from mark i to mark i+1 is charged to (level, slot) of mark i.
 struct VProf {
@@ -739,12 +818,13 @@ static int vcycle(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, c
       AMGDD_MARK(1);
       AMGDD_TRY(launch_cast(r, true, L.r64.p, false, L.n, skip, s));
       AMGDD_MARK(0);
-      AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, L.r64.p, L.x64.p, false, SEG_STORE, skip, s));
+      AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, L.r64.p, L.x64.p, false, SEG_STORE, skip, s, nullptr, nullptr,
+                           L.Wt64.p));
       AMGDD_MARK(5);
       return launch_cast(L.x64.p, false, x, true, L.n, skip, s);
     }
     AMGDD_MARK(0);
-    return launch_seg(L.ras, L.W64.p, false, r, x, false, SEG_STORE, skip, s);
+    return launch_seg(L.ras, L.W64.p, false, r, x, false, SEG_STORE, skip, s, nullptr, nullptr, L.Wt64.p);
   }
   Level& N = *h.lv[l + 1];
   const void* W = f32 ? (const void*)L.W32.p : (const void*)L.W64.p;
@@ -754,27 +834,24 @@ static int vcycle(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, c
   void* sv = f32 ? (void*)L.s32.p : (void*)L.s64.p;
   void* rn = f32 ? (void*)N.r32.p : (void*)N.r64.p;
   void* xn = f32 ? (void*)N.x32.p : (void*)N.x64.p;
-  // pre-smoothing from x = 0: x = M_RAS^{-1} r  (Eq. ras)
+  // pre-smoothing from x = 0: x = M_RAS^{-1} r  (Eq. ras); the same launch
+  // copies s(omega_i) = r(omega_i) for the residual
   AMGDD_MARK(0);
-  AMGDD_TRY(launch_seg(L.ras, W, f32, r, x, f32, SEG_STORE, skip, s));
+  AMGDD_TRY(launch_seg(L.ras, W, f32, r, x, f32, SEG_STORE, skip, s, r, sv, Wt));
   // s = r - A x ; r_c = P^T s
-  AMGDD_MARK(1);
-  AMGDD_TRY(launch_copy_vec(r, sv, f32, L.n, skip, s));
   AMGDD_MARK(2);
   AMGDD_TRY(launch_apply(L.aplan, L, f32, x, sv, -1, skip, s));
   AMGDD_MARK(3);
-  AMGDD_TRY(launch_seg(L.restr, Zt, f32, sv, rn, f32, SEG_STORE, skip, s));
+  AMGDD_TRY(launch_seg(L.restr, Zt, f32, sv, rn, f32, SEG_STORE, skip, s, nullptr, nullptr, Z));
   // x_c = B_{l+1} r_c ; x += P x_c  (Eq. cgc)
   AMGDD_TRY(vcycle(h, l + 1, f32, rn, xn, skip, s, prof));
   AMGDD_MARK(4);
-  AMGDD_TRY(launch_seg(L.prol, Z, f32, xn, x, f32, SEG_ADD, skip, s));
+  AMGDD_TRY(launch_seg(L.prol, Z, f32, xn, x, f32, SEG_ADD, skip, s, r, sv, Zt));
   // post-smoothing: x += M_RAS-T^{-1} (r - A x)  (Eq. ras-t)
-  AMGDD_MARK(1);
-  AMGDD_TRY(launch_copy_vec(r, sv, f32, L.n, skip, s));
   AMGDD_MARK(2);
   AMGDD_TRY(launch_apply(L.aplan, L, f32, x, sv, -1, skip, s));
   AMGDD_MARK(7);
-  AMGDD_TRY(launch_seg(L.rast, Wt, f32, sv, x, f32, SEG_ATOMIC_ADD, skip, s));
+  AMGDD_TRY(launch_seg(L.rast, Wt, f32, sv, x, f32, SEG_ATOMIC_ADD, skip, s, nullptr, nullptr, W));
   return AMGDD_OK;
 }
 
@@ -796,7 +873,8 @@ static int apply_fine64(amgdd_hierarchy& h, const double* p, double* q, const in
   return launch_apply(L0.aplan, L0, false, p, q, +1, skip, s);
 }
 
-static int pcg_iteration(amgdd_hierarchy& h, cudaStream_t s) {
+static int pcg_iteration(amgdd_hierarchy& h, cudaStream_t s, cudaGraphConditionalHandle cond = 0,
+                         int use_cond = 0) {
   const int64_t n = h.n;
   PcgState* st = h.st.p;
   const int* done = &st->done;
@@ -809,8 +887,64 @@ static int pcg_iteration(amgdd_hierarchy& h, cudaStream_t s) {
   AMGDD_TRY(precondition(h, h.r.p, h.z.p, done, s));
   const bool flex = h.precision == AMGDD_MIXED32;
   AMGDD_TRY(launch_dot_partial(h.r.p, h.z.p, flex ? h.zold.p : nullptr, n, h.partials.p, done, s));
-  AMGDD_TRY(launch_pcg_scalar(3, st, h.partials.p, s));
+  AMGDD_TRY(launch_pcg_scalar(3, st, h.partials.p, s, cond, use_cond));
   AMGDD_TRY(launch_update_p(st, h.p.p, h.z.p, flex ? h.zold.p : nullptr, n, s));
+  return AMGDD_OK;
+}
+
+// CG start: r = b, x = 0, ||b||^2, z = B r, p = z, r^T z.
+static int pcg_start(amgdd_hierarchy& h, cudaStream_t s) {
+  const int64_t n = h.n;
+  PcgState* st = h.st.p;
+  const int* done = &st->done;
+  AMGDD_CUDA(cudaMemcpyAsync(h.r.p, h.b.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  AMGDD_CUDA(cudaMemsetAsync(h.x.p, 0, n * sizeof(double), s));
+  AMGDD_TRY(launch_dot_partial(h.b.p, h.b.p, nullptr, n, h.partials.p, nullptr, s));
+  AMGDD_TRY(launch_pcg_scalar(4, st, h.partials.p, s));
+  AMGDD_TRY(precondition(h, h.r.p, h.z.p, done, s));
+  AMGDD_TRY(launch_copy_vec(h.z.p, h.p.p, false, n, done, s));
+  if (h.precision == AMGDD_MIXED32) AMGDD_TRY(launch_copy_vec(h.z.p, h.zold.p, false, n, done, s));
+  AMGDD_TRY(launch_dot_partial(h.r.p, h.z.p, nullptr, n, h.partials.p, done, s));
+  AMGDD_TRY(launch_pcg_scalar(0, st, h.partials.p, s));
+  return AMGDD_OK;
+}
+
+// Graphs of one precision: the CG start, and a WHILE node whose body is one
+// CG iteration; the iteration's scalar kernel sets the loop condition on the
+// device, so a whole solve runs without returning to the host.
+static int build_solve_graphs(amgdd_hierarchy& h, int pi, cudaStream_t s) {
+  cudaGraph_t g;
+  AMGDD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  capture_begin();
+  int rc = pcg_start(h, s);
+  h.ginit_kernels[pi] = capture_end();
+  cudaError_t ce = cudaStreamEndCapture(s, &g);
+  if (rc != AMGDD_OK) return rc;
+  AMGDD_CUDA(ce);
+  AMGDD_CUDA(cudaGraphInstantiate(&h.ginit[pi], g, 0));
+  cudaGraphDestroy(g);
+
+  cudaGraph_t lg;
+  AMGDD_CUDA(cudaGraphCreate(&lg, 0));
+  cudaGraphConditionalHandle cond;
+  AMGDD_CUDA(cudaGraphConditionalHandleCreate(&cond, lg, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  AMGDD_CUDA(cudaGraphAddNode(&node, lg, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  AMGDD_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  capture_begin();
+  rc = pcg_iteration(h, s, cond, 1);
+  h.gloop_kernels[pi] = capture_end();
+  ce = cudaStreamEndCapture(s, &body);
+  if (rc != AMGDD_OK) return rc;
+  AMGDD_CUDA(ce);
+  AMGDD_CUDA(cudaGraphInstantiate(&h.gloop[pi], lg, 0));
+  cudaGraphDestroy(lg);
   return AMGDD_OK;
 }
 
@@ -823,54 +957,30 @@ static int solve_one(amgdd_hierarchy& h, const double* bsrc, bool bdev, double t
   AMGDD_CUDA(cudaEventRecord(e0, s));
   AMGDD_CUDA(cudaMemcpyAsync(h.b.p, bsrc, n * sizeof(double), bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                              s));
-  AMGDD_CUDA(cudaMemcpyAsync(h.r.p, h.b.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  AMGDD_CUDA(cudaMemsetAsync(h.x.p, 0, n * sizeof(double), s));
   PcgState init{};
   init.tol2 = tol * tol;
   init.max_iter = h.prm.max_iter;
   init.flexible = h.precision == AMGDD_MIXED32 ? 1 : 0;
   *h.st_host = init;
   AMGDD_CUDA(cudaMemcpyAsync(h.st.p, h.st_host, sizeof(PcgState), cudaMemcpyHostToDevice, s));
-  PcgState* st = h.st.p;
-  const int* done = &st->done;
-  AMGDD_TRY(launch_dot_partial(h.b.p, h.b.p, nullptr, n, h.partials.p, nullptr, s));
-  AMGDD_TRY(launch_pcg_scalar(4, st, h.partials.p, s));
-  AMGDD_TRY(precondition(h, h.r.p, h.z.p, done, s));
-  AMGDD_TRY(launch_copy_vec(h.z.p, h.p.p, false, n, done, s));
-  if (h.precision == AMGDD_MIXED32) AMGDD_TRY(launch_copy_vec(h.z.p, h.zold.p, false, n, done, s));
-  AMGDD_TRY(launch_dot_partial(h.r.p, h.z.p, nullptr, n, h.partials.p, done, s));
-  AMGDD_TRY(launch_pcg_scalar(0, st, h.partials.p, s));
-  const int K = std::max(1, h.prm.check_every);
   const int pi = h.precision == AMGDD_MIXED32 ? 1 : 0;
-  bool first_batch = true;
-  for (;;) {
-    if (h.prm.use_graph && h.gexec[pi] != nullptr) {
-      AMGDD_CUDA(cudaGraphLaunch(h.gexec[pi], s));
-      count_graph_launch(h.gkernels[pi]);
-    } else if (h.prm.use_graph && !first_batch) {
-      cudaGraph_t g;
-      AMGDD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      capture_begin();
-      int rc = AMGDD_OK;
-      for (int k = 0; k < K && rc == AMGDD_OK; ++k) rc = pcg_iteration(h, s);
-      h.gkernels[pi] = capture_end();
-      cudaError_t ce = cudaStreamEndCapture(s, &g);
-      if (rc != AMGDD_OK) return rc;
-      AMGDD_CUDA(ce);
-      AMGDD_CUDA(cudaGraphInstantiate(&h.gexec[pi], g, 0));
-      cudaGraphDestroy(g);
-      AMGDD_CUDA(cudaGraphLaunch(h.gexec[pi], s));
-      count_graph_launch(h.gkernels[pi]);
-    } else {
-      for (int k = 0; k < K; ++k) AMGDD_TRY(pcg_iteration(h, s));
-    }
-    first_batch = false;
+  if (h.prm.use_graph) {
+    if (h.gloop[pi] == nullptr) AMGDD_TRY(build_solve_graphs(h, pi, s));
+    AMGDD_CUDA(cudaGraphLaunch(h.ginit[pi], s));
+    count_graph_launch(h.ginit_kernels[pi]);
+    AMGDD_CUDA(cudaGraphLaunch(h.gloop[pi], s));
     AMGDD_CUDA(cudaMemcpyAsync(h.st_host, h.st.p, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-    AMGDD_CUDA(cudaStreamSynchronize(s));
-    if (h.st_host->done) break;
+  } else {
+    AMGDD_TRY(pcg_start(h, s));
+    const int K = std::max(1, h.prm.check_every);
+    for (;;) {
+      for (int k = 0; k < K; ++k) AMGDD_TRY(pcg_iteration(h, s));
+      AMGDD_CUDA(cudaMemcpyAsync(h.st_host, h.st.p, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+      AMGDD_CUDA(cudaStreamSynchronize(s));
+      if (h.st_host->done) break;
+    }
   }
-  const PcgState fin = *h.st_host;
-  // true residual ||b - A x|| in FP64
+  // true residual ||b - A x|| in FP64 (enqueued behind the solve; one sync)
   AMGDD_CUDA(cudaMemcpyAsync(h.q.p, h.b.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   AMGDD_TRY(launch_apply(h.lv[0]->aplan, *h.lv[0], false, h.x.p, h.q.p, -1, nullptr, s));
   AMGDD_TRY(launch_dot_partial(h.q.p, h.q.p, nullptr, n, h.partials.p, nullptr, s));
@@ -879,6 +989,8 @@ static int solve_one(amgdd_hierarchy& h, const double* bsrc, bool bdev, double t
                              s));
   AMGDD_CUDA(cudaEventRecord(e1, s));
   AMGDD_TRY(download(part, h.partials.p, 2 * kDotBlocks, s));
+  const PcgState fin = *h.st_host;
+  if (h.prm.use_graph) count_graph_launch(h.gloop_kernels[pi] * std::max(fin.iters, 1));
   double qq = 0.0;
   for (int i = 0; i < kDotBlocks; ++i) qq += part[2 * i];
   float ms = 0.f;
@@ -1189,14 +1301,14 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
       set_error("amgdd_apply: COARSE needs the coarsest level");
       return AMGDD_ERR_INVALID_ARG;
     }
-    AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, x, y, false, SEG_STORE, nullptr, s));
+    AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, x, y, false, SEG_STORE, nullptr, s, nullptr, nullptr, L.Wt64.p));
     return AMGDD_OK;
   }
   if (L.coarsest && op != AMGDD_OP_A) {
     set_error("amgdd_apply: operator not defined on the coarsest level");
     return AMGDD_ERR_INVALID_ARG;
   }
-  if (op == AMGDD_OP_A && L.aplan.ntasks == 0 && L.n > 0 && !(level == 0)) {
+  if (op == AMGDD_OP_A && L.coarsest && level != 0) {
     set_error("amgdd_apply: A is not stored on the coarsest level");
     return AMGDD_ERR_INVALID_ARG;
   }
@@ -1221,21 +1333,22 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
       break;
     case AMGDD_OP_RAS:
       AMGDD_TRY(launch_seg(L.ras, f32 ? (const void*)L.W32.p : (const void*)L.W64.p, f32, xin, yout, f32, SEG_STORE,
-                           nullptr, s));
+                           nullptr, s, nullptr, nullptr, f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p));
       break;
     case AMGDD_OP_RAST:
       AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
       AMGDD_TRY(launch_seg(L.rast, f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p, f32, xin, yout, f32,
-                           SEG_ATOMIC_ADD, nullptr, s));
+                           SEG_ATOMIC_ADD, nullptr, s, nullptr, nullptr,
+                           f32 ? (const void*)L.W32.p : (const void*)L.W64.p));
       break;
     case AMGDD_OP_RESTRICT:
       AMGDD_TRY(launch_seg(L.restr, f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p, f32, xin, yout, f32,
-                           SEG_STORE, nullptr, s));
+                           SEG_STORE, nullptr, s, nullptr, nullptr, f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p));
       break;
     case AMGDD_OP_PROLONG:
       AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
       AMGDD_TRY(launch_seg(L.prol, f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p, f32, xin, yout, f32, SEG_ADD,
-                           nullptr, s));
+                           nullptr, s, nullptr, nullptr, f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p));
       break;
     case AMGDD_OP_VCYCLE:
       AMGDD_TRY(vcycle(*h, level, f32, xin, yout, nullptr, s));
@@ -1298,7 +1411,7 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
       set_error("amgdd_apply_noalloc: COARSE needs the coarsest level");
       return AMGDD_ERR_INVALID_ARG;
     }
-    AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, x, y, false, SEG_STORE, nullptr, s));
+    AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, x, y, false, SEG_STORE, nullptr, s, nullptr, nullptr, L.Wt64.p));
     AMGDD_CUDA(cudaStreamSynchronize(s));
     return AMGDD_OK;
   }
@@ -1306,7 +1419,7 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
     set_error("amgdd_apply_noalloc: operator not defined on the coarsest level");
     return AMGDD_ERR_INVALID_ARG;
   }
-  if (op == AMGDD_OP_A && L.aplan.ntasks == 0 && level != 0) {
+  if (op == AMGDD_OP_A && L.coarsest && level != 0) {
     set_error("amgdd_apply_noalloc: A is not stored on the coarsest level");
     return AMGDD_ERR_INVALID_ARG;
   }
@@ -1339,21 +1452,22 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
       break;
     case AMGDD_OP_RAS:
       AMGDD_TRY(launch_seg(L.ras, f32 ? (const void*)L.W32.p : (const void*)L.W64.p, f32, xin, yout, f32, SEG_STORE,
-                           nullptr, s));
+                           nullptr, s, nullptr, nullptr, f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p));
       break;
     case AMGDD_OP_RAST:
       AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
       AMGDD_TRY(launch_seg(L.rast, f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p, f32, xin, yout, f32,
-                           SEG_ATOMIC_ADD, nullptr, s));
+                           SEG_ATOMIC_ADD, nullptr, s, nullptr, nullptr,
+                           f32 ? (const void*)L.W32.p : (const void*)L.W64.p));
       break;
     case AMGDD_OP_RESTRICT:
       AMGDD_TRY(launch_seg(L.restr, f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p, f32, xin, yout, f32,
-                           SEG_STORE, nullptr, s));
+                           SEG_STORE, nullptr, s, nullptr, nullptr, f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p));
       break;
     case AMGDD_OP_PROLONG:
       AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
       AMGDD_TRY(launch_seg(L.prol, f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p, f32, xin, yout, f32, SEG_ADD,
-                           nullptr, s));
+                           nullptr, s, nullptr, nullptr, f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p));
       break;
     case AMGDD_OP_VCYCLE:
       AMGDD_TRY(vcycle(*h, level, f32, xin, yout, nullptr, s));
@@ -1400,24 +1514,16 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes
   for (int l = 0; l < nl; ++l) {
     const Level& L = *h->lv[l];
     double* b = bytes + l * VProf::kSlots;
-    auto seg = [&](const SegPlan& p, int64_t nin, int64_t nout, bool rmw, size_t e) {
-      return (double)p.mat_len * e + (double)(p.in_len + p.out_len) * 4.0 + (double)nin * e +
-             (double)nout * e * (rmw ? 2.0 : 1.0);
-    };
     if (L.coarsest) {
-      b[0] = seg(L.ras, L.n, L.n, false, 8);
+      b[0] = seg_bytes(L.ras, L.n, L.n, false, 8);
       if (f32) b[1] = b[5] = (double)L.n * 12.0;
     } else {
       const int64_t nn = L.col0.back();
-      double ap = (double)L.aplan.r_len * esz + 3.0 * L.n * esz;
-      for (size_t g = 0; g + 1 < L.g_ptr.size(); ++g)
-        if (L.g_rank[g] > 0) ap += (double)(L.g_ptr[g + 1] - L.g_ptr[g]) * 4.0;
-      b[0] = seg(L.ras, L.n, L.n, false, esz);
-      b[1] = 2.0 * 2.0 * L.n * esz;  // two r -> s copies
-      b[2] = 2.0 * ap;                // two residual A-applies
-      b[3] = seg(L.restr, L.n, nn, false, esz);
-      b[4] = seg(L.prol, nn, L.n, true, esz);
-      b[7] = seg(L.rast, L.n, L.n, true, esz);
+      b[0] = seg_bytes(L.ras, L.n, L.n, false, esz) + L.n * esz;  // + fused copy r -> s
+      b[2] = 2.0 * apply_bytes(L, esz);                            // two residual A-applies
+      b[3] = seg_bytes(L.restr, L.n, nn, false, esz);
+      b[4] = seg_bytes(L.prol, nn, L.n, true, esz) + L.n * esz;   // + fused copy r -> s
+      b[7] = seg_bytes(L.rast, L.n, L.n, true, esz);
     }
   }
   for (int i = 0; i < nl * VProf::kSlots; ++i) ms[i] = acc[i] / reps;
@@ -1504,34 +1610,26 @@ int amgdd_level_export(const amgdd_hierarchy* h, int level, int which, void* dst
 }
 
 static void level_bytes(const amgdd_hierarchy& h, const Level& L, size_t esz, double& cyc) {
-  auto seg = [&](const SegPlan& p, int64_t nin, int64_t nout, bool rmw) {
-    return (double)p.mat_len * esz + (double)(p.in_len + p.out_len) * 4.0 + (double)nin * esz +
-           (double)nout * esz * (rmw ? 2.0 : 1.0);
-  };
   if (L.coarsest) {
     cyc += (double)L.n * L.n * 8.0 + 2.0 * L.n * 8.0;
     return;
   }
   const int64_t nn = L.col0.back();
-  double apply = (double)L.aplan.r_len * esz + 3.0 * L.n * esz;
-  for (size_t g = 0; g + 1 < L.g_ptr.size(); ++g)
-    if (L.g_rank[g] > 0) apply += (double)(L.g_ptr[g + 1] - L.g_ptr[g]) * 4.0;
-  cyc += seg(L.ras, L.n, L.n, false) + seg(L.rast, L.n, L.n, true) + seg(L.restr, L.n, nn, false) +
-         seg(L.prol, nn, L.n, true) + 2.0 * (apply + 2.0 * L.n * esz);
+  cyc += seg_bytes(L.ras, L.n, L.n, false, esz) + seg_bytes(L.rast, L.n, L.n, true, esz) +
+         seg_bytes(L.restr, L.n, nn, false, esz) + seg_bytes(L.prol, nn, L.n, true, esz) +
+         2.0 * (apply_bytes(L, esz) + L.n * esz);  // the residual copy rides on RAS / prolongation
   (void)h;
 }
 
-int amgdd_bytes_model(const amgdd_hierarchy* h, double* vcycle_bytes, double* apply_bytes) {
+int amgdd_bytes_model(const amgdd_hierarchy* h, double* vcycle_bytes, double* apply_out) {
   if (h == nullptr) return AMGDD_ERR_INVALID_ARG;
   const size_t esz = h->precision == AMGDD_MIXED32 ? 4 : 8;
   double cyc = 0.0;
   for (const auto& L : h->lv) level_bytes(*h, *L, esz, cyc);
   const Level& L0 = *h->lv[0];
-  double ap = (double)L0.aplan.r_len * 8.0 + 3.0 * L0.n * 8.0;
-  for (size_t g = 0; g + 1 < L0.g_ptr.size(); ++g)
-    if (L0.g_rank[g] > 0) ap += (double)(L0.g_ptr[g + 1] - L0.g_ptr[g]) * 4.0;
+  const double ap = apply_bytes(L0, 8);
   if (vcycle_bytes) *vcycle_bytes = cyc;
-  if (apply_bytes) *apply_bytes = ap;
+  if (apply_out) *apply_out = ap;
   return AMGDD_OK;
 }
 

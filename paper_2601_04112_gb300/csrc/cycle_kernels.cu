@@ -23,7 +23,7 @@ namespace amgdd {
 
 namespace {
 
-constexpr int kSegThreads = 256;
+constexpr int kSegThreads = 128;
 
 template <class T>
 __device__ __forceinline__ void atomic_add(T* p, T v) {
@@ -51,7 +51,28 @@ __device__ __forceinline__ unsigned group_mask() {
 // Batched gather-GEMV-scatter.  One CTA takes `rows_per_chunk` rows of one
 // block; the gathered input x(in_idx) is staged once in shared memory and L
 // lanes stream each row of the row-major block with coalesced loads.
-template <class T, int L, int MODE>
+template <class T>
+struct Vec2 {};
+template <>
+struct Vec2<float> {
+  using type = float4;
+  static constexpr int width = 4;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+  static constexpr int width = 2;
+};
+
+__device__ __forceinline__ float vdot(const float4& a, const float4& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
+__device__ __forceinline__ double vdot(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
+
+// VEC: every row of every block starts on a 16-byte boundary and has a
+// multiple of the vector width entries (checked when the plan is built);
+// rows and the staged x are then read 16 bytes per lane.
+template <class T, int L, int MODE, bool VEC>
 __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__ chunk_blk,
                                                      const int32_t* __restrict__ chunk_row0, int rows_per_chunk,
                                                      const int64_t* __restrict__ m_off, const int32_t* __restrict__ nr,
@@ -60,7 +81,8 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
                                                      const int64_t* __restrict__ out_off,
                                                      const int32_t* __restrict__ in_idx,
                                                      const int32_t* __restrict__ out_idx, const T* __restrict__ M,
-                                                     const T* __restrict__ x, T* __restrict__ y, const int* skip) {
+                                                     const T* __restrict__ x, T* __restrict__ y, const int* skip,
+                                                     const T* __restrict__ csrc, T* __restrict__ cdst) {
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw);
@@ -80,47 +102,157 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
   for (int r = r0 + grp; r < r1; r += ngrp) {
     const T* row = Mb + (int64_t)r * ncb;
     T acc = T(0);
-    for (int c = lane; c < ncb; c += L) acc += row[c] * xs[c];
+    if constexpr (VEC) {
+      using V = typename Vec2<T>::type;
+      constexpr int W = Vec2<T>::width;
+      const V* rv = reinterpret_cast<const V*>(row);
+      const V* xv = reinterpret_cast<const V*>(xs);
+      const int nv = ncb / W;
+      for (int c = lane; c < nv; c += L) acc += vdot(rv[c], xv[c]);
+    } else {
+      for (int c = lane; c < ncb; c += L) acc += row[c] * xs[c];
+    }
     acc = group_sum<L>(acc, mask);
     if (lane == 0) {
-      T* dst = y + oo[r];
+      const int o = oo[r];
+      T* dst = y + o;
       if (MODE == SEG_STORE)
         *dst = acc;
       else if (MODE == SEG_ADD)
         *dst += acc;
-      else
+      else if (MODE == SEG_ATOMIC_ADD)
         atomic_add(dst, acc);
+      else
+        atomic_add(dst, -acc);
+      if (cdst != nullptr) cdst[o] = csrc[o];
     }
+  }
+}
+
+// Short rows, row per lane: a task (block, first row, up to L rows) belongs
+// to L lanes; lane l owns output row r0 + l and streams column c of the
+// block's transposed copy MT (nc x nr, row-major), so the L lanes read L
+// consecutive values.  x(in_idx) is staged once per task in shared memory.
+// Outputs, atomics and the fused copy are issued by all lanes at once.
+template <class T, int L, int MODE>
+__global__ void __launch_bounds__(128) k_seg_rows(const int32_t* __restrict__ task_blk,
+                                                  const int32_t* __restrict__ task_row0,
+                                                  const int32_t* __restrict__ task_nrow, int ntasks, int max_nc,
+                                                  const int64_t* __restrict__ m_off, const int32_t* __restrict__ nr,
+                                                  const int32_t* __restrict__ nc, const int64_t* __restrict__ in_off,
+                                                  const int64_t* __restrict__ out_off,
+                                                  const int32_t* __restrict__ in_idx,
+                                                  const int32_t* __restrict__ out_idx, const T* __restrict__ MT,
+                                                  const T* __restrict__ x, T* __restrict__ y, const int* skip,
+                                                  const T* __restrict__ csrc, T* __restrict__ cdst) {
+  if (skip != nullptr && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int grp = (int)threadIdx.x / L;
+  const int t = blockIdx.x * (128 / L) + grp;
+  if (t >= ntasks) return;
+  const int lane = threadIdx.x % L;
+  const unsigned mask = group_mask<L>();
+  T* xs = reinterpret_cast<T*>(smem_raw) + (size_t)grp * max_nc;
+  const int b = task_blk[t];
+  const int r0 = task_row0[t];
+  const int rows = task_nrow[t];
+  const int ncb = nc[b], nrb = nr[b];
+  const int32_t* ii = in_idx + in_off[b];
+  for (int c = lane; c < ncb; c += L) xs[c] = x[ii[c]];
+  __syncwarp(mask);
+  if (lane >= rows) return;
+  const int r = r0 + lane;
+  const T* col = MT + m_off[b] + r;
+  T acc = T(0);
+  for (int c = 0; c < ncb; ++c) acc += col[(int64_t)c * nrb] * xs[c];
+  const int o = out_idx[out_off[b] + r];
+  T* dst = y + o;
+  if (MODE == SEG_STORE)
+    *dst = acc;
+  else if (MODE == SEG_ADD)
+    *dst += acc;
+  else if (MODE == SEG_ATOMIC_ADD)
+    atomic_add(dst, acc);
+  else
+    atomic_add(dst, -acc);
+  if (cdst != nullptr) cdst[o] = csrc[o];
+}
+
+template <class T, int L, int MODE>
+int seg_rows_launch(const SegPlan& p, const T* MT, const T* x, T* y, const int* skip, cudaStream_t s, const T* csrc,
+                    T* cdst) {
+  const int per = 128 / L;
+  const int grid = (p.ntasks + per - 1) / per;
+  const size_t smem = (size_t)per * p.max_nc * sizeof(T);
+  auto kern = k_seg_rows<T, L, MODE>;
+  if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, 128, smem, s>>>(p.task_blk.p, p.task_row0.p, p.task_nrow.p, p.ntasks, p.max_nc, p.m_off.p, p.nr.p,
+                               p.nc.p, p.in_off.p, p.out_off.p, p.in_idx_ext, p.out_idx_ext, MT, x, y, skip, csrc,
+                               cdst);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
+template <class T, int L>
+int seg_rows_mode(const SegPlan& p, const T* MT, const T* x, T* y, SegMode mode, const int* skip, cudaStream_t s,
+                  const T* csrc, T* cdst) {
+  switch (mode) {
+    case SEG_STORE: return seg_rows_launch<T, L, SEG_STORE>(p, MT, x, y, skip, s, csrc, cdst);
+    case SEG_ADD: return seg_rows_launch<T, L, SEG_ADD>(p, MT, x, y, skip, s, csrc, cdst);
+    case SEG_ATOMIC_ADD: return seg_rows_launch<T, L, SEG_ATOMIC_ADD>(p, MT, x, y, skip, s, csrc, cdst);
+    default: return seg_rows_launch<T, L, SEG_ATOMIC_SUB>(p, MT, x, y, skip, s, csrc, cdst);
   }
 }
 
 template <class T, int L>
 int seg_dispatch_mode(const SegPlan& p, const T* M, const T* x, T* y, SegMode mode, const int* skip,
-                      cudaStream_t s) {
+                      cudaStream_t s, const T* csrc, T* cdst) {
   const size_t smem = (size_t)p.max_nc * sizeof(T);
   auto launch = [&](auto kern) -> int {
     if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<p.nchunks, kSegThreads, smem, s>>>(p.chunk_blk.p, p.chunk_row0.p, p.rows_per_chunk, p.m_off.p, p.nr.p,
                                               p.nc.p, p.in_off.p, p.out_off.p, p.in_idx_ext, p.out_idx_ext, M, x, y,
-                                              skip);
+                                              skip, csrc, cdst);
     AMGDD_CUDA(cudaGetLastError());
     count_kernels(1);
     return AMGDD_OK;
   };
+  if (p.vec) {
+    switch (mode) {
+      case SEG_STORE: return launch(k_seg<T, L, SEG_STORE, true>);
+      case SEG_ADD: return launch(k_seg<T, L, SEG_ADD, true>);
+      case SEG_ATOMIC_ADD: return launch(k_seg<T, L, SEG_ATOMIC_ADD, true>);
+      default: return launch(k_seg<T, L, SEG_ATOMIC_SUB, true>);
+    }
+  }
   switch (mode) {
-    case SEG_STORE: return launch(k_seg<T, L, SEG_STORE>);
-    case SEG_ADD: return launch(k_seg<T, L, SEG_ADD>);
-    default: return launch(k_seg<T, L, SEG_ATOMIC_ADD>);
+    case SEG_STORE: return launch(k_seg<T, L, SEG_STORE, false>);
+    case SEG_ADD: return launch(k_seg<T, L, SEG_ADD, false>);
+    case SEG_ATOMIC_ADD: return launch(k_seg<T, L, SEG_ATOMIC_ADD, false>);
+    default: return launch(k_seg<T, L, SEG_ATOMIC_SUB, false>);
   }
 }
 
 template <class T>
-int seg_dispatch(const SegPlan& p, const T* M, const T* x, T* y, SegMode mode, const int* skip, cudaStream_t s) {
+int seg_dispatch(const SegPlan& p, const T* M, const T* MT, const T* x, T* y, SegMode mode, const int* skip,
+                 cudaStream_t s, const T* csrc, T* cdst) {
+  if (p.rows_mode) {
+    if (MT == nullptr) {
+      set_error("launch_seg: row-per-lane plan needs the transposed operator");
+      return AMGDD_ERR_INTERNAL;
+    }
+    switch (p.kind) {
+      case 8: return seg_rows_mode<T, 8>(p, MT, x, y, mode, skip, s, csrc, cdst);
+      case 16: return seg_rows_mode<T, 16>(p, MT, x, y, mode, skip, s, csrc, cdst);
+      default: return seg_rows_mode<T, 32>(p, MT, x, y, mode, skip, s, csrc, cdst);
+    }
+  }
   switch (p.lanes) {
-    case 4: return seg_dispatch_mode<T, 4>(p, M, x, y, mode, skip, s);
-    case 8: return seg_dispatch_mode<T, 8>(p, M, x, y, mode, skip, s);
-    case 16: return seg_dispatch_mode<T, 16>(p, M, x, y, mode, skip, s);
-    default: return seg_dispatch_mode<T, 32>(p, M, x, y, mode, skip, s);
+    case 4: return seg_dispatch_mode<T, 4>(p, M, x, y, mode, skip, s, csrc, cdst);
+    case 8: return seg_dispatch_mode<T, 8>(p, M, x, y, mode, skip, s, csrc, cdst);
+    case 16: return seg_dispatch_mode<T, 16>(p, M, x, y, mode, skip, s, csrc, cdst);
+    default: return seg_dispatch_mode<T, 32>(p, M, x, y, mode, skip, s, csrc, cdst);
   }
 }
 
@@ -183,10 +315,14 @@ __device__ __forceinline__ void apply_task(const ApplyArgs& a, int task, const T
   }
 }
 
-// Large supports: one warp per task, x(S) and acc in shared memory.
+constexpr int kApplyThreads = 128;
+
+// Supports of at most 4 nodes (every cell group of a 2D Q1 level 0): one
+// thread owns a group, keeps x(S) and the rows of R_g in registers, and
+// needs no shuffles.
 template <class T>
-__device__ void apply_task_smem(const ApplyArgs& a, int task, const T* __restrict__ R, const T* __restrict__ x,
-                                T* __restrict__ y, T sign, T* xs, T* accs) {
+__device__ __forceinline__ void apply_task_thread(const ApplyArgs& a, int task, const T* __restrict__ R,
+                                                  const T* __restrict__ x, T* __restrict__ y, T sign) {
   const int g = a.task_grp[task];
   const int row0 = a.task_row0[task];
   const int nrow = a.task_nrow[task];
@@ -194,27 +330,37 @@ __device__ void apply_task_smem(const ApplyArgs& a, int task, const T* __restric
   const int s = (int)(a.g_ptr[g + 1] - sp);
   const int32_t* S = a.g_idx + sp;
   const T* Rg = R + a.r_off[g];
-  const int lane = threadIdx.x & 31;
-  for (int c = lane; c < s; c += 32) {
-    xs[c] = x[S[c]];
-    accs[c] = T(0);
+  int idx[4];
+  T xr[4], acc[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    idx[c] = c < s ? S[c] : 0;
+    xr[c] = c < s ? x[idx[c]] : T(0);
+    acc[c] = T(0);
   }
-  __syncwarp();
   for (int r = row0; r < row0 + nrow; ++r) {
     const T* row = Rg + (int64_t)r * s;
+    T rv[4];
     T t = T(0);
-    for (int c = lane; c < s; c += 32) t += row[c] * xs[c];
-    t = group_sum<32>(t, 0xffffffffu);
-    for (int c = lane; c < s; c += 32) accs[c] += row[c] * t;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      rv[c] = c < s ? row[c] : T(0);
+      t += rv[c] * xr[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c] += rv[c] * t;
   }
-  __syncwarp();
-  for (int c = lane; c < s; c += 32) atomic_add(y + S[c], sign * accs[c]);
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    if (c < s) atomic_add(y + idx[c], sign * acc[c]);
 }
 
-constexpr int kApplyThreads = 128;
-constexpr int kApplySmemMaxS = 2048;  // largest support of the shared-memory kind
-
-template <class T>
+// Grouped A-apply, two kernels so that the narrow kinds are not held to
+// the register budget of the wide ones.  BIG = false: kind 0 (at most 4
+// nodes, one thread per group) and kinds 1-3 (8, 16, 32 lanes, one column
+// per lane).  BIG = true: kinds 4-7 (32 lanes, 2/4/8/16 columns per lane).
+// Supports above 512 nodes go through two gather-GEMV passes instead.
+template <class T, bool BIG>
 __global__ void __launch_bounds__(kApplyThreads) k_apply(ApplyArgs a, const T* __restrict__ R,
                                                          const T* __restrict__ x, T* __restrict__ y, T sign,
                                                          const int* skip) {
@@ -223,15 +369,6 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(ApplyArgs a, const T* _
   while (bkt + 1 < a.nbuckets && (int)blockIdx.x >= a.bucket_start[bkt + 1]) ++bkt;
   const int kind = a.bucket_kind[bkt];
   const int cta = blockIdx.x - a.bucket_start[bkt];
-  if (kind == 8) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5;
-    T* base = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 2 * kApplySmemMaxS;
-    const int t = cta * (kApplyThreads / 32) + warp;
-    if (t < a.bucket_tasks[bkt]) apply_task_smem<T>(a, a.bucket_task0[bkt] + t, R, x, y, sign, base, base + kApplySmemMaxS);
-    return;
-  }
-  switch (kind) {
 #define AMGDD_KIND(K, LL, JJ)                                                               \
   case K: {                                                                                 \
     const int t = cta * (kApplyThreads / LL) + (int)threadIdx.x / LL;                       \
@@ -239,17 +376,28 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(ApplyArgs a, const T* _
       apply_task<T, LL, JJ>(a, a.bucket_task0[bkt] + t, R, x, y, sign, group_mask<LL>());    \
     return;                                                                                 \
   }
-    AMGDD_KIND(0, 4, 1)
-    AMGDD_KIND(1, 8, 1)
-    AMGDD_KIND(2, 16, 1)
-    AMGDD_KIND(3, 32, 1)
-    AMGDD_KIND(4, 32, 2)
-    AMGDD_KIND(5, 32, 4)
-    AMGDD_KIND(6, 32, 8)
-    AMGDD_KIND(7, 32, 16)
-#undef AMGDD_KIND
-    default: return;
+  if constexpr (BIG) {
+    switch (kind) {
+      AMGDD_KIND(4, 32, 2)
+      AMGDD_KIND(5, 32, 4)
+      AMGDD_KIND(6, 32, 8)
+      AMGDD_KIND(7, 32, 16)
+      default: return;
+    }
+  } else {
+    if (kind == 0) {
+      const int t = cta * kApplyThreads + (int)threadIdx.x;
+      if (t < a.bucket_tasks[bkt]) apply_task_thread<T>(a, a.bucket_task0[bkt] + t, R, x, y, sign);
+      return;
+    }
+    switch (kind) {
+      AMGDD_KIND(1, 8, 1)
+      AMGDD_KIND(2, 16, 1)
+      AMGDD_KIND(3, 32, 1)
+      default: return;
+    }
   }
+#undef AMGDD_KIND
 }
 
 // ---------------------------------------------------------------------------
@@ -314,8 +462,12 @@ __global__ void __launch_bounds__(kDotThreads) k_dot_partial(const double* __res
 //        2: rr = sum(r.r); convergence / iteration limit
 //        3: rzn = sum(r.z_new), rzo = sum(r.z_old); beta; rz = rzn
 //        4: bnorm2 = sum(b.b); tol2 = tol^2 bnorm2 (tol passed in st->tol2)
-__global__ void __launch_bounds__(1024) k_pcg_scalar(int which, PcgState* st, const double* __restrict__ partials) {
-  if (which != 0 && which != 4 && st->done) return;
+__global__ void __launch_bounds__(1024) k_pcg_scalar(int which, PcgState* st, const double* __restrict__ partials,
+                                                     cudaGraphConditionalHandle cond, int use_cond) {
+  if (which != 0 && which != 4 && st->done) {
+    if (which == 3 && use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+    return;
+  }
   __shared__ double s0[1024], s1[1024];
   double v0 = 0.0, v1 = 0.0;
   for (int i = threadIdx.x; i < kDotBlocks; i += blockDim.x) {
@@ -367,6 +519,7 @@ __global__ void __launch_bounds__(1024) k_pcg_scalar(int which, PcgState* st, co
       st->rzo = b;
       st->beta = st->flexible ? (a - b) / st->rz : a / st->rz;
       st->rz = a;
+      if (use_cond) cudaGraphSetConditional(cond, 1u);
       break;
     case 4:
       st->bnorm2 = a;
@@ -404,53 +557,68 @@ __global__ void k_update_p(const PcgState* __restrict__ st, double* __restrict__
 
 // ---------------------------------------------------------------------------
 int launch_seg(const SegPlan& p, const void* M, bool m_fp32, const void* x, void* y, bool v_fp32, SegMode mode,
-               const int* skip, cudaStream_t s) {
-  if (p.nchunks == 0) return AMGDD_OK;
+               const int* skip, cudaStream_t s, const void* csrc, void* cdst, const void* MT) {
+  if (p.rows_mode ? p.ntasks == 0 : p.nchunks == 0) return AMGDD_OK;
   if (m_fp32 != v_fp32) {
     set_error("launch_seg: matrix and vector precision differ");
     return AMGDD_ERR_INTERNAL;
   }
   if (m_fp32)
-    return seg_dispatch<float>(p, (const float*)M, (const float*)x, (float*)y, mode, skip, s);
-  return seg_dispatch<double>(p, (const double*)M, (const double*)x, (double*)y, mode, skip, s);
+    return seg_dispatch<float>(p, (const float*)M, (const float*)MT, (const float*)x, (float*)y, mode, skip, s,
+                               (const float*)csrc, (float*)cdst);
+  return seg_dispatch<double>(p, (const double*)M, (const double*)MT, (const double*)x, (double*)y, mode, skip, s,
+                              (const double*)csrc, (double*)cdst);
 }
 
 int launch_apply(const ApplyPlan& p, const Level& L, bool fp32, const void* x, void* y, int sign, const int* skip,
                  cudaStream_t s) {
-  if (p.ntasks == 0) return AMGDD_OK;
-  ApplyArgs a{};
-  a.task_grp = p.task_grp.p;
-  a.task_row0 = p.task_row0.p;
-  a.task_nrow = p.task_nrow.p;
-  a.g_ptr = L.d_g_ptr.p;
-  a.g_idx = L.d_g_idx.p;
-  a.r_off = L.d_h_off.p;
-  a.nbuckets = p.nbuckets;
-  int task0 = 0, nblocks = 0;
-  bool has_smem = false;
-  for (int b = 0; b < p.nbuckets; ++b) {
-    a.bucket_start[b] = p.bucket_start[b];
-    a.bucket_kind[b] = p.bucket_kind[b];
-    a.bucket_task0[b] = task0;
-    a.bucket_tasks[b] = p.bucket_tasks[b];
-    task0 += p.bucket_tasks[b];
-    if (p.bucket_kind[b] == 8) has_smem = true;
+  // buckets are ordered by kind: kinds 0-3 run in the narrow kernel, 4-7 in the wide one
+  for (int big = 0; big < 2 && p.ntasks > 0; ++big) {
+    ApplyArgs a{};
+    a.task_grp = p.task_grp.p;
+    a.task_row0 = p.task_row0.p;
+    a.task_nrow = p.task_nrow.p;
+    a.g_ptr = L.d_g_ptr.p;
+    a.g_idx = L.d_g_idx.p;
+    a.r_off = L.d_h_off.p;
+    int task0 = 0, cta = 0;
+    a.nbuckets = 0;
+    for (int b = 0; b < p.nbuckets; ++b) {
+      if ((p.bucket_kind[b] >= 4) == (big == 1)) {
+        const int k = a.nbuckets++;
+        a.bucket_start[k] = cta;
+        a.bucket_kind[k] = p.bucket_kind[b];
+        a.bucket_task0[k] = task0;
+        a.bucket_tasks[k] = p.bucket_tasks[b];
+        cta += p.bucket_start[b + 1] - p.bucket_start[b];
+      }
+      task0 += p.bucket_tasks[b];
+    }
+    if (a.nbuckets == 0) continue;
+    if (fp32) {
+      if (big)
+        k_apply<float, true><<<cta, kApplyThreads, 0, s>>>(a, L.d_R32.p, (const float*)x, (float*)y, (float)sign, skip);
+      else
+        k_apply<float, false><<<cta, kApplyThreads, 0, s>>>(a, L.d_R32.p, (const float*)x, (float*)y, (float)sign,
+                                                             skip);
+    } else {
+      if (big)
+        k_apply<double, true><<<cta, kApplyThreads, 0, s>>>(a, L.d_R64.p, (const double*)x, (double*)y,
+                                                             (double)sign, skip);
+      else
+        k_apply<double, false><<<cta, kApplyThreads, 0, s>>>(a, L.d_R64.p, (const double*)x, (double*)y,
+                                                              (double)sign, skip);
+    }
+    AMGDD_CUDA(cudaGetLastError());
+    count_kernels(1);
   }
-  nblocks = p.bucket_start[p.nbuckets];
-  const size_t esz = fp32 ? sizeof(float) : sizeof(double);
-  const size_t smem = has_smem ? (size_t)(kApplyThreads / 32) * 2 * kApplySmemMaxS * esz : 0;
-  if (fp32) {
-    if (smem > 48 * 1024)
-      AMGDD_CUDA(cudaFuncSetAttribute(k_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_apply<float><<<nblocks, kApplyThreads, smem, s>>>(a, L.d_R32.p, (const float*)x, (float*)y, (float)sign, skip);
-  } else {
-    if (smem > 48 * 1024)
-      AMGDD_CUDA(cudaFuncSetAttribute(k_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_apply<double><<<nblocks, kApplyThreads, smem, s>>>(a, L.d_R64.p, (const double*)x, (double*)y, (double)sign,
-                                                          skip);
+  if (L.t_len > 0) {
+    const void* R = fp32 ? (const void*)L.d_R32.p : (const void*)L.d_R64.p;
+    void* t = fp32 ? (void*)L.t32.p : (void*)L.t64.p;
+    AMGDD_TRY(launch_seg(L.gt1, R, fp32, x, t, fp32, SEG_STORE, skip, s));
+    AMGDD_TRY(launch_seg(L.gt2, nullptr, fp32, t, y, fp32, sign > 0 ? SEG_ATOMIC_ADD : SEG_ATOMIC_SUB, skip, s,
+                         nullptr, nullptr, R));
   }
-  AMGDD_CUDA(cudaGetLastError());
-  count_kernels(1);
   return AMGDD_OK;
 }
 
@@ -482,8 +650,9 @@ int launch_dot_partial(const double* a, const double* b, const double* c, int64_
   return AMGDD_OK;
 }
 
-int launch_pcg_scalar(int which, PcgState* st, const double* partials, cudaStream_t s) {
-  k_pcg_scalar<<<1, 1024, 0, s>>>(which, st, partials);
+int launch_pcg_scalar(int which, PcgState* st, const double* partials, cudaStream_t s,
+                      cudaGraphConditionalHandle cond, int use_cond) {
+  k_pcg_scalar<<<1, 1024, 0, s>>>(which, st, partials, cond, use_cond);
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
   return AMGDD_OK;

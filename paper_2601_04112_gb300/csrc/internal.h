@@ -74,13 +74,14 @@ struct DBuf {
 // with M_b row-major (nr_b x nc_b, leading dimension nc_b) at m_off[b].
 // Used for RAS (W_i), RAS-T (W_i^T), restriction (Z_i^T), prolongation (Z_i)
 // and the coarsest solve (A_L^{-1} as a single block).
-enum SegMode { SEG_STORE = 0, SEG_ADD = 1, SEG_ATOMIC_ADD = 2 };
+enum SegMode { SEG_STORE = 0, SEG_ADD = 1, SEG_ATOMIC_ADD = 2, SEG_ATOMIC_SUB = 3 };
 
 struct SegPlan {
   int nblocks = 0;
   int nchunks = 0;      // CTAs: chunks of at most `rows_per_chunk` rows of one block
   int rows_per_chunk = 0;
   int lanes = 32;       // lanes cooperating on one row (4, 8, 16 or 32)
+  bool vec = false;     // every row 16-byte aligned with a whole number of vectors
   int max_nc = 0;       // longest row (shared-memory staging of the gathered x)
   int64_t mat_len = 0;  // total stored matrix entries
   int64_t in_len = 0, out_len = 0;
@@ -90,6 +91,12 @@ struct SegPlan {
   // index arrays owned elsewhere (level Omega lists or the identity)
   const int32_t* in_idx_ext = nullptr;
   const int32_t* out_idx_ext = nullptr;
+  // short rows: one lane per output row over the transposed copy; tasks are
+  // (block, first row, rows) and kind is the number of lanes per task
+  bool rows_mode = false;
+  int kind = 0;
+  int ntasks = 0;
+  DBuf<int32_t> task_blk, task_row0, task_nrow;
 };
 
 // Row groups of G_l (rows sharing one support), compressed: R_g has rank_g
@@ -119,7 +126,14 @@ struct Level {
   DBuf<double> d_H;     // Grams H_g = sum_rows g^T g (setup only, freed after use)
   DBuf<double> d_R64;   // compressed rows, capacity s x s per group
   DBuf<float> d_R32;
-  ApplyPlan aplan;
+  ApplyPlan aplan;  // supports of at most 32 nodes
+  // supports above 32 nodes: t = R_g x(S_g) (gt1), then y(S_g) -/+= R_g^T t
+  // (gt2, one lane per support node reading R_g as the transposed copy)
+  SegPlan gt1, gt2;
+  int64_t t_len = 0;
+  DBuf<double> t64;
+  DBuf<float> t32;
+  DBuf<int32_t> d_tidx;  // identity over t
   // ---- aggregates and subdomains ------------------------------------------
   std::vector<int32_t> agg;      // n
   std::vector<int64_t> om_ptr;   // nagg+1
@@ -141,8 +155,12 @@ struct Level {
 
 // ---------------------------------------------------------------------------
 // kernels (cycle_kernels.cu)
+// csrc/cdst (optional, same precision): cdst[out] = csrc[out] for every
+// output row, fused into the same launch (the residual's copy of r).
+// MT: the block-wise transpose of M (needed by row-per-lane plans).
 int launch_seg(const SegPlan& p, const void* M, bool m_fp32, const void* x, void* y, bool v_fp32, SegMode mode,
-               const int* skip, cudaStream_t s);
+               const int* skip, cudaStream_t s, const void* csrc = nullptr, void* cdst = nullptr,
+               const void* MT = nullptr);
 int launch_apply(const ApplyPlan& p, const Level& L, bool fp32, const void* x, void* y, int sign, const int* skip,
                  cudaStream_t s);
 int launch_cast(const void* src, bool src32, void* dst, bool dst32, int64_t n, const int* skip, cudaStream_t s);
@@ -173,7 +191,10 @@ constexpr int kDotBlocks = 608;  // 4 x 152 SMs; partial sums per dot product
 
 int launch_dot_partial(const double* a, const double* b, const double* c, int64_t n, double* partials,
                        const int* skip, cudaStream_t s);
-int launch_pcg_scalar(int which, PcgState* st, const double* partials, cudaStream_t s);
+// which == 3 also sets the conditional of an enclosing CUDA-graph WHILE
+// node (when use_cond): 1 to run another iteration, 0 once done.
+int launch_pcg_scalar(int which, PcgState* st, const double* partials, cudaStream_t s,
+                      cudaGraphConditionalHandle cond = 0, int use_cond = 0);
 int launch_update_xr(PcgState* st, double* x, double* r, const double* p, const double* q, int64_t n,
                      cudaStream_t s);
 int launch_update_p(PcgState* st, double* p, const double* z, double* zold, int64_t n, cudaStream_t s);
