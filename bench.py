@@ -345,8 +345,13 @@ def run_ours(args):
         kname, kms, kby = "k_apply (grouped G then G^T residual, all levels, FP32)", app_ms, app_by
         nlaunch = 2 * (ms.shape[0] - 1)
     achieved = kby / (kms * 1e-3) / 1e9
+    # DRAM bytes per V-cycle of the k_seg family from one ncu capture of this
+    # workload (profiles/dram_kseg_kapply_q1_512_rot.md); valid while those
+    # kernels are unchanged.  Traffic of k_apply was not captured separately.
+    traffic = 718.98e6 if kname.startswith("k_seg") and args.workload == WORKLOAD and args.N is None else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": kname, "launches_per_vcycle": nlaunch,
+                "traffic": traffic, "traffic_unit": "bytes per V-cycle (kernel family)",
+                "kernel": kname, "launches_per_vcycle": nlaunch,
                 "bytes_per_vcycle": kby, "ms_per_vcycle": kms,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
                 "vcycle": {"ms": vcyc_ms, "bytes": float(by.sum()),

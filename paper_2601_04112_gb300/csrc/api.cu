@@ -149,6 +149,8 @@ int build_seg(SegPlan& p, const std::vector<int32_t>& nr, const std::vector<int3
   p.in_idx_ext = in_ext;
   p.out_idx_ext = out_ext;
   // short rows: one lane per output row over the transposed copy
+  // row per lane needs no reduction but walks columns with a stride, which
+  // streams well only for short rows (measured: long rows lose 2x)
   p.rows_mode = force == 2 || (force == 0 && p.max_nc <= 128);
   if (p.rows_mode) {
     int max_nr = 0;
@@ -239,7 +241,7 @@ int build_apply(Level& L, cudaStream_t s) {
   int cta = 0;
   for (int kd = 0; kd < 8; ++kd) {
     if (tg[kd].empty()) continue;
-    const int per = kd == 0 ? 128 : 128 / kKindLanes[kd];
+    const int per = kd == 0 ? 256 : 128 / kKindLanes[kd];  // kind 0: two groups per thread
     p.bucket_kind[p.nbuckets] = kd;
     p.bucket_start[p.nbuckets] = cta;
     p.bucket_tasks[p.nbuckets] = (int)tg[kd].size();

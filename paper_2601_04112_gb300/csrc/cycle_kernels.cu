@@ -324,31 +324,32 @@ template <class T>
 __device__ __forceinline__ void apply_task_thread(const ApplyArgs& a, int task, const T* __restrict__ R,
                                                   const T* __restrict__ x, T* __restrict__ y, T sign) {
   const int g = a.task_grp[task];
-  const int row0 = a.task_row0[task];
-  const int nrow = a.task_nrow[task];
+  const int nrow = min(a.task_nrow[task], 4);
   const int64_t sp = a.g_ptr[g];
   const int s = (int)(a.g_ptr[g + 1] - sp);
   const int32_t* S = a.g_idx + sp;
   const T* Rg = R + a.r_off[g];
+  // issue every load of the group before using any of them
   int idx[4];
-  T xr[4], acc[4];
+  T xr[4], acc[4], rv[4][4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) idx[c] = c < s ? S[c] : 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) rv[r][c] = (r < nrow && c < s) ? Rg[r * s + c] : T(0);
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    idx[c] = c < s ? S[c] : 0;
     xr[c] = c < s ? x[idx[c]] : T(0);
     acc[c] = T(0);
   }
-  for (int r = row0; r < row0 + nrow; ++r) {
-    const T* row = Rg + (int64_t)r * s;
-    T rv[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
     T t = T(0);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      rv[c] = c < s ? row[c] : T(0);
-      t += rv[c] * xr[c];
-    }
+    for (int c = 0; c < 4; ++c) t += rv[r][c] * xr[c];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[c] += rv[c] * t;
+    for (int c = 0; c < 4; ++c) acc[c] += rv[r][c] * t;
   }
 #pragma unroll
   for (int c = 0; c < 4; ++c)
@@ -386,8 +387,11 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(ApplyArgs a, const T* _
     }
   } else {
     if (kind == 0) {
-      const int t = cta * kApplyThreads + (int)threadIdx.x;
+      // two groups per thread (independent work for latency hiding)
+      const int t = cta * (2 * kApplyThreads) + (int)threadIdx.x;
       if (t < a.bucket_tasks[bkt]) apply_task_thread<T>(a, a.bucket_task0[bkt] + t, R, x, y, sign);
+      if (t + kApplyThreads < a.bucket_tasks[bkt])
+        apply_task_thread<T>(a, a.bucket_task0[bkt] + t + kApplyThreads, R, x, y, sign);
       return;
     }
     switch (kind) {

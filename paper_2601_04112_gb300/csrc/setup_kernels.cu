@@ -8,9 +8,12 @@
 //  k_chol        A_i = L L^T (the omega-first ordering makes the leading
 //                block the Cholesky factor of A_ww)
 //  k_schur       S~ = A~_ww - A~_wG A~_GG^+ A~_Gw (Eq. gevp-S) by eliminating
-//                the Gamma pivots; pivots below rtol * max diag are zero
+//                the Gamma pivots, largest diagonal first; pivots below
+//                rtol * max diag are the null space of A~_GG
 //  k_inv_rows    A_i^{-1}(:, omega_i): the RAS / RAS-T operators
-//  k_gep         S~ u = mu A_ww u via C = L^{-1} S~ L^{-T}, cyclic Jacobi,
+//  k_gep         S~ u = mu A_ww u via C = L^{-1} S~ L^{-T}; cyclic Jacobi for
+//                small blocks, Householder tridiagonalisation + implicit QL
+//                for large ones;
 //                ascending mu, selection, Z = L^{-T} V, sign convention
 //  k_pack_z      Z_i and Z_i^T in FP64 and FP32
 //  k_next_gram   Grams of G_{l+1} = G_l P_l, per new support group
@@ -272,32 +275,60 @@ __global__ void k_chol(const int32_t* __restrict__ mdim, const int64_t* __restri
   if (tm.rank == 0) status[b] = bad;
 }
 
-// Eliminate the Gamma pivots (local indices no..m-1) of the symmetric A~
-// (lower triangle maintained); the omega block becomes the Schur complement.
+// Eliminate the Gamma pivots of the symmetric A~ (local indices no..m-1,
+// lower triangle maintained) so that the omega block becomes the Schur
+// complement.  Pivots are taken largest remaining Gamma diagonal first
+// (diagonal pivoting, which reveals the rank of a singular PSD A~_GG) and
+// elimination stops once the largest remaining one is <= rtol * the largest
+// initial one: those directions are treated as the null space of A~_GG.
+// Every CTA of the team chooses the same pivot from the same data.
 template <int CL>
 __global__ void k_schur(const int32_t* __restrict__ mdim, const int32_t* __restrict__ nodim,
                         const int64_t* __restrict__ a_off, double* __restrict__ Atpool, double rtol) {
+  extern __shared__ int elim[];  // m - no flags, one per Gamma index
+  __shared__ double sh_best;
+  __shared__ int sh_p;
   const Team<CL> tm;
   const int b = blockIdx.x / CL;
   const int m = mdim[b], no = nodim[b];
+  const int ng = m - no;
   double* A = Atpool + a_off[b];
+  auto at = [&](int i, int j) -> double& { return i >= j ? A[i + (int64_t)j * m] : A[j + (int64_t)i * m]; };
+  for (int q = threadIdx.x; q < ng; q += blockDim.x) elim[q] = 0;
   double dmax = 0.0;
   for (int p = no; p < m; ++p) dmax = fmax(dmax, A[p + (int64_t)p * m]);
   tm.sync();
-  for (int p = no; p < m; ++p) {
-    const double d = A[p + (int64_t)p * m];
-    tm.sync();
-    if (!(d > rtol * dmax)) continue;
-    // remaining set: 0..no-1 then p+1..m-1
-    const int r = no + (m - 1 - p);
-    for (int64_t e = tm.rank; e < (int64_t)r * r; e += tm.size) {
-      const int jj = (int)(e / r), ii = (int)(e % r);
-      if (ii < jj) continue;
-      const int i = ii < no ? ii : p + 1 + (ii - no);
-      const int j = jj < no ? jj : p + 1 + (jj - no);
-      const double vi = i > p ? A[i + (int64_t)p * m] : A[p + (int64_t)i * m];
-      const double vj = j > p ? A[j + (int64_t)p * m] : A[p + (int64_t)j * m];
-      A[i + (int64_t)j * m] -= vi * vj / d;
+  for (int step = 0; step < ng; ++step) {
+    // argmax of the remaining Gamma diagonal (smallest index on ties), per CTA
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int bi = m;
+      for (int q = threadIdx.x; q < ng; q += 32) {
+        if (elim[q]) continue;
+        const double d = A[(no + q) + (int64_t)(no + q) * m];
+        if (d > best || (d == best && no + q < bi)) {
+          best = d;
+          bi = no + q;
+        }
+      }
+      best = warp_max_idx(best, bi);
+      if (threadIdx.x == 0) {
+        sh_best = best;
+        sh_p = bi;
+      }
+    }
+    __syncthreads();
+    const double d = sh_best;
+    const int p = sh_p;
+    if (!(d > rtol * dmax)) break;
+    if (threadIdx.x == 0) elim[p - no] = 1;
+    __syncthreads();
+    // update every remaining pair (i >= j), i, j in omega or a live Gamma index
+    for (int64_t e = tm.rank; e < (int64_t)m * m; e += tm.size) {
+      const int j = (int)(e / m), i = (int)(e % m);
+      if (i < j) continue;
+      if ((i >= no && elim[i - no]) || (j >= no && elim[j - no])) continue;
+      A[i + (int64_t)j * m] -= at(i, p) * at(j, p) / d;
     }
     tm.sync();
   }
@@ -401,7 +432,7 @@ __device__ void tri_bwd_cols(const double* __restrict__ L, int ldl, double* X, i
 // Generalized eigenproblem S~ u = mu A_ww u on one aggregate (one team).
 // Global scratch per matrix: C, Cn, V, Vn, T (n x n each), perm (n ints),
 // red (CL doubles), kslot.  Shared: rotation coefficients of one round.
-template <int CL>
+template <int CL, bool QL>
 __global__ void k_gep(const int32_t* __restrict__ mdim, const int32_t* __restrict__ nodim,
                       const int64_t* __restrict__ a_off, const double* __restrict__ Lpool,
                       const double* __restrict__ Spool, const int32_t* __restrict__ capv, double thresh,
@@ -465,83 +496,242 @@ __global__ void k_gep(const int32_t* __restrict__ mdim, const int32_t* __restric
     Cn = t0;
   }
 
-  // Cyclic Jacobi, parallel (round-robin) ordering: each round applies n/2
-  // disjoint rotations at once, C <- J^T C J, V <- V J.  Every CTA of the
-  // team computes all rotation angles of a round (same inputs, same
-  // results) and updates its share of the entries.
-  const int ne = n + (n & 1);
-  const int mr = ne - 1;
-  const double tolf = 4.0 * (double)max(n, 16) * DBL_EPSILON;
-  for (int sweep = 0; sweep < 40 && n > 1; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int64_t e = tm.rank; e < (int64_t)n * n; e += tm.size) {
-      const int i = (int)(e % n), j = (int)(e / n);
-      const double v = C[e] * C[e];
-      tot += v;
-      if (i != j) off += v;
-    }
-    off = tm.sum(off, sh, red);
-    tot = tm.sum(tot, sh, red);
-    if (!(off > tolf * tolf * tot)) break;
-    for (int r = 0; r < mr; ++r) {
-      for (int k = threadIdx.x; k < ne / 2; k += blockDim.x) {
-        int p, q;
-        if (k == 0) {
-          p = 0;
-          q = r + 1;
-        } else {
-          p = ((r + k) % mr) + 1;
-          q = (((r - k) % mr) + mr) % mr + 1;
-        }
-        if (p > q) {
-          const int t = p;
-          p = q;
-          q = t;
-        }
-        if (q >= n) {  // dummy partner (odd n)
-          if (p < n) {
-            partner[p] = p;
-            cself[p] = 1.0;
-            cpart[p] = 0.0;
-          }
-          continue;
-        }
-        const double app = C[p + (int64_t)p * n], aqq = C[q + (int64_t)q * n], apq = C[p + (int64_t)q * n];
-        double c = 1.0, s = 0.0;
-        if (apq != 0.0) {
-          const double th = (aqq - app) / (2.0 * apq);
-          const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
-          c = 1.0 / sqrt(1.0 + t * t);
-          s = t * c;
-        }
-        partner[p] = q;
-        partner[q] = p;
-        cself[p] = c;
-        cpart[p] = -s;
-        cself[q] = c;
-        cpart[q] = s;
-      }
-      __syncthreads();
-      for (int64_t e = tm.rank; e < (int64_t)n * n; e += tm.size) {
-        const int i = (int)(e % n), j = (int)(e / n);
-        const int pi = partner[i], pj = partner[j];
-        const double si = cself[i], ti = cpart[i], sj = cself[j], tj = cpart[j];
-        double v = si * sj * C[i + (int64_t)j * n];
-        if (pj != j) v += si * tj * C[i + (int64_t)pj * n];
-        if (pi != i) v += ti * sj * C[pi + (int64_t)j * n];
-        if (pi != i && pj != j) v += ti * tj * C[pi + (int64_t)pj * n];
-        Cn[e] = v;
-        double w = sj * V[i + (int64_t)j * n];
-        if (pj != j) w += tj * V[i + (int64_t)pj * n];
-        Vn[e] = w;
+  if constexpr (QL) {
+    // Large blocks: Householder reduction to tridiagonal form, explicit
+    // accumulation of the reflectors into V, then implicit QL sweeps with
+    // Wilkinson shifts.  One thread computes each sweep's rotation chain; the
+    // whole team applies the chain to its rows of V.
+    double* d = Cn;
+    double* e = d + n;
+    double* tau = e + n;
+    double* pv = tau + n;
+    double* rc = pv + n;
+    double* rs = rc + n;
+    int* ri = reinterpret_cast<int*>(rs + n);
+    int* ctl = ri + n;  // [0] rotations in the sweep, [1] finished, [2] l, [3] iterations at l
+    for (int k = 0; k + 2 < n; ++k) {
+      const int mm = n - k - 1;
+      double* x = C + (k + 1) + (int64_t)k * n;  // column k below the diagonal
+      double ss = 0.0;
+      for (int i = tm.rank; i < mm; i += tm.size) ss += x[i] * x[i];
+      ss = tm.sum(ss, sh, red);
+      const double x0 = x[0];
+      const double xn = sqrt(ss);
+      // H = I - tk u u^T with u = x - alpha e_0, alpha = -sign(x0) ||x||,
+      // u^T u = 2 (||x||^2 + |x0| ||x||)
+      const double alpha = xn == 0.0 ? 0.0 : (x0 >= 0.0 ? -xn : xn);
+      const double tk = xn == 0.0 ? 0.0 : 1.0 / (xn * (xn + fabs(x0)));
+      tm.sync();
+      if (tm.rank == 0) {
+        x[0] = x0 - alpha;
+        tau[k] = tk;
+        e[k] = alpha;
+        d[k] = C[k + (int64_t)k * n];
       }
       tm.sync();
-      double* t0 = C;
-      C = Cn;
-      Cn = t0;
-      double* t1 = V;
-      V = Vn;
-      Vn = t1;
+      if (tk != 0.0) {
+        double* A = C + (k + 1) + (int64_t)(k + 1) * n;  // trailing block, leading dimension n
+        for (int i = tm.rank; i < mm; i += tm.size) {
+          double acc = 0.0;
+          for (int j = 0; j < mm; ++j) acc += A[i + (int64_t)j * n] * x[j];
+          pv[i] = tk * acc;
+        }
+        tm.sync();
+        double pu = 0.0;
+        for (int i = tm.rank; i < mm; i += tm.size) pu += pv[i] * x[i];
+        pu = tm.sum(pu, sh, red);
+        const double K = 0.5 * tk * pu;
+        for (int64_t q = tm.rank; q < (int64_t)mm * mm; q += tm.size) {
+          const int i = (int)(q % mm), j = (int)(q / mm);
+          A[i + (int64_t)j * n] -= x[i] * (pv[j] - K * x[j]) + (pv[i] - K * x[i]) * x[j];
+        }
+        tm.sync();
+      }
+    }
+    if (tm.rank == 0) {
+      if (n >= 2) {
+        d[n - 2] = C[(n - 2) + (int64_t)(n - 2) * n];
+        e[n - 2] = C[(n - 1) + (int64_t)(n - 2) * n];
+      }
+      d[n - 1] = C[(n - 1) + (int64_t)(n - 1) * n];
+      e[n - 1] = 0.0;
+      ctl[2] = 0;
+      ctl[3] = 0;
+    }
+    tm.sync();
+    // V = H_0 H_1 ... H_{n-3}, accumulated backwards
+    for (int k = n - 3; k >= 0; --k) {
+      const double tk = tau[k];
+      if (tk == 0.0) continue;
+      const int mm = n - k - 1;
+      const double* u = C + (k + 1) + (int64_t)k * n;
+      double* Q = V + (k + 1) + (int64_t)(k + 1) * n;
+      for (int j = tm.rank; j < mm; j += tm.size) {
+        double acc = 0.0;
+        for (int i = 0; i < mm; ++i) acc += u[i] * Q[i + (int64_t)j * n];
+        pv[j] = tk * acc;
+      }
+      tm.sync();
+      for (int64_t q = tm.rank; q < (int64_t)mm * mm; q += tm.size) {
+        const int i = (int)(q % mm), j = (int)(q / mm);
+        Q[i + (int64_t)j * n] -= u[i] * pv[j];
+      }
+      tm.sync();
+    }
+    // implicit QL on (d, e): e[i] couples i and i+1
+    for (int guard = 0; guard < 64 * n + 64; ++guard) {
+      if (tm.rank == 0) {
+        int l = ctl[2], iter = ctl[3], nrot = 0, fin = 0;
+        for (;;) {
+          if (l >= n) {
+            fin = 1;
+            break;
+          }
+          int mm = l;
+          for (; mm < n - 1; ++mm)
+            if (fabs(e[mm]) <= DBL_EPSILON * (fabs(d[mm]) + fabs(d[mm + 1]))) break;
+          if (mm == l || iter >= 60) {  // d[l] converged (or the iteration budget is spent)
+            ++l;
+            iter = 0;
+            continue;
+          }
+          ++iter;
+          double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+          double r = hypot(g, 1.0);
+          g = d[mm] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
+          double sn = 1.0, cs = 1.0, p = 0.0;
+          bool split = false;
+          for (int i = mm - 1; i >= l; --i) {
+            const double f = sn * e[i], bb = cs * e[i];
+            r = hypot(f, g);
+            e[i + 1] = r;
+            if (r == 0.0) {  // the chain split: recheck convergence before finishing
+              d[i + 1] -= p;
+              e[mm] = 0.0;
+              split = true;
+              break;
+            }
+            sn = f / r;
+            cs = g / r;
+            g = d[i + 1] - p;
+            r = (d[i] - g) * sn + 2.0 * cs * bb;
+            p = sn * r;
+            d[i + 1] = g + p;
+            g = cs * r - bb;
+            rc[nrot] = cs;
+            rs[nrot] = sn;
+            ri[nrot] = i;
+            ++nrot;
+          }
+          if (!split) {
+            d[l] -= p;
+            e[l] = g;
+            e[mm] = 0.0;
+          }
+          break;
+        }
+        ctl[0] = nrot;
+        ctl[1] = fin;
+        ctl[2] = l;
+        ctl[3] = iter;
+      }
+      tm.sync();
+      const int nrot = ctl[0];
+      const int fin = ctl[1];
+      if (fin) break;
+      for (int row = tm.rank; row < n; row += tm.size) {
+        for (int q = 0; q < nrot; ++q) {
+          const int i = ri[q];
+          const double cs = rc[q], sn = rs[q];
+          double* vi = V + row + (int64_t)i * n;
+          const double a0 = vi[0], a1 = vi[n];
+          vi[n] = sn * a0 + cs * a1;
+          vi[0] = cs * a0 - sn * a1;
+        }
+      }
+      tm.sync();
+    }
+    for (int i = tm.rank; i < n; i += tm.size) C[i + (int64_t)i * n] = d[i];
+    tm.sync();
+  } else {
+    // Cyclic Jacobi, parallel (round-robin) ordering: each round applies n/2
+    // disjoint rotations at once, C <- J^T C J, V <- V J.  Every CTA of the
+    // team computes all rotation angles of a round (same inputs, same
+    // results) and updates its share of the entries.
+    const int ne = n + (n & 1);
+    const int mr = ne - 1;
+    const double tolf = 4.0 * (double)max(n, 16) * DBL_EPSILON;
+    for (int sweep = 0; sweep < 40 && n > 1; ++sweep) {
+      double off = 0.0, tot = 0.0;
+      for (int64_t e = tm.rank; e < (int64_t)n * n; e += tm.size) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        const double v = C[e] * C[e];
+        tot += v;
+        if (i != j) off += v;
+      }
+      off = tm.sum(off, sh, red);
+      tot = tm.sum(tot, sh, red);
+      if (!(off > tolf * tolf * tot)) break;
+      for (int r = 0; r < mr; ++r) {
+        for (int k = threadIdx.x; k < ne / 2; k += blockDim.x) {
+          int p, q;
+          if (k == 0) {
+            p = 0;
+            q = r + 1;
+          } else {
+            p = ((r + k) % mr) + 1;
+            q = (((r - k) % mr) + mr) % mr + 1;
+          }
+          if (p > q) {
+            const int t = p;
+            p = q;
+            q = t;
+          }
+          if (q >= n) {  // dummy partner (odd n)
+            if (p < n) {
+              partner[p] = p;
+              cself[p] = 1.0;
+              cpart[p] = 0.0;
+            }
+            continue;
+          }
+          const double app = C[p + (int64_t)p * n], aqq = C[q + (int64_t)q * n], apq = C[p + (int64_t)q * n];
+          double c = 1.0, s = 0.0;
+          if (apq != 0.0) {
+            const double th = (aqq - app) / (2.0 * apq);
+            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+          partner[p] = q;
+          partner[q] = p;
+          cself[p] = c;
+          cpart[p] = -s;
+          cself[q] = c;
+          cpart[q] = s;
+        }
+        __syncthreads();
+        for (int64_t e = tm.rank; e < (int64_t)n * n; e += tm.size) {
+          const int i = (int)(e % n), j = (int)(e / n);
+          const int pi = partner[i], pj = partner[j];
+          const double si = cself[i], ti = cpart[i], sj = cself[j], tj = cpart[j];
+          double v = si * sj * C[i + (int64_t)j * n];
+          if (pj != j) v += si * tj * C[i + (int64_t)pj * n];
+          if (pi != i) v += ti * sj * C[pi + (int64_t)j * n];
+          if (pi != i && pj != j) v += ti * tj * C[pi + (int64_t)pj * n];
+          Cn[e] = v;
+          double w = sj * V[i + (int64_t)j * n];
+          if (pj != j) w += tj * V[i + (int64_t)pj * n];
+          Vn[e] = w;
+        }
+        tm.sync();
+        double* t0 = C;
+        C = Cn;
+        Cn = t0;
+        double* t1 = V;
+        V = Vn;
+        Vn = t1;
+      }
     }
   }
   // ascending mu (stable on ties)
@@ -743,8 +933,10 @@ int launch_chol(int nb, int max_m, const int32_t* m, const int64_t* a_off, doubl
 int launch_schur(int nb, int max_m, const int32_t* m, const int32_t* no, const int64_t* a_off, double* Atpool,
                  double rtol, cudaStream_t s) {
   if (nb == 0) return AMGDD_OK;
-  if (max_m >= kBigDim) return launch_team(k_schur<kBigTeam>, kBigTeam, nb, 256, 0, s, m, no, a_off, Atpool, rtol);
-  return launch_team(k_schur<1>, 1, nb, threads_for((int64_t)max_m * max_m), 0, s, m, no, a_off, Atpool, rtol);
+  const size_t smem = (size_t)max_m * sizeof(int);
+  if (max_m >= kBigDim)
+    return launch_team(k_schur<kBigTeam>, kBigTeam, nb, 256, smem, s, m, no, a_off, Atpool, rtol);
+  return launch_team(k_schur<1>, 1, nb, threads_for((int64_t)max_m * max_m), smem, s, m, no, a_off, Atpool, rtol);
 }
 
 int launch_inv_rows(int nb, int max_m, const int32_t* m, const int32_t* no, const int64_t* a_off,
@@ -768,10 +960,10 @@ int launch_gep(int nb, int max_no, const int32_t* m, const int32_t* no, const in
   if (nb == 0) return AMGDD_OK;
   const size_t smem = (size_t)(2 * (max_no + 1)) * sizeof(double) + (size_t)(max_no + 1) * sizeof(int);
   if (max_no >= kBigDim)
-    return launch_team(k_gep<kBigTeam>, kBigTeam, nb, 256, smem, s, m, no, a_off, Lpool, Spool, cap, thresh, mu_off,
-                       mu, z_off_cap, Zcap, kout, scratch, scr_off);
-  return launch_team(k_gep<1>, 1, nb, threads_for((int64_t)max_no * max_no), smem, s, m, no, a_off, Lpool, Spool, cap,
-                     thresh, mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off);
+    return launch_team(k_gep<kBigTeam, true>, kBigTeam, nb, 256, smem, s, m, no, a_off, Lpool, Spool, cap, thresh,
+                       mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off);
+  return launch_team(k_gep<1, false>, 1, nb, threads_for((int64_t)max_no * max_no), smem, s, m, no, a_off, Lpool,
+                     Spool, cap, thresh, mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off);
 }
 
 int launch_pack_z(int nb, const int32_t* no, const int32_t* k, const int64_t* z_off_cap, const double* Zcap,

@@ -6,15 +6,19 @@ Every check runs the same seeded problem through both sides.  Structures
 * 1e-12 relative per FP64 V-cycle application (every level), 1e-10
   relative on the final x, the mixed form reaching the same 1e-8 relative
   residual;
-* level 0: local eigenvalues within 1e-11 and per-aggregate subspace angles
-  within 1e-10 (or the Davis-Kahan scale 64 n eps / gap where the gap at the
-  selection cut is smaller; aggregates whose cut falls inside a cluster with
-  relative gap <= 1e-8 have no unique subspace and are skipped);
-* coarse levels: the Schur complement of Eq. gevp-S is taken from Gram
-  matrices A~_GG that are exactly singular with a continuum of tiny
-  eigenvalues, which fixes S~ only to ~ eps / lambda_min; there the spectra
-  are compared to 1e-5 and angles to 1e-4, and the level operators that
-  depend on the coarse basis (A_l, RAS, RAS-T for l >= 1) to 1e-10.
+* local eigenvalues within 1e-11 on level 0 and 1e-10 on coarse levels;
+  per-aggregate subspace angles within 1e-10 on level 0 and 1e-9 on coarse
+  levels, or the Davis-Kahan scale 64 n eps / gap where the gap at the
+  selection cut is smaller; aggregates whose cut falls inside a cluster
+  with relative gap <= 1e-8 have no unique subspace and are skipped;
+* level operators that are written in a coarse basis (A_l, RAS, RAS-T for
+  l >= 1, the coarsest solve) to 1e-10 / 1e-9: that basis itself carries the
+  eigenvector tolerance above.
+
+The coarse-level A~_GG blocks are exactly singular (hundreds of eigenvalues
+at the rounding floor, none between 1e-14 and 1e-8 of the largest), so the
+pseudo-inverse of Eq. gevp-S is well defined; both sides reveal that null
+space (eigenvalues in the oracle, diagonal pivoting on the GPU).
 """
 import math
 
@@ -106,8 +110,8 @@ def _degenerate_cut(mu, k, no):
 
 
 def _check_spectra(amg, H, ho, lvl, tol_mu=None, tol_angle=None):
-    tol_mu = tol_mu if tol_mu is not None else (1e-11 if lvl == 0 else 1e-5)
-    tol_angle = tol_angle if tol_angle is not None else (1e-10 if lvl == 0 else 1e-4)
+    tol_mu = tol_mu if tol_mu is not None else (1e-11 if lvl == 0 else 1e-10)
+    tol_angle = tol_angle if tol_angle is not None else (1e-10 if lvl == 0 else 1e-9)
     Lo = ho.levels[lvl]
     mu = H.export(lvl, amg.ARR_MU)
     Z = H.export(lvl, amg.ARR_Z)
@@ -143,6 +147,10 @@ CASES = {
     "ragged_3lvl": dict(N=23, theta=0.4, eps=1e-2, bs=4, overlap=1, c_min=(2, 3), n_coarse=40),
     # overlap 2 with D1 rows and 8x8 aggregates
     "overlap2_d1": dict(N=32, theta=1.0, eps=1e-4, bs=8, overlap=2, c_min=(4, 5), n_coarse=60, d1=1e-3),
+    # large coarse blocks (|omega| up to 264, |Omega| up to 480; one level-2
+    # aggregate covering every dof): cluster-team Cholesky / Schur and the
+    # tridiagonal + QL eigensolver path
+    "large_blocks": dict(N=40, theta=0.7, eps=1e-2, bs=8, overlap=1, c_min=(2,), n_coarse=200),
 }
 
 
@@ -185,7 +193,7 @@ def test_level_operators_fp64(amg, name):
         rc = _apply(amg, H, amg.OP_RESTRICT, lvl, x, nn)
         y = _apply(amg, H, amg.OP_PROLONG, lvl, rc, Lo.n)
         yo = Lo.P @ (Lo.P.T @ x)
-        tP = 1e-10 if lvl == 0 else 1e-4
+        tP = 1e-10 if lvl == 0 else 1e-9
         for i in range(Lo.nagg):
             if _degenerate_cut(Lo.mu[i], Lo.Z[i].shape[1], Lo.omega[i].shape[0]):
                 continue
@@ -196,9 +204,8 @@ def test_level_operators_fp64(amg, name):
     Lc = ho.levels[-1]
     xc = rng.standard_normal(Lc.n)
     ref = np.linalg.solve(Lc.A.toarray(), xc)
-    # A_L is written in the basis of level L-1; that basis carries the
-    # coarse-level Schur sensitivity once L-1 >= 1
-    tC = 1e-11 if len(ho.levels) == 2 else 1e-4
+    # A_L is written in the basis of level L-1
+    tC = 1e-11 if len(ho.levels) == 2 else 1e-9
     assert _rel(_apply(amg, H, amg.OP_COARSE, len(ho.levels) - 1, xc, Lc.n), ref) <= tC
 
 
