@@ -407,6 +407,7 @@ def run_ours(args):
         "vcycles_per_s": {"mixed": vc_mix, "fp64": vc_64},
         "iters": it_mix, "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "setup_s": setup_s, "levels": stats["n"], "op_complexity": stats["op_complexity"],
+        "coarse_A": [c["form"] for c in stats["coarse_A"]],
         "roofline": roofline, "vcycle_profile_us_gbs": vprof,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
         "cpu_baseline": cpu,

@@ -23,6 +23,11 @@
 #include "structure.h"
 
 namespace amgdd {
+struct Level;
+}
+static double apply_bytes(const amgdd::Level& L, size_t esz);
+
+namespace amgdd {
 
 static thread_local std::string g_last_error;
 
@@ -265,6 +270,144 @@ int build_apply(Level& L, cudaStream_t s) {
     AMGDD_TRY(L.t32.alloc(toff));
     AMGDD_TRY(build_seg(L.gt1, n1, c1, moff, in1, out1, L.d_g_idx.p, L.d_tidx.p, s, 1));
     AMGDD_TRY(build_seg(L.gt2, n2, c2, moff, in2, out2, L.d_tidx.p, L.d_g_idx.p, s, 2));
+  }
+  return AMGDD_OK;
+}
+
+// A_l by block rows (Eq. 1 summed per row group): blocks are runs of
+// consecutive dofs with identical group lists.  On coarse levels every G_l
+// row touches whole blocks of coarse dofs (the columns of one Z_i), so a
+// block's rows share the support in_b and A(D_b, in_b) is dense.  Used when
+// it moves no more bytes than the matrix-free form.
+int build_blockrows(Level& L, cudaStream_t s) {
+  Supports S;
+  S.ptr = L.g_ptr;
+  S.idx = L.g_idx;
+  std::vector<int64_t> nptr;
+  std::vector<int32_t> ngrp;
+  node_groups(S, L.n, nptr, ngrp);
+  const int64_t n = L.n;
+  auto same_groups = [&](int64_t u, int64_t v) {
+    return nptr[u + 1] - nptr[u] == nptr[v + 1] - nptr[v] &&
+           std::equal(ngrp.begin() + nptr[u], ngrp.begin() + nptr[u + 1], ngrp.begin() + nptr[v]);
+  };
+  std::vector<int32_t> nr, nc, pgrp, pp0, map, blk_in;
+  std::vector<int64_t> moff, ioff, ooff, pptr(1, 0), pmap;
+  std::vector<int64_t> mark(n, -1);
+  std::vector<int32_t> loc(n, -1);
+  int64_t mat = 0;
+  for (int64_t d0 = 0; d0 < n;) {
+    int64_t d1 = d0 + 1;
+    while (d1 < n && same_groups(d0, d1)) ++d1;
+    const int32_t kb = (int32_t)(d1 - d0);
+    const int64_t b = (int64_t)nr.size();
+    const int64_t i0 = (int64_t)blk_in.size();
+    for (int64_t q = nptr[d0]; q < nptr[d0 + 1]; ++q) {
+      const int32_t g = ngrp[q];
+      for (int64_t e = L.g_ptr[g]; e < L.g_ptr[g + 1]; ++e) {
+        const int32_t v = L.g_idx[e];
+        if (mark[v] != b) {
+          mark[v] = b;
+          blk_in.push_back(v);
+        }
+      }
+    }
+    std::sort(blk_in.begin() + i0, blk_in.end());
+    const int32_t nin = (int32_t)(blk_in.size() - i0);
+    for (int32_t c = 0; c < nin; ++c) loc[blk_in[i0 + c]] = c;
+    for (int64_t q = nptr[d0]; q < nptr[d0 + 1]; ++q) {
+      const int32_t g = ngrp[q];
+      const auto first = L.g_idx.begin() + L.g_ptr[g], last = L.g_idx.begin() + L.g_ptr[g + 1];
+      const int64_t p0 = std::lower_bound(first, last, (int32_t)d0) - first;
+      if (p0 + kb > last - first || *(first + p0 + kb - 1) != (int32_t)(d1 - 1)) {
+        set_error("block rows: dofs %lld..%lld are not contiguous in a group support", (long long)d0,
+                  (long long)(d1 - 1));
+        return AMGDD_ERR_INTERNAL;
+      }
+      pgrp.push_back(g);
+      pp0.push_back((int32_t)p0);
+      pmap.push_back((int64_t)map.size());
+      for (auto it = first; it != last; ++it) map.push_back(loc[*it]);
+    }
+    for (int32_t c = 0; c < nin; ++c) loc[blk_in[i0 + c]] = -1;
+    pptr.push_back((int64_t)pgrp.size());
+    nr.push_back(kb);
+    nc.push_back(nin);
+    moff.push_back(mat);
+    ioff.push_back(i0);
+    ooff.push_back(d0);
+    mat += (int64_t)kb * nin;
+    d0 = d1;
+  }
+  const int nblk = (int)nr.size();
+  // bytes of one residual in FP32: block rows against the matrix-free form
+  const double blk_bytes = (double)mat * 4.0 + (double)blk_in.size() * 4.0 + 3.0 * n * 4.0;
+  const double mf_bytes = apply_bytes(L, 4);
+  L.blk_mb = blk_bytes / 1e6;
+  L.mf_mb = mf_bytes / 1e6;
+  if (nblk * 2 > n) return AMGDD_OK;  // (near-)singleton blocks: nothing to gain
+  DBuf<int32_t> dnr, dnc, dpgrp, dpp0, dmap;
+  DBuf<int64_t> dmoff, dpptr, dpmap;
+  AMGDD_TRY(dnr.upload(nr, s));
+  AMGDD_TRY(dnc.upload(nc, s));
+  AMGDD_TRY(dmoff.upload(moff, s));
+  AMGDD_TRY(dpptr.upload(pptr, s));
+  AMGDD_TRY(dpgrp.upload(pgrp, s));
+  AMGDD_TRY(dpp0.upload(pp0, s));
+  AMGDD_TRY(dpmap.upload(pmap, s));
+  AMGDD_TRY(dmap.upload(map, s));
+  AMGDD_TRY(L.A64.alloc(mat));
+  AMGDD_TRY(L.At64.alloc(mat));
+  AMGDD_TRY(L.A32.alloc(mat));
+  AMGDD_TRY(L.At32.alloc(mat));
+  AMGDD_TRY(launch_blockrows(nblk, dnr.p, dnc.p, dmoff.p, dpptr.p, dpgrp.p, dpp0.p, dpmap.p, dmap.p, L.d_g_ptr.p,
+                             L.d_h_off.p, L.d_H.p, L.A64.p, L.A32.p, L.At64.p, L.At32.p, s));
+  AMGDD_TRY(L.d_blk_in.upload(blk_in, s));
+  std::vector<int32_t> io(n);
+  std::iota(io.begin(), io.end(), 0);
+  AMGDD_TRY(L.d_blk_out.upload(io, s));
+  AMGDD_TRY(build_seg(L.ablk, nr, nc, moff, ioff, ooff, L.d_blk_in.p, L.d_blk_out.p, s));
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  L.has_blk = true;
+  return AMGDD_OK;
+}
+
+// Setup-time tuning of the coarse A-apply: time one FP32 residual of level L
+// in both stored forms and keep the faster.  Block rows move more bytes than
+// the compressed row groups but need no atomics and stream dense rows.
+int tune_level_A(Level& L, cudaStream_t s) {
+  if (!L.has_blk) return AMGDD_OK;
+  AMGDD_TRY(L.x32.zero(s));
+  AMGDD_TRY(L.r32.zero(s));
+  cudaEvent_t e[3];
+  for (auto& v : e) AMGDD_CUDA(cudaEventCreate(&v));
+  float t[2] = {0.f, 0.f};
+  constexpr int kReps = 10;
+  int rc = AMGDD_OK;
+  for (int form = 0; form < 2 && rc == AMGDD_OK; ++form) {
+    for (int rep = 0; rep < kReps + 2 && rc == AMGDD_OK; ++rep) {
+      if (rep == 2) cudaEventRecord(e[0], s);
+      rc = form == 0 ? launch_seg(L.ablk, L.A32.p, true, L.x32.p, L.s32.p, true, SEG_RESID, nullptr, s, L.r32.p,
+                                  nullptr, L.At32.p)
+                     : launch_apply(L.aplan, L, true, L.x32.p, L.s32.p, -1, nullptr, s);
+    }
+    cudaEventRecord(e[1], s);
+    if (cudaEventSynchronize(e[1]) != cudaSuccess || cudaEventElapsedTime(&t[form], e[0], e[1]) != cudaSuccess)
+      rc = AMGDD_ERR_CUDA;
+  }
+  for (auto& v : e) cudaEventDestroy(v);
+  AMGDD_TRY(rc);
+  L.blk_us = 1e3 * t[0] / kReps;
+  L.mf_us = 1e3 * t[1] / kReps;
+  if (g_timer.on)
+    fprintf(stderr, "[amgdd] n=%lld A-apply: block rows %.1f MB %.1f us, matrix-free %.1f MB %.1f us\n",
+            (long long)L.n, L.blk_mb, L.blk_us, L.mf_mb, L.mf_us);
+  if (L.mf_us <= L.blk_us) {
+    L.has_blk = false;
+    L.A64.release();
+    L.At64.release();
+    L.A32.release();
+    L.At32.release();
   }
   return AMGDD_OK;
 }
@@ -784,6 +927,34 @@ static double apply_bytes(const Level& L, size_t esz) {
   return b;
 }
 
+// One residual s = r - A x of a non-coarsest level, with the copy of r that
+// the matrix-free form needs.
+static double resid_bytes(const Level& L, size_t esz) {
+  if (L.has_blk) return seg_bytes(L.ablk, L.n, L.n, true, esz);
+  return apply_bytes(L, esz) + (double)L.n * esz;
+}
+
+// y = A_l x (Eq. 1) in the level's working precision: block rows when stored,
+// else G then G^T by row groups.
+static int level_apply_A(const Level& L, bool f32, const void* x, void* y, cudaStream_t s) {
+  if (L.has_blk)
+    return launch_seg(L.ablk, f32 ? (const void*)L.A32.p : (const void*)L.A64.p, f32, x, y, f32, SEG_STORE, nullptr,
+                      s, nullptr, nullptr, f32 ? (const void*)L.At32.p : (const void*)L.At64.p);
+  AMGDD_CUDA(cudaMemsetAsync(y, 0, L.n * (f32 ? sizeof(float) : sizeof(double)), s));
+  return launch_apply(L.aplan, L, f32, x, y, +1, nullptr, s);
+}
+
+// s = r - A_l x.  The matrix-free form subtracts A x from s in place, so the
+// launch before it must have copied r into s (`rcopy` tells those launches).
+static int level_residual(const Level& L, bool f32, const void* x, const void* r, void* sv, const int* skip,
+                          cudaStream_t s) {
+  if (L.has_blk)
+    return launch_seg(L.ablk, f32 ? (const void*)L.A32.p : (const void*)L.A64.p, f32, x, sv, f32, SEG_RESID, skip,
+                      s, r, nullptr, f32 ? (const void*)L.At32.p : (const void*)L.At64.p);
+  return launch_apply(L.aplan, L, f32, x, sv, -1, skip, s);
+}
+static bool rcopy(const Level& L) { return !L.has_blk; }
+
 // ---------------------------------------------------------------------------
 // Event marks between the launches of one V-cycle (profiling only): the time
 // from mark i to mark i+1 is charged to (level, slot) of mark i.
@@ -839,19 +1010,21 @@ static int vcycle(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, c
   // pre-smoothing from x = 0: x = M_RAS^{-1} r  (Eq. ras); the same launch
   // copies s(omega_i) = r(omega_i) for the residual
   AMGDD_MARK(0);
-  AMGDD_TRY(launch_seg(L.ras, W, f32, r, x, f32, SEG_STORE, skip, s, r, sv, Wt));
+  AMGDD_TRY(launch_seg(L.ras, W, f32, r, x, f32, SEG_STORE, skip, s, rcopy(L) ? r : nullptr, rcopy(L) ? sv : nullptr,
+                       Wt));
   // s = r - A x ; r_c = P^T s
   AMGDD_MARK(2);
-  AMGDD_TRY(launch_apply(L.aplan, L, f32, x, sv, -1, skip, s));
+  AMGDD_TRY(level_residual(L, f32, x, r, sv, skip, s));
   AMGDD_MARK(3);
   AMGDD_TRY(launch_seg(L.restr, Zt, f32, sv, rn, f32, SEG_STORE, skip, s, nullptr, nullptr, Z));
   // x_c = B_{l+1} r_c ; x += P x_c  (Eq. cgc)
   AMGDD_TRY(vcycle(h, l + 1, f32, rn, xn, skip, s, prof));
   AMGDD_MARK(4);
-  AMGDD_TRY(launch_seg(L.prol, Z, f32, xn, x, f32, SEG_ADD, skip, s, r, sv, Zt));
+  AMGDD_TRY(launch_seg(L.prol, Z, f32, xn, x, f32, SEG_ADD, skip, s, rcopy(L) ? r : nullptr, rcopy(L) ? sv : nullptr,
+                       Zt));
   // post-smoothing: x += M_RAS-T^{-1} (r - A x)  (Eq. ras-t)
   AMGDD_MARK(2);
-  AMGDD_TRY(launch_apply(L.aplan, L, f32, x, sv, -1, skip, s));
+  AMGDD_TRY(level_residual(L, f32, x, r, sv, skip, s));
   AMGDD_MARK(7);
   AMGDD_TRY(launch_seg(L.rast, Wt, f32, sv, x, f32, SEG_ATOMIC_ADD, skip, s, nullptr, nullptr, W));
   return AMGDD_OK;
@@ -1195,6 +1368,11 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     }
     AMGDD_TRY(build_level(*H, L, lvl, lvl == 0 ? aggh.data() : nullptr, s));
     AMGDD_TRY(build_plans(*H, L, L.d_om_idx, s));
+    if (lvl > 0) {
+      Phase ph(9, "block rows", s);
+      AMGDD_TRY(build_blockrows(L, s));
+      AMGDD_TRY(tune_level_A(L, s));
+    }
     std::unique_ptr<Level> N(new Level());
     {
       Phase ph(7, "next level", s);
@@ -1330,8 +1508,7 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
   const size_t esz = f32 ? sizeof(float) : sizeof(double);
   switch (op) {
     case AMGDD_OP_A:
-      AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
-      AMGDD_TRY(launch_apply(L.aplan, L, f32, xin, yout, +1, nullptr, s));
+      AMGDD_TRY(level_apply_A(L, f32, xin, yout, s));
       break;
     case AMGDD_OP_RAS:
       AMGDD_TRY(launch_seg(L.ras, f32 ? (const void*)L.W32.p : (const void*)L.W64.p, f32, xin, yout, f32, SEG_STORE,
@@ -1449,8 +1626,7 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
   const size_t esz = f32 ? sizeof(float) : sizeof(double);
   switch (op) {
     case AMGDD_OP_A:
-      AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
-      AMGDD_TRY(launch_apply(L.aplan, L, f32, xin, yout, +1, nullptr, s));
+      AMGDD_TRY(level_apply_A(L, f32, xin, yout, s));
       break;
     case AMGDD_OP_RAS:
       AMGDD_TRY(launch_seg(L.ras, f32 ? (const void*)L.W32.p : (const void*)L.W64.p, f32, xin, yout, f32, SEG_STORE,
@@ -1521,10 +1697,11 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes
       if (f32) b[1] = b[5] = (double)L.n * 12.0;
     } else {
       const int64_t nn = L.col0.back();
-      b[0] = seg_bytes(L.ras, L.n, L.n, false, esz) + L.n * esz;  // + fused copy r -> s
-      b[2] = 2.0 * apply_bytes(L, esz);                            // two residual A-applies
+      const double cp = rcopy(L) ? (double)L.n * esz : 0.0;  // fused copy r -> s
+      b[0] = seg_bytes(L.ras, L.n, L.n, false, esz) + cp;
+      b[2] = 2.0 * (resid_bytes(L, esz) - cp);  // two residuals
       b[3] = seg_bytes(L.restr, L.n, nn, false, esz);
-      b[4] = seg_bytes(L.prol, nn, L.n, true, esz) + L.n * esz;   // + fused copy r -> s
+      b[4] = seg_bytes(L.prol, nn, L.n, true, esz) + cp;
       b[7] = seg_bytes(L.rast, L.n, L.n, true, esz);
     }
   }
@@ -1619,7 +1796,7 @@ static void level_bytes(const amgdd_hierarchy& h, const Level& L, size_t esz, do
   const int64_t nn = L.col0.back();
   cyc += seg_bytes(L.ras, L.n, L.n, false, esz) + seg_bytes(L.rast, L.n, L.n, true, esz) +
          seg_bytes(L.restr, L.n, nn, false, esz) + seg_bytes(L.prol, nn, L.n, true, esz) +
-         2.0 * (apply_bytes(L, esz) + L.n * esz);  // the residual copy rides on RAS / prolongation
+         2.0 * resid_bytes(L, esz);
   (void)h;
 }
 
@@ -1660,6 +1837,14 @@ int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap) {
     amgdd_level_desc d;
     amgdd_level_describe(h, (int)l, &d);
     s += (l ? ", " : "") + std::to_string(d.w_vals);
+  }
+  s += "], \"coarse_A\": [";
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    const Level& L = *h->lv[l];
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "%s{\"form\": \"%s\", \"block_rows_us\": %.2f, \"matrix_free_us\": %.2f}",
+                  l ? ", " : "", L.coarsest ? "none" : (L.has_blk ? "block rows" : "matrix-free"), L.blk_us, L.mf_us);
+    s += buf;
   }
   double vb = 0, ab = 0;
   amgdd_bytes_model(h, &vb, &ab);

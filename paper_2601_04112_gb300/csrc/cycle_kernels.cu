@@ -122,9 +122,11 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
         *dst += acc;
       else if (MODE == SEG_ATOMIC_ADD)
         atomic_add(dst, acc);
-      else
+      else if (MODE == SEG_ATOMIC_SUB)
         atomic_add(dst, -acc);
-      if (cdst != nullptr) cdst[o] = csrc[o];
+      else
+        *dst = csrc[o] - acc;
+      if (MODE != SEG_RESID && cdst != nullptr) cdst[o] = csrc[o];
     }
   }
 }
@@ -173,9 +175,11 @@ __global__ void __launch_bounds__(128) k_seg_rows(const int32_t* __restrict__ ta
     *dst += acc;
   else if (MODE == SEG_ATOMIC_ADD)
     atomic_add(dst, acc);
-  else
+  else if (MODE == SEG_ATOMIC_SUB)
     atomic_add(dst, -acc);
-  if (cdst != nullptr) cdst[o] = csrc[o];
+  else
+    *dst = csrc[o] - acc;
+  if (MODE != SEG_RESID && cdst != nullptr) cdst[o] = csrc[o];
 }
 
 template <class T, int L, int MODE>
@@ -201,7 +205,8 @@ int seg_rows_mode(const SegPlan& p, const T* MT, const T* x, T* y, SegMode mode,
     case SEG_STORE: return seg_rows_launch<T, L, SEG_STORE>(p, MT, x, y, skip, s, csrc, cdst);
     case SEG_ADD: return seg_rows_launch<T, L, SEG_ADD>(p, MT, x, y, skip, s, csrc, cdst);
     case SEG_ATOMIC_ADD: return seg_rows_launch<T, L, SEG_ATOMIC_ADD>(p, MT, x, y, skip, s, csrc, cdst);
-    default: return seg_rows_launch<T, L, SEG_ATOMIC_SUB>(p, MT, x, y, skip, s, csrc, cdst);
+    case SEG_ATOMIC_SUB: return seg_rows_launch<T, L, SEG_ATOMIC_SUB>(p, MT, x, y, skip, s, csrc, cdst);
+    default: return seg_rows_launch<T, L, SEG_RESID>(p, MT, x, y, skip, s, csrc, cdst);
   }
 }
 
@@ -223,14 +228,16 @@ int seg_dispatch_mode(const SegPlan& p, const T* M, const T* x, T* y, SegMode mo
       case SEG_STORE: return launch(k_seg<T, L, SEG_STORE, true>);
       case SEG_ADD: return launch(k_seg<T, L, SEG_ADD, true>);
       case SEG_ATOMIC_ADD: return launch(k_seg<T, L, SEG_ATOMIC_ADD, true>);
-      default: return launch(k_seg<T, L, SEG_ATOMIC_SUB, true>);
+      case SEG_ATOMIC_SUB: return launch(k_seg<T, L, SEG_ATOMIC_SUB, true>);
+      default: return launch(k_seg<T, L, SEG_RESID, true>);
     }
   }
   switch (mode) {
     case SEG_STORE: return launch(k_seg<T, L, SEG_STORE, false>);
     case SEG_ADD: return launch(k_seg<T, L, SEG_ADD, false>);
     case SEG_ATOMIC_ADD: return launch(k_seg<T, L, SEG_ATOMIC_ADD, false>);
-    default: return launch(k_seg<T, L, SEG_ATOMIC_SUB, false>);
+    case SEG_ATOMIC_SUB: return launch(k_seg<T, L, SEG_ATOMIC_SUB, false>);
+    default: return launch(k_seg<T, L, SEG_RESID, false>);
   }
 }
 
@@ -565,6 +572,10 @@ int launch_seg(const SegPlan& p, const void* M, bool m_fp32, const void* x, void
   if (p.rows_mode ? p.ntasks == 0 : p.nchunks == 0) return AMGDD_OK;
   if (m_fp32 != v_fp32) {
     set_error("launch_seg: matrix and vector precision differ");
+    return AMGDD_ERR_INTERNAL;
+  }
+  if (mode == SEG_RESID && csrc == nullptr) {
+    set_error("launch_seg: the residual mode needs the right-hand side");
     return AMGDD_ERR_INTERNAL;
   }
   if (m_fp32)

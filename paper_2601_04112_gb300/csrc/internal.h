@@ -74,7 +74,9 @@ struct DBuf {
 // with M_b row-major (nr_b x nc_b, leading dimension nc_b) at m_off[b].
 // Used for RAS (W_i), RAS-T (W_i^T), restriction (Z_i^T), prolongation (Z_i)
 // and the coarsest solve (A_L^{-1} as a single block).
-enum SegMode { SEG_STORE = 0, SEG_ADD = 1, SEG_ATOMIC_ADD = 2, SEG_ATOMIC_SUB = 3 };
+// SEG_RESID writes y[o] = c[o] - (M x)[o] with c the csrc argument (the
+// residual s = r - A x of a level whose A is stored by block rows).
+enum SegMode { SEG_STORE = 0, SEG_ADD = 1, SEG_ATOMIC_ADD = 2, SEG_ATOMIC_SUB = 3, SEG_RESID = 4 };
 
 struct SegPlan {
   int nblocks = 0;
@@ -134,6 +136,17 @@ struct Level {
   DBuf<double> t64;
   DBuf<float> t32;
   DBuf<int32_t> d_tidx;  // identity over t
+  // ---- A_l assembled by block rows (coarse levels) -------------------------
+  // A block is a run of consecutive dofs with identical lists of G groups;
+  // its rows share one support in_b, so A(D_b, in_b) is stored dense
+  // (row-major, plus the block-wise transpose) and applied by k_seg.
+  bool has_blk = false;
+  SegPlan ablk;
+  DBuf<int32_t> d_blk_in;   // concatenated supports in_b
+  DBuf<int32_t> d_blk_out;  // identity over the level's dofs
+  DBuf<double> A64, At64;
+  DBuf<float> A32, At32;
+  double blk_mb = 0, mf_mb = 0, blk_us = 0, mf_us = 0;  // setup-time comparison of the two forms
   // ---- aggregates and subdomains ------------------------------------------
   std::vector<int32_t> agg;      // n
   std::vector<int64_t> om_ptr;   // nagg+1
@@ -261,6 +274,12 @@ int launch_gep(int nb, int max_no, const int32_t* m, const int32_t* no, const in
                cudaStream_t s);
 int launch_pack_z(int nb, const int32_t* no, const int32_t* k, const int64_t* z_off_cap, const double* Zcap,
                   const int64_t* z_off, double* Z64, float* Z32, double* Zt64, float* Zt32, cudaStream_t s);
+// Block rows of A_l = sum_g H_g: for block b, rows p0 .. p0+nr_b-1 of each
+// touching group's Gram, columns mapped into in_b by `map`.
+int launch_blockrows(int nblk, const int32_t* nr, const int32_t* nc, const int64_t* m_off, const int64_t* pair_ptr,
+                     const int32_t* pair_grp, const int32_t* pair_p0, const int64_t* pair_map, const int32_t* map,
+                     const int64_t* g_ptr, const int64_t* h_off, const double* H, double* A64, float* A32,
+                     double* At64, float* At32, cudaStream_t s);
 int launch_next_gram(const NextGramPlan& p, int max_sn, const int64_t* g_ptr, const int64_t* h_off, const double* H,
                      const double* Z64, double* Hn, double* scratch, int64_t first, int64_t count, cudaStream_t s);
 

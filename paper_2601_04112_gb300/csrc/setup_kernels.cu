@@ -986,4 +986,57 @@ int launch_next_gram(const NextGramPlan& p, int max_sn, const int64_t* g_ptr, co
   return AMGDD_OK;
 }
 
+namespace {
+// One CTA per block of consecutive dofs D_b = d0 .. d0+nr_b-1 sharing the
+// row support in_b: A(D_b, in_b) = sum over the groups g whose support holds
+// D_b of rows p0_g .. p0_g+nr_b-1 of H_g (Eq. 1: A = sum_g G_g^T G_g), each
+// group's columns scattered to their positions in in_b.  Groups are summed in
+// a fixed order, so the result is deterministic.  Also writes the FP32 copy
+// and the block-wise transposes.
+__global__ void k_blockrows(const int32_t* __restrict__ nr, const int32_t* __restrict__ nc,
+                            const int64_t* __restrict__ m_off, const int64_t* __restrict__ pair_ptr,
+                            const int32_t* __restrict__ pair_grp, const int32_t* __restrict__ pair_p0,
+                            const int64_t* __restrict__ pair_map, const int32_t* __restrict__ map,
+                            const int64_t* __restrict__ g_ptr, const int64_t* __restrict__ h_off,
+                            const double* __restrict__ H, double* __restrict__ A64, float* __restrict__ A32,
+                            double* __restrict__ At64, float* __restrict__ At32) {
+  const int b = blockIdx.x;
+  const int kb = nr[b], nin = nc[b];
+  const int64_t len = (int64_t)kb * nin;
+  double* Ab = A64 + m_off[b];
+  for (int64_t e = threadIdx.x; e < len; e += blockDim.x) Ab[e] = 0.0;
+  __syncthreads();
+  for (int64_t q = pair_ptr[b]; q < pair_ptr[b + 1]; ++q) {
+    const int g = pair_grp[q];
+    const int sg = (int)(g_ptr[g + 1] - g_ptr[g]);
+    const double* Hg = H + h_off[g] + (int64_t)pair_p0[q] * sg;
+    const int32_t* mp = map + pair_map[q];
+    for (int64_t e = threadIdx.x; e < (int64_t)kb * sg; e += blockDim.x) {
+      const int r = (int)(e / sg), c = (int)(e - (int64_t)r * sg);
+      Ab[(int64_t)r * nin + mp[c]] += Hg[(int64_t)r * sg + c];
+    }
+    __syncthreads();
+  }
+  for (int64_t e = threadIdx.x; e < len; e += blockDim.x) {
+    const int r = (int)(e / nin), c = (int)(e - (int64_t)r * nin);
+    const double v = Ab[e];
+    A32[m_off[b] + e] = (float)v;
+    At64[m_off[b] + (int64_t)c * kb + r] = v;
+    At32[m_off[b] + (int64_t)c * kb + r] = (float)v;
+  }
+}
+}  // namespace
+
+int launch_blockrows(int nblk, const int32_t* nr, const int32_t* nc, const int64_t* m_off, const int64_t* pair_ptr,
+                     const int32_t* pair_grp, const int32_t* pair_p0, const int64_t* pair_map, const int32_t* map,
+                     const int64_t* g_ptr, const int64_t* h_off, const double* H, double* A64, float* A32,
+                     double* At64, float* At32, cudaStream_t s) {
+  if (nblk == 0) return AMGDD_OK;
+  k_blockrows<<<nblk, 256, 0, s>>>(nr, nc, m_off, pair_ptr, pair_grp, pair_p0, pair_map, map, g_ptr, h_off, H, A64,
+                                   A32, At64, At32);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
 }  // namespace amgdd
