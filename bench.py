@@ -37,6 +37,10 @@ if ROOT not in sys.path:
 
 METRIC = "V-cycles/s & solves/s to 1e-8 rel. residual (mixed vs FP64); p50/p99 latency"
 WORKLOAD = "q1_512_rot"
+# DRAM bytes per V-cycle by kernel family, from ncu captures of WORKLOAD
+# (dram__bytes_read.sum + dram__bytes_write.sum summed over one V-cycle's
+# launches; profiles/).  Entries are removed when their kernels change.
+TRAFFIC = {}
 
 
 def parse_args():
@@ -331,33 +335,49 @@ def run_ours(args):
     # per-step V-cycle profile (CUDA events between launches) -> roofline
     H.set_precision(amg.MIXED32)
     ms, by = H.profile_vcycle(10)
-    seg_slots, app_slots = (0, 3, 4, 7), (2,)
-    seg_ms = float(sum(ms[l, s] for l in range(ms.shape[0]) for s in seg_slots))
-    seg_by = float(sum(by[l, s] for l in range(ms.shape[0]) for s in seg_slots))
-    app_ms = float(sum(ms[l, s] for l in range(ms.shape[0]) for s in app_slots))
-    app_by = float(sum(by[l, s] for l in range(ms.shape[0]) for s in app_slots))
+    # kernel families by profile slot: slot 6 is the persistent tail (one
+    # cooperative launch for every level from its first), slot 2 the two
+    # residuals (k_seg over block rows or grouped k_apply), slots 1/5 casts
+    forms = [c["form"] for c in stats["coarse_A"]]
+    fam_ms, fam_by, fam_n = {}, {}, {}
+    for l in range(ms.shape[0]):
+        for k in range(ms.shape[1]):
+            if ms[l, k] <= 0:
+                continue
+            if k == 6:
+                fam, nk = "k_persistent", 1
+            elif k == 2:
+                fam, nk = ("k_seg" if forms[l] == "block rows" else "k_apply"), 2
+            elif k in (1, 5):
+                fam, nk = "k_cast", 1
+            else:
+                fam, nk = "k_seg", 1
+            fam_ms[fam] = fam_ms.get(fam, 0.0) + float(ms[l, k])
+            fam_by[fam] = fam_by.get(fam, 0.0) + float(by[l, k])
+            fam_n[fam] = fam_n.get(fam, 0) + nk
     vcyc_ms = float(ms.sum())
     peak, peak_kind = hbm_peak()
-    if seg_ms >= app_ms:
-        kname, kms, kby = "k_seg (RAS/RAS-T/P/R gather-GEMV-scatter, all levels, FP32)", seg_ms, seg_by
-        nlaunch = 4 * (ms.shape[0] - 1) + 1
-    else:
-        kname, kms, kby = "k_apply (grouped G then G^T residual, all levels, FP32)", app_ms, app_by
-        nlaunch = 2 * (ms.shape[0] - 1)
+    top = max(fam_ms, key=fam_ms.get)
+    kdesc = {"k_seg": "k_seg (batched gather-GEMV-scatter: RAS, RAS-T, P, R, block-row residuals; FP32)",
+             "k_apply": "k_apply (grouped G then G^T residual; FP32)",
+             "k_persistent": "k_persistent (cooperative V-cycle tail: every phase of the coarse levels; FP32)",
+             "k_cast": "k_cast"}
+    kms, kby = fam_ms[top], fam_by[top]
     achieved = kby / (kms * 1e-3) / 1e9
-    # DRAM bytes per V-cycle of the k_seg family from one ncu capture of this
-    # workload (profiles/dram_kseg_kapply_q1_512_rot.md); valid while those
-    # kernels are unchanged.  Traffic of k_apply was not captured separately.
-    traffic = 718.98e6 if kname.startswith("k_seg") and args.workload == WORKLOAD and args.N is None else None
+    # DRAM bytes per V-cycle of a kernel family from an ncu capture of this
+    # workload (profiles/); valid only while those kernels are unchanged
+    traffic = TRAFFIC.get(top) if args.workload == WORKLOAD and args.N is None else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per V-cycle (kernel family)",
-                "kernel": kname, "launches_per_vcycle": nlaunch,
+                "kernel": kdesc.get(top, top), "launches_per_vcycle": fam_n[top],
                 "bytes_per_vcycle": kby, "ms_per_vcycle": kms,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "families": {f: {"ms": round(fam_ms[f], 4), "gbs": round(fam_by[f] / (fam_ms[f] * 1e-3) / 1e9, 1),
+                                 "launches": fam_n[f]} for f in fam_ms},
                 "vcycle": {"ms": vcyc_ms, "bytes": float(by.sum()),
                            "achieved_gbs": float(by.sum()) / (vcyc_ms * 1e-3) / 1e9}}
     slot_names = {0: "ras_or_coarse", 1: "cast_in", 2: "residual_applies", 3: "restrict", 4: "prolong",
-                  5: "cast_out", 7: "rast"}
+                  5: "cast_out", 6: "persistent_tail", 7: "rast"}
     vprof = []
     for l in range(ms.shape[0]):
         vprof.append({slot_names[k]: [round(float(ms[l, k]) * 1e3, 1),
@@ -408,6 +428,7 @@ def run_ours(args):
         "iters": it_mix, "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "setup_s": setup_s, "levels": stats["n"], "op_complexity": stats["op_complexity"],
         "coarse_A": [c["form"] for c in stats["coarse_A"]],
+        "persistent_tail_from": {"mixed": stats["tail"]["mixed"]["from"], "fp64": stats["tail"]["fp64"]["from"]},
         "roofline": roofline, "vcycle_profile_us_gbs": vprof,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
         "cpu_baseline": cpu,

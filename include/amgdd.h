@@ -47,6 +47,7 @@ extern "C" {
 #define AMGDD_ERR_OOM -6            /* device allocation failed            */
 #define AMGDD_ERR_CUDA -7           /* any other CUDA runtime error        */
 #define AMGDD_ERR_INTERNAL -8       /* violated internal invariant         */
+#define AMGDD_ERR_TIMEOUT -9        /* a bounded device-side wait expired  */
 
 /* ---- memory spaces and precisions ------------------------------------ */
 #define AMGDD_HOST 0

@@ -30,6 +30,7 @@ static double apply_bytes(const amgdd::Level& L, size_t esz);
 namespace amgdd {
 
 static thread_local std::string g_last_error;
+thread_local int* g_err_word = nullptr;
 
 static std::atomic<int64_t> g_kernels{0};
 static thread_local bool g_capturing = false;
@@ -119,6 +120,116 @@ int fetch_any(std::vector<T>& h, const T* src, size_t n, bool dev, cudaStream_t 
 
 int lanes_for(int max_nc) { return max_nc >= 64 ? 32 : (max_nc >= 24 ? 16 : (max_nc >= 8 ? 8 : 4)); }
 
+// Items of the staged kernel.  An item is a contiguous range of the stored
+// matrix: consecutive whole blocks (at most 32) or a slice of rows of one
+// large block.  Items hold at most 8 KB of FP32 matrix, fewer on small
+// levels so that every SM gets about 16 of them.  Per item the host packs
+// the block tables and flat lists of the input and output indices, so that a
+// CTA reaches all of its global data in two dependent steps.  Plans with
+// rows longer than kItemMaxIn keep the unstaged kernels.
+constexpr int64_t kItemElems = 2048;
+constexpr int kItemMaxIn = 1024;
+constexpr int kItemMaxRows = 256;
+constexpr int kItemMaxBlocks = 32;
+int build_items(SegPlan& p, const std::vector<int32_t>& nr, const std::vector<int32_t>& nc,
+                const std::vector<int64_t>& m_off, const std::vector<int64_t>& in_off,
+                const std::vector<int64_t>& out_off, const int32_t* in_ext, const int32_t* out_ext, cudaStream_t s) {
+  p.staged = false;
+  p.nitems = 0;
+  const int nb = (int)nr.size();
+  if (nb == 0 || in_ext == nullptr || out_ext == nullptr) return AMGDD_OK;
+  int64_t total = 0, in_end = 0, out_end = 0;
+  double ncsum = 0.0, rows = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    if (nc[b] > kItemMaxIn) return AMGDD_OK;
+    total += (int64_t)nr[b] * nc[b];
+    ncsum += (double)nr[b] * nc[b];
+    rows += nr[b];
+    in_end = std::max(in_end, in_off[b] + nc[b]);
+    out_end = std::max(out_end, out_off[b] + nr[b]);
+  }
+  std::vector<int32_t> hin, hout;
+  AMGDD_TRY(download(hin, in_ext, (size_t)in_end, s));
+  AMGDD_TRY(download(hout, out_ext, (size_t)out_end, s));
+  const int64_t tgt = std::max<int64_t>(256, std::min<int64_t>(kItemElems, total / (152 * 16)));
+  std::vector<ItemDesc> items;
+  std::vector<int32_t> tabs, gidx, gout;
+  int max_in = 0, max_m = 0, max_rows = 0;
+  // one item over blocks [b0, b0 + cnt) (cnt == 1: rows [r0, r1) of b0)
+  auto emit = [&](int b0, int cnt, int r0, int r1) {
+    ItemDesc d{};
+    d.nb = cnt;
+    d.tab = (int)tabs.size();
+    d.xin = (int)gidx.size();
+    d.out = (int)gout.size();
+    std::vector<int32_t> rp(cnt + 1, 0), mp(cnt + 1, 0), ip(cnt + 1, 0), ncs(cnt);
+    for (int j = 0; j < cnt; ++j) {
+      const int b = b0 + j;
+      const int rs = cnt == 1 ? r0 : 0, re = cnt == 1 ? r1 : nr[b];
+      rp[j + 1] = rp[j] + (re - rs);
+      mp[j + 1] = mp[j] + (re - rs) * nc[b];
+      ip[j + 1] = ip[j] + nc[b];
+      ncs[j] = nc[b];
+      gidx.insert(gidx.end(), hin.begin() + in_off[b], hin.begin() + in_off[b] + nc[b]);
+      gout.insert(gout.end(), hout.begin() + out_off[b] + rs, hout.begin() + out_off[b] + re);
+    }
+    tabs.insert(tabs.end(), rp.begin(), rp.end());
+    tabs.insert(tabs.end(), mp.begin(), mp.end());
+    tabs.insert(tabs.end(), ip.begin(), ip.end());
+    tabs.insert(tabs.end(), ncs.begin(), ncs.end());
+    d.m_start = m_off[b0] + (int64_t)(cnt == 1 ? r0 : 0) * nc[b0];
+    d.m_len = mp[cnt];
+    d.nin = ip[cnt];
+    d.nrows = rp[cnt];
+    items.push_back(d);
+    max_in = std::max(max_in, d.nin);
+    max_m = std::max(max_m, d.m_len + 8);
+    max_rows = std::max(max_rows, d.nrows);
+  };
+  int cb0 = 0, cnb = 0;
+  int64_t cm = 0, cin = 0, crows = 0;
+  auto flush = [&]() {
+    if (cnb > 0) emit(cb0, cnb, 0, cnb == 1 ? nr[cb0] : 0);
+    cnb = 0;
+    cm = cin = crows = 0;
+  };
+  for (int b = 0; b < nb; ++b) {
+    const int64_t mb = (int64_t)nr[b] * nc[b];
+    if (mb > tgt || nr[b] > kItemMaxRows) {
+      flush();
+      const int per = (int)std::min<int64_t>(kItemMaxRows, std::max<int64_t>(1, tgt / std::max(nc[b], 1)));
+      for (int r = 0; r < nr[b]; r += per) emit(b, 1, r, std::min(nr[b], r + per));
+      continue;
+    }
+    const bool contiguous = cnb > 0 && m_off[b] == m_off[b - 1] + (int64_t)nr[b - 1] * nc[b - 1];
+    if (cnb > 0 && (!contiguous || cm + mb > tgt || cin + nc[b] > kItemMaxIn || crows + nr[b] > kItemMaxRows ||
+                    cnb == kItemMaxBlocks))
+      flush();
+    if (cnb == 0) cb0 = b;
+    ++cnb;
+    cm += mb;
+    cin += nc[b];
+    crows += nr[b];
+  }
+  flush();
+  if (gidx.size() >= ((size_t)1 << 31) || gout.size() >= ((size_t)1 << 31) || tabs.size() >= ((size_t)1 << 31))
+    return AMGDD_OK;
+  // lanes per row from the mean row length in 16-byte vectors of FP32
+  const double nvec = (rows > 0 ? ncsum / rows : 0.0) / 4.0;
+  p.item_lanes = nvec >= 48 ? 32 : (nvec >= 16 ? 16 : (nvec >= 6 ? 8 : 4));
+  p.item_max_in = max_in;
+  p.item_max_m = max_m;
+  p.item_max_rows = max_rows;
+  p.nitems = (int)items.size();
+  AMGDD_TRY(p.items.upload(items, s));
+  AMGDD_TRY(p.tabs.upload(tabs, s));
+  AMGDD_TRY(p.gidx.upload(gidx, s));
+  AMGDD_TRY(p.gout.upload(gout, s));
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  p.staged = true;
+  return AMGDD_OK;
+}
+
 // force: 0 picks the mode from the row length, 1 lanes-per-row chunks,
 // 2 row per lane (the caller then passes the transposed copy).
 int build_seg(SegPlan& p, const std::vector<int32_t>& nr, const std::vector<int32_t>& nc,
@@ -189,7 +300,7 @@ int build_seg(SegPlan& p, const std::vector<int32_t>& nr, const std::vector<int3
   AMGDD_TRY(p.out_off.upload(out_off, s));
   AMGDD_TRY(p.chunk_blk.upload(cb, s));
   AMGDD_TRY(p.chunk_row0.upload(cr, s));
-  return AMGDD_OK;
+  return build_items(p, nr, nc, m_off, in_off, out_off, in_ext, out_ext, s);
 }
 
 int apply_kind(int sz) {
@@ -372,6 +483,62 @@ int build_blockrows(Level& L, cudaStream_t s) {
   return AMGDD_OK;
 }
 
+// Setup-time choice between the staged and unstaged gather-GEMV kernels for
+// one plan: time both on scratch vectors (`nin` inputs, `nout` outputs) and
+// keep the faster.  The staged form's arrays are freed when it loses.
+template <class T>
+int tune_seg(SegPlan& p, const T* M, const T* MT, int64_t nin, int64_t nout, SegMode mode, cudaStream_t s) {
+  if (!p.staged || g_err_word == nullptr || M == nullptr) return AMGDD_OK;
+  DBuf<T> xin, yout, cin;
+  AMGDD_TRY(xin.alloc(std::max<int64_t>(nin, 1)));
+  AMGDD_TRY(yout.alloc(std::max<int64_t>(nout, 1)));
+  AMGDD_TRY(cin.alloc(std::max<int64_t>(nout, 1)));
+  AMGDD_TRY(xin.zero(s));
+  AMGDD_TRY(yout.zero(s));
+  AMGDD_TRY(cin.zero(s));
+  const bool f32 = sizeof(T) == 4;
+  cudaEvent_t e[2];
+  for (auto& v : e) AMGDD_CUDA(cudaEventCreate(&v));
+  float t[2] = {0.f, 0.f};
+  constexpr int kReps = 8;
+  int rc = AMGDD_OK;
+  for (int form = 0; form < 2 && rc == AMGDD_OK; ++form) {
+    p.staged = form == 0;
+    for (int rep = 0; rep < kReps + 2 && rc == AMGDD_OK; ++rep) {
+      if (rep == 2) cudaEventRecord(e[0], s);
+      rc = launch_seg(p, M, f32, xin.p, yout.p, f32, mode, nullptr, s, mode == SEG_RESID ? cin.p : nullptr, nullptr,
+                      MT);
+    }
+    cudaEventRecord(e[1], s);
+    if (cudaEventSynchronize(e[1]) != cudaSuccess || cudaEventElapsedTime(&t[form], e[0], e[1]) != cudaSuccess)
+      rc = AMGDD_ERR_CUDA;
+  }
+  for (auto& v : e) cudaEventDestroy(v);
+  AMGDD_TRY(rc);
+  p.staged = t[0] < t[1];
+  if (g_timer.on)
+    fprintf(stderr, "[amgdd]   plan %d blocks: staged %.1f us, unstaged %.1f us -> %s\n", p.nblocks, 1e3 * t[0] / kReps,
+            1e3 * t[1] / kReps, p.staged ? "staged" : "unstaged");
+  if (!p.staged) {
+    p.items.release();
+    p.tabs.release();
+    p.gidx.release();
+    p.gout.release();
+  }
+  return AMGDD_OK;
+}
+
+// Staged/unstaged choice for every gather-GEMV plan of a level.
+int tune_level_plans(Level& L, int64_t n_next, cudaStream_t s) {
+  if (L.coarsest) return tune_seg<double>(L.ras, L.W64.p, L.Wt64.p, L.n, L.n, SEG_STORE, s);
+  AMGDD_TRY(tune_seg<float>(L.ras, L.W32.p, L.Wt32.p, L.n, L.n, SEG_STORE, s));
+  AMGDD_TRY(tune_seg<float>(L.rast, L.Wt32.p, L.W32.p, L.n, L.n, SEG_ATOMIC_ADD, s));
+  AMGDD_TRY(tune_seg<float>(L.restr, L.Zt32.p, L.Z32.p, L.n, n_next, SEG_STORE, s));
+  AMGDD_TRY(tune_seg<float>(L.prol, L.Z32.p, L.Zt32.p, n_next, L.n, SEG_ADD, s));
+  if (L.A32.p) AMGDD_TRY(tune_seg<float>(L.ablk, L.A32.p, L.At32.p, L.n, L.n, SEG_RESID, s));
+  return AMGDD_OK;
+}
+
 // Setup-time tuning of the coarse A-apply: time one FP32 residual of level L
 // in both stored forms and keep the faster.  Block rows move more bytes than
 // the compressed row groups but need no atomics and stream dense rows.
@@ -434,6 +601,15 @@ struct amgdd_hierarchy {
   cudaStream_t work = nullptr;  // solves run here (capturable, unlike the legacy stream)
   cudaEvent_t join[2] = {nullptr, nullptr};
   double setup_ms = 0.0;
+  // persistent V-cycle tail per precision (index 1 = MIXED32): phase list,
+  // launch shape, first level (0 = not used); barrier words
+  DBuf<PhaseDesc> d_ph[2];
+  int nph[2] = {0, 0};
+  size_t ph_smem[2] = {0, 0};
+  int ph_grid[2] = {0, 0};
+  int persist_from[2] = {0, 0};
+  double persist_us[2][16] = {};  // setup-time V-cycle timings by first level (0 = all separate launches)
+  DBuf<unsigned> bar;
   ~amgdd_hierarchy() {
     for (int i = 0; i < 2; ++i) {
       if (ginit[i]) cudaGraphExecDestroy(ginit[i]);
@@ -986,6 +1162,13 @@ struct VProf {
 static int vcycle(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, const int* skip, cudaStream_t s,
                   VProf* prof = nullptr) {
   Level& L = *h.lv[l];
+  const int pi = f32 ? 1 : 0;
+  if (l > 0 && h.persist_from[pi] == l && r == (f32 ? (const void*)L.r32.p : (const void*)L.r64.p) &&
+      x == (f32 ? (void*)L.x32.p : (void*)L.x64.p)) {
+    AMGDD_MARK(6);
+    return launch_persistent(h.d_ph[pi].p, h.nph[pi], h.ph_smem[pi], h.ph_grid[pi], h.bar.p, &h.st.p->vc_err, skip,
+                             s);
+  }
   if (L.coarsest) {
     if (f32) {
       AMGDD_MARK(1);
@@ -1027,6 +1210,132 @@ static int vcycle(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, c
   AMGDD_TRY(level_residual(L, f32, x, r, sv, skip, s));
   AMGDD_MARK(7);
   AMGDD_TRY(launch_seg(L.rast, Wt, f32, sv, x, f32, SEG_ATOMIC_ADD, skip, s, nullptr, nullptr, W));
+  return AMGDD_OK;
+}
+
+// Phases of the V-cycle from level `from` >= 1 to the coarsest and back, in
+// the order the separate launches of `vcycle` take (Section 3.1).  Needs A by
+// block rows on every non-coarsest level of the tail; returns false if not.
+static bool tail_phases(amgdd_hierarchy& h, int from, bool f32, std::vector<PhaseDesc>& ph) {
+  const int nl = (int)h.lv.size();
+  ph.clear();
+  for (int l = from; l < nl; ++l)
+    if (!h.lv[l]->coarsest && !h.lv[l]->has_blk) return false;
+  for (int l = from; l < nl; ++l) {
+    Level& L = *h.lv[l];
+    if (L.coarsest) {
+      if (f32) {
+        ph.push_back(cast_phase(L.r32.p, true, L.r64.p, false, L.n));
+        ph.push_back(seg_phase(L.ras, L.W64.p, L.Wt64.p, false, L.r64.p, L.x64.p, SEG_STORE));
+        ph.push_back(cast_phase(L.x64.p, false, L.x32.p, true, L.n));
+      } else {
+        ph.push_back(seg_phase(L.ras, L.W64.p, L.Wt64.p, false, L.r64.p, L.x64.p, SEG_STORE));
+      }
+      break;
+    }
+    Level& N = *h.lv[l + 1];
+    const void* r = f32 ? (const void*)L.r32.p : (const void*)L.r64.p;
+    void* x = f32 ? (void*)L.x32.p : (void*)L.x64.p;
+    void* sv = f32 ? (void*)L.s32.p : (void*)L.s64.p;
+    void* rn = f32 ? (void*)N.r32.p : (void*)N.r64.p;
+    ph.push_back(seg_phase(L.ras, f32 ? (const void*)L.W32.p : (const void*)L.W64.p,
+                           f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p, f32, r, x, SEG_STORE));
+    ph.push_back(seg_phase(L.ablk, f32 ? (const void*)L.A32.p : (const void*)L.A64.p,
+                           f32 ? (const void*)L.At32.p : (const void*)L.At64.p, f32, x, sv, SEG_RESID, r));
+    ph.push_back(seg_phase(L.restr, f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p,
+                           f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p, f32, sv, rn, SEG_STORE));
+  }
+  for (int l = nl - 2; l >= from; --l) {
+    Level& L = *h.lv[l];
+    Level& N = *h.lv[l + 1];
+    const void* r = f32 ? (const void*)L.r32.p : (const void*)L.r64.p;
+    void* x = f32 ? (void*)L.x32.p : (void*)L.x64.p;
+    void* sv = f32 ? (void*)L.s32.p : (void*)L.s64.p;
+    const void* xn = f32 ? (const void*)N.x32.p : (const void*)N.x64.p;
+    ph.push_back(seg_phase(L.prol, f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p,
+                           f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p, f32, xn, x, SEG_ADD));
+    ph.push_back(seg_phase(L.ablk, f32 ? (const void*)L.A32.p : (const void*)L.A64.p,
+                           f32 ? (const void*)L.At32.p : (const void*)L.At64.p, f32, x, sv, SEG_RESID, r));
+    ph.push_back(seg_phase(L.rast, f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p,
+                           f32 ? (const void*)L.W32.p : (const void*)L.W64.p, f32, sv, x, SEG_ATOMIC_ADD));
+  }
+  return true;
+}
+
+static int set_tail(amgdd_hierarchy& h, int pi, int from) {
+  h.persist_from[pi] = 0;
+  h.nph[pi] = 0;
+  if (from <= 0) return AMGDD_OK;
+  std::vector<PhaseDesc> ph;
+  if (!tail_phases(h, from, pi == 1, ph)) return AMGDD_OK;
+  size_t smem = 0;
+  for (const auto& d : ph) smem = std::max(smem, phase_smem(d));
+  AMGDD_TRY(persistent_grid(smem, &h.ph_grid[pi]));
+  AMGDD_TRY(h.d_ph[pi].upload(ph, h.work));
+  AMGDD_CUDA(cudaStreamSynchronize(h.work));
+  h.nph[pi] = (int)ph.size();
+  h.ph_smem[pi] = smem;
+  h.persist_from[pi] = from;
+  return AMGDD_OK;
+}
+
+// Setup-time choice of the persistent tail: time V-cycles with the tail
+// starting at each level (and with none) and keep the fastest, per precision.
+static int tune_tail(amgdd_hierarchy& h) {
+  cudaStream_t s = h.work;
+  const int nl = (int)h.lv.size();
+  AMGDD_TRY(h.bar.alloc(2));
+  AMGDD_TRY(h.bar.zero(s));
+  AMGDD_TRY(h.st.zero(s));
+  Level& L0 = *h.lv[0];
+  AMGDD_TRY(L0.r32.zero(s));
+  AMGDD_TRY(h.r.zero(s));
+  cudaEvent_t e0, e1;
+  AMGDD_CUDA(cudaEventCreate(&e0));
+  AMGDD_CUDA(cudaEventCreate(&e1));
+  int rc = AMGDD_OK;
+  for (int pi = 0; pi < 2 && rc == AMGDD_OK; ++pi) {
+    const bool f32 = pi == 1;
+    const void* r = f32 ? (const void*)L0.r32.p : (const void*)h.r.p;
+    void* x = f32 ? (void*)L0.x32.p : (void*)h.z.p;
+    int best = 0;
+    double best_us = 0.0;
+    for (int from = 0; from < std::min(nl, 16) && rc == AMGDD_OK; ++from) {
+      if ((rc = set_tail(h, pi, from)) != AMGDD_OK) break;
+      if (from > 0 && h.persist_from[pi] != from) continue;  // tail not expressible from this level
+      constexpr int kWarm = 3, kReps = 10;
+      for (int k = 0; k < kWarm + kReps && rc == AMGDD_OK; ++k) {
+        if (k == kWarm) cudaEventRecord(e0, s);
+        rc = vcycle(h, 0, f32, r, x, nullptr, s);
+      }
+      if (rc != AMGDD_OK) break;
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = AMGDD_ERR_CUDA;
+        break;
+      }
+      const double us = 1e3 * ms / kReps;
+      h.persist_us[pi][from] = us;
+      if (from == 0 || us < best_us) {
+        best = from;
+        best_us = us;
+      }
+    }
+    if (rc == AMGDD_OK) rc = set_tail(h, pi, best);
+    if (g_timer.on && rc == AMGDD_OK)
+      fprintf(stderr, "[amgdd] %s V-cycle: persistent tail from level %d (%.1f us)\n", f32 ? "mixed" : "fp64", best,
+              best_us);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  AMGDD_TRY(rc);
+  PcgState st{};
+  AMGDD_CUDA(cudaMemcpy(&st, h.st.p, sizeof st, cudaMemcpyDeviceToHost));
+  if (st.vc_err != 0) {
+    set_error("persistent V-cycle: grid barrier timed out during setup");
+    return AMGDD_ERR_TIMEOUT;
+  }
   return AMGDD_OK;
 }
 
@@ -1087,7 +1396,12 @@ static int pcg_start(amgdd_hierarchy& h, cudaStream_t s) {
 // Graphs of one precision: the CG start, and a WHILE node whose body is one
 // CG iteration; the iteration's scalar kernel sets the loop condition on the
 // device, so a whole solve runs without returning to the host.
-static int build_solve_graphs(amgdd_hierarchy& h, int pi, cudaStream_t s) {
+static int build_solve_graphs_once(amgdd_hierarchy& h, int pi, cudaStream_t s) {
+  for (auto* ge : {&h.ginit[pi], &h.gloop[pi]})
+    if (*ge) {
+      cudaGraphExecDestroy(*ge);
+      *ge = nullptr;
+    }
   cudaGraph_t g;
   AMGDD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   capture_begin();
@@ -1121,6 +1435,17 @@ static int build_solve_graphs(amgdd_hierarchy& h, int pi, cudaStream_t s) {
   AMGDD_CUDA(cudaGraphInstantiate(&h.gloop[pi], lg, 0));
   cudaGraphDestroy(lg);
   return AMGDD_OK;
+}
+
+// CUDA graphs of the solve.  If the persistent V-cycle tail cannot be
+// captured (a cooperative launch inside the conditional loop body), the tail
+// is dropped for this precision and the graphs are captured again.
+static int build_solve_graphs(amgdd_hierarchy& h, int pi, cudaStream_t s) {
+  int rc = build_solve_graphs_once(h, pi, s);
+  if (rc == AMGDD_OK || h.persist_from[pi] == 0) return rc;
+  (void)cudaGetLastError();
+  AMGDD_TRY(set_tail(h, pi, 0));
+  return build_solve_graphs_once(h, pi, s);
 }
 
 static int solve_one(amgdd_hierarchy& h, const double* bsrc, bool bdev, double tol, double* xdst, bool xdev,
@@ -1165,6 +1490,12 @@ static int solve_one(amgdd_hierarchy& h, const double* bsrc, bool bdev, double t
   AMGDD_CUDA(cudaEventRecord(e1, s));
   AMGDD_TRY(download(part, h.partials.p, 2 * kDotBlocks, s));
   const PcgState fin = *h.st_host;
+  if (fin.vc_err != 0) {
+    AMGDD_TRY(h.bar.zero(s));
+    AMGDD_CUDA(cudaStreamSynchronize(s));
+    set_error("persistent V-cycle: grid barrier timed out");
+    return AMGDD_ERR_TIMEOUT;
+  }
   if (h.prm.use_graph) count_graph_launch(h.gloop_kernels[pi] * std::max(fin.iters, 1));
   double qq = 0.0;
   for (int i = 0; i < kDotBlocks; ++i) qq += part[2 * i];
@@ -1183,6 +1514,20 @@ static int solve_one(amgdd_hierarchy& h, const double* bsrc, bool bdev, double t
 }
 
 // ---------------------------------------------------------------------------
+// After a call that launched kernels on `s`: report (and clear) an expired
+// bounded wait recorded in the hierarchy's error word.
+static int take_err_word(amgdd_hierarchy& h, cudaStream_t s) {
+  int v = 0;
+  AMGDD_CUDA(cudaMemcpyAsync(&v, &h.st.p->vc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  if (v == 0) return AMGDD_OK;
+  AMGDD_CUDA(cudaMemsetAsync(&h.st.p->vc_err, 0, sizeof(int), s));
+  if (h.bar.p) AMGDD_TRY(h.bar.zero(s));
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  set_error("a bounded device-side wait expired (staged copy or grid barrier)");
+  return AMGDD_ERR_TIMEOUT;
+}
+
 extern "C" {
 
 amgdd_params amgdd_params_default(void) {
@@ -1291,6 +1636,9 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   H->n = n;
   H->precision = prm.precision;
   AMGDD_CUDA(cudaGetDevice(&H->device));
+  AMGDD_TRY(H->st.alloc(1));
+  AMGDD_TRY(H->st.zero(s));
+  ErrScope err_scope(&H->st.p->vc_err);
   // ---- level 0 row groups: consecutive rows with identical supports ----
   std::unique_ptr<Level> L0(new Level());
   L0->n = n;
@@ -1364,6 +1712,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     if (coarsest) {
       Phase ph(8, "coarsest", s);
       AMGDD_TRY(build_coarsest(*H, L, s));
+      AMGDD_TRY(tune_level_plans(L, 0, s));
       break;
     }
     AMGDD_TRY(build_level(*H, L, lvl, lvl == 0 ? aggh.data() : nullptr, s));
@@ -1371,7 +1720,11 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     if (lvl > 0) {
       Phase ph(9, "block rows", s);
       AMGDD_TRY(build_blockrows(L, s));
-      AMGDD_TRY(tune_level_A(L, s));
+    }
+    {
+      Phase ph(10, "tune", s);
+      AMGDD_TRY(tune_level_plans(L, L.col0.back(), s));
+      if (lvl > 0) AMGDD_TRY(tune_level_A(L, s));
     }
     std::unique_ptr<Level> N(new Level());
     {
@@ -1403,12 +1756,12 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   AMGDD_TRY(H->q.alloc(n));
   AMGDD_TRY(H->b.alloc(n));
   AMGDD_TRY(H->partials.alloc(2 * kDotBlocks));
-  AMGDD_TRY(H->st.alloc(1));
   AMGDD_CUDA(cudaMallocHost((void**)&H->st_host, sizeof(PcgState)));
   AMGDD_CUDA(cudaStreamCreateWithFlags(&H->work, cudaStreamNonBlocking));
   AMGDD_CUDA(cudaEventCreateWithFlags(&H->join[0], cudaEventDisableTiming));
   AMGDD_CUDA(cudaEventCreateWithFlags(&H->join[1], cudaEventDisableTiming));
   AMGDD_CUDA(cudaStreamSynchronize(s));
+  AMGDD_TRY(tune_tail(*H));
   H->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = H.release();
   return AMGDD_OK;
@@ -1434,6 +1787,7 @@ int amgdd_solve(amgdd_hierarchy* h, const double* b, int nrhs, double tol, doubl
     return AMGDD_ERR_INVALID_ARG;
   }
   try {
+    ErrScope err_scope(&h->st.p->vc_err);
     cudaStream_t us = (cudaStream_t)stream;
     cudaStream_t s = h->work;
     AMGDD_CUDA(cudaEventRecord(h->join[0], us));
@@ -1472,6 +1826,7 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
     set_error("amgdd_apply: invalid argument");
     return AMGDD_ERR_INVALID_ARG;
   }
+  ErrScope err_scope(&h->st.p->vc_err);
   cudaStream_t s = (cudaStream_t)stream;
   Level& L = *h->lv[level];
   const bool f32 = h->precision == AMGDD_MIXED32;
@@ -1482,7 +1837,7 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
       return AMGDD_ERR_INVALID_ARG;
     }
     AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, x, y, false, SEG_STORE, nullptr, s, nullptr, nullptr, L.Wt64.p));
-    return AMGDD_OK;
+    return take_err_word(*h, s);
   }
   if (L.coarsest && op != AMGDD_OP_A) {
     set_error("amgdd_apply: operator not defined on the coarsest level");
@@ -1537,8 +1892,7 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
       return AMGDD_ERR_INVALID_ARG;
   }
   if (f32) AMGDD_TRY(launch_cast(yout32.p, true, y, false, nout, nullptr, s));
-  AMGDD_CUDA(cudaStreamSynchronize(s));
-  return AMGDD_OK;
+  return take_err_word(*h, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1581,6 +1935,7 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
     set_error("amgdd_apply_noalloc: invalid argument");
     return AMGDD_ERR_INVALID_ARG;
   }
+  ErrScope err_scope(&h->st.p->vc_err);
   cudaStream_t s = (cudaStream_t)stream;
   Level& L = *h->lv[level];
   const bool f32 = h->precision == AMGDD_MIXED32;
@@ -1591,8 +1946,7 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
       return AMGDD_ERR_INVALID_ARG;
     }
     AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, x, y, false, SEG_STORE, nullptr, s, nullptr, nullptr, L.Wt64.p));
-    AMGDD_CUDA(cudaStreamSynchronize(s));
-    return AMGDD_OK;
+    return take_err_word(*h, s);
   }
   if (L.coarsest && op != AMGDD_OP_A) {
     set_error("amgdd_apply_noalloc: operator not defined on the coarsest level");
@@ -1655,8 +2009,7 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
       return AMGDD_ERR_INVALID_ARG;
   }
   if (f32) AMGDD_TRY(launch_cast(yout, true, y, false, nout, nullptr, s));
-  AMGDD_CUDA(cudaStreamSynchronize(s));
-  return AMGDD_OK;
+  return take_err_word(*h, s);
 }
 
 int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes, int cap) {
@@ -1665,6 +2018,7 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes
     set_error("amgdd_profile_vcycle: invalid argument (cap must be >= levels * %d)", VProf::kSlots);
     return AMGDD_ERR_INVALID_ARG;
   }
+  ErrScope err_scope(&h->st.p->vc_err);
   const int nl = (int)h->lv.size();
   for (int i = 0; i < nl * VProf::kSlots; ++i) ms[i] = bytes[i] = 0.0;
   cudaStream_t s = h->work;
@@ -1705,8 +2059,17 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes
       b[7] = seg_bytes(L.rast, L.n, L.n, true, esz);
     }
   }
+  const int pf = h->persist_from[f32 ? 1 : 0];
+  if (pf > 0) {
+    double tail = 0.0;
+    for (int i = pf * VProf::kSlots; i < nl * VProf::kSlots; ++i) {
+      tail += bytes[i];
+      bytes[i] = 0.0;
+    }
+    bytes[pf * VProf::kSlots + 6] = tail;
+  }
   for (int i = 0; i < nl * VProf::kSlots; ++i) ms[i] = acc[i] / reps;
-  return AMGDD_OK;
+  return take_err_word(*h, s);
 }
 
 int64_t amgdd_kernel_launches(void) { return g_kernels.load(); }
@@ -1846,9 +2209,21 @@ int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap) {
                   l ? ", " : "", L.coarsest ? "none" : (L.has_blk ? "block rows" : "matrix-free"), L.blk_us, L.mf_us);
     s += buf;
   }
+  s += "], \"tail\": {";
+  for (int pi = 0; pi < 2; ++pi) {
+    s += std::string(pi ? ", " : "") + (pi ? "\"mixed\"" : "\"fp64\"") + ": {\"from\": " +
+         std::to_string(h->persist_from[pi]) + ", \"vcycle_us_by_from\": [";
+    for (size_t l = 0; l < std::min<size_t>(h->lv.size(), 16); ++l) {
+      char buf[32];
+      std::snprintf(buf, sizeof buf, "%s%.1f", l ? ", " : "", h->persist_us[pi][l]);
+      s += buf;
+    }
+    s += "]}";
+  }
+  s += "}";
   double vb = 0, ab = 0;
   amgdd_bytes_model(h, &vb, &ab);
-  s += "], \"vcycle_bytes\": " + std::to_string(vb) + ", \"apply64_bytes\": " + std::to_string(ab);
+  s += ", \"vcycle_bytes\": " + std::to_string(vb) + ", \"apply64_bytes\": " + std::to_string(ab);
   s += ", \"setup_ms\": " + std::to_string(h->setup_ms) + "}";
   if (s.size() + 1 > cap) return AMGDD_ERR_INVALID_ARG;
   std::memcpy(json, s.c_str(), s.size() + 1);

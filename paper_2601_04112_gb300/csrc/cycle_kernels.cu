@@ -15,6 +15,9 @@
 // iterations is a no-op after convergence.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
 #include <cstdint>
 
 #include "internal.h"
@@ -180,6 +183,187 @@ __global__ void __launch_bounds__(128) k_seg_rows(const int32_t* __restrict__ ta
   else
     *dst = csrc[o] - acc;
   if (MODE != SEG_RESID && cdst != nullptr) cdst[o] = csrc[o];
+}
+
+// ---------------------------------------------------------------------------
+// Staged gather-GEMV-scatter.  One item (a contiguous range of the stored
+// matrix: consecutive whole blocks, or a row slice of one block) is moved to
+// shared memory by a single bulk copy completing on an mbarrier, while the
+// CTA gathers the item's inputs x(in_idx) with independent loads; rows are
+// then computed from shared memory by groups of L lanes.
+
+constexpr long long kWaitCycles = 2000000000LL;  // about 1 s at 2 GHz
+constexpr int kItemThreads = 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// one bulk copy global -> shared of `bytes` (16-byte aligned addresses and
+// size), completing the current phase of `bar`
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// bounded wait for phase `parity` of `bar`, backing off between polls so
+// that a waiting warp takes few issue slots; false on timeout.  One thread
+// waits and the CTA then meets at a barrier, which orders the copied data
+// before every thread's reads.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const long long t0 = clock64();
+  unsigned ns = 32;
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+    __nanosleep(ns);
+    ns = ns < 256 ? 2 * ns : 256;
+  }
+}
+
+// Shared memory of the staged kernels: mbarrier (16 bytes), tables (132
+// ints), gathered inputs xs, per-row operand values cs (residual source or
+// previous output) and cc (copied source), output indices os, then the
+// staged matrix.
+constexpr int kTabInts = 132;
+__host__ __device__ constexpr size_t a16(size_t b) { return (b + 15) / 16 * 16; }
+__host__ __device__ constexpr size_t staged_bytes(int max_in, int max_rows, int max_m, size_t esz) {
+  return 16 + (size_t)kTabInts * 4 + a16((size_t)max_in * esz) + 2 * a16((size_t)max_rows * esz) +
+         a16((size_t)max_rows * 4) + a16((size_t)max_m * esz);
+}
+
+// Processes item `it` of a staged phase.  `use` counts completed phases of
+// `bar`.  Returns false after an expired wait (err set, copy waited for).
+template <class T, int L>
+__device__ bool item_run(const PhaseDesc& P, int it, unsigned char* smem, uint64_t* bar, unsigned& use, int* err) {
+  constexpr int V = 16 / sizeof(T);
+  using VT = typename Vec2<T>::type;
+  int* tab = reinterpret_cast<int*>(smem + 16);
+  T* xs = reinterpret_cast<T*>(smem + 16 + kTabInts * 4);
+  T* cs = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(xs) + a16((size_t)P.max_in * sizeof(T)));
+  T* cc = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(cs) + a16((size_t)P.max_rows * sizeof(T)));
+  int* os = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(cc) + a16((size_t)P.max_rows * sizeof(T)));
+  T* Ms = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(os) + a16((size_t)P.max_rows * 4));
+  const ItemDesc d = P.items[it];
+  const int64_t a0 = d.m_start & ~(int64_t)(V - 1);
+  const int64_t a1 = (d.m_start + d.m_len + V - 1) & ~(int64_t)(V - 1);
+  const int delta = (int)(d.m_start - a0);
+  if (threadIdx.x == 0) bulk_load(Ms, (const T*)P.M + a0, (unsigned)((a1 - a0) * sizeof(T)), bar);
+  const int ntab = 4 * d.nb + 3;
+  for (int t = threadIdx.x; t < ntab; t += kItemThreads) tab[t] = P.tabs[d.tab + t];
+  // inputs and per-row operands: all index loads, then all value loads
+  {
+    const T* x = (const T*)P.x;
+    const bool need_c = P.mode == SEG_RESID || P.mode == SEG_ADD;
+    const T* csrc = P.mode == SEG_ADD ? (const T*)P.y : (const T*)P.csrc;
+    constexpr int U = 8;
+    for (int base = 0; base < d.nin || base < d.nrows; base += U * kItemThreads) {
+      int ix[U], io[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = base + u * kItemThreads + (int)threadIdx.x;
+        ix[u] = c < d.nin ? P.gidx[d.xin + c] : -1;
+        io[u] = c < d.nrows ? P.gout[d.out + c] : -1;
+      }
+      T xv[U], cv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        xv[u] = ix[u] >= 0 ? __ldcg(x + ix[u]) : T(0);
+        cv[u] = (need_c && io[u] >= 0) ? __ldcg(csrc + io[u]) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = base + u * kItemThreads + (int)threadIdx.x;
+        if (c < d.nin) xs[c] = xv[u];
+        if (c < d.nrows) {
+          os[c] = io[u];
+          cs[c] = cv[u];
+        }
+      }
+    }
+    // the fused copy cdst = csrc (level-0 residual source) is rare: own loop
+    if (P.cdst != nullptr && P.mode != SEG_RESID) {
+      __syncthreads();
+      for (int c = threadIdx.x; c < d.nrows; c += kItemThreads) cc[c] = __ldcg((const T*)P.csrc + os[c]);
+    }
+  }
+  const bool ok = threadIdx.x != 0 || mbar_wait(bar, use & 1u);
+  ++use;
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, 2);
+      (void)mbar_wait(bar, (use - 1) & 1u);
+    }
+    return false;
+  }
+  // rows: group g of L lanes takes rows g, g + ngrp, ...
+  const int nb = d.nb;
+  const int* rp = tab;
+  const int* mp = tab + nb + 1;
+  const int* ip = mp + nb + 1;
+  const int* ncs = ip + nb + 1;
+  const int lane = (int)threadIdx.x % L;
+  constexpr int ngrp = kItemThreads / L;
+  const unsigned mask = group_mask<L>();
+  T* y = (T*)P.y;
+  int j = 0;
+  for (int q = (int)threadIdx.x / L; q < d.nrows; q += ngrp) {
+    while (rp[j + 1] <= q) ++j;
+    const int rl = q - rp[j];
+    const int ncb = ncs[j];
+    const int moff = delta + mp[j] + rl * ncb;
+    const T* row = Ms + moff;
+    const T* xb = xs + ip[j];
+    T acc = T(0);
+    if (((moff | ip[j] | ncb) & (V - 1)) == 0) {
+      const VT* rv = reinterpret_cast<const VT*>(row);
+      const VT* xv = reinterpret_cast<const VT*>(xb);
+      const int nv = ncb / V;
+      for (int c = lane; c < nv; c += L) acc += vdot(rv[c], xv[c]);
+    } else {
+      for (int c = lane; c < ncb; c += L) acc += row[c] * xb[c];
+    }
+    acc = group_sum<L>(acc, mask);
+    if (lane == 0) {
+      const int o = os[q];
+      switch (P.mode) {
+        case SEG_STORE: y[o] = acc; break;
+        case SEG_ADD: y[o] = cs[q] + acc; break;
+        case SEG_ATOMIC_ADD: atomicAdd(y + o, acc); break;
+        case SEG_ATOMIC_SUB: atomicAdd(y + o, -acc); break;
+        default: y[o] = cs[q] - acc; break;
+      }
+      if (P.cdst != nullptr && P.mode != SEG_RESID) ((T*)P.cdst)[o] = cc[q];
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+template <class T, int L>
+__global__ void __launch_bounds__(kItemThreads) k_seg_staged(const __grid_constant__ PhaseDesc P, const int* skip,
+                                                             int* err) {
+  if (skip != nullptr && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  if (threadIdx.x == 0) mbar_init(bar);
+  __syncthreads();
+  unsigned use = 0;
+  (void)item_run<T, L>(P, blockIdx.x, smem_raw, bar, use, err);
 }
 
 template <class T, int L, int MODE>
@@ -578,6 +762,34 @@ int launch_seg(const SegPlan& p, const void* M, bool m_fp32, const void* x, void
     set_error("launch_seg: the residual mode needs the right-hand side");
     return AMGDD_ERR_INTERNAL;
   }
+  // the staged kernel streams M itself; callers that pass only the
+  // transposed copy (row-per-lane plans) keep the unstaged kernels
+  if (p.staged && g_err_word != nullptr && M != nullptr) {
+    const PhaseDesc d = seg_phase(p, M, MT, m_fp32, x, y, mode, csrc, cdst);
+    const size_t smem = phase_smem(d);
+    auto go = [&](auto kern) -> int {
+      if (smem > 48 * 1024)
+        AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<p.nitems, kItemThreads, smem, s>>>(d, skip, g_err_word);
+      AMGDD_CUDA(cudaGetLastError());
+      count_kernels(1);
+      return AMGDD_OK;
+    };
+    if (m_fp32) {
+      switch (p.item_lanes) {
+        case 4: return go(k_seg_staged<float, 4>);
+        case 8: return go(k_seg_staged<float, 8>);
+        case 16: return go(k_seg_staged<float, 16>);
+        default: return go(k_seg_staged<float, 32>);
+      }
+    }
+    switch (p.item_lanes) {
+      case 4: return go(k_seg_staged<double, 4>);
+      case 8: return go(k_seg_staged<double, 8>);
+      case 16: return go(k_seg_staged<double, 16>);
+      default: return go(k_seg_staged<double, 32>);
+    }
+  }
   if (m_fp32)
     return seg_dispatch<float>(p, (const float*)M, (const float*)MT, (const float*)x, (float*)y, mode, skip, s,
                                (const float*)csrc, (float*)cdst);
@@ -684,6 +896,315 @@ int launch_update_xr(PcgState* st, double* x, double* r, const double* p, const 
 int launch_update_p(PcgState* st, double* p, const double* z, double* zold, int64_t n, cudaStream_t s) {
   k_update_p<<<grid_for(n, 256), 256, 0, s>>>(st, p, z, zold, n);
   AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent V-cycle tail (cooperative launch).  Vectors are written by other
+// CTAs in earlier phases of the same launch, so they are read through L2
+// (__ldcg) and never through the non-coherent read-only path; matrices and
+// index arrays are read-only for the whole launch.
+namespace {
+
+constexpr long long kBarrierCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+// Grid barrier for a cooperative launch (all CTAs resident).  bar[0] counts
+// arrivals, bar[1] is the generation.  The wait is bounded: on timeout, or if
+// another CTA already reported one, it sets *err and returns, and every later
+// barrier of the launch returns at once.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    volatile int* verr = err;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (*verr != 0 || clock64() - t0 > kBarrierCycles) {
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+template <class T>
+__device__ __forceinline__ void phase_out(const PhaseDesc& P, int o, T acc) {
+  T* y = (T*)P.y;
+  switch (P.mode) {
+    case SEG_STORE: y[o] = acc; break;
+    case SEG_ADD: y[o] = __ldcg(y + o) + acc; break;
+    case SEG_ATOMIC_ADD: atomicAdd(y + o, acc); break;
+    case SEG_ATOMIC_SUB: atomicAdd(y + o, -acc); break;
+    default: y[o] = __ldcg((const T*)P.csrc + o) - acc; break;
+  }
+  if (P.mode != SEG_RESID && P.cdst != nullptr) ((T*)P.cdst)[o] = __ldcg((const T*)P.csrc + o);
+}
+
+// One chunk of an unstaged lanes-per-row plan (the body of k_seg).
+template <class T, int L, bool VEC>
+__device__ __forceinline__ void phase_chunk(const PhaseDesc& P, int chunk, T* xs) {
+  const int b = P.chunk_blk[chunk];
+  const int r0 = P.chunk_row0[chunk];
+  const int ncb = P.nc[b];
+  const int r1 = min(P.nr[b], r0 + P.rows_per_chunk);
+  const int32_t* ii = P.in_idx + P.in_off[b];
+  const T* x = (const T*)P.x;
+  for (int c = threadIdx.x; c < ncb; c += blockDim.x) xs[c] = __ldcg(x + ii[c]);
+  __syncthreads();
+  const int lane = threadIdx.x % L;
+  const int grp = threadIdx.x / L;
+  const int ngrp = blockDim.x / L;
+  const unsigned mask = group_mask<L>();
+  const T* Mb = (const T*)P.M + P.m_off[b];
+  const int32_t* oo = P.out_idx + P.out_off[b];
+  for (int r = r0 + grp; r < r1; r += ngrp) {
+    const T* row = Mb + (int64_t)r * ncb;
+    T acc = T(0);
+    if constexpr (VEC) {
+      using V = typename Vec2<T>::type;
+      constexpr int W = Vec2<T>::width;
+      const V* rv = reinterpret_cast<const V*>(row);
+      const V* xv = reinterpret_cast<const V*>(xs);
+      const int nv = ncb / W;
+      for (int c = lane; c < nv; c += L) acc += vdot(rv[c], xv[c]);
+    } else {
+      for (int c = lane; c < ncb; c += L) acc += row[c] * xs[c];
+    }
+    acc = group_sum<L>(acc, mask);
+    if (lane == 0) phase_out<T>(P, oo[r], acc);
+  }
+  __syncthreads();
+}
+
+// One task of an unstaged row-per-lane plan (the body of k_seg_rows).
+template <class T, int L>
+__device__ __forceinline__ void phase_task(const PhaseDesc& P, int t, T* xs, int lane, unsigned mask) {
+  const int b = P.task_blk[t];
+  const int r0 = P.task_row0[t];
+  const int rows = P.task_nrow[t];
+  const int ncb = P.nc[b], nrb = P.nr[b];
+  const int32_t* ii = P.in_idx + P.in_off[b];
+  const T* x = (const T*)P.x;
+  for (int c = lane; c < ncb; c += L) xs[c] = __ldcg(x + ii[c]);
+  __syncwarp(mask);
+  if (lane < rows) {
+    const int r = r0 + lane;
+    const T* col = (const T*)P.MT + P.m_off[b] + r;
+    T acc = T(0);
+    for (int c = 0; c < ncb; ++c) acc += col[(int64_t)c * nrb] * xs[c];
+    phase_out<T>(P, P.out_idx[P.out_off[b] + r], acc);
+  }
+  __syncwarp(mask);
+}
+
+template <class T, int L>
+__device__ void run_chunks(const PhaseDesc& P, unsigned char* smem) {
+  T* xs = reinterpret_cast<T*>(smem);
+  if (P.vec) {
+    for (int c = blockIdx.x; c < P.nwork; c += gridDim.x) phase_chunk<T, L, true>(P, c, xs);
+  } else {
+    for (int c = blockIdx.x; c < P.nwork; c += gridDim.x) phase_chunk<T, L, false>(P, c, xs);
+  }
+}
+
+template <class T, int L>
+__device__ void run_tasks(const PhaseDesc& P, unsigned char* smem) {
+  const int per = (int)blockDim.x / L;
+  const int grp = (int)threadIdx.x / L;
+  const int lane = (int)threadIdx.x % L;
+  const unsigned mask = group_mask<L>();
+  T* xs = reinterpret_cast<T*>(smem) + (size_t)grp * P.max_nc;
+  for (int tb = blockIdx.x; tb * per < P.nwork; tb += gridDim.x) {
+    const int t = tb * per + grp;
+    if (t < P.nwork) phase_task<T, L>(P, t, xs, lane, mask);
+  }
+}
+
+template <class T>
+__device__ void run_seg(const PhaseDesc& P, unsigned char* smem) {
+  if (P.rows_mode) {
+    switch (P.lanes) {
+      case 8: run_tasks<T, 8>(P, smem); break;
+      case 16: run_tasks<T, 16>(P, smem); break;
+      default: run_tasks<T, 32>(P, smem); break;
+    }
+  } else {
+    switch (P.lanes) {
+      case 4: run_chunks<T, 4>(P, smem); break;
+      case 8: run_chunks<T, 8>(P, smem); break;
+      case 16: run_chunks<T, 16>(P, smem); break;
+      default: run_chunks<T, 32>(P, smem); break;
+    }
+  }
+}
+
+__device__ void run_cast(const PhaseDesc& P) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.n; i += stride) {
+    const double v = P.src32 ? (double)__ldcg((const float*)P.x + i) : __ldcg((const double*)P.x + i);
+    if (P.dst32)
+      ((float*)P.y)[i] = (float)v;
+    else
+      ((double*)P.y)[i] = v;
+  }
+}
+
+template <class T, int L>
+__device__ bool run_items_l(const PhaseDesc& P, unsigned char* smem, uint64_t* bar, unsigned& use, int* err) {
+  for (int it = blockIdx.x; it < P.nwork; it += gridDim.x)
+    if (!item_run<T, L>(P, it, smem, bar, use, err)) return false;
+  return true;
+}
+
+template <class T>
+__device__ bool run_items(const PhaseDesc& P, unsigned char* smem, uint64_t* bar, unsigned& use, int* err) {
+  switch (P.lanes) {
+    case 4: return run_items_l<T, 4>(P, smem, bar, use, err);
+    case 8: return run_items_l<T, 8>(P, smem, bar, use, err);
+    case 16: return run_items_l<T, 16>(P, smem, bar, use, err);
+    default: return run_items_l<T, 32>(P, smem, bar, use, err);
+  }
+}
+
+// Every phase is a gather-GEMV (staged: CTAs loop over its items; unstaged:
+// over its chunks or row tasks) or a cast; CTAs meet at a grid barrier
+// between phases.
+__global__ void __launch_bounds__(kItemThreads, 6) k_persistent(const PhaseDesc* __restrict__ phases, int nphases,
+                                                               unsigned* bar, int* err, const int* skip) {
+  if ((skip != nullptr && *skip) || *(volatile int*)err != 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);
+  if (threadIdx.x == 0) mbar_init(mbar);
+  __syncthreads();
+  unsigned use = 0;
+  bool alive = true;
+  for (int k = 0; k < nphases; ++k) {
+    const PhaseDesc& P = phases[k];
+    if (alive) {
+      if (P.op == PH_CAST)
+        run_cast(P);
+      else if (P.items != nullptr)
+        alive = P.fp32 ? run_items<float>(P, smem_raw, mbar, use, err) : run_items<double>(P, smem_raw, mbar, use, err);
+      else if (P.fp32)
+        run_seg<float>(P, smem_raw + 16);
+      else
+        run_seg<double>(P, smem_raw + 16);
+    }
+    if (k + 1 < nphases) grid_barrier(bar, err);
+  }
+}
+
+}  // namespace
+
+PhaseDesc seg_phase(const SegPlan& p, const void* M, const void* MT, bool fp32, const void* x, void* y, SegMode mode,
+                    const void* csrc, void* cdst) {
+  PhaseDesc d;
+  d.op = PH_SEG;
+  d.fp32 = fp32 ? 1 : 0;
+  d.mode = (int)mode;
+  d.rows_mode = p.rows_mode ? 1 : 0;
+  d.lanes = p.rows_mode ? p.kind : p.lanes;
+  d.vec = p.vec ? 1 : 0;
+  d.rows_per_chunk = p.rows_per_chunk;
+  d.nwork = p.rows_mode ? p.ntasks : p.nchunks;
+  d.max_nc = p.max_nc;
+  d.chunk_blk = p.chunk_blk.p;
+  d.chunk_row0 = p.chunk_row0.p;
+  d.task_blk = p.task_blk.p;
+  d.task_row0 = p.task_row0.p;
+  d.task_nrow = p.task_nrow.p;
+  d.m_off = p.m_off.p;
+  d.in_off = p.in_off.p;
+  d.out_off = p.out_off.p;
+  d.nr = p.nr.p;
+  d.nc = p.nc.p;
+  d.in_idx = p.in_idx_ext;
+  d.out_idx = p.out_idx_ext;
+  d.M = M;
+  d.MT = MT;
+  d.x = x;
+  d.y = y;
+  d.csrc = csrc;
+  d.cdst = cdst;
+  if (p.staged && M != nullptr) {
+    d.items = p.items.p;
+    d.tabs = p.tabs.p;
+    d.gidx = p.gidx.p;
+    d.gout = p.gout.p;
+    d.nwork = p.nitems;
+    d.lanes = p.item_lanes;
+    d.rows_mode = 0;
+    d.max_in = p.item_max_in;
+    d.max_m = p.item_max_m;
+    d.max_rows = p.item_max_rows;
+  }
+  return d;
+}
+
+PhaseDesc cast_phase(const void* src, bool src32, void* dst, bool dst32, int64_t n) {
+  PhaseDesc d;
+  d.op = PH_CAST;
+  d.x = src;
+  d.y = dst;
+  d.src32 = src32 ? 1 : 0;
+  d.dst32 = dst32 ? 1 : 0;
+  d.n = n;
+  return d;
+}
+
+size_t staged_smem(int max_in, int max_rows, int max_m, size_t esz) {
+  return staged_bytes(max_in, max_rows, max_m, esz);
+}
+
+size_t phase_smem(const PhaseDesc& d) {
+  if (d.op != PH_SEG) return 16;
+  const size_t esz = d.fp32 ? sizeof(float) : sizeof(double);
+  if (d.items != nullptr) return staged_smem(d.max_in, d.max_rows, d.max_m, esz);
+  return 16 + (size_t)d.max_nc * esz * (d.rows_mode ? (size_t)(kItemThreads / d.lanes) : 1);
+}
+
+int persistent_grid(size_t smem, int* grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  AMGDD_CUDA(cudaGetDevice(&dev));
+  AMGDD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (smem > 48 * 1024)
+    AMGDD_CUDA(cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  AMGDD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent, kItemThreads, smem));
+  if (per_sm < 1) {
+    set_error("persistent V-cycle: no CTA fits with %zu bytes of shared memory", smem);
+    return AMGDD_ERR_INTERNAL;
+  }
+  *grid = sms * std::min(per_sm, 16);
+  return AMGDD_OK;
+}
+
+int launch_persistent(const PhaseDesc* d_phases, int nphases, size_t smem, int grid, unsigned* bar, int* err,
+                      const int* skip, cudaStream_t s) {
+  if (nphases == 0) return AMGDD_OK;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kItemThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  AMGDD_CUDA(cudaLaunchKernelEx(&cfg, k_persistent, d_phases, nphases, bar, err, skip));
   count_kernels(1);
   return AMGDD_OK;
 }

@@ -47,7 +47,9 @@ struct DBuf {
   int alloc(size_t count) {
     release();
     if (count == 0) return AMGDD_OK;
-    cudaError_t e = cudaMalloc((void**)&p, count * sizeof(T));
+    // 16 bytes of tail padding: staged copies round their ranges out to
+    // 16-byte boundaries and may touch up to 12 bytes past the last element
+    cudaError_t e = cudaMalloc((void**)&p, count * sizeof(T) + 16);
     if (e != cudaSuccess) {
       p = nullptr;
       set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
@@ -78,6 +80,19 @@ struct DBuf {
 // residual s = r - A x of a level whose A is stored by block rows).
 enum SegMode { SEG_STORE = 0, SEG_ADD = 1, SEG_ATOMIC_ADD = 2, SEG_ATOMIC_SUB = 3, SEG_RESID = 4 };
 
+// One item of a staged gather-GEMV plan (see SegPlan).
+struct alignas(16) ItemDesc {
+  int64_t m_start;  // first stored matrix element
+  int m_len;        // stored matrix elements
+  int nb;           // blocks (1 for a row slice)
+  int tab;          // offset of the item's tables in SegPlan::tabs
+  int nin;          // gathered inputs
+  int xin;          // offset of its input indices in SegPlan::gidx
+  int nrows;        // output rows
+  int out;          // offset of its output indices in SegPlan::gout
+  int pad;
+};
+
 struct SegPlan {
   int nblocks = 0;
   int nchunks = 0;      // CTAs: chunks of at most `rows_per_chunk` rows of one block
@@ -99,6 +114,20 @@ struct SegPlan {
   int kind = 0;
   int ntasks = 0;
   DBuf<int32_t> task_blk, task_row0, task_nrow;
+  // staged form (preferred when built): items of contiguous matrix rows,
+  // either up to 32 whole consecutive blocks or a row slice of one block,
+  // each moved to shared memory by one bulk copy; per item the host packs
+  // the block tables and flat lists of its input and output indices.
+  bool staged = false;
+  int nitems = 0;
+  int item_lanes = 8;     // lanes per row in the staged kernel
+  int item_max_in = 0;    // largest gathered input of an item (elements)
+  int item_max_m = 0;     // largest staged matrix range (elements, incl. alignment slack)
+  int item_max_rows = 0;  // most output rows of an item
+  DBuf<ItemDesc> items;
+  DBuf<int32_t> tabs;     // per item: rp[nb+1], mp[nb+1], ip[nb+1], ncs[nb]
+  DBuf<int32_t> gidx;     // per item: indices of its inputs
+  DBuf<int32_t> gout;     // per item: indices of its output rows
 };
 
 // Row groups of G_l (rows sharing one support), compressed: R_g has rank_g
@@ -179,6 +208,56 @@ int launch_apply(const ApplyPlan& p, const Level& L, bool fp32, const void* x, v
 int launch_cast(const void* src, bool src32, void* dst, bool dst32, int64_t n, const int* skip, cudaStream_t s);
 int launch_copy_vec(const void* src, void* dst, bool fp32, int64_t n, const int* skip, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Persistent V-cycle tail: the levels from some l >= 1 down to the coarsest
+// and back, as a list of phases run by one cooperative launch with a grid
+// barrier between phases (the small coarse levels are otherwise bound by
+// launch latency).  Every phase is a gather-GEMV-scatter over a SegPlan or a
+// precision cast.
+enum PhaseOp { PH_SEG = 0, PH_CAST = 1 };
+struct PhaseDesc {
+  int op = PH_SEG;
+  int fp32 = 0;  // PH_SEG: operand precision
+  int mode = 0;  // SegMode
+  int rows_mode = 0, lanes = 32, vec = 0, rows_per_chunk = 0, nwork = 0, max_nc = 0;
+  const int32_t *chunk_blk = nullptr, *chunk_row0 = nullptr;
+  const int32_t *task_blk = nullptr, *task_row0 = nullptr, *task_nrow = nullptr;
+  const int64_t *m_off = nullptr, *in_off = nullptr, *out_off = nullptr;
+  const int32_t *nr = nullptr, *nc = nullptr, *in_idx = nullptr, *out_idx = nullptr;
+  const void *M = nullptr, *MT = nullptr, *x = nullptr, *csrc = nullptr;
+  void *y = nullptr, *cdst = nullptr;
+  int src32 = 0, dst32 = 0;  // PH_CAST
+  int64_t n = 0;
+  // staged form (nwork = items)
+  const ItemDesc* items = nullptr;
+  const int32_t *tabs = nullptr, *gidx = nullptr, *gout = nullptr;
+  int max_in = 0, max_m = 0, max_rows = 0;
+};
+PhaseDesc seg_phase(const SegPlan& p, const void* M, const void* MT, bool fp32, const void* x, void* y, SegMode mode,
+                    const void* csrc = nullptr, void* cdst = nullptr);
+PhaseDesc cast_phase(const void* src, bool src32, void* dst, bool dst32, int64_t n);
+size_t phase_smem(const PhaseDesc& d);
+// shared memory of the staged kernel for items of at most `max_in` gathered
+// inputs, `max_rows` output rows and `max_m` staged matrix entries of `esz` bytes
+size_t staged_smem(int max_in, int max_rows, int max_m, size_t esz);
+// CTAs of the cooperative launch for `smem` bytes of dynamic shared memory
+int persistent_grid(size_t smem, int* grid);
+// bar: two device words (arrival count, generation), zero before first use;
+// err: set to 1 by a barrier wait that timed out (the launch then drains).
+int launch_persistent(const PhaseDesc* d_phases, int nphases, size_t smem, int grid, unsigned* bar, int* err,
+                      const int* skip, cudaStream_t s);
+
+// Device word that staged and persistent kernels set when a bounded wait
+// expires (the vc_err field of the hierarchy's CG state); set for the
+// duration of each API call on a hierarchy.  Staged kernels are used only
+// while it is set.
+extern thread_local int* g_err_word;
+struct ErrScope {
+  int* prev;
+  explicit ErrScope(int* w) : prev(g_err_word) { g_err_word = w; }
+  ~ErrScope() { g_err_word = prev; }
+};
+
 // Kernel-launch accounting (kernels launched directly, plus the kernels of
 // each captured CUDA graph every time it is launched).
 void count_kernels(int64_t k);
@@ -197,7 +276,8 @@ struct PcgState {
   double bnorm2;
   double tol2;    // tol^2 * ||b||^2
   double relres;
-  int iters, max_iter, done, status, flexible, pad;
+  int iters, max_iter, done, status, flexible;
+  int vc_err;  // set by a persistent V-cycle whose grid barrier timed out
 };
 
 constexpr int kDotBlocks = 608;  // 4 x 152 SMs; partial sums per dot product
