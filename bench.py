@@ -40,7 +40,7 @@ WORKLOAD = "q1_512_rot"
 # DRAM bytes per V-cycle by kernel family, from ncu captures of WORKLOAD
 # (dram__bytes_read.sum + dram__bytes_write.sum summed over one V-cycle's
 # launches; profiles/).  Entries are removed when their kernels change.
-TRAFFIC = {}
+TRAFFIC = {"k_seg": 953.5e6}  # profiles/dram_solve_kernels_q1_512_rot.md
 
 
 def parse_args():
@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--N", type=int, default=None, help="cells per axis (smaller captures)")
+    ap.add_argument("--tune-cache", default=None,
+                    help="file of setup-time kernel choices: read if present, written after tuning "
+                         "(profiling runs replay the choices of a plain run)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="setup + a few solves, no timing line")
     ap.add_argument("--oracle-solve", default=None, help=argparse.SUPPRESS)
@@ -262,7 +265,7 @@ def run_ours(args):
     n = prob.n
     t0 = time.time()
     H = amg.Hierarchy.from_problem(prob, overlap=cfg["overlap"], c_min=cfg["c_min"], n_coarse=cfg["n_coarse"],
-                                   thresh=cfg["thresh"], precision=amg.MIXED32)
+                                   thresh=cfg["thresh"], precision=amg.MIXED32, tune_cache=args.tune_cache)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     stats = H.stats()
@@ -311,7 +314,11 @@ def run_ours(args):
         timed(prec, 0, args.warmup, B, X)
     if args.profile_only:
         H.set_precision(amg.MIXED32)
+        # the NVTX range lets a profiler select these V-cycles (setup's own
+        # tuning launches run the same kernels)
+        torch.cuda.nvtx.range_push("vcycle_profile")
         ms, by = H.profile_vcycle(10)
+        torch.cuda.nvtx.range_pop()
         print(json.dumps({"stats": stats, "profile_ms": ms.tolist(), "profile_bytes": by.tolist()}))
         return
     sampler = ClockSampler(local)

@@ -86,6 +86,11 @@ typedef struct {
                        /*   treated as zero (pseudo-inverse reading)      */
   int use_graph;       /* capture the CG iteration in a CUDA graph        */
   int check_every;     /* host reads the convergence flag every k iters   */
+  int tune;            /* 1: setup times the alternative kernel forms of  */
+                       /*   each step and keeps the fastest; 0: defaults  */
+  const char* tune_cache; /* NULL, or a text file of earlier choices keyed */
+                       /*   by problem, GPU, level and step: read before  */
+                       /*   timing, rewritten with new choices at the end */
 } amgdd_params;
 
 typedef struct amgdd_hierarchy amgdd_hierarchy; /* opaque, library-owned */
@@ -100,7 +105,8 @@ typedef struct {
 } amgdd_info;
 
 /* Defaults: L_max 10, n_coarse 2000, thresh 0.1, c_min = {2,3,4} (LS_{2,3,4}),
- * FP64, max_iter 1000, schur_rtol 1e-12, graphs on, check_every 4.      */
+ * FP64, max_iter 1000, schur_rtol 1e-12, graphs on, check_every 4, tune 1,
+ * no tune cache.                                                          */
 amgdd_params amgdd_params_default(void);
 
 /* ---- setup: Algorithm 1 ---------------------------------------------- */

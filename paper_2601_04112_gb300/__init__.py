@@ -45,7 +45,7 @@ class Params(ctypes.Structure):
     _fields_ = [("L_max", ctypes.c_int), ("n_coarse", ctypes.c_int64), ("thresh", ctypes.c_double),
                 ("c_min", ctypes.c_int * 8), ("n_cmin", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("schur_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
-                ("check_every", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("tune", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
 
 
 class Info(ctypes.Structure):
@@ -141,6 +141,8 @@ def params(**kw) -> Params:
             for i, c in enumerate(v):
                 p.c_min[i] = int(c)
             p.n_cmin = len(v)
+        elif k == "tune_cache":
+            p.tune_cache = None if v is None else str(v).encode()
         else:
             setattr(p, k, v)
     return p

@@ -32,6 +32,48 @@ namespace amgdd {
 static thread_local std::string g_last_error;
 thread_local int* g_err_word = nullptr;
 
+// Setup-time tuning context: whether to time alternatives, the problem/GPU
+// signature that keys the cache, and the cached choices (`key\tvalue` lines).
+struct TuneCtx {
+  bool on = true;
+  std::string path, sig;
+  std::map<std::string, double> kv;
+  bool dirty = false;
+  bool get(const std::string& k, double& v) const {
+    auto it = kv.find(sig + "|" + k);
+    if (it == kv.end()) return false;
+    v = it->second;
+    return true;
+  }
+  void put(const std::string& k, double v) {
+    kv[sig + "|" + k] = v;
+    dirty = true;
+  }
+  void load() {
+    if (path.empty()) return;
+    FILE* f = std::fopen(path.c_str(), "r");
+    if (!f) return;
+    char line[1024];
+    while (std::fgets(line, sizeof line, f)) {
+      char* tab = std::strchr(line, '\t');
+      if (!tab) continue;
+      *tab = 0;
+      kv[line] = std::atof(tab + 1);
+    }
+    std::fclose(f);
+  }
+  void save() const {
+    if (path.empty() || !dirty) return;
+    const std::string tmp = path + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return;
+    for (const auto& e : kv) std::fprintf(f, "%s\t%.17g\n", e.first.c_str(), e.second);
+    std::fclose(f);
+    std::rename(tmp.c_str(), path.c_str());
+  }
+};
+static thread_local TuneCtx* g_tune = nullptr;
+
 static std::atomic<int64_t> g_kernels{0};
 static thread_local bool g_capturing = false;
 static thread_local int64_t g_capture_kernels = 0;
@@ -487,8 +529,20 @@ int build_blockrows(Level& L, cudaStream_t s) {
 // one plan: time both on scratch vectors (`nin` inputs, `nout` outputs) and
 // keep the faster.  The staged form's arrays are freed when it loses.
 template <class T>
-int tune_seg(SegPlan& p, const T* M, const T* MT, int64_t nin, int64_t nout, SegMode mode, cudaStream_t s) {
+int tune_seg(SegPlan& p, const std::string& key, const T* M, const T* MT, int64_t nin, int64_t nout, SegMode mode,
+             cudaStream_t s) {
   if (!p.staged || g_err_word == nullptr || M == nullptr) return AMGDD_OK;
+  double cached = 0.0;
+  if (g_tune && (g_tune->get(key, cached) || !g_tune->on)) {
+    p.staged = g_tune->on ? cached != 0.0 : false;  // default without tuning: unstaged
+    if (!p.staged) {
+      p.items.release();
+      p.tabs.release();
+      p.gidx.release();
+      p.gout.release();
+    }
+    return AMGDD_OK;
+  }
   DBuf<T> xin, yout, cin;
   AMGDD_TRY(xin.alloc(std::max<int64_t>(nin, 1)));
   AMGDD_TRY(yout.alloc(std::max<int64_t>(nout, 1)));
@@ -516,6 +570,7 @@ int tune_seg(SegPlan& p, const T* M, const T* MT, int64_t nin, int64_t nout, Seg
   for (auto& v : e) cudaEventDestroy(v);
   AMGDD_TRY(rc);
   p.staged = t[0] < t[1];
+  if (g_tune) g_tune->put(key, p.staged ? 1.0 : 0.0);
   if (g_timer.on)
     fprintf(stderr, "[amgdd]   plan %d blocks: staged %.1f us, unstaged %.1f us -> %s\n", p.nblocks, 1e3 * t[0] / kReps,
             1e3 * t[1] / kReps, p.staged ? "staged" : "unstaged");
@@ -528,22 +583,36 @@ int tune_seg(SegPlan& p, const T* M, const T* MT, int64_t nin, int64_t nout, Seg
   return AMGDD_OK;
 }
 
-// Staged/unstaged choice for every gather-GEMV plan of a level.
-int tune_level_plans(Level& L, int64_t n_next, cudaStream_t s) {
-  if (L.coarsest) return tune_seg<double>(L.ras, L.W64.p, L.Wt64.p, L.n, L.n, SEG_STORE, s);
-  AMGDD_TRY(tune_seg<float>(L.ras, L.W32.p, L.Wt32.p, L.n, L.n, SEG_STORE, s));
-  AMGDD_TRY(tune_seg<float>(L.rast, L.Wt32.p, L.W32.p, L.n, L.n, SEG_ATOMIC_ADD, s));
-  AMGDD_TRY(tune_seg<float>(L.restr, L.Zt32.p, L.Z32.p, L.n, n_next, SEG_STORE, s));
-  AMGDD_TRY(tune_seg<float>(L.prol, L.Z32.p, L.Zt32.p, n_next, L.n, SEG_ADD, s));
-  if (L.A32.p) AMGDD_TRY(tune_seg<float>(L.ablk, L.A32.p, L.At32.p, L.n, L.n, SEG_RESID, s));
+// Staged/unstaged choice for every gather-GEMV plan of level `lvl`.
+int tune_level_plans(Level& L, int lvl, int64_t n_next, cudaStream_t s) {
+  const std::string k = "L" + std::to_string(lvl) + "|";
+  if (L.coarsest) return tune_seg<double>(L.ras, k + "coarse", L.W64.p, L.Wt64.p, L.n, L.n, SEG_STORE, s);
+  AMGDD_TRY(tune_seg<float>(L.ras, k + "ras", L.W32.p, L.Wt32.p, L.n, L.n, SEG_STORE, s));
+  AMGDD_TRY(tune_seg<float>(L.rast, k + "rast", L.Wt32.p, L.W32.p, L.n, L.n, SEG_ATOMIC_ADD, s));
+  AMGDD_TRY(tune_seg<float>(L.restr, k + "restrict", L.Zt32.p, L.Z32.p, L.n, n_next, SEG_STORE, s));
+  AMGDD_TRY(tune_seg<float>(L.prol, k + "prolong", L.Z32.p, L.Zt32.p, n_next, L.n, SEG_ADD, s));
+  if (L.A32.p) AMGDD_TRY(tune_seg<float>(L.ablk, k + "blockrows", L.A32.p, L.At32.p, L.n, L.n, SEG_RESID, s));
   return AMGDD_OK;
 }
 
 // Setup-time tuning of the coarse A-apply: time one FP32 residual of level L
 // in both stored forms and keep the faster.  Block rows move more bytes than
 // the compressed row groups but need no atomics and stream dense rows.
-int tune_level_A(Level& L, cudaStream_t s) {
+int tune_level_A(Level& L, int lvl, cudaStream_t s) {
   if (!L.has_blk) return AMGDD_OK;
+  const std::string key = "L" + std::to_string(lvl) + "|A";
+  double cached = 0.0;
+  if (g_tune && (g_tune->get(key, cached) || !g_tune->on)) {
+    // default without tuning: block rows (faster on every coarse level measured)
+    if (g_tune->on && cached == 0.0) {
+      L.has_blk = false;
+      L.A64.release();
+      L.At64.release();
+      L.A32.release();
+      L.At32.release();
+    }
+    return AMGDD_OK;
+  }
   AMGDD_TRY(L.x32.zero(s));
   AMGDD_TRY(L.r32.zero(s));
   cudaEvent_t e[3];
@@ -569,6 +638,7 @@ int tune_level_A(Level& L, cudaStream_t s) {
   if (g_timer.on)
     fprintf(stderr, "[amgdd] n=%lld A-apply: block rows %.1f MB %.1f us, matrix-free %.1f MB %.1f us\n",
             (long long)L.n, L.blk_mb, L.blk_us, L.mf_mb, L.mf_us);
+  if (g_tune) g_tune->put(key, L.mf_us <= L.blk_us ? 0.0 : 1.0);
   if (L.mf_us <= L.blk_us) {
     L.has_blk = false;
     L.A64.release();
@@ -1296,6 +1366,12 @@ static int tune_tail(amgdd_hierarchy& h) {
   int rc = AMGDD_OK;
   for (int pi = 0; pi < 2 && rc == AMGDD_OK; ++pi) {
     const bool f32 = pi == 1;
+    const std::string key = f32 ? "tail|mixed" : "tail|fp64";
+    double cached = 0.0;
+    if (g_tune && (g_tune->get(key, cached) || !g_tune->on)) {
+      rc = set_tail(h, pi, g_tune->on ? (int)cached : 0);
+      continue;
+    }
     const void* r = f32 ? (const void*)L0.r32.p : (const void*)h.r.p;
     void* x = f32 ? (void*)L0.x32.p : (void*)h.z.p;
     int best = 0;
@@ -1323,6 +1399,7 @@ static int tune_tail(amgdd_hierarchy& h) {
       }
     }
     if (rc == AMGDD_OK) rc = set_tail(h, pi, best);
+    if (rc == AMGDD_OK && g_tune) g_tune->put(key, (double)best);
     if (g_timer.on && rc == AMGDD_OK)
       fprintf(stderr, "[amgdd] %s V-cycle: persistent tail from level %d (%.1f us)\n", f32 ? "mixed" : "fp64", best,
               best_us);
@@ -1545,6 +1622,8 @@ amgdd_params amgdd_params_default(void) {
   p.schur_rtol = 1e-12;
   p.use_graph = 1;
   p.check_every = 4;
+  p.tune = 1;
+  p.tune_cache = nullptr;
   return p;
 }
 
@@ -1639,6 +1718,26 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   AMGDD_TRY(H->st.alloc(1));
   AMGDD_TRY(H->st.zero(s));
   ErrScope err_scope(&H->st.p->vc_err);
+  TuneCtx tctx;
+  tctx.on = prm.tune != 0;
+  tctx.path = prm.tune_cache ? prm.tune_cache : "";
+  {
+    cudaDeviceProp prop;
+    AMGDD_CUDA(cudaGetDeviceProperties(&prop, H->device));
+    std::string sig = std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "|m" +
+                      std::to_string(m) + "|n" + std::to_string(n) + "|nnz" + std::to_string(nnz) + "|ov" +
+                      std::to_string(overlap) + "|nc" + std::to_string(prm.n_coarse) + "|L" +
+                      std::to_string(prm.L_max) + "|c";
+    for (int i = 0; i < prm.n_cmin; ++i) sig += std::to_string(prm.c_min[i]) + ",";
+    char buf[64];
+    std::snprintf(buf, sizeof buf, "|t%.6g|d1%d", prm.thresh, D1 ? 1 : 0);
+    tctx.sig = sig + buf;
+  }
+  tctx.load();
+  struct TuneScope {
+    explicit TuneScope(TuneCtx* t) { g_tune = t; }
+    ~TuneScope() { g_tune = nullptr; }
+  } tune_scope(&tctx);
   // ---- level 0 row groups: consecutive rows with identical supports ----
   std::unique_ptr<Level> L0(new Level());
   L0->n = n;
@@ -1712,7 +1811,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     if (coarsest) {
       Phase ph(8, "coarsest", s);
       AMGDD_TRY(build_coarsest(*H, L, s));
-      AMGDD_TRY(tune_level_plans(L, 0, s));
+      AMGDD_TRY(tune_level_plans(L, lvl, 0, s));
       break;
     }
     AMGDD_TRY(build_level(*H, L, lvl, lvl == 0 ? aggh.data() : nullptr, s));
@@ -1723,8 +1822,8 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     }
     {
       Phase ph(10, "tune", s);
-      AMGDD_TRY(tune_level_plans(L, L.col0.back(), s));
-      if (lvl > 0) AMGDD_TRY(tune_level_A(L, s));
+      AMGDD_TRY(tune_level_plans(L, lvl, L.col0.back(), s));
+      if (lvl > 0) AMGDD_TRY(tune_level_A(L, lvl, s));
     }
     std::unique_ptr<Level> N(new Level());
     {
@@ -1762,6 +1861,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   AMGDD_CUDA(cudaEventCreateWithFlags(&H->join[1], cudaEventDisableTiming));
   AMGDD_CUDA(cudaStreamSynchronize(s));
   AMGDD_TRY(tune_tail(*H));
+  tctx.save();
   H->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = H.release();
   return AMGDD_OK;
