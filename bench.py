@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--N", type=int, default=None, help="cells per axis (smaller captures)")
+    ap.add_argument("--tune-mode", choices=("timed", "defaults", "staged"), default="timed",
+                    help="setup-time kernel choices: timed (default), fixed defaults, or staged kernels wherever "
+                         "a plan allows them (profiling)")
     ap.add_argument("--tune-cache", default=None,
                     help="file of setup-time kernel choices: read if present, written after tuning "
                          "(profiling runs replay the choices of a plain run)")
@@ -265,7 +268,8 @@ def run_ours(args):
     n = prob.n
     t0 = time.time()
     H = amg.Hierarchy.from_problem(prob, overlap=cfg["overlap"], c_min=cfg["c_min"], n_coarse=cfg["n_coarse"],
-                                   thresh=cfg["thresh"], precision=amg.MIXED32, tune_cache=args.tune_cache)
+                                   thresh=cfg["thresh"], precision=amg.MIXED32, tune_cache=args.tune_cache,
+                                   tune={"timed": 1, "defaults": 0, "staged": 2}[args.tune_mode])
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     stats = H.stats()
@@ -399,6 +403,32 @@ def run_ours(args):
     t_e2e = maxrank(max(t_e2e, w_e2e))
     e2e = {"value": solves / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
 
+    # batched right-hand sides: batches of 8 columns (each its own CG) share
+    # every V-cycle launch; same right-hand sides, both precisions
+    def timed_batched(prec, nbatch, K=8):
+        H.set_precision(prec)
+        Bk = torch.from_numpy(np.ascontiguousarray(seeded_rhs(n, K, cfg["seed"] * 1000 + 500 + rank))).cuda()
+        H.solve(Bk, tol=1e-8)  # warm-up (graph capture)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        its = []
+        for _ in range(nbatch):
+            _, inf = H.solve(Bk, tol=1e-8)
+            its.append(max(i["iters"] for i in inf))
+            assert all(i["status"] == 0 and i["relres_true"] <= 1e-8 for i in inf), inf
+        e1.record()
+        torch.cuda.synchronize()
+        return maxrank(e0.elapsed_time(e1) / 1e3), its
+
+    nbatch = max(3, args.steps // 4)
+    tb_mix, itb_mix = timed_batched(amg.MIXED32, nbatch)
+    tb_64, itb_64 = timed_batched(amg.FP64, nbatch)
+    batched = {"nrhs_per_batch": 8, "batches": nbatch * world, "unit": "solves/s",
+               "mixed": 8 * nbatch * world / tb_mix, "fp64": 8 * nbatch * world / tb_64,
+               "max_iters_per_batch": {"mixed": itb_mix[0], "fp64": itb_64[0]}}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle in a process of its own, single-threaded BLAS
@@ -437,6 +467,7 @@ def run_ours(args):
         "coarse_A": [c["form"] for c in stats["coarse_A"]],
         "persistent_tail_from": {"mixed": stats["tail"]["mixed"]["from"], "fp64": stats["tail"]["fp64"]["from"]},
         "roofline": roofline, "vcycle_profile_us_gbs": vprof,
+        "batched": batched,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
         "cpu_baseline": cpu,
     }

@@ -88,6 +88,9 @@ typedef struct {
   int check_every;     /* host reads the convergence flag every k iters   */
   int tune;            /* 1: setup times the alternative kernel forms of  */
                        /*   each step and keeps the fastest; 0: defaults  */
+                       /*   (unstaged kernels, block rows, no persistent  */
+                       /*   tail); 2: as 0 with staged kernels wherever a */
+                       /*   plan allows them (for profiling them)         */
   const char* tune_cache; /* NULL, or a text file of earlier choices keyed */
                        /*   by problem, GPU, level and step: read before  */
                        /*   timing, rewritten with new choices at the end */
@@ -134,6 +137,12 @@ int amgdd_setup(const amgdd_csr* G, const double* D1, const int32_t* agg, int ov
  * ||r_k|| <= tol ||b|| on the recursively updated residual (the check runs
  * every params.check_every iterations; iterations after convergence leave x
  * unchanged).  info (host, nrhs entries) may be NULL.
+ * With nrhs > 1 (and CUDA graphs on) the right-hand sides are solved in
+ * batches of up to 8 that share every V-cycle and A-apply launch: each
+ * column is its own CG (own scalars and stopping test, x frozen once it has
+ * converged), so a batch reads the hierarchy's matrices once per iteration
+ * for all of its columns.  Per-column results agree with single solves to
+ * rounding (the batched kernels sum in another order).
  * Returns the first non-OK per-RHS status, or an error code.             */
 int amgdd_solve(amgdd_hierarchy* h, const double* b, int nrhs, double tol, double* x, void* stream,
                 amgdd_info* info);

@@ -199,10 +199,25 @@ class Hierarchy:
             if x is None:
                 x = np.zeros_like(b, order="F")
         else:
-            assert b.is_contiguous() or nrhs == 1
-            if x is None:
-                import torch
+            import torch
 
+            if nrhs > 1:
+                # the C ABI takes column-major n x nrhs: pass (nrhs, n) row-major storage
+                bc = b.t().contiguous()
+                xc = torch.zeros_like(bc) if x is None else x.t().contiguous()
+                infos = (Info * nrhs)()
+                st = self._lib.amgdd_solve(self._h, _ptr(bc)[0], nrhs, float(tol), _ptr(xc)[0], _stream(stream),
+                                           infos)
+                if st not in (0, -4, -5, -3):
+                    _check(st)
+                if x is None:
+                    x = xc.t()
+                else:
+                    x.copy_(xc.t())
+                return x, [dict(iters=i.iters, status=i.status, relres=i.relres, relres_true=i.relres_true,
+                                solve_ms=i.solve_ms) for i in infos]
+            assert b.is_contiguous()
+            if x is None:
                 x = torch.zeros_like(b)
         infos = (Info * nrhs)()
         st = self._lib.amgdd_solve(self._h, _ptr(b)[0], nrhs, float(tol), _ptr(x)[0], _stream(stream), infos)

@@ -36,6 +36,7 @@ thread_local int* g_err_word = nullptr;
 // signature that keys the cache, and the cached choices (`key\tvalue` lines).
 struct TuneCtx {
   bool on = true;
+  bool prefer_staged = false;
   std::string path, sig;
   std::map<std::string, double> kv;
   bool dirty = false;
@@ -534,7 +535,8 @@ int tune_seg(SegPlan& p, const std::string& key, const T* M, const T* MT, int64_
   if (!p.staged || g_err_word == nullptr || M == nullptr) return AMGDD_OK;
   double cached = 0.0;
   if (g_tune && (g_tune->get(key, cached) || !g_tune->on)) {
-    p.staged = g_tune->on ? cached != 0.0 : false;  // default without tuning: unstaged
+    // without timing: unstaged, or staged when asked for (tune = 2)
+    p.staged = g_tune->on ? cached != 0.0 : g_tune->prefer_staged;
     if (!p.staged) {
       p.items.release();
       p.tabs.release();
@@ -680,12 +682,30 @@ struct amgdd_hierarchy {
   int persist_from[2] = {0, 0};
   double persist_us[2][16] = {};  // setup-time V-cycle timings by first level (0 = all separate launches)
   DBuf<unsigned> bar;
+  // batched right-hand sides: CG vectors (n x kMaxRhs, interleaved), K
+  // states, graphs per precision and K in {2, 4, 8}; allocated at the first
+  // batched solve
+  struct Multi {
+    bool ready = false;
+    DBuf<double> x, r, z, zold, p, q, b, stage, partials;
+    DBuf<PcgState> st;
+    DBuf<int> grp;
+    PcgState* st_host = nullptr;
+    cudaGraphExec_t ginit[2][3] = {}, gloop[2][3] = {};
+    int64_t ginit_kernels[2][3] = {}, gloop_kernels[2][3] = {};
+  } mw;
   ~amgdd_hierarchy() {
     for (int i = 0; i < 2; ++i) {
       if (ginit[i]) cudaGraphExecDestroy(ginit[i]);
       if (gloop[i]) cudaGraphExecDestroy(gloop[i]);
     }
     if (st_host) cudaFreeHost(st_host);
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 3; ++j) {
+        if (mw.ginit[i][j]) cudaGraphExecDestroy(mw.ginit[i][j]);
+        if (mw.gloop[i][j]) cudaGraphExecDestroy(mw.gloop[i][j]);
+      }
+    if (mw.st_host) cudaFreeHost(mw.st_host);
     for (auto& e : join)
       if (e) cudaEventDestroy(e);
     if (work) cudaStreamDestroy(work);
@@ -792,6 +812,10 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
   AMGDD_TRY(L.Wt64.alloc(w_off[nagg]));
   AMGDD_TRY(L.W32.alloc(w_off[nagg]));
   AMGDD_TRY(L.Wt32.alloc(w_off[nagg]));
+  AMGDD_TRY(L.Aw64.alloc(w_off[nagg]));
+  AMGDD_TRY(L.AwT64.alloc(w_off[nagg]));
+  AMGDD_TRY(L.Aw32.alloc(w_off[nagg]));
+  AMGDD_TRY(L.AwT32.alloc(w_off[nagg]));
   AMGDD_TRY(L.mu.alloc(mu_off[nagg]));
   DBuf<double> inv_scratch;
   AMGDD_TRY(inv_scratch.alloc(w_off[nagg]));
@@ -888,6 +912,8 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
       Phase ph(1, "assemble", s);
       AMGDD_TRY(launch_assemble(nb, max_m, B, L.d_g_ptr.p, L.d_h_off.p, L.d_H.p, dM.p, Apool.p, Atpool.p, s));
     }
+    AMGDD_TRY(launch_copy_wrows(nb, B.m.p, B.no.p, B.a_off.p, Apool.p, dwoff.p, L.Aw64.p, L.Aw32.p, L.AwT64.p,
+                                L.AwT32.p, s));
     {
       Phase ph(2, "cholesky", s);
       AMGDD_TRY(launch_chol(nb, max_m, B.m.p, B.a_off.p, Apool.p, dstat.p, s));
@@ -1605,6 +1631,226 @@ static int take_err_word(amgdd_hierarchy& h, cudaStream_t s) {
   return AMGDD_ERR_TIMEOUT;
 }
 
+// ---------------------------------------------------------------------------
+// Batched right-hand sides: K in {2, 4, 8} independent CGs that share every
+// V-cycle and A-apply launch (multi_kernels.cu).
+constexpr int kMaxRhs = 8;
+static int kidx(int K) { return K == 2 ? 0 : (K == 4 ? 1 : 2); }
+
+static int ensure_multi(amgdd_hierarchy& h) {
+  auto& M = h.mw;
+  if (M.ready) return AMGDD_OK;
+  const int64_t nk = h.n * kMaxRhs;
+  for (auto* v : {&M.x, &M.r, &M.z, &M.zold, &M.p, &M.q, &M.b, &M.stage}) AMGDD_TRY(v->alloc(nk));
+  AMGDD_TRY(M.partials.alloc((int64_t)kDotBlocks * 2 * kMaxRhs));
+  AMGDD_TRY(M.st.alloc(kMaxRhs));
+  AMGDD_TRY(M.grp.alloc(4));
+  AMGDD_CUDA(cudaMallocHost((void**)&M.st_host, kMaxRhs * sizeof(PcgState)));
+  for (auto& Lp : h.lv) {
+    Level& L = *Lp;
+    const int64_t lk = L.n * kMaxRhs;
+    AMGDD_TRY(L.mr64.alloc(lk));
+    AMGDD_TRY(L.mx64.alloc(lk));
+    AMGDD_TRY(L.ms64.alloc(lk));
+    AMGDD_TRY(L.mr32.alloc(lk));
+    AMGDD_TRY(L.mx32.alloc(lk));
+    AMGDD_TRY(L.ms32.alloc(lk));
+  }
+  M.ready = true;
+  return AMGDD_OK;
+}
+
+// s = r - A x for K columns: block rows where stored, else the rows omega_i
+// of A over Omega_i (with the RAS plan's index lists).
+static int resid_multi(const Level& L, bool f32, int K, const void* x, const void* r, void* sv, const int* skip,
+                       cudaStream_t s) {
+  if (L.has_blk)
+    return launch_seg_multi(L.ablk, f32 ? (const void*)L.A32.p : (const void*)L.A64.p,
+                            f32 ? (const void*)L.At32.p : (const void*)L.At64.p, f32, x, sv, SEG_RESID, r, K, skip, s);
+  return launch_seg_multi(L.ras, f32 ? (const void*)L.Aw32.p : (const void*)L.Aw64.p,
+                          f32 ? (const void*)L.AwT32.p : (const void*)L.AwT64.p, f32, x, sv, SEG_RESID, r, K, skip, s);
+}
+
+// The V-cycle of Section 3.1 for K interleaved columns.
+static int vcycle_multi(amgdd_hierarchy& h, int l, bool f32, int K, const void* r, void* x, const int* skip,
+                        cudaStream_t s) {
+  Level& L = *h.lv[l];
+  if (L.coarsest) {
+    if (f32) {
+      AMGDD_TRY(launch_cast(r, true, L.mr64.p, false, L.n * K, skip, s));
+      AMGDD_TRY(launch_seg_multi(L.ras, L.W64.p, L.Wt64.p, false, L.mr64.p, L.mx64.p, SEG_STORE, nullptr, K, skip, s));
+      return launch_cast(L.mx64.p, false, x, true, L.n * K, skip, s);
+    }
+    return launch_seg_multi(L.ras, L.W64.p, L.Wt64.p, false, r, x, SEG_STORE, nullptr, K, skip, s);
+  }
+  Level& N = *h.lv[l + 1];
+  const void* W = f32 ? (const void*)L.W32.p : (const void*)L.W64.p;
+  const void* Wt = f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p;
+  const void* Z = f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p;
+  const void* Zt = f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p;
+  void* sv = f32 ? (void*)L.ms32.p : (void*)L.ms64.p;
+  void* rn = f32 ? (void*)N.mr32.p : (void*)N.mr64.p;
+  void* xn = f32 ? (void*)N.mx32.p : (void*)N.mx64.p;
+  AMGDD_TRY(launch_seg_multi(L.ras, W, Wt, f32, r, x, SEG_STORE, nullptr, K, skip, s));
+  AMGDD_TRY(resid_multi(L, f32, K, x, r, sv, skip, s));
+  AMGDD_TRY(launch_seg_multi(L.restr, Zt, Z, f32, sv, rn, SEG_STORE, nullptr, K, skip, s));
+  AMGDD_TRY(vcycle_multi(h, l + 1, f32, K, rn, xn, skip, s));
+  AMGDD_TRY(launch_seg_multi(L.prol, Z, Zt, f32, xn, x, SEG_ADD, nullptr, K, skip, s));
+  AMGDD_TRY(resid_multi(L, f32, K, x, r, sv, skip, s));
+  return launch_seg_multi(L.rast, Wt, W, f32, sv, x, SEG_ATOMIC_ADD, nullptr, K, skip, s);
+}
+
+static int precondition_multi(amgdd_hierarchy& h, int K, const double* r, double* z, const int* skip,
+                              cudaStream_t s) {
+  Level& L0 = *h.lv[0];
+  if (h.precision == AMGDD_MIXED32) {
+    AMGDD_TRY(launch_cast(r, false, L0.mr32.p, true, h.n * K, skip, s));
+    AMGDD_TRY(vcycle_multi(h, 0, true, K, L0.mr32.p, L0.mx32.p, skip, s));
+    return launch_cast(L0.mx32.p, true, z, false, h.n * K, skip, s);
+  }
+  return vcycle_multi(h, 0, false, K, r, z, skip, s);
+}
+
+static int pcg_start_multi(amgdd_hierarchy& h, int K, cudaStream_t s) {
+  auto& M = h.mw;
+  const int64_t n = h.n, nk = h.n * K;
+  const int* skip = M.grp.p;
+  AMGDD_CUDA(cudaMemcpyAsync(M.r.p, M.b.p, nk * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  AMGDD_CUDA(cudaMemsetAsync(M.x.p, 0, nk * sizeof(double), s));
+  AMGDD_TRY(launch_dot_multi(M.b.p, M.b.p, nullptr, n, K, M.partials.p, nullptr, s));
+  AMGDD_TRY(launch_pcg_scalar_multi(4, M.st.p, M.grp.p, M.partials.p, K, s));
+  AMGDD_TRY(precondition_multi(h, K, M.r.p, M.z.p, skip, s));
+  AMGDD_TRY(launch_copy_vec(M.z.p, M.p.p, false, nk, skip, s));
+  if (h.precision == AMGDD_MIXED32) AMGDD_TRY(launch_copy_vec(M.z.p, M.zold.p, false, nk, skip, s));
+  AMGDD_TRY(launch_dot_multi(M.r.p, M.z.p, nullptr, n, K, M.partials.p, skip, s));
+  return launch_pcg_scalar_multi(0, M.st.p, M.grp.p, M.partials.p, K, s);
+}
+
+static int pcg_iteration_multi(amgdd_hierarchy& h, int K, cudaStream_t s, cudaGraphConditionalHandle cond = 0,
+                               int use_cond = 0) {
+  auto& M = h.mw;
+  const int64_t n = h.n;
+  const int* skip = M.grp.p;
+  Level& L0 = *h.lv[0];
+  AMGDD_TRY(launch_seg_multi(L0.ras, L0.Aw64.p, L0.AwT64.p, false, M.p.p, M.q.p, SEG_STORE, nullptr, K, skip, s));
+  AMGDD_TRY(launch_dot_multi(M.p.p, M.q.p, nullptr, n, K, M.partials.p, skip, s));
+  AMGDD_TRY(launch_pcg_scalar_multi(1, M.st.p, M.grp.p, M.partials.p, K, s));
+  AMGDD_TRY(launch_update_xr_multi(M.st.p, M.grp.p, M.x.p, M.r.p, M.p.p, M.q.p, n, K, s));
+  AMGDD_TRY(launch_dot_multi(M.r.p, M.r.p, nullptr, n, K, M.partials.p, skip, s));
+  AMGDD_TRY(launch_pcg_scalar_multi(2, M.st.p, M.grp.p, M.partials.p, K, s));
+  AMGDD_TRY(precondition_multi(h, K, M.r.p, M.z.p, skip, s));
+  const bool flex = h.precision == AMGDD_MIXED32;
+  AMGDD_TRY(launch_dot_multi(M.r.p, M.z.p, flex ? M.zold.p : nullptr, n, K, M.partials.p, skip, s));
+  AMGDD_TRY(launch_pcg_scalar_multi(3, M.st.p, M.grp.p, M.partials.p, K, s, cond, use_cond));
+  return launch_update_p_multi(M.st.p, M.grp.p, M.p.p, M.z.p, flex ? M.zold.p : nullptr, n, K, s);
+}
+
+// Graphs of the batched solve (start; WHILE loop over iterations), as for
+// one right-hand side.
+static int build_multi_graphs(amgdd_hierarchy& h, int pi, int K, cudaStream_t s) {
+  auto& M = h.mw;
+  const int ki = kidx(K);
+  cudaGraph_t g;
+  AMGDD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  capture_begin();
+  int rc = pcg_start_multi(h, K, s);
+  M.ginit_kernels[pi][ki] = capture_end();
+  cudaError_t ce = cudaStreamEndCapture(s, &g);
+  if (rc != AMGDD_OK) return rc;
+  AMGDD_CUDA(ce);
+  AMGDD_CUDA(cudaGraphInstantiate(&M.ginit[pi][ki], g, 0));
+  cudaGraphDestroy(g);
+  cudaGraph_t lg;
+  AMGDD_CUDA(cudaGraphCreate(&lg, 0));
+  cudaGraphConditionalHandle cond;
+  AMGDD_CUDA(cudaGraphConditionalHandleCreate(&cond, lg, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  AMGDD_CUDA(cudaGraphAddNode(&node, lg, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  AMGDD_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  capture_begin();
+  rc = pcg_iteration_multi(h, K, s, cond, 1);
+  M.gloop_kernels[pi][ki] = capture_end();
+  ce = cudaStreamEndCapture(s, &body);
+  if (rc != AMGDD_OK) return rc;
+  AMGDD_CUDA(ce);
+  AMGDD_CUDA(cudaGraphInstantiate(&M.gloop[pi][ki], lg, 0));
+  cudaGraphDestroy(lg);
+  return AMGDD_OK;
+}
+
+// Solves `ncols` <= K columns of b (column-major, leading dimension n) as one
+// batch of K; the padding columns are zero and finish at once.
+static int solve_group(amgdd_hierarchy& h, const double* b, bool bdev, int ncols, int K, double tol, double* x,
+                       bool xdev, cudaStream_t s, amgdd_info* info) {
+  auto& M = h.mw;
+  const int64_t n = h.n;
+  AMGDD_TRY(ensure_multi(h));
+  cudaEvent_t e0, e1;
+  AMGDD_CUDA(cudaEventCreate(&e0));
+  AMGDD_CUDA(cudaEventCreate(&e1));
+  AMGDD_CUDA(cudaEventRecord(e0, s));
+  AMGDD_CUDA(cudaMemcpyAsync(M.stage.p, b, n * ncols * sizeof(double),
+                             bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  AMGDD_TRY(launch_interleave(M.stage.p, n, ncols, M.b.p, n, K, s));
+  for (int k = 0; k < K; ++k) {
+    PcgState init{};
+    init.tol2 = tol * tol;
+    init.max_iter = h.prm.max_iter;
+    init.flexible = h.precision == AMGDD_MIXED32 ? 1 : 0;
+    M.st_host[k] = init;
+  }
+  AMGDD_CUDA(cudaMemcpyAsync(M.st.p, M.st_host, K * sizeof(PcgState), cudaMemcpyHostToDevice, s));
+  AMGDD_CUDA(cudaMemsetAsync(M.grp.p, 0, sizeof(int), s));
+  const int pi = h.precision == AMGDD_MIXED32 ? 1 : 0, ki = kidx(K);
+  if (M.gloop[pi][ki] == nullptr) AMGDD_TRY(build_multi_graphs(h, pi, K, s));
+  AMGDD_CUDA(cudaGraphLaunch(M.ginit[pi][ki], s));
+  count_graph_launch(M.ginit_kernels[pi][ki]);
+  AMGDD_CUDA(cudaGraphLaunch(M.gloop[pi][ki], s));
+  AMGDD_CUDA(cudaMemcpyAsync(M.st_host, M.st.p, K * sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  // true residuals b - A x in FP64
+  Level& L0 = *h.lv[0];
+  AMGDD_TRY(launch_seg_multi(L0.ras, L0.Aw64.p, L0.AwT64.p, false, M.x.p, M.q.p, SEG_RESID, M.b.p, K, nullptr, s));
+  AMGDD_TRY(launch_dot_multi(M.q.p, M.q.p, nullptr, n, K, M.partials.p, nullptr, s));
+  AMGDD_TRY(launch_deinterleave(M.x.p, n, K, M.stage.p, n, ncols, s));
+  AMGDD_CUDA(cudaMemcpyAsync(x, M.stage.p, n * ncols * sizeof(double),
+                             xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  AMGDD_CUDA(cudaEventRecord(e1, s));
+  std::vector<double> part;
+  AMGDD_TRY(download(part, M.partials.p, (size_t)kDotBlocks * 2 * K, s));
+  float ms = 0.f;
+  AMGDD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int maxit = 0;
+  for (int k = 0; k < K; ++k) maxit = std::max(maxit, M.st_host[k].iters);
+  count_graph_launch(M.gloop_kernels[pi][ki] * std::max(maxit, 1));
+  int first_bad = AMGDD_OK;
+  for (int k = 0; k < ncols; ++k) {
+    const PcgState& f = M.st_host[k];
+    if (f.vc_err != 0) {
+      set_error("a bounded device-side wait expired");
+      return AMGDD_ERR_TIMEOUT;
+    }
+    double qq = 0.0;
+    for (int i = 0; i < kDotBlocks; ++i) qq += part[(size_t)i * 2 * K + k];
+    if (info) {
+      info[k].iters = f.iters;
+      info[k].status = f.status;
+      info[k].relres = f.relres;
+      info[k].relres_true = f.bnorm2 > 0 ? std::sqrt(qq / f.bnorm2) : 0.0;
+      info[k].solve_ms = ms;
+    }
+    if (f.status != AMGDD_OK && first_bad == AMGDD_OK) first_bad = f.status;
+  }
+  return first_bad;
+}
+
 extern "C" {
 
 amgdd_params amgdd_params_default(void) {
@@ -1719,7 +1965,8 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   AMGDD_TRY(H->st.zero(s));
   ErrScope err_scope(&H->st.p->vc_err);
   TuneCtx tctx;
-  tctx.on = prm.tune != 0;
+  tctx.on = prm.tune == 1;
+  tctx.prefer_staged = prm.tune == 2;
   tctx.path = prm.tune_cache ? prm.tune_cache : "";
   {
     cudaDeviceProp prop;
@@ -1824,6 +2071,12 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
       Phase ph(10, "tune", s);
       AMGDD_TRY(tune_level_plans(L, lvl, L.col0.back(), s));
       if (lvl > 0) AMGDD_TRY(tune_level_A(L, lvl, s));
+      if (L.has_blk) {  // the batched residual uses the block rows
+        L.Aw64.release();
+        L.AwT64.release();
+        L.Aw32.release();
+        L.AwT32.release();
+      }
     }
     std::unique_ptr<Level> N(new Level());
     {
@@ -1894,6 +2147,22 @@ int amgdd_solve(amgdd_hierarchy* h, const double* b, int nrhs, double tol, doubl
     AMGDD_CUDA(cudaStreamWaitEvent(s, h->join[0], 0));
     const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
     int first_bad = AMGDD_OK;
+    if (nrhs > 1 && h->prm.use_graph && h->lv[0]->Aw64.p != nullptr) {
+      for (int j0 = 0; j0 < nrhs; j0 += kMaxRhs) {
+        const int g = std::min(kMaxRhs, nrhs - j0);
+        const int K = g <= 2 ? 2 : (g <= 4 ? 4 : 8);
+        std::vector<amgdd_info> tmp(g);
+        const int st = solve_group(*h, b + (int64_t)j0 * h->n, bdev, g, K, tol, x + (int64_t)j0 * h->n, xdev, s,
+                                   info ? info + j0 : tmp.data());
+        const bool per_rhs = st == AMGDD_OK || st == AMGDD_ERR_BREAKDOWN || st == AMGDD_ERR_NO_CONVERGENCE ||
+                             st == AMGDD_ERR_NONFINITE;
+        if (!per_rhs) return st;
+        if (st != AMGDD_OK && first_bad == AMGDD_OK) first_bad = st;
+      }
+      AMGDD_CUDA(cudaEventRecord(h->join[1], s));
+      AMGDD_CUDA(cudaStreamWaitEvent(us, h->join[1], 0));
+      return first_bad;
+    }
     for (int j = 0; j < nrhs; ++j) {
       amgdd_info tmp{};
       const int st = solve_one(*h, b + (int64_t)j * h->n, bdev, tol, x + (int64_t)j * h->n, xdev, s,

@@ -20,6 +20,7 @@
 #include <mutex>
 #include <cstdint>
 
+#include "device_util.cuh"
 #include "internal.h"
 
 namespace amgdd {
@@ -31,23 +32,6 @@ constexpr int kSegThreads = 128;
 template <class T>
 __device__ __forceinline__ void atomic_add(T* p, T v) {
   atomicAdd(p, v);
-}
-
-template <int L, class T>
-__device__ __forceinline__ T group_sum(T v, unsigned mask) {
-#pragma unroll
-  for (int off = L / 2; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off, L);
-  return v;
-}
-
-template <int L>
-__device__ __forceinline__ unsigned group_mask() {
-  if constexpr (L == 32) {
-    return 0xffffffffu;
-  } else {
-    const int g = (threadIdx.x & 31) / L;
-    return ((1u << L) - 1u) << (g * L);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -614,11 +598,6 @@ int grid_for(int64_t n, int threads) {
 // reductions in a fixed order; stage 2 is done by k_pcg_scalar.
 constexpr int kDotThreads = 256;
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  return v;
-}
 
 __global__ void __launch_bounds__(kDotThreads) k_dot_partial(const double* __restrict__ a, const double* __restrict__ b,
                                                              const double* __restrict__ c, int64_t n,

@@ -190,9 +190,17 @@ struct Level {
   SegPlan ras, rast, restr, prol;
   DBuf<double> W64, Wt64, Z64, Zt64, mu;
   DBuf<float> W32, Wt32, Z32, Zt32;
+  // rows omega_i of A over Omega_i (layout of W_i; the residual of the
+  // batched solver where A has no block rows), applied with the RAS plan
+  DBuf<double> Aw64, AwT64;
+  DBuf<float> Aw32, AwT32;
   // ---- work vectors of the V-cycle ----------------------------------------
   DBuf<double> r64, x64, s64;
   DBuf<float> r32, x32, s32;
+  // the same for up to kMaxRhs right-hand sides (interleaved; allocated at
+  // the first batched solve)
+  DBuf<double> mr64, mx64, ms64;
+  DBuf<float> mr32, mx32, ms32;
 };
 
 // ---------------------------------------------------------------------------
@@ -293,6 +301,27 @@ int launch_update_xr(PcgState* st, double* x, double* r, const double* p, const 
 int launch_update_p(PcgState* st, double* p, const double* z, double* zold, int64_t n, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// K right-hand sides at once (multi_kernels.cu): vectors interleaved by node
+// (v[i * K + k]), K in {2, 4, 8}.  Modes as launch_seg (SEG_RESID reads c).
+int launch_seg_multi(const SegPlan& p, const void* M, const void* MT, bool fp32, const void* x, void* y, SegMode mode,
+                     const void* csrc, int K, const int* skip, cudaStream_t s);
+// partials: kDotBlocks x 2K (a.b then a.c per column)
+int launch_dot_multi(const double* a, const double* b, const double* c, int64_t n, int K, double* partials,
+                     const int* skip, cudaStream_t s);
+// st: K states; grp[0] set to 1 once every column is done
+int launch_pcg_scalar_multi(int which, PcgState* st, int* grp, const double* partials, int K, cudaStream_t s,
+                            cudaGraphConditionalHandle cond = 0, int use_cond = 0);
+int launch_update_xr_multi(const PcgState* st, const int* grp, double* x, double* r, const double* p, const double* q,
+                           int64_t n, int K, cudaStream_t s);
+int launch_update_p_multi(const PcgState* st, const int* grp, double* p, const double* z, double* zold, int64_t n,
+                          int K, cudaStream_t s);
+// column-major (leading dimension ld, ncols <= K columns; the rest zero) <->
+// interleaved
+int launch_interleave(const double* src, int64_t ld, int ncols, double* dst, int64_t n, int K, cudaStream_t s);
+int launch_deinterleave(const double* src, int64_t n, int K, double* dst, int64_t ld, int ncols, cudaStream_t s);
+
+
+// ---------------------------------------------------------------------------
 // setup kernels (setup_kernels.cu); all FP64
 struct LocalBatch {
   // one entry per aggregate of the batch
@@ -354,6 +383,10 @@ int launch_gep(int nb, int max_no, const int32_t* m, const int32_t* no, const in
                cudaStream_t s);
 int launch_pack_z(int nb, const int32_t* no, const int32_t* k, const int64_t* z_off_cap, const double* Zcap,
                   const int64_t* z_off, double* Z64, float* Z32, double* Zt64, float* Zt32, cudaStream_t s);
+// Rows omega_i of each assembled A_i (before its Cholesky) in the layout of
+// W_i, plus the block transposes, in FP64 and FP32.
+int launch_copy_wrows(int nb, const int32_t* m, const int32_t* no, const int64_t* a_off, const double* Apool,
+                      const int64_t* w_off, double* Aw64, float* Aw32, double* AwT64, float* AwT32, cudaStream_t s);
 // Block rows of A_l = sum_g H_g: for block b, rows p0 .. p0+nr_b-1 of each
 // touching group's Gram, columns mapped into in_b by `map`.
 int launch_blockrows(int nblk, const int32_t* nr, const int32_t* nc, const int64_t* m_off, const int64_t* pair_ptr,

@@ -1039,4 +1039,37 @@ int launch_blockrows(int nblk, const int32_t* nr, const int32_t* nc, const int64
   return AMGDD_OK;
 }
 
+namespace {
+// Rows omega_i of the assembled A_i = A(Omega_i, Omega_i) (symmetric, so row
+// r is contiguous), in the layout of the smoother rows W_i: A(omega_i,
+// Omega_i) row-major at w_off and its block transpose.  The residual of
+// rows omega_i reads exactly these, since Omega_i holds their support.
+__global__ void k_copy_wrows(const int32_t* __restrict__ mdim, const int32_t* __restrict__ nodim,
+                             const int64_t* __restrict__ a_off, const double* __restrict__ Apool,
+                             const int64_t* __restrict__ w_off, double* __restrict__ Aw64, float* __restrict__ Aw32,
+                             double* __restrict__ AwT64, float* __restrict__ AwT32) {
+  const int b = blockIdx.x;
+  const int m = mdim[b], no = nodim[b];
+  const double* A = Apool + a_off[b];
+  const int64_t o = w_off[b];
+  for (int64_t e = threadIdx.x; e < (int64_t)no * m; e += blockDim.x) {
+    const int r = (int)(e / m), c = (int)(e - (int64_t)r * m);
+    const double v = A[e];
+    Aw64[o + e] = v;
+    Aw32[o + e] = (float)v;
+    AwT64[o + (int64_t)c * no + r] = v;
+    AwT32[o + (int64_t)c * no + r] = (float)v;
+  }
+}
+}  // namespace
+
+int launch_copy_wrows(int nb, const int32_t* m, const int32_t* no, const int64_t* a_off, const double* Apool,
+                      const int64_t* w_off, double* Aw64, float* Aw32, double* AwT64, float* AwT32, cudaStream_t s) {
+  if (nb == 0) return AMGDD_OK;
+  k_copy_wrows<<<nb, 256, 0, s>>>(m, no, a_off, Apool, w_off, Aw64, Aw32, AwT64, AwT32);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
 }  // namespace amgdd

@@ -257,7 +257,9 @@ def test_multi_rhs_device_buffers_and_zero_rhs(amg):
     for j in (0, 2):
         assert infos[j].relres_true <= 1e-8
         xh, ih = H.solve(B[:, j], tol=1e-8)
-        assert _rel(X[:, j], xh[:, 0] if xh.ndim == 2 else xh) <= 1e-12
+        # the batched kernels sum in another order: agreement to CG rounding
+        assert abs(infos[j].iters - ih[0]["iters"]) <= 1
+        assert _rel(X[:, j], xh[:, 0] if xh.ndim == 2 else xh) <= 1e-9
 
 
 def test_cleanup_of_unaggregated_nodes(amg):
