@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--N", type=int, default=None, help="cells per axis (smaller captures)")
+    ap.add_argument("--serve", action="store_true",
+                    help="run the serving workload (many operators and right-hand-side counts) instead")
+    ap.add_argument("--no-serving", action="store_true", help="skip the small serving run of the default line")
     ap.add_argument("--tune-mode", choices=("timed", "defaults", "staged"), default="timed",
                     help="setup-time kernel choices: timed (default), fixed defaults, or staged kernels wherever "
                          "a plan allows them (profiling)")
@@ -241,6 +244,71 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def serving_run(amg, seed, sides, nops, nreq, max_rhs, rate_frac=0.8, slots=4):
+    """Requests over a pool of operators of several grid sizes through the
+    continuous-batching server: throughput with every request queued at once,
+    then latency under open-loop Poisson arrivals at rate_frac of it.
+    Operators: sides cycle through `sides`, theta ~ U[0, pi), eps
+    log-uniform in [1e-6, 1], 4x4 aggregates, LS_{2,3,4}, mixed precision;
+    requests: a uniform operator and 1..max_rhs right-hand sides."""
+    import numpy as np
+    from inputs import block_aggregates_2d, q1_2d, rotated_sqrtK, seeded_rhs
+
+    rng = np.random.default_rng(seed)
+    srv = amg.Server(slots=slots)
+    ops = []
+    t0 = time.perf_counter()
+    for j in range(nops):
+        N = sides[j % len(sides)]
+        theta, eps = float(rng.uniform(0.0, math.pi)), float(10.0 ** rng.uniform(-6.0, 0.0))
+        prob = q1_2d(N, rotated_sqrtK(theta, eps), agg=block_aggregates_2d(N, 4))
+        op, _ = srv.add_operator(prob, key=j, c_min=(2, 3, 4), n_coarse=2000, precision=amg.MIXED32)
+        ops.append((op, prob.n))
+    setup_s = time.perf_counter() - t0
+    reqs = []
+    for i in range(nreq):
+        k = int(rng.integers(nops))
+        reqs.append((ops[k][0], seeded_rhs(ops[k][1], int(rng.integers(1, max_rhs + 1)), seed * 100000 + i)))
+    cols = sum(B.shape[1] for _, B in reqs)
+    # saturation: everything queued at once
+    t0 = time.perf_counter()
+    rids = [srv.submit(op, B) for op, B in reqs]
+    for rid in rids:
+        r = srv.poll(rid)
+        assert r[3] == 0, r[1]
+    sat = time.perf_counter() - t0
+    s_sat = srv.stats()
+    # open loop at rate_frac of the saturated request rate
+    lam = rate_frac * nreq / sat
+    gaps = rng.exponential(1.0 / lam, nreq)
+    lats = []
+    t0 = time.perf_counter()
+    due = t0
+    pending = []
+    for (op, B), g in zip(reqs, gaps):
+        due += g
+        while time.perf_counter() < due:
+            pass
+        pending.append(srv.submit(op, B))
+    for rid in pending:
+        x, infos, lat, st = srv.poll(rid)
+        assert st == 0
+        lats.append(lat)
+    s_all = srv.stats()
+    srv.close()
+    lats.sort()
+    pct = lambda q: lats[min(len(lats) - 1, int(q * len(lats)))]
+    return {"operators": nops, "sides": list(sides), "requests": nreq, "rhs_columns": cols, "slots": slots,
+            "setup_s": setup_s, "saturated": {"requests_per_s": nreq / sat, "solves_per_s": cols / sat,
+                                              "mean_batch_columns": s_sat["mean_batch_columns"],
+                                              "p50_ms": s_sat["p50_ms"], "p99_ms": s_sat["p99_ms"]},
+            "open_loop": {"rate_per_s": lam, "p50_ms": pct(0.5), "p99_ms": pct(0.99),
+                          "mean_batch_columns": (s_all["mean_batch_columns"] * s_all["batches"] -
+                                                 s_sat["mean_batch_columns"] * s_sat["batches"]) /
+                          max(1, s_all["batches"] - s_sat["batches"])},
+            "precision": "mixed", "data": "synthetic, seeded"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -256,6 +324,15 @@ def run_ours(args):
     __graft_entry__.build()
     import paper_2601_04112_gb300 as amg
     from inputs.q1 import config_problem, seeded_rhs
+
+    if args.serve:
+        # the serving workload on its own: operators of 32^2 .. 512^2 cells,
+        # 1..64 right-hand sides per request
+        out = serving_run(amg, seed=5, sides=(32, 64, 128, 256, 512), nops=10, nreq=512, max_rhs=64)
+        if rank == 0:
+            print(json.dumps({"metric": "serving solves/s and p50/p99 latency (mixed)", "impl": "ours",
+                              "n_gpus": world, **out}), flush=True)
+        return
 
     over = {}
     if args.theta is not None:
@@ -429,6 +506,10 @@ def run_ours(args):
                "mixed": 8 * nbatch * world / tb_mix, "fp64": 8 * nbatch * world / tb_64,
                "max_iters_per_batch": {"mixed": itb_mix[0], "fp64": itb_64[0]}}
 
+    serving = None
+    if not args.no_serving:
+        serving = serving_run(amg, seed=5, sides=(64, 128, 256), nops=3, nreq=96, max_rhs=4)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle in a process of its own, single-threaded BLAS
@@ -467,7 +548,7 @@ def run_ours(args):
         "coarse_A": [c["form"] for c in stats["coarse_A"]],
         "persistent_tail_from": {"mixed": stats["tail"]["mixed"]["from"], "fp64": stats["tail"]["fp64"]["from"]},
         "roofline": roofline, "vcycle_profile_us_gbs": vprof,
-        "batched": batched,
+        "batched": batched, "serving": serving,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
         "cpu_baseline": cpu,
     }

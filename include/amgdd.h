@@ -242,6 +242,60 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes
  * captured CUDA graph counts every kernel in it).                         */
 int64_t amgdd_kernel_launches(void);
 
+/* Device bytes the hierarchy holds: what setup kept, plus the batched-solve
+ * workspace once allocated (with_batched != 0: counted even before it is,
+ * as an admission estimate).  -1 for NULL.                               */
+int64_t amgdd_device_bytes(const amgdd_hierarchy* h, int with_batched);
+
+/* ---- serving: continuous batching over cached hierarchies ------------ */
+/* A server keeps hierarchies ("operators") resident on the device within
+ * hbm_budget bytes (setup plus batched-solve workspace, amgdd_device_bytes)
+ * and solves queued requests with `slots` worker threads, each on its own
+ * stream.  A worker takes the oldest request whose operator is idle and
+ * merges the other queued requests for that operator and tolerance into one
+ * batched amgdd_solve of at most max_batch (<= 8) columns; requests that
+ * arrive meanwhile join later batches as slots free, and batches of
+ * different operators overlap on the device.  The serving workload of many
+ * grid sizes and right-hand-side counts is beyond the paper (which solves
+ * one system at a time); each result is the solve of its own right-hand
+ * side and agrees with a solve alone to CG rounding.                      */
+typedef struct amgdd_server amgdd_server; /* opaque */
+typedef struct {
+  int64_t hbm_budget;  /* device bytes for resident operators             */
+  int slots;           /* concurrent batches (worker threads)             */
+  int max_batch;       /* columns per batched solve, 1..8                 */
+} amgdd_server_params;
+
+#define AMGDD_PENDING 1 /* amgdd_server_poll: not finished yet            */
+
+/* Defaults: 64 GiB budget, 4 slots, batches of 8 columns.                 */
+amgdd_server_params amgdd_server_params_default(void);
+int amgdd_server_create(const amgdd_server_params* params, amgdd_server** out);
+/* Builds the hierarchy of (G, D1, agg, overlap, params) on the calling
+ * thread and makes it resident, evicting idle operators with no queued
+ * requests (least recently used first) to stay within the budget; OOM if it
+ * cannot fit.  `key` names the operator: adding a key that is resident
+ * returns its id with *cached = 1 and builds nothing.                     */
+int amgdd_server_add_operator(amgdd_server* s, int64_t key, const amgdd_csr* G, const double* D1,
+                              const int32_t* agg, int overlap, const amgdd_params* params, int64_t* op,
+                              int* cached);
+/* Queues a solve of nrhs columns (host buffers, column-major n x nrhs; both
+ * must stay valid until the request is polled to completion) and returns at
+ * once with the request id.  INVALID_ARG for an unknown operator or device
+ * pointers.                                                               */
+int amgdd_server_submit(amgdd_server* s, int64_t op, const double* b, int nrhs, double tol, double* x, int64_t* req);
+/* AMGDD_PENDING while queued or running (waits up to wait_ms first; < 0:
+ * until done); else the request's status, with info (nrhs entries, may be
+ * NULL) and the latency from submit to completion, and the request is
+ * forgotten.                                                              */
+int amgdd_server_poll(amgdd_server* s, int64_t req, int wait_ms, amgdd_info* info, double* latency_ms);
+/* JSON: completed requests, batches, mean columns per batch, latency
+ * p50/p99/max (ms, over every completed request), resident operators and
+ * bytes, evictions, cache hits, queue length, seconds since creation.    */
+int amgdd_server_stats(amgdd_server* s, char* json, size_t cap);
+/* Stops the workers after their current batches and frees every operator. */
+void amgdd_server_destroy(amgdd_server* s);
+
 void amgdd_free(amgdd_hierarchy* h);
 const char* amgdd_status_string(int status);
 const char* amgdd_last_error(void);

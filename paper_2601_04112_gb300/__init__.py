@@ -31,8 +31,15 @@ EXPORTED = [
     "amgdd_params_default", "amgdd_setup", "amgdd_solve", "amgdd_set_precision", "amgdd_apply",
     "amgdd_num_levels", "amgdd_level_describe", "amgdd_level_export", "amgdd_hierarchy_stats",
     "amgdd_bytes_model", "amgdd_free", "amgdd_status_string", "amgdd_last_error", "amgdd_profile_vcycle",
-    "amgdd_kernel_launches", "amgdd_apply_noalloc",
+    "amgdd_kernel_launches", "amgdd_apply_noalloc", "amgdd_device_bytes", "amgdd_server_params_default",
+    "amgdd_server_create", "amgdd_server_add_operator", "amgdd_server_submit", "amgdd_server_poll",
+    "amgdd_server_stats", "amgdd_server_destroy",
 ]
+AMGDD_PENDING = 1
+
+
+class ServerParams(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_int64), ("slots", ctypes.c_int), ("max_batch", ctypes.c_int)]
 
 
 class Csr(ctypes.Structure):
@@ -93,6 +100,21 @@ def load_library(path: str = LIB_PATH):
     lib.amgdd_profile_vcycle.argtypes = [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl), i32]
     lib.amgdd_profile_vcycle.restype = i32
     lib.amgdd_kernel_launches.restype = ctypes.c_int64
+    lib.amgdd_device_bytes.argtypes = [vp, i32]
+    lib.amgdd_device_bytes.restype = ctypes.c_int64
+    lib.amgdd_server_params_default.restype = ServerParams
+    lib.amgdd_server_create.argtypes = [ctypes.POINTER(ServerParams), ctypes.POINTER(vp)]
+    lib.amgdd_server_add_operator.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(Csr), vp, vp, i32,
+                                              ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(i32)]
+    lib.amgdd_server_submit.argtypes = [vp, ctypes.c_int64, vp, i32, dbl, vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.amgdd_server_poll.argtypes = [vp, ctypes.c_int64, i32, ctypes.POINTER(Info), ctypes.POINTER(dbl)]
+    lib.amgdd_server_stats.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.amgdd_server_destroy.argtypes = [vp]
+    lib.amgdd_server_destroy.restype = None
+    for name in ("amgdd_server_create", "amgdd_server_add_operator", "amgdd_server_submit", "amgdd_server_poll",
+                 "amgdd_server_stats"):
+        getattr(lib, name).restype = i32
     for name in ("amgdd_setup", "amgdd_solve", "amgdd_set_precision", "amgdd_apply", "amgdd_num_levels",
                  "amgdd_level_describe", "amgdd_level_export", "amgdd_hierarchy_stats", "amgdd_bytes_model"):
         getattr(lib, name).restype = i32
@@ -271,3 +293,80 @@ class Hierarchy:
         v, a = ctypes.c_double(), ctypes.c_double()
         _check(self._lib.amgdd_bytes_model(self._h, ctypes.byref(v), ctypes.byref(a)))
         return v.value, a.value
+
+    def device_bytes(self, with_batched: bool = False) -> int:
+        return int(self._lib.amgdd_device_bytes(self._h, int(bool(with_batched))))
+
+
+class Server:
+    """Continuous-batching solve server (amgdd_server_*): operators resident
+    on the device within a byte budget, requests batched per operator."""
+
+    def __init__(self, hbm_budget=None, slots=None, max_batch=None):
+        self._lib = load_library()
+        p = self._lib.amgdd_server_params_default()
+        if hbm_budget is not None:
+            p.hbm_budget = int(hbm_budget)
+        if slots is not None:
+            p.slots = int(slots)
+        if max_batch is not None:
+            p.max_batch = int(max_batch)
+        self._s = ctypes.c_void_p()
+        _check(self._lib.amgdd_server_create(ctypes.byref(p), ctypes.byref(self._s)))
+        self._bufs = {}  # request id -> (b, x, nrhs) kept alive until polled
+
+    def add_operator(self, prob, key: int, overlap: int = 1, **kw):
+        """Build (or find, by key) the hierarchy of an inputs.Problem; returns (op id, cached)."""
+        rowptr = np.ascontiguousarray(prob.rowptr, dtype=np.int64)
+        col = np.ascontiguousarray(prob.col, dtype=np.int32)
+        val = np.ascontiguousarray(prob.val, dtype=np.float64)
+        agg = np.ascontiguousarray(prob.agg, dtype=np.int32)
+        d1 = None if prob.D1 is None else np.ascontiguousarray(prob.D1, dtype=np.float64)
+        csr = Csr(len(rowptr) - 1, prob.n, len(col), rowptr.ctypes.data, col.ctypes.data, val.ctypes.data, 0)
+        prm = params(**kw)
+        op, cached = ctypes.c_int64(), ctypes.c_int()
+        _check(self._lib.amgdd_server_add_operator(self._s, int(key), ctypes.byref(csr), _ptr(d1)[0], agg.ctypes.data,
+                                                   int(overlap), ctypes.byref(prm), ctypes.byref(op),
+                                                   ctypes.byref(cached)))
+        return op.value, bool(cached.value)
+
+    def submit(self, op: int, b: np.ndarray, tol: float = 1e-8) -> int:
+        """Queue a solve (b: n or n x nrhs host array); returns the request id."""
+        b = np.asfortranarray(b, dtype=np.float64)
+        nrhs = 1 if b.ndim == 1 else b.shape[1]
+        x = np.zeros_like(b, order="F")
+        rid = ctypes.c_int64()
+        _check(self._lib.amgdd_server_submit(self._s, int(op), b.ctypes.data, nrhs, float(tol), x.ctypes.data,
+                                             ctypes.byref(rid)))
+        self._bufs[rid.value] = (b, x, nrhs)
+        return rid.value
+
+    def poll(self, rid: int, wait_ms: int = -1):
+        """None while pending; else (x, infos, latency_ms, status)."""
+        b, x, nrhs = self._bufs[rid]
+        infos = (Info * nrhs)()
+        lat = ctypes.c_double()
+        st = self._lib.amgdd_server_poll(self._s, int(rid), int(wait_ms), infos, ctypes.byref(lat))
+        if st == AMGDD_PENDING:
+            return None
+        del self._bufs[rid]
+        if st not in (0, -4, -5, -3):
+            _check(st)
+        return x, [dict(iters=i.iters, status=i.status, relres=i.relres, relres_true=i.relres_true)
+                   for i in infos], lat.value, st
+
+    def stats(self) -> dict:
+        buf = ctypes.create_string_buffer(4096)
+        _check(self._lib.amgdd_server_stats(self._s, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
+    def close(self):
+        if self._s:
+            self._lib.amgdd_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

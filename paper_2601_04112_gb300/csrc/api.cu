@@ -31,6 +31,7 @@ namespace amgdd {
 
 static thread_local std::string g_last_error;
 thread_local int* g_err_word = nullptr;
+thread_local int64_t g_alloc_bytes = 0;
 
 // Setup-time tuning context: whether to time alternatives, the problem/GPU
 // signature that keys the cache, and the cached choices (`key\tvalue` lines).
@@ -673,6 +674,8 @@ struct amgdd_hierarchy {
   cudaStream_t work = nullptr;  // solves run here (capturable, unlike the legacy stream)
   cudaEvent_t join[2] = {nullptr, nullptr};
   double setup_ms = 0.0;
+  int64_t setup_bytes = 0;  // device bytes held after setup
+  int64_t multi_bytes = 0;  // device bytes of the batched-solve workspace, once allocated
   // persistent V-cycle tail per precision (index 1 = MIXED32): phase list,
   // launch shape, first level (0 = not used); barrier words
   DBuf<PhaseDesc> d_ph[2];
@@ -1640,6 +1643,7 @@ static int kidx(int K) { return K == 2 ? 0 : (K == 4 ? 1 : 2); }
 static int ensure_multi(amgdd_hierarchy& h) {
   auto& M = h.mw;
   if (M.ready) return AMGDD_OK;
+  const int64_t bytes0 = g_alloc_bytes;
   const int64_t nk = h.n * kMaxRhs;
   for (auto* v : {&M.x, &M.r, &M.z, &M.zold, &M.p, &M.q, &M.b, &M.stage}) AMGDD_TRY(v->alloc(nk));
   AMGDD_TRY(M.partials.alloc((int64_t)kDotBlocks * 2 * kMaxRhs));
@@ -1657,7 +1661,15 @@ static int ensure_multi(amgdd_hierarchy& h) {
     AMGDD_TRY(L.ms32.alloc(lk));
   }
   M.ready = true;
+  h.multi_bytes = g_alloc_bytes - bytes0;
   return AMGDD_OK;
+}
+
+// Device bytes of the batched-solve workspace (allocated or not).
+static int64_t multi_bytes_estimate(const amgdd_hierarchy& h) {
+  int64_t b = (int64_t)8 * h.n * kMaxRhs * 8 + (int64_t)kDotBlocks * 2 * kMaxRhs * 8;
+  for (const auto& L : h.lv) b += L->n * kMaxRhs * (3 * 8 + 3 * 4);
+  return b;
 }
 
 // s = r - A x for K columns: block rows where stored, else the rows omega_i
@@ -1955,6 +1967,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
       set_error("amgdd_setup: D1 must be finite and >= 0");
       return AMGDD_ERR_NONFINITE;
     }
+  const int64_t bytes0 = g_alloc_bytes;
   std::unique_ptr<amgdd_hierarchy> H(new amgdd_hierarchy());
   H->prm = prm;
   H->overlap = overlap;
@@ -2116,6 +2129,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   AMGDD_TRY(tune_tail(*H));
   tctx.save();
   H->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  H->setup_bytes = g_alloc_bytes - bytes0;
   *out = H.release();
   return AMGDD_OK;
 }
@@ -2442,6 +2456,13 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes
 }
 
 int64_t amgdd_kernel_launches(void) { return g_kernels.load(); }
+
+int64_t amgdd_device_bytes(const amgdd_hierarchy* h, int with_batched) {
+  if (h == nullptr) return -1;
+  int64_t b = h->setup_bytes + h->multi_bytes;
+  if (with_batched && !h->mw.ready) b += multi_bytes_estimate(*h);
+  return b;
+}
 
 int amgdd_num_levels(const amgdd_hierarchy* h) { return h ? (int)h->lv.size() : 0; }
 

@@ -30,6 +30,10 @@ void set_error(const char* fmt, ...);
     if (s_ != AMGDD_OK) return s_; \
   } while (0)
 
+// Net device bytes allocated through DBuf by the calling thread (setup
+// measures a hierarchy's footprint as the change over its build).
+extern thread_local int64_t g_alloc_bytes;
+
 // Owning device buffer.
 template <class T>
 struct DBuf {
@@ -40,7 +44,10 @@ struct DBuf {
   DBuf& operator=(const DBuf&) = delete;
   ~DBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      g_alloc_bytes -= (int64_t)(n * sizeof(T) + 16);
+    }
     p = nullptr;
     n = 0;
   }
@@ -56,6 +63,7 @@ struct DBuf {
       return e == cudaErrorMemoryAllocation ? AMGDD_ERR_OOM : AMGDD_ERR_CUDA;
     }
     n = count;
+    g_alloc_bytes += (int64_t)(count * sizeof(T) + 16);
     return AMGDD_OK;
   }
   int upload(const std::vector<T>& h, cudaStream_t s) {
