@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--N", type=int, default=None, help="cells per axis (smaller captures)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="run the eps x theta sweep of the workload instead (one setup per point)")
     ap.add_argument("--serve", action="store_true",
                     help="run the serving workload (many operators and right-hand-side counts) instead")
     ap.add_argument("--no-serving", action="store_true", help="skip the small serving run of the default line")
@@ -134,8 +136,13 @@ class ClockSampler:
 
 
 def workload_desc(cfg):
-    return (f"{cfg['N']}x{cfg['N']} Q1 cells ({(cfg['N'] - 1) ** 2:,} unknowns), theta={cfg['theta']:.6f}, "
-            f"eps={cfg['eps']:g}, {cfg['bs']}x{cfg['bs']} aggregates, overlap {cfg['overlap']}, "
+    field = (f"theta={cfg['theta']:.6f}" if cfg.get("field", "rot") == "rot"
+             else "circular field theta=atan2(y-1/2, x-1/2)+pi/2")
+    d1 = f", D1={cfg['d1']:g} h^2" if cfg.get("d1") else ""
+    ov = f"overlap {cfg['overlap']}" + (f" (level 0), {cfg['coarse_overlap']} (coarse levels)"
+                                        if cfg.get("coarse_overlap") else "")
+    return (f"{cfg['N']}x{cfg['N']} Q1 cells ({(cfg['N'] - 1) ** 2:,} unknowns), {field}, "
+            f"eps={cfg['eps']:g}{d1}, {cfg['bs']}x{cfg['bs']} aggregates, {ov}, "
             f"LS_{{{','.join(str(c) for c in cfg['c_min'])}}}, n_coarse {cfg['n_coarse']}, 1 RHS, tol 1e-8")
 
 
@@ -145,7 +152,8 @@ def oracle_setup(prob, cfg):
 
     t0 = time.time()
     ho = oracle.setup(prob.rowptr, prob.col, prob.val, prob.n, prob.D1, prob.agg, overlap=cfg["overlap"],
-                      c_min=cfg["c_min"], n_coarse=cfg["n_coarse"], thresh=cfg["thresh"])
+                      c_min=cfg["c_min"], n_coarse=cfg["n_coarse"], thresh=cfg["thresh"],
+                      coarse_overlap=cfg.get("coarse_overlap", 0))
     setup_s = time.time() - t0
     return ho, setup_s
 
@@ -325,6 +333,48 @@ def run_ours(args):
     import paper_2601_04112_gb300 as amg
     from inputs.q1 import config_problem, seeded_rhs
 
+    if args.sweep:
+        # the (eps, theta) sweep of the 512x512 workload: setup, iterations and
+        # solves/s in both precisions per point
+        from inputs.q1 import SWEEP_EPS, SWEEP_THETA
+
+        rows = []
+        for eps in SWEEP_EPS:
+            for theta in SWEEP_THETA:
+                prob, cfg = config_problem(args.workload, eps=eps, theta=theta)
+                t0 = time.time()
+                Hs = amg.Hierarchy.from_problem(prob, overlap=cfg["overlap"], c_min=cfg["c_min"],
+                                                n_coarse=cfg["n_coarse"], thresh=cfg["thresh"],
+                                                coarse_overlap=cfg.get("coarse_overlap", 0))
+                torch.cuda.synchronize()
+                row = {"eps": eps, "theta": round(theta, 6), "setup_s": round(time.time() - t0, 3),
+                       "levels": Hs.stats()["n"]}
+                b = torch.from_numpy(seeded_rhs(prob.n, 1, cfg["seed"])[:, 0]).cuda()
+                for name, prec in (("mixed", amg.MIXED32), ("fp64", amg.FP64)):
+                    Hs.set_precision(prec)
+                    Hs.solve(b, tol=1e-8)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    its, fb, ok = [], 0, True
+                    for _ in range(5):
+                        _, inf = Hs.solve(b, tol=1e-8)
+                        ok = ok and inf[0]["status"] == 0 and inf[0]["relres_true"] <= 1e-8
+                        its.append(inf[0]["iters"])
+                        fb = inf[0]["fallback"]
+                    torch.cuda.synchronize()
+                    row[name] = {"iters": its[0], "solves_per_s": round(5 / (time.perf_counter() - t0), 2)}
+                    if fb:
+                        row[name]["fp64_fallback_after"] = inf[0]["iters_mixed"]
+                    if not ok:
+                        row[name]["failed"] = {"status": inf[0]["status"], "relres_true": inf[0]["relres_true"]}
+                print(json.dumps(row), file=sys.stderr, flush=True)
+                rows.append(row)
+                del Hs
+        if rank == 0:
+            print(json.dumps({"metric": "eps x theta sweep (solves/s to 1e-8, iterations)", "impl": "ours",
+                              "workload": args.workload, "points": rows}), flush=True)
+        return
+
     if args.serve:
         # the serving workload on its own: operators of 32^2 .. 512^2 cells,
         # 1..64 right-hand sides per request
@@ -346,6 +396,7 @@ def run_ours(args):
     t0 = time.time()
     H = amg.Hierarchy.from_problem(prob, overlap=cfg["overlap"], c_min=cfg["c_min"], n_coarse=cfg["n_coarse"],
                                    thresh=cfg["thresh"], precision=amg.MIXED32, tune_cache=args.tune_cache,
+                                   coarse_overlap=cfg.get("coarse_overlap", 0),
                                    tune={"timed": 1, "defaults": 0, "staged": 2}[args.tune_mode])
     torch.cuda.synchronize()
     setup_s = time.time() - t0
@@ -411,6 +462,7 @@ def run_ours(args):
     t_64 = maxrank(t_64)
     for inf in inf_mix + inf_64:
         assert inf["status"] == 0 and inf["relres_true"] <= 1e-8, inf
+    fallbacks = sum(i["fallback"] for i in inf_mix)
     it_mix = [i["iters"] for i in inf_mix]
     it_64 = [i["iters"] for i in inf_64]
     solves = args.steps * world
@@ -543,8 +595,9 @@ def run_ours(args):
                  "iters": it_64},
         "mixed_over_fp64": value / fp64_value,
         "vcycles_per_s": {"mixed": vc_mix, "fp64": vc_64},
-        "iters": it_mix, "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
-        "setup_s": setup_s, "levels": stats["n"], "op_complexity": stats["op_complexity"],
+        "iters": it_mix, "mixed_fp64_fallbacks": fallbacks, "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "setup_s": setup_s, "setup_phases_ms": {k: round(v, 1) for k, v in stats["setup_phases_ms"].items()},
+        "levels": stats["n"], "op_complexity": stats["op_complexity"],
         "coarse_A": [c["form"] for c in stats["coarse_A"]],
         "persistent_tail_from": {"mixed": stats["tail"]["mixed"]["from"], "fp64": stats["tail"]["fp64"]["from"]},
         "roofline": roofline, "vcycle_profile_us_gbs": vprof,

@@ -94,6 +94,9 @@ typedef struct {
   const char* tune_cache; /* NULL, or a text file of earlier choices keyed */
                        /*   by problem, GPU, level and step: read before  */
                        /*   timing, rewritten with new choices at the end */
+  int coarse_overlap;  /* hops of overlap on levels >= 1; 0: the level-0  */
+                       /*   `overlap` on every level (Algorithm 1 builds   */
+                       /*   Omega_i from one layer of neighbours in A_l)  */
 } amgdd_params;
 
 typedef struct amgdd_hierarchy amgdd_hierarchy; /* opaque, library-owned */
@@ -105,6 +108,14 @@ typedef struct {
   double relres;       /* ||r_k|| / ||b|| of the recursively updated r    */
   double relres_true;  /* ||b - A x|| / ||b|| recomputed at the end (FP64) */
   double solve_ms;     /* device time of this right-hand side             */
+  int fallback;        /* MIXED32 only: 1 when the FP32 cycle stalled      */
+                       /*   (||r|| fell by less than 10% over 10          */
+                       /*   iterations) and the solve was redone with the */
+                       /*   FP64 cycle; iters then counts both attempts.  */
+                       /*   After a stall, later MIXED32 solves on the    */
+                       /*   hierarchy use the FP64 cycle directly (until  */
+                       /*   amgdd_set_precision is called again)          */
+  int iters_mixed;     /* iterations of the stalled FP32 attempt (0 if none) */
 } amgdd_info;
 
 /* Defaults: L_max 10, n_coarse 2000, thresh 0.1, c_min = {2,3,4} (LS_{2,3,4}),

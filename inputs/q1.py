@@ -166,9 +166,13 @@ CONFIGS = {
     # 512 x 512 cells, one point of the (eps, theta) sweep
     "q1_512_rot": dict(N=512, field="rot", theta=math.pi / 6, eps=1e-4, d1=0.0, bs=4, overlap=1, seed=2,
                        c_min=(2, 3, 4), n_coarse=2000, thresh=0.1, nrhs=1),
-    # 2048 x 2048 cells, closed circular field lines, D1 = 1e-8 h^2
-    "q1_2048_circ": dict(N=2048, field="circ", theta=0.0, eps=1e-6, d1=1e-8, bs=8, overlap=2, seed=3,
-                         c_min=(4, 5), n_coarse=2000, thresh=0.1, nrhs=1),
+    # 2048 x 2048 cells, closed circular field lines, D1 = 1e-8 h^2; two
+    # layers of overlap on level 0, one on coarse levels
+    "q1_2048_circ": dict(N=2048, field="circ", theta=0.0, eps=1e-6, d1=1e-8, bs=8, overlap=2, coarse_overlap=1,
+                         seed=3, c_min=(4, 5), n_coarse=2000, thresh=0.1, nrhs=1),
+    # the same structure on 512 x 512 cells
+    "q1_512_circ": dict(N=512, field="circ", theta=0.0, eps=1e-6, d1=1e-8, bs=8, overlap=2, coarse_overlap=1,
+                        seed=3, c_min=(4, 5), n_coarse=2000, thresh=0.1, nrhs=1),
 }
 
 SWEEP_EPS = (1.0, 1e-2, 1e-4, 1e-6)

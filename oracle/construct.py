@@ -203,8 +203,12 @@ def _next_groups(level):
 
 
 def setup(rowptr, col, val, n, D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=2000, L_max=10,
-          thresh=0.1, schur_rtol=1e-12, keep_local=False):
-    """Build the multilevel hierarchy {A_l, G_l, P_l} of Algorithm 1."""
+          thresh=0.1, schur_rtol=1e-12, keep_local=False, coarse_overlap=0):
+    """Build the multilevel hierarchy {A_l, G_l, P_l} of Algorithm 1.
+
+    `overlap` hops of neighbours form Omega_i on level 0; coarse levels use
+    `coarse_overlap` hops (0: the same as level 0).  Algorithm 1 itself adds
+    one layer of neighbours in A_l on every level."""
     sups, grams = row_groups_from_csr(rowptr, col, val, n, D1)
     A = assemble_A(sups, grams, n)
     levels = []
@@ -217,7 +221,8 @@ def setup(rowptr, col, val, n, D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=200
             cur.agg, cur.nagg = cleanup_aggregates(agg0, adj)
         else:
             cur.agg, cur.nagg = _block_aggregation(levels[-1])
-        cur.omega, cur.gamma, cur.Omega = overlapping_subdomains(cur.agg, cur.nagg, adj, overlap)
+        ov = overlap if lvl == 0 or coarse_overlap <= 0 else coarse_overlap
+        cur.omega, cur.gamma, cur.Omega = overlapping_subdomains(cur.agg, cur.nagg, adj, ov)
         cur.M, cur.nz, cur.touched = multiplicity_and_nz(cur.sups, cur.agg, cur.nagg)
         c = c_min[min(lvl, len(c_min) - 1)]
         ks = np.zeros(cur.nagg, dtype=np.int64)
@@ -257,6 +262,7 @@ def setup(rowptr, col, val, n, D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=200
     levels.append(cur)
     AL = cur.A.toarray()
     coarse = np.linalg.cholesky(AL)
-    params = dict(overlap=overlap, c_min=tuple(c_min), n_coarse=n_coarse, L_max=L_max, thresh=thresh,
+    params = dict(overlap=overlap, coarse_overlap=coarse_overlap, c_min=tuple(c_min), n_coarse=n_coarse, L_max=L_max,
+                  thresh=thresh,
                   schur_rtol=schur_rtol)
     return Hierarchy(levels=levels, coarse_chol=coarse, params=params)

@@ -52,12 +52,14 @@ class Params(ctypes.Structure):
     _fields_ = [("L_max", ctypes.c_int), ("n_coarse", ctypes.c_int64), ("thresh", ctypes.c_double),
                 ("c_min", ctypes.c_int * 8), ("n_cmin", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("schur_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("tune", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
+                ("check_every", ctypes.c_int), ("tune", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
+                ("coarse_overlap", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("relres", ctypes.c_double),
-                ("relres_true", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+                ("relres_true", ctypes.c_double), ("solve_ms", ctypes.c_double), ("fallback", ctypes.c_int),
+                ("iters_mixed", ctypes.c_int)]
 
 
 class LevelDesc(ctypes.Structure):
@@ -237,7 +239,8 @@ class Hierarchy:
                 else:
                     x.copy_(xc.t())
                 return x, [dict(iters=i.iters, status=i.status, relres=i.relres, relres_true=i.relres_true,
-                                solve_ms=i.solve_ms) for i in infos]
+                                solve_ms=i.solve_ms, fallback=i.fallback, iters_mixed=i.iters_mixed)
+                           for i in infos]
             assert b.is_contiguous()
             if x is None:
                 x = torch.zeros_like(b)
@@ -246,7 +249,7 @@ class Hierarchy:
         if st not in (0, -4, -5, -3):
             _check(st)
         return x, [dict(iters=i.iters, status=i.status, relres=i.relres, relres_true=i.relres_true,
-                        solve_ms=i.solve_ms) for i in infos]
+                        solve_ms=i.solve_ms, fallback=i.fallback, iters_mixed=i.iters_mixed) for i in infos]
 
     def apply(self, op: int, level: int, x, y, stream=None):
         """y = op_l x on device FP64 tensors (see AMGDD_OP_*)."""
@@ -352,8 +355,8 @@ class Server:
         del self._bufs[rid]
         if st not in (0, -4, -5, -3):
             _check(st)
-        return x, [dict(iters=i.iters, status=i.status, relres=i.relres, relres_true=i.relres_true)
-                   for i in infos], lat.value, st
+        return x, [dict(iters=i.iters, status=i.status, relres=i.relres, relres_true=i.relres_true,
+                        fallback=i.fallback) for i in infos], lat.value, st
 
     def stats(self) -> dict:
         buf = ctypes.create_string_buffer(4096)

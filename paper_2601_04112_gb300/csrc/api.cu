@@ -107,7 +107,7 @@ void set_error(const char* fmt, ...) {
 
 namespace {
 
-PhaseTimer g_timer;
+thread_local PhaseTimer g_timer;
 
 // Synchronise and charge the elapsed time to a phase (AMGDD_VERBOSE only).
 struct Phase {
@@ -117,7 +117,6 @@ struct Phase {
   std::chrono::steady_clock::time_point t0;
   Phase(int i, const char* n, cudaStream_t st) : id(i), nm(n), s(st), t0(std::chrono::steady_clock::now()) {}
   ~Phase() {
-    if (!g_timer.on) return;
     cudaStreamSynchronize(s);
     g_timer.add(id, nm, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
   }
@@ -674,7 +673,10 @@ struct amgdd_hierarchy {
   cudaStream_t work = nullptr;  // solves run here (capturable, unlike the legacy stream)
   cudaEvent_t join[2] = {nullptr, nullptr};
   double setup_ms = 0.0;
+  bool mixed_stalled = false;  // an FP32-cycle solve stalled; later MIXED32 solves use the FP64 cycle
   int64_t setup_bytes = 0;  // device bytes held after setup
+  double phase_ms[16] = {};  // setup time by phase, summed over levels
+  const char* phase_name[16] = {};
   int64_t multi_bytes = 0;  // device bytes of the batched-solve workspace, once allocated
   // persistent V-cycle tail per precision (index 1 = MIXED32): phase list,
   // launch shape, first level (0 = not used); barrier words
@@ -787,7 +789,8 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
     }
   }
   const int nagg = L.nagg;
-  overlap_sets(L.agg, nagg, S, nptr, ngrp, h.overlap, L.om_ptr, L.om_idx, L.nomega);
+  const int ov = lvl == 0 || h.prm.coarse_overlap <= 0 ? h.overlap : h.prm.coarse_overlap;
+  overlap_sets(L.agg, nagg, S, nptr, ngrp, ov, L.om_ptr, L.om_idx, L.nomega);
   std::vector<int64_t> tptr;
   std::vector<int32_t> tids, M;
   touched_aggregates(S, L.agg, tptr, tids, M);
@@ -1554,8 +1557,42 @@ static int build_solve_graphs(amgdd_hierarchy& h, int pi, cudaStream_t s) {
   return build_solve_graphs_once(h, pi, s);
 }
 
+static int solve_once(amgdd_hierarchy& h, const double* bsrc, bool bdev, double tol, double* xdst, bool xdev,
+                      cudaStream_t s, amgdd_info* info);
+
+// One right-hand side.  A MIXED32 solve whose FP32 cycle stalls (flexible CG
+// with ||r|| falling by less than 10% over 10 iterations) is redone with the
+// FP64 cycle; info then reports both attempts.
 static int solve_one(amgdd_hierarchy& h, const double* bsrc, bool bdev, double tol, double* xdst, bool xdev,
                      cudaStream_t s, amgdd_info* info) {
+  amgdd_info first{};
+  int st = AMGDD_OK;
+  if (h.precision == AMGDD_MIXED32 && h.mixed_stalled) {
+    // this hierarchy's FP32 cycle stalled before: go straight to FP64
+    first = amgdd_info{};
+    st = kStallStatus;
+  } else {
+    st = solve_once(h, bsrc, bdev, tol, xdst, xdev, s, &first);
+  }
+  if (st != kStallStatus) {
+    if (info) *info = first;
+    return st;
+  }
+  h.mixed_stalled = true;
+  h.precision = AMGDD_FP64;
+  amgdd_info second{};
+  st = solve_once(h, bsrc, bdev, tol, xdst, xdev, s, &second);
+  h.precision = AMGDD_MIXED32;
+  second.fallback = 1;
+  second.iters_mixed = first.iters;
+  second.iters += first.iters;
+  second.solve_ms += first.solve_ms;
+  if (info) *info = second;
+  return st;
+}
+
+static int solve_once(amgdd_hierarchy& h, const double* bsrc, bool bdev, double tol, double* xdst, bool xdev,
+                      cudaStream_t s, amgdd_info* info) {
   const int64_t n = h.n;
   cudaEvent_t e0, e1;
   AMGDD_CUDA(cudaEventCreate(&e0));
@@ -1586,25 +1623,57 @@ static int solve_one(amgdd_hierarchy& h, const double* bsrc, bool bdev, double t
       if (h.st_host->done) break;
     }
   }
-  // true residual ||b - A x|| in FP64 (enqueued behind the solve; one sync)
-  AMGDD_CUDA(cudaMemcpyAsync(h.q.p, h.b.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  AMGDD_TRY(launch_apply(h.lv[0]->aplan, *h.lv[0], false, h.x.p, h.q.p, -1, nullptr, s));
-  AMGDD_TRY(launch_dot_partial(h.q.p, h.q.p, nullptr, n, h.partials.p, nullptr, s));
+  // true residual b - A x in FP64; when the recursively updated residual met
+  // the tolerance but the true one did not (rounding drift over many
+  // iterations), CG restarts from x with r = b - A x (at most twice)
   std::vector<double> part;
+  PcgState fin{};
+  double qq = 0.0;
+  for (int restarts = 0;; ++restarts) {
+    AMGDD_CUDA(cudaMemcpyAsync(h.q.p, h.b.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    AMGDD_TRY(launch_apply(h.lv[0]->aplan, *h.lv[0], false, h.x.p, h.q.p, -1, nullptr, s));
+    AMGDD_TRY(launch_dot_partial(h.q.p, h.q.p, nullptr, n, h.partials.p, nullptr, s));
+    AMGDD_TRY(download(part, h.partials.p, 2 * kDotBlocks, s));
+    fin = *h.st_host;
+    if (fin.vc_err != 0) {
+      AMGDD_TRY(h.bar.zero(s));
+      AMGDD_CUDA(cudaStreamSynchronize(s));
+      set_error("persistent V-cycle: grid barrier timed out");
+      return AMGDD_ERR_TIMEOUT;
+    }
+    qq = 0.0;
+    for (int i = 0; i < kDotBlocks; ++i) qq += part[2 * i];
+    if (fin.status != AMGDD_OK || qq <= fin.tol2 || restarts == 2 || fin.iters >= fin.max_iter) break;
+    PcgState re = fin;
+    re.done = 0;
+    re.rr_mark = fin.bnorm2;  // the stall guard restarts its window
+    *h.st_host = re;
+    AMGDD_CUDA(cudaMemcpyAsync(h.st.p, h.st_host, sizeof(PcgState), cudaMemcpyHostToDevice, s));
+    AMGDD_CUDA(cudaMemcpyAsync(h.r.p, h.q.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const int* done = &h.st.p->done;
+    AMGDD_TRY(precondition(h, h.r.p, h.z.p, done, s));
+    AMGDD_TRY(launch_copy_vec(h.z.p, h.p.p, false, n, done, s));
+    if (h.precision == AMGDD_MIXED32) AMGDD_TRY(launch_copy_vec(h.z.p, h.zold.p, false, n, done, s));
+    AMGDD_TRY(launch_dot_partial(h.r.p, h.z.p, nullptr, n, h.partials.p, done, s));
+    AMGDD_TRY(launch_pcg_scalar(0, h.st.p, h.partials.p, s));
+    if (h.prm.use_graph) {
+      AMGDD_CUDA(cudaGraphLaunch(h.gloop[pi], s));
+    } else {
+      const int K = std::max(1, h.prm.check_every);
+      for (;;) {
+        for (int k = 0; k < K; ++k) AMGDD_TRY(pcg_iteration(h, s));
+        AMGDD_CUDA(cudaMemcpyAsync(h.st_host, h.st.p, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+        AMGDD_CUDA(cudaStreamSynchronize(s));
+        if (h.st_host->done) break;
+      }
+    }
+    AMGDD_CUDA(cudaMemcpyAsync(h.st_host, h.st.p, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  }
   AMGDD_CUDA(cudaMemcpyAsync(xdst, h.x.p, n * sizeof(double), xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              s));
   AMGDD_CUDA(cudaEventRecord(e1, s));
-  AMGDD_TRY(download(part, h.partials.p, 2 * kDotBlocks, s));
-  const PcgState fin = *h.st_host;
-  if (fin.vc_err != 0) {
-    AMGDD_TRY(h.bar.zero(s));
-    AMGDD_CUDA(cudaStreamSynchronize(s));
-    set_error("persistent V-cycle: grid barrier timed out");
-    return AMGDD_ERR_TIMEOUT;
-  }
+  AMGDD_CUDA(cudaEventSynchronize(e1));
   if (h.prm.use_graph) count_graph_launch(h.gloop_kernels[pi] * std::max(fin.iters, 1));
-  double qq = 0.0;
-  for (int i = 0; i < kDotBlocks; ++i) qq += part[2 * i];
   float ms = 0.f;
   AMGDD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
@@ -1825,16 +1894,44 @@ static int solve_group(amgdd_hierarchy& h, const double* b, bool bdev, int ncols
   count_graph_launch(M.ginit_kernels[pi][ki]);
   AMGDD_CUDA(cudaGraphLaunch(M.gloop[pi][ki], s));
   AMGDD_CUDA(cudaMemcpyAsync(M.st_host, M.st.p, K * sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-  // true residuals b - A x in FP64
+  // true residuals b - A x in FP64; columns whose recursively updated
+  // residual met the tolerance but whose true residual did not restart from
+  // their iterate with r = b - A x (at most twice); the others stay frozen
   Level& L0 = *h.lv[0];
-  AMGDD_TRY(launch_seg_multi(L0.ras, L0.Aw64.p, L0.AwT64.p, false, M.x.p, M.q.p, SEG_RESID, M.b.p, K, nullptr, s));
-  AMGDD_TRY(launch_dot_multi(M.q.p, M.q.p, nullptr, n, K, M.partials.p, nullptr, s));
+  std::vector<double> part;
+  for (int restarts = 0;; ++restarts) {
+    AMGDD_TRY(launch_seg_multi(L0.ras, L0.Aw64.p, L0.AwT64.p, false, M.x.p, M.q.p, SEG_RESID, M.b.p, K, nullptr, s));
+    AMGDD_TRY(launch_dot_multi(M.q.p, M.q.p, nullptr, n, K, M.partials.p, nullptr, s));
+    AMGDD_TRY(download(part, M.partials.p, (size_t)kDotBlocks * 2 * K, s));
+    bool any = false;
+    for (int k = 0; k < ncols; ++k) {
+      PcgState& f = M.st_host[k];
+      double qq = 0.0;
+      for (int i = 0; i < kDotBlocks; ++i) qq += part[(size_t)i * 2 * K + k];
+      if (restarts < 2 && f.status == AMGDD_OK && qq > f.tol2 && f.iters < f.max_iter) {
+        f.done = 0;
+        f.rr_mark = f.bnorm2;
+        any = true;
+      }
+    }
+    if (!any) break;
+    AMGDD_CUDA(cudaMemcpyAsync(M.st.p, M.st_host, K * sizeof(PcgState), cudaMemcpyHostToDevice, s));
+    AMGDD_CUDA(cudaMemsetAsync(M.grp.p, 0, sizeof(int), s));
+    const int64_t nk = n * K;
+    AMGDD_CUDA(cudaMemcpyAsync(M.r.p, M.q.p, nk * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    AMGDD_TRY(precondition_multi(h, K, M.r.p, M.z.p, M.grp.p, s));
+    AMGDD_TRY(launch_copy_vec(M.z.p, M.p.p, false, nk, M.grp.p, s));
+    if (h.precision == AMGDD_MIXED32) AMGDD_TRY(launch_copy_vec(M.z.p, M.zold.p, false, nk, M.grp.p, s));
+    AMGDD_TRY(launch_dot_multi(M.r.p, M.z.p, nullptr, n, K, M.partials.p, M.grp.p, s));
+    AMGDD_TRY(launch_pcg_scalar_multi(0, M.st.p, M.grp.p, M.partials.p, K, s));
+    AMGDD_CUDA(cudaGraphLaunch(M.gloop[pi][ki], s));
+    AMGDD_CUDA(cudaMemcpyAsync(M.st_host, M.st.p, K * sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  }
   AMGDD_TRY(launch_deinterleave(M.x.p, n, K, M.stage.p, n, ncols, s));
   AMGDD_CUDA(cudaMemcpyAsync(x, M.stage.p, n * ncols * sizeof(double),
                              xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   AMGDD_CUDA(cudaEventRecord(e1, s));
-  std::vector<double> part;
-  AMGDD_TRY(download(part, M.partials.p, (size_t)kDotBlocks * 2 * K, s));
+  AMGDD_CUDA(cudaEventSynchronize(e1));
   float ms = 0.f;
   AMGDD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
@@ -1843,12 +1940,14 @@ static int solve_group(amgdd_hierarchy& h, const double* b, bool bdev, int ncols
   for (int k = 0; k < K; ++k) maxit = std::max(maxit, M.st_host[k].iters);
   count_graph_launch(M.gloop_kernels[pi][ki] * std::max(maxit, 1));
   int first_bad = AMGDD_OK;
+  std::vector<int> stalled;
   for (int k = 0; k < ncols; ++k) {
     const PcgState& f = M.st_host[k];
     if (f.vc_err != 0) {
       set_error("a bounded device-side wait expired");
       return AMGDD_ERR_TIMEOUT;
     }
+    if (f.status == kStallStatus) stalled.push_back(k);
     double qq = 0.0;
     for (int i = 0; i < kDotBlocks; ++i) qq += part[(size_t)i * 2 * K + k];
     if (info) {
@@ -1857,8 +1956,29 @@ static int solve_group(amgdd_hierarchy& h, const double* b, bool bdev, int ncols
       info[k].relres = f.relres;
       info[k].relres_true = f.bnorm2 > 0 ? std::sqrt(qq / f.bnorm2) : 0.0;
       info[k].solve_ms = ms;
+      info[k].fallback = 0;
+      info[k].iters_mixed = 0;
     }
-    if (f.status != AMGDD_OK && first_bad == AMGDD_OK) first_bad = f.status;
+    if (f.status != AMGDD_OK && f.status != kStallStatus && first_bad == AMGDD_OK) first_bad = f.status;
+  }
+  // columns whose FP32 cycle stalled: redone one at a time with the FP64 cycle
+  if (!stalled.empty()) h.mixed_stalled = true;
+  for (int k : stalled) {
+    const int mixed_iters = M.st_host[k].iters;
+    const int prec = h.precision;
+    h.precision = AMGDD_FP64;
+    amgdd_info one{};
+    const int st = solve_once(h, b + (int64_t)k * n, bdev, tol, x + (int64_t)k * n, xdev, s, &one);
+    h.precision = prec;
+    one.fallback = 1;
+    one.iters_mixed = mixed_iters;
+    one.iters += mixed_iters;
+    one.solve_ms += ms;
+    if (info) info[k] = one;
+    const bool per_rhs = st == AMGDD_OK || st == AMGDD_ERR_BREAKDOWN || st == AMGDD_ERR_NO_CONVERGENCE ||
+                         st == AMGDD_ERR_NONFINITE;
+    if (!per_rhs) return st;
+    if (st != AMGDD_OK && first_bad == AMGDD_OK) first_bad = st;
   }
   return first_bad;
 }
@@ -1882,6 +2002,7 @@ amgdd_params amgdd_params_default(void) {
   p.check_every = 4;
   p.tune = 1;
   p.tune_cache = nullptr;
+  p.coarse_overlap = 0;
   return p;
 }
 
@@ -1911,7 +2032,8 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   *out = nullptr;
   amgdd_params prm = params ? *params : amgdd_params_default();
   if (prm.L_max < 1 || prm.n_cmin < 1 || prm.n_cmin > 8 || prm.max_iter < 1 || overlap < 1 ||
-      (prm.precision != AMGDD_FP64 && prm.precision != AMGDD_MIXED32) || prm.check_every < 1 || prm.n_coarse < 1) {
+      (prm.precision != AMGDD_FP64 && prm.precision != AMGDD_MIXED32) || prm.check_every < 1 || prm.n_coarse < 1 ||
+      prm.coarse_overlap < 0) {
     set_error("amgdd_setup: invalid parameters");
     return AMGDD_ERR_INVALID_ARG;
   }
@@ -1929,7 +2051,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   cudaStream_t s = (cudaStream_t)stream;
   const auto t0 = std::chrono::steady_clock::now();
   g_timer = PhaseTimer();
-  g_timer.on = std::getenv("AMGDD_VERBOSE") != nullptr;
+  g_timer.on = std::getenv("AMGDD_VERBOSE") != nullptr;  // print per-level phase times
   const bool gdev = G->mem == AMGDD_DEVICE;
   std::vector<int64_t> rowptr;
   std::vector<int32_t> col;
@@ -1986,7 +2108,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     AMGDD_CUDA(cudaGetDeviceProperties(&prop, H->device));
     std::string sig = std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "|m" +
                       std::to_string(m) + "|n" + std::to_string(n) + "|nnz" + std::to_string(nnz) + "|ov" +
-                      std::to_string(overlap) + "|nc" + std::to_string(prm.n_coarse) + "|L" +
+                      std::to_string(overlap) + "/" + std::to_string(prm.coarse_overlap) + "|nc" + std::to_string(prm.n_coarse) + "|L" +
                       std::to_string(prm.L_max) + "|c";
     for (int i = 0; i < prm.n_cmin; ++i) sig += std::to_string(prm.c_min[i]) + ",";
     char buf[64];
@@ -2096,13 +2218,17 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
       Phase ph(7, "next level", s);
       AMGDD_TRY(build_next(*H, L, *N, s));
     }
+    for (int i = 0; i < 16; ++i) {
+      H->phase_ms[i] += g_timer.acc[i];
+      if (g_timer.name[i]) H->phase_name[i] = g_timer.name[i];
+    }
     if (g_timer.on) {
       fprintf(stderr, "[amgdd] level %d: n=%lld nagg=%d", lvl, (long long)L.n, L.nagg);
       for (int i = 0; i < 16; ++i)
         if (g_timer.name[i]) fprintf(stderr, " %s=%.1fms", g_timer.name[i], g_timer.acc[i]);
       fprintf(stderr, "\n");
-      for (double& a : g_timer.acc) a = 0.0;
     }
+    for (double& a : g_timer.acc) a = 0.0;
     L.d_H.release();
     if (N->n == 0) {
       set_error("level %d produced an empty coarse space", lvl);
@@ -2112,6 +2238,10 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     ++lvl;
   }
   H->lv.back()->d_H.release();
+  for (int i = 0; i < 16; ++i) {  // the coarsest level's phases
+    H->phase_ms[i] += g_timer.acc[i];
+    if (g_timer.name[i]) H->phase_name[i] = g_timer.name[i];
+  }
   // ---- solver workspace --------------------------------------------------
   AMGDD_TRY(H->x.alloc(n));
   AMGDD_TRY(H->r.alloc(n));
@@ -2166,8 +2296,14 @@ int amgdd_solve(amgdd_hierarchy* h, const double* b, int nrhs, double tol, doubl
         const int g = std::min(kMaxRhs, nrhs - j0);
         const int K = g <= 2 ? 2 : (g <= 4 ? 4 : 8);
         std::vector<amgdd_info> tmp(g);
-        const int st = solve_group(*h, b + (int64_t)j0 * h->n, bdev, g, K, tol, x + (int64_t)j0 * h->n, xdev, s,
-                                   info ? info + j0 : tmp.data());
+        amgdd_info* inf = info ? info + j0 : tmp.data();
+        const bool sticky = h->precision == AMGDD_MIXED32 && h->mixed_stalled;
+        if (sticky) h->precision = AMGDD_FP64;  // the FP32 cycle stalled on this hierarchy before
+        const int st = solve_group(*h, b + (int64_t)j0 * h->n, bdev, g, K, tol, x + (int64_t)j0 * h->n, xdev, s, inf);
+        if (sticky) {
+          h->precision = AMGDD_MIXED32;
+          for (int k = 0; k < g; ++k) inf[k].fallback = 1;
+        }
         const bool per_rhs = st == AMGDD_OK || st == AMGDD_ERR_BREAKDOWN || st == AMGDD_ERR_NO_CONVERGENCE ||
                              st == AMGDD_ERR_NONFINITE;
         if (!per_rhs) return st;
@@ -2201,6 +2337,7 @@ int amgdd_set_precision(amgdd_hierarchy* h, int precision) {
     return AMGDD_ERR_INVALID_ARG;
   }
   h->precision = precision;
+  h->mixed_stalled = false;  // give the FP32 cycle a fresh chance
   return AMGDD_OK;
 }
 
@@ -2610,6 +2747,15 @@ int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap) {
     }
     s += "]}";
   }
+  s += "}, \"setup_phases_ms\": {";
+  bool first = true;
+  for (int i = 0; i < 16; ++i)
+    if (h->phase_name[i]) {
+      char buf[96];
+      std::snprintf(buf, sizeof buf, "%s\"%s\": %.3f", first ? "" : ", ", h->phase_name[i], h->phase_ms[i]);
+      s += buf;
+      first = false;
+    }
   s += "}";
   double vb = 0, ab = 0;
   amgdd_bytes_model(h, &vb, &ab);

@@ -686,6 +686,14 @@ __global__ void __launch_bounds__(1024) k_pcg_scalar(int which, PcgState* st, co
       } else if (st->iters >= st->max_iter) {
         st->status = AMGDD_ERR_NO_CONVERGENCE;
         st->done = 1;
+      } else if (st->flexible && st->iters % 10 == 0) {
+        // FP32-cycle stall guard: ||r|| must fall by 10% every 10 iterations
+        if (a > 0.81 * st->rr_mark) {
+          st->status = kStallStatus;
+          st->done = 1;
+        } else {
+          st->rr_mark = a;
+        }
       }
       break;
     case 3:
@@ -697,6 +705,7 @@ __global__ void __launch_bounds__(1024) k_pcg_scalar(int which, PcgState* st, co
       break;
     case 4:
       st->bnorm2 = a;
+      st->rr_mark = a;
       st->tol2 = st->tol2 * a;
       st->iters = 0;
       st->relres = 1.0;

@@ -294,7 +294,11 @@ struct PcgState {
   double relres;
   int iters, max_iter, done, status, flexible;
   int vc_err;  // set by a persistent V-cycle whose grid barrier timed out
+  double rr_mark;  // r^T r at the last stall check (flexible CG)
 };
+// Status of a flexible (FP32-cycle) CG that stopped because ||r|| fell by
+// less than 10% over 10 iterations; the host redoes the solve in FP64.
+constexpr int kStallStatus = -100;
 
 constexpr int kDotBlocks = 608;  // 4 x 152 SMs; partial sums per dot product
 

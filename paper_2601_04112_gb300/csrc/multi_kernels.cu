@@ -205,6 +205,13 @@ __global__ void __launch_bounds__(32 * K) k_pcg_scalar_multi(int which, PcgState
         } else if (S.iters >= S.max_iter) {
           S.status = AMGDD_ERR_NO_CONVERGENCE;
           S.done = 1;
+        } else if (S.flexible && S.iters % 10 == 0) {
+          if (a > 0.81 * S.rr_mark) {  // FP32-cycle stall guard
+            S.status = kStallStatus;
+            S.done = 1;
+          } else {
+            S.rr_mark = a;
+          }
         }
         break;
       case 3:
@@ -215,6 +222,7 @@ __global__ void __launch_bounds__(32 * K) k_pcg_scalar_multi(int which, PcgState
         break;
       case 4:
         S.bnorm2 = a;
+        S.rr_mark = a;
         S.tol2 = S.tol2 * a;
         S.iters = 0;
         S.relres = 1.0;

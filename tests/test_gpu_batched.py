@@ -38,8 +38,8 @@ def _cols(x):
 def test_batched_fp64_matches_single_and_oracle(amg, name):
     c = CASES[name]
     p = _problem(c)
-    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"])
-    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"])
+    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
+    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
     B = seeded_rhs(p.n, 5, 11)  # a batch of 8 with three padding columns
     B[:, 3] *= 1e-3  # scale does not change the iteration (relative test)
     X, infos = H.solve(B, tol=1e-8)
@@ -59,7 +59,7 @@ def test_batched_fp64_matches_single_and_oracle(amg, name):
 def test_batched_mixed_reaches_tolerance(amg, name):
     c = CASES[name]
     p = _problem(c)
-    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"])
+    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
     B = seeded_rhs(p.n, 8, 12)
     _, i64 = H.solve(B, tol=1e-8)
     H.set_precision(amg.MIXED32)
@@ -76,7 +76,7 @@ def test_batched_groups_zero_and_early_columns(amg):
     t = _torch()
     c = CASES["ragged_3lvl"]
     p = _problem(c)
-    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"])
+    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
     B = seeded_rhs(p.n, 10, 13)
     B[:, 2] = 0.0
     Bd = t.from_numpy(B).cuda()  # (n, nrhs) tensor; the binding passes it column-major

@@ -26,7 +26,7 @@ import numpy as np
 import pytest
 
 import oracle
-from inputs import block_aggregates_2d, q1_2d, rotated_sqrtK, seeded_rhs
+from inputs import block_aggregates_2d, circular_sqrtK, q1_2d, rotated_sqrtK, seeded_rhs
 from inputs.q1 import config_problem
 
 pytestmark = pytest.mark.gpu
@@ -49,14 +49,14 @@ def _torch():
     return torch
 
 
-def _oracle(p, overlap, c_min, n_coarse, L_max=10, thresh=0.1):
+def _oracle(p, overlap, c_min, n_coarse, L_max=10, thresh=0.1, coarse_overlap=0):
     return oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, overlap=overlap, c_min=c_min, n_coarse=n_coarse,
-                        L_max=L_max, thresh=thresh, keep_local=True)
+                        L_max=L_max, thresh=thresh, keep_local=True, coarse_overlap=coarse_overlap)
 
 
-def _gpu(amg, p, overlap, c_min, n_coarse, L_max=10, thresh=0.1, precision=0):
+def _gpu(amg, p, overlap, c_min, n_coarse, L_max=10, thresh=0.1, precision=0, coarse_overlap=0):
     return amg.Hierarchy.from_problem(p, overlap=overlap, c_min=c_min, n_coarse=n_coarse, L_max=L_max, thresh=thresh,
-                                      precision=precision)
+                                      precision=precision, coarse_overlap=coarse_overlap)
 
 
 def _dev(x):
@@ -151,6 +151,14 @@ CASES = {
     # aggregate covering every dof): cluster-team Cholesky / Schur and the
     # tridiagonal + QL eigensolver path
     "large_blocks": dict(N=40, theta=0.7, eps=1e-2, bs=8, overlap=1, c_min=(2,), n_coarse=200),
+    # the 2048x2048 circular workload's structure at 32x32: closed circular
+    # field lines, eps = 1e-6, D1 = 1e-8 h^2, 8x8 aggregates, two layers of
+    # overlap on level 0 and one above.  Its level-0 blocks reach
+    # kappa(A_i) ~ 1e6; the explicit inverse rows the GPU applies and the
+    # oracle's Cholesky solves then agree to ~kappa * eps_machine ~ 3e-10, so
+    # its V-cycle bound is 1e-10 instead of 1e-12.
+    "circ_ov2": dict(N=32, circ=True, eps=1e-6, bs=8, overlap=2, coarse_overlap=1, c_min=(4, 5), n_coarse=60,
+                     d1=1e-8 / 32 ** 2, tol_vcycle=1e-10),
 }
 
 
@@ -159,15 +167,16 @@ def _problem(c):
     D1 = None
     if c.get("d1"):
         D1 = np.full((N - 1) ** 2, c["d1"])
-    return q1_2d(N, rotated_sqrtK(c["theta"], c["eps"]), D1=D1, agg=block_aggregates_2d(N, c["bs"]))
+    K = circular_sqrtK(c["eps"]) if c.get("circ") else rotated_sqrtK(c["theta"], c["eps"])
+    return q1_2d(N, K, D1=D1, agg=block_aggregates_2d(N, c["bs"]))
 
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_structure_and_spectra(amg, name):
     c = CASES[name]
     p = _problem(c)
-    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"])
-    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"])
+    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
+    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
     _check_structure(amg, H, ho)
     for lvl in range(len(ho.levels) - 1):
         _check_spectra(amg, H, ho, lvl)
@@ -177,8 +186,8 @@ def test_structure_and_spectra(amg, name):
 def test_level_operators_fp64(amg, name):
     c = CASES[name]
     p = _problem(c)
-    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"])
-    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"])
+    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
+    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
     rng = np.random.default_rng(11)
     for lvl, Lo in enumerate(ho.levels[:-1]):
         x = rng.standard_normal(Lo.n)
@@ -200,7 +209,8 @@ def test_level_operators_fp64(amg, name):
             om = Lo.omega[i]
             assert np.abs(y[om] - yo[om]).max() <= tP * np.abs(yo).max(), (lvl, i)
         v = _apply(amg, H, amg.OP_VCYCLE, lvl, x, Lo.n)
-        assert _rel(v, oracle.vcycle(ho, x, lvl)) <= 1e-12, (lvl, _rel(v, oracle.vcycle(ho, x, lvl)))
+        tV = c.get("tol_vcycle", 1e-12)
+        assert _rel(v, oracle.vcycle(ho, x, lvl)) <= tV, (lvl, _rel(v, oracle.vcycle(ho, x, lvl)))
     Lc = ho.levels[-1]
     xc = rng.standard_normal(Lc.n)
     ref = np.linalg.solve(Lc.A.toarray(), xc)
@@ -213,8 +223,8 @@ def test_level_operators_fp64(amg, name):
 def test_pcg_fp64_matches_oracle(amg, name):
     c = CASES[name]
     p = _problem(c)
-    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"])
-    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"])
+    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
+    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
     b = seeded_rhs(p.n, 1, 1)[:, 0]
     xo, io = oracle.pcg(ho, b, tol=1e-8)
     xg, ig = H.solve(b, tol=1e-8)
@@ -228,7 +238,7 @@ def test_pcg_fp64_matches_oracle(amg, name):
 def test_pcg_mixed_reaches_tolerance(amg, name):
     c = CASES[name]
     p = _problem(c)
-    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"])
+    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
     b = seeded_rhs(p.n, 1, 1)[:, 0]
     _, i64 = H.solve(b, tol=1e-8)
     H.set_precision(amg.MIXED32)
@@ -242,7 +252,7 @@ def test_multi_rhs_device_buffers_and_zero_rhs(amg):
     t = _torch()
     c = CASES["ragged_3lvl"]
     p = _problem(c)
-    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"])
+    H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
     B = seeded_rhs(p.n, 3, 4)
     B[:, 1] = 0.0
     bd = t.from_numpy(np.ascontiguousarray(B.T)).cuda()  # column-major n x 3 == row-major 3 x n
@@ -287,3 +297,23 @@ def test_invalid_inputs_rejected(amg):
     assert e.value.status == -3
     with pytest.raises(amg.AmgddError):
         amg.Hierarchy(p.rowptr, p.col, p.val, p.n, agg=p.agg, overlap=0)
+
+
+def test_mixed_stall_falls_back_to_fp64(amg):
+    """A grid-aligned eps = 1e-6 problem on 256x256 cells needs ~150 FP64
+    iterations; there the FP32 cycle stalls the flexible CG.  The solve
+    notices (||r|| falls by less than 10% over 10 iterations), redoes the
+    right-hand side with the FP64 cycle, reaches 1e-8 and reports both."""
+    p, cfg = config_problem("q1_512_rot", N=256, eps=1e-6, theta=0.0)
+    H = amg.Hierarchy.from_problem(p, overlap=1, c_min=cfg["c_min"], n_coarse=cfg["n_coarse"])
+    b = seeded_rhs(p.n, 2, 1)
+    _, i64 = H.solve(np.ascontiguousarray(b[:, 0]), tol=1e-8)
+    H.set_precision(amg.MIXED32)
+    _, i32 = H.solve(np.ascontiguousarray(b[:, 0]), tol=1e-8)
+    assert i32[0]["status"] == 0 and i32[0]["relres_true"] <= 1e-8
+    if i32[0]["fallback"]:
+        assert i32[0]["iters_mixed"] >= 10 and i32[0]["iters"] == i32[0]["iters_mixed"] + i64[0]["iters"]
+    # batched: every column reaches the tolerance, stalled ones through FP64
+    X, ib = H.solve(b, tol=1e-8)
+    for inf in ib:
+        assert inf["status"] == 0 and inf["relres_true"] <= 1e-8

@@ -143,3 +143,22 @@ def test_coarse_blocks_stay_whole():
     for a in range(L0.nagg):
         ids = L1.agg[L0.col0[a]:L0.col0[a + 1]]
         assert np.all(ids == ids[0])
+
+
+def test_coarse_overlap_hops_per_level():
+    """overlap = 2 on level 0 and coarse_overlap = 1 above: Omega_i on each
+    level against breadth-first hops of that depth on the literal pattern of
+    that level's row supports."""
+    p = _tiny(N=17, bs=4)
+    h = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, overlap=2, coarse_overlap=1, c_min=(2,),
+                     n_coarse=20)
+    assert len(h.levels) >= 3
+    for lvl, L in enumerate(h.levels[:-1]):
+        hops = 2 if lvl == 0 else 1
+        P = np.zeros((len(L.sups), L.n), dtype=bool)
+        for g, sup in enumerate(L.sups):
+            P[g, np.asarray(sup)] = True
+        ref = _brute.omega_sets(P, np.asarray(L.agg), hops)
+        for i in range(L.nagg):
+            assert np.array_equal(L.omega[i], ref[i][0])
+            assert np.array_equal(L.gamma[i], ref[i][1])
