@@ -136,6 +136,11 @@ class ClockSampler:
 
 
 def workload_desc(cfg):
+    if cfg.get("dim", 2) == 3:
+        return (f"{cfg['N']}^3 Q1 hexahedral cells ({(cfg['N'] - 1) ** 3:,} unknowns), K = eps I + (1-eps) b b^T with "
+                f"b a smooth seeded Fourier field, eps={cfg['eps']:g}, greedy strength-graph aggregates "
+                f"(theta {cfg.get('soc', 0.03)}), overlap {cfg['overlap']}, "
+                f"LS_{{{','.join(str(c) for c in cfg['c_min'])}}}, n_coarse {cfg['n_coarse']}, 1 RHS, tol 1e-8")
     field = (f"theta={cfg['theta']:.6f}" if cfg.get("field", "rot") == "rot"
              else "circular field theta=atan2(y-1/2, x-1/2)+pi/2")
     d1 = f", D1={cfg['d1']:g} h^2" if cfg.get("d1") else ""

@@ -16,3 +16,4 @@ from .q1 import (  # noqa: F401
     circular_sqrtK,
     config_problem,
 )
+from .q1_3d import q1_3d, field_sqrtK, strength_graph, greedy_aggregates  # noqa: F401

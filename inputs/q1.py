@@ -173,6 +173,13 @@ CONFIGS = {
     # the same structure on 512 x 512 cells
     "q1_512_circ": dict(N=512, field="circ", theta=0.0, eps=1e-6, d1=1e-8, bs=8, overlap=2, coarse_overlap=1,
                         seed=3, c_min=(4, 5), n_coarse=2000, thresh=0.1, nrhs=1),
+    # 3D: 128^3 hexahedral cells, K = eps I + (1 - eps) b b^T with b a smooth
+    # seeded unit field, greedy strength-graph aggregates, 8 right-hand sides
+    "q1_3d_128": dict(N=128, dim=3, field="fourier", theta=0.0, eps=1e-4, d1=0.0, bs=0, overlap=1, seed=4,
+                      field_seed=44, soc=0.03, c_min=(3, 4), n_coarse=2000, thresh=0.1, nrhs=8),
+    # the same on 32^3 cells (29,791 unknowns)
+    "q1_3d_32": dict(N=32, dim=3, field="fourier", theta=0.0, eps=1e-4, d1=0.0, bs=0, overlap=1, seed=4,
+                     field_seed=44, soc=0.03, c_min=(3, 4), n_coarse=2000, thresh=0.1, nrhs=8),
 }
 
 SWEEP_EPS = (1.0, 1e-2, 1e-4, 1e-6)
@@ -188,6 +195,14 @@ def config_problem(name: str | None = None, **over) -> tuple[Q1Problem, dict]:
     cfg = dict(CONFIGS[name]) if name is not None else {}
     cfg.update(over)
     N = int(cfg["N"])
+    if cfg.get("dim", 2) == 3:
+        from .q1_3d import field_sqrtK, greedy_aggregates, q1_3d, strength_graph
+
+        prob = q1_3d(N, field_sqrtK(float(cfg["eps"]), int(cfg["field_seed"])),
+                     desc=dict(name=name, dim=3, field="fourier", eps=cfg["eps"]))
+        ip, ix = strength_graph(prob, float(cfg.get("soc", 0.03)))
+        prob.agg = greedy_aggregates(ip, ix, prob.n)
+        return prob, cfg
     if cfg["field"] == "rot":
         sk = rotated_sqrtK(float(cfg["theta"]), float(cfg["eps"]))
     elif cfg["field"] == "circ":

@@ -159,10 +159,15 @@ CASES = {
     # its V-cycle bound is 1e-10 instead of 1e-12.
     "circ_ov2": dict(N=32, circ=True, eps=1e-6, bs=8, overlap=2, coarse_overlap=1, c_min=(4, 5), n_coarse=60,
                      d1=1e-8 / 32 ** 2, tol_vcycle=1e-10),
+    # the 3D workload on 12^3 cells: trilinear G (24 rows per cell), smooth
+    # Fourier direction field, eps = 1e-4, irregular greedy aggregates
+    "q1_3d_12": dict(cfg="q1_3d_32", N=12, overlap=1, c_min=(3, 4), n_coarse=100),
 }
 
 
 def _problem(c):
+    if c.get("cfg"):
+        return config_problem(c["cfg"], N=c["N"])[0]
     N = c["N"]
     D1 = None
     if c.get("d1"):
@@ -209,7 +214,10 @@ def test_level_operators_fp64(amg, name):
             om = Lo.omega[i]
             assert np.abs(y[om] - yo[om]).max() <= tP * np.abs(yo).max(), (lvl, i)
         v = _apply(amg, H, amg.OP_VCYCLE, lvl, x, Lo.n)
-        tV = c.get("tol_vcycle", 1e-12)
+        # the V-cycle from level 0 (the preconditioner) is basis-independent;
+        # from a coarse level it is written in the basis the level above
+        # selected, like A_l and the smoothers there
+        tV = c.get("tol_vcycle", 1e-12) if lvl == 0 else 1e-10
         assert _rel(v, oracle.vcycle(ho, x, lvl)) <= tV, (lvl, _rel(v, oracle.vcycle(ho, x, lvl)))
     Lc = ho.levels[-1]
     xc = rng.standard_normal(Lc.n)
@@ -312,7 +320,11 @@ def test_mixed_stall_falls_back_to_fp64(amg):
     _, i32 = H.solve(np.ascontiguousarray(b[:, 0]), tol=1e-8)
     assert i32[0]["status"] == 0 and i32[0]["relres_true"] <= 1e-8
     if i32[0]["fallback"]:
-        assert i32[0]["iters_mixed"] >= 10 and i32[0]["iters"] == i32[0]["iters_mixed"] + i64[0]["iters"]
+        # the FP64 redo needs about as many iterations as an FP64 solve (not
+        # exactly: RAS-T scatters with atomics, so FP64 runs are not bitwise
+        # reproducible, and a residual-replacement restart may add a few)
+        assert i32[0]["iters_mixed"] >= 10
+        assert abs(i32[0]["iters"] - i32[0]["iters_mixed"] - i64[0]["iters"]) <= 0.15 * i64[0]["iters"] + 5
     # batched: every column reaches the tolerance, stalled ones through FP64
     X, ib = H.solve(b, tol=1e-8)
     for inf in ib:
