@@ -97,6 +97,8 @@ typedef struct {
   int coarse_overlap;  /* hops of overlap on levels >= 1; 0: the level-0  */
                        /*   `overlap` on every level (Algorithm 1 builds   */
                        /*   Omega_i from one layer of neighbours in A_l)  */
+  int coarse_refine;   /* 1: one step of iterative refinement after the   */
+                       /*   explicit-inverse coarsest solve (FP64)        */
 } amgdd_params;
 
 typedef struct amgdd_hierarchy amgdd_hierarchy; /* opaque, library-owned */

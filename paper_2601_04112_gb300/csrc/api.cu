@@ -1151,6 +1151,9 @@ int build_coarsest(amgdd_hierarchy& h, Level& L, cudaStream_t s) {
   AMGDD_TRY(Atpool.alloc(m * m));
   AMGDD_TRY(scratch.alloc(m * m));
   AMGDD_TRY(launch_assemble(1, (int)m, B, L.d_g_ptr.p, L.d_h_off.p, L.d_H.p, dM.p, Apool.p, Atpool.p, s));
+  // A_L itself (symmetric) for the refinement step of the coarsest solve
+  AMGDD_TRY(L.Aw64.alloc(m * m));
+  AMGDD_CUDA(cudaMemcpyAsync(L.Aw64.p, Apool.p, m * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
   AMGDD_TRY(launch_chol(1, (int)m, B.m.p, B.a_off.p, Apool.p, dstat.p, s));
   std::vector<int32_t> stat;
   AMGDD_TRY(download(stat, dstat.p, 1, s));
@@ -1260,6 +1263,18 @@ struct VProf {
 #define AMGDD_MARK(slot) \
   if (prof) AMGDD_TRY(prof->mark(s, l, (slot)))
 
+// Exact coarsest solve x = A_L^{-1} r (FP64) with the explicit inverse W and
+// one step of iterative refinement, x += W (r - A_L x): the inverse of an
+// ill-conditioned A_L (kappa ~ 1e7 on the closed-field-line workload) is
+// accurate to ~kappa * eps only.  `sv` is scratch of the level's length.
+static int coarse_solve(const amgdd_hierarchy& h, const Level& L, const void* r, void* x, void* sv, const int* skip,
+                        cudaStream_t s) {
+  AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, r, x, false, SEG_STORE, skip, s, nullptr, nullptr, L.Wt64.p));
+  if (!h.prm.coarse_refine || L.Aw64.p == nullptr) return AMGDD_OK;
+  AMGDD_TRY(launch_seg(L.ras, L.Aw64.p, false, x, sv, false, SEG_RESID, skip, s, r, nullptr, L.Aw64.p));
+  return launch_seg(L.ras, L.W64.p, false, sv, x, false, SEG_ADD, skip, s, nullptr, nullptr, L.Wt64.p);
+}
+
 // V-cycle of Section 3.1 from level l: z = B_l r.
 static int vcycle(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, const int* skip, cudaStream_t s,
                   VProf* prof = nullptr) {
@@ -1276,13 +1291,12 @@ static int vcycle(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, c
       AMGDD_MARK(1);
       AMGDD_TRY(launch_cast(r, true, L.r64.p, false, L.n, skip, s));
       AMGDD_MARK(0);
-      AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, L.r64.p, L.x64.p, false, SEG_STORE, skip, s, nullptr, nullptr,
-                           L.Wt64.p));
+      AMGDD_TRY(coarse_solve(h, L, L.r64.p, L.x64.p, L.s64.p, skip, s));
       AMGDD_MARK(5);
       return launch_cast(L.x64.p, false, x, true, L.n, skip, s);
     }
     AMGDD_MARK(0);
-    return launch_seg(L.ras, L.W64.p, false, r, x, false, SEG_STORE, skip, s, nullptr, nullptr, L.Wt64.p);
+    return coarse_solve(h, L, r, x, L.s64.p, skip, s);
   }
   Level& N = *h.lv[l + 1];
   const void* W = f32 ? (const void*)L.W32.p : (const void*)L.W64.p;
@@ -1326,13 +1340,13 @@ static bool tail_phases(amgdd_hierarchy& h, int from, bool f32, std::vector<Phas
   for (int l = from; l < nl; ++l) {
     Level& L = *h.lv[l];
     if (L.coarsest) {
-      if (f32) {
-        ph.push_back(cast_phase(L.r32.p, true, L.r64.p, false, L.n));
-        ph.push_back(seg_phase(L.ras, L.W64.p, L.Wt64.p, false, L.r64.p, L.x64.p, SEG_STORE));
-        ph.push_back(cast_phase(L.x64.p, false, L.x32.p, true, L.n));
-      } else {
-        ph.push_back(seg_phase(L.ras, L.W64.p, L.Wt64.p, false, L.r64.p, L.x64.p, SEG_STORE));
+      if (f32) ph.push_back(cast_phase(L.r32.p, true, L.r64.p, false, L.n));
+      ph.push_back(seg_phase(L.ras, L.W64.p, L.Wt64.p, false, L.r64.p, L.x64.p, SEG_STORE));
+      if (h.prm.coarse_refine && L.Aw64.p) {
+        ph.push_back(seg_phase(L.ras, L.Aw64.p, L.Aw64.p, false, L.x64.p, L.s64.p, SEG_RESID, L.r64.p));
+        ph.push_back(seg_phase(L.ras, L.W64.p, L.Wt64.p, false, L.s64.p, L.x64.p, SEG_ADD));
       }
+      if (f32) ph.push_back(cast_phase(L.x64.p, false, L.x32.p, true, L.n));
       break;
     }
     Level& N = *h.lv[l + 1];
@@ -1757,12 +1771,19 @@ static int vcycle_multi(amgdd_hierarchy& h, int l, bool f32, int K, const void* 
                         cudaStream_t s) {
   Level& L = *h.lv[l];
   if (L.coarsest) {
+    const void* r64 = r;
+    void* x64 = x;
     if (f32) {
       AMGDD_TRY(launch_cast(r, true, L.mr64.p, false, L.n * K, skip, s));
-      AMGDD_TRY(launch_seg_multi(L.ras, L.W64.p, L.Wt64.p, false, L.mr64.p, L.mx64.p, SEG_STORE, nullptr, K, skip, s));
-      return launch_cast(L.mx64.p, false, x, true, L.n * K, skip, s);
+      r64 = L.mr64.p;
+      x64 = L.mx64.p;
     }
-    return launch_seg_multi(L.ras, L.W64.p, L.Wt64.p, false, r, x, SEG_STORE, nullptr, K, skip, s);
+    AMGDD_TRY(launch_seg_multi(L.ras, L.W64.p, L.Wt64.p, false, r64, x64, SEG_STORE, nullptr, K, skip, s));
+    if (h.prm.coarse_refine && L.Aw64.p) {  // one step of refinement, as coarse_solve
+      AMGDD_TRY(launch_seg_multi(L.ras, L.Aw64.p, L.Aw64.p, false, x64, L.ms64.p, SEG_RESID, r64, K, skip, s));
+      AMGDD_TRY(launch_seg_multi(L.ras, L.W64.p, L.Wt64.p, false, L.ms64.p, x64, SEG_ADD, nullptr, K, skip, s));
+    }
+    return f32 ? launch_cast(L.mx64.p, false, x, true, L.n * K, skip, s) : AMGDD_OK;
   }
   Level& N = *h.lv[l + 1];
   const void* W = f32 ? (const void*)L.W32.p : (const void*)L.W64.p;
@@ -2003,6 +2024,7 @@ amgdd_params amgdd_params_default(void) {
   p.tune = 1;
   p.tune_cache = nullptr;
   p.coarse_overlap = 0;
+  p.coarse_refine = 1;
   return p;
 }
 
@@ -2108,7 +2130,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     AMGDD_CUDA(cudaGetDeviceProperties(&prop, H->device));
     std::string sig = std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "|m" +
                       std::to_string(m) + "|n" + std::to_string(n) + "|nnz" + std::to_string(nnz) + "|ov" +
-                      std::to_string(overlap) + "/" + std::to_string(prm.coarse_overlap) + "|nc" + std::to_string(prm.n_coarse) + "|L" +
+                      std::to_string(overlap) + "/" + std::to_string(prm.coarse_overlap) + "|cr" + std::to_string(prm.coarse_refine) + "|nc" + std::to_string(prm.n_coarse) + "|L" +
                       std::to_string(prm.L_max) + "|c";
     for (int i = 0; i < prm.n_cmin; ++i) sig += std::to_string(prm.c_min[i]) + ",";
     char buf[64];
@@ -2356,7 +2378,7 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
       set_error("amgdd_apply: COARSE needs the coarsest level");
       return AMGDD_ERR_INVALID_ARG;
     }
-    AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, x, y, false, SEG_STORE, nullptr, s, nullptr, nullptr, L.Wt64.p));
+    AMGDD_TRY(coarse_solve(*h, L, x, y, L.s64.p, nullptr, s));
     return take_err_word(*h, s);
   }
   if (L.coarsest && op != AMGDD_OP_A) {
@@ -2465,7 +2487,7 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
       set_error("amgdd_apply_noalloc: COARSE needs the coarsest level");
       return AMGDD_ERR_INVALID_ARG;
     }
-    AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, x, y, false, SEG_STORE, nullptr, s, nullptr, nullptr, L.Wt64.p));
+    AMGDD_TRY(coarse_solve(*h, L, x, y, L.s64.p, nullptr, s));
     return take_err_word(*h, s);
   }
   if (L.coarsest && op != AMGDD_OP_A) {
@@ -2567,7 +2589,7 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes
     const Level& L = *h->lv[l];
     double* b = bytes + l * VProf::kSlots;
     if (L.coarsest) {
-      b[0] = seg_bytes(L.ras, L.n, L.n, false, 8);
+      b[0] = seg_bytes(L.ras, L.n, L.n, false, 8) * (h->prm.coarse_refine && L.Aw64.p ? 3.0 : 1.0);
       if (f32) b[1] = b[5] = (double)L.n * 12.0;
     } else {
       const int64_t nn = L.col0.back();
@@ -2680,7 +2702,7 @@ int amgdd_level_export(const amgdd_hierarchy* h, int level, int which, void* dst
 
 static void level_bytes(const amgdd_hierarchy& h, const Level& L, size_t esz, double& cyc) {
   if (L.coarsest) {
-    cyc += (double)L.n * L.n * 8.0 + 2.0 * L.n * 8.0;
+    cyc += ((double)L.n * L.n * 8.0 + 2.0 * L.n * 8.0) * (h.prm.coarse_refine && L.Aw64.p ? 3.0 : 1.0);
     return;
   }
   const int64_t nn = L.col0.back();
