@@ -70,6 +70,25 @@ def parse_args():
     return ap.parse_args()
 
 
+def replica_max(v, world, device="cuda"):
+    """Max of a per-rank value over the replicas (the slowest rank's time
+    sets whole-job throughput); the identity with one rank."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, seconds, world, device="cuda"):
+    """Whole-job rate of independent replicas: every rank's units over the
+    slowest rank's time (weak scaling: per-rank work fixed)."""
+    return units_per_rank * world / replica_max(seconds, world, device)
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -438,13 +457,7 @@ def run_ours(args):
         return e0.elapsed_time(e1) / 1e3, wall, infos, amg.kernel_launches() - k0
 
     def maxrank(v):
-        if world == 1:
-            return v
-        import torch.distributed as dist
-
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(v, world)
 
     # warm-up (both precisions: graph capture, first-touch)
     for prec in (amg.FP64, amg.MIXED32):
