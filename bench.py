@@ -58,9 +58,9 @@ def parse_args():
     ap.add_argument("--serve", action="store_true",
                     help="run the serving workload (many operators and right-hand-side counts) instead")
     ap.add_argument("--no-serving", action="store_true", help="skip the small serving run of the default line")
-    ap.add_argument("--tune-mode", choices=("timed", "defaults", "staged"), default="timed",
-                    help="setup-time kernel choices: timed (default), fixed defaults, or staged kernels wherever "
-                         "a plan allows them (profiling)")
+    ap.add_argument("--tune-mode", choices=("timed", "defaults", "staged", "shifted", "lanes"), default="timed",
+                    help="setup-time kernel choices: timed (default), fixed defaults, or the staged kernel, "
+                         "shifted vector loads or lanes per row wherever a plan allows them (profiling)")
     ap.add_argument("--tune-cache", default=None,
                     help="file of setup-time kernel choices: read if present, written after tuning "
                          "(profiling runs replay the choices of a plain run)")
@@ -421,7 +421,7 @@ def run_ours(args):
     H = amg.Hierarchy.from_problem(prob, overlap=cfg["overlap"], c_min=cfg["c_min"], n_coarse=cfg["n_coarse"],
                                    thresh=cfg["thresh"], precision=amg.MIXED32, tune_cache=args.tune_cache,
                                    coarse_overlap=cfg.get("coarse_overlap", 0),
-                                   tune={"timed": 1, "defaults": 0, "staged": 2}[args.tune_mode])
+                                   tune={"timed": 1, "defaults": 0, "staged": 2, "shifted": 3, "lanes": 4}[args.tune_mode])
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     stats = H.stats()

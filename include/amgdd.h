@@ -88,17 +88,23 @@ typedef struct {
   int check_every;     /* host reads the convergence flag every k iters   */
   int tune;            /* 1: setup times the alternative kernel forms of  */
                        /*   each step and keeps the fastest; 0: defaults  */
-                       /*   (unstaged kernels, block rows, no persistent  */
-                       /*   tail); 2: as 0 with staged kernels wherever a */
-                       /*   plan allows them (for profiling them)         */
+                       /*   (unstaged kernels, row per lane for rows of   */
+                       /*   <= 128 entries, block rows, no persistent     */
+                       /*   tail); 2, 3, 4: as 0 with, wherever a plan    */
+                       /*   allows it, the staged kernel (2), shifted     */
+                       /*   vector loads (3) or lanes per row (4) (for    */
+                       /*   profiling and testing each form)              */
   const char* tune_cache; /* NULL, or a text file of earlier choices keyed */
                        /*   by problem, GPU, level and step: read before  */
                        /*   timing, rewritten with new choices at the end */
   int coarse_overlap;  /* hops of overlap on levels >= 1; 0: the level-0  */
                        /*   `overlap` on every level (Algorithm 1 builds   */
                        /*   Omega_i from one layer of neighbours in A_l)  */
-  int coarse_refine;   /* 1: one step of iterative refinement after the   */
-                       /*   explicit-inverse coarsest solve (FP64)        */
+  int coarse_refine;   /* one step of iterative refinement after the      */
+                       /*   explicit-inverse coarsest solve (FP64):       */
+                       /*   0 never; 1 (default) when setup measures      */
+                       /*   ||W A v - v|| / ||v|| > 1e-13 for a seeded v  */
+                       /*   (W the computed inverse); 2 always            */
 } amgdd_params;
 
 typedef struct amgdd_hierarchy amgdd_hierarchy; /* opaque, library-owned */

@@ -37,7 +37,7 @@ thread_local int64_t g_alloc_bytes = 0;
 // signature that keys the cache, and the cached choices (`key\tvalue` lines).
 struct TuneCtx {
   bool on = true;
-  bool prefer_staged = false;
+  int prefer_form = -1;  // without timing: force this gather-GEMV form where a plan allows it
   std::string path, sig;
   std::map<std::string, double> kv;
   bool dirty = false;
@@ -275,6 +275,20 @@ int build_items(SegPlan& p, const std::vector<int32_t>& nr, const std::vector<in
 
 // force: 0 picks the mode from the row length, 1 lanes-per-row chunks,
 // 2 row per lane (the caller then passes the transposed copy).
+// CTA chunks of the lanes-per-row form: `rpc` rows of one block each.
+int set_chunks(SegPlan& p, int rpc, cudaStream_t s) {
+  std::vector<int32_t> cb, cr;
+  for (int b = 0; b < p.nblocks; ++b)
+    for (int r = 0; r < p.h_nr[b]; r += rpc) {
+      cb.push_back(b);
+      cr.push_back(r);
+    }
+  p.rows_per_chunk = rpc;
+  p.nchunks = (int)cb.size();
+  AMGDD_TRY(p.chunk_blk.upload(cb, s));
+  return p.chunk_row0.upload(cr, s);
+}
+
 int build_seg(SegPlan& p, const std::vector<int32_t>& nr, const std::vector<int32_t>& nc,
               const std::vector<int64_t>& m_off, const std::vector<int64_t>& in_off,
               const std::vector<int64_t>& out_off, const int32_t* in_ext, const int32_t* out_ext, cudaStream_t s,
@@ -310,7 +324,9 @@ int build_seg(SegPlan& p, const std::vector<int32_t>& nr, const std::vector<int3
   // short rows: one lane per output row over the transposed copy
   // row per lane needs no reduction but walks columns with a stride, which
   // streams well only for short rows (measured: long rows lose 2x)
+  // (short-row plans carry both forms; the tuner may switch to lanes per row)
   p.rows_mode = force == 2 || (force == 0 && p.max_nc <= 128);
+  p.unroll = !p.rows_mode && p.lanes == 32 && rows > 0 && (double)p.mat_len / (double)rows >= 512.0;
   if (p.rows_mode) {
     int max_nr = 0;
     for (int b = 0; b < p.nblocks; ++b) max_nr = std::max(max_nr, nr[b]);
@@ -328,21 +344,17 @@ int build_seg(SegPlan& p, const std::vector<int32_t>& nr, const std::vector<int3
     AMGDD_TRY(p.task_row0.upload(tr, s));
     AMGDD_TRY(p.task_nrow.upload(tn, s));
   }
-  std::vector<int32_t> cb, cr;
-  if (!p.rows_mode)
-    for (int b = 0; b < p.nblocks; ++b)
-      for (int r = 0; r < nr[b]; r += p.rows_per_chunk) {
-        cb.push_back(b);
-        cr.push_back(r);
-      }
-  p.nchunks = (int)cb.size();
+  p.h_nr = nr;
+  if (force != 2) {
+    AMGDD_TRY(set_chunks(p, p.rows_per_chunk, s));
+  } else {
+    p.nchunks = 0;
+  }
   AMGDD_TRY(p.nr.upload(nr, s));
   AMGDD_TRY(p.nc.upload(nc, s));
   AMGDD_TRY(p.m_off.upload(m_off, s));
   AMGDD_TRY(p.in_off.upload(in_off, s));
   AMGDD_TRY(p.out_off.upload(out_off, s));
-  AMGDD_TRY(p.chunk_blk.upload(cb, s));
-  AMGDD_TRY(p.chunk_row0.upload(cr, s));
   return build_items(p, nr, nc, m_off, in_off, out_off, in_ext, out_ext, s);
 }
 
@@ -526,23 +538,66 @@ int build_blockrows(Level& L, cudaStream_t s) {
   return AMGDD_OK;
 }
 
-// Setup-time choice between the staged and unstaged gather-GEMV kernels for
-// one plan: time both on scratch vectors (`nin` inputs, `nout` outputs) and
-// keep the faster.  The staged form's arrays are freed when it loses.
+// Setup-time choice of the gather-GEMV form for one plan: time the unstaged
+// scalar, staged and shifted-vector kernels and the row-per-lane kernel that
+// apply on scratch vectors (`nin` inputs, `nout` outputs) and keep the
+// fastest.  The staged form's arrays are freed when it loses.  The choice is
+// made in the precision T; `shift_only` then re-times, in the other
+// precision, only shifted against scalar loads for a plan that kept the
+// lanes-per-row form (the flag of each precision is separate).
 template <class T>
 int tune_seg(SegPlan& p, const std::string& key, const T* M, const T* MT, int64_t nin, int64_t nout, SegMode mode,
-             cudaStream_t s) {
-  if (!p.staged || g_err_word == nullptr || M == nullptr) return AMGDD_OK;
+             cudaStream_t s, bool shift_only = false) {
+  constexpr bool f32 = sizeof(T) == 4;
+  bool& shift = f32 ? p.shift : p.shift64;
+  // candidate forms: 0 lanes per row, scalar loads; 1 staged (when built);
+  // 2 lanes per row with shifted vector loads (rows at any alignment, 32
+  // lanes per row; the W shifted copies of x take about 16 bytes of shared
+  // memory per column); 3 row per lane over the transposed copy (short rows)
+  const bool chunk_now = !p.staged && !p.rows_mode;
+  const bool can_rows = !shift_only && p.ntasks > 0 && MT != nullptr;
+  const bool can_chunk = p.nchunks > 0 && (!shift_only || chunk_now);
+  const bool can_shift = can_chunk && !p.vec && p.lanes == 32 && 16.0 * (p.max_nc + 8) <= 160.0 * 1024.0;
+  const bool rows0 = p.rows_mode;
+  auto drop_staged = [&p] {
+    p.items.release();
+    p.tabs.release();
+    p.gidx.release();
+    p.gout.release();
+  };
+  shift = false;
+  if (shift_only ? !can_shift : (!p.staged && !can_shift && !(can_rows && can_chunk))) return AMGDD_OK;
+  if (g_err_word == nullptr || M == nullptr) return AMGDD_OK;
+  auto set_form = [&](int form) {
+    shift = form == 2;
+    if (shift_only) return;
+    p.staged = form == 1;
+    p.rows_mode = form == 3 || (form == 1 && rows0);
+  };
+  // rows per CTA of the lanes-per-row forms: the default (enough CTAs to
+  // fill the GPU) and larger chunks, which gather x(in_idx) fewer times
+  // (plans of a few large blocks on coarse levels)
+  const int rpc0 = p.rows_per_chunk;
+  std::vector<int> rpcs{rpc0};
+  if (!shift_only && can_chunk)
+    for (int r = 2 * rpc0; r <= 64; r *= 2) rpcs.push_back(r);
   double cached = 0.0;
   if (g_tune && (g_tune->get(key, cached) || !g_tune->on)) {
-    // without timing: unstaged, or staged when asked for (tune = 2)
-    p.staged = g_tune->on ? cached != 0.0 : g_tune->prefer_staged;
-    if (!p.staged) {
-      p.items.release();
-      p.tabs.release();
-      p.gidx.release();
-      p.gout.release();
+    // without timing: the built form (row per lane for short rows), or the
+    // form asked for (tune = 2, 3, 4) where the plan allows it
+    const int code = (int)cached;
+    int form = g_tune->on ? code % 16 : (g_tune->prefer_form >= 0 ? g_tune->prefer_form : (rows0 ? 3 : 0));
+    if (shift_only) {
+      set_form(form == 2 ? 2 : 0);
+      return AMGDD_OK;
     }
+    if ((form == 1 && !p.staged) || (form == 2 && !can_shift) || (form == 3 && !can_rows) ||
+        ((form == 0 || form == 2) && !can_chunk))
+      form = rows0 ? 3 : 0;
+    set_form(form);
+    const int rpc = g_tune->on ? code / 16 : 0;
+    if ((form == 0 || form == 2) && rpc > 0 && rpc != rpc0 && rpc <= 64) AMGDD_TRY(set_chunks(p, rpc, s));
+    if (!p.staged) drop_staged();
     return AMGDD_OK;
   }
   DBuf<T> xin, yout, cin;
@@ -552,36 +607,48 @@ int tune_seg(SegPlan& p, const std::string& key, const T* M, const T* MT, int64_
   AMGDD_TRY(xin.zero(s));
   AMGDD_TRY(yout.zero(s));
   AMGDD_TRY(cin.zero(s));
-  const bool f32 = sizeof(T) == 4;
+  const bool built = !shift_only && p.staged;
   cudaEvent_t e[2];
   for (auto& v : e) AMGDD_CUDA(cudaEventCreate(&v));
-  float t[2] = {0.f, 0.f};
+  float t[4] = {0.f, 0.f, 0.f, 0.f};
+  int best_rpc[4] = {rpc0, rpc0, rpc0, rpc0};
+  const bool ok[4] = {can_chunk, built, can_shift, can_rows};
   constexpr int kReps = 8;
   int rc = AMGDD_OK;
-  for (int form = 0; form < 2 && rc == AMGDD_OK; ++form) {
-    p.staged = form == 0;
-    for (int rep = 0; rep < kReps + 2 && rc == AMGDD_OK; ++rep) {
-      if (rep == 2) cudaEventRecord(e[0], s);
-      rc = launch_seg(p, M, f32, xin.p, yout.p, f32, mode, nullptr, s, mode == SEG_RESID ? cin.p : nullptr, nullptr,
-                      MT);
+  for (int form = 0; form < 4 && rc == AMGDD_OK; ++form) {
+    if (!ok[form]) continue;
+    set_form(form);
+    const bool chunked = form == 0 || form == 2;
+    for (size_t ri = 0; ri < (chunked ? rpcs.size() : 1) && rc == AMGDD_OK; ++ri) {
+      if (chunked && p.rows_per_chunk != rpcs[ri]) rc = set_chunks(p, rpcs[ri], s);
+      for (int rep = 0; rep < kReps + 2 && rc == AMGDD_OK; ++rep) {
+        if (rep == 2) cudaEventRecord(e[0], s);
+        rc = launch_seg(p, M, f32, xin.p, yout.p, f32, mode, nullptr, s, mode == SEG_RESID ? cin.p : nullptr,
+                        nullptr, MT);
+      }
+      cudaEventRecord(e[1], s);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e[1]) != cudaSuccess || cudaEventElapsedTime(&ms, e[0], e[1]) != cudaSuccess)
+        rc = AMGDD_ERR_CUDA;
+      if (ri == 0 || ms < t[form]) {
+        t[form] = ms;
+        best_rpc[form] = rpcs[ri];
+      }
     }
-    cudaEventRecord(e[1], s);
-    if (cudaEventSynchronize(e[1]) != cudaSuccess || cudaEventElapsedTime(&t[form], e[0], e[1]) != cudaSuccess)
-      rc = AMGDD_ERR_CUDA;
   }
   for (auto& v : e) cudaEventDestroy(v);
   AMGDD_TRY(rc);
-  p.staged = t[0] < t[1];
-  if (g_tune) g_tune->put(key, p.staged ? 1.0 : 0.0);
+  int best = -1;
+  for (int form = 0; form < 4; ++form)
+    if (ok[form] && (best < 0 || t[form] < t[best])) best = form;
+  set_form(best);
+  if (p.rows_per_chunk != best_rpc[best] && can_chunk) AMGDD_TRY(set_chunks(p, best_rpc[best], s));
+  if (g_tune) g_tune->put(key, (double)(best + (shift_only ? 0 : 16 * p.rows_per_chunk)));
   if (g_timer.on)
-    fprintf(stderr, "[amgdd]   plan %d blocks: staged %.1f us, unstaged %.1f us -> %s\n", p.nblocks, 1e3 * t[0] / kReps,
-            1e3 * t[1] / kReps, p.staged ? "staged" : "unstaged");
-  if (!p.staged) {
-    p.items.release();
-    p.tabs.release();
-    p.gidx.release();
-    p.gout.release();
-  }
+    fprintf(stderr, "[amgdd]   plan %d blocks (%s): lanes/row %.1f us, staged %.1f us, shifted %.1f us, row/lane %.1f us -> %d (%d rows per CTA)\n",
+            p.nblocks, f32 ? "fp32" : "fp64", 1e3 * t[0] / kReps, 1e3 * t[1] / kReps, 1e3 * t[2] / kReps,
+            1e3 * t[3] / kReps, best, p.rows_per_chunk);
+  if (!shift_only && !p.staged) drop_staged();
   return AMGDD_OK;
 }
 
@@ -594,6 +661,12 @@ int tune_level_plans(Level& L, int lvl, int64_t n_next, cudaStream_t s) {
   AMGDD_TRY(tune_seg<float>(L.restr, k + "restrict", L.Zt32.p, L.Z32.p, L.n, n_next, SEG_STORE, s));
   AMGDD_TRY(tune_seg<float>(L.prol, k + "prolong", L.Z32.p, L.Zt32.p, n_next, L.n, SEG_ADD, s));
   if (L.A32.p) AMGDD_TRY(tune_seg<float>(L.ablk, k + "blockrows", L.A32.p, L.At32.p, L.n, L.n, SEG_RESID, s));
+  // FP64 copies: shifted or scalar loads, within the form chosen above
+  AMGDD_TRY(tune_seg<double>(L.ras, k + "ras64", L.W64.p, L.Wt64.p, L.n, L.n, SEG_STORE, s, true));
+  AMGDD_TRY(tune_seg<double>(L.rast, k + "rast64", L.Wt64.p, L.W64.p, L.n, L.n, SEG_ATOMIC_ADD, s, true));
+  AMGDD_TRY(tune_seg<double>(L.restr, k + "restrict64", L.Zt64.p, L.Z64.p, L.n, n_next, SEG_STORE, s, true));
+  AMGDD_TRY(tune_seg<double>(L.prol, k + "prolong64", L.Z64.p, L.Zt64.p, n_next, L.n, SEG_ADD, s, true));
+  if (L.A64.p) AMGDD_TRY(tune_seg<double>(L.ablk, k + "blockrows64", L.A64.p, L.At64.p, L.n, L.n, SEG_RESID, s, true));
   return AMGDD_OK;
 }
 
@@ -1183,6 +1256,35 @@ int build_coarsest(amgdd_hierarchy& h, Level& L, cudaStream_t s) {
   std::vector<int32_t> nr{(int32_t)m}, nc{(int32_t)m};
   std::vector<int64_t> moff{0}, ioff{0}, ooff{0};
   AMGDD_TRY(build_seg(L.ras, nr, nc, moff, ioff, ooff, h.iota.p, h.iota.p, s));
+  // A posteriori accuracy of the computed inverse: e = ||W (A_L v) - v|| / ||v||
+  // for a fixed pseudo-random v (xorshift64).  e is about kappa(A_L) * eps;
+  // refinement is kept only where it can change the solve beyond rounding.
+  {
+    std::vector<double> v(m), w;
+    uint64_t z = 0x9E3779B97F4A7C15ull;
+    for (auto& e : v) {
+      z ^= z << 13;
+      z ^= z >> 7;
+      z ^= z << 17;
+      e = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    }
+    DBuf<double> dv, dr, dw;
+    AMGDD_TRY(dv.upload(v, s));
+    AMGDD_TRY(dr.alloc(m));
+    AMGDD_TRY(dw.alloc(m));
+    AMGDD_TRY(launch_seg(L.ras, L.Aw64.p, false, dv.p, dr.p, false, SEG_STORE, nullptr, s, nullptr, nullptr, L.Aw64.p));
+    AMGDD_TRY(launch_seg(L.ras, L.W64.p, false, dr.p, dw.p, false, SEG_STORE, nullptr, s, nullptr, nullptr, L.Wt64.p));
+    AMGDD_TRY(download(w, dw.p, m, s));
+    double num = 0.0, den = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+      num += (w[i] - v[i]) * (w[i] - v[i]);
+      den += v[i] * v[i];
+    }
+    L.inv_err = std::sqrt(num / den);
+    // (a one-level hierarchy keeps A_L: the batched residual applies it)
+    const bool keep = h.prm.coarse_refine == 2 || (h.prm.coarse_refine == 1 && L.inv_err > 1e-13);
+    if (!keep && &L != h.lv[0].get()) L.Aw64.release();
+  }
   AMGDD_CUDA(cudaStreamSynchronize(s));
   return AMGDD_OK;
 }
@@ -2123,12 +2225,13 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   ErrScope err_scope(&H->st.p->vc_err);
   TuneCtx tctx;
   tctx.on = prm.tune == 1;
-  tctx.prefer_staged = prm.tune == 2;
+  tctx.prefer_form = prm.tune == 2 ? 1 : (prm.tune == 3 ? 2 : (prm.tune == 4 ? 0 : -1));
   tctx.path = prm.tune_cache ? prm.tune_cache : "";
   {
     cudaDeviceProp prop;
     AMGDD_CUDA(cudaGetDeviceProperties(&prop, H->device));
-    std::string sig = std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "|m" +
+    // "f5": plan choices take the four forms of tune_seg and rows per CTA
+    std::string sig = std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "|f5|m" +
                       std::to_string(m) + "|n" + std::to_string(n) + "|nnz" + std::to_string(nnz) + "|ov" +
                       std::to_string(overlap) + "/" + std::to_string(prm.coarse_overlap) + "|cr" + std::to_string(prm.coarse_refine) + "|nc" + std::to_string(prm.n_coarse) + "|L" +
                       std::to_string(prm.L_max) + "|c";
@@ -2758,7 +2861,14 @@ int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap) {
                   l ? ", " : "", L.coarsest ? "none" : (L.has_blk ? "block rows" : "matrix-free"), L.blk_us, L.mf_us);
     s += buf;
   }
-  s += "], \"tail\": {";
+  {
+    const Level& C = *h->lv.back();
+    char buf[96];
+    std::snprintf(buf, sizeof buf, "], \"coarsest_inv_err\": %.3e, \"coarsest_refined\": %s", C.inv_err,
+                  (h->prm.coarse_refine && C.Aw64.p) ? "true" : "false");
+    s += buf;
+  }
+  s += ", \"tail\": {";
   for (int pi = 0; pi < 2; ++pi) {
     s += std::string(pi ? ", " : "") + (pi ? "\"mixed\"" : "\"fp64\"") + ": {\"from\": " +
          std::to_string(h->persist_from[pi]) + ", \"vcycle_us_by_from\": [";

@@ -56,10 +56,29 @@ __device__ __forceinline__ float vdot(const float4& a, const float4& b) {
 }
 __device__ __forceinline__ double vdot(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
 
-// VEC: every row of every block starts on a 16-byte boundary and has a
-// multiple of the vector width entries (checked when the plan is built);
-// rows and the staged x are then read 16 bytes per lane.
-template <class T, int L, int MODE, bool VEC>
+// VK (vector kind) 0: scalar loads.  VK 1: every row of every block starts on
+// a 16-byte boundary and has a multiple of the vector width W entries (checked
+// when the plan is built); rows and the staged x are read 16 bytes per lane.
+// VK 2 (any rows): a row starting a = (offset mod W) elements past a 16-byte
+// boundary is read as aligned vectors from that boundary, against the copy of
+// the staged x shifted right by a.  Shared memory then holds W copies of
+// stride S = ceil(nc / W) W + W, zero outside the row, so the entries of the
+// neighbouring rows that the aligned vectors take in (stored, finite values)
+// are multiplied by zero.  A vector that would cross the end of the stored
+// matrix (m_len entries) is read element by element up to that end.
+// U = 4 (plans with long rows only): the gather and the row loop keep four
+// independent loads per thread in flight.
+template <class T, int VK>
+__device__ __forceinline__ void seg_stage(T* xs, int S, int c, T v) {
+  if constexpr (VK == 2) {
+#pragma unroll
+    for (int k = 0; k < Vec2<T>::width; ++k) xs[k * S + c + k] = v;
+  } else {
+    xs[c] = v;
+  }
+}
+
+template <class T, int L, int MODE, int VK, int U = 1>
 __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__ chunk_blk,
                                                      const int32_t* __restrict__ chunk_row0, int rows_per_chunk,
                                                      const int64_t* __restrict__ m_off, const int32_t* __restrict__ nr,
@@ -69,35 +88,106 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
                                                      const int32_t* __restrict__ in_idx,
                                                      const int32_t* __restrict__ out_idx, const T* __restrict__ M,
                                                      const T* __restrict__ x, T* __restrict__ y, const int* skip,
-                                                     const T* __restrict__ csrc, T* __restrict__ cdst) {
+                                                     const T* __restrict__ csrc, T* __restrict__ cdst, int64_t m_len) {
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  using V = typename Vec2<T>::type;
+  constexpr int W = Vec2<T>::width;
   T* xs = reinterpret_cast<T*>(smem_raw);
   const int b = chunk_blk[blockIdx.x];
   const int r0 = chunk_row0[blockIdx.x];
   const int ncb = nc[b];
   const int r1 = min(nr[b], r0 + rows_per_chunk);
   const int32_t* ii = in_idx + in_off[b];
-  for (int c = threadIdx.x; c < ncb; c += blockDim.x) xs[c] = x[ii[c]];
+  const int S = VK == 2 ? ((ncb + W - 1) / W) * W + W : 0;
+  if constexpr (VK == 2) {
+    const int E = S - ncb;  // zeros per copy: k ahead of the row, E - k after it
+    for (int t = threadIdx.x; t < W * E; t += blockDim.x) {
+      const int k = t / E, e = t - k * E;
+      xs[k * S + (e < k ? e : ncb + e)] = T(0);
+    }
+  }
+  if constexpr (U == 1) {
+    for (int c = threadIdx.x; c < ncb; c += blockDim.x) seg_stage<T, VK>(xs, S, c, x[ii[c]]);
+  } else {
+    const int step = (int)blockDim.x;
+    int c = threadIdx.x;
+    for (; c + (U - 1) * step < ncb; c += U * step) {
+      int id[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) id[u] = ii[c + u * step];
+      T v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = x[id[u]];
+#pragma unroll
+      for (int u = 0; u < U; ++u) seg_stage<T, VK>(xs, S, c + u * step, v[u]);
+    }
+    for (; c < ncb; c += step) seg_stage<T, VK>(xs, S, c, x[ii[c]]);
+  }
   __syncthreads();
   const int lane = threadIdx.x % L;
   const int grp = threadIdx.x / L;
   const int ngrp = blockDim.x / L;
   const unsigned mask = group_mask<L>();
-  const T* Mb = M + m_off[b];
   const int32_t* oo = out_idx + out_off[b];
   for (int r = r0 + grp; r < r1; r += ngrp) {
-    const T* row = Mb + (int64_t)r * ncb;
     T acc = T(0);
-    if constexpr (VEC) {
-      using V = typename Vec2<T>::type;
-      constexpr int W = Vec2<T>::width;
-      const V* rv = reinterpret_cast<const V*>(row);
-      const V* xv = reinterpret_cast<const V*>(xs);
-      const int nv = ncb / W;
-      for (int c = lane; c < nv; c += L) acc += vdot(rv[c], xv[c]);
+    if constexpr (VK != 0) {
+      const V* rv;
+      const V* xv;
+      int nv;
+      if constexpr (VK == 1) {
+        rv = reinterpret_cast<const V*>(M + m_off[b] + (int64_t)r * ncb);
+        xv = reinterpret_cast<const V*>(xs);
+        nv = ncb / W;
+      } else {
+        const int64_t e0 = m_off[b] + (int64_t)r * ncb;
+        const int a = (int)(e0 & (W - 1));
+        const int64_t base = e0 - a;
+        rv = reinterpret_cast<const V*>(M + base);
+        xv = reinterpret_cast<const V*>(xs + a * S);
+        nv = (ncb + a + W - 1) / W;
+        if (base + (int64_t)nv * W > m_len) {  // last row of the matrix: at most one vector crosses its end
+          --nv;
+          const T* xa = xs + a * S;
+          if (lane == 0)
+            for (int j = nv * W; base + j < m_len; ++j) acc += M[base + j] * xa[j];
+        }
+      }
+      int c = lane;
+      if constexpr (U > 1) {
+        T a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) a[u] = T(0);
+        for (; c + (U - 1) * L < nv; c += U * L) {
+          V m[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) m[u] = rv[c + u * L];
+#pragma unroll
+          for (int u = 0; u < U; ++u) a[u] += vdot(m[u], xv[c + u * L]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc += a[u];
+      }
+      for (; c < nv; c += L) acc += vdot(rv[c], xv[c]);
     } else {
-      for (int c = lane; c < ncb; c += L) acc += row[c] * xs[c];
+      const T* row = M + m_off[b] + (int64_t)r * ncb;
+      int c = lane;
+      if constexpr (U > 1) {
+        T a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) a[u] = T(0);
+        for (; c + (U - 1) * L < ncb; c += U * L) {
+          T m[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) m[u] = row[c + u * L];
+#pragma unroll
+          for (int u = 0; u < U; ++u) a[u] += m[u] * xs[c + u * L];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc += a[u];
+      }
+      for (; c < ncb; c += L) acc += row[c] * xs[c];
     }
     acc = group_sum<L>(acc, mask);
     if (lane == 0) {
@@ -378,35 +468,51 @@ int seg_rows_mode(const SegPlan& p, const T* MT, const T* x, T* y, SegMode mode,
   }
 }
 
-template <class T, int L>
-int seg_dispatch_mode(const SegPlan& p, const T* M, const T* x, T* y, SegMode mode, const int* skip,
-                      cudaStream_t s, const T* csrc, T* cdst) {
-  const size_t smem = (size_t)p.max_nc * sizeof(T);
+template <class T, int L, int VK, int U>
+int seg_launch_kind(const SegPlan& p, const T* M, const T* x, T* y, SegMode mode, const int* skip, cudaStream_t s,
+                    const T* csrc, T* cdst, size_t smem) {
   auto launch = [&](auto kern) -> int {
     if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<p.nchunks, kSegThreads, smem, s>>>(p.chunk_blk.p, p.chunk_row0.p, p.rows_per_chunk, p.m_off.p, p.nr.p,
                                               p.nc.p, p.in_off.p, p.out_off.p, p.in_idx_ext, p.out_idx_ext, M, x, y,
-                                              skip, csrc, cdst);
+                                              skip, csrc, cdst, p.mat_len);
     AMGDD_CUDA(cudaGetLastError());
     count_kernels(1);
     return AMGDD_OK;
   };
-  if (p.vec) {
-    switch (mode) {
-      case SEG_STORE: return launch(k_seg<T, L, SEG_STORE, true>);
-      case SEG_ADD: return launch(k_seg<T, L, SEG_ADD, true>);
-      case SEG_ATOMIC_ADD: return launch(k_seg<T, L, SEG_ATOMIC_ADD, true>);
-      case SEG_ATOMIC_SUB: return launch(k_seg<T, L, SEG_ATOMIC_SUB, true>);
-      default: return launch(k_seg<T, L, SEG_RESID, true>);
-    }
-  }
   switch (mode) {
-    case SEG_STORE: return launch(k_seg<T, L, SEG_STORE, false>);
-    case SEG_ADD: return launch(k_seg<T, L, SEG_ADD, false>);
-    case SEG_ATOMIC_ADD: return launch(k_seg<T, L, SEG_ATOMIC_ADD, false>);
-    case SEG_ATOMIC_SUB: return launch(k_seg<T, L, SEG_ATOMIC_SUB, false>);
-    default: return launch(k_seg<T, L, SEG_RESID, false>);
+    case SEG_STORE: return launch(k_seg<T, L, SEG_STORE, VK, U>);
+    case SEG_ADD: return launch(k_seg<T, L, SEG_ADD, VK, U>);
+    case SEG_ATOMIC_ADD: return launch(k_seg<T, L, SEG_ATOMIC_ADD, VK, U>);
+    case SEG_ATOMIC_SUB: return launch(k_seg<T, L, SEG_ATOMIC_SUB, VK, U>);
+    default: return launch(k_seg<T, L, SEG_RESID, VK, U>);
   }
+}
+
+// Shared memory of the shifted-vector form (W copies of the staged input).
+template <class T>
+size_t seg_shift_smem(const SegPlan& p) {
+  constexpr int W = Vec2<T>::width;
+  return (size_t)W * (size_t)(((p.max_nc + W - 1) / W) * W + W) * sizeof(T);
+}
+
+template <class T, int L>
+int seg_dispatch_mode(const SegPlan& p, const T* M, const T* x, T* y, SegMode mode, const int* skip,
+                      cudaStream_t s, const T* csrc, T* cdst) {
+  const size_t smem = (size_t)p.max_nc * sizeof(T);
+  if constexpr (L == 32) {
+    // the shifted form needs a 16-byte aligned base (device allocations are)
+    if ((sizeof(T) == 4 ? p.shift : p.shift64) && !p.vec && ((uintptr_t)M & 15) == 0) {
+      const size_t sm2 = seg_shift_smem<T>(p);
+      return p.unroll ? seg_launch_kind<T, L, 2, 4>(p, M, x, y, mode, skip, s, csrc, cdst, sm2)
+                      : seg_launch_kind<T, L, 2, 1>(p, M, x, y, mode, skip, s, csrc, cdst, sm2);
+    }
+    if (p.unroll)
+      return p.vec ? seg_launch_kind<T, L, 1, 4>(p, M, x, y, mode, skip, s, csrc, cdst, smem)
+                   : seg_launch_kind<T, L, 0, 4>(p, M, x, y, mode, skip, s, csrc, cdst, smem);
+  }
+  return p.vec ? seg_launch_kind<T, L, 1, 1>(p, M, x, y, mode, skip, s, csrc, cdst, smem)
+               : seg_launch_kind<T, L, 0, 1>(p, M, x, y, mode, skip, s, csrc, cdst, smem);
 }
 
 template <class T>

@@ -107,12 +107,16 @@ struct SegPlan {
   int rows_per_chunk = 0;
   int lanes = 32;       // lanes cooperating on one row (4, 8, 16 or 32)
   bool vec = false;     // every row 16-byte aligned with a whole number of vectors
+  bool shift = false;   // 32 lanes, rows at any alignment: aligned vector loads against shifted copies of x
+  bool shift64 = false; // the same for the FP64 copies (chosen separately)
+  bool unroll = false;  // long rows (32 lanes, >= 512 entries on average): 4-way unrolled loops
   int max_nc = 0;       // longest row (shared-memory staging of the gathered x)
   int64_t mat_len = 0;  // total stored matrix entries
   int64_t in_len = 0, out_len = 0;
   DBuf<int64_t> m_off, in_off, out_off;
   DBuf<int32_t> nr, nc;
   DBuf<int32_t> chunk_blk, chunk_row0;
+  std::vector<int32_t> h_nr;  // rows per block (host), to rebuild the chunks
   // index arrays owned elsewhere (level Omega lists or the identity)
   const int32_t* in_idx_ext = nullptr;
   const int32_t* out_idx_ext = nullptr;
@@ -202,6 +206,7 @@ struct Level {
   // batched solver where A has no block rows), applied with the RAS plan
   DBuf<double> Aw64, AwT64;
   DBuf<float> Aw32, AwT32;
+  double inv_err = 0.0;  // coarsest level: measured ||W A v - v|| / ||v||
   // ---- work vectors of the V-cycle ----------------------------------------
   DBuf<double> r64, x64, s64;
   DBuf<float> r32, x32, s32;

@@ -193,6 +193,30 @@ def test_level_operators_fp64(amg, name):
     p = _problem(c)
     ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
     H = _gpu(amg, p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
+    _check_level_operators(amg, c, H, ho)
+
+
+# tune = 2, 3, 4 force the staged kernel, shifted vector loads and lanes per
+# row (instead of row per lane) on every plan that allows them
+@pytest.mark.parametrize("tune", [2, 3, 4])
+@pytest.mark.parametrize("name", ["ragged_3lvl", "large_blocks", "q1_3d_12"])
+def test_kernel_forms_match_oracle(amg, name, tune):
+    c = CASES[name]
+    p = _problem(c)
+    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
+    H = amg.Hierarchy.from_problem(p, overlap=c["overlap"], c_min=c["c_min"], n_coarse=c["n_coarse"],
+                                   coarse_overlap=c.get("coarse_overlap", 0), tune=tune)
+    _check_level_operators(amg, c, H, ho)
+    b = seeded_rhs(p.n, 1, 5)[:, 0]
+    for prec in (amg.FP64, amg.MIXED32):
+        H.set_precision(prec)
+        x, info = H.solve(b, tol=1e-8)
+        assert info[0]["status"] == 0 and info[0]["relres_true"] <= 1e-8
+        x = x[:, 0] if x.ndim == 2 else x
+        assert np.linalg.norm(b - ho.levels[0].A @ x) <= 1.01e-8 * np.linalg.norm(b)
+
+
+def _check_level_operators(amg, c, H, ho):
     rng = np.random.default_rng(11)
     for lvl, Lo in enumerate(ho.levels[:-1]):
         x = rng.standard_normal(Lo.n)
@@ -225,6 +249,33 @@ def test_level_operators_fp64(amg, name):
     # A_L is written in the basis of level L-1
     tC = 1e-11 if len(ho.levels) == 2 else 1e-9
     assert _rel(_apply(amg, H, amg.OP_COARSE, len(ho.levels) - 1, xc, Lc.n), ref) <= tC
+
+
+@pytest.mark.parametrize("name", ["q1_64", "circ_ov2"])
+def test_coarsest_refinement_rule(amg, name):
+    """coarse_refine 0 / 1 / 2: never, when the measured inverse error
+    ||W A v - v|| / ||v|| exceeds 1e-13, always.  Refinement never makes the
+    coarsest solve worse than the plain explicit inverse."""
+    c = CASES[name]
+    p = _problem(c)
+    Hs = {m: amg.Hierarchy.from_problem(p, overlap=c["overlap"], c_min=c["c_min"], n_coarse=c["n_coarse"],
+                                        coarse_overlap=c.get("coarse_overlap", 0), coarse_refine=m)
+          for m in (0, 1, 2)}
+    st = {m: H.stats() for m, H in Hs.items()}
+    e = st[1]["coarsest_inv_err"]
+    assert 0.0 < e < 1e-6
+    assert st[0]["coarsest_refined"] is False
+    assert st[2]["coarsest_refined"] is True
+    assert st[1]["coarsest_refined"] is (e > 1e-13)
+    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
+    Lc = ho.levels[-1]
+    xc = np.random.default_rng(12).standard_normal(Lc.n)
+    ref = np.linalg.solve(Lc.A.toarray(), xc)
+    lc = len(ho.levels) - 1
+    err = {m: _rel(_apply(amg, H, amg.OP_COARSE, lc, xc, Lc.n), ref) for m, H in Hs.items()}
+    tC = 1e-11 if len(ho.levels) == 2 else 1e-9
+    assert max(err.values()) <= tC, err
+    assert err[2] <= 2.0 * err[0] + 1e-14, err
 
 
 @pytest.mark.parametrize("name", list(CASES))
