@@ -105,6 +105,10 @@ typedef struct {
                        /*   0 never; 1 (default) when setup measures      */
                        /*   ||W A v - v|| / ||v|| > 1e-13 for a seeded v  */
                        /*   (W the computed inverse); 2 always            */
+  int pdl;             /* 1: solve-phase kernels use programmatic         */
+                       /*   dependent launch (each starts while the one   */
+                       /*   before it drains, then waits for its results);*/
+                       /*   0 (default): plain stream order               */
 } amgdd_params;
 
 typedef struct amgdd_hierarchy amgdd_hierarchy; /* opaque, library-owned */

@@ -32,6 +32,7 @@ namespace amgdd {
 static thread_local std::string g_last_error;
 thread_local int* g_err_word = nullptr;
 thread_local int64_t g_alloc_bytes = 0;
+thread_local bool g_pdl = false;
 
 // Setup-time tuning context: whether to time alternatives, the problem/GPU
 // signature that keys the cache, and the cached choices (`key\tvalue` lines).
@@ -275,6 +276,14 @@ int build_items(SegPlan& p, const std::vector<int32_t>& nr, const std::vector<in
 
 // force: 0 picks the mode from the row length, 1 lanes-per-row chunks,
 // 2 row per lane (the caller then passes the transposed copy).
+// Default rows per CTA of the lanes-per-row form: enough CTAs to fill the GPU
+// (8 per SM), at least one row per lane group, at most 64.
+int default_rpc(int64_t rows, int lanes) {
+  const int ngrp = 128 / lanes;
+  const int64_t rpc = rows / (152 * 8);
+  return (int)std::max<int64_t>(ngrp, std::min<int64_t>(64, (rpc + ngrp - 1) / ngrp * ngrp));
+}
+
 // CTA chunks of the lanes-per-row form: `rpc` rows of one block each.
 int set_chunks(SegPlan& p, int rpc, cudaStream_t s) {
   std::vector<int32_t> cb, cr;
@@ -306,14 +315,7 @@ int build_seg(SegPlan& p, const std::vector<int32_t>& nr, const std::vector<int3
   p.in_len = cols;
   p.out_len = rows;
   p.lanes = lanes_for(p.max_nc);
-  // rows per CTA: enough CTAs to fill the GPU (8 per SM), at least one row
-  // per lane group
-  {
-    const int ngrp = 128 / p.lanes;
-    int64_t rpc = rows / (152 * 8);
-    rpc = std::max<int64_t>(ngrp, std::min<int64_t>(64, (rpc + ngrp - 1) / ngrp * ngrp));
-    p.rows_per_chunk = (int)rpc;
-  }
+  p.rows_per_chunk = default_rpc(rows, p.lanes);
   // 16-byte vector loads when every row starts aligned (FP32 and FP64 copies
   // share offsets, so 4-element alignment serves both)
   p.vec = p.nblocks > 0;
@@ -541,24 +543,30 @@ int build_blockrows(Level& L, cudaStream_t s) {
 // Setup-time choice of the gather-GEMV form for one plan: time the unstaged
 // scalar, staged and shifted-vector kernels and the row-per-lane kernel that
 // apply on scratch vectors (`nin` inputs, `nout` outputs) and keep the
-// fastest.  The staged form's arrays are freed when it loses.  The choice is
-// made in the precision T; `shift_only` then re-times, in the other
-// precision, only shifted against scalar loads for a plan that kept the
-// lanes-per-row form (the flag of each precision is separate).
+// fastest; the lanes-per-row forms also over lanes per row and rows per CTA.
+// The staged form's arrays are freed when it loses.  The choice is made in
+// the precision T; `shift_only` then re-times, in the other precision, only
+// shifted against scalar loads for a plan that kept a lanes-per-row form
+// (the flag of each precision is separate).  Cached choices are coded
+// form + 16 rows-per-CTA + 4096 lanes.
 template <class T>
 int tune_seg(SegPlan& p, const std::string& key, const T* M, const T* MT, int64_t nin, int64_t nout, SegMode mode,
              cudaStream_t s, bool shift_only = false) {
   constexpr bool f32 = sizeof(T) == 4;
   bool& shift = f32 ? p.shift : p.shift64;
   // candidate forms: 0 lanes per row, scalar loads; 1 staged (when built);
-  // 2 lanes per row with shifted vector loads (rows at any alignment, 32
-  // lanes per row; the W shifted copies of x take about 16 bytes of shared
+  // 2 lanes per row with shifted vector loads (rows at any alignment; the
+  // W shifted copies of x take about 16 bytes of shared
   // memory per column); 3 row per lane over the transposed copy (short rows)
   const bool chunk_now = !p.staged && !p.rows_mode;
   const bool can_rows = !shift_only && p.ntasks > 0 && MT != nullptr;
   const bool can_chunk = p.nchunks > 0 && (!shift_only || chunk_now);
-  const bool can_shift = can_chunk && !p.vec && p.lanes == 32 && 16.0 * (p.max_nc + 8) <= 160.0 * 1024.0;
+  const bool shift_fits = !p.vec && 16.0 * (p.max_nc + 8) <= 160.0 * 1024.0;
+  const bool can_shift = can_chunk && shift_fits;
   const bool rows0 = p.rows_mode;
+  const int lanes0 = p.lanes, rpc0 = p.rows_per_chunk;
+  int64_t nrows = 0;
+  for (int v : p.h_nr) nrows += v;
   auto drop_staged = [&p] {
     p.items.release();
     p.tabs.release();
@@ -574,13 +582,14 @@ int tune_seg(SegPlan& p, const std::string& key, const T* M, const T* MT, int64_
     p.staged = form == 1;
     p.rows_mode = form == 3 || (form == 1 && rows0);
   };
-  // rows per CTA of the lanes-per-row forms: the default (enough CTAs to
-  // fill the GPU) and larger chunks, which gather x(in_idx) fewer times
-  // (plans of a few large blocks on coarse levels)
-  const int rpc0 = p.rows_per_chunk;
-  std::vector<int> rpcs{rpc0};
-  if (!shift_only && can_chunk)
-    for (int r = 2 * rpc0; r <= 64; r *= 2) rpcs.push_back(r);
+  // lanes-per-row layout (lanes, rows per CTA); restores the built one for
+  // the other forms
+  auto set_layout = [&](int lanes, int rpc) -> int {
+    if (p.lanes == lanes && p.rows_per_chunk == rpc) return AMGDD_OK;
+    p.lanes = lanes;
+    p.unroll = lanes == 32 && nrows > 0 && (double)p.mat_len / (double)nrows >= 512.0;
+    return set_chunks(p, rpc, s);
+  };
   double cached = 0.0;
   if (g_tune && (g_tune->get(key, cached) || !g_tune->on)) {
     // without timing: the built form (row per lane for short rows), or the
@@ -591,12 +600,15 @@ int tune_seg(SegPlan& p, const std::string& key, const T* M, const T* MT, int64_
       set_form(form == 2 ? 2 : 0);
       return AMGDD_OK;
     }
+    const int lanes = g_tune->on ? code / 4096 : 0, rpc = g_tune->on ? (code / 16) % 256 : 0;
+    const bool lanes_ok = lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32;
+    if (lanes_ok && rpc > 0 && can_chunk) AMGDD_TRY(set_layout(lanes, rpc));
     if ((form == 1 && !p.staged) || (form == 2 && !can_shift) || (form == 3 && !can_rows) ||
-        ((form == 0 || form == 2) && !can_chunk))
+        ((form == 0 || form == 2) && !can_chunk)) {
       form = rows0 ? 3 : 0;
+      if (can_chunk) AMGDD_TRY(set_layout(lanes0, rpc0));
+    }
     set_form(form);
-    const int rpc = g_tune->on ? code / 16 : 0;
-    if ((form == 0 || form == 2) && rpc > 0 && rpc != rpc0 && rpc <= 64) AMGDD_TRY(set_chunks(p, rpc, s));
     if (!p.staged) drop_staged();
     return AMGDD_OK;
   }
@@ -608,46 +620,68 @@ int tune_seg(SegPlan& p, const std::string& key, const T* M, const T* MT, int64_
   AMGDD_TRY(yout.zero(s));
   AMGDD_TRY(cin.zero(s));
   const bool built = !shift_only && p.staged;
+  // candidates (form, lanes, rows per CTA)
+  struct Cand {
+    int form, lanes, rpc;
+  };
+  std::vector<Cand> cands;
+  if (shift_only) {
+    cands.push_back({0, lanes0, rpc0});
+    cands.push_back({2, lanes0, rpc0});
+  } else {
+    if (built) cands.push_back({1, lanes0, rpc0});
+    if (can_rows) cands.push_back({3, lanes0, rpc0});
+    if (can_chunk)
+      for (int form : {0, 2}) {
+        if (form == 2 && !can_shift) continue;
+        std::vector<int> ls{lanes0};
+        for (int l : {4, 8, 16, 32})
+          if (l != lanes0) ls.push_back(l);
+        for (int l : ls) {
+          const int r0 = l == lanes0 ? rpc0 : default_rpc(nrows, l);
+          for (int r = r0; r <= std::max(r0, 128); r *= 2) cands.push_back({form, l, r});
+        }
+      }
+  }
   cudaEvent_t e[2];
   for (auto& v : e) AMGDD_CUDA(cudaEventCreate(&v));
-  float t[4] = {0.f, 0.f, 0.f, 0.f};
-  int best_rpc[4] = {rpc0, rpc0, rpc0, rpc0};
-  const bool ok[4] = {can_chunk, built, can_shift, can_rows};
   constexpr int kReps = 8;
   int rc = AMGDD_OK;
-  for (int form = 0; form < 4 && rc == AMGDD_OK; ++form) {
-    if (!ok[form]) continue;
-    set_form(form);
-    const bool chunked = form == 0 || form == 2;
-    for (size_t ri = 0; ri < (chunked ? rpcs.size() : 1) && rc == AMGDD_OK; ++ri) {
-      if (chunked && p.rows_per_chunk != rpcs[ri]) rc = set_chunks(p, rpcs[ri], s);
-      for (int rep = 0; rep < kReps + 2 && rc == AMGDD_OK; ++rep) {
-        if (rep == 2) cudaEventRecord(e[0], s);
-        rc = launch_seg(p, M, f32, xin.p, yout.p, f32, mode, nullptr, s, mode == SEG_RESID ? cin.p : nullptr,
-                        nullptr, MT);
-      }
-      cudaEventRecord(e[1], s);
-      float ms = 0.f;
-      if (cudaEventSynchronize(e[1]) != cudaSuccess || cudaEventElapsedTime(&ms, e[0], e[1]) != cudaSuccess)
-        rc = AMGDD_ERR_CUDA;
-      if (ri == 0 || ms < t[form]) {
-        t[form] = ms;
-        best_rpc[form] = rpcs[ri];
-      }
+  float best_t = 0.f;
+  int best = -1;
+  float tf[4] = {0.f, 0.f, 0.f, 0.f};
+  for (size_t ci = 0; ci < cands.size() && rc == AMGDD_OK; ++ci) {
+    const Cand& c = cands[ci];
+    set_form(c.form);
+    if (c.form == 0 || c.form == 2) rc = set_layout(c.lanes, c.rpc);
+    for (int rep = 0; rep < kReps + 2 && rc == AMGDD_OK; ++rep) {
+      if (rep == 2) cudaEventRecord(e[0], s);
+      rc = launch_seg(p, M, f32, xin.p, yout.p, f32, mode, nullptr, s, mode == SEG_RESID ? cin.p : nullptr, nullptr,
+                      MT);
+    }
+    cudaEventRecord(e[1], s);
+    float ms = 0.f;
+    if (rc == AMGDD_OK &&
+        (cudaEventSynchronize(e[1]) != cudaSuccess || cudaEventElapsedTime(&ms, e[0], e[1]) != cudaSuccess))
+      rc = AMGDD_ERR_CUDA;
+    if (tf[c.form] == 0.f || ms < tf[c.form]) tf[c.form] = ms;
+    if (best < 0 || ms < best_t) {
+      best = (int)ci;
+      best_t = ms;
     }
   }
   for (auto& v : e) cudaEventDestroy(v);
   AMGDD_TRY(rc);
-  int best = -1;
-  for (int form = 0; form < 4; ++form)
-    if (ok[form] && (best < 0 || t[form] < t[best])) best = form;
-  set_form(best);
-  if (p.rows_per_chunk != best_rpc[best] && can_chunk) AMGDD_TRY(set_chunks(p, best_rpc[best], s));
-  if (g_tune) g_tune->put(key, (double)(best + (shift_only ? 0 : 16 * p.rows_per_chunk)));
+  const Cand& b = cands[best];
+  set_form(b.form);
+  if (can_chunk) AMGDD_TRY((b.form == 0 || b.form == 2) ? set_layout(b.lanes, b.rpc) : set_layout(lanes0, rpc0));
+  if (g_tune) g_tune->put(key, (double)(b.form + (shift_only ? 0 : 16 * p.rows_per_chunk + 4096 * p.lanes)));
   if (g_timer.on)
-    fprintf(stderr, "[amgdd]   plan %d blocks (%s): lanes/row %.1f us, staged %.1f us, shifted %.1f us, row/lane %.1f us -> %d (%d rows per CTA)\n",
-            p.nblocks, f32 ? "fp32" : "fp64", 1e3 * t[0] / kReps, 1e3 * t[1] / kReps, 1e3 * t[2] / kReps,
-            1e3 * t[3] / kReps, best, p.rows_per_chunk);
+    fprintf(stderr,
+            "[amgdd]   plan %d blocks (%s): lanes/row %.1f us, staged %.1f us, shifted %.1f us, row/lane %.1f us -> "
+            "%d (%d lanes, %d rows per CTA)\n",
+            p.nblocks, f32 ? "fp32" : "fp64", 1e3 * tf[0] / kReps, 1e3 * tf[1] / kReps, 1e3 * tf[2] / kReps,
+            1e3 * tf[3] / kReps, b.form, p.lanes, p.rows_per_chunk);
   if (!shift_only && !p.staged) drop_staged();
   return AMGDD_OK;
 }
@@ -759,6 +793,10 @@ struct amgdd_hierarchy {
   int ph_grid[2] = {0, 0};
   int persist_from[2] = {0, 0};
   double persist_us[2][16] = {};  // setup-time V-cycle timings by first level (0 = all separate launches)
+  // dense tail per precision: the V-cycle from this level down is one
+  // GEMV with the matrix B of that level (0 = not used)
+  int dense_from[2] = {0, 0};
+  double dense_us[2][16] = {};  // setup-time V-cycle timings by dense level (0 = none)
   DBuf<unsigned> bar;
   // batched right-hand sides: CG vectors (n x kMaxRhs, interleaved), K
   // states, graphs per precision and K in {2, 4, 8}; allocated at the first
@@ -1388,6 +1426,11 @@ static int vcycle(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, c
     return launch_persistent(h.d_ph[pi].p, h.nph[pi], h.ph_smem[pi], h.ph_grid[pi], h.bar.p, &h.st.p->vc_err, skip,
                              s);
   }
+  if (l > 0 && h.dense_from[pi] == l) {  // the V-cycle from here down as one GEMV
+    AMGDD_MARK(0);
+    return launch_seg(L.dplan, f32 ? (const void*)L.B32.p : (const void*)L.B64.p, f32, r, x, f32, SEG_STORE, skip, s,
+                      nullptr, nullptr, f32 ? (const void*)L.Bt32.p : (const void*)L.Bt64.p);
+  }
   if (L.coarsest) {
     if (f32) {
       AMGDD_MARK(1);
@@ -1435,12 +1478,21 @@ static int vcycle(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, c
 // the order the separate launches of `vcycle` take (Section 3.1).  Needs A by
 // block rows on every non-coarsest level of the tail; returns false if not.
 static bool tail_phases(amgdd_hierarchy& h, int from, bool f32, std::vector<PhaseDesc>& ph) {
-  const int nl = (int)h.lv.size();
+  const int df = h.dense_from[f32 ? 1 : 0];
+  const int nl = df > 0 ? df + 1 : (int)h.lv.size();  // the dense tail ends the descent
   ph.clear();
+  if (df > 0 && from >= df) return false;
   for (int l = from; l < nl; ++l)
-    if (!h.lv[l]->coarsest && !h.lv[l]->has_blk) return false;
+    if (!h.lv[l]->coarsest && l != df && !h.lv[l]->has_blk) return false;
   for (int l = from; l < nl; ++l) {
     Level& L = *h.lv[l];
+    if (l == df) {
+      ph.push_back(seg_phase(L.dplan, f32 ? (const void*)L.B32.p : (const void*)L.B64.p,
+                             f32 ? (const void*)L.Bt32.p : (const void*)L.Bt64.p, f32,
+                             f32 ? (const void*)L.r32.p : (const void*)L.r64.p, f32 ? (void*)L.x32.p : (void*)L.x64.p,
+                             SEG_STORE));
+      break;
+    }
     if (L.coarsest) {
       if (f32) ph.push_back(cast_phase(L.r32.p, true, L.r64.p, false, L.n));
       ph.push_back(seg_phase(L.ras, L.W64.p, L.Wt64.p, false, L.r64.p, L.x64.p, SEG_STORE));
@@ -1497,6 +1549,173 @@ static int set_tail(amgdd_hierarchy& h, int pi, int from) {
   return AMGDD_OK;
 }
 
+// Mean device time, in microseconds, of one V-cycle from level l on (r, x),
+// captured in a graph as the solve runs it (eager launches would add host
+// launch time): 3 warm-up and 10 timed graph launches.
+static int time_vcycle_graph(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, double* us) {
+  cudaStream_t s = h.work;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  AMGDD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int rc = vcycle(h, l, f32, r, x, nullptr, s);
+  const cudaError_t ce = cudaStreamEndCapture(s, &g);
+  if (rc == AMGDD_OK && (ce != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess)) {
+    set_error("V-cycle graph capture failed during setup");
+    rc = AMGDD_ERR_CUDA;
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaEvent_t e[2] = {nullptr, nullptr};
+  for (auto& v : e)
+    if (rc == AMGDD_OK && cudaEventCreate(&v) != cudaSuccess) rc = AMGDD_ERR_CUDA;
+  for (int k = 0; k < 13 && rc == AMGDD_OK; ++k) {
+    if (k == 3) cudaEventRecord(e[0], s);
+    if (cudaGraphLaunch(ge, s) != cudaSuccess) rc = AMGDD_ERR_CUDA;
+  }
+  float ms = 0.f;
+  if (rc == AMGDD_OK) {
+    cudaEventRecord(e[1], s);
+    if (cudaEventSynchronize(e[1]) != cudaSuccess || cudaEventElapsedTime(&ms, e[0], e[1]) != cudaSuccess)
+      rc = AMGDD_ERR_CUDA;
+  }
+  if (ge) cudaGraphExecDestroy(ge);
+  for (auto& v : e)
+    if (v) cudaEventDestroy(v);
+  *us = 1e3 * ms / 10.0;
+  return rc;
+}
+
+// Dense tail of level l: B = the FP64 V-cycle from l applied to the unit
+// vectors (the cycle is a fixed linear map of r when x starts at 0, Section
+// 3.1), so that the cycle from l down becomes one GEMV.  Column j of B is
+// computed into row j of Bt64 (Bt64 = B^T, row-major); B64, B32 and Bt32
+// follow by a tiled transpose and casts.  Any dense tail already chosen
+// below l serves the computation.
+static int build_dense(amgdd_hierarchy& h, int l) {
+  cudaStream_t s = h.work;
+  Level& L = *h.lv[l];
+  const int64_t n = L.n;
+  AMGDD_TRY(L.Bt64.alloc((size_t)(n * n)));
+  DBuf<double> rv, xv, one;
+  AMGDD_TRY(rv.alloc(n));
+  AMGDD_TRY(xv.alloc(n));
+  const std::vector<double> unit{1.0};
+  AMGDD_TRY(one.upload(unit, s));
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  AMGDD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int rc = vcycle(h, l, false, rv.p, xv.p, nullptr, s);
+  const cudaError_t ce = cudaStreamEndCapture(s, &g);
+  if (rc == AMGDD_OK && (ce != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess)) {
+    set_error("dense tail: V-cycle graph capture failed");
+    rc = AMGDD_ERR_CUDA;
+  }
+  if (g) cudaGraphDestroy(g);
+  for (int64_t j = 0; j < n && rc == AMGDD_OK; ++j) {
+    if (cudaMemsetAsync(rv.p, 0, n * sizeof(double), s) != cudaSuccess ||
+        cudaMemcpyAsync(rv.p + j, one.p, sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaGraphLaunch(ge, s) != cudaSuccess ||
+        cudaMemcpyAsync(L.Bt64.p + j * n, xv.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      rc = AMGDD_ERR_CUDA;
+  }
+  if (ge) cudaGraphExecDestroy(ge);
+  AMGDD_TRY(rc);
+  AMGDD_TRY(L.B64.alloc((size_t)(n * n)));
+  AMGDD_TRY(L.B32.alloc((size_t)(n * n)));
+  AMGDD_TRY(L.Bt32.alloc((size_t)(n * n)));
+  AMGDD_TRY(launch_dense_pack(L.Bt64.p, (int)n, L.B64.p, L.B32.p, L.Bt32.p, s));
+  const std::vector<int32_t> nr{(int32_t)n}, nc{(int32_t)n};
+  const std::vector<int64_t> zero{0};
+  AMGDD_TRY(build_seg(L.dplan, nr, nc, zero, zero, zero, h.iota.p, h.iota.p, s));
+  const std::string k = "L" + std::to_string(l) + "|dense";
+  AMGDD_TRY(tune_seg<float>(L.dplan, k, L.B32.p, L.Bt32.p, n, n, SEG_STORE, s));
+  AMGDD_TRY(tune_seg<double>(L.dplan, k + "64", L.B64.p, L.Bt64.p, n, n, SEG_STORE, s, true));
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  return AMGDD_OK;
+}
+
+static void drop_dense(Level& L) {
+  L.B64.release();
+  L.Bt64.release();
+  L.B32.release();
+  L.Bt32.release();
+}
+
+// Setup-time choice of the dense tail, per precision.  Candidates are the
+// levels l >= 1 above the coarsest with n_l <= kDenseMaxN, deepest first;
+// a candidate is built only while a GEMV of its FP32 matrix at the measured
+// copy bandwidth could beat the measured V-cycle from l.  Every built
+// candidate is timed in the V-cycle from level 0 (graph), against none.
+constexpr int64_t kDenseMaxN = 12288;
+constexpr double kHbmBytesPerUs = 6.8e6;
+
+static int tune_dense(amgdd_hierarchy& h) {
+  cudaStream_t s = h.work;
+  const int nl = (int)h.lv.size();
+  Level& L0 = *h.lv[0];
+  h.dense_from[0] = h.dense_from[1] = 0;
+  double c64 = 0.0, c32 = 0.0;
+  if (g_tune && ((g_tune->get("dense|fp64", c64) && g_tune->get("dense|mixed", c32)) || !g_tune->on)) {
+    const int want[2] = {g_tune->on ? (int)c64 : 0, g_tune->on ? (int)c32 : 0};
+    // build deepest first, so that a shallower matrix is computed through it
+    for (int l = nl - 2; l >= 1; --l) {
+      if (want[0] != l && want[1] != l) continue;
+      if (h.lv[l]->coarsest || h.lv[l]->n > kDenseMaxN) continue;
+      AMGDD_TRY(build_dense(h, l));
+      for (int pi = 0; pi < 2; ++pi)
+        if (want[pi] == l) h.dense_from[pi] = l;
+    }
+    return AMGDD_OK;
+  }
+  AMGDD_TRY(L0.r32.zero(s));
+  AMGDD_TRY(h.r.zero(s));
+  const void* r[2] = {h.r.p, L0.r32.p};
+  void* x[2] = {h.z.p, L0.x32.p};
+  double best_us[2];
+  int best[2] = {0, 0};
+  for (int pi = 0; pi < 2; ++pi) {
+    AMGDD_TRY(time_vcycle_graph(h, 0, pi == 1, r[pi], x[pi], &best_us[pi]));
+    h.dense_us[pi][0] = best_us[pi];
+  }
+  for (int l = nl - 2; l >= 1; --l) {
+    Level& L = *h.lv[l];
+    if (L.coarsest || L.n > kDenseMaxN) break;
+    double from_l = 0.0;
+    AMGDD_TRY(L.r32.zero(s));
+    AMGDD_TRY(time_vcycle_graph(h, l, true, L.r32.p, L.x32.p, &from_l));
+    L.vc_us[1] = from_l;
+    if ((double)L.n * (double)L.n * 4.0 / kHbmBytesPerUs >= from_l) break;
+    AMGDD_TRY(build_dense(h, l));
+    bool keep = false;
+    for (int pi = 0; pi < 2; ++pi) {
+      const int prev = h.dense_from[pi];
+      h.dense_from[pi] = l;
+      double us = 0.0;
+      AMGDD_TRY(time_vcycle_graph(h, 0, pi == 1, r[pi], x[pi], &us));
+      h.dense_us[pi][l] = us;
+      if (us < best_us[pi]) {
+        best_us[pi] = us;
+        best[pi] = l;
+        keep = true;
+      } else {
+        h.dense_from[pi] = prev;
+      }
+    }
+    if (!keep) drop_dense(L);
+  }
+  for (int l = 1; l + 1 < nl; ++l)
+    if (l != best[0] && l != best[1]) drop_dense(*h.lv[l]);
+  h.dense_from[0] = best[0];
+  h.dense_from[1] = best[1];
+  if (g_tune) {
+    g_tune->put("dense|fp64", (double)best[0]);
+    g_tune->put("dense|mixed", (double)best[1]);
+  }
+  if (g_timer.on)
+    fprintf(stderr, "[amgdd] dense tail: fp64 from level %d (%.1f us), mixed from level %d (%.1f us)\n", best[0],
+            best_us[0], best[1], best_us[1]);
+  return AMGDD_OK;
+}
+
 // Setup-time choice of the persistent tail: time V-cycles with the tail
 // starting at each level (and with none) and keep the fastest, per precision.
 static int tune_tail(amgdd_hierarchy& h) {
@@ -1508,9 +1727,6 @@ static int tune_tail(amgdd_hierarchy& h) {
   Level& L0 = *h.lv[0];
   AMGDD_TRY(L0.r32.zero(s));
   AMGDD_TRY(h.r.zero(s));
-  cudaEvent_t e0, e1;
-  AMGDD_CUDA(cudaEventCreate(&e0));
-  AMGDD_CUDA(cudaEventCreate(&e1));
   int rc = AMGDD_OK;
   for (int pi = 0; pi < 2 && rc == AMGDD_OK; ++pi) {
     const bool f32 = pi == 1;
@@ -1527,19 +1743,8 @@ static int tune_tail(amgdd_hierarchy& h) {
     for (int from = 0; from < std::min(nl, 16) && rc == AMGDD_OK; ++from) {
       if ((rc = set_tail(h, pi, from)) != AMGDD_OK) break;
       if (from > 0 && h.persist_from[pi] != from) continue;  // tail not expressible from this level
-      constexpr int kWarm = 3, kReps = 10;
-      for (int k = 0; k < kWarm + kReps && rc == AMGDD_OK; ++k) {
-        if (k == kWarm) cudaEventRecord(e0, s);
-        rc = vcycle(h, 0, f32, r, x, nullptr, s);
-      }
-      if (rc != AMGDD_OK) break;
-      cudaEventRecord(e1, s);
-      float ms = 0.f;
-      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-        rc = AMGDD_ERR_CUDA;
-        break;
-      }
-      const double us = 1e3 * ms / kReps;
+      double us = 0.0;
+      if ((rc = time_vcycle_graph(h, 0, f32, r, x, &us)) != AMGDD_OK) break;
       h.persist_us[pi][from] = us;
       if (from == 0 || us < best_us) {
         best = from;
@@ -1552,8 +1757,6 @@ static int tune_tail(amgdd_hierarchy& h) {
       fprintf(stderr, "[amgdd] %s V-cycle: persistent tail from level %d (%.1f us)\n", f32 ? "mixed" : "fp64", best,
               best_us);
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   AMGDD_TRY(rc);
   PcgState st{};
   AMGDD_CUDA(cudaMemcpy(&st, h.st.p, sizeof st, cudaMemcpyDeviceToHost));
@@ -1872,6 +2075,12 @@ static int resid_multi(const Level& L, bool f32, int K, const void* x, const voi
 static int vcycle_multi(amgdd_hierarchy& h, int l, bool f32, int K, const void* r, void* x, const int* skip,
                         cudaStream_t s) {
   Level& L = *h.lv[l];
+  // the dense tail stages K columns of its whole input in shared memory;
+  // beyond that the separate levels below it serve
+  if (l > 0 && h.dense_from[f32 ? 1 : 0] == l && L.n * K * (f32 ? 4 : 8) <= 200 * 1024)
+    return launch_seg_multi(L.dplan, f32 ? (const void*)L.B32.p : (const void*)L.B64.p,
+                            f32 ? (const void*)L.Bt32.p : (const void*)L.Bt64.p, f32, r, x, SEG_STORE, nullptr, K,
+                            skip, s);
   if (L.coarsest) {
     const void* r64 = r;
     void* x64 = x;
@@ -2127,6 +2336,7 @@ amgdd_params amgdd_params_default(void) {
   p.tune_cache = nullptr;
   p.coarse_overlap = 0;
   p.coarse_refine = 1;
+  p.pdl = 0;
   return p;
 }
 
@@ -2223,6 +2433,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   AMGDD_TRY(H->st.alloc(1));
   AMGDD_TRY(H->st.zero(s));
   ErrScope err_scope(&H->st.p->vc_err);
+  PdlScope pdl_scope(prm.pdl != 0);
   TuneCtx tctx;
   tctx.on = prm.tune == 1;
   tctx.prefer_form = prm.tune == 2 ? 1 : (prm.tune == 3 ? 2 : (prm.tune == 4 ? 0 : -1));
@@ -2230,8 +2441,8 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   {
     cudaDeviceProp prop;
     AMGDD_CUDA(cudaGetDeviceProperties(&prop, H->device));
-    // "f5": plan choices take the four forms of tune_seg and rows per CTA
-    std::string sig = std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "|f5|m" +
+    // "f8": plan choices code form, rows per CTA and lanes per row; tails timed as graphs
+    std::string sig = std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "|f8|m" +
                       std::to_string(m) + "|n" + std::to_string(n) + "|nnz" + std::to_string(nnz) + "|ov" +
                       std::to_string(overlap) + "/" + std::to_string(prm.coarse_overlap) + "|cr" + std::to_string(prm.coarse_refine) + "|nc" + std::to_string(prm.n_coarse) + "|L" +
                       std::to_string(prm.L_max) + "|c";
@@ -2381,6 +2592,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   AMGDD_CUDA(cudaEventCreateWithFlags(&H->join[0], cudaEventDisableTiming));
   AMGDD_CUDA(cudaEventCreateWithFlags(&H->join[1], cudaEventDisableTiming));
   AMGDD_CUDA(cudaStreamSynchronize(s));
+  AMGDD_TRY(tune_dense(*H));
   AMGDD_TRY(tune_tail(*H));
   tctx.save();
   H->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -2410,6 +2622,7 @@ int amgdd_solve(amgdd_hierarchy* h, const double* b, int nrhs, double tol, doubl
   }
   try {
     ErrScope err_scope(&h->st.p->vc_err);
+    PdlScope pdl_scope(h->prm.pdl != 0);
     cudaStream_t us = (cudaStream_t)stream;
     cudaStream_t s = h->work;
     AMGDD_CUDA(cudaEventRecord(h->join[0], us));
@@ -2472,6 +2685,7 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
     return AMGDD_ERR_INVALID_ARG;
   }
   ErrScope err_scope(&h->st.p->vc_err);
+  PdlScope pdl_scope(h->prm.pdl != 0);
   cudaStream_t s = (cudaStream_t)stream;
   Level& L = *h->lv[level];
   const bool f32 = h->precision == AMGDD_MIXED32;
@@ -2581,6 +2795,7 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
     return AMGDD_ERR_INVALID_ARG;
   }
   ErrScope err_scope(&h->st.p->vc_err);
+  PdlScope pdl_scope(h->prm.pdl != 0);
   cudaStream_t s = (cudaStream_t)stream;
   Level& L = *h->lv[level];
   const bool f32 = h->precision == AMGDD_MIXED32;
@@ -2664,6 +2879,7 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes
     return AMGDD_ERR_INVALID_ARG;
   }
   ErrScope err_scope(&h->st.p->vc_err);
+  PdlScope pdl_scope(h->prm.pdl != 0);
   const int nl = (int)h->lv.size();
   for (int i = 0; i < nl * VProf::kSlots; ++i) ms[i] = bytes[i] = 0.0;
   cudaStream_t s = h->work;
@@ -2688,9 +2904,14 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes
     }
   }
   const size_t esz = f32 ? 4 : 8;
+  const int df = h->dense_from[f32 ? 1 : 0];
   for (int l = 0; l < nl; ++l) {
     const Level& L = *h->lv[l];
     double* b = bytes + l * VProf::kSlots;
+    if (df > 0 && l >= df) {  // the dense tail: one GEMV at level df, nothing below
+      if (l == df) b[0] = seg_bytes(L.dplan, L.n, L.n, false, esz);
+      continue;
+    }
     if (L.coarsest) {
       b[0] = seg_bytes(L.ras, L.n, L.n, false, 8) * (h->prm.coarse_refine && L.Aw64.p ? 3.0 : 1.0);
       if (f32) b[1] = b[5] = (double)L.n * 12.0;
@@ -2818,8 +3039,16 @@ static void level_bytes(const amgdd_hierarchy& h, const Level& L, size_t esz, do
 int amgdd_bytes_model(const amgdd_hierarchy* h, double* vcycle_bytes, double* apply_out) {
   if (h == nullptr) return AMGDD_ERR_INVALID_ARG;
   const size_t esz = h->precision == AMGDD_MIXED32 ? 4 : 8;
+  const int df = h->dense_from[esz == 4 ? 1 : 0];
   double cyc = 0.0;
-  for (const auto& L : h->lv) level_bytes(*h, *L, esz, cyc);
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    const Level& L = *h->lv[l];
+    if (df > 0 && (int)l == df) {
+      cyc += seg_bytes(L.dplan, L.n, L.n, false, esz);
+      break;
+    }
+    level_bytes(*h, L, esz, cyc);
+  }
   const Level& L0 = *h->lv[0];
   const double ap = apply_bytes(L0, 8);
   if (vcycle_bytes) *vcycle_bytes = cyc;
@@ -2868,7 +3097,18 @@ int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap) {
                   (h->prm.coarse_refine && C.Aw64.p) ? "true" : "false");
     s += buf;
   }
-  s += ", \"tail\": {";
+  s += ", \"dense_tail\": {";
+  for (int pi = 0; pi < 2; ++pi) {
+    s += std::string(pi ? ", " : "") + (pi ? "\"mixed\"" : "\"fp64\"") + ": {\"from\": " +
+         std::to_string(h->dense_from[pi]) + ", \"vcycle_us_by_level\": [";
+    for (size_t l = 0; l < std::min<size_t>(h->lv.size(), 16); ++l) {
+      char buf[32];
+      std::snprintf(buf, sizeof buf, "%s%.1f", l ? ", " : "", h->dense_us[pi][l]);
+      s += buf;
+    }
+    s += "]}";
+  }
+  s += "}, \"tail\": {";
   for (int pi = 0; pi < 2; ++pi) {
     s += std::string(pi ? ", " : "") + (pi ? "\"mixed\"" : "\"fp64\"") + ": {\"from\": " +
          std::to_string(h->persist_from[pi]) + ", \"vcycle_us_by_from\": [";

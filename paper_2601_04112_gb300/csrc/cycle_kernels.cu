@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
                                                      const int32_t* __restrict__ out_idx, const T* __restrict__ M,
                                                      const T* __restrict__ x, T* __restrict__ y, const int* skip,
                                                      const T* __restrict__ csrc, T* __restrict__ cdst, int64_t m_len) {
+  pdl_prologue();
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using V = typename Vec2<T>::type;
@@ -224,6 +225,7 @@ __global__ void __launch_bounds__(128) k_seg_rows(const int32_t* __restrict__ ta
                                                   const int32_t* __restrict__ out_idx, const T* __restrict__ MT,
                                                   const T* __restrict__ x, T* __restrict__ y, const int* skip,
                                                   const T* __restrict__ csrc, T* __restrict__ cdst) {
+  pdl_prologue();
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int grp = (int)threadIdx.x / L;
@@ -431,6 +433,7 @@ __device__ bool item_run(const PhaseDesc& P, int it, unsigned char* smem, uint64
 template <class T, int L>
 __global__ void __launch_bounds__(kItemThreads) k_seg_staged(const __grid_constant__ PhaseDesc P, const int* skip,
                                                              int* err) {
+  pdl_prologue();
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -448,9 +451,9 @@ int seg_rows_launch(const SegPlan& p, const T* MT, const T* x, T* y, const int* 
   const size_t smem = (size_t)per * p.max_nc * sizeof(T);
   auto kern = k_seg_rows<T, L, MODE>;
   if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, 128, smem, s>>>(p.task_blk.p, p.task_row0.p, p.task_nrow.p, p.ntasks, p.max_nc, p.m_off.p, p.nr.p,
+  AMGDD_CUDA(launch_k(g_pdl, kern, grid, 128, smem, s, p.task_blk.p, p.task_row0.p, p.task_nrow.p, p.ntasks, p.max_nc, p.m_off.p, p.nr.p,
                                p.nc.p, p.in_off.p, p.out_off.p, p.in_idx_ext, p.out_idx_ext, MT, x, y, skip, csrc,
-                               cdst);
+                               cdst));
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
   return AMGDD_OK;
@@ -473,9 +476,9 @@ int seg_launch_kind(const SegPlan& p, const T* M, const T* x, T* y, SegMode mode
                     const T* csrc, T* cdst, size_t smem) {
   auto launch = [&](auto kern) -> int {
     if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<p.nchunks, kSegThreads, smem, s>>>(p.chunk_blk.p, p.chunk_row0.p, p.rows_per_chunk, p.m_off.p, p.nr.p,
+    AMGDD_CUDA(launch_k(g_pdl, kern, p.nchunks, kSegThreads, smem, s, p.chunk_blk.p, p.chunk_row0.p, p.rows_per_chunk, p.m_off.p, p.nr.p,
                                               p.nc.p, p.in_off.p, p.out_off.p, p.in_idx_ext, p.out_idx_ext, M, x, y,
-                                              skip, csrc, cdst, p.mat_len);
+                                              skip, csrc, cdst, p.mat_len));
     AMGDD_CUDA(cudaGetLastError());
     count_kernels(1);
     return AMGDD_OK;
@@ -500,13 +503,11 @@ template <class T, int L>
 int seg_dispatch_mode(const SegPlan& p, const T* M, const T* x, T* y, SegMode mode, const int* skip,
                       cudaStream_t s, const T* csrc, T* cdst) {
   const size_t smem = (size_t)p.max_nc * sizeof(T);
+  // the shifted form (always with the 4-way unrolled gather and row loops)
+  // needs a 16-byte aligned base (device allocations are)
+  if ((sizeof(T) == 4 ? p.shift : p.shift64) && !p.vec && ((uintptr_t)M & 15) == 0)
+    return seg_launch_kind<T, L, 2, 4>(p, M, x, y, mode, skip, s, csrc, cdst, seg_shift_smem<T>(p));
   if constexpr (L == 32) {
-    // the shifted form needs a 16-byte aligned base (device allocations are)
-    if ((sizeof(T) == 4 ? p.shift : p.shift64) && !p.vec && ((uintptr_t)M & 15) == 0) {
-      const size_t sm2 = seg_shift_smem<T>(p);
-      return p.unroll ? seg_launch_kind<T, L, 2, 4>(p, M, x, y, mode, skip, s, csrc, cdst, sm2)
-                      : seg_launch_kind<T, L, 2, 1>(p, M, x, y, mode, skip, s, csrc, cdst, sm2);
-    }
     if (p.unroll)
       return p.vec ? seg_launch_kind<T, L, 1, 4>(p, M, x, y, mode, skip, s, csrc, cdst, smem)
                    : seg_launch_kind<T, L, 0, 4>(p, M, x, y, mode, skip, s, csrc, cdst, smem);
@@ -646,6 +647,7 @@ template <class T, bool BIG>
 __global__ void __launch_bounds__(kApplyThreads) k_apply(ApplyArgs a, const T* __restrict__ R,
                                                          const T* __restrict__ x, T* __restrict__ y, T sign,
                                                          const int* skip) {
+  pdl_prologue();
   if (skip != nullptr && *skip) return;
   int bkt = 0;
   while (bkt + 1 < a.nbuckets && (int)blockIdx.x >= a.bucket_start[bkt + 1]) ++bkt;
@@ -688,6 +690,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(ApplyArgs a, const T* _
 // ---------------------------------------------------------------------------
 template <class S, class D>
 __global__ void k_cast(const S* __restrict__ src, D* __restrict__ dst, int64_t n, const int* skip) {
+  pdl_prologue();
   if (skip != nullptr && *skip) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = (D)src[i];
@@ -708,6 +711,7 @@ constexpr int kDotThreads = 256;
 __global__ void __launch_bounds__(kDotThreads) k_dot_partial(const double* __restrict__ a, const double* __restrict__ b,
                                                              const double* __restrict__ c, int64_t n,
                                                              double* __restrict__ partials, const int* skip) {
+  pdl_prologue();
   if (skip != nullptr && *skip) return;
   double s0 = 0.0, s1 = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -744,6 +748,7 @@ __global__ void __launch_bounds__(kDotThreads) k_dot_partial(const double* __res
 //        4: bnorm2 = sum(b.b); tol2 = tol^2 bnorm2 (tol passed in st->tol2)
 __global__ void __launch_bounds__(1024) k_pcg_scalar(int which, PcgState* st, const double* __restrict__ partials,
                                                      cudaGraphConditionalHandle cond, int use_cond) {
+  pdl_prologue();
   if (which != 0 && which != 4 && st->done) {
     if (which == 3 && use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
     return;
@@ -824,6 +829,7 @@ __global__ void __launch_bounds__(1024) k_pcg_scalar(int which, PcgState* st, co
 
 __global__ void k_update_xr(const PcgState* __restrict__ st, double* __restrict__ x, double* __restrict__ r,
                             const double* __restrict__ p, const double* __restrict__ q, int64_t n) {
+  pdl_prologue();
   if (st->done) return;
   const double al = st->alpha;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -834,6 +840,7 @@ __global__ void k_update_xr(const PcgState* __restrict__ st, double* __restrict_
 
 __global__ void k_update_p(const PcgState* __restrict__ st, double* __restrict__ p, const double* __restrict__ z,
                            double* __restrict__ zold, int64_t n) {
+  pdl_prologue();
   if (st->done) return;
   const double be = st->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -864,7 +871,7 @@ int launch_seg(const SegPlan& p, const void* M, bool m_fp32, const void* x, void
     auto go = [&](auto kern) -> int {
       if (smem > 48 * 1024)
         AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      kern<<<p.nitems, kItemThreads, smem, s>>>(d, skip, g_err_word);
+      AMGDD_CUDA(launch_k(g_pdl, kern, p.nitems, kItemThreads, smem, s, d, skip, g_err_word));
       AMGDD_CUDA(cudaGetLastError());
       count_kernels(1);
       return AMGDD_OK;
@@ -918,17 +925,17 @@ int launch_apply(const ApplyPlan& p, const Level& L, bool fp32, const void* x, v
     if (a.nbuckets == 0) continue;
     if (fp32) {
       if (big)
-        k_apply<float, true><<<cta, kApplyThreads, 0, s>>>(a, L.d_R32.p, (const float*)x, (float*)y, (float)sign, skip);
+        AMGDD_CUDA(launch_k(g_pdl, k_apply<float, true>, cta, kApplyThreads, 0, s, a, L.d_R32.p, (const float*)x, (float*)y, (float)sign, skip));
       else
-        k_apply<float, false><<<cta, kApplyThreads, 0, s>>>(a, L.d_R32.p, (const float*)x, (float*)y, (float)sign,
-                                                             skip);
+        AMGDD_CUDA(launch_k(g_pdl, k_apply<float, false>, cta, kApplyThreads, 0, s, a, L.d_R32.p, (const float*)x, (float*)y, (float)sign,
+                                                             skip));
     } else {
       if (big)
-        k_apply<double, true><<<cta, kApplyThreads, 0, s>>>(a, L.d_R64.p, (const double*)x, (double*)y,
-                                                             (double)sign, skip);
+        AMGDD_CUDA(launch_k(g_pdl, k_apply<double, true>, cta, kApplyThreads, 0, s, a, L.d_R64.p, (const double*)x, (double*)y,
+                                                             (double)sign, skip));
       else
-        k_apply<double, false><<<cta, kApplyThreads, 0, s>>>(a, L.d_R64.p, (const double*)x, (double*)y,
-                                                              (double)sign, skip);
+        AMGDD_CUDA(launch_k(g_pdl, k_apply<double, false>, cta, kApplyThreads, 0, s, a, L.d_R64.p, (const double*)x, (double*)y,
+                                                              (double)sign, skip));
     }
     AMGDD_CUDA(cudaGetLastError());
     count_kernels(1);
@@ -947,13 +954,13 @@ int launch_cast(const void* src, bool src32, void* dst, bool dst32, int64_t n, c
   if (n == 0) return AMGDD_OK;
   const int g = grid_for(n, 256);
   if (src32 && !dst32)
-    k_cast<float, double><<<g, 256, 0, s>>>((const float*)src, (double*)dst, n, skip);
+    AMGDD_CUDA(launch_k(g_pdl, k_cast<float, double>, g, 256, 0, s, (const float*)src, (double*)dst, n, skip));
   else if (!src32 && dst32)
-    k_cast<double, float><<<g, 256, 0, s>>>((const double*)src, (float*)dst, n, skip);
+    AMGDD_CUDA(launch_k(g_pdl, k_cast<double, float>, g, 256, 0, s, (const double*)src, (float*)dst, n, skip));
   else if (src32)
-    k_cast<float, float><<<g, 256, 0, s>>>((const float*)src, (float*)dst, n, skip);
+    AMGDD_CUDA(launch_k(g_pdl, k_cast<float, float>, g, 256, 0, s, (const float*)src, (float*)dst, n, skip));
   else
-    k_cast<double, double><<<g, 256, 0, s>>>((const double*)src, (double*)dst, n, skip);
+    AMGDD_CUDA(launch_k(g_pdl, k_cast<double, double>, g, 256, 0, s, (const double*)src, (double*)dst, n, skip));
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
   return AMGDD_OK;
@@ -965,7 +972,7 @@ int launch_copy_vec(const void* src, void* dst, bool fp32, int64_t n, const int*
 
 int launch_dot_partial(const double* a, const double* b, const double* c, int64_t n, double* partials,
                        const int* skip, cudaStream_t s) {
-  k_dot_partial<<<kDotBlocks, kDotThreads, 0, s>>>(a, b, c, n, partials, skip);
+  AMGDD_CUDA(launch_k(g_pdl, k_dot_partial, kDotBlocks, kDotThreads, 0, s, a, b, c, n, partials, skip));
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
   return AMGDD_OK;
@@ -973,7 +980,7 @@ int launch_dot_partial(const double* a, const double* b, const double* c, int64_
 
 int launch_pcg_scalar(int which, PcgState* st, const double* partials, cudaStream_t s,
                       cudaGraphConditionalHandle cond, int use_cond) {
-  k_pcg_scalar<<<1, 1024, 0, s>>>(which, st, partials, cond, use_cond);
+  AMGDD_CUDA(launch_k(g_pdl, k_pcg_scalar, 1, 1024, 0, s, which, st, partials, cond, use_cond));
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
   return AMGDD_OK;
@@ -981,14 +988,14 @@ int launch_pcg_scalar(int which, PcgState* st, const double* partials, cudaStrea
 
 int launch_update_xr(PcgState* st, double* x, double* r, const double* p, const double* q, int64_t n,
                      cudaStream_t s) {
-  k_update_xr<<<grid_for(n, 256), 256, 0, s>>>(st, x, r, p, q, n);
+  AMGDD_CUDA(launch_k(g_pdl, k_update_xr, grid_for(n, 256), 256, 0, s, st, x, r, p, q, n));
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
   return AMGDD_OK;
 }
 
 int launch_update_p(PcgState* st, double* p, const double* z, double* zold, int64_t n, cudaStream_t s) {
-  k_update_p<<<grid_for(n, 256), 256, 0, s>>>(st, p, z, zold, n);
+  AMGDD_CUDA(launch_k(g_pdl, k_update_p, grid_for(n, 256), 256, 0, s, st, p, z, zold, n));
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
   return AMGDD_OK;
@@ -1178,6 +1185,7 @@ __device__ bool run_items(const PhaseDesc& P, unsigned char* smem, uint64_t* bar
 // between phases.
 __global__ void __launch_bounds__(kItemThreads, 6) k_persistent(const PhaseDesc* __restrict__ phases, int nphases,
                                                                unsigned* bar, int* err, const int* skip) {
+  pdl_prologue();
   if ((skip != nullptr && *skip) || *(volatile int*)err != 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);

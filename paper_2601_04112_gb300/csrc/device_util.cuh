@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <utility>
+
 namespace amgdd {
 
 // Sum over the aligned group of L lanes (L a power of two dividing 32) that
@@ -24,6 +26,34 @@ __device__ __forceinline__ unsigned group_mask() {
   }
 }
 
+
+// Programmatic dependent launch.  Every solve-phase kernel begins with
+// pdl_prologue(): it waits until the grids it depends on have completed and
+// their memory is visible (a no-op for a launch without the attribute), then
+// lets the next grid of the stream start its launch.  Nothing before the wait
+// touches global memory, so a dependent grid that starts early only spends
+// the wait resident on the SMs.
+__device__ __forceinline__ void pdl_prologue() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
+// Launch with the programmatic-stream-serialization attribute when `pdl`.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll

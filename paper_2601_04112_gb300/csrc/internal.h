@@ -34,6 +34,10 @@ void set_error(const char* fmt, ...);
 // measures a hierarchy's footprint as the change over its build).
 extern thread_local int64_t g_alloc_bytes;
 
+// Solve-phase kernels are launched with programmatic dependent launch while
+// set (per thread: each hierarchy call sets it from its parameters).
+extern thread_local bool g_pdl;
+
 // Owning device buffer.
 template <class T>
 struct DBuf {
@@ -207,6 +211,12 @@ struct Level {
   DBuf<double> Aw64, AwT64;
   DBuf<float> Aw32, AwT32;
   double inv_err = 0.0;  // coarsest level: measured ||W A v - v|| / ||v||
+  // dense tail: the V-cycle from this level to the coarsest as one n x n
+  // matrix B (B = its action on the unit vectors), with its transpose
+  DBuf<double> B64, Bt64;
+  DBuf<float> B32, Bt32;
+  SegPlan dplan;
+  double vc_us[2] = {0.0, 0.0};  // measured V-cycle from this level (graph), FP64 / mixed
   // ---- work vectors of the V-cycle ----------------------------------------
   DBuf<double> r64, x64, s64;
   DBuf<float> r32, x32, s32;
@@ -277,6 +287,12 @@ struct ErrScope {
   int* prev;
   explicit ErrScope(int* w) : prev(g_err_word) { g_err_word = w; }
   ~ErrScope() { g_err_word = prev; }
+};
+
+struct PdlScope {
+  bool prev;
+  explicit PdlScope(bool on) : prev(g_pdl) { g_pdl = on; }
+  ~PdlScope() { g_pdl = prev; }
 };
 
 // Kernel-launch accounting (kernels launched directly, plus the kernels of
@@ -402,6 +418,7 @@ int launch_pack_z(int nb, const int32_t* no, const int32_t* k, const int64_t* z_
                   const int64_t* z_off, double* Z64, float* Z32, double* Zt64, float* Zt32, cudaStream_t s);
 // Rows omega_i of each assembled A_i (before its Cholesky) in the layout of
 // W_i, plus the block transposes, in FP64 and FP32.
+int launch_dense_pack(const double* C, int n, double* B64, float* B32, float* C32, cudaStream_t s);
 int launch_copy_wrows(int nb, const int32_t* m, const int32_t* no, const int64_t* a_off, const double* Apool,
                       const int64_t* w_off, double* Aw64, float* Aw32, double* AwT64, float* AwT32, cudaStream_t s);
 // Block rows of A_l = sum_g H_g: for block b, rows p0 .. p0+nr_b-1 of each

@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(kMultiThreads) k_seg_multi(const int32_t* __re
                                                              const T* __restrict__ M, const T* __restrict__ x,
                                                              T* __restrict__ y, const T* __restrict__ c, int mode,
                                                              const int* skip) {
+  pdl_prologue();
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw);
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(kMultiThreads) k_seg_rows_multi(
     const int32_t* __restrict__ nc, const int64_t* __restrict__ in_off, const int64_t* __restrict__ out_off,
     const int32_t* __restrict__ in_idx, const int32_t* __restrict__ out_idx, const T* __restrict__ MT,
     const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ c, int mode, const int* skip) {
+  pdl_prologue();
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int grp = (int)threadIdx.x / L;
@@ -130,6 +132,7 @@ template <int K>
 __global__ void __launch_bounds__(256) k_dot_multi(const double* __restrict__ a, const double* __restrict__ b,
                                                    const double* __restrict__ c, int64_t len,
                                                    double* __restrict__ partials, const int* skip) {
+  pdl_prologue();
   if (skip != nullptr && *skip) return;
   double s0 = 0.0, s1 = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
@@ -168,6 +171,7 @@ template <int K>
 __global__ void __launch_bounds__(32 * K) k_pcg_scalar_multi(int which, PcgState* st, int* grp,
                                                              const double* __restrict__ partials, int nblk,
                                                              cudaGraphConditionalHandle cond, int use_cond) {
+  pdl_prologue();
   const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   PcgState& S = st[k];
   const bool skip_col = which != 0 && which != 4 && S.done;
@@ -245,6 +249,7 @@ template <int K>
 __global__ void k_update_xr_multi(const PcgState* __restrict__ st, const int* grp, double* __restrict__ x,
                                   double* __restrict__ r, const double* __restrict__ p, const double* __restrict__ q,
                                   int64_t len) {
+  pdl_prologue();
   if (grp[0]) return;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
     const PcgState& S = st[e % K];
@@ -257,6 +262,7 @@ __global__ void k_update_xr_multi(const PcgState* __restrict__ st, const int* gr
 template <int K>
 __global__ void k_update_p_multi(const PcgState* __restrict__ st, const int* grp, double* __restrict__ p,
                                  const double* __restrict__ z, double* __restrict__ zold, int64_t len) {
+  pdl_prologue();
   if (grp[0]) return;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
     const PcgState& S = st[e % K];
@@ -269,6 +275,7 @@ __global__ void k_update_p_multi(const PcgState* __restrict__ st, const int* grp
 // Column-major (n x K, leading dimension ld) <-> node-major interleaved.
 __global__ void k_interleave(const double* __restrict__ src, int64_t ld, int ncols, double* __restrict__ dst, int64_t n,
                              int K) {
+  pdl_prologue();
   const int64_t len = n * K;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / K;
@@ -279,6 +286,7 @@ __global__ void k_interleave(const double* __restrict__ src, int64_t ld, int nco
 
 __global__ void k_deinterleave(const double* __restrict__ src, int64_t n, int K, double* __restrict__ dst, int64_t ld,
                                int ncols) {
+  pdl_prologue();
   const int64_t len = n * ncols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = e / n;
@@ -304,9 +312,9 @@ int seg_multi_k(const SegPlan& p, const T* M, const T* MT, const T* x, T* y, Seg
       const int per = kMultiThreads / L;
       const size_t smem = (size_t)per * p.max_nc * K * sizeof(T);
       if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      kern<<<(p.ntasks + per - 1) / per, kMultiThreads, smem, s>>>(
+      AMGDD_CUDA(launch_k(g_pdl, kern, (p.ntasks + per - 1) / per, kMultiThreads, smem, s, 
           p.task_blk.p, p.task_row0.p, p.task_nrow.p, p.ntasks, p.max_nc, p.m_off.p, p.nr.p, p.nc.p, p.in_off.p,
-          p.out_off.p, p.in_idx_ext, p.out_idx_ext, MT, x, y, c, (int)mode, skip);
+          p.out_off.p, p.in_idx_ext, p.out_idx_ext, MT, x, y, c, (int)mode, skip));
       AMGDD_CUDA(cudaGetLastError());
       count_kernels(1);
       return AMGDD_OK;
@@ -320,9 +328,9 @@ int seg_multi_k(const SegPlan& p, const T* M, const T* MT, const T* x, T* y, Seg
   auto go = [&](auto kern) -> int {
     const size_t smem = (size_t)p.max_nc * K * sizeof(T);
     if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<p.nchunks, kMultiThreads, smem, s>>>(p.chunk_blk.p, p.chunk_row0.p, p.rows_per_chunk, p.m_off.p, p.nr.p,
+    AMGDD_CUDA(launch_k(g_pdl, kern, p.nchunks, kMultiThreads, smem, s, p.chunk_blk.p, p.chunk_row0.p, p.rows_per_chunk, p.m_off.p, p.nr.p,
                                                 p.nc.p, p.in_off.p, p.out_off.p, p.in_idx_ext, p.out_idx_ext, M, x, y, c,
-                                                (int)mode, skip);
+                                                (int)mode, skip));
     AMGDD_CUDA(cudaGetLastError());
     count_kernels(1);
     return AMGDD_OK;
@@ -368,9 +376,9 @@ int launch_dot_multi(const double* a, const double* b, const double* c, int64_t 
                      const int* skip, cudaStream_t s) {
   const int64_t len = n * K;
   switch (K) {
-    case 2: k_dot_multi<2><<<kDotBlocks, 256, 0, s>>>(a, b, c, len, partials, skip); break;
-    case 4: k_dot_multi<4><<<kDotBlocks, 256, 0, s>>>(a, b, c, len, partials, skip); break;
-    case 8: k_dot_multi<8><<<kDotBlocks, 256, 0, s>>>(a, b, c, len, partials, skip); break;
+    case 2: AMGDD_CUDA(launch_k(g_pdl, k_dot_multi<2>, kDotBlocks, 256, 0, s, a, b, c, len, partials, skip)); break;
+    case 4: AMGDD_CUDA(launch_k(g_pdl, k_dot_multi<4>, kDotBlocks, 256, 0, s, a, b, c, len, partials, skip)); break;
+    case 8: AMGDD_CUDA(launch_k(g_pdl, k_dot_multi<8>, kDotBlocks, 256, 0, s, a, b, c, len, partials, skip)); break;
     default: set_error("launch_dot_multi: K must be 2, 4 or 8"); return AMGDD_ERR_INTERNAL;
   }
   AMGDD_CUDA(cudaGetLastError());
@@ -381,9 +389,9 @@ int launch_dot_multi(const double* a, const double* b, const double* c, int64_t 
 int launch_pcg_scalar_multi(int which, PcgState* st, int* grp, const double* partials, int K, cudaStream_t s,
                             cudaGraphConditionalHandle cond, int use_cond) {
   switch (K) {
-    case 2: k_pcg_scalar_multi<2><<<1, 64, 0, s>>>(which, st, grp, partials, kDotBlocks, cond, use_cond); break;
-    case 4: k_pcg_scalar_multi<4><<<1, 128, 0, s>>>(which, st, grp, partials, kDotBlocks, cond, use_cond); break;
-    case 8: k_pcg_scalar_multi<8><<<1, 256, 0, s>>>(which, st, grp, partials, kDotBlocks, cond, use_cond); break;
+    case 2: AMGDD_CUDA(launch_k(g_pdl, k_pcg_scalar_multi<2>, 1, 64, 0, s, which, st, grp, partials, kDotBlocks, cond, use_cond)); break;
+    case 4: AMGDD_CUDA(launch_k(g_pdl, k_pcg_scalar_multi<4>, 1, 128, 0, s, which, st, grp, partials, kDotBlocks, cond, use_cond)); break;
+    case 8: AMGDD_CUDA(launch_k(g_pdl, k_pcg_scalar_multi<8>, 1, 256, 0, s, which, st, grp, partials, kDotBlocks, cond, use_cond)); break;
     default: set_error("launch_pcg_scalar_multi: K must be 2, 4 or 8"); return AMGDD_ERR_INTERNAL;
   }
   AMGDD_CUDA(cudaGetLastError());
@@ -396,9 +404,9 @@ int launch_update_xr_multi(const PcgState* st, const int* grp, double* x, double
   const int64_t len = n * K;
   const int g = grid_of(len, 256);
   switch (K) {
-    case 2: k_update_xr_multi<2><<<g, 256, 0, s>>>(st, grp, x, r, p, q, len); break;
-    case 4: k_update_xr_multi<4><<<g, 256, 0, s>>>(st, grp, x, r, p, q, len); break;
-    default: k_update_xr_multi<8><<<g, 256, 0, s>>>(st, grp, x, r, p, q, len); break;
+    case 2: AMGDD_CUDA(launch_k(g_pdl, k_update_xr_multi<2>, g, 256, 0, s, st, grp, x, r, p, q, len)); break;
+    case 4: AMGDD_CUDA(launch_k(g_pdl, k_update_xr_multi<4>, g, 256, 0, s, st, grp, x, r, p, q, len)); break;
+    default: AMGDD_CUDA(launch_k(g_pdl, k_update_xr_multi<8>, g, 256, 0, s, st, grp, x, r, p, q, len)); break;
   }
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
@@ -410,9 +418,9 @@ int launch_update_p_multi(const PcgState* st, const int* grp, double* p, const d
   const int64_t len = n * K;
   const int g = grid_of(len, 256);
   switch (K) {
-    case 2: k_update_p_multi<2><<<g, 256, 0, s>>>(st, grp, p, z, zold, len); break;
-    case 4: k_update_p_multi<4><<<g, 256, 0, s>>>(st, grp, p, z, zold, len); break;
-    default: k_update_p_multi<8><<<g, 256, 0, s>>>(st, grp, p, z, zold, len); break;
+    case 2: AMGDD_CUDA(launch_k(g_pdl, k_update_p_multi<2>, g, 256, 0, s, st, grp, p, z, zold, len)); break;
+    case 4: AMGDD_CUDA(launch_k(g_pdl, k_update_p_multi<4>, g, 256, 0, s, st, grp, p, z, zold, len)); break;
+    default: AMGDD_CUDA(launch_k(g_pdl, k_update_p_multi<8>, g, 256, 0, s, st, grp, p, z, zold, len)); break;
   }
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
@@ -420,14 +428,14 @@ int launch_update_p_multi(const PcgState* st, const int* grp, double* p, const d
 }
 
 int launch_interleave(const double* src, int64_t ld, int ncols, double* dst, int64_t n, int K, cudaStream_t s) {
-  k_interleave<<<grid_of(n * K, 256), 256, 0, s>>>(src, ld, ncols, dst, n, K);
+  AMGDD_CUDA(launch_k(g_pdl, k_interleave, grid_of(n * K, 256), 256, 0, s, src, ld, ncols, dst, n, K));
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
   return AMGDD_OK;
 }
 
 int launch_deinterleave(const double* src, int64_t n, int K, double* dst, int64_t ld, int ncols, cudaStream_t s) {
-  k_deinterleave<<<grid_of(n * ncols, 256), 256, 0, s>>>(src, n, K, dst, ld, ncols);
+  AMGDD_CUDA(launch_k(g_pdl, k_deinterleave, grid_of(n * ncols, 256), 256, 0, s, src, n, K, dst, ld, ncols));
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
   return AMGDD_OK;

@@ -1061,7 +1061,42 @@ __global__ void k_copy_wrows(const int32_t* __restrict__ mdim, const int32_t* __
     AwT32[o + (int64_t)c * no + r] = (float)v;
   }
 }
+
+// Dense tail matrices: from C (row j = B e_j, i.e. C = B^T row-major) write
+// B (row-major) in FP64 and FP32 and the FP32 copy of C.  32 x 32 tiles
+// through shared memory, 32 x 8 threads.
+__global__ void k_dense_pack(const double* __restrict__ C, int n, double* __restrict__ B64, float* __restrict__ B32,
+                             float* __restrict__ C32) {
+  __shared__ double t[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int r = by + k, c = bx + threadIdx.x;
+    if (r < n && c < n) {
+      const double v = C[(int64_t)r * n + c];
+      t[k][threadIdx.x] = v;
+      C32[(int64_t)r * n + c] = (float)v;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int r = bx + k, c = by + threadIdx.x;
+    if (r < n && c < n) {
+      const double v = t[threadIdx.x][k];
+      B64[(int64_t)r * n + c] = v;
+      B32[(int64_t)r * n + c] = (float)v;
+    }
+  }
+}
 }  // namespace
+
+int launch_dense_pack(const double* C, int n, double* B64, float* B32, float* C32, cudaStream_t s) {
+  if (n <= 0) return AMGDD_OK;
+  const dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+  k_dense_pack<<<grid, block, 0, s>>>(C, n, B64, B32, C32);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
 
 int launch_copy_wrows(int nb, const int32_t* m, const int32_t* no, const int64_t* a_off, const double* Apool,
                       const int64_t* w_off, double* Aw64, float* Aw32, double* AwT64, float* AwT32, cudaStream_t s) {
