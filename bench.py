@@ -40,7 +40,7 @@ WORKLOAD = "q1_512_rot"
 # DRAM bytes per V-cycle by kernel family, from ncu captures of WORKLOAD
 # (dram__bytes_read.sum + dram__bytes_write.sum summed over one V-cycle's
 # launches; profiles/).  Entries are removed when their kernels change.
-TRAFFIC = {"k_seg": 953.5e6}  # profiles/dram_solve_kernels_q1_512_rot.md
+TRAFFIC = {}  # profiles/dram_solve_kernels_q1_512_rot.md (re-taken after each kernel change)
 
 
 def parse_args():
@@ -497,6 +497,7 @@ def run_ours(args):
     # cooperative launch for every level from its first), slot 2 the two
     # residuals (k_seg over block rows or grouped k_apply), slots 1/5 casts
     forms = [c["form"] for c in stats["coarse_A"]]
+    dense_l = stats.get("dense_tail", {}).get("mixed", {}).get("from", 0)
     fam_ms, fam_by, fam_n = {}, {}, {}
     for l in range(ms.shape[0]):
         for k in range(ms.shape[1]):
@@ -504,6 +505,8 @@ def run_ours(args):
                 continue
             if k == 6:
                 fam, nk = "k_persistent", 1
+            elif k == 0 and dense_l > 0 and l == dense_l:
+                fam, nk = "k_dense", 1
             elif k == 2:
                 fam, nk = ("k_seg" if forms[l] == "block rows" else "k_apply"), 2
             elif k in (1, 5):
@@ -519,6 +522,7 @@ def run_ours(args):
     kdesc = {"k_seg": "k_seg (batched gather-GEMV-scatter: RAS, RAS-T, P, R, block-row residuals; FP32)",
              "k_apply": "k_apply (grouped G then G^T residual; FP32)",
              "k_persistent": "k_persistent (cooperative V-cycle tail: every phase of the coarse levels; FP32)",
+             "k_dense": "k_dense (dense V-cycle tail GEMV; FP32)",
              "k_cast": "k_cast"}
     kms, kby = fam_ms[top], fam_by[top]
     achieved = kby / (kms * 1e-3) / 1e9
@@ -534,7 +538,7 @@ def run_ours(args):
                                  "launches": fam_n[f]} for f in fam_ms},
                 "vcycle": {"ms": vcyc_ms, "bytes": float(by.sum()),
                            "achieved_gbs": float(by.sum()) / (vcyc_ms * 1e-3) / 1e9}}
-    slot_names = {0: "ras_or_coarse", 1: "cast_in", 2: "residual_applies", 3: "restrict", 4: "prolong",
+    slot_names = {0: "ras_coarse_or_dense", 1: "cast_in", 2: "residual_applies", 3: "restrict", 4: "prolong",
                   5: "cast_out", 6: "persistent_tail", 7: "rast"}
     vprof = []
     for l in range(ms.shape[0]):

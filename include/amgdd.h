@@ -109,6 +109,11 @@ typedef struct {
                        /*   dependent launch (each starts while the one   */
                        /*   before it drains, then waits for its results);*/
                        /*   0 (default): plain stream order               */
+  int dense_tail;      /* the V-cycle from a coarse level l down applied  */
+                       /*   as one dense matrix (its action on the unit   */
+                       /*   vectors, computed at setup): 0 (default) the  */
+                       /*   level chosen by timing when tune = 1, else    */
+                       /*   none; -1 none; l >= 1 from level l            */
 } amgdd_params;
 
 typedef struct amgdd_hierarchy amgdd_hierarchy; /* opaque, library-owned */

@@ -1428,8 +1428,10 @@ static int vcycle(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, c
   }
   if (l > 0 && h.dense_from[pi] == l) {  // the V-cycle from here down as one GEMV
     AMGDD_MARK(0);
+    if ((((uintptr_t)r | (uintptr_t)x) & 15) == 0)
+      return launch_dense(f32 ? (const void*)L.B32.p : (const void*)L.B64.p, L.dld, (int)L.n, f32, r, x, skip, s);
     return launch_seg(L.dplan, f32 ? (const void*)L.B32.p : (const void*)L.B64.p, f32, r, x, f32, SEG_STORE, skip, s,
-                      nullptr, nullptr, f32 ? (const void*)L.Bt32.p : (const void*)L.Bt64.p);
+                      nullptr, nullptr, nullptr);
   }
   if (L.coarsest) {
     if (f32) {
@@ -1487,8 +1489,7 @@ static bool tail_phases(amgdd_hierarchy& h, int from, bool f32, std::vector<Phas
   for (int l = from; l < nl; ++l) {
     Level& L = *h.lv[l];
     if (l == df) {
-      ph.push_back(seg_phase(L.dplan, f32 ? (const void*)L.B32.p : (const void*)L.B64.p,
-                             f32 ? (const void*)L.Bt32.p : (const void*)L.Bt64.p, f32,
+      ph.push_back(seg_phase(L.dplan, f32 ? (const void*)L.B32.p : (const void*)L.B64.p, nullptr, f32,
                              f32 ? (const void*)L.r32.p : (const void*)L.r64.p, f32 ? (void*)L.x32.p : (void*)L.x64.p,
                              SEG_STORE));
       break;
@@ -1587,15 +1588,15 @@ static int time_vcycle_graph(amgdd_hierarchy& h, int l, bool f32, const void* r,
 // Dense tail of level l: B = the FP64 V-cycle from l applied to the unit
 // vectors (the cycle is a fixed linear map of r when x starts at 0, Section
 // 3.1), so that the cycle from l down becomes one GEMV.  Column j of B is
-// computed into row j of Bt64 (Bt64 = B^T, row-major); B64, B32 and Bt32
-// follow by a tiled transpose and casts.  Any dense tail already chosen
-// below l serves the computation.
+// computed into row j of a scratch C = B^T; B64 and B32 (row-major, leading
+// dimension n rounded up to 4, zero columns) follow by a tiled transpose.
+// Any dense tail already chosen below l serves the computation.
 static int build_dense(amgdd_hierarchy& h, int l) {
   cudaStream_t s = h.work;
   Level& L = *h.lv[l];
   const int64_t n = L.n;
-  AMGDD_TRY(L.Bt64.alloc((size_t)(n * n)));
-  DBuf<double> rv, xv, one;
+  DBuf<double> C, rv, xv, one;
+  AMGDD_TRY(C.alloc((size_t)(n * n)));
   AMGDD_TRY(rv.alloc(n));
   AMGDD_TRY(xv.alloc(n));
   const std::vector<double> unit{1.0};
@@ -1614,30 +1615,30 @@ static int build_dense(amgdd_hierarchy& h, int l) {
     if (cudaMemsetAsync(rv.p, 0, n * sizeof(double), s) != cudaSuccess ||
         cudaMemcpyAsync(rv.p + j, one.p, sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
         cudaGraphLaunch(ge, s) != cudaSuccess ||
-        cudaMemcpyAsync(L.Bt64.p + j * n, xv.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        cudaMemcpyAsync(C.p + j * n, xv.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
       rc = AMGDD_ERR_CUDA;
   }
   if (ge) cudaGraphExecDestroy(ge);
   AMGDD_TRY(rc);
-  AMGDD_TRY(L.B64.alloc((size_t)(n * n)));
-  AMGDD_TRY(L.B32.alloc((size_t)(n * n)));
-  AMGDD_TRY(L.Bt32.alloc((size_t)(n * n)));
-  AMGDD_TRY(launch_dense_pack(L.Bt64.p, (int)n, L.B64.p, L.B32.p, L.Bt32.p, s));
-  const std::vector<int32_t> nr{(int32_t)n}, nc{(int32_t)n};
+  L.dld = (n + 3) / 4 * 4;
+  AMGDD_TRY(L.B64.alloc((size_t)(n * L.dld)));
+  AMGDD_TRY(L.B32.alloc((size_t)(n * L.dld)));
+  AMGDD_TRY(launch_dense_pack(C.p, (int)n, L.dld, L.B64.p, L.B32.p, s));
+  // dplan: one n x dld block; inputs n..dld-1 gather x[0] against zero columns
+  std::vector<int32_t> idx(L.dld, 0);
+  for (int64_t j = 0; j < n; ++j) idx[j] = (int32_t)j;
+  AMGDD_TRY(L.d_didx.upload(idx, s));
+  const std::vector<int32_t> nr{(int32_t)n}, nc{(int32_t)L.dld};
   const std::vector<int64_t> zero{0};
-  AMGDD_TRY(build_seg(L.dplan, nr, nc, zero, zero, zero, h.iota.p, h.iota.p, s));
-  const std::string k = "L" + std::to_string(l) + "|dense";
-  AMGDD_TRY(tune_seg<float>(L.dplan, k, L.B32.p, L.Bt32.p, n, n, SEG_STORE, s));
-  AMGDD_TRY(tune_seg<double>(L.dplan, k + "64", L.B64.p, L.Bt64.p, n, n, SEG_STORE, s, true));
+  AMGDD_TRY(build_seg(L.dplan, nr, nc, zero, zero, zero, L.d_didx.p, h.iota.p, s, 1));
   AMGDD_CUDA(cudaStreamSynchronize(s));
   return AMGDD_OK;
 }
 
 static void drop_dense(Level& L) {
   L.B64.release();
-  L.Bt64.release();
   L.B32.release();
-  L.Bt32.release();
+  L.d_didx.release();
 }
 
 // Setup-time choice of the dense tail, per precision.  Candidates are the
@@ -1653,6 +1654,18 @@ static int tune_dense(amgdd_hierarchy& h) {
   const int nl = (int)h.lv.size();
   Level& L0 = *h.lv[0];
   h.dense_from[0] = h.dense_from[1] = 0;
+  if (h.prm.dense_tail < 0) return AMGDD_OK;
+  if (h.prm.dense_tail > 0) {  // forced level
+    const int l = h.prm.dense_tail;
+    if (l + 1 >= nl || h.lv[l]->n > kDenseMaxN) {
+      set_error("dense_tail = %d: level must be above the coarsest with at most %lld unknowns", l,
+                (long long)kDenseMaxN);
+      return AMGDD_ERR_INVALID_ARG;
+    }
+    AMGDD_TRY(build_dense(h, l));
+    h.dense_from[0] = h.dense_from[1] = l;
+    return AMGDD_OK;
+  }
   double c64 = 0.0, c32 = 0.0;
   if (g_tune && ((g_tune->get("dense|fp64", c64) && g_tune->get("dense|mixed", c32)) || !g_tune->on)) {
     const int want[2] = {g_tune->on ? (int)c64 : 0, g_tune->on ? (int)c32 : 0};
@@ -2077,9 +2090,9 @@ static int vcycle_multi(amgdd_hierarchy& h, int l, bool f32, int K, const void* 
   Level& L = *h.lv[l];
   // the dense tail stages K columns of its whole input in shared memory;
   // beyond that the separate levels below it serve
-  if (l > 0 && h.dense_from[f32 ? 1 : 0] == l && L.n * K * (f32 ? 4 : 8) <= 200 * 1024)
-    return launch_seg_multi(L.dplan, f32 ? (const void*)L.B32.p : (const void*)L.B64.p,
-                            f32 ? (const void*)L.Bt32.p : (const void*)L.Bt64.p, f32, r, x, SEG_STORE, nullptr, K,
+  if (l > 0 && h.dense_from[f32 ? 1 : 0] == l && L.dld * K * (f32 ? 4 : 8) <= 200 * 1024)
+    return launch_seg_multi(L.dplan, f32 ? (const void*)L.B32.p : (const void*)L.B64.p, nullptr, f32, r, x,
+                            SEG_STORE, nullptr, K,
                             skip, s);
   if (L.coarsest) {
     const void* r64 = r;
@@ -2909,7 +2922,7 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes
     const Level& L = *h->lv[l];
     double* b = bytes + l * VProf::kSlots;
     if (df > 0 && l >= df) {  // the dense tail: one GEMV at level df, nothing below
-      if (l == df) b[0] = seg_bytes(L.dplan, L.n, L.n, false, esz);
+      if (l == df) b[0] = ((double)L.n * L.dld + 2.0 * L.n) * esz;
       continue;
     }
     if (L.coarsest) {
@@ -3044,7 +3057,7 @@ int amgdd_bytes_model(const amgdd_hierarchy* h, double* vcycle_bytes, double* ap
   for (size_t l = 0; l < h->lv.size(); ++l) {
     const Level& L = *h->lv[l];
     if (df > 0 && (int)l == df) {
-      cyc += seg_bytes(L.dplan, L.n, L.n, false, esz);
+      cyc += ((double)L.n * L.dld + 2.0 * L.n) * esz;
       break;
     }
     level_bytes(*h, L, esz, cyc);

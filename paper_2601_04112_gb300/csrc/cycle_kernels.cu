@@ -539,6 +539,65 @@ int seg_dispatch(const SegPlan& p, const T* M, const T* MT, const T* x, T* y, Se
 }
 
 // ---------------------------------------------------------------------------
+// Dense GEMV y = B x (the dense V-cycle tail).  S warps share a row (each
+// takes every S-th run of 32 vectors), 8 / S rows per CTA of 256 threads;
+// rows and x are read as 16-byte vectors straight from global memory (x is
+// small and stays in L1/L2), four vectors per lane in flight, and the n mod
+// W last columns element by element, so x is never read past n.  The S
+// partial sums of a row meet in shared memory in a fixed order.
+template <class T, int S>
+__global__ void __launch_bounds__(256) k_dense(const T* __restrict__ B, int64_t ld, int n, const T* __restrict__ x,
+                                               T* __restrict__ y, const int* skip) {
+  pdl_prologue();
+  if (skip != nullptr && *skip) return;
+  using V = typename Vec2<T>::type;
+  constexpr int W = Vec2<T>::width;
+  constexpr int U = 4;
+  __shared__ T part[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = blockIdx.x * (8 / S) + warp / S;
+  const int sub = warp % S;
+  const int nv = n / W;
+  T acc = T(0);
+  if (r < n) {
+    const T* row = B + (int64_t)r * ld;
+    const V* rv = reinterpret_cast<const V*>(row);
+    const V* xv = reinterpret_cast<const V*>(x);
+    T a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) a[u] = T(0);
+    int c = sub * 32 + lane;
+    for (; c + (U - 1) * 32 * S < nv; c += U * 32 * S) {
+      V m[U], v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        m[u] = rv[c + u * 32 * S];
+        v[u] = xv[c + u * 32 * S];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) a[u] += vdot(m[u], v[u]);
+    }
+    acc = (a[0] + a[1]) + (a[2] + a[3]);
+    for (; c < nv; c += 32 * S) acc += vdot(rv[c], xv[c]);
+    if (sub == 0)
+      for (int j = nv * W + lane; j < n; j += 32) acc += row[j] * x[j];
+    acc = group_sum<32>(acc, 0xffffffffu);
+  }
+  if constexpr (S == 1) {
+    if (r < n && lane == 0) y[r] = acc;
+  } else {
+    if (lane == 0) part[warp] = acc;
+    __syncthreads();
+    if (r < n && sub == 0 && lane == 0) {
+      T t = part[warp];
+#pragma unroll
+      for (int k = 1; k < S; ++k) t += part[warp + k];
+      y[r] = t;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // A-apply by compressed row groups.  A task is (group, first row, rows);
 // L lanes share it, lane l owning support columns l, l+L, ...  For each row
 // t = R_row . x(S) (group reduction), then acc += R_row * t; finally the
@@ -948,6 +1007,34 @@ int launch_apply(const ApplyPlan& p, const Level& L, bool fp32, const void* x, v
                          nullptr, nullptr, R));
   }
   return AMGDD_OK;
+}
+
+int launch_dense(const void* B, int64_t ld, int n, bool fp32, const void* x, void* y, const int* skip,
+                 cudaStream_t s) {
+  if (n <= 0) return AMGDD_OK;
+  if (ld % 4 != 0 || (((uintptr_t)B | (uintptr_t)x) & 15) != 0) {
+    set_error("launch_dense: B, x and the leading dimension must be 16-byte aligned");
+    return AMGDD_ERR_INTERNAL;
+  }
+  // warps per row: about 8 vectors per lane or more, at most 8 warps
+  const int W = fp32 ? 4 : 2;
+  const int64_t per = ((int64_t)n / W + 255) / 256;
+  const int S = per >= 8 ? 8 : (per >= 4 ? 4 : (per >= 2 ? 2 : 1));
+  const int grid = (int)(((int64_t)n * S + 7) / 8);
+  auto go = [&](auto kf, auto kd) -> int {
+    if (fp32)
+      AMGDD_CUDA(launch_k(g_pdl, kf, grid, 256, 0, s, (const float*)B, ld, n, (const float*)x, (float*)y, skip));
+    else
+      AMGDD_CUDA(launch_k(g_pdl, kd, grid, 256, 0, s, (const double*)B, ld, n, (const double*)x, (double*)y, skip));
+    count_kernels(1);
+    return AMGDD_OK;
+  };
+  switch (S) {
+    case 8: return go(k_dense<float, 8>, k_dense<double, 8>);
+    case 4: return go(k_dense<float, 4>, k_dense<double, 4>);
+    case 2: return go(k_dense<float, 2>, k_dense<double, 2>);
+    default: return go(k_dense<float, 1>, k_dense<double, 1>);
+  }
 }
 
 int launch_cast(const void* src, bool src32, void* dst, bool dst32, int64_t n, const int* skip, cudaStream_t s) {

@@ -212,9 +212,14 @@ struct Level {
   DBuf<float> Aw32, AwT32;
   double inv_err = 0.0;  // coarsest level: measured ||W A v - v|| / ||v||
   // dense tail: the V-cycle from this level to the coarsest as one n x n
-  // matrix B (B = its action on the unit vectors), with its transpose
-  DBuf<double> B64, Bt64;
-  DBuf<float> B32, Bt32;
+  // matrix B (B = its action on the unit vectors), row-major with leading
+  // dimension dld = n rounded up to 4 (zero columns); dplan applies it as
+  // one block (gathered input index n..dld-1 -> 0) for the batched and
+  // persistent forms
+  DBuf<double> B64;
+  DBuf<float> B32;
+  DBuf<int32_t> d_didx;
+  int64_t dld = 0;
   SegPlan dplan;
   double vc_us[2] = {0.0, 0.0};  // measured V-cycle from this level (graph), FP64 / mixed
   // ---- work vectors of the V-cycle ----------------------------------------
@@ -418,7 +423,11 @@ int launch_pack_z(int nb, const int32_t* no, const int32_t* k, const int64_t* z_
                   const int64_t* z_off, double* Z64, float* Z32, double* Zt64, float* Zt32, cudaStream_t s);
 // Rows omega_i of each assembled A_i (before its Cholesky) in the layout of
 // W_i, plus the block transposes, in FP64 and FP32.
-int launch_dense_pack(const double* C, int n, double* B64, float* B32, float* C32, cudaStream_t s);
+int launch_dense_pack(const double* C, int n, int64_t ld, double* B64, float* B32, cudaStream_t s);
+// y = B x for the dense tail (B n x n row-major, leading dimension ld a
+// multiple of 4; x and y 16-byte aligned)
+int launch_dense(const void* B, int64_t ld, int n, bool fp32, const void* x, void* y, const int* skip,
+                 cudaStream_t s);
 int launch_copy_wrows(int nb, const int32_t* m, const int32_t* no, const int64_t* a_off, const double* Apool,
                       const int64_t* w_off, double* Aw64, float* Aw32, double* AwT64, float* AwT32, cudaStream_t s);
 // Block rows of A_l = sum_g H_g: for block b, rows p0 .. p0+nr_b-1 of each

@@ -1062,37 +1062,34 @@ __global__ void k_copy_wrows(const int32_t* __restrict__ mdim, const int32_t* __
   }
 }
 
-// Dense tail matrices: from C (row j = B e_j, i.e. C = B^T row-major) write
-// B (row-major) in FP64 and FP32 and the FP32 copy of C.  32 x 32 tiles
-// through shared memory, 32 x 8 threads.
-__global__ void k_dense_pack(const double* __restrict__ C, int n, double* __restrict__ B64, float* __restrict__ B32,
-                             float* __restrict__ C32) {
+// Dense tail matrices: from C (row j = B e_j, i.e. C = B^T row-major, n x n)
+// write B row-major with leading dimension ld >= n (columns n..ld-1 zero) in
+// FP64 and FP32.  32 x 32 tiles through shared memory, 32 x 8 threads.
+__global__ void k_dense_pack(const double* __restrict__ C, int n, int64_t ld, double* __restrict__ B64,
+                             float* __restrict__ B32) {
   __shared__ double t[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
   for (int k = threadIdx.y; k < 32; k += 8) {
     const int r = by + k, c = bx + threadIdx.x;
-    if (r < n && c < n) {
-      const double v = C[(int64_t)r * n + c];
-      t[k][threadIdx.x] = v;
-      C32[(int64_t)r * n + c] = (float)v;
-    }
+    t[k][threadIdx.x] = (r < n && c < n) ? C[(int64_t)r * n + c] : 0.0;
   }
   __syncthreads();
   for (int k = threadIdx.y; k < 32; k += 8) {
     const int r = bx + k, c = by + threadIdx.x;
-    if (r < n && c < n) {
+    if (r < n && c < ld) {
       const double v = t[threadIdx.x][k];
-      B64[(int64_t)r * n + c] = v;
-      B32[(int64_t)r * n + c] = (float)v;
+      B64[(int64_t)r * ld + c] = v;
+      B32[(int64_t)r * ld + c] = (float)v;
     }
   }
 }
 }  // namespace
 
-int launch_dense_pack(const double* C, int n, double* B64, float* B32, float* C32, cudaStream_t s) {
+int launch_dense_pack(const double* C, int n, int64_t ld, double* B64, float* B32, cudaStream_t s) {
   if (n <= 0) return AMGDD_OK;
-  const dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
-  k_dense_pack<<<grid, block, 0, s>>>(C, n, B64, B32, C32);
+  // x: tiles of B's rows (C's columns), y: tiles of B's columns (C's rows)
+  const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((ld + 31) / 32)), block(32, 8);
+  k_dense_pack<<<grid, block, 0, s>>>(C, n, ld, B64, B32);
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
   return AMGDD_OK;

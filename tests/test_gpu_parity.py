@@ -216,6 +216,32 @@ def test_kernel_forms_match_oracle(amg, name, tune):
         assert np.linalg.norm(b - ho.levels[0].A @ x) <= 1.01e-8 * np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("name", ["ragged_3lvl", "large_blocks", "q1_3d_12", "circ_ov2"])
+def test_dense_tail_matches_oracle(amg, name):
+    """dense_tail = 1: the V-cycle from level 1 down is one dense matrix
+    (its action on the unit vectors).  The cycle is linear in r, so every
+    V-cycle, the FP64 and mixed PCG and a batched solve must agree with the
+    oracle as without it."""
+    c = CASES[name]
+    p = _problem(c)
+    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
+    H = amg.Hierarchy.from_problem(p, overlap=c["overlap"], c_min=c["c_min"], n_coarse=c["n_coarse"],
+                                   coarse_overlap=c.get("coarse_overlap", 0), dense_tail=1)
+    st = H.stats()
+    assert st["dense_tail"]["fp64"]["from"] == 1 and st["dense_tail"]["mixed"]["from"] == 1
+    _check_level_operators(amg, c, H, ho)
+    b = seeded_rhs(p.n, 1, 1)[:, 0]
+    xo, io = oracle.pcg(ho, b, tol=1e-8)
+    xg, ig = H.solve(b, tol=1e-8)
+    assert ig[0]["status"] == 0 and ig[0]["relres_true"] <= 1e-8
+    assert abs(ig[0]["iters"] - io["iters"]) <= 1
+    H.set_precision(amg.MIXED32)
+    B = seeded_rhs(p.n, 3, 2)
+    X, inf = H.solve(B, tol=1e-8)
+    for j in range(3):
+        assert inf[j]["status"] == 0 and inf[j]["relres_true"] <= 1e-8
+
+
 def _check_level_operators(amg, c, H, ho):
     rng = np.random.default_rng(11)
     for lvl, Lo in enumerate(ho.levels[:-1]):
