@@ -101,6 +101,28 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
   const int r1 = min(nr[b], r0 + rows_per_chunk);
   const int32_t* ii = in_idx + in_off[b];
   const int S = VK == 2 ? ((ncb + W - 1) / W) * W + W : 0;
+  const int lane = threadIdx.x % L;
+  const int grp = threadIdx.x / L;
+  const int ngrp = blockDim.x / L;
+  // shifted form: the group's first row is requested before the gather, so
+  // that its loads overlap the gather's two dependent loads
+  const int rf = r0 + grp;
+  V pre[U];
+  if constexpr (VK == 2) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) pre[u] = V{};
+    if (rf < r1) {
+      const int64_t e0 = m_off[b] + (int64_t)rf * ncb;
+      const int a = (int)(e0 & (W - 1));
+      const int64_t base = e0 - a;
+      int nv = (ncb + a + W - 1) / W;
+      if (base + (int64_t)nv * W > m_len) --nv;
+      const V* rv = reinterpret_cast<const V*>(M + base);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (lane + u * L < nv) pre[u] = rv[lane + u * L];
+    }
+  }
   if constexpr (VK == 2) {
     const int E = S - ncb;  // zeros per copy: k ahead of the row, E - k after it
     for (int t = threadIdx.x; t < W * E; t += blockDim.x) {
@@ -126,9 +148,6 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
     for (; c < ncb; c += step) seg_stage<T, VK>(xs, S, c, x[ii[c]]);
   }
   __syncthreads();
-  const int lane = threadIdx.x % L;
-  const int grp = threadIdx.x / L;
-  const int ngrp = blockDim.x / L;
   const unsigned mask = group_mask<L>();
   const int32_t* oo = out_idx + out_off[b];
   for (int r = r0 + grp; r < r1; r += ngrp) {
@@ -156,6 +175,14 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
         }
       }
       int c = lane;
+      if constexpr (VK == 2) {
+        if (r == rf) {  // the prefetched first U vectors per lane
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (lane + u * L < nv) acc += vdot(pre[u], xv[lane + u * L]);
+          c = lane + U * L;
+        }
+      }
       if constexpr (U > 1) {
         T a[U];
 #pragma unroll
@@ -239,14 +266,26 @@ __global__ void __launch_bounds__(128) k_seg_rows(const int32_t* __restrict__ ta
   const int rows = task_nrow[t];
   const int ncb = nc[b], nrb = nr[b];
   const int32_t* ii = in_idx + in_off[b];
-  for (int c = lane; c < ncb; c += L) xs[c] = x[ii[c]];
-  __syncwarp(mask);
-  if (lane >= rows) return;
+  // the lane's first kPre column entries, its output index and the copied
+  // value are requested before the gather, overlapping its dependent loads
+  constexpr int kPre = 16;
+  const bool act = lane < rows;
   const int r = r0 + lane;
   const T* col = MT + m_off[b] + r;
+  T pre[kPre];
+#pragma unroll
+  for (int c = 0; c < kPre; ++c) pre[c] = (act && c < ncb) ? col[(int64_t)c * nrb] : T(0);
+  const int o = act ? out_idx[out_off[b] + r] : 0;
+  const bool need_c = MODE == SEG_RESID || cdst != nullptr;
+  const T cv = (act && need_c) ? csrc[o] : T(0);
+  for (int c = lane; c < ncb; c += L) xs[c] = x[ii[c]];
+  __syncwarp(mask);
+  if (!act) return;
   T acc = T(0);
-  for (int c = 0; c < ncb; ++c) acc += col[(int64_t)c * nrb] * xs[c];
-  const int o = out_idx[out_off[b] + r];
+#pragma unroll
+  for (int c = 0; c < kPre; ++c)
+    if (c < ncb) acc += pre[c] * xs[c];
+  for (int c = kPre; c < ncb; ++c) acc += col[(int64_t)c * nrb] * xs[c];
   T* dst = y + o;
   if (MODE == SEG_STORE)
     *dst = acc;
@@ -257,8 +296,8 @@ __global__ void __launch_bounds__(128) k_seg_rows(const int32_t* __restrict__ ta
   else if (MODE == SEG_ATOMIC_SUB)
     atomic_add(dst, -acc);
   else
-    *dst = csrc[o] - acc;
-  if (MODE != SEG_RESID && cdst != nullptr) cdst[o] = csrc[o];
+    *dst = cv - acc;
+  if (MODE != SEG_RESID && cdst != nullptr) cdst[o] = cv;
 }
 
 // ---------------------------------------------------------------------------
