@@ -508,7 +508,7 @@ def run_ours(args):
             elif k == 0 and dense_l > 0 and l == dense_l:
                 fam, nk = "k_dense", 1
             elif k == 2:
-                fam, nk = ("k_seg" if forms[l] == "block rows" else "k_apply"), 2
+                fam, nk = {"block rows": "k_seg", "ELL rows": "k_ell"}.get(forms[l], "k_apply"), 2
             elif k in (1, 5):
                 fam, nk = "k_cast", 1
             else:
@@ -523,6 +523,7 @@ def run_ours(args):
              "k_apply": "k_apply (grouped G then G^T residual; FP32)",
              "k_persistent": "k_persistent (cooperative V-cycle tail: every phase of the coarse levels; FP32)",
              "k_dense": "k_dense (dense V-cycle tail GEMV; FP32)",
+             "k_ell": "k_ell (level-0 residual by ELL rows of A; FP32)",
              "k_cast": "k_cast"}
     kms, kby = fam_ms[top], fam_by[top]
     achieved = kby / (kms * 1e-3) / 1e9

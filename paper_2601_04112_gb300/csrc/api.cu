@@ -704,6 +704,132 @@ int tune_level_plans(Level& L, int lvl, int64_t n_next, cudaStream_t s) {
   return AMGDD_OK;
 }
 
+// A of level 0 by rows in ELL form, from the rows omega_i of A over Omega_i
+// (Aw, which holds every entry of those rows once Omega_i contains their
+// graph neighbours, i.e. with overlap >= 1).  A row's columns are the union
+// of the supports of the G row groups that contain its node.  Not built (and
+// the row groups serve) where a column falls outside Omega_i.
+int build_ell(Level& L, cudaStream_t s) {
+  if (L.Aw64.p == nullptr || L.nagg == 0 || L.n <= 0) return AMGDD_OK;
+  const int64_t n = L.n;
+  const int64_t ng = (int64_t)L.g_ptr.size() - 1;
+  std::vector<int64_t> ip(n + 1, 0);
+  for (int64_t g = 0; g < ng; ++g)
+    for (int64_t q = L.g_ptr[g]; q < L.g_ptr[g + 1]; ++q) ++ip[L.g_idx[q] + 1];
+  for (int64_t i = 0; i < n; ++i) ip[i + 1] += ip[i];
+  std::vector<int64_t> ig(ip[n]), fill(ip.begin(), ip.end() - 1);
+  for (int64_t g = 0; g < ng; ++g)
+    for (int64_t q = L.g_ptr[g]; q < L.g_ptr[g + 1]; ++q) ig[fill[L.g_idx[q]]++] = g;
+  // row lists
+  std::vector<int64_t> rp(n + 1, 0);
+  std::vector<int32_t> rc;
+  std::vector<int32_t> tmp;
+  for (int64_t i = 0; i < n; ++i) {
+    tmp.clear();
+    for (int64_t q = ip[i]; q < ip[i + 1]; ++q) {
+      const int64_t g = ig[q];
+      tmp.insert(tmp.end(), L.g_idx.begin() + L.g_ptr[g], L.g_idx.begin() + L.g_ptr[g + 1]);
+    }
+    std::sort(tmp.begin(), tmp.end());
+    tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+    rc.insert(rc.end(), tmp.begin(), tmp.end());
+    rp[i + 1] = (int64_t)rc.size();
+  }
+  int w = 0;
+  for (int64_t i = 0; i < n; ++i) w = std::max<int>(w, (int)(rp[i + 1] - rp[i]));
+  if (w == 0 || w > 64) return AMGDD_OK;
+  std::vector<int64_t> src((size_t)(n * w), -1);
+  std::vector<int32_t> col((size_t)(n * w));
+  for (int64_t k = 0; k < w; ++k)
+    for (int64_t i = 0; i < n; ++i) col[k * n + i] = (int32_t)i;
+  std::vector<int32_t> pos(n, -1);
+  int64_t woff = 0;
+  for (int a = 0; a < L.nagg; ++a) {
+    const int64_t o0 = L.om_ptr[a], no = L.om_ptr[a + 1] - o0;
+    for (int64_t c = 0; c < no; ++c) pos[L.om_idx[o0 + c]] = (int32_t)c;
+    bool ok = true;
+    for (int r = 0; r < L.nomega[a] && ok; ++r) {
+      const int32_t i = L.om_idx[o0 + r];
+      for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
+        const int32_t j = rc[q];
+        if (pos[j] < 0) {
+          ok = false;
+          break;
+        }
+        const int64_t k = q - rp[i];
+        src[k * n + i] = woff + (int64_t)r * no + pos[j];
+        col[k * n + i] = j;
+      }
+    }
+    for (int64_t c = 0; c < no; ++c) pos[L.om_idx[o0 + c]] = -1;
+    if (!ok) return AMGDD_OK;  // a row reaches outside its subdomain
+    woff += (int64_t)L.nomega[a] * no;
+  }
+  DBuf<int64_t> dsrc;
+  AMGDD_TRY(dsrc.upload(src, s));
+  AMGDD_TRY(L.ellc.upload(col, s));
+  AMGDD_TRY(L.ell64.alloc((size_t)(n * w)));
+  AMGDD_TRY(L.ell32.alloc((size_t)(n * w)));
+  AMGDD_TRY(launch_ell_fill(n * w, dsrc.p, L.Aw64.p, L.ell64.p, L.ell32.p, s));
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  L.ell_w = w;
+  return AMGDD_OK;
+}
+
+// Setup-time choice between the ELL rows and the row groups for level 0's A:
+// time one FP32 residual in each and keep the faster (row groups without
+// timing).
+int tune_ell(Level& L, cudaStream_t s) {
+  if (L.ell_w == 0) return AMGDD_OK;
+  auto drop = [&L] {
+    L.use_ell = false;
+    L.ellc.release();
+    L.ell64.release();
+    L.ell32.release();
+    L.ell_w = 0;
+  };
+  double cached = 0.0;
+  if (g_tune && (g_tune->get("L0|ell", cached) || !g_tune->on)) {
+    if (g_tune->on && cached != 0.0)
+      L.use_ell = true;
+    else
+      drop();
+    return AMGDD_OK;
+  }
+  AMGDD_TRY(L.x32.zero(s));
+  AMGDD_TRY(L.r32.zero(s));
+  cudaEvent_t e[2];
+  for (auto& v : e) AMGDD_CUDA(cudaEventCreate(&v));
+  float t[2] = {0.f, 0.f};
+  constexpr int kReps = 10;
+  int rc = AMGDD_OK;
+  for (int form = 0; form < 2 && rc == AMGDD_OK; ++form) {
+    for (int rep = 0; rep < kReps + 2 && rc == AMGDD_OK; ++rep) {
+      if (rep == 2) cudaEventRecord(e[0], s);
+      rc = form == 0 ? launch_ell(L, true, L.x32.p, L.s32.p, L.r32.p, nullptr, s)
+                     : launch_apply(L.aplan, L, true, L.x32.p, L.s32.p, -1, nullptr, s);
+    }
+    cudaEventRecord(e[1], s);
+    if (rc == AMGDD_OK &&
+        (cudaEventSynchronize(e[1]) != cudaSuccess || cudaEventElapsedTime(&t[form], e[0], e[1]) != cudaSuccess))
+      rc = AMGDD_ERR_CUDA;
+  }
+  for (auto& v : e) cudaEventDestroy(v);
+  AMGDD_TRY(rc);
+  L.ell_us = 1e3 * t[0] / kReps;
+  L.mf_us = 1e3 * t[1] / kReps;
+  const bool use = L.ell_us < L.mf_us;
+  if (g_tune) g_tune->put("L0|ell", use ? 1.0 : 0.0);
+  if (g_timer.on)
+    fprintf(stderr, "[amgdd] level 0 A-apply: ELL (%d slots) %.1f us, row groups %.1f us\n", L.ell_w, L.ell_us,
+            L.mf_us);
+  if (use)
+    L.use_ell = true;
+  else
+    drop();
+  return AMGDD_OK;
+}
+
 // Setup-time tuning of the coarse A-apply: time one FP32 residual of level L
 // in both stored forms and keep the faster.  Block rows move more bytes than
 // the compressed row groups but need no atomics and stream dense rows.
@@ -1351,6 +1477,7 @@ static double apply_bytes(const Level& L, size_t esz) {
 // One residual s = r - A x of a non-coarsest level, with the copy of r that
 // the matrix-free form needs.
 static double resid_bytes(const Level& L, size_t esz) {
+  if (L.use_ell) return (double)L.n * L.ell_w * (esz + 4.0) + 3.0 * L.n * esz;
   if (L.has_blk) return seg_bytes(L.ablk, L.n, L.n, true, esz);
   return apply_bytes(L, esz) + (double)L.n * esz;
 }
@@ -1358,6 +1485,7 @@ static double resid_bytes(const Level& L, size_t esz) {
 // y = A_l x (Eq. 1) in the level's working precision: block rows when stored,
 // else G then G^T by row groups.
 static int level_apply_A(const Level& L, bool f32, const void* x, void* y, cudaStream_t s) {
+  if (L.use_ell) return launch_ell(L, f32, x, y, nullptr, nullptr, s);
   if (L.has_blk)
     return launch_seg(L.ablk, f32 ? (const void*)L.A32.p : (const void*)L.A64.p, f32, x, y, f32, SEG_STORE, nullptr,
                       s, nullptr, nullptr, f32 ? (const void*)L.At32.p : (const void*)L.At64.p);
@@ -1369,12 +1497,13 @@ static int level_apply_A(const Level& L, bool f32, const void* x, void* y, cudaS
 // launch before it must have copied r into s (`rcopy` tells those launches).
 static int level_residual(const Level& L, bool f32, const void* x, const void* r, void* sv, const int* skip,
                           cudaStream_t s) {
+  if (L.use_ell) return launch_ell(L, f32, x, sv, r, skip, s);
   if (L.has_blk)
     return launch_seg(L.ablk, f32 ? (const void*)L.A32.p : (const void*)L.A64.p, f32, x, sv, f32, SEG_RESID, skip,
                       s, r, nullptr, f32 ? (const void*)L.At32.p : (const void*)L.At64.p);
   return launch_apply(L.aplan, L, f32, x, sv, -1, skip, s);
 }
-static bool rcopy(const Level& L) { return !L.has_blk; }
+static bool rcopy(const Level& L) { return !L.has_blk && !L.use_ell; }
 
 // ---------------------------------------------------------------------------
 // Event marks between the launches of one V-cycle (profiling only): the time
@@ -1794,6 +1923,7 @@ static int precondition(amgdd_hierarchy& h, const double* r, double* z, const in
 // q = A p in FP64 on level 0.
 static int apply_fine64(amgdd_hierarchy& h, const double* p, double* q, const int* skip, cudaStream_t s) {
   Level& L0 = *h.lv[0];
+  if (L0.use_ell) return launch_ell(L0, false, p, q, nullptr, skip, s);
   AMGDD_CUDA(cudaMemsetAsync(q, 0, L0.n * sizeof(double), s));
   return launch_apply(L0.aplan, L0, false, p, q, +1, skip, s);
 }
@@ -1962,8 +2092,12 @@ static int solve_once(amgdd_hierarchy& h, const double* bsrc, bool bdev, double 
   PcgState fin{};
   double qq = 0.0;
   for (int restarts = 0;; ++restarts) {
-    AMGDD_CUDA(cudaMemcpyAsync(h.q.p, h.b.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    AMGDD_TRY(launch_apply(h.lv[0]->aplan, *h.lv[0], false, h.x.p, h.q.p, -1, nullptr, s));
+    if (h.lv[0]->use_ell) {
+      AMGDD_TRY(launch_ell(*h.lv[0], false, h.x.p, h.q.p, h.b.p, nullptr, s));
+    } else {
+      AMGDD_CUDA(cudaMemcpyAsync(h.q.p, h.b.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      AMGDD_TRY(launch_apply(h.lv[0]->aplan, *h.lv[0], false, h.x.p, h.q.p, -1, nullptr, s));
+    }
     AMGDD_TRY(launch_dot_partial(h.q.p, h.q.p, nullptr, n, h.partials.p, nullptr, s));
     AMGDD_TRY(download(part, h.partials.p, 2 * kDotBlocks, s));
     fin = *h.st_host;
@@ -2555,6 +2689,10 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
       Phase ph(10, "tune", s);
       AMGDD_TRY(tune_level_plans(L, lvl, L.col0.back(), s));
       if (lvl > 0) AMGDD_TRY(tune_level_A(L, lvl, s));
+      if (lvl == 0) {
+        AMGDD_TRY(build_ell(L, s));
+        AMGDD_TRY(tune_ell(L, s));
+      }
       if (L.has_blk) {  // the batched residual uses the block rows
         L.Aw64.release();
         L.AwT64.release();
@@ -3063,7 +3201,7 @@ int amgdd_bytes_model(const amgdd_hierarchy* h, double* vcycle_bytes, double* ap
     level_bytes(*h, L, esz, cyc);
   }
   const Level& L0 = *h->lv[0];
-  const double ap = apply_bytes(L0, 8);
+  const double ap = L0.use_ell ? (double)L0.n * L0.ell_w * 12.0 + 2.0 * L0.n * 8.0 : apply_bytes(L0, 8);
   if (vcycle_bytes) *vcycle_bytes = cyc;
   if (apply_out) *apply_out = ap;
   return AMGDD_OK;
@@ -3100,7 +3238,8 @@ int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap) {
     const Level& L = *h->lv[l];
     char buf[160];
     std::snprintf(buf, sizeof buf, "%s{\"form\": \"%s\", \"block_rows_us\": %.2f, \"matrix_free_us\": %.2f}",
-                  l ? ", " : "", L.coarsest ? "none" : (L.has_blk ? "block rows" : "matrix-free"), L.blk_us, L.mf_us);
+                  l ? ", " : "", L.coarsest ? "none" : (L.use_ell ? "ELL rows" : (L.has_blk ? "block rows" : "matrix-free")),
+                  L.use_ell ? L.ell_us : L.blk_us, L.mf_us);
     s += buf;
   }
   {

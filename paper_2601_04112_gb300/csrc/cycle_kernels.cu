@@ -637,6 +637,38 @@ __global__ void __launch_bounds__(256) k_dense(const T* __restrict__ B, int64_t 
 }
 
 // ---------------------------------------------------------------------------
+// A-apply by rows in ELL form (level 0): one thread per row, the slots'
+// column indices and values requested eight at a time before the gathered
+// x entries; y = A x, or y = c - A x (residual).
+template <class T, bool RESID>
+__global__ void __launch_bounds__(256) k_ell(const T* __restrict__ val, const int32_t* __restrict__ col, int w,
+                                             int64_t n, const T* __restrict__ x, T* __restrict__ y,
+                                             const T* __restrict__ c, const int* skip) {
+  pdl_prologue();
+  if (skip != nullptr && *skip) return;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T cv = RESID ? c[i] : T(0);
+  T acc = T(0);
+  int k = 0;
+  for (; k + 8 <= w; k += 8) {
+    int ci[8];
+    T v[8], xv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      ci[u] = col[(int64_t)(k + u) * n + i];
+      v[u] = val[(int64_t)(k + u) * n + i];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) xv[u] = x[ci[u]];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc += v[u] * xv[u];
+  }
+  for (; k < w; ++k) acc += val[(int64_t)k * n + i] * x[col[(int64_t)k * n + i]];
+  y[i] = RESID ? cv - acc : acc;
+}
+
+// ---------------------------------------------------------------------------
 // A-apply by compressed row groups.  A task is (group, first row, rows);
 // L lanes share it, lane l owning support columns l, l+L, ...  For each row
 // t = R_row . x(S) (group reduction), then acc += R_row * t; finally the
@@ -1045,6 +1077,33 @@ int launch_apply(const ApplyPlan& p, const Level& L, bool fp32, const void* x, v
     AMGDD_TRY(launch_seg(L.gt2, nullptr, fp32, t, y, fp32, sign > 0 ? SEG_ATOMIC_ADD : SEG_ATOMIC_SUB, skip, s,
                          nullptr, nullptr, R));
   }
+  return AMGDD_OK;
+}
+
+int launch_ell(const Level& L, bool fp32, const void* x, void* y, const void* csrc, const int* skip,
+               cudaStream_t s) {
+  if (L.n <= 0) return AMGDD_OK;
+  const int grid = (int)((L.n + 255) / 256);
+  const bool res = csrc != nullptr;
+  if (fp32) {
+    if (res)
+      AMGDD_CUDA(launch_k(g_pdl, k_ell<float, true>, grid, 256, 0, s, (const float*)L.ell32.p, (const int32_t*)L.ellc.p,
+                          L.ell_w, L.n, (const float*)x, (float*)y, (const float*)csrc, skip));
+    else
+      AMGDD_CUDA(launch_k(g_pdl, k_ell<float, false>, grid, 256, 0, s, (const float*)L.ell32.p,
+                          (const int32_t*)L.ellc.p, L.ell_w, L.n, (const float*)x, (float*)y, (const float*)nullptr,
+                          skip));
+  } else {
+    if (res)
+      AMGDD_CUDA(launch_k(g_pdl, k_ell<double, true>, grid, 256, 0, s, (const double*)L.ell64.p,
+                          (const int32_t*)L.ellc.p, L.ell_w, L.n, (const double*)x, (double*)y, (const double*)csrc,
+                          skip));
+    else
+      AMGDD_CUDA(launch_k(g_pdl, k_ell<double, false>, grid, 256, 0, s, (const double*)L.ell64.p,
+                          (const int32_t*)L.ellc.p, L.ell_w, L.n, (const double*)x, (double*)y,
+                          (const double*)nullptr, skip));
+  }
+  count_kernels(1);
   return AMGDD_OK;
 }
 

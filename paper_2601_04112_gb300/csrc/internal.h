@@ -192,6 +192,16 @@ struct Level {
   DBuf<double> A64, At64;
   DBuf<float> A32, At32;
   double blk_mb = 0, mf_mb = 0, blk_us = 0, mf_us = 0;  // setup-time comparison of the two forms
+  // ---- A_l by rows in ELL form (level 0) -----------------------------------
+  // ell_w slots per row, slot-major (slot k of row i at k n + i); unused
+  // slots hold 0 against the row's own index.  Used when setup measured it
+  // faster than the row groups (use_ell).
+  int ell_w = 0;
+  bool use_ell = false;
+  DBuf<int32_t> ellc;
+  DBuf<double> ell64;
+  DBuf<float> ell32;
+  double ell_us = 0;
   // ---- aggregates and subdomains ------------------------------------------
   std::vector<int32_t> agg;      // n
   std::vector<int64_t> om_ptr;   // nagg+1
@@ -423,6 +433,10 @@ int launch_pack_z(int nb, const int32_t* no, const int32_t* k, const int64_t* z_
                   const int64_t* z_off, double* Z64, float* Z32, double* Zt64, float* Zt32, cudaStream_t s);
 // Rows omega_i of each assembled A_i (before its Cholesky) in the layout of
 // W_i, plus the block transposes, in FP64 and FP32.
+int launch_ell_fill(int64_t total, const int64_t* src, const double* Aw64, double* v64, float* v32,
+                    cudaStream_t s);
+// y = A x (csrc null) or y = csrc - A x over the ELL rows of L
+int launch_ell(const Level& L, bool fp32, const void* x, void* y, const void* csrc, const int* skip, cudaStream_t s);
 int launch_dense_pack(const double* C, int n, int64_t ld, double* B64, float* B32, cudaStream_t s);
 // y = B x for the dense tail (B n x n row-major, leading dimension ld a
 // multiple of 4; x and y 16-byte aligned)

@@ -23,6 +23,8 @@
 // rows use the same code.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cfloat>
 #include <cstdint>
 
@@ -1062,6 +1064,18 @@ __global__ void k_copy_wrows(const int32_t* __restrict__ mdim, const int32_t* __
   }
 }
 
+// ELL values of level 0 from the rows omega_i of A over Omega_i: entry e
+// takes Aw64[src[e]] (0 where src[e] < 0, an unused slot).
+__global__ void k_ell_fill(int64_t total, const int64_t* __restrict__ src, const double* __restrict__ Aw64,
+                           double* __restrict__ v64, float* __restrict__ v32) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = src[e];
+    const double v = o >= 0 ? Aw64[o] : 0.0;
+    v64[e] = v;
+    v32[e] = (float)v;
+  }
+}
+
 // Dense tail matrices: from C (row j = B e_j, i.e. C = B^T row-major, n x n)
 // write B row-major with leading dimension ld >= n (columns n..ld-1 zero) in
 // FP64 and FP32.  32 x 32 tiles through shared memory, 32 x 8 threads.
@@ -1084,6 +1098,16 @@ __global__ void k_dense_pack(const double* __restrict__ C, int n, int64_t ld, do
   }
 }
 }  // namespace
+
+int launch_ell_fill(int64_t total, const int64_t* src, const double* Aw64, double* v64, float* v32,
+                    cudaStream_t s) {
+  if (total <= 0) return AMGDD_OK;
+  const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  k_ell_fill<<<grid, 256, 0, s>>>(total, src, Aw64, v64, v32);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
 
 int launch_dense_pack(const double* C, int n, int64_t ld, double* B64, float* B32, cudaStream_t s) {
   if (n <= 0) return AMGDD_OK;
