@@ -46,7 +46,7 @@ TRAFFIC = {}  # profiles/dram_solve_kernels_q1_512_rot.md (re-taken after each k
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
@@ -105,7 +105,7 @@ def hbm_peak():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
+    """nvidia-smi clock/throttle samples every 50 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -121,7 +121,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -473,6 +473,7 @@ def run_ours(args):
         return
     sampler = ClockSampler(local)
     sampler.start()
+    time.sleep(0.3)  # nvidia-smi's own start-up, so that its samples fall inside the timed region
     t_mix, w_mix, inf_mix, launches = timed(amg.MIXED32, args.warmup, args.steps, B, X)
     clocks = sampler.stop()
     t_64, w_64, inf_64, _ = timed(amg.FP64, args.warmup, args.steps, B, X)

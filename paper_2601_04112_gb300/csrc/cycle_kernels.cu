@@ -107,7 +107,11 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
   // shifted form: the group's first row is requested before the gather, so
   // that its loads overlap the gather's two dependent loads
   const int rf = r0 + grp;
+  const int32_t* oo = out_idx + out_off[b];
+  const bool need_c = MODE == SEG_RESID || cdst != nullptr;
   V pre[U];
+  int po = 0;
+  T pc = T(0), py = T(0);
   if constexpr (VK == 2) {
 #pragma unroll
     for (int u = 0; u < U; ++u) pre[u] = V{};
@@ -121,6 +125,11 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (lane + u * L < nv) pre[u] = rv[lane + u * L];
+      if (lane == 0) {
+        po = oo[rf];
+        if (need_c) pc = csrc[po];
+        if (MODE == SEG_ADD) py = y[po];
+      }
     }
   }
   if constexpr (VK == 2) {
@@ -149,40 +158,98 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
   }
   __syncthreads();
   const unsigned mask = group_mask<L>();
-  const int32_t* oo = out_idx + out_off[b];
+  if constexpr (VK == 2) {
+    // software pipeline over the group's rows: the next row's first U
+    // vectors, output index, copied value and (add mode) old output are
+    // requested before the current row is summed
+    for (int r = rf; r < r1; r += ngrp) {
+      const int64_t e0 = m_off[b] + (int64_t)r * ncb;
+      const int a = (int)(e0 & (W - 1));
+      const int64_t base = e0 - a;
+      const V* rv = reinterpret_cast<const V*>(M + base);
+      const V* xv = reinterpret_cast<const V*>(xs + a * S);
+      int nv = (ncb + a + W - 1) / W;
+      const bool cut = base + (int64_t)nv * W > m_len;  // last row of the matrix: one vector crosses its end
+      if (cut) --nv;
+      const int rn = r + ngrp;
+      V nxt[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) nxt[u] = V{};
+      int no = 0;
+      T nc_ = T(0), ny = T(0);
+      if (rn < r1) {
+        const int64_t e1 = m_off[b] + (int64_t)rn * ncb;
+        const int a1 = (int)(e1 & (W - 1));
+        const int64_t base1 = e1 - a1;
+        int nv1 = (ncb + a1 + W - 1) / W;
+        if (base1 + (int64_t)nv1 * W > m_len) --nv1;
+        const V* rv1 = reinterpret_cast<const V*>(M + base1);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (lane + u * L < nv1) nxt[u] = rv1[lane + u * L];
+        if (lane == 0) {
+          no = oo[rn];
+          if (need_c) nc_ = csrc[no];
+          if (MODE == SEG_ADD) ny = y[no];
+        }
+      }
+      T acc = T(0);
+      if (cut && lane == 0) {
+        const T* xa = xs + a * S;
+        for (int j = nv * W; base + j < m_len; ++j) acc += M[base + j] * xa[j];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (lane + u * L < nv) acc += vdot(pre[u], xv[lane + u * L]);
+      int c = lane + U * L;
+      {
+        T q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) q[u] = T(0);
+        for (; c + (U - 1) * L < nv; c += U * L) {
+          V m[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) m[u] = rv[c + u * L];
+#pragma unroll
+          for (int u = 0; u < U; ++u) q[u] += vdot(m[u], xv[c + u * L]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc += q[u];
+      }
+      for (; c < nv; c += L) acc += vdot(rv[c], xv[c]);
+      acc = group_sum<L>(acc, mask);
+      if (lane == 0) {
+        T* dst = y + po;
+        if (MODE == SEG_STORE)
+          *dst = acc;
+        else if (MODE == SEG_ADD)
+          *dst = py + acc;
+        else if (MODE == SEG_ATOMIC_ADD)
+          atomic_add(dst, acc);
+        else if (MODE == SEG_ATOMIC_SUB)
+          atomic_add(dst, -acc);
+        else
+          *dst = pc - acc;
+        if (MODE != SEG_RESID && cdst != nullptr) cdst[po] = pc;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) pre[u] = nxt[u];
+      po = no;
+      pc = nc_;
+      py = ny;
+    }
+    return;
+  }
   for (int r = r0 + grp; r < r1; r += ngrp) {
     T acc = T(0);
     if constexpr (VK != 0) {
       const V* rv;
       const V* xv;
       int nv;
-      if constexpr (VK == 1) {
-        rv = reinterpret_cast<const V*>(M + m_off[b] + (int64_t)r * ncb);
-        xv = reinterpret_cast<const V*>(xs);
-        nv = ncb / W;
-      } else {
-        const int64_t e0 = m_off[b] + (int64_t)r * ncb;
-        const int a = (int)(e0 & (W - 1));
-        const int64_t base = e0 - a;
-        rv = reinterpret_cast<const V*>(M + base);
-        xv = reinterpret_cast<const V*>(xs + a * S);
-        nv = (ncb + a + W - 1) / W;
-        if (base + (int64_t)nv * W > m_len) {  // last row of the matrix: at most one vector crosses its end
-          --nv;
-          const T* xa = xs + a * S;
-          if (lane == 0)
-            for (int j = nv * W; base + j < m_len; ++j) acc += M[base + j] * xa[j];
-        }
-      }
+      rv = reinterpret_cast<const V*>(M + m_off[b] + (int64_t)r * ncb);  // VK 1: aligned rows
+      xv = reinterpret_cast<const V*>(xs);
+      nv = ncb / W;
       int c = lane;
-      if constexpr (VK == 2) {
-        if (r == rf) {  // the prefetched first U vectors per lane
-#pragma unroll
-          for (int u = 0; u < U; ++u)
-            if (lane + u * L < nv) acc += vdot(pre[u], xv[lane + u * L]);
-          c = lane + U * L;
-        }
-      }
       if constexpr (U > 1) {
         T a[U];
 #pragma unroll
