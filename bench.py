@@ -624,6 +624,7 @@ def run_ours(args):
         "levels": stats["n"], "op_complexity": stats["op_complexity"],
         "coarse_A": [c["form"] for c in stats["coarse_A"]],
         "persistent_tail_from": {"mixed": stats["tail"]["mixed"]["from"], "fp64": stats["tail"]["fp64"]["from"]},
+        "dense_tail_from": {"mixed": stats["dense_tail"]["mixed"]["from"], "fp64": stats["dense_tail"]["fp64"]["from"]},
         "roofline": roofline, "vcycle_profile_us_gbs": vprof,
         "batched": batched, "serving": serving,
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
