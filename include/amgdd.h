@@ -114,6 +114,11 @@ typedef struct {
                        /*   vectors, computed at setup): 0 (default) the  */
                        /*   level chosen by timing when tune = 1, else    */
                        /*   none; -1 none; l >= 1 from level l            */
+  int ell;             /* level 0's A by ELL rows (CG product, residuals,  */
+                       /*   fused CG steps): 0 (default) when faster by   */
+                       /*   setup timing (tune = 1), else the row groups; */
+                       /*   1 always (where Omega_i holds the rows); -1   */
+                       /*   never                                         */
 } amgdd_params;
 
 typedef struct amgdd_hierarchy amgdd_hierarchy; /* opaque, library-owned */

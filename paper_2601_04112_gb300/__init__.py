@@ -54,7 +54,7 @@ class Params(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("schur_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("tune", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
                 ("coarse_overlap", ctypes.c_int), ("coarse_refine", ctypes.c_int),
-                ("pdl", ctypes.c_int), ("dense_tail", ctypes.c_int)]
+                ("pdl", ctypes.c_int), ("dense_tail", ctypes.c_int), ("ell", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -779,7 +779,7 @@ int build_ell(Level& L, cudaStream_t s) {
 // Setup-time choice between the ELL rows and the row groups for level 0's A:
 // time one FP32 residual in each and keep the faster (row groups without
 // timing).
-int tune_ell(Level& L, cudaStream_t s) {
+int tune_ell(Level& L, int forced, cudaStream_t s) {
   if (L.ell_w == 0) return AMGDD_OK;
   auto drop = [&L] {
     L.use_ell = false;
@@ -788,6 +788,13 @@ int tune_ell(Level& L, cudaStream_t s) {
     L.ell32.release();
     L.ell_w = 0;
   };
+  if (forced != 0) {
+    if (forced > 0)
+      L.use_ell = true;
+    else
+      drop();
+    return AMGDD_OK;
+  }
   double cached = 0.0;
   if (g_tune && (g_tune->get("L0|ell", cached) || !g_tune->on)) {
     if (g_tune->on && cached != 0.0)
@@ -1933,6 +1940,21 @@ static int pcg_iteration(amgdd_hierarchy& h, cudaStream_t s, cudaGraphConditiona
   const int64_t n = h.n;
   PcgState* st = h.st.p;
   const int* done = &st->done;
+  const bool flex = h.precision == AMGDD_MIXED32;
+  Level& L0 = *h.lv[0];
+  if (L0.use_ell) {
+    // fused: four launches besides the V-cycle, each reducing its own dot
+    // product and taking the scalar step in its last CTA
+    AMGDD_TRY(launch_cg_ap(L0, st, h.p.p, h.q.p, h.partials.p, s));
+    AMGDD_TRY(launch_cg_xr(st, h.x.p, h.r.p, flex ? L0.r32.p : nullptr, h.p.p, h.q.p, n, h.partials.p, s));
+    if (flex)
+      AMGDD_TRY(vcycle(h, 0, true, L0.r32.p, L0.x32.p, done, s));
+    else
+      AMGDD_TRY(vcycle(h, 0, false, h.r.p, h.z.p, done, s));
+    AMGDD_TRY(launch_cg_zdot(st, flex ? L0.x32.p : nullptr, h.z.p, h.r.p, flex ? h.zold.p : nullptr, n, h.partials.p,
+                             s, cond, use_cond));
+    return launch_update_p(st, h.p.p, h.z.p, flex ? h.zold.p : nullptr, n, s);
+  }
   AMGDD_TRY(apply_fine64(h, h.p.p, h.q.p, done, s));
   AMGDD_TRY(launch_dot_partial(h.p.p, h.q.p, nullptr, n, h.partials.p, done, s));
   AMGDD_TRY(launch_pcg_scalar(1, st, h.partials.p, s));
@@ -1940,7 +1962,6 @@ static int pcg_iteration(amgdd_hierarchy& h, cudaStream_t s, cudaGraphConditiona
   AMGDD_TRY(launch_dot_partial(h.r.p, h.r.p, nullptr, n, h.partials.p, done, s));
   AMGDD_TRY(launch_pcg_scalar(2, st, h.partials.p, s));
   AMGDD_TRY(precondition(h, h.r.p, h.z.p, done, s));
-  const bool flex = h.precision == AMGDD_MIXED32;
   AMGDD_TRY(launch_dot_partial(h.r.p, h.z.p, flex ? h.zold.p : nullptr, n, h.partials.p, done, s));
   AMGDD_TRY(launch_pcg_scalar(3, st, h.partials.p, s, cond, use_cond));
   AMGDD_TRY(launch_update_p(st, h.p.p, h.z.p, flex ? h.zold.p : nullptr, n, s));
@@ -2689,9 +2710,9 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
       Phase ph(10, "tune", s);
       AMGDD_TRY(tune_level_plans(L, lvl, L.col0.back(), s));
       if (lvl > 0) AMGDD_TRY(tune_level_A(L, lvl, s));
-      if (lvl == 0) {
+      if (lvl == 0 && prm.ell >= 0) {
         AMGDD_TRY(build_ell(L, s));
-        AMGDD_TRY(tune_ell(L, s));
+        AMGDD_TRY(tune_ell(L, prm.ell, s));
       }
       if (L.has_blk) {  // the batched residual uses the block rows
         L.Aw64.release();

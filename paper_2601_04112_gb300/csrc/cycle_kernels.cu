@@ -943,31 +943,9 @@ __global__ void __launch_bounds__(kDotThreads) k_dot_partial(const double* __res
 //        2: rr = sum(r.r); convergence / iteration limit
 //        3: rzn = sum(r.z_new), rzo = sum(r.z_old); beta; rz = rzn
 //        4: bnorm2 = sum(b.b); tol2 = tol^2 bnorm2 (tol passed in st->tol2)
-__global__ void __launch_bounds__(1024) k_pcg_scalar(int which, PcgState* st, const double* __restrict__ partials,
-                                                     cudaGraphConditionalHandle cond, int use_cond) {
-  pdl_prologue();
-  if (which != 0 && which != 4 && st->done) {
-    if (which == 3 && use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
-    return;
-  }
-  __shared__ double s0[1024], s1[1024];
-  double v0 = 0.0, v1 = 0.0;
-  for (int i = threadIdx.x; i < kDotBlocks; i += blockDim.x) {
-    v0 += partials[2 * i];
-    v1 += partials[2 * i + 1];
-  }
-  s0[threadIdx.x] = v0;
-  s1[threadIdx.x] = v1;
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h) {
-      s0[threadIdx.x] += s0[threadIdx.x + h];
-      s1[threadIdx.x] += s1[threadIdx.x + h];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x != 0) return;
-  const double a = s0[0], b = s1[0];
+// The scalar step `which` given the two reduced sums a, b (thread 0 only).
+__device__ void pcg_scalar_step(int which, PcgState* st, double a, double b, cudaGraphConditionalHandle cond,
+                                int use_cond) {
   switch (which) {
     case 0:
       st->rz = a;
@@ -1022,6 +1000,162 @@ __global__ void __launch_bounds__(1024) k_pcg_scalar(int which, PcgState* st, co
       if (a == 0.0) st->relres = 0.0;
       break;
   }
+}
+
+__global__ void __launch_bounds__(1024) k_pcg_scalar(int which, PcgState* st, const double* __restrict__ partials,
+                                                     cudaGraphConditionalHandle cond, int use_cond) {
+  pdl_prologue();
+  if (which != 0 && which != 4 && st->done) {
+    if (which == 3 && use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+    return;
+  }
+  __shared__ double s0[1024], s1[1024];
+  double v0 = 0.0, v1 = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += blockDim.x) {
+    v0 += partials[2 * i];
+    v1 += partials[2 * i + 1];
+  }
+  s0[threadIdx.x] = v0;
+  s1[threadIdx.x] = v1;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      s0[threadIdx.x] += s0[threadIdx.x + h];
+      s1[threadIdx.x] += s1[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  pcg_scalar_step(which, st, s0[0], s1[0], cond, use_cond);
+}
+
+// Fused CG kernels: kDotBlocks CTAs of kDotThreads.  Each CTA writes its
+// partial sums (s0, s1); the last CTA to finish (device-scope ticket) sums
+// all partials in a fixed order, runs the scalar step and resets the ticket.
+// The result does not depend on which CTA finishes last.
+__device__ void cg_finish(double s0, double s1, double* partials, PcgState* st, int which,
+                          cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ double sh0[kDotThreads / 32], sh1[kDotThreads / 32];
+  __shared__ int last;
+  s0 = warp_sum_d(s0);
+  s1 = warp_sum_d(s1);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sh0[w] = s0;
+    sh1[w] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v0 = 0.0, v1 = 0.0;
+    for (int k = 0; k < kDotThreads / 32; ++k) {
+      v0 += sh0[k];
+      v1 += sh1[k];
+    }
+    partials[2 * blockIdx.x] = v0;
+    partials[2 * blockIdx.x + 1] = v1;
+    __threadfence();
+    last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1 ? 1 : 0;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v0 = 0.0, v1 = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    v0 += __ldcg(partials + 2 * i);
+    v1 += __ldcg(partials + 2 * i + 1);
+  }
+  v0 = warp_sum_d(v0);
+  v1 = warp_sum_d(v1);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    sh0[w] = v0;
+    sh1[w] = v1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < kDotThreads / 32; ++k) {
+      a += sh0[k];
+      b += sh1[k];
+    }
+    st->ticket = 0u;
+    pcg_scalar_step(which, st, a, b, cond, use_cond);
+  }
+}
+
+// q = A p over level 0's ELL rows; p.q; alpha
+__global__ void __launch_bounds__(kDotThreads) k_cg_ap(const double* __restrict__ val, const int32_t* __restrict__ col,
+                                                       int w, int64_t n, const double* __restrict__ p,
+                                                       double* __restrict__ q, double* partials, PcgState* st) {
+  pdl_prologue();
+  if (st->done) return;
+  double s0 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    int k = 0;
+    for (; k + 8 <= w; k += 8) {
+      int ci[8];
+      double v[8], xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        ci[u] = col[(int64_t)(k + u) * n + i];
+        v[u] = val[(int64_t)(k + u) * n + i];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xv[u] = p[ci[u]];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc += v[u] * xv[u];
+    }
+    for (; k < w; ++k) acc += val[(int64_t)k * n + i] * p[col[(int64_t)k * n + i]];
+    q[i] = acc;
+    s0 += p[i] * acc;
+  }
+  cg_finish(s0, 0.0, partials, st, 1, 0, 0);
+}
+
+// x += alpha p, r -= alpha q (r32 = r when given); r.r; convergence
+__global__ void __launch_bounds__(kDotThreads) k_cg_xr(double* __restrict__ x, double* __restrict__ r,
+                                                       float* __restrict__ r32, const double* __restrict__ p,
+                                                       const double* __restrict__ q, int64_t n, double* partials,
+                                                       PcgState* st) {
+  pdl_prologue();
+  if (st->done) return;
+  const double al = st->alpha;
+  double s0 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += al * p[i];
+    const double ri = r[i] - al * q[i];
+    r[i] = ri;
+    if (r32 != nullptr) r32[i] = (float)ri;
+    s0 += ri * ri;
+  }
+  cg_finish(s0, 0.0, partials, st, 2, 0, 0);
+}
+
+// z = x32 when given; r.z and r.z_old; beta; graph condition
+__global__ void __launch_bounds__(kDotThreads) k_cg_zdot(const float* __restrict__ x32, double* __restrict__ z,
+                                                         const double* __restrict__ r,
+                                                         const double* __restrict__ zold, int64_t n, double* partials,
+                                                         PcgState* st, cudaGraphConditionalHandle cond, int use_cond) {
+  pdl_prologue();
+  if (st->done) {
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+    return;
+  }
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double zi;
+    if (x32 != nullptr) {
+      zi = (double)x32[i];
+      z[i] = zi;
+    } else {
+      zi = z[i];
+    }
+    const double ri = r[i];
+    s0 += ri * zi;
+    if (zold != nullptr) s1 += ri * zold[i];
+  }
+  cg_finish(s0, s1, partials, st, 3, cond, use_cond);
 }
 
 __global__ void k_update_xr(const PcgState* __restrict__ st, double* __restrict__ x, double* __restrict__ r,
@@ -1249,6 +1383,28 @@ int launch_update_xr(PcgState* st, double* x, double* r, const double* p, const 
 int launch_update_p(PcgState* st, double* p, const double* z, double* zold, int64_t n, cudaStream_t s) {
   AMGDD_CUDA(launch_k(g_pdl, k_update_p, grid_for(n, 256), 256, 0, s, st, p, z, zold, n));
   AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
+int launch_cg_ap(const Level& L0, PcgState* st, const double* p, double* q, double* partials, cudaStream_t s) {
+  AMGDD_CUDA(launch_k(g_pdl, k_cg_ap, kDotBlocks, kDotThreads, 0, s, (const double*)L0.ell64.p,
+                      (const int32_t*)L0.ellc.p, L0.ell_w, L0.n, p, q, partials, st));
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
+int launch_cg_xr(PcgState* st, double* x, double* r, float* r32, const double* p, const double* q, int64_t n,
+                 double* partials, cudaStream_t s) {
+  AMGDD_CUDA(launch_k(g_pdl, k_cg_xr, kDotBlocks, kDotThreads, 0, s, x, r, r32, p, q, n, partials, st));
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
+int launch_cg_zdot(PcgState* st, const float* x32, double* z, const double* r, const double* zold, int64_t n,
+                   double* partials, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
+  AMGDD_CUDA(launch_k(g_pdl, k_cg_zdot, kDotBlocks, kDotThreads, 0, s, x32, z, r, zold, n, partials, st, cond,
+                      use_cond));
   count_kernels(1);
   return AMGDD_OK;
 }

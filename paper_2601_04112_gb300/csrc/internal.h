@@ -331,6 +331,7 @@ struct PcgState {
   int iters, max_iter, done, status, flexible;
   int vc_err;  // set by a persistent V-cycle whose grid barrier timed out
   double rr_mark;  // r^T r at the last stall check (flexible CG)
+  unsigned ticket;  // CTAs finished in a fused CG kernel (the last one resets it)
 };
 // Status of a flexible (FP32-cycle) CG that stopped because ||r|| fell by
 // less than 10% over 10 iterations; the host redoes the solve in FP64.
@@ -347,6 +348,18 @@ int launch_pcg_scalar(int which, PcgState* st, const double* partials, cudaStrea
 int launch_update_xr(PcgState* st, double* x, double* r, const double* p, const double* q, int64_t n,
                      cudaStream_t s);
 int launch_update_p(PcgState* st, double* p, const double* z, double* zold, int64_t n, cudaStream_t s);
+// Fused CG steps (single right-hand side, level 0 by ELL rows): each kernel
+// also reduces its dot product and, in its last CTA, runs the scalar step.
+//   cg_ap:   q = A p; alpha = rz / (p.q)
+//   cg_xr:   x += alpha p, r -= alpha q, r32 = r (when given); r.r and the
+//            convergence test
+//   cg_zdot: z = x32 (when given); beta from r.z (and r.z_old); sets the
+//            graph condition
+int launch_cg_ap(const Level& L0, PcgState* st, const double* p, double* q, double* partials, cudaStream_t s);
+int launch_cg_xr(PcgState* st, double* x, double* r, float* r32, const double* p, const double* q, int64_t n,
+                 double* partials, cudaStream_t s);
+int launch_cg_zdot(PcgState* st, const float* x32, double* z, const double* r, const double* zold, int64_t n,
+                   double* partials, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond);
 
 // ---------------------------------------------------------------------------
 // K right-hand sides at once (multi_kernels.cu): vectors interleaved by node

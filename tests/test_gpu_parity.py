@@ -242,6 +242,30 @@ def test_dense_tail_matches_oracle(amg, name):
         assert inf[j]["status"] == 0 and inf[j]["relres_true"] <= 1e-8
 
 
+@pytest.mark.parametrize("ell", [1, -1])
+@pytest.mark.parametrize("name", ["q1_64", "overlap2_d1", "q1_3d_12"])
+def test_level0_forms_match_oracle(amg, name, ell):
+    """ell = 1 / -1: level 0's A by ELL rows (with the fused CG steps) or by
+    the G row groups; both must give the oracle's operators and PCG."""
+    c = CASES[name]
+    p = _problem(c)
+    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
+    H = amg.Hierarchy.from_problem(p, overlap=c["overlap"], c_min=c["c_min"], n_coarse=c["n_coarse"],
+                                   coarse_overlap=c.get("coarse_overlap", 0), ell=ell)
+    assert (H.stats()["coarse_A"][0]["form"] == "ELL rows") == (ell == 1)
+    _check_level_operators(amg, c, H, ho)
+    b = seeded_rhs(p.n, 1, 1)[:, 0]
+    xo, io = oracle.pcg(ho, b, tol=1e-8)
+    xg, ig = H.solve(b, tol=1e-8)
+    assert ig[0]["status"] == 0 and ig[0]["relres_true"] <= 1e-8
+    assert abs(ig[0]["iters"] - io["iters"]) <= 1
+    if ig[0]["iters"] == io["iters"]:
+        assert _rel(xg[:, 0] if xg.ndim == 2 else xg, xo) <= 1e-10
+    H.set_precision(amg.MIXED32)
+    _, im = H.solve(b, tol=1e-8)
+    assert im[0]["status"] == 0 and im[0]["relres_true"] <= 1e-8
+
+
 def _check_level_operators(amg, c, H, ho):
     rng = np.random.default_rng(11)
     for lvl, Lo in enumerate(ho.levels[:-1]):
