@@ -2232,6 +2232,7 @@ static int64_t multi_bytes_estimate(const amgdd_hierarchy& h) {
 // of A over Omega_i (with the RAS plan's index lists).
 static int resid_multi(const Level& L, bool f32, int K, const void* x, const void* r, void* sv, const int* skip,
                        cudaStream_t s) {
+  if (L.use_ell) return launch_ell_multi(L, f32, x, sv, r, K, skip, s);
   if (L.has_blk)
     return launch_seg_multi(L.ablk, f32 ? (const void*)L.A32.p : (const void*)L.A64.p,
                             f32 ? (const void*)L.At32.p : (const void*)L.At64.p, f32, x, sv, SEG_RESID, r, K, skip, s);
@@ -2313,7 +2314,10 @@ static int pcg_iteration_multi(amgdd_hierarchy& h, int K, cudaStream_t s, cudaGr
   const int64_t n = h.n;
   const int* skip = M.grp.p;
   Level& L0 = *h.lv[0];
-  AMGDD_TRY(launch_seg_multi(L0.ras, L0.Aw64.p, L0.AwT64.p, false, M.p.p, M.q.p, SEG_STORE, nullptr, K, skip, s));
+  if (L0.use_ell)
+    AMGDD_TRY(launch_ell_multi(L0, false, M.p.p, M.q.p, nullptr, K, skip, s));
+  else
+    AMGDD_TRY(launch_seg_multi(L0.ras, L0.Aw64.p, L0.AwT64.p, false, M.p.p, M.q.p, SEG_STORE, nullptr, K, skip, s));
   AMGDD_TRY(launch_dot_multi(M.p.p, M.q.p, nullptr, n, K, M.partials.p, skip, s));
   AMGDD_TRY(launch_pcg_scalar_multi(1, M.st.p, M.grp.p, M.partials.p, K, s));
   AMGDD_TRY(launch_update_xr_multi(M.st.p, M.grp.p, M.x.p, M.r.p, M.p.p, M.q.p, n, K, s));
@@ -2400,7 +2404,11 @@ static int solve_group(amgdd_hierarchy& h, const double* b, bool bdev, int ncols
   Level& L0 = *h.lv[0];
   std::vector<double> part;
   for (int restarts = 0;; ++restarts) {
-    AMGDD_TRY(launch_seg_multi(L0.ras, L0.Aw64.p, L0.AwT64.p, false, M.x.p, M.q.p, SEG_RESID, M.b.p, K, nullptr, s));
+    if (L0.use_ell)
+      AMGDD_TRY(launch_ell_multi(L0, false, M.x.p, M.q.p, M.b.p, K, nullptr, s));
+    else
+      AMGDD_TRY(launch_seg_multi(L0.ras, L0.Aw64.p, L0.AwT64.p, false, M.x.p, M.q.p, SEG_RESID, M.b.p, K, nullptr,
+                                 s));
     AMGDD_TRY(launch_dot_multi(M.q.p, M.q.p, nullptr, n, K, M.partials.p, nullptr, s));
     AMGDD_TRY(download(part, M.partials.p, (size_t)kDotBlocks * 2 * K, s));
     bool any = false;

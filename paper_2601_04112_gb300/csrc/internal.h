@@ -450,6 +450,9 @@ int launch_ell_fill(int64_t total, const int64_t* src, const double* Aw64, doubl
                     cudaStream_t s);
 // y = A x (csrc null) or y = csrc - A x over the ELL rows of L
 int launch_ell(const Level& L, bool fp32, const void* x, void* y, const void* csrc, const int* skip, cudaStream_t s);
+// the same for K in {2, 4, 8} interleaved columns
+int launch_ell_multi(const Level& L, bool fp32, const void* x, void* y, const void* c, int K, const int* skip,
+                     cudaStream_t s);
 int launch_dense_pack(const double* C, int n, int64_t ld, double* B64, float* B32, cudaStream_t s);
 // y = B x for the dense tail (B n x n row-major, leading dimension ld a
 // multiple of 4; x and y 16-byte aligned)

@@ -74,7 +74,17 @@ __global__ void __launch_bounds__(kMultiThreads) k_seg_multi(const int32_t* __re
     T acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = T(0);
-    for (int cc = lane; cc < ncb; cc += L) {
+    int cc = lane;
+    for (; cc + 3 * L < ncb; cc += 4 * L) {  // four row entries per lane in flight
+      T m[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) m[u] = row[cc + u * L];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] += m[u] * xs[(cc + u * L) * K + k];
+    }
+    for (; cc < ncb; cc += L) {
       const T m = row[cc];
 #pragma unroll
       for (int k = 0; k < K; ++k) acc[k] += m * xs[cc * K + k];
@@ -83,6 +93,39 @@ __global__ void __launch_bounds__(kMultiThreads) k_seg_multi(const int32_t* __re
     for (int k = 0; k < K; ++k) acc[k] = group_sum<L>(acc[k], mask);
     if (lane == 0) multi_out<T, K>((SegMode)mode, y, c, oo[r], acc);
   }
+}
+
+// Level-0 A by ELL rows for K interleaved columns: one thread per row reads
+// each slot's index and value once and applies it to the K columns
+// (consecutive in memory); y = A x, or y = c - A x (residual).
+template <class T, int K, bool RESID>
+__global__ void __launch_bounds__(256) k_ell_multi(const T* __restrict__ val, const int32_t* __restrict__ col, int w,
+                                                   int64_t n, const T* __restrict__ x, T* __restrict__ y,
+                                                   const T* __restrict__ c, const int* skip) {
+  pdl_prologue();
+  if (skip != nullptr && *skip) return;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = T(0);
+  for (int q = 0; q < w; q += 4) {
+    int ci[4];
+    T v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      ci[u] = q + u < w ? col[(int64_t)(q + u) * n + i] : (int32_t)i;
+      v[u] = q + u < w ? val[(int64_t)(q + u) * n + i] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const T* xr = x + (int64_t)ci[u] * K;
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] += v[u] * xr[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) y[i * K + k] = RESID ? c[i * K + k] - acc[k] : acc[k];
 }
 
 // Row-per-lane plans over the block-wise transposed copy MT.
@@ -439,6 +482,37 @@ int launch_deinterleave(const double* src, int64_t n, int K, double* dst, int64_
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
   return AMGDD_OK;
+}
+
+int launch_ell_multi(const Level& L, bool fp32, const void* x, void* y, const void* c, int K, const int* skip,
+                     cudaStream_t s) {
+  if (L.n <= 0) return AMGDD_OK;
+  const int grid = (int)((L.n + 255) / 256);
+  auto go = [&](auto kf32, auto kf64) -> int {
+    if (fp32)
+      AMGDD_CUDA(launch_k(g_pdl, kf32, grid, 256, 0, s, (const float*)L.ell32.p, (const int32_t*)L.ellc.p, L.ell_w,
+                          L.n, (const float*)x, (float*)y, (const float*)c, skip));
+    else
+      AMGDD_CUDA(launch_k(g_pdl, kf64, grid, 256, 0, s, (const double*)L.ell64.p, (const int32_t*)L.ellc.p, L.ell_w,
+                          L.n, (const double*)x, (double*)y, (const double*)c, skip));
+    count_kernels(1);
+    return AMGDD_OK;
+  };
+  const bool res = c != nullptr;
+  switch (K) {
+    case 2:
+      return res ? go(k_ell_multi<float, 2, true>, k_ell_multi<double, 2, true>)
+                 : go(k_ell_multi<float, 2, false>, k_ell_multi<double, 2, false>);
+    case 4:
+      return res ? go(k_ell_multi<float, 4, true>, k_ell_multi<double, 4, true>)
+                 : go(k_ell_multi<float, 4, false>, k_ell_multi<double, 4, false>);
+    case 8:
+      return res ? go(k_ell_multi<float, 8, true>, k_ell_multi<double, 8, true>)
+                 : go(k_ell_multi<float, 8, false>, k_ell_multi<double, 8, false>);
+    default:
+      set_error("launch_ell_multi: K must be 2, 4 or 8");
+      return AMGDD_ERR_INVALID_ARG;
+  }
 }
 
 }  // namespace amgdd
