@@ -119,6 +119,12 @@ typedef struct {
                        /*   setup timing (tune = 1), else the row groups; */
                        /*   1 always (where Omega_i holds the rows); -1   */
                        /*   never                                         */
+  int deterministic;   /* 1: no atomics on the solve path, so repeated    */
+                       /*   solves on one hierarchy give bitwise equal x: */
+                       /*   RAS-T stores W_i^T s(omega_i) per subdomain   */
+                       /*   entry and gathers per node in a fixed order   */
+                       /*   (Eq. ras-t); level 0 by ELL rows (ell = 1),   */
+                       /*   coarse A by block rows, no persistent tail    */
 } amgdd_params;
 
 typedef struct amgdd_hierarchy amgdd_hierarchy; /* opaque, library-owned */
@@ -328,6 +334,17 @@ int amgdd_server_poll(amgdd_server* s, int64_t req, int wait_ms, amgdd_info* inf
 int amgdd_server_stats(amgdd_server* s, char* json, size_t cap);
 /* Stops the workers after their current batches and frees every operator. */
 void amgdd_server_destroy(amgdd_server* s);
+
+/* Save a hierarchy to `path`: its setup inputs (G, D1, aggregates, overlap),
+ * parameters and setup-time kernel choices (a binary file of this library
+ * version).  Load runs the setup (Algorithm 1) again from the file with
+ * those choices replayed instead of timed, on `stream`, so the loaded
+ * hierarchy applies the same arithmetic with the same kernels on a GPU of
+ * the same model.  Errors: AMGDD_ERR_INVALID_ARG for a path that cannot be
+ * written or read or a file of another format or version; setup's errors.
+ * The caller frees the loaded hierarchy with amgdd_free.                 */
+int amgdd_hierarchy_save(const amgdd_hierarchy* h, const char* path);
+int amgdd_hierarchy_load(const char* path, void* stream, amgdd_hierarchy** out);
 
 void amgdd_free(amgdd_hierarchy* h);
 const char* amgdd_status_string(int status);

@@ -33,7 +33,7 @@ EXPORTED = [
     "amgdd_bytes_model", "amgdd_free", "amgdd_status_string", "amgdd_last_error", "amgdd_profile_vcycle",
     "amgdd_kernel_launches", "amgdd_apply_noalloc", "amgdd_device_bytes", "amgdd_server_params_default",
     "amgdd_server_create", "amgdd_server_add_operator", "amgdd_server_submit", "amgdd_server_poll",
-    "amgdd_server_stats", "amgdd_server_destroy",
+    "amgdd_server_stats", "amgdd_server_destroy", "amgdd_hierarchy_save", "amgdd_hierarchy_load",
 ]
 AMGDD_PENDING = 1
 
@@ -54,7 +54,8 @@ class Params(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("schur_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("tune", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
                 ("coarse_overlap", ctypes.c_int), ("coarse_refine", ctypes.c_int),
-                ("pdl", ctypes.c_int), ("dense_tail", ctypes.c_int), ("ell", ctypes.c_int)]
+                ("pdl", ctypes.c_int), ("dense_tail", ctypes.c_int), ("ell", ctypes.c_int),
+                ("deterministic", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -96,6 +97,8 @@ def load_library(path: str = LIB_PATH):
     lib.amgdd_hierarchy_stats.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.amgdd_bytes_model.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     lib.amgdd_free.argtypes = [vp]
+    lib.amgdd_hierarchy_save.argtypes = [vp, ctypes.c_char_p]
+    lib.amgdd_hierarchy_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
     lib.amgdd_free.restype = None
     lib.amgdd_status_string.argtypes = [i32]
     lib.amgdd_status_string.restype = ctypes.c_char_p
@@ -200,6 +203,27 @@ class Hierarchy:
     @classmethod
     def from_problem(cls, prob, overlap=1, **kw):
         return cls(prob.rowptr, prob.col, prob.val, prob.n, D1=prob.D1, agg=prob.agg, overlap=overlap, **kw)
+
+    def save(self, path):
+        """Write the setup inputs, parameters and kernel choices (amgdd_hierarchy_save)."""
+        _check(self._lib.amgdd_hierarchy_save(self._h, str(path).encode()))
+
+    @classmethod
+    def load(cls, path, stream=None):
+        """Rebuild a saved hierarchy with its kernel choices replayed (amgdd_hierarchy_load)."""
+        lib = load_library()
+        h = ctypes.c_void_p()
+        import torch
+
+        st = _stream(stream) if (stream is not None or torch.cuda.is_available()) else None
+        _check(lib.amgdd_hierarchy_load(str(path).encode(), st, ctypes.byref(h)))
+        obj = cls.__new__(cls)
+        obj._lib = lib
+        obj._keep = []
+        obj._h = h
+        obj.n = int(obj.describe(0)["n"])
+        obj.params = None
+        return obj
 
     def close(self):
         if getattr(self, "_h", None):

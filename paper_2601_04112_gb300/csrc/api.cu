@@ -692,12 +692,16 @@ int tune_level_plans(Level& L, int lvl, int64_t n_next, cudaStream_t s) {
   if (L.coarsest) return tune_seg<double>(L.ras, k + "coarse", L.W64.p, L.Wt64.p, L.n, L.n, SEG_STORE, s);
   AMGDD_TRY(tune_seg<float>(L.ras, k + "ras", L.W32.p, L.Wt32.p, L.n, L.n, SEG_STORE, s));
   AMGDD_TRY(tune_seg<float>(L.rast, k + "rast", L.Wt32.p, L.W32.p, L.n, L.n, SEG_ATOMIC_ADD, s));
+  if (L.yd32.p) AMGDD_TRY(tune_seg<float>(L.rast_det, k + "rastd", L.Wt32.p, L.W32.p, L.n, L.om_ptr.back(), SEG_STORE, s));
   AMGDD_TRY(tune_seg<float>(L.restr, k + "restrict", L.Zt32.p, L.Z32.p, L.n, n_next, SEG_STORE, s));
   AMGDD_TRY(tune_seg<float>(L.prol, k + "prolong", L.Z32.p, L.Zt32.p, n_next, L.n, SEG_ADD, s));
   if (L.A32.p) AMGDD_TRY(tune_seg<float>(L.ablk, k + "blockrows", L.A32.p, L.At32.p, L.n, L.n, SEG_RESID, s));
   // FP64 copies: shifted or scalar loads, within the form chosen above
   AMGDD_TRY(tune_seg<double>(L.ras, k + "ras64", L.W64.p, L.Wt64.p, L.n, L.n, SEG_STORE, s, true));
   AMGDD_TRY(tune_seg<double>(L.rast, k + "rast64", L.Wt64.p, L.W64.p, L.n, L.n, SEG_ATOMIC_ADD, s, true));
+  if (L.yd64.p)
+    AMGDD_TRY(tune_seg<double>(L.rast_det, k + "rastd64", L.Wt64.p, L.W64.p, L.n, L.om_ptr.back(), SEG_STORE, s,
+                               true));
   AMGDD_TRY(tune_seg<double>(L.restr, k + "restrict64", L.Zt64.p, L.Z64.p, L.n, n_next, SEG_STORE, s, true));
   AMGDD_TRY(tune_seg<double>(L.prol, k + "prolong64", L.Z64.p, L.Zt64.p, n_next, L.n, SEG_ADD, s, true));
   if (L.A64.p) AMGDD_TRY(tune_seg<double>(L.ablk, k + "blockrows64", L.A64.p, L.At64.p, L.n, L.n, SEG_RESID, s, true));
@@ -900,6 +904,13 @@ struct amgdd_hierarchy {
   amgdd_params prm{};
   int overlap = 1;
   int64_t n = 0;
+  // the setup inputs and the setup-time kernel choices, kept for
+  // amgdd_hierarchy_save (host memory)
+  std::vector<int64_t> in_rowptr;
+  std::vector<int32_t> in_col, in_agg;
+  std::vector<double> in_val, in_d1;
+  bool in_has_d1 = false;
+  std::vector<std::pair<std::string, double>> tune_kv;
   int precision = AMGDD_FP64;
   int device = 0;
   std::vector<std::unique_ptr<Level>> lv;
@@ -1240,6 +1251,25 @@ int build_plans(amgdd_hierarchy& h, Level& L, DBuf<int32_t>& d_om_idx, cudaStrea
   // RAS-T: x(Omega_i) += W_i^T s(omega_i)
   for (int i = 0; i < nagg; ++i) std::swap(nr[i], nc[i]);
   AMGDD_TRY(build_seg(L.rast, nr, nc, moff, ioff, ooff, d_om_idx.p, d_om_idx.p, s));
+  if (h.prm.deterministic) {
+    // the same products stored at the Omega-list positions, and per node the
+    // positions that hold its entries (ascending)
+    const int64_t tot = L.om_ptr[nagg];
+    std::vector<int32_t> io(tot);
+    std::iota(io.begin(), io.end(), 0);
+    AMGDD_TRY(L.d_pos_iota.upload(io, s));
+    AMGDD_TRY(build_seg(L.rast_det, nr, nc, moff, ioff, ooff, d_om_idx.p, L.d_pos_iota.p, s));
+    std::vector<int64_t> dp(L.n + 1, 0);
+    for (int64_t q = 0; q < tot; ++q) ++dp[L.om_idx[q] + 1];
+    for (int64_t j = 0; j < L.n; ++j) dp[j + 1] += dp[j];
+    std::vector<int32_t> pos(tot);
+    std::vector<int64_t> fill(dp.begin(), dp.end() - 1);
+    for (int64_t q = 0; q < tot; ++q) pos[fill[L.om_idx[q]]++] = (int32_t)q;
+    AMGDD_TRY(L.det_ptr.upload(dp, s));
+    AMGDD_TRY(L.det_pos.upload(pos, s));
+    AMGDD_TRY(L.yd64.alloc(tot));
+    AMGDD_TRY(L.yd32.alloc(tot));
+  }
   // restriction: r_c[col0_i + c] = (Z_i^T s(omega_i))_c
   for (int i = 0; i < nagg; ++i) {
     nr[i] = L.k[i];
@@ -1470,6 +1500,15 @@ static double seg_bytes(const SegPlan& p, int64_t nin, int64_t nout, bool rmw, s
          (double)nout * esz * (rmw ? 2.0 : 1.0);
 }
 
+// One RAS-T: the scatter-add form, or the stored products plus the per-node
+// gather (positions, pointers, the stored values and x read and written).
+static double rast_bytes(const Level& L, size_t esz) {
+  if (L.yd64.p == nullptr) return seg_bytes(L.rast, L.n, L.n, true, esz);
+  const double tot = (double)L.om_ptr.back();
+  return seg_bytes(L.rast_det, L.n, (int64_t)tot, false, esz) + tot * (4.0 + esz) + (L.n + 1) * 8.0 +
+         2.0 * L.n * esz;
+}
+
 // One A-apply (residual form y -= A x) of level L.
 static double apply_bytes(const Level& L, size_t esz) {
   double b = (double)L.aplan.r_len * esz + 3.0 * L.n * esz;
@@ -1511,6 +1550,24 @@ static int level_residual(const Level& L, bool f32, const void* x, const void* r
   return launch_apply(L.aplan, L, f32, x, sv, -1, skip, s);
 }
 static bool rcopy(const Level& L) { return !L.has_blk && !L.use_ell; }
+
+// x(Omega_i) += W_i^T s(omega_i) for all i (Eq. ras-t): atomic scatter-add,
+// or (deterministic hierarchies) stored per Omega-list position and summed
+// per node in a fixed order.  K > 1: K interleaved columns.
+static int apply_rast(const Level& L, bool f32, const void* sv, void* x, const int* skip, cudaStream_t s, int K = 1) {
+  const void* Wt = f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p;
+  const void* W = f32 ? (const void*)L.W32.p : (const void*)L.W64.p;
+  if (L.yd64.p == nullptr) {
+    if (K == 1) return launch_seg(L.rast, Wt, f32, sv, x, f32, SEG_ATOMIC_ADD, skip, s, nullptr, nullptr, W);
+    return launch_seg_multi(L.rast, Wt, W, f32, sv, x, SEG_ATOMIC_ADD, nullptr, K, skip, s);
+  }
+  void* Y = K == 1 ? (f32 ? (void*)L.yd32.p : (void*)L.yd64.p) : (f32 ? (void*)L.myd32.p : (void*)L.myd64.p);
+  if (K == 1)
+    AMGDD_TRY(launch_seg(L.rast_det, Wt, f32, sv, Y, f32, SEG_STORE, skip, s, nullptr, nullptr, W));
+  else
+    AMGDD_TRY(launch_seg_multi(L.rast_det, Wt, W, f32, sv, Y, SEG_STORE, nullptr, K, skip, s));
+  return launch_gather_add(L.det_ptr.p, L.det_pos.p, Y, x, L.n, K, f32, skip, s);
+}
 
 // ---------------------------------------------------------------------------
 // Event marks between the launches of one V-cycle (profiling only): the time
@@ -1608,8 +1665,7 @@ static int vcycle(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, c
   AMGDD_MARK(2);
   AMGDD_TRY(level_residual(L, f32, x, r, sv, skip, s));
   AMGDD_MARK(7);
-  AMGDD_TRY(launch_seg(L.rast, Wt, f32, sv, x, f32, SEG_ATOMIC_ADD, skip, s, nullptr, nullptr, W));
-  return AMGDD_OK;
+  return apply_rast(L, f32, sv, x, skip, s);
 }
 
 // Phases of the V-cycle from level `from` >= 1 to the coarsest and back, in
@@ -1881,6 +1937,10 @@ static int tune_tail(amgdd_hierarchy& h) {
     const bool f32 = pi == 1;
     const std::string key = f32 ? "tail|mixed" : "tail|fp64";
     double cached = 0.0;
+    if (h.prm.deterministic) {  // the persistent phases scatter RAS-T with atomics
+      rc = set_tail(h, pi, 0);
+      continue;
+    }
     if (g_tune && (g_tune->get(key, cached) || !g_tune->on)) {
       rc = set_tail(h, pi, g_tune->on ? (int)cached : 0);
       continue;
@@ -2215,6 +2275,10 @@ static int ensure_multi(amgdd_hierarchy& h) {
     AMGDD_TRY(L.mr32.alloc(lk));
     AMGDD_TRY(L.mx32.alloc(lk));
     AMGDD_TRY(L.ms32.alloc(lk));
+    if (L.yd64.p) {
+      AMGDD_TRY(L.myd64.alloc((size_t)L.om_ptr.back() * kMaxRhs));
+      AMGDD_TRY(L.myd32.alloc((size_t)L.om_ptr.back() * kMaxRhs));
+    }
   }
   M.ready = true;
   h.multi_bytes = g_alloc_bytes - bytes0;
@@ -2279,7 +2343,7 @@ static int vcycle_multi(amgdd_hierarchy& h, int l, bool f32, int K, const void* 
   AMGDD_TRY(vcycle_multi(h, l + 1, f32, K, rn, xn, skip, s));
   AMGDD_TRY(launch_seg_multi(L.prol, Z, Zt, f32, xn, x, SEG_ADD, nullptr, K, skip, s));
   AMGDD_TRY(resid_multi(L, f32, K, x, r, sv, skip, s));
-  return launch_seg_multi(L.rast, Wt, W, f32, sv, x, SEG_ATOMIC_ADD, nullptr, K, skip, s);
+  return apply_rast(L, f32, sv, x, skip, s, K);
 }
 
 static int precondition_multi(amgdd_hierarchy& h, int K, const double* r, double* z, const int* skip,
@@ -2491,6 +2555,24 @@ static int solve_group(amgdd_hierarchy& h, const double* b, bool bdev, int ncols
   return first_bad;
 }
 
+// Binary helpers of the saved-hierarchy format.
+namespace {
+constexpr char kSaveMagic[8] = {'A', 'M', 'G', 'D', 'D', 'H', 'v', '1'};
+
+template <class T>
+bool put_vec(FILE* f, const std::vector<T>& v) {
+  const uint64_t c = v.size();
+  return std::fwrite(&c, sizeof c, 1, f) == 1 && (c == 0 || std::fwrite(v.data(), sizeof(T), c, f) == c);
+}
+template <class T>
+bool get_vec(FILE* f, std::vector<T>& v, uint64_t max_count) {
+  uint64_t c = 0;
+  if (std::fread(&c, sizeof c, 1, f) != 1 || c > max_count) return false;
+  v.resize(c);
+  return c == 0 || std::fread(v.data(), sizeof(T), c, f) == c;
+}
+}  // namespace
+
 extern "C" {
 
 amgdd_params amgdd_params_default(void) {
@@ -2534,7 +2616,8 @@ const char* amgdd_status_string(int st) {
 const char* amgdd_last_error(void) { return g_last_error.c_str(); }
 
 static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, int overlap,
-                      const amgdd_params* params, void* stream, amgdd_hierarchy** out) {
+                      const amgdd_params* params, void* stream, amgdd_hierarchy** out,
+                      const std::vector<std::pair<std::string, double>>* preset = nullptr) {
   if (out == nullptr || G == nullptr || agg == nullptr) {
     set_error("amgdd_setup: G, agg and out must not be NULL");
     return AMGDD_ERR_INVALID_ARG;
@@ -2602,8 +2685,15 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   const int64_t bytes0 = g_alloc_bytes;
   std::unique_ptr<amgdd_hierarchy> H(new amgdd_hierarchy());
   H->prm = prm;
+  H->prm.tune_cache = nullptr;  // the caller's string is not kept
   H->overlap = overlap;
   H->n = n;
+  H->in_rowptr = rowptr;
+  H->in_col = col;
+  H->in_val = val;
+  H->in_agg = aggh;
+  H->in_d1 = d1;
+  H->in_has_d1 = D1 != nullptr;
   H->precision = prm.precision;
   AMGDD_CUDA(cudaGetDevice(&H->device));
   AMGDD_TRY(H->st.alloc(1));
@@ -2628,6 +2718,10 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     tctx.sig = sig + buf;
   }
   tctx.load();
+  if (preset) {  // choices saved with a hierarchy: replayed, not re-timed
+    for (const auto& kv : *preset) tctx.kv[kv.first] = kv.second;
+    tctx.on = true;
+  }
   struct TuneScope {
     explicit TuneScope(TuneCtx* t) { g_tune = t; }
     ~TuneScope() { g_tune = nullptr; }
@@ -2717,10 +2811,11 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     {
       Phase ph(10, "tune", s);
       AMGDD_TRY(tune_level_plans(L, lvl, L.col0.back(), s));
-      if (lvl > 0) AMGDD_TRY(tune_level_A(L, lvl, s));
-      if (lvl == 0 && prm.ell >= 0) {
+      if (lvl > 0 && !prm.deterministic) AMGDD_TRY(tune_level_A(L, lvl, s));  // deterministic: block rows
+      const int ell_mode = prm.deterministic ? 1 : prm.ell;  // the row groups scatter with atomics
+      if (lvl == 0 && ell_mode >= 0) {
         AMGDD_TRY(build_ell(L, s));
-        AMGDD_TRY(tune_ell(L, prm.ell, s));
+        AMGDD_TRY(tune_ell(L, ell_mode, s));
       }
       if (L.has_blk) {  // the batched residual uses the block rows
         L.Aw64.release();
@@ -2775,6 +2870,8 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   AMGDD_TRY(tune_dense(*H));
   AMGDD_TRY(tune_tail(*H));
   tctx.save();
+  for (const auto& kv : tctx.kv)
+    if (kv.first.compare(0, tctx.sig.size(), tctx.sig) == 0) H->tune_kv.emplace_back(kv.first, kv.second);
   H->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   H->setup_bytes = g_alloc_bytes - bytes0;
   *out = H.release();
@@ -2910,9 +3007,7 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
       break;
     case AMGDD_OP_RAST:
       AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
-      AMGDD_TRY(launch_seg(L.rast, f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p, f32, xin, yout, f32,
-                           SEG_ATOMIC_ADD, nullptr, s, nullptr, nullptr,
-                           f32 ? (const void*)L.W32.p : (const void*)L.W64.p));
+      AMGDD_TRY(apply_rast(L, f32, xin, yout, nullptr, s));
       break;
     case AMGDD_OP_RESTRICT:
       AMGDD_TRY(launch_seg(L.restr, f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p, f32, xin, yout, f32,
@@ -3028,9 +3123,7 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
       break;
     case AMGDD_OP_RAST:
       AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
-      AMGDD_TRY(launch_seg(L.rast, f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p, f32, xin, yout, f32,
-                           SEG_ATOMIC_ADD, nullptr, s, nullptr, nullptr,
-                           f32 ? (const void*)L.W32.p : (const void*)L.W64.p));
+      AMGDD_TRY(apply_rast(L, f32, xin, yout, nullptr, s));
       break;
     case AMGDD_OP_RESTRICT:
       AMGDD_TRY(launch_seg(L.restr, f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p, f32, xin, yout, f32,
@@ -3102,7 +3195,7 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes
       b[2] = 2.0 * (resid_bytes(L, esz) - cp);  // two residuals
       b[3] = seg_bytes(L.restr, L.n, nn, false, esz);
       b[4] = seg_bytes(L.prol, nn, L.n, true, esz) + cp;
-      b[7] = seg_bytes(L.rast, L.n, L.n, true, esz);
+      b[7] = rast_bytes(L, esz);
     }
   }
   const int pf = h->persist_from[f32 ? 1 : 0];
@@ -3210,7 +3303,7 @@ static void level_bytes(const amgdd_hierarchy& h, const Level& L, size_t esz, do
     return;
   }
   const int64_t nn = L.col0.back();
-  cyc += seg_bytes(L.ras, L.n, L.n, false, esz) + seg_bytes(L.rast, L.n, L.n, true, esz) +
+  cyc += seg_bytes(L.ras, L.n, L.n, false, esz) + rast_bytes(L, esz) +
          seg_bytes(L.restr, L.n, nn, false, esz) + seg_bytes(L.prol, nn, L.n, true, esz) +
          2.0 * resid_bytes(L, esz);
   (void)h;
@@ -3317,6 +3410,109 @@ int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap) {
   if (s.size() + 1 > cap) return AMGDD_ERR_INVALID_ARG;
   std::memcpy(json, s.c_str(), s.size() + 1);
   return AMGDD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Saved hierarchies: the setup inputs (G, D1, aggregates, overlap), the
+// parameters and the setup-time kernel choices.  Loading runs the setup
+// again with those choices replayed instead of timed, so the loaded
+// hierarchy applies the same arithmetic with the same kernels (on a GPU of
+// the same model; elsewhere the choices are timed anew).
+int amgdd_hierarchy_save(const amgdd_hierarchy* h, const char* path) {
+  if (h == nullptr || path == nullptr) {
+    set_error("amgdd_hierarchy_save: invalid argument");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  FILE* f = std::fopen(path, "wb");
+  if (!f) {
+    set_error("amgdd_hierarchy_save: cannot open %s", path);
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  const uint32_t psz = sizeof(amgdd_params);
+  const int32_t ov = h->overlap, hd = h->in_has_d1 ? 1 : 0;
+  const int64_t n = h->n;
+  amgdd_params prm = h->prm;
+  prm.tune_cache = nullptr;
+  bool ok = std::fwrite(kSaveMagic, 1, 8, f) == 8 && std::fwrite(&psz, sizeof psz, 1, f) == 1 &&
+            std::fwrite(&prm, psz, 1, f) == 1 && std::fwrite(&ov, sizeof ov, 1, f) == 1 &&
+            std::fwrite(&hd, sizeof hd, 1, f) == 1 && std::fwrite(&n, sizeof n, 1, f) == 1 &&
+            put_vec(f, h->in_rowptr) && put_vec(f, h->in_col) && put_vec(f, h->in_val) && put_vec(f, h->in_agg) &&
+            put_vec(f, h->in_d1);
+  const uint64_t nkv = h->tune_kv.size();
+  ok = ok && std::fwrite(&nkv, sizeof nkv, 1, f) == 1;
+  for (const auto& kv : h->tune_kv) {
+    const uint32_t len = (uint32_t)kv.first.size();
+    ok = ok && std::fwrite(&len, sizeof len, 1, f) == 1 && std::fwrite(kv.first.data(), 1, len, f) == len &&
+         std::fwrite(&kv.second, sizeof(double), 1, f) == 1;
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) {
+    set_error("amgdd_hierarchy_save: write to %s failed", path);
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  return AMGDD_OK;
+}
+
+int amgdd_hierarchy_load(const char* path, void* stream, amgdd_hierarchy** out) {
+  if (path == nullptr || out == nullptr) {
+    set_error("amgdd_hierarchy_load: invalid argument");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    set_error("amgdd_hierarchy_load: cannot open %s", path);
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  char magic[8];
+  uint32_t psz = 0;
+  amgdd_params prm;
+  int32_t ov = 0, hd = 0;
+  int64_t n = 0;
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> col, agg;
+  std::vector<double> val, d1;
+  std::vector<std::pair<std::string, double>> kv;
+  constexpr uint64_t kMax = (uint64_t)1 << 40;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kSaveMagic, 8) == 0 &&
+            std::fread(&psz, sizeof psz, 1, f) == 1 && psz == sizeof(amgdd_params) &&
+            std::fread(&prm, psz, 1, f) == 1 && std::fread(&ov, sizeof ov, 1, f) == 1 &&
+            std::fread(&hd, sizeof hd, 1, f) == 1 && std::fread(&n, sizeof n, 1, f) == 1 && get_vec(f, rowptr, kMax) &&
+            get_vec(f, col, kMax) && get_vec(f, val, kMax) && get_vec(f, agg, kMax) && get_vec(f, d1, kMax);
+  uint64_t nkv = 0;
+  ok = ok && std::fread(&nkv, sizeof nkv, 1, f) == 1 && nkv < (1u << 20);
+  for (uint64_t i = 0; ok && i < nkv; ++i) {
+    uint32_t len = 0;
+    double v = 0.0;
+    ok = std::fread(&len, sizeof len, 1, f) == 1 && len < 4096;
+    std::string k(ok ? len : 0, '\0');
+    ok = ok && std::fread(&k[0], 1, len, f) == len && std::fread(&v, sizeof v, 1, f) == 1;
+    if (ok) kv.emplace_back(std::move(k), v);
+  }
+  std::fclose(f);
+  if (!ok || rowptr.empty() || col.size() != val.size() || (int64_t)agg.size() != n ||
+      (hd && (int64_t)d1.size() != n)) {
+    set_error("amgdd_hierarchy_load: %s is not a saved hierarchy of this library version", path);
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  prm.tune_cache = nullptr;
+  amgdd_csr G;
+  G.m = (int64_t)rowptr.size() - 1;
+  G.n = n;
+  G.nnz = (int64_t)val.size();
+  G.rowptr = rowptr.data();
+  G.col = col.data();
+  G.val = val.data();
+  G.mem = AMGDD_HOST;
+  try {
+    return setup_impl(&G, hd ? d1.data() : nullptr, agg.data(), ov, &prm, stream, out, &kv);
+  } catch (const std::bad_alloc&) {
+    set_error("amgdd_hierarchy_load: host allocation failed");
+    return AMGDD_ERR_OOM;
+  } catch (...) {
+    set_error("amgdd_hierarchy_load: unexpected exception");
+    return AMGDD_ERR_INTERNAL;
+  }
 }
 
 void amgdd_free(amgdd_hierarchy* h) {

@@ -704,6 +704,24 @@ __global__ void __launch_bounds__(256) k_dense(const T* __restrict__ B, int64_t 
 }
 
 // ---------------------------------------------------------------------------
+// Deterministic RAS-T, second half: x_j += sum of the stored y entries of
+// node j, in ascending position order (one thread per node and column).
+template <class T, int K>
+__global__ void __launch_bounds__(256) k_gather_add(const int64_t* __restrict__ ptr, const int32_t* __restrict__ pos,
+                                                    const T* __restrict__ Y, T* __restrict__ x, int64_t n,
+                                                    const int* skip) {
+  pdl_prologue();
+  if (skip != nullptr && *skip) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * K) return;
+  const int64_t j = t / K;
+  const int k = (int)(t - j * K);
+  T acc = T(0);
+  for (int64_t q = ptr[j]; q < ptr[j + 1]; ++q) acc += Y[(int64_t)pos[q] * K + k];
+  x[t] += acc;
+}
+
+// ---------------------------------------------------------------------------
 // A-apply by rows in ELL form (level 0): one thread per row, the slots'
 // column indices and values requested eight at a time before the gathered
 // x entries; y = A x, or y = c - A x (residual).
@@ -1279,6 +1297,29 @@ int launch_apply(const ApplyPlan& p, const Level& L, bool fp32, const void* x, v
                          nullptr, nullptr, R));
   }
   return AMGDD_OK;
+}
+
+int launch_gather_add(const int64_t* ptr, const int32_t* pos, const void* Y, void* x, int64_t n, int K, bool fp32,
+                      const int* skip, cudaStream_t s) {
+  if (n <= 0) return AMGDD_OK;
+  const int grid = (int)((n * K + 255) / 256);
+  auto go = [&](auto kf, auto kd) -> int {
+    if (fp32)
+      AMGDD_CUDA(launch_k(g_pdl, kf, grid, 256, 0, s, ptr, pos, (const float*)Y, (float*)x, n, skip));
+    else
+      AMGDD_CUDA(launch_k(g_pdl, kd, grid, 256, 0, s, ptr, pos, (const double*)Y, (double*)x, n, skip));
+    count_kernels(1);
+    return AMGDD_OK;
+  };
+  switch (K) {
+    case 1: return go(k_gather_add<float, 1>, k_gather_add<double, 1>);
+    case 2: return go(k_gather_add<float, 2>, k_gather_add<double, 2>);
+    case 4: return go(k_gather_add<float, 4>, k_gather_add<double, 4>);
+    case 8: return go(k_gather_add<float, 8>, k_gather_add<double, 8>);
+    default:
+      set_error("launch_gather_add: K must be 1, 2, 4 or 8");
+      return AMGDD_ERR_INVALID_ARG;
+  }
 }
 
 int launch_ell(const Level& L, bool fp32, const void* x, void* y, const void* csrc, const int* skip,

@@ -214,6 +214,18 @@ struct Level {
   DBuf<int32_t> d_om_idx;        // Omega lists on the device
   // ---- smoother and transfer operators -------------------------------------
   SegPlan ras, rast, restr, prol;
+  // deterministic RAS-T: y_i = W_i^T s(omega_i) stored at the positions of
+  // the Omega lists (rast_det), then x_j += the y entries of node j in
+  // ascending position order (det_ptr / det_pos: positions p with
+  // om_idx[p] = j); no atomics
+  SegPlan rast_det;
+  DBuf<int32_t> d_pos_iota;  // identity over the positions of the Omega lists
+  DBuf<int64_t> det_ptr;
+  DBuf<int32_t> det_pos;
+  DBuf<double> yd64;
+  DBuf<float> yd32;
+  DBuf<double> myd64;  // the same for kMaxRhs interleaved columns (batched)
+  DBuf<float> myd32;
   DBuf<double> W64, Wt64, Z64, Zt64, mu;
   DBuf<float> W32, Wt32, Z32, Zt32;
   // rows omega_i of A over Omega_i (layout of W_i; the residual of the
@@ -446,6 +458,9 @@ int launch_pack_z(int nb, const int32_t* no, const int32_t* k, const int64_t* z_
                   const int64_t* z_off, double* Z64, float* Z32, double* Zt64, float* Zt32, cudaStream_t s);
 // Rows omega_i of each assembled A_i (before its Cholesky) in the layout of
 // W_i, plus the block transposes, in FP64 and FP32.
+// x_j (+)= sum of Y[pos] over the positions of node j, K interleaved columns
+int launch_gather_add(const int64_t* ptr, const int32_t* pos, const void* Y, void* x, int64_t n, int K, bool fp32,
+                      const int* skip, cudaStream_t s);
 int launch_ell_fill(int64_t total, const int64_t* src, const double* Aw64, double* v64, float* v32,
                     cudaStream_t s);
 // y = A x (csrc null) or y = csrc - A x over the ELL rows of L

@@ -40,3 +40,19 @@ def test_params_default_without_gpu():
     p = amg.params(c_min=(2, 3, 4))
     assert p.L_max == 10 and p.n_coarse == 2000 and abs(p.thresh - 0.1) < 1e-15
     assert list(p.c_min)[:3] == [2, 3, 4] and p.n_cmin == 3
+
+
+def test_hierarchy_load_rejects_bad_files(tmp_path):
+    """amgdd_hierarchy_load checks the file before any device work."""
+    import paper_2601_04112_gb300 as amg
+
+    amg.load_library()
+    bad = tmp_path / "bad.amgdd"
+    bad.write_bytes(b"not a hierarchy" * 10)
+    for path in (bad, tmp_path / "missing.amgdd"):
+        try:
+            amg.Hierarchy.load(path)
+        except amg.AmgddError as e:
+            assert e.status == -1
+        else:
+            raise AssertionError("load accepted " + str(path))

@@ -266,6 +266,62 @@ def test_level0_forms_match_oracle(amg, name, ell):
     assert im[0]["status"] == 0 and im[0]["relres_true"] <= 1e-8
 
 
+@pytest.mark.parametrize("name", ["ragged_3lvl", "circ_ov2", "q1_3d_12"])
+def test_deterministic_repeats_bitwise(amg, name):
+    """deterministic = 1: no atomics on the solve path.  Repeated solves of
+    one right-hand side give bitwise equal x (FP64, mixed, batched), and the
+    operators and PCG still match the oracle."""
+    c = CASES[name]
+    p = _problem(c)
+    ho = _oracle(p, c["overlap"], c["c_min"], c["n_coarse"], coarse_overlap=c.get("coarse_overlap", 0))
+    H = amg.Hierarchy.from_problem(p, overlap=c["overlap"], c_min=c["c_min"], n_coarse=c["n_coarse"],
+                                   coarse_overlap=c.get("coarse_overlap", 0), deterministic=1)
+    _check_level_operators(amg, c, H, ho)
+    b = seeded_rhs(p.n, 1, 3)[:, 0]
+    B = seeded_rhs(p.n, 3, 4)
+    for prec in (amg.FP64, amg.MIXED32):
+        H.set_precision(prec)
+        x1, i1 = H.solve(b, tol=1e-8)
+        x2, i2 = H.solve(b, tol=1e-8)
+        assert i1[0]["status"] == 0 and i1[0]["relres_true"] <= 1e-8
+        assert i1[0]["iters"] == i2[0]["iters"]
+        assert np.array_equal(np.asarray(x1), np.asarray(x2))
+        X1, _ = H.solve(B, tol=1e-8)
+        X2, _ = H.solve(B, tol=1e-8)
+        assert np.array_equal(np.asarray(X1), np.asarray(X2))
+    H.set_precision(amg.FP64)
+    xo, io = oracle.pcg(ho, b, tol=1e-8)
+    xg, ig = H.solve(b, tol=1e-8)
+    assert abs(ig[0]["iters"] - io["iters"]) <= 1
+    if ig[0]["iters"] == io["iters"]:
+        assert _rel(xg[:, 0] if xg.ndim == 2 else xg, xo) <= 1e-10
+
+
+def test_saved_hierarchy_reloads(amg, tmp_path):
+    """amgdd_hierarchy_save / _load: the reloaded hierarchy has the same
+    levels, aggregates and kernel choices, and solves to the same x."""
+    c = CASES["ragged_3lvl"]
+    p = _problem(c)
+    H = amg.Hierarchy.from_problem(p, overlap=c["overlap"], c_min=c["c_min"], n_coarse=c["n_coarse"],
+                                   deterministic=1)
+    path = tmp_path / "h.amgdd"
+    H.save(path)
+    H2 = amg.Hierarchy.load(path)
+    assert H2.num_levels == H.num_levels and H2.n == H.n
+    for lvl in range(H.num_levels - 1):
+        assert np.array_equal(H.export(lvl, amg.ARR_AGG), H2.export(lvl, amg.ARR_AGG))
+    s1, s2 = H.stats(), H2.stats()
+    assert [d["form"] for d in s1["coarse_A"]] == [d["form"] for d in s2["coarse_A"]]
+    assert s1["dense_tail"]["fp64"]["from"] == s2["dense_tail"]["fp64"]["from"]
+    b = seeded_rhs(p.n, 1, 9)[:, 0]
+    x1, i1 = H.solve(b, tol=1e-8)
+    x2, i2 = H2.solve(b, tol=1e-8)
+    assert i1[0]["iters"] == i2[0]["iters"]
+    assert _rel(np.asarray(x2), np.asarray(x1)) <= 1e-12
+    with pytest.raises(RuntimeError):
+        amg.Hierarchy.load(tmp_path / "missing.amgdd")
+
+
 def _check_level_operators(amg, c, H, ho):
     rng = np.random.default_rng(11)
     for lvl, Lo in enumerate(ho.levels[:-1]):
