@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--serve", action="store_true",
                     help="run the serving workload (many operators and right-hand-side counts) instead")
     ap.add_argument("--no-serving", action="store_true", help="skip the small serving run of the default line")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="build the hierarchy in deterministic mode (no atomics; bitwise repeatable solves)")
     ap.add_argument("--tune-mode", choices=("timed", "defaults", "staged", "shifted", "lanes"), default="timed",
                     help="setup-time kernel choices: timed (default), fixed defaults, or the staged kernel, "
                          "shifted vector loads or lanes per row wherever a plan allows them (profiling)")
@@ -421,7 +423,8 @@ def run_ours(args):
     H = amg.Hierarchy.from_problem(prob, overlap=cfg["overlap"], c_min=cfg["c_min"], n_coarse=cfg["n_coarse"],
                                    thresh=cfg["thresh"], precision=amg.MIXED32, tune_cache=args.tune_cache,
                                    coarse_overlap=cfg.get("coarse_overlap", 0),
-                                   tune={"timed": 1, "defaults": 0, "staged": 2, "shifted": 3, "lanes": 4}[args.tune_mode])
+                                   tune={"timed": 1, "defaults": 0, "staged": 2, "shifted": 3, "lanes": 4}[args.tune_mode],
+                                   deterministic=1 if args.deterministic else 0)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     stats = H.stats()
@@ -614,7 +617,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": workload_desc(cfg), "precision": "FP32 V-cycle, FP64 flexible CG",
                    "l2": "inputs larger than L2: one V-cycle moves %.2f GB" % (float(by.sum()) / 1e9),
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "mode": "deterministic (no atomics)" if args.deterministic else "default"},
         "fp64": {"value": fp64_value, "unit": "solves/s", "ms_per_step": t_64 / args.steps * 1e3,
                  "iters": it_64},
         "mixed_over_fp64": value / fp64_value,
