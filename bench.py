@@ -533,7 +533,8 @@ def run_ours(args):
     achieved = kby / (kms * 1e-3) / 1e9
     # DRAM bytes per V-cycle of a kernel family from an ncu capture of this
     # workload (profiles/); valid only while those kernels are unchanged
-    traffic = TRAFFIC.get(top) if args.workload == WORKLOAD and args.N is None else None
+    traffic = (TRAFFIC.get(top) if args.workload == WORKLOAD and args.N is None and not args.deterministic
+               and args.tune_mode == "timed" else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per V-cycle (kernel family)",
                 "kernel": kdesc.get(top, top), "launches_per_vcycle": fam_n[top],

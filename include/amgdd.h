@@ -346,6 +346,17 @@ void amgdd_server_destroy(amgdd_server* s);
 int amgdd_hierarchy_save(const amgdd_hierarchy* h, const char* path);
 int amgdd_hierarchy_load(const char* path, void* stream, amgdd_hierarchy** out);
 
+/* Failure detection of the bounded device-side waits, without a fault:
+ * launches a grid barrier (the wait of the persistent V-cycle) whose last
+ * CTA never arrives, then an mbarrier wait (the wait of the staged copies)
+ * that nothing completes, on `stream`.  Each gives up after its limit
+ * (about 2 s and 1 s at 2 GHz) and sets an error word that the host reads;
+ * *barrier_status and *mbarrier_status receive AMGDD_ERR_TIMEOUT when the
+ * wait reported its expiry (AMGDD_OK otherwise).  The context stays
+ * usable.  Returns AMGDD_ERR_INVALID_ARG for null outputs, AMGDD_ERR_CUDA
+ * if a launch fails.                                                     */
+int amgdd_selftest_wait_timeouts(void* stream, int* barrier_status, int* mbarrier_status);
+
 void amgdd_free(amgdd_hierarchy* h);
 const char* amgdd_status_string(int status);
 const char* amgdd_last_error(void);

@@ -34,6 +34,7 @@ EXPORTED = [
     "amgdd_kernel_launches", "amgdd_apply_noalloc", "amgdd_device_bytes", "amgdd_server_params_default",
     "amgdd_server_create", "amgdd_server_add_operator", "amgdd_server_submit", "amgdd_server_poll",
     "amgdd_server_stats", "amgdd_server_destroy", "amgdd_hierarchy_save", "amgdd_hierarchy_load",
+    "amgdd_selftest_wait_timeouts",
 ]
 AMGDD_PENDING = 1
 
@@ -99,6 +100,7 @@ def load_library(path: str = LIB_PATH):
     lib.amgdd_free.argtypes = [vp]
     lib.amgdd_hierarchy_save.argtypes = [vp, ctypes.c_char_p]
     lib.amgdd_hierarchy_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
+    lib.amgdd_selftest_wait_timeouts.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.amgdd_free.restype = None
     lib.amgdd_status_string.argtypes = [i32]
     lib.amgdd_status_string.restype = ctypes.c_char_p
@@ -154,6 +156,14 @@ def _stream(stream):
     import torch
 
     return torch.cuda.current_stream().cuda_stream
+
+
+def selftest_wait_timeouts(stream=None) -> tuple[int, int]:
+    """Statuses of the two bounded-wait probes (AMGDD_ERR_TIMEOUT = -9 when reported)."""
+    lib = load_library()
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib.amgdd_selftest_wait_timeouts(_stream(stream), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def kernel_launches() -> int:

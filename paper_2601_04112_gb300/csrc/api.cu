@@ -3515,6 +3515,29 @@ int amgdd_hierarchy_load(const char* path, void* stream, amgdd_hierarchy** out) 
   }
 }
 
+int amgdd_selftest_wait_timeouts(void* stream, int* barrier_status, int* mbarrier_status) {
+  if (barrier_status == nullptr || mbarrier_status == nullptr) {
+    set_error("amgdd_selftest_wait_timeouts: invalid argument");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  DBuf<unsigned> bar;
+  DBuf<int> err;
+  AMGDD_TRY(bar.alloc(2));
+  AMGDD_TRY(err.alloc(1));
+  int* out[2] = {barrier_status, mbarrier_status};
+  for (int which = 0; which < 2; ++which) {
+    AMGDD_TRY(bar.zero(s));
+    AMGDD_TRY(err.zero(s));
+    AMGDD_TRY(launch_wait_probe(which, bar.p, err.p, s));
+    int e = 0;
+    AMGDD_CUDA(cudaMemcpyAsync(&e, err.p, sizeof e, cudaMemcpyDeviceToHost, s));
+    AMGDD_CUDA(cudaStreamSynchronize(s));
+    *out[which] = e != 0 ? AMGDD_ERR_TIMEOUT : AMGDD_OK;
+  }
+  return AMGDD_OK;
+}
+
 void amgdd_free(amgdd_hierarchy* h) {
   if (h == nullptr) return;
   delete h;

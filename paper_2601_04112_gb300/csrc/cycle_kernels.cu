@@ -1490,6 +1490,23 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, int* err) {
   __syncthreads();
 }
 
+// Failure-detection probe of the bounded waits: which 0, a grid barrier that
+// the last CTA never reaches; which 1, an mbarrier phase that no copy or
+// arrival completes.  Each wait gives up after its limit (about 2 s and 1 s)
+// and sets the error word; no copy is in flight, nothing faults.
+__global__ void k_wait_probe(unsigned* bar, int* err, int which) {
+  if (which == 0) {
+    if (blockIdx.x == gridDim.x - 1) return;  // the CTA that never arrives
+    grid_barrier(bar, err);
+  } else {
+    __shared__ __align__(8) uint64_t mb;
+    if (threadIdx.x == 0) mbar_init(&mb);
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&mb, 0u)) atomicExch(err, 1);
+    __syncthreads();
+  }
+}
+
 template <class T>
 __device__ __forceinline__ void phase_out(const PhaseDesc& P, int o, T acc) {
   T* y = (T*)P.y;
@@ -1659,6 +1676,13 @@ __global__ void __launch_bounds__(kItemThreads, 6) k_persistent(const PhaseDesc*
 }
 
 }  // namespace
+
+int launch_wait_probe(int which, unsigned* bar, int* err, cudaStream_t s) {
+  k_wait_probe<<<which == 0 ? 2 : 1, 32, 0, s>>>(bar, err, which);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
 
 PhaseDesc seg_phase(const SegPlan& p, const void* M, const void* MT, bool fp32, const void* x, void* y, SegMode mode,
                     const void* csrc, void* cdst) {

@@ -458,6 +458,8 @@ int launch_pack_z(int nb, const int32_t* no, const int32_t* k, const int64_t* z_
                   const int64_t* z_off, double* Z64, float* Z32, double* Zt64, float* Zt32, cudaStream_t s);
 // Rows omega_i of each assembled A_i (before its Cholesky) in the layout of
 // W_i, plus the block transposes, in FP64 and FP32.
+// failure-detection probe of the bounded waits (0: grid barrier, 1: mbarrier)
+int launch_wait_probe(int which, unsigned* bar, int* err, cudaStream_t s);
 // x_j (+)= sum of Y[pos] over the positions of node j, K interleaved columns
 int launch_gather_add(const int64_t* ptr, const int32_t* pos, const void* Y, void* x, int64_t n, int K, bool fp32,
                       const int* skip, cudaStream_t s);
