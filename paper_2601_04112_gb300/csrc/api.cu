@@ -287,14 +287,18 @@ int default_rpc(int64_t rows, int lanes) {
 // CTA chunks of the lanes-per-row form: `rpc` rows of one block each.
 int set_chunks(SegPlan& p, int rpc, cudaStream_t s) {
   std::vector<int32_t> cb, cr;
+  std::vector<SegDesc> cd;
   for (int b = 0; b < p.nblocks; ++b)
     for (int r = 0; r < p.h_nr[b]; r += rpc) {
       cb.push_back(b);
       cr.push_back(r);
+      cd.push_back(SegDesc{p.h_moff[b], p.h_ioff[b], p.h_ooff[b], r, std::min(p.h_nr[b], r + rpc), p.h_nc[b],
+                           p.h_nr[b]});
     }
   p.rows_per_chunk = rpc;
   p.nchunks = (int)cb.size();
   AMGDD_TRY(p.chunk_blk.upload(cb, s));
+  AMGDD_TRY(p.chunk_desc.upload(cd, s));
   return p.chunk_row0.upload(cr, s);
 }
 
@@ -334,19 +338,26 @@ int build_seg(SegPlan& p, const std::vector<int32_t>& nr, const std::vector<int3
     for (int b = 0; b < p.nblocks; ++b) max_nr = std::max(max_nr, nr[b]);
     p.kind = max_nr >= 24 ? 32 : (max_nr >= 12 ? 16 : 8);
     std::vector<int32_t> tb, tr, tn;
+    std::vector<SegDesc> td;
     for (int b = 0; b < p.nblocks; ++b) {
       for (int r = 0; r < nr[b]; r += p.kind) {
         tb.push_back(b);
         tr.push_back(r);
         tn.push_back(std::min(p.kind, nr[b] - r));
+        td.push_back(SegDesc{m_off[b], in_off[b], out_off[b], r, r + std::min(p.kind, nr[b] - r), nc[b], nr[b]});
       }
     }
     p.ntasks = (int)tb.size();
     AMGDD_TRY(p.task_blk.upload(tb, s));
     AMGDD_TRY(p.task_row0.upload(tr, s));
     AMGDD_TRY(p.task_nrow.upload(tn, s));
+    AMGDD_TRY(p.task_desc.upload(td, s));
   }
   p.h_nr = nr;
+  p.h_nc = nc;
+  p.h_moff = m_off;
+  p.h_ioff = in_off;
+  p.h_ooff = out_off;
   if (force != 2) {
     AMGDD_TRY(set_chunks(p, p.rows_per_chunk, s));
   } else {

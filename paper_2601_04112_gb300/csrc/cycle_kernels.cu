@@ -79,12 +79,7 @@ __device__ __forceinline__ void seg_stage(T* xs, int S, int c, T v) {
 }
 
 template <class T, int L, int MODE, int VK, int U = 1>
-__global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__ chunk_blk,
-                                                     const int32_t* __restrict__ chunk_row0, int rows_per_chunk,
-                                                     const int64_t* __restrict__ m_off, const int32_t* __restrict__ nr,
-                                                     const int32_t* __restrict__ nc,
-                                                     const int64_t* __restrict__ in_off,
-                                                     const int64_t* __restrict__ out_off,
+__global__ void __launch_bounds__(kSegThreads) k_seg(const SegDesc* __restrict__ desc,
                                                      const int32_t* __restrict__ in_idx,
                                                      const int32_t* __restrict__ out_idx, const T* __restrict__ M,
                                                      const T* __restrict__ x, T* __restrict__ y, const int* skip,
@@ -95,11 +90,12 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
   using V = typename Vec2<T>::type;
   constexpr int W = Vec2<T>::width;
   T* xs = reinterpret_cast<T*>(smem_raw);
-  const int b = chunk_blk[blockIdx.x];
-  const int r0 = chunk_row0[blockIdx.x];
-  const int ncb = nc[b];
-  const int r1 = min(nr[b], r0 + rows_per_chunk);
-  const int32_t* ii = in_idx + in_off[b];
+  const SegDesc dsc = desc[blockIdx.x];  // the chunk's block, in one dependent step
+  const int r0 = dsc.r0;
+  const int ncb = dsc.nc;
+  const int r1 = dsc.r1;
+  const int64_t mob = dsc.m_off;
+  const int32_t* ii = in_idx + dsc.in_off;
   const int S = VK == 2 ? ((ncb + W - 1) / W) * W + W : 0;
   const int lane = threadIdx.x % L;
   const int grp = threadIdx.x / L;
@@ -107,7 +103,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
   // shifted form: the group's first row is requested before the gather, so
   // that its loads overlap the gather's two dependent loads
   const int rf = r0 + grp;
-  const int32_t* oo = out_idx + out_off[b];
+  const int32_t* oo = out_idx + dsc.out_off;
   const bool need_c = MODE == SEG_RESID || cdst != nullptr;
   V pre[U];
   int po = 0;
@@ -116,7 +112,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
 #pragma unroll
     for (int u = 0; u < U; ++u) pre[u] = V{};
     if (rf < r1) {
-      const int64_t e0 = m_off[b] + (int64_t)rf * ncb;
+      const int64_t e0 = mob + (int64_t)rf * ncb;
       const int a = (int)(e0 & (W - 1));
       const int64_t base = e0 - a;
       int nv = (ncb + a + W - 1) / W;
@@ -163,7 +159,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
     // vectors, output index, copied value and (add mode) old output are
     // requested before the current row is summed
     for (int r = rf; r < r1; r += ngrp) {
-      const int64_t e0 = m_off[b] + (int64_t)r * ncb;
+      const int64_t e0 = mob + (int64_t)r * ncb;
       const int a = (int)(e0 & (W - 1));
       const int64_t base = e0 - a;
       const V* rv = reinterpret_cast<const V*>(M + base);
@@ -178,7 +174,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
       int no = 0;
       T nc_ = T(0), ny = T(0);
       if (rn < r1) {
-        const int64_t e1 = m_off[b] + (int64_t)rn * ncb;
+        const int64_t e1 = mob + (int64_t)rn * ncb;
         const int a1 = (int)(e1 & (W - 1));
         const int64_t base1 = e1 - a1;
         int nv1 = (ncb + a1 + W - 1) / W;
@@ -246,7 +242,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
       const V* rv;
       const V* xv;
       int nv;
-      rv = reinterpret_cast<const V*>(M + m_off[b] + (int64_t)r * ncb);  // VK 1: aligned rows
+      rv = reinterpret_cast<const V*>(M + mob + (int64_t)r * ncb);  // VK 1: aligned rows
       xv = reinterpret_cast<const V*>(xs);
       nv = ncb / W;
       int c = lane;
@@ -266,7 +262,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
       }
       for (; c < nv; c += L) acc += vdot(rv[c], xv[c]);
     } else {
-      const T* row = M + m_off[b] + (int64_t)r * ncb;
+      const T* row = M + mob + (int64_t)r * ncb;
       int c = lane;
       if constexpr (U > 1) {
         T a[U];
@@ -309,12 +305,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const int32_t* __restrict__
 // consecutive values.  x(in_idx) is staged once per task in shared memory.
 // Outputs, atomics and the fused copy are issued by all lanes at once.
 template <class T, int L, int MODE>
-__global__ void __launch_bounds__(128) k_seg_rows(const int32_t* __restrict__ task_blk,
-                                                  const int32_t* __restrict__ task_row0,
-                                                  const int32_t* __restrict__ task_nrow, int ntasks, int max_nc,
-                                                  const int64_t* __restrict__ m_off, const int32_t* __restrict__ nr,
-                                                  const int32_t* __restrict__ nc, const int64_t* __restrict__ in_off,
-                                                  const int64_t* __restrict__ out_off,
+__global__ void __launch_bounds__(128) k_seg_rows(const SegDesc* __restrict__ desc, int ntasks, int max_nc,
                                                   const int32_t* __restrict__ in_idx,
                                                   const int32_t* __restrict__ out_idx, const T* __restrict__ MT,
                                                   const T* __restrict__ x, T* __restrict__ y, const int* skip,
@@ -328,21 +319,21 @@ __global__ void __launch_bounds__(128) k_seg_rows(const int32_t* __restrict__ ta
   const int lane = threadIdx.x % L;
   const unsigned mask = group_mask<L>();
   T* xs = reinterpret_cast<T*>(smem_raw) + (size_t)grp * max_nc;
-  const int b = task_blk[t];
-  const int r0 = task_row0[t];
-  const int rows = task_nrow[t];
-  const int ncb = nc[b], nrb = nr[b];
-  const int32_t* ii = in_idx + in_off[b];
+  const SegDesc dsc = desc[t];  // the task's block, in one dependent step
+  const int r0 = dsc.r0;
+  const int rows = dsc.r1 - dsc.r0;
+  const int ncb = dsc.nc, nrb = dsc.nr;
+  const int32_t* ii = in_idx + dsc.in_off;
   // the lane's first kPre column entries, its output index and the copied
   // value are requested before the gather, overlapping its dependent loads
   constexpr int kPre = 16;
   const bool act = lane < rows;
   const int r = r0 + lane;
-  const T* col = MT + m_off[b] + r;
+  const T* col = MT + dsc.m_off + r;
   T pre[kPre];
 #pragma unroll
   for (int c = 0; c < kPre; ++c) pre[c] = (act && c < ncb) ? col[(int64_t)c * nrb] : T(0);
-  const int o = act ? out_idx[out_off[b] + r] : 0;
+  const int o = act ? out_idx[dsc.out_off + r] : 0;
   const bool need_c = MODE == SEG_RESID || cdst != nullptr;
   const T cv = (act && need_c) ? csrc[o] : T(0);
   for (int c = lane; c < ncb; c += L) xs[c] = x[ii[c]];
@@ -557,9 +548,8 @@ int seg_rows_launch(const SegPlan& p, const T* MT, const T* x, T* y, const int* 
   const size_t smem = (size_t)per * p.max_nc * sizeof(T);
   auto kern = k_seg_rows<T, L, MODE>;
   if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  AMGDD_CUDA(launch_k(g_pdl, kern, grid, 128, smem, s, p.task_blk.p, p.task_row0.p, p.task_nrow.p, p.ntasks, p.max_nc, p.m_off.p, p.nr.p,
-                               p.nc.p, p.in_off.p, p.out_off.p, p.in_idx_ext, p.out_idx_ext, MT, x, y, skip, csrc,
-                               cdst));
+  AMGDD_CUDA(launch_k(g_pdl, kern, grid, 128, smem, s, (const SegDesc*)p.task_desc.p, p.ntasks, p.max_nc,
+                      p.in_idx_ext, p.out_idx_ext, MT, x, y, skip, csrc, cdst));
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
   return AMGDD_OK;
@@ -582,9 +572,8 @@ int seg_launch_kind(const SegPlan& p, const T* M, const T* x, T* y, SegMode mode
                     const T* csrc, T* cdst, size_t smem) {
   auto launch = [&](auto kern) -> int {
     if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    AMGDD_CUDA(launch_k(g_pdl, kern, p.nchunks, kSegThreads, smem, s, p.chunk_blk.p, p.chunk_row0.p, p.rows_per_chunk, p.m_off.p, p.nr.p,
-                                              p.nc.p, p.in_off.p, p.out_off.p, p.in_idx_ext, p.out_idx_ext, M, x, y,
-                                              skip, csrc, cdst, p.mat_len));
+    AMGDD_CUDA(launch_k(g_pdl, kern, p.nchunks, kSegThreads, smem, s, (const SegDesc*)p.chunk_desc.p,
+                        p.in_idx_ext, p.out_idx_ext, M, x, y, skip, csrc, cdst, p.mat_len));
     AMGDD_CUDA(cudaGetLastError());
     count_kernels(1);
     return AMGDD_OK;

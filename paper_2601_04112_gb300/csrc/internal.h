@@ -105,6 +105,14 @@ struct alignas(16) ItemDesc {
   int pad;
 };
 
+// Everything a gather-GEMV CTA (chunk) or task needs about its block, in one
+// record, so that it is read in a single dependent step.
+struct SegDesc {
+  int64_t m_off, in_off, out_off;
+  int32_t r0, r1;  // rows r0 <= r < r1 of the block (task: r1 = r0 + rows)
+  int32_t nc, nr;
+};
+
 struct SegPlan {
   int nblocks = 0;
   int nchunks = 0;      // CTAs: chunks of at most `rows_per_chunk` rows of one block
@@ -120,7 +128,10 @@ struct SegPlan {
   DBuf<int64_t> m_off, in_off, out_off;
   DBuf<int32_t> nr, nc;
   DBuf<int32_t> chunk_blk, chunk_row0;
+  DBuf<SegDesc> chunk_desc;   // per chunk (the single right-hand-side kernel)
   std::vector<int32_t> h_nr;  // rows per block (host), to rebuild the chunks
+  std::vector<int32_t> h_nc;
+  std::vector<int64_t> h_moff, h_ioff, h_ooff;
   // index arrays owned elsewhere (level Omega lists or the identity)
   const int32_t* in_idx_ext = nullptr;
   const int32_t* out_idx_ext = nullptr;
@@ -130,6 +141,7 @@ struct SegPlan {
   int kind = 0;
   int ntasks = 0;
   DBuf<int32_t> task_blk, task_row0, task_nrow;
+  DBuf<SegDesc> task_desc;    // per task (the single right-hand-side kernel)
   // staged form (preferred when built): items of contiguous matrix rows,
   // either up to 32 whole consecutive blocks or a row slice of one block,
   // each moved to shared memory by one bulk copy; per item the host packs
