@@ -37,13 +37,7 @@ __device__ __forceinline__ void multi_out(SegMode mode, T* y, const T* c, int o,
 // Lanes-per-row plans: one CTA per chunk (block b, rows r0..r1); the K
 // columns of the gathered input are staged in shared memory, node-major.
 template <class T, int L, int K>
-__global__ void __launch_bounds__(kMultiThreads) k_seg_multi(const int32_t* __restrict__ chunk_blk,
-                                                             const int32_t* __restrict__ chunk_row0,
-                                                             int rows_per_chunk, const int64_t* __restrict__ m_off,
-                                                             const int32_t* __restrict__ nr,
-                                                             const int32_t* __restrict__ nc,
-                                                             const int64_t* __restrict__ in_off,
-                                                             const int64_t* __restrict__ out_off,
+__global__ void __launch_bounds__(kMultiThreads) k_seg_multi(const SegDesc* __restrict__ desc,
                                                              const int32_t* __restrict__ in_idx,
                                                              const int32_t* __restrict__ out_idx,
                                                              const T* __restrict__ M, const T* __restrict__ x,
@@ -53,11 +47,11 @@ __global__ void __launch_bounds__(kMultiThreads) k_seg_multi(const int32_t* __re
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw);
-  const int b = chunk_blk[blockIdx.x];
-  const int r0 = chunk_row0[blockIdx.x];
-  const int ncb = nc[b];
-  const int r1 = min(nr[b], r0 + rows_per_chunk);
-  const int32_t* ii = in_idx + in_off[b];
+  const SegDesc dsc = desc[blockIdx.x];  // the chunk's block, in one dependent step
+  const int r0 = dsc.r0;
+  const int ncb = dsc.nc;
+  const int r1 = dsc.r1;
+  const int32_t* ii = in_idx + dsc.in_off;
   for (int e = threadIdx.x; e < ncb * K; e += blockDim.x) {
     const int cc = e / K, k = e - cc * K;
     xs[e] = x[(int64_t)ii[cc] * K + k];
@@ -67,8 +61,8 @@ __global__ void __launch_bounds__(kMultiThreads) k_seg_multi(const int32_t* __re
   const int grp = threadIdx.x / L;
   const int ngrp = blockDim.x / L;
   const unsigned mask = group_mask<L>();
-  const T* Mb = M + m_off[b];
-  const int32_t* oo = out_idx + out_off[b];
+  const T* Mb = M + dsc.m_off;
+  const int32_t* oo = out_idx + dsc.out_off;
   for (int r = r0 + grp; r < r1; r += ngrp) {
     const T* row = Mb + (int64_t)r * ncb;
     T acc[K];
@@ -131,10 +125,7 @@ __global__ void __launch_bounds__(256) k_ell_multi(const T* __restrict__ val, co
 // Row-per-lane plans over the block-wise transposed copy MT.
 template <class T, int L, int K>
 __global__ void __launch_bounds__(kMultiThreads) k_seg_rows_multi(
-    const int32_t* __restrict__ task_blk, const int32_t* __restrict__ task_row0, const int32_t* __restrict__ task_nrow,
-    int ntasks, int max_nc, const int64_t* __restrict__ m_off, const int32_t* __restrict__ nr,
-    const int32_t* __restrict__ nc, const int64_t* __restrict__ in_off, const int64_t* __restrict__ out_off,
-    const int32_t* __restrict__ in_idx, const int32_t* __restrict__ out_idx, const T* __restrict__ MT,
+    const SegDesc* __restrict__ desc, int ntasks, int max_nc, const int32_t* __restrict__ in_idx, const int32_t* __restrict__ out_idx, const T* __restrict__ MT,
     const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ c, int mode, const int* skip) {
   pdl_prologue();
   if (skip != nullptr && *skip) return;
@@ -145,11 +136,11 @@ __global__ void __launch_bounds__(kMultiThreads) k_seg_rows_multi(
   const int lane = threadIdx.x % L;
   const unsigned mask = group_mask<L>();
   T* xs = reinterpret_cast<T*>(smem_raw) + (size_t)grp * max_nc * K;
-  const int b = task_blk[t];
-  const int r0 = task_row0[t];
-  const int rows = task_nrow[t];
-  const int ncb = nc[b], nrb = nr[b];
-  const int32_t* ii = in_idx + in_off[b];
+  const SegDesc dsc = desc[t];  // the task's block, in one dependent step
+  const int r0 = dsc.r0;
+  const int rows = dsc.r1 - dsc.r0;
+  const int ncb = dsc.nc, nrb = dsc.nr;
+  const int32_t* ii = in_idx + dsc.in_off;
   for (int e = lane; e < ncb * K; e += L) {
     const int cc = e / K, k = e - cc * K;
     xs[e] = x[(int64_t)ii[cc] * K + k];
@@ -157,7 +148,7 @@ __global__ void __launch_bounds__(kMultiThreads) k_seg_rows_multi(
   __syncwarp(mask);
   if (lane >= rows) return;
   const int r = r0 + lane;
-  const T* col = MT + m_off[b] + r;
+  const T* col = MT + dsc.m_off + r;
   T acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = T(0);
@@ -166,7 +157,7 @@ __global__ void __launch_bounds__(kMultiThreads) k_seg_rows_multi(
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] += m * xs[cc * K + k];
   }
-  multi_out<T, K>((SegMode)mode, y, c, out_idx[out_off[b] + r], acc);
+  multi_out<T, K>((SegMode)mode, y, c, out_idx[dsc.out_off + r], acc);
 }
 
 // K dot products a_k . b_k (and a_k . c_k) per CTA; the grid stride is a
@@ -355,9 +346,9 @@ int seg_multi_k(const SegPlan& p, const T* M, const T* MT, const T* x, T* y, Seg
       const int per = kMultiThreads / L;
       const size_t smem = (size_t)per * p.max_nc * K * sizeof(T);
       if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      AMGDD_CUDA(launch_k(g_pdl, kern, (p.ntasks + per - 1) / per, kMultiThreads, smem, s, 
-          p.task_blk.p, p.task_row0.p, p.task_nrow.p, p.ntasks, p.max_nc, p.m_off.p, p.nr.p, p.nc.p, p.in_off.p,
-          p.out_off.p, p.in_idx_ext, p.out_idx_ext, MT, x, y, c, (int)mode, skip));
+      AMGDD_CUDA(launch_k(g_pdl, kern, (p.ntasks + per - 1) / per, kMultiThreads, smem, s,
+                          (const SegDesc*)p.task_desc.p, p.ntasks, p.max_nc, p.in_idx_ext, p.out_idx_ext, MT, x, y,
+                          c, (int)mode, skip));
       AMGDD_CUDA(cudaGetLastError());
       count_kernels(1);
       return AMGDD_OK;
@@ -371,9 +362,8 @@ int seg_multi_k(const SegPlan& p, const T* M, const T* MT, const T* x, T* y, Seg
   auto go = [&](auto kern) -> int {
     const size_t smem = (size_t)p.max_nc * K * sizeof(T);
     if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    AMGDD_CUDA(launch_k(g_pdl, kern, p.nchunks, kMultiThreads, smem, s, p.chunk_blk.p, p.chunk_row0.p, p.rows_per_chunk, p.m_off.p, p.nr.p,
-                                                p.nc.p, p.in_off.p, p.out_off.p, p.in_idx_ext, p.out_idx_ext, M, x, y, c,
-                                                (int)mode, skip));
+    AMGDD_CUDA(launch_k(g_pdl, kern, p.nchunks, kMultiThreads, smem, s, (const SegDesc*)p.chunk_desc.p,
+                        p.in_idx_ext, p.out_idx_ext, M, x, y, c, (int)mode, skip));
     AMGDD_CUDA(cudaGetLastError());
     count_kernels(1);
     return AMGDD_OK;
