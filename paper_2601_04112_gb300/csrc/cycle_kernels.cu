@@ -234,67 +234,67 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const SegDesc* __restrict__
       pc = nc_;
       py = ny;
     }
-    return;
-  }
-  for (int r = r0 + grp; r < r1; r += ngrp) {
-    T acc = T(0);
-    if constexpr (VK != 0) {
-      const V* rv;
-      const V* xv;
-      int nv;
-      rv = reinterpret_cast<const V*>(M + mob + (int64_t)r * ncb);  // VK 1: aligned rows
-      xv = reinterpret_cast<const V*>(xs);
-      nv = ncb / W;
-      int c = lane;
-      if constexpr (U > 1) {
-        T a[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) a[u] = T(0);
-        for (; c + (U - 1) * L < nv; c += U * L) {
-          V m[U];
-#pragma unroll
-          for (int u = 0; u < U; ++u) m[u] = rv[c + u * L];
-#pragma unroll
-          for (int u = 0; u < U; ++u) a[u] += vdot(m[u], xv[c + u * L]);
+  } else {
+    for (int r = r0 + grp; r < r1; r += ngrp) {
+      T acc = T(0);
+      if constexpr (VK != 0) {
+        const V* rv;
+        const V* xv;
+        int nv;
+        rv = reinterpret_cast<const V*>(M + mob + (int64_t)r * ncb);  // VK 1: aligned rows
+        xv = reinterpret_cast<const V*>(xs);
+        nv = ncb / W;
+        int c = lane;
+        if constexpr (U > 1) {
+          T a[U];
+  #pragma unroll
+          for (int u = 0; u < U; ++u) a[u] = T(0);
+          for (; c + (U - 1) * L < nv; c += U * L) {
+            V m[U];
+  #pragma unroll
+            for (int u = 0; u < U; ++u) m[u] = rv[c + u * L];
+  #pragma unroll
+            for (int u = 0; u < U; ++u) a[u] += vdot(m[u], xv[c + u * L]);
+          }
+  #pragma unroll
+          for (int u = 0; u < U; ++u) acc += a[u];
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) acc += a[u];
-      }
-      for (; c < nv; c += L) acc += vdot(rv[c], xv[c]);
-    } else {
-      const T* row = M + mob + (int64_t)r * ncb;
-      int c = lane;
-      if constexpr (U > 1) {
-        T a[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) a[u] = T(0);
-        for (; c + (U - 1) * L < ncb; c += U * L) {
-          T m[U];
-#pragma unroll
-          for (int u = 0; u < U; ++u) m[u] = row[c + u * L];
-#pragma unroll
-          for (int u = 0; u < U; ++u) a[u] += m[u] * xs[c + u * L];
+        for (; c < nv; c += L) acc += vdot(rv[c], xv[c]);
+      } else {
+        const T* row = M + mob + (int64_t)r * ncb;
+        int c = lane;
+        if constexpr (U > 1) {
+          T a[U];
+  #pragma unroll
+          for (int u = 0; u < U; ++u) a[u] = T(0);
+          for (; c + (U - 1) * L < ncb; c += U * L) {
+            T m[U];
+  #pragma unroll
+            for (int u = 0; u < U; ++u) m[u] = row[c + u * L];
+  #pragma unroll
+            for (int u = 0; u < U; ++u) a[u] += m[u] * xs[c + u * L];
+          }
+  #pragma unroll
+          for (int u = 0; u < U; ++u) acc += a[u];
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) acc += a[u];
+        for (; c < ncb; c += L) acc += row[c] * xs[c];
       }
-      for (; c < ncb; c += L) acc += row[c] * xs[c];
-    }
-    acc = group_sum<L>(acc, mask);
-    if (lane == 0) {
-      const int o = oo[r];
-      T* dst = y + o;
-      if (MODE == SEG_STORE)
-        *dst = acc;
-      else if (MODE == SEG_ADD)
-        *dst += acc;
-      else if (MODE == SEG_ATOMIC_ADD)
-        atomic_add(dst, acc);
-      else if (MODE == SEG_ATOMIC_SUB)
-        atomic_add(dst, -acc);
-      else
-        *dst = csrc[o] - acc;
-      if (MODE != SEG_RESID && cdst != nullptr) cdst[o] = csrc[o];
+      acc = group_sum<L>(acc, mask);
+      if (lane == 0) {
+        const int o = oo[r];
+        T* dst = y + o;
+        if (MODE == SEG_STORE)
+          *dst = acc;
+        else if (MODE == SEG_ADD)
+          *dst += acc;
+        else if (MODE == SEG_ATOMIC_ADD)
+          atomic_add(dst, acc);
+        else if (MODE == SEG_ATOMIC_SUB)
+          atomic_add(dst, -acc);
+        else
+          *dst = csrc[o] - acc;
+        if (MODE != SEG_RESID && cdst != nullptr) cdst[o] = csrc[o];
+      }
     }
   }
 }
