@@ -49,4 +49,4 @@ from .structure import (  # noqa: F401
     vanek_aggregation,
 )
 from .construct import Hierarchy, Level, setup, local_splitting, schur_complement, local_gep  # noqa: F401
-from .cycle import ras, rast, vcycle, pcg, apply_A, metrics  # noqa: F401
+from .cycle import ras, rast, vcycle, pcg, apply_A, metrics, additive_schwarz, two_level_additive  # noqa: F401

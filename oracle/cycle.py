@@ -9,6 +9,9 @@
 * V-cycle (Section 2.1 coarse-grid correction; Section 3.1: one RAS pre-,
   one RAS-T post-smoothing, recursion to an exact coarsest solve), started
   from x = 0 so that it applies a fixed linear preconditioner B;
+* the additive two-level method M_2^{-1} = P (P^T A P)^{-1} P^T + M_1^{-1}
+  with additive Schwarz M_1^{-1} = sum_i R_i^T A_i^{-1} R_i (Section 3.1,
+  after Eq. cgc), on two-level hierarchies;
 * preconditioned CG (Hestenes-Stiefel, x_0 = 0), stopped when the
   recursively updated residual satisfies ||r_k|| <= tol ||b||, plus the
   flexible variant beta = r_{k+1}^T (z_{k+1} - z_k) / (r_k^T z_k);
@@ -71,8 +74,32 @@ def vcycle(h, r, lvl=0):
     return x
 
 
-def pcg(h, b, tol=1e-8, maxit=1000, flexible=False):
-    """Preconditioned CG with the V-cycle; one right-hand side.
+def additive_schwarz(level, r):
+    """x = M_1^{-1} r = sum_i R_i^T A_i^{-1} R_i r: the Schwarz smoother of
+    Eq. ras without the partition of unity (additive Schwarz); every local
+    solution is added back on all of Omega_i."""
+    x = np.zeros(level.n)
+    for i in range(level.nagg):
+        Om = level.Omega[i]
+        x[Om] += _local_solve(level.chol[i], r[Om])
+    return x
+
+
+def two_level_additive(h, r):
+    """z = M_2^{-1} r = P (P^T A P)^{-1} P^T r + M_1^{-1} r, the additive
+    two-level method the paper sets beside the multiplicative cycle (Section
+    3.1), with M_1 additive Schwarz and an exact solve of the level-1
+    operator P^T A P.  Defined on two-level hierarchies."""
+    if len(h.levels) != 2:
+        raise ValueError("the additive two-level method needs a two-level hierarchy")
+    L = h.levels[0]
+    xc = sla.cho_solve((h.coarse_chol, True), L.P.T @ r)
+    return additive_schwarz(L, r) + L.P @ xc
+
+
+def pcg(h, b, tol=1e-8, maxit=1000, flexible=False, precond=None):
+    """Preconditioned CG with the V-cycle (or `precond(h, r)`, e.g. the
+    additive two-level method); one right-hand side.
 
     Returns (x, info) with info = dict(iters, relres (recursive), relres_true,
     history (recursive relative residuals), status) where status is 0 on
@@ -84,8 +111,9 @@ def pcg(h, b, tol=1e-8, maxit=1000, flexible=False):
     x = np.zeros_like(b)
     if bn == 0.0:
         return x, dict(iters=0, relres=0.0, relres_true=0.0, history=[0.0], status=0)
+    apply_B = vcycle if precond is None else precond
     r = b.copy()
-    z = vcycle(h, r)
+    z = apply_B(h, r)
     p = z.copy()
     rz = float(r @ z)
     hist = [1.0]
@@ -106,7 +134,7 @@ def pcg(h, b, tol=1e-8, maxit=1000, flexible=False):
         if rel <= tol:
             status = 0
             break
-        zn = vcycle(h, r)
+        zn = apply_B(h, r)
         if flexible:
             rzn = float(r @ zn)
             beta = float(r @ (zn - z)) / rz
