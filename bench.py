@@ -58,6 +58,9 @@ def parse_args():
     ap.add_argument("--serve", action="store_true",
                     help="run the serving workload (many operators and right-hand-side counts) instead")
     ap.add_argument("--no-serving", action="store_true", help="skip the small serving run of the default line")
+    ap.add_argument("--additive", action="store_true",
+                    help="time PCG with the additive two-level method (cycle = 1) beside the multiplicative two-level "
+                         "cycle, FP64, on the 64x64 workload's two-level hierarchy, instead")
     ap.add_argument("--deterministic", action="store_true",
                     help="build the hierarchy in deterministic mode (no atomics; bitwise repeatable solves)")
     ap.add_argument("--tune-mode", choices=("timed", "defaults", "staged", "shifted", "lanes"), default="timed",
@@ -358,6 +361,33 @@ def run_ours(args):
     __graft_entry__.build()
     import paper_2601_04112_gb300 as amg
     from inputs.q1 import config_problem, seeded_rhs
+
+    if args.additive:
+        # the additive two-level method M_2 against the multiplicative two-level
+        # V-cycle on the same two-level hierarchy (FP64 PCG to 1e-8)
+        name = "q1_64_rot" if args.workload == WORKLOAD else args.workload
+        prob, cfg = config_problem(name)
+        b = torch.from_numpy(seeded_rhs(prob.n, 1, cfg["seed"])[:, 0]).cuda()
+        out = {"metric": "solves/s to 1e-8 rel. residual, additive two-level M_2 vs multiplicative two-level cycle "
+                         "(FP64)", "impl": "ours", "workload": workload_desc(cfg) + ", L_max 2"}
+        for label, cyc in (("multiplicative", 0), ("additive", 1)):
+            Hc = amg.Hierarchy.from_problem(prob, overlap=cfg["overlap"], c_min=cfg["c_min"],
+                                            n_coarse=cfg["n_coarse"], thresh=cfg["thresh"], L_max=2, cycle=cyc)
+            for _ in range(args.warmup):
+                Hc.solve(b, tol=1e-8)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its = []
+            for _ in range(args.steps):
+                _, inf = Hc.solve(b, tol=1e-8)
+                assert inf[0]["status"] == 0 and inf[0]["relres_true"] <= 1e-8, inf
+                its.append(inf[0]["iters"])
+            torch.cuda.synchronize()
+            out[label] = {"solves_per_s": args.steps / (time.perf_counter() - t0), "iters": its[0],
+                          "levels": Hc.stats()["n"]}
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
 
     if args.sweep:
         # the (eps, theta) sweep of the 512x512 workload: setup, iterations and

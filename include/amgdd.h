@@ -125,6 +125,12 @@ typedef struct {
                        /*   entry and gathers per node in a fixed order   */
                        /*   (Eq. ras-t); level 0 by ELL rows (ell = 1),   */
                        /*   coarse A by block rows, no persistent tail    */
+  int cycle;           /* preconditioner: 0 (default) the multiplicative  */
+                       /*   V-cycle (Section 3.1); 1 the additive two-    */
+                       /*   level method M_2^{-1} = P (P^T A P)^{-1} P^T  */
+                       /*   + sum_i R_i^T A_i^{-1} R_i (additive Schwarz, */
+                       /*   Section 3.1 after Eq. cgc): needs a two-level */
+                       /*   hierarchy (setup fails otherwise), runs FP64  */
 } amgdd_params;
 
 typedef struct amgdd_hierarchy amgdd_hierarchy; /* opaque, library-owned */
@@ -197,6 +203,8 @@ int amgdd_set_precision(amgdd_hierarchy* h, int precision);
 #define AMGDD_OP_PROLONG 4  /* y = P_l x    (x of length n_{l+1})         */
 #define AMGDD_OP_VCYCLE 5   /* y = B_l x: V-cycle from level l, x_0 = 0   */
 #define AMGDD_OP_COARSE 6   /* y = A_L^{-1} x on the coarsest level       */
+#define AMGDD_OP_M2 7       /* y = M_2^{-1} x, additive two-level method  */
+                            /*   (level 0 of a cycle = 1 hierarchy)       */
 /* Applies one operator of level `level` in the hierarchy's current
  * precision; x and y are device arrays of FP64 (converted internally in
  * MIXED32).  x and y must not alias.                                     */

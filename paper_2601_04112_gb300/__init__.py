@@ -24,7 +24,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "not SPD", -3: "non-finite", -4: 
           -5: "no convergence", -6: "out of device memory", -7: "CUDA error", -8: "internal error"}
 HOST, DEVICE = 0, 1
 FP64, MIXED32 = 0, 1
-OP_A, OP_RAS, OP_RAST, OP_RESTRICT, OP_PROLONG, OP_VCYCLE, OP_COARSE = range(7)
+OP_A, OP_RAS, OP_RAST, OP_RESTRICT, OP_PROLONG, OP_VCYCLE, OP_COARSE, OP_M2 = range(8)
 ARR_AGG, ARR_OMEGA_PTR, ARR_OMEGA_IDX, ARR_NOMEGA, ARR_K, ARR_Z, ARR_MU = range(7)
 
 EXPORTED = [
@@ -56,7 +56,7 @@ class Params(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("tune", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
                 ("coarse_overlap", ctypes.c_int), ("coarse_refine", ctypes.c_int),
                 ("pdl", ctypes.c_int), ("dense_tail", ctypes.c_int), ("ell", ctypes.c_int),
-                ("deterministic", ctypes.c_int)]
+                ("deterministic", ctypes.c_int), ("cycle", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -704,6 +704,8 @@ int tune_level_plans(Level& L, int lvl, int64_t n_next, cudaStream_t s) {
   AMGDD_TRY(tune_seg<float>(L.ras, k + "ras", L.W32.p, L.Wt32.p, L.n, L.n, SEG_STORE, s));
   AMGDD_TRY(tune_seg<float>(L.rast, k + "rast", L.Wt32.p, L.W32.p, L.n, L.n, SEG_ATOMIC_ADD, s));
   if (L.yd32.p) AMGDD_TRY(tune_seg<float>(L.rast_det, k + "rastd", L.Wt32.p, L.W32.p, L.n, L.om_ptr.back(), SEG_STORE, s));
+  if (L.Wf64.p)  // the additive form runs in FP64 only
+    AMGDD_TRY(tune_seg<double>(L.asp, k + "as64", L.Wf64.p, L.Wft64.p, L.n, L.n, SEG_ATOMIC_ADD, s));
   AMGDD_TRY(tune_seg<float>(L.restr, k + "restrict", L.Zt32.p, L.Z32.p, L.n, n_next, SEG_STORE, s));
   AMGDD_TRY(tune_seg<float>(L.prol, k + "prolong", L.Z32.p, L.Zt32.p, n_next, L.n, SEG_ADD, s));
   if (L.A32.p) AMGDD_TRY(tune_seg<float>(L.ablk, k + "blockrows", L.A32.p, L.At32.p, L.n, L.n, SEG_RESID, s));
@@ -1091,6 +1093,18 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
   AMGDD_TRY(L.mu.alloc(mu_off[nagg]));
   DBuf<double> inv_scratch;
   AMGDD_TRY(inv_scratch.alloc(w_off[nagg]));
+  // additive Schwarz (cycle = 1): every row of A_i^{-1}
+  const bool full_inv = h.prm.cycle == 1 && lvl == 0;
+  DBuf<double> full_scratch;
+  if (full_inv) {
+    L.wf_off.assign(nagg + 1, 0);
+    for (int i = 0; i < nagg; ++i) L.wf_off[i + 1] = L.wf_off[i] + (int64_t)mdim[i] * mdim[i];
+    AMGDD_TRY(L.Wf64.alloc(L.wf_off[nagg]));
+    AMGDD_TRY(L.Wft64.alloc(L.wf_off[nagg]));
+    AMGDD_TRY(L.Wf32.alloc(L.wf_off[nagg]));
+    AMGDD_TRY(L.Wft32.alloc(L.wf_off[nagg]));
+    AMGDD_TRY(full_scratch.alloc(L.wf_off[nagg]));
+  }
   DBuf<int64_t> d_w_off, d_mu_off;
   AMGDD_TRY(d_w_off.upload(w_off, s));
   AMGDD_TRY(d_mu_off.upload(mu_off, s));
@@ -1215,6 +1229,24 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
       AMGDD_TRY(dcc.upload(cc, s));
       AMGDD_TRY(launch_inv_rows(nb, max_m, B.m.p, B.no.p, B.a_off.p, Apool.p, dwoff.p, L.W64.p, L.W32.p, L.Wt64.p,
                                 L.Wt32.p, inv_scratch.p, dcb.p, dcc.p, (int)cb.size(), kInvChunk, s));
+      if (full_inv) {  // the same solves for every column of A_i^{-1} (rows = columns: m per block)
+        std::vector<int32_t> fb, fc;
+        std::vector<int64_t> fo(nb);
+        for (int t = 0; t < nb; ++t) {
+          fo[t] = L.wf_off[i0 + t];
+          for (int c = 0; c < bm[t]; c += kInvChunk) {
+            fb.push_back(t);
+            fc.push_back(c);
+          }
+        }
+        DBuf<int32_t> dfb, dfc;
+        DBuf<int64_t> dfo;
+        AMGDD_TRY(dfb.upload(fb, s));
+        AMGDD_TRY(dfc.upload(fc, s));
+        AMGDD_TRY(dfo.upload(fo, s));
+        AMGDD_TRY(launch_inv_rows(nb, max_m, B.m.p, B.m.p, B.a_off.p, Apool.p, dfo.p, L.Wf64.p, L.Wf32.p, L.Wft64.p,
+                                  L.Wft32.p, full_scratch.p, dfb.p, dfc.p, (int)fb.size(), kInvChunk, s));
+      }
       AMGDD_CUDA(cudaStreamSynchronize(s));
     }
     {
@@ -1259,6 +1291,12 @@ int build_plans(amgdd_hierarchy& h, Level& L, DBuf<int32_t>& d_om_idx, cudaStrea
     ooff[i] = L.om_ptr[i];
   }
   AMGDD_TRY(build_seg(L.ras, nr, nc, moff, ioff, ooff, d_om_idx.p, d_om_idx.p, s));
+  if (L.Wf64.p) {  // additive Schwarz: x(Omega_i) += A_i^{-1} r(Omega_i)
+    std::vector<int32_t> fr(nagg);
+    for (int i = 0; i < nagg; ++i) fr[i] = nc[i];
+    std::vector<int64_t> fo(L.wf_off.begin(), L.wf_off.end() - 1);
+    AMGDD_TRY(build_seg(L.asp, fr, fr, fo, ioff, ooff, d_om_idx.p, d_om_idx.p, s));
+  }
   // RAS-T: x(Omega_i) += W_i^T s(omega_i)
   for (int i = 0; i < nagg; ++i) std::swap(nr[i], nc[i]);
   AMGDD_TRY(build_seg(L.rast, nr, nc, moff, ioff, ooff, d_om_idx.p, d_om_idx.p, s));
@@ -1988,8 +2026,22 @@ static int tune_tail(amgdd_hierarchy& h) {
 }
 
 // z = B r on FP64 PCG vectors, in the hierarchy's precision.
+// z = M_2^{-1} r, the additive two-level method (FP64): additive Schwarz
+// z = sum_i R_i^T A_i^{-1} R_i r (scatter-add), plus P A_1^{-1} P^T r with
+// the exact coarsest solve of level 1.
+static int precondition_additive(amgdd_hierarchy& h, const double* r, double* z, const int* skip, cudaStream_t s) {
+  Level& L0 = *h.lv[0];
+  Level& L1 = *h.lv[1];
+  AMGDD_CUDA(cudaMemsetAsync(z, 0, L0.n * sizeof(double), s));
+  AMGDD_TRY(launch_seg(L0.asp, L0.Wf64.p, false, r, z, false, SEG_ATOMIC_ADD, skip, s, nullptr, nullptr, L0.Wft64.p));
+  AMGDD_TRY(launch_seg(L0.restr, L0.Zt64.p, false, r, L1.r64.p, false, SEG_STORE, skip, s, nullptr, nullptr, L0.Z64.p));
+  AMGDD_TRY(coarse_solve(h, L1, L1.r64.p, L1.x64.p, L1.s64.p, skip, s));
+  return launch_seg(L0.prol, L0.Z64.p, false, L1.x64.p, z, false, SEG_ADD, skip, s, nullptr, nullptr, L0.Zt64.p);
+}
+
 static int precondition(amgdd_hierarchy& h, const double* r, double* z, const int* skip, cudaStream_t s) {
   Level& L0 = *h.lv[0];
+  if (h.prm.cycle == 1) return precondition_additive(h, r, z, skip, s);
   if (h.precision == AMGDD_MIXED32) {
     AMGDD_TRY(launch_cast(r, false, L0.r32.p, true, L0.n, skip, s));
     AMGDD_TRY(vcycle(h, 0, true, L0.r32.p, L0.x32.p, skip, s));
@@ -2018,7 +2070,9 @@ static int pcg_iteration(amgdd_hierarchy& h, cudaStream_t s, cudaGraphConditiona
     // product and taking the scalar step in its last CTA
     AMGDD_TRY(launch_cg_ap(L0, st, h.p.p, h.q.p, h.partials.p, s));
     AMGDD_TRY(launch_cg_xr(st, h.x.p, h.r.p, flex ? L0.r32.p : nullptr, h.p.p, h.q.p, n, h.partials.p, s));
-    if (flex)
+    if (h.prm.cycle == 1)
+      AMGDD_TRY(precondition_additive(h, h.r.p, h.z.p, done, s));
+    else if (flex)
       AMGDD_TRY(vcycle(h, 0, true, L0.r32.p, L0.x32.p, done, s));
     else
       AMGDD_TRY(vcycle(h, 0, false, h.r.p, h.z.p, done, s));
@@ -2637,7 +2691,8 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   amgdd_params prm = params ? *params : amgdd_params_default();
   if (prm.L_max < 1 || prm.n_cmin < 1 || prm.n_cmin > 8 || prm.max_iter < 1 || overlap < 1 ||
       (prm.precision != AMGDD_FP64 && prm.precision != AMGDD_MIXED32) || prm.check_every < 1 || prm.n_coarse < 1 ||
-      prm.coarse_overlap < 0) {
+      prm.coarse_overlap < 0 || prm.cycle < 0 || prm.cycle > 1 ||
+      (prm.cycle == 1 && prm.precision != AMGDD_FP64)) {
     set_error("amgdd_setup: invalid parameters");
     return AMGDD_ERR_INVALID_ARG;
   }
@@ -2860,6 +2915,11 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     ++lvl;
   }
   H->lv.back()->d_H.release();
+  if (prm.cycle == 1 && H->lv.size() != 2) {
+    set_error("amgdd_setup: the additive two-level method needs exactly two levels (got %zu; raise n_coarse or set "
+              "L_max = 2)", H->lv.size());
+    return AMGDD_ERR_INVALID_ARG;
+  }
   for (int i = 0; i < 16; ++i) {  // the coarsest level's phases
     H->phase_ms[i] += g_timer.acc[i];
     if (g_timer.name[i]) H->phase_name[i] = g_timer.name[i];
@@ -2917,7 +2977,7 @@ int amgdd_solve(amgdd_hierarchy* h, const double* b, int nrhs, double tol, doubl
     AMGDD_CUDA(cudaStreamWaitEvent(s, h->join[0], 0));
     const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
     int first_bad = AMGDD_OK;
-    if (nrhs > 1 && h->prm.use_graph && h->lv[0]->Aw64.p != nullptr) {
+    if (nrhs > 1 && h->prm.use_graph && h->lv[0]->Aw64.p != nullptr && h->prm.cycle == 0) {
       for (int j0 = 0; j0 < nrhs; j0 += kMaxRhs) {
         const int g = std::min(kMaxRhs, nrhs - j0);
         const int K = g <= 2 ? 2 : (g <= 4 ? 4 : 8);
@@ -2962,6 +3022,10 @@ int amgdd_set_precision(amgdd_hierarchy* h, int precision) {
     set_error("amgdd_set_precision: invalid argument");
     return AMGDD_ERR_INVALID_ARG;
   }
+  if (h->prm.cycle == 1 && precision != AMGDD_FP64) {
+    set_error("amgdd_set_precision: the additive two-level method runs in FP64 only");
+    return AMGDD_ERR_INVALID_ARG;
+  }
   h->precision = precision;
   h->mixed_stalled = false;  // give the FP32 cycle a fresh chance
   return AMGDD_OK;
@@ -2977,6 +3041,14 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
   cudaStream_t s = (cudaStream_t)stream;
   Level& L = *h->lv[level];
   const bool f32 = h->precision == AMGDD_MIXED32;
+  if (op == AMGDD_OP_M2) {
+    if (h->prm.cycle != 1 || level != 0) {
+      set_error("amgdd_apply: M2 needs level 0 of a hierarchy built with cycle = 1");
+      return AMGDD_ERR_INVALID_ARG;
+    }
+    AMGDD_TRY(precondition_additive(*h, x, y, nullptr, s));
+    return take_err_word(*h, s);
+  }
   const bool coarsest_op = op == AMGDD_OP_COARSE || (op == AMGDD_OP_VCYCLE && L.coarsest);
   if (coarsest_op) {
     if (!L.coarsest) {
@@ -3085,6 +3157,14 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
   cudaStream_t s = (cudaStream_t)stream;
   Level& L = *h->lv[level];
   const bool f32 = h->precision == AMGDD_MIXED32;
+  if (op == AMGDD_OP_M2) {
+    if (h->prm.cycle != 1 || level != 0) {
+      set_error("amgdd_apply: M2 needs level 0 of a hierarchy built with cycle = 1");
+      return AMGDD_ERR_INVALID_ARG;
+    }
+    AMGDD_TRY(precondition_additive(*h, x, y, nullptr, s));
+    return take_err_word(*h, s);
+  }
   const bool coarsest_op = op == AMGDD_OP_COARSE || (op == AMGDD_OP_VCYCLE && L.coarsest);
   if (coarsest_op) {
     if (!L.coarsest) {

@@ -230,6 +230,13 @@ struct Level {
   // the Omega lists (rast_det), then x_j += the y entries of node j in
   // ascending position order (det_ptr / det_pos: positions p with
   // om_idx[p] = j); no atomics
+  // additive Schwarz (cycle = 1, level 0): every row of A_i^{-1} (|Omega_i|^2
+  // per aggregate, row-major, and its block transpose), applied by asp as
+  // x(Omega_i) += A_i^{-1} r(Omega_i)
+  SegPlan asp;
+  DBuf<double> Wf64, Wft64;
+  DBuf<float> Wf32, Wft32;
+  std::vector<int64_t> wf_off;
   SegPlan rast_det;
   DBuf<int32_t> d_pos_iota;  // identity over the positions of the Omega lists
   DBuf<int64_t> det_ptr;
