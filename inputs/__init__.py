@@ -17,3 +17,4 @@ from .q1 import (  # noqa: F401
     config_problem,
 )
 from .q1_3d import q1_3d, field_sqrtK, strength_graph, greedy_aggregates  # noqa: F401
+from .fd import fd_2d, fd_block_aggregates  # noqa: F401

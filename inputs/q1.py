@@ -173,6 +173,12 @@ CONFIGS = {
     # the same structure on 512 x 512 cells
     "q1_512_circ": dict(N=512, field="circ", theta=0.0, eps=1e-6, d1=1e-8, bs=8, overlap=2, coarse_overlap=1,
                         seed=3, c_min=(4, 5), n_coarse=2000, thresh=0.1, nrhs=1),
+    # the paper's own finite-difference discretization (Section 4.1): 500 x 500
+    # unknowns, theta = pi/6, 4x4 aggregates, the threshold from kappa = 50
+    "fd_500_rot": dict(N=500, field="fd", theta=math.pi / 6, eps=1e-4, d1=0.0, bs=4, overlap=1, seed=6,
+                       c_min=(2, 3, 4), n_coarse=2000, thresh=0.1, kappa=50.0, nrhs=1),
+    "fd_64_rot": dict(N=64, field="fd", theta=math.pi / 6, eps=1e-4, d1=0.0, bs=4, overlap=1, seed=6,
+                      c_min=(2, 3, 4), n_coarse=2000, thresh=0.1, kappa=50.0, nrhs=1),
     # 3D: 128^3 hexahedral cells, K = eps I + (1 - eps) b b^T with b a smooth
     # seeded unit field, greedy strength-graph aggregates, 8 right-hand sides
     "q1_3d_128": dict(N=128, dim=3, field="fourier", theta=0.0, eps=1e-4, d1=0.0, bs=0, overlap=1, seed=4,
@@ -202,6 +208,12 @@ def config_problem(name: str | None = None, **over) -> tuple[Q1Problem, dict]:
                      desc=dict(name=name, dim=3, field="fourier", eps=cfg["eps"]))
         ip, ix = strength_graph(prob, float(cfg.get("soc", 0.03)))
         prob.agg = greedy_aggregates(ip, ix, prob.n)
+        return prob, cfg
+    if cfg["field"] == "fd":
+        from .fd import fd_2d, fd_block_aggregates
+
+        prob = fd_2d(N, float(cfg["theta"]), float(cfg["eps"]), agg=fd_block_aggregates(N, int(cfg["bs"])),
+                     desc=dict(name=name, field="fd", theta=cfg["theta"], eps=cfg["eps"], bs=cfg["bs"]))
         return prob, cfg
     if cfg["field"] == "rot":
         sk = rotated_sqrtK(float(cfg["theta"]), float(cfg["eps"]))
