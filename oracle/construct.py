@@ -37,6 +37,8 @@ import scipy.sparse as sp
 from .structure import (
     cleanup_aggregates,
     multiplicity_and_nz,
+    subdomain_colouring,
+    kappa_threshold,
     overlapping_subdomains,
     row_groups_from_csr,
     structural_adjacency,
@@ -67,6 +69,9 @@ class Level:
     Atil: list = field(default_factory=list)  # kept only when keep_local
     S: list = field(default_factory=list)  # kept only when keep_local
     Ai: list = field(default_factory=list)  # kept only when keep_local
+    thresh: float = 0.1  # eigenvalue threshold used on this level
+    n_color: int = 0  # with kappa: colours of the subdomain colouring
+    n_mult: int = 0  # with kappa: largest row multiplicity M(j)
 
 
 @dataclass
@@ -203,8 +208,14 @@ def _next_groups(level):
 
 
 def setup(rowptr, col, val, n, D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=2000, L_max=10,
-          thresh=0.1, schur_rtol=1e-12, keep_local=False, coarse_overlap=0):
+          thresh=0.1, schur_rtol=1e-12, keep_local=False, coarse_overlap=0, kappa=None):
     """Build the multilevel hierarchy {A_l, G_l, P_l} of Algorithm 1.
+
+    With `kappa` given, each level's eigenvalue threshold is derived from it
+    (Section 3.4): max{0.1, (kappa - n_color) / (n_color n_multiplicity)}, with
+    n_color the colours of `subdomain_colouring` and n_multiplicity the largest
+    row multiplicity M(j) of the level's G; otherwise `thresh` holds on every
+    level.
 
     `overlap` hops of neighbours form Omega_i on level 0; coarse levels use
     `coarse_overlap` hops (0: the same as level 0).  Algorithm 1 itself adds
@@ -224,6 +235,12 @@ def setup(rowptr, col, val, n, D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=200
         ov = overlap if lvl == 0 or coarse_overlap <= 0 else coarse_overlap
         cur.omega, cur.gamma, cur.Omega = overlapping_subdomains(cur.agg, cur.nagg, adj, ov)
         cur.M, cur.nz, cur.touched = multiplicity_and_nz(cur.sups, cur.agg, cur.nagg)
+        if kappa is not None:
+            _, cur.n_color = subdomain_colouring(cur.Omega, adj, cur.n)
+            cur.n_mult = int(cur.M.max()) if cur.M.shape[0] else 1
+            cur.thresh = kappa_threshold(float(kappa), cur.n_color, cur.n_mult)
+        else:
+            cur.thresh = thresh
         c = c_min[min(lvl, len(c_min) - 1)]
         ks = np.zeros(cur.nagg, dtype=np.int64)
         Acsr = cur.A
@@ -235,7 +252,7 @@ def setup(rowptr, col, val, n, D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=200
             cur.chol.append(L)
             At = local_splitting(Om, cur.nz[i], cur.sups, cur.grams, cur.M)
             S = schur_complement(At, no, schur_rtol)
-            mu, Z = local_gep(S, Ai[:no, :no], max(1, no // c), thresh)
+            mu, Z = local_gep(S, Ai[:no, :no], max(1, no // c), cur.thresh)
             cur.mu.append(mu)
             cur.Z.append(Z)
             ks[i] = Z.shape[1]
@@ -263,6 +280,6 @@ def setup(rowptr, col, val, n, D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=200
     AL = cur.A.toarray()
     coarse = np.linalg.cholesky(AL)
     params = dict(overlap=overlap, coarse_overlap=coarse_overlap, c_min=tuple(c_min), n_coarse=n_coarse, L_max=L_max,
-                  thresh=thresh,
+                  thresh=thresh, kappa=kappa,
                   schur_rtol=schur_rtol)
     return Hierarchy(levels=levels, coarse_chol=coarse, params=params)

@@ -168,6 +168,39 @@ def multiplicity_and_nz(sups, agg, nagg):
     return M, nz, touched
 
 
+def subdomain_colouring(Omega, adj, n):
+    """Greedy colouring of the overlapping subdomains Omega_i (Section 3.4's n_color).
+
+    Reading: Omega_i and Omega_j need distinct colours when A couples them, i.e.
+    A(Omega_i, Omega_j) has a structural nonzero (the A-orthogonality of
+    same-coloured subdomains in the cited bound); sharing a node is such a
+    coupling since A's diagonal is nonzero.  Subdomains are coloured in
+    ascending index, each with the smallest colour no earlier coupled subdomain
+    holds.  Returns (colour per subdomain, number of colours)."""
+    nagg = len(Omega)
+    if nagg == 0:
+        return np.zeros(0, dtype=np.int64), 0
+    rows = np.concatenate([np.full(o.shape[0], i, dtype=np.int64) for i, o in enumerate(Omega)])
+    cols = np.concatenate(Omega).astype(np.int64)
+    T = sp.csr_matrix((np.ones(rows.shape[0], dtype=np.int32), (rows, cols)), shape=(nagg, n))
+    C = (T @ adj.astype(np.int32) @ T.T).tocsr()
+    colour = np.full(nagg, -1, dtype=np.int64)
+    for i in range(nagg):
+        nb = C.indices[C.indptr[i]:C.indptr[i + 1]]
+        used = {int(colour[j]) for j in nb if j < i}
+        c = 0
+        while c in used:
+            c += 1
+        colour[i] = c
+    return colour, int(colour.max()) + 1
+
+
+def kappa_threshold(kappa, n_color, n_mult):
+    """Local eigenvalue threshold from a target condition number (Section 3.4):
+    max{0.1, (kappa - n_color) / (n_color n_multiplicity)}."""
+    return max(0.1, (kappa - n_color) / (n_color * n_mult))
+
+
 def vanek_aggregation(adj_nodiag):
     """Standard aggregation with every edge strong (Section 2.1).
 

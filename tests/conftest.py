@@ -10,6 +10,9 @@ import pytest  # noqa: E402
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+HERE = os.path.dirname(os.path.abspath(__file__))  # test modules share helpers by plain import
+if HERE not in sys.path:
+    sys.path.insert(1, HERE)
 
 
 def pytest_configure(config):

@@ -1,0 +1,98 @@
+"""Pins of the kappa-derived eigenvalue threshold (Section 3.4).
+
+* the colouring is proper (subdomains coupled by A differ) and greedy (a subdomain of colour c has, for
+  every c' < c, an earlier coupled subdomain of colour c'), against a brute-force coupling test on the
+  dense A;
+* the 2D finite-difference workload with 4x4 aggregates: the subdomain graph is the king's graph of the
+  blocks (the stencil's (i+1, j)-(i, j+1) coupling reaches the diagonal blocks, two blocks apart nothing
+  couples), which needs 4 colours; a row of G spans 3 nodes that can sit in 3 blocks, so n_multiplicity = 3
+  and thresh = (50 - 4) / (4 * 3);
+* one aggregate: n_color = n_multiplicity = 1, thresh = kappa - 1;
+* the 0.1 floor binds when kappa <= n_color;
+* with kappa, setup keeps exactly the eigenpairs with lambda > thresh (below the cap).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.structure import kappa_threshold, structural_adjacency, subdomain_colouring
+from oracle.construct import row_groups_from_csr
+from oracle.structure import cleanup_aggregates, overlapping_subdomains
+from inputs import fd_2d, fd_block_aggregates, q1_2d, rotated_sqrtK, block_aggregates_2d
+
+
+def _subdomains(p, overlap=1):
+    sups, _ = row_groups_from_csr(p.rowptr, p.col, p.val, p.n, p.D1)
+    adj = structural_adjacency(sups, p.n)
+    agg, nagg = cleanup_aggregates(p.agg, adj)
+    _, _, Om = overlapping_subdomains(agg, nagg, adj, overlap)
+    return Om, adj
+
+
+def _dense_coupled(p, Om):
+    Gs = np.zeros((p.m, p.n), dtype=bool)  # structural: every listed entry counts
+    for r in range(p.m):
+        Gs[r, p.col[p.rowptr[r]:p.rowptr[r + 1]]] = True
+    Ad = (Gs.T.astype(int) @ Gs.astype(int) + np.eye(p.n, dtype=int)) > 0
+    k = len(Om)
+    C = np.zeros((k, k), dtype=bool)
+    for i in range(k):
+        for j in range(k):
+            C[i, j] = Ad[np.ix_(Om[i], Om[j])].any()
+    return C
+
+
+@pytest.mark.parametrize("make", [lambda: fd_2d(13, 0.5, 1e-3, agg=fd_block_aggregates(13, 3)),
+                                  lambda: q1_2d(12, rotated_sqrtK(0.4, 1e-3), agg=block_aggregates_2d(12, 3))])
+def test_colouring_is_proper_and_greedy(make):
+    p = make()
+    Om, adj = _subdomains(p)
+    col, nc = subdomain_colouring(Om, adj, p.n)
+    C = _dense_coupled(p, Om)
+    assert nc == col.max() + 1
+    for i in range(len(Om)):
+        for j in range(len(Om)):
+            if i != j and C[i, j]:
+                assert col[i] != col[j]
+        for c in range(col[i]):
+            assert any(C[i, j] and col[j] == c for j in range(i))
+
+
+def test_fd_blocks_need_four_colours_and_multiplicity_three():
+    N = 16
+    p = fd_2d(N, math.pi / 6, 1e-4, agg=fd_block_aggregates(N, 4))
+    h = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, overlap=1, c_min=(2,), n_coarse=1, L_max=2,
+                     kappa=50.0)
+    L0 = h.levels[0]
+    assert (L0.n_color, L0.n_mult) == (4, 3)
+    assert L0.thresh == (50.0 - 4) / 12
+
+
+def test_single_aggregate():
+    N = 6
+    p = fd_2d(N, 0.3, 1e-2, agg=fd_block_aggregates(N, N))
+    h = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, overlap=1, c_min=(2,), n_coarse=1, L_max=2,
+                     kappa=20.0)
+    L0 = h.levels[0]
+    assert (L0.n_color, L0.n_mult, L0.thresh) == (1, 1, 19.0)
+
+
+def test_floor():
+    assert kappa_threshold(3.0, 4, 3) == 0.1
+    assert kappa_threshold(4.0, 4, 3) == 0.1
+    assert kappa_threshold(50.0, 5, 9) == 1.0
+
+
+def test_selection_follows_derived_threshold():
+    N = 16
+    p = fd_2d(N, math.pi / 6, 1e-4, agg=fd_block_aggregates(N, 4))
+    h = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, overlap=1, c_min=(2,), n_coarse=1, L_max=2,
+                     kappa=50.0)
+    L0 = h.levels[0]
+    for i in range(L0.nagg):
+        mu = L0.mu[i]
+        lam = np.where(mu > 0, 1.0 / np.where(mu > 0, mu, 1.0), np.inf)
+        want = min(int(np.sum(lam > L0.thresh)), max(1, L0.omega[i].shape[0] // 2))
+        assert L0.Z[i].shape[1] == want
