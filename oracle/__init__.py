@@ -47,6 +47,9 @@ from .structure import (  # noqa: F401
     overlapping_subdomains,
     multiplicity_and_nz,
     vanek_aggregation,
+    standard_aggregation,
+    subdomain_colouring,
+    kappa_threshold,
 )
 from .construct import Hierarchy, Level, setup, local_splitting, schur_complement, local_gep  # noqa: F401
 from .cycle import ras, rast, vcycle, pcg, apply_A, metrics, additive_schwarz, two_level_additive  # noqa: F401

@@ -168,6 +168,32 @@ def multiplicity_and_nz(sups, agg, nagg):
     return M, nz, touched
 
 
+def standard_aggregation(sups, n, passes=1):
+    """Level-0 aggregates from the graph of A itself, no strength of connection
+    (Section 3.3: the standard routine on the matrix entries), repeated
+    `passes` times on the aggregates (aggregating aggregates): T_1 from the
+    graph of A, T_2 from the graph of T_1^T A T_1, and so on; the aggregation
+    matrix is T_1 T_2 ...  Returns (agg, nagg) with ids in creation order of
+    the last pass."""
+    if passes < 1:
+        raise ValueError("passes must be >= 1")
+    adj = structural_adjacency(sups, n).astype(np.int32)
+    off = adj.copy()
+    off.setdiag(0)
+    off.eliminate_zeros()
+    off.sort_indices()
+    agg, nagg = vanek_aggregation(off)
+    for _ in range(passes - 1):
+        T = sp.csr_matrix((np.ones(n, dtype=np.int32), (np.arange(n), agg)), shape=(n, nagg))
+        C = (T.T @ adj @ T).tocsr()
+        C.setdiag(0)
+        C.eliminate_zeros()
+        C.sort_indices()
+        bagg, nagg = vanek_aggregation(C)
+        agg = bagg[agg]
+    return agg.astype(np.int64), int(nagg)
+
+
 def subdomain_colouring(Omega, adj, n):
     """Greedy colouring of the overlapping subdomains Omega_i (Section 3.4's n_color).
 
