@@ -69,6 +69,9 @@ def parse_args():
     ap.add_argument("--tune-cache", default=None,
                     help="file of setup-time kernel choices: read if present, written after tuning "
                          "(profiling runs replay the choices of a plain run)")
+    ap.add_argument("--ls-study", choices=("eps", "size", "angle"), default=None,
+                    help="Section 4.1's finite-difference studies of the LS variants (FP64 iterations per digit, "
+                         "convergence factor, operator complexity) over eps, grid size or angle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="setup + a few solves, no timing line")
     ap.add_argument("--oracle-solve", default=None, help=argparse.SUPPRESS)
@@ -160,6 +163,13 @@ class ClockSampler:
 
 
 def workload_desc(cfg):
+    if cfg.get("field") == "fd":
+        return (f"{cfg['N']}x{cfg['N']} finite-difference unknowns (G = B^T grad^+, Dirichlet), "
+                f"theta={cfg['theta']:.6f}, eps={cfg['eps']:g}, "
+                + (f"{cfg['bs']}x{cfg['bs']} aggregates, " if cfg['bs'] else
+                   f"standard aggregation ({cfg.get('agg_passes', 1)} pass), ") +
+                f"overlap {cfg['overlap']}, LS_{{{','.join(str(c) for c in cfg['c_min'])}}}, "
+                f"thresh from kappa={cfg['kappa']:g}, n_coarse {cfg['n_coarse']}, 1 RHS, tol 1e-8")
     if cfg.get("dim", 2) == 3:
         return (f"{cfg['N']}^3 Q1 hexahedral cells ({(cfg['N'] - 1) ** 3:,} unknowns), K = eps I + (1-eps) b b^T with "
                 f"b a smooth seeded Fourier field, eps={cfg['eps']:g}, greedy strength-graph aggregates "
@@ -180,11 +190,25 @@ def oracle_setup(prob, cfg):
     import oracle
 
     t0 = time.time()
-    ho = oracle.setup(prob.rowptr, prob.col, prob.val, prob.n, prob.D1, prob.agg, overlap=cfg["overlap"],
+    agg = prob.agg
+    if agg is None:  # the oracle's own standard aggregation (Section 3.3)
+        sups, _ = oracle.construct.row_groups_from_csr(prob.rowptr, prob.col, prob.val, prob.n, prob.D1)
+        agg, _ = oracle.standard_aggregation(sups, prob.n, cfg.get("agg_passes", 1))
+    ho = oracle.setup(prob.rowptr, prob.col, prob.val, prob.n, prob.D1, agg, overlap=cfg["overlap"],
                       c_min=cfg["c_min"], n_coarse=cfg["n_coarse"], thresh=cfg["thresh"],
-                      coarse_overlap=cfg.get("coarse_overlap", 0))
+                      kappa=cfg.get("kappa") or None, coarse_overlap=cfg.get("coarse_overlap", 0))
     setup_s = time.time() - t0
     return ho, setup_s
+
+
+def convergence(info):
+    """Average convergence factor rho = (||r_k|| / ||r_0||)^(1/k) of an FP64 solve and the iterations per
+    tenfold residual reduction, log(0.1) / log(rho) (the measure of Section 4.1's studies)."""
+    k, rr = info["iters"], info["relres"]
+    if k < 1 or not rr > 0:
+        return {"rho_fp64": None, "iters_per_digit": None}
+    rho = rr ** (1.0 / k)
+    return {"rho_fp64": round(rho, 4), "iters_per_digit": round(math.log(0.1) / math.log(rho), 3) if rho < 1 else None}
 
 
 def cpu_threads():
@@ -372,7 +396,7 @@ def run_ours(args):
                          "(FP64)", "impl": "ours", "workload": workload_desc(cfg) + ", L_max 2"}
         for label, cyc in (("multiplicative", 0), ("additive", 1)):
             Hc = amg.Hierarchy.from_problem(prob, overlap=cfg["overlap"], c_min=cfg["c_min"],
-                                            n_coarse=cfg["n_coarse"], thresh=cfg["thresh"], L_max=2, cycle=cyc)
+                                            n_coarse=cfg["n_coarse"], thresh=cfg["thresh"], kappa=cfg.get("kappa", 0.0), agg_passes=cfg.get("agg_passes", 1), L_max=2, cycle=cyc)
             for _ in range(args.warmup):
                 Hc.solve(b, tol=1e-8)
             torch.cuda.synchronize()
@@ -400,7 +424,7 @@ def run_ours(args):
                 prob, cfg = config_problem(args.workload, eps=eps, theta=theta)
                 t0 = time.time()
                 Hs = amg.Hierarchy.from_problem(prob, overlap=cfg["overlap"], c_min=cfg["c_min"],
-                                                n_coarse=cfg["n_coarse"], thresh=cfg["thresh"],
+                                                n_coarse=cfg["n_coarse"], thresh=cfg["thresh"], kappa=cfg.get("kappa", 0.0), agg_passes=cfg.get("agg_passes", 1),
                                                 coarse_overlap=cfg.get("coarse_overlap", 0))
                 torch.cuda.synchronize()
                 row = {"eps": eps, "theta": round(theta, 6), "setup_s": round(time.time() - t0, 3),
@@ -431,6 +455,43 @@ def run_ours(args):
                               "workload": args.workload, "points": rows}), flush=True)
         return
 
+    if args.ls_study:
+        # Section 4.1: theta = pi/6, eps from 1 to 1e-7 on 500^2; eps = 1e-5 up to 1000^2; angles in (0, pi/2)
+        variants = {"LS_4": (4,), "LS_3,4": (3, 4), "LS_2,3": (2, 3), "LS_3": (3,), "LS_2,3,4": (2, 3, 4)}
+        if args.ls_study == "eps":
+            points = [dict(eps=10.0 ** -k) for k in range(8)]
+        elif args.ls_study == "size":
+            points = [dict(eps=1e-5, N=N) for N in (125, 250, 500, 1000)]
+        else:
+            points = [dict(eps=1e-5, theta=math.pi / 2 * j / 8) for j in range(1, 8)]
+            variants = {"LS_2,3,4": (2, 3, 4)}
+        rows = []
+        for pt in points:
+            for vname, cm in variants.items():
+                prob, cfg = config_problem("fd_500_rot", c_min=cm, **pt)
+                t0 = time.time()
+                Hs = amg.Hierarchy.from_problem(prob, overlap=cfg["overlap"], c_min=cm, n_coarse=cfg["n_coarse"],
+                                                thresh=cfg["thresh"], kappa=cfg["kappa"],
+                                                agg_passes=cfg.get("agg_passes", 1))
+                torch.cuda.synchronize()
+                setup_s = time.time() - t0
+                st = Hs.stats()
+                b = torch.from_numpy(seeded_rhs(prob.n, 1, cfg["seed"])[:, 0]).cuda()
+                _, inf = Hs.solve(b, tol=1e-8)
+                row = {"variant": vname, **{k: (round(v, 6) if isinstance(v, float) else v) for k, v in pt.items()},
+                       "n": prob.n, "iters": inf[0]["iters"], "status": inf[0]["status"],
+                       "relres_true": inf[0]["relres_true"], **convergence(inf[0]),
+                       "op_complexity": round(st["op_complexity"], 3), "levels": st["n"],
+                       "thresh": [round(t, 4) for t in st["thresh"]], "setup_s": round(setup_s, 2)}
+                print(json.dumps(row), file=sys.stderr, flush=True)
+                rows.append(row)
+                del Hs
+        if rank == 0:
+            print(json.dumps({"metric": f"LS variants over {args.ls_study} (FP64 PCG to 1e-8)", "impl": "ours",
+                              "workload": workload_desc(config_problem("fd_500_rot")[1]), "points": rows}),
+                  flush=True)
+        return
+
     if args.serve:
         # the serving workload on its own: operators of 32^2 .. 512^2 cells,
         # 1..64 right-hand sides per request
@@ -451,7 +512,7 @@ def run_ours(args):
     n = prob.n
     t0 = time.time()
     H = amg.Hierarchy.from_problem(prob, overlap=cfg["overlap"], c_min=cfg["c_min"], n_coarse=cfg["n_coarse"],
-                                   thresh=cfg["thresh"], precision=amg.MIXED32, tune_cache=args.tune_cache,
+                                   thresh=cfg["thresh"], kappa=cfg.get("kappa", 0.0), agg_passes=cfg.get("agg_passes", 1), precision=amg.MIXED32, tune_cache=args.tune_cache,
                                    coarse_overlap=cfg.get("coarse_overlap", 0),
                                    tune={"timed": 1, "defaults": 0, "staged": 2, "shifted": 3, "lanes": 4}[args.tune_mode],
                                    deterministic=1 if args.deterministic else 0)
@@ -657,6 +718,7 @@ def run_ours(args):
         "iters": it_mix, "mixed_fp64_fallbacks": fallbacks, "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "setup_s": setup_s, "setup_phases_ms": {k: round(v, 1) for k, v in stats["setup_phases_ms"].items()},
         "levels": stats["n"], "op_complexity": stats["op_complexity"],
+        "convergence": convergence(inf_64[0]),
         "coarse_A": [c["form"] for c in stats["coarse_A"]],
         "persistent_tail_from": {"mixed": stats["tail"]["mixed"]["from"], "fp64": stats["tail"]["fp64"]["from"]},
         "dense_tail_from": {"mixed": stats["dense_tail"]["mixed"]["from"], "fp64": stats["dense_tail"]["fp64"]["from"]},

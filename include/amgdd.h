@@ -131,6 +131,18 @@ typedef struct {
                        /*   + sum_i R_i^T A_i^{-1} R_i (additive Schwarz, */
                        /*   Section 3.1 after Eq. cgc): needs a two-level */
                        /*   hierarchy (setup fails otherwise), runs FP64  */
+  double kappa;        /* target condition number (Section 3.4): > 0      */
+                       /*   replaces `thresh` on each level by            */
+                       /*   max{0.1, (kappa - n_color) /                  */
+                       /*   (n_color n_multiplicity)}, with n_color the   */
+                       /*   colours of a greedy colouring of the Omega_i  */
+                       /*   (ascending index; two subdomains coupled by A */
+                       /*   differ) and n_multiplicity the largest row    */
+                       /*   multiplicity M(j) of the level's G; 0         */
+                       /*   (default): `thresh` on every level            */
+  int agg_passes;      /* amgdd_setup with agg = NULL: level-0 aggregates */
+                       /*   by this many passes of standard aggregation   */
+                       /*   (see amgdd_aggregate); >= 1, default 1        */
 } amgdd_params;
 
 typedef struct amgdd_hierarchy amgdd_hierarchy; /* opaque, library-owned */
@@ -152,10 +164,30 @@ typedef struct {
   int iters_mixed;     /* iterations of the stalled FP32 attempt (0 if none) */
 } amgdd_info;
 
-/* Defaults: L_max 10, n_coarse 2000, thresh 0.1, c_min = {2,3,4} (LS_{2,3,4}),
+/* Defaults: L_max 10, n_coarse 2000, thresh 0.1 (kappa 0), c_min = {2,3,4} (LS_{2,3,4}),
  * FP64, max_iter 1000, schur_rtol 1e-12, graphs on, check_every 4, tune 1,
- * no tune cache.                                                          */
+ * no tune cache, agg_passes 1.                                            */
 amgdd_params amgdd_params_default(void);
+
+/* ---- level-0 aggregation (Section 3.3) ------------------------------- */
+/* Standard aggregation on the graph of A = D1 + G^T G, read from the matrix
+ * pattern itself with no strength-of-connection test (two unknowns are
+ * adjacent when a row of G holds both).  Pass 1 visits unknowns in ascending
+ * order and makes every unknown whose neighbours are all unaggregated a root
+ * of a new aggregate {root} u neighbours; pass 2 puts each remaining unknown
+ * in the aggregate of its lowest-index neighbour aggregated in pass 1;
+ * pass 3 starts a new aggregate at each unknown still left, with its
+ * unaggregated neighbours.  With passes > 1 the same routine aggregates the
+ * aggregates, on the graph of T^T A T (T the 0/1 aggregation matrix so far),
+ * and the result is the product T_1 T_2 ... (aggregating aggregates).
+ *   G      : CSR as above (only the pattern is read); host or device.
+ *   passes : >= 1.
+ *   agg    : receives n aggregate ids 0..nagg-1 (creation order of the last
+ *            pass); host or device buffer owned by the caller.
+ *   nagg   : receives the number of aggregates (may be NULL).
+ * Host computation (the passes are sequential by definition); `stream`
+ * orders the copies of device buffers.  Errors: INVALID_ARG.             */
+int amgdd_aggregate(const amgdd_csr* G, int passes, void* stream, int32_t* agg, int64_t* nagg);
 
 /* ---- setup: Algorithm 1 ---------------------------------------------- */
 /* Builds the hierarchy {G_l, P_l, smoothers} for A = D1 + G^T G.
@@ -165,7 +197,8 @@ amgdd_params amgdd_params_default(void);
  *              aggregates; -1 marks an unaggregated node, which joins the
  *              smallest aggregate id among its neighbours in the graph of A
  *              (Section 3.3); ids are relabelled 0..nagg-1 in ascending
- *              order, skipping unused ids.
+ *              order, skipping unused ids.  NULL: the library aggregates
+ *              with params->agg_passes passes (amgdd_aggregate).
  *   overlap  : number of graph hops added around each aggregate (>= 1)
  *              to form Omega_i = omega_i u Gamma_i (Section 2.2).
  *   params   : NULL for amgdd_params_default().

@@ -32,7 +32,8 @@ from .q1 import Q1Problem
 
 def fd_2d(N: int, theta: float, eps: float, D1: np.ndarray | None = None, agg: np.ndarray | None = None,
           desc: dict | None = None) -> Q1Problem:
-    """G = B^T grad^+ for an N x N grid of unknowns (2 rows per difference point)."""
+    """G = B^T grad^+ for an N x N grid of unknowns (2 rows per difference point).  With agg = None the
+    problem carries no level-0 aggregates: the solver chooses them."""
     if N < 2:
         raise ValueError("need at least 2 unknowns per axis")
     h = 1.0 / (N + 1)
@@ -60,12 +61,11 @@ def fd_2d(N: int, theta: float, eps: float, D1: np.ndarray | None = None, agg: n
                     vals.append(Bt[d, 0] * gx + Bt[d, 1] * gy)
                 rows_ptr.append(len(cols))
     rowptr = np.asarray(rows_ptr, dtype=np.int64)
-    if agg is None:
-        agg = np.zeros(n, dtype=np.int32)
     return Q1Problem(N=N, n=n, m=len(rowptr) - 1, rowptr=rowptr, col=np.asarray(cols, dtype=np.int32),
                      val=np.asarray(vals, dtype=np.float64),
                      D1=None if D1 is None else np.ascontiguousarray(D1, dtype=np.float64),
-                     agg=np.ascontiguousarray(agg, dtype=np.int32), desc=dict(desc or {}))
+                     agg=None if agg is None else np.ascontiguousarray(agg, dtype=np.int32),
+                     desc=dict(desc or {}))
 
 
 def fd_block_aggregates(N: int, bs: int) -> np.ndarray:

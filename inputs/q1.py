@@ -49,7 +49,7 @@ class Q1Problem:
     col: np.ndarray  # int32, nnz
     val: np.ndarray  # float64, nnz
     D1: np.ndarray | None  # float64, n, or None for D1 = 0
-    agg: np.ndarray  # int32, n, level-0 aggregate ids
+    agg: np.ndarray | None  # int32, n, level-0 aggregate ids; None: the solver aggregates
     desc: dict = field(default_factory=dict)
 
     @property
@@ -175,7 +175,10 @@ CONFIGS = {
                         seed=3, c_min=(4, 5), n_coarse=2000, thresh=0.1, nrhs=1),
     # the paper's own finite-difference discretization (Section 4.1): 500 x 500
     # unknowns, theta = pi/6, 4x4 aggregates, the threshold from kappa = 50
-    "fd_500_rot": dict(N=500, field="fd", theta=math.pi / 6, eps=1e-4, d1=0.0, bs=4, overlap=1, seed=6,
+    # (level-0 aggregates from one pass of standard aggregation, chosen by each solver itself)
+    "fd_500_rot": dict(N=500, field="fd", theta=math.pi / 6, eps=1e-4, d1=0.0, bs=0, agg_passes=1, overlap=1,
+                       seed=6, c_min=(2, 3, 4), n_coarse=2000, thresh=0.1, kappa=50.0, nrhs=1),
+    "fd_500_blk": dict(N=500, field="fd", theta=math.pi / 6, eps=1e-4, d1=0.0, bs=4, overlap=1, seed=6,
                        c_min=(2, 3, 4), n_coarse=2000, thresh=0.1, kappa=50.0, nrhs=1),
     "fd_64_rot": dict(N=64, field="fd", theta=math.pi / 6, eps=1e-4, d1=0.0, bs=4, overlap=1, seed=6,
                       c_min=(2, 3, 4), n_coarse=2000, thresh=0.1, kappa=50.0, nrhs=1),
@@ -212,7 +215,8 @@ def config_problem(name: str | None = None, **over) -> tuple[Q1Problem, dict]:
     if cfg["field"] == "fd":
         from .fd import fd_2d, fd_block_aggregates
 
-        prob = fd_2d(N, float(cfg["theta"]), float(cfg["eps"]), agg=fd_block_aggregates(N, int(cfg["bs"])),
+        prob = fd_2d(N, float(cfg["theta"]), float(cfg["eps"]),
+                     agg=fd_block_aggregates(N, int(cfg["bs"])) if cfg["bs"] else None,
                      desc=dict(name=name, field="fd", theta=cfg["theta"], eps=cfg["eps"], bs=cfg["bs"]))
         return prob, cfg
     if cfg["field"] == "rot":

@@ -34,7 +34,7 @@ EXPORTED = [
     "amgdd_kernel_launches", "amgdd_apply_noalloc", "amgdd_device_bytes", "amgdd_server_params_default",
     "amgdd_server_create", "amgdd_server_add_operator", "amgdd_server_submit", "amgdd_server_poll",
     "amgdd_server_stats", "amgdd_server_destroy", "amgdd_hierarchy_save", "amgdd_hierarchy_load",
-    "amgdd_selftest_wait_timeouts",
+    "amgdd_selftest_wait_timeouts", "amgdd_aggregate",
 ]
 AMGDD_PENDING = 1
 
@@ -56,7 +56,8 @@ class Params(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("tune", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
                 ("coarse_overlap", ctypes.c_int), ("coarse_refine", ctypes.c_int),
                 ("pdl", ctypes.c_int), ("dense_tail", ctypes.c_int), ("ell", ctypes.c_int),
-                ("deterministic", ctypes.c_int), ("cycle", ctypes.c_int)]
+                ("deterministic", ctypes.c_int), ("cycle", ctypes.c_int),
+                ("kappa", ctypes.c_double), ("agg_passes", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -101,6 +102,7 @@ def load_library(path: str = LIB_PATH):
     lib.amgdd_hierarchy_save.argtypes = [vp, ctypes.c_char_p]
     lib.amgdd_hierarchy_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
     lib.amgdd_selftest_wait_timeouts.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.amgdd_aggregate.argtypes = [ctypes.POINTER(Csr), i32, vp, vp, ctypes.POINTER(ctypes.c_int64)]
     lib.amgdd_free.restype = None
     lib.amgdd_status_string.argtypes = [i32]
     lib.amgdd_status_string.restype = ctypes.c_char_p
@@ -156,6 +158,22 @@ def _stream(stream):
     import torch
 
     return torch.cuda.current_stream().cuda_stream
+
+
+def aggregate(rowptr, col, n, passes=1, stream=None):
+    """Level-0 aggregates of A = D1 + G^T G by `passes` passes of standard
+    aggregation on its graph (amgdd_aggregate).  Host arrays in, a host
+    int32 array and the aggregate count out."""
+    lib = load_library()
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    dummy = np.zeros(1, dtype=np.float64)  # the pattern only: values are not read
+    csr = Csr(m=len(rp) - 1, n=int(n), nnz=int(len(cl)), rowptr=rp.ctypes.data, col=cl.ctypes.data,
+              val=dummy.ctypes.data, mem=HOST)
+    out = np.empty(int(n), dtype=np.int32)
+    na = ctypes.c_int64()
+    _check(lib.amgdd_aggregate(ctypes.byref(csr), int(passes), stream, out.ctypes.data, ctypes.byref(na)))
+    return out, int(na.value)
 
 
 def selftest_wait_timeouts(stream=None) -> tuple[int, int]:

@@ -1062,6 +1062,13 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
   std::vector<int64_t> tptr;
   std::vector<int32_t> tids, M;
   touched_aggregates(S, L.agg, tptr, tids, M);
+  L.thresh = h.prm.thresh;
+  if (h.prm.kappa > 0) {
+    L.n_color = colour_subdomains(L.om_ptr, L.om_idx, L.n, S, nptr, ngrp);
+    L.n_mult = 1;
+    for (int32_t v : M) L.n_mult = std::max(L.n_mult, (int)v);
+    L.thresh = kappa_threshold(h.prm.kappa, L.n_color, L.n_mult);
+  }
   const int c = h.prm.c_min[std::min(lvl, h.prm.n_cmin - 1)];
   if (g_timer.on)
     g_timer.add(0, "structure", std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count());
@@ -1251,7 +1258,7 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
     }
     {
       Phase ph(5, "eigen", s);
-      AMGDD_TRY(launch_gep(nb, max_no, B.m.p, B.no.p, B.a_off.p, Apool.p, Atpool.p, dcap.p, h.prm.thresh, dmuoff.p,
+      AMGDD_TRY(launch_gep(nb, max_no, B.m.p, B.no.p, B.a_off.p, Apool.p, Atpool.p, dcap.p, L.thresh, dmuoff.p,
                            L.mu.p, dzcap.p, Zcap.p, dk.p, gscr.p, dscr.p, s));
     }
     std::vector<int32_t> kb;
@@ -2660,6 +2667,7 @@ amgdd_params amgdd_params_default(void) {
   p.coarse_overlap = 0;
   p.coarse_refine = 1;
   p.pdl = 0;
+  p.agg_passes = 1;
   return p;
 }
 
@@ -2680,18 +2688,68 @@ const char* amgdd_status_string(int st) {
 
 const char* amgdd_last_error(void) { return g_last_error.c_str(); }
 
+// CSR pattern rules shared by setup and aggregation: rowptr[0] = 0,
+// rowptr[m] = nnz, nondecreasing, column ids strictly increasing in [0, n).
+static int check_pattern(const char* who, const std::vector<int64_t>& rowptr, const std::vector<int32_t>& col,
+                         int64_t m, int64_t n, int64_t nnz) {
+  if (rowptr[0] != 0 || rowptr[m] != nnz) {
+    set_error("%s: rowptr[0] must be 0 and rowptr[m] = nnz", who);
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  for (int64_t r = 0; r < m; ++r) {
+    if (rowptr[r + 1] < rowptr[r]) {
+      set_error("%s: rowptr decreases at row %lld", who, (long long)r);
+      return AMGDD_ERR_INVALID_ARG;
+    }
+    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+      if (col[e] < 0 || col[e] >= n || (e > rowptr[r] && col[e] <= col[e - 1])) {
+        set_error("%s: row %lld: column ids must increase strictly within [0, n)", who, (long long)r);
+        return AMGDD_ERR_INVALID_ARG;
+      }
+    }
+  }
+  return AMGDD_OK;
+}
+
+static bool bad_header(const amgdd_csr* G) {
+  return G->m < 0 || G->n < 1 || G->nnz < 0 || G->n >= (int64_t)1 << 31 || G->rowptr == nullptr ||
+         (G->nnz > 0 && (G->col == nullptr || G->val == nullptr));
+}
+
+// Level-0 aggregates by `passes` passes of standard aggregation on the graph
+// of A (rows of G as hyperedges; consecutive rows with one support counted once).
+static void aggregate_rows(const std::vector<int64_t>& rowptr, const std::vector<int32_t>& col, int64_t m,
+                           int64_t n, int passes, std::vector<int32_t>& agg, int64_t& nagg) {
+  Supports S;
+  S.ptr.assign(1, 0);
+  S.idx.reserve(col.size());
+  int64_t last = -1;
+  for (int64_t r = 0; r < m; ++r) {
+    const int64_t a = rowptr[r], b = rowptr[r + 1];
+    if (b == a) continue;
+    if (last >= 0 && rowptr[last + 1] - rowptr[last] == b - a &&
+        std::equal(col.begin() + a, col.begin() + b, col.begin() + rowptr[last]))
+      continue;
+    S.idx.insert(S.idx.end(), col.begin() + a, col.begin() + b);
+    S.ptr.push_back((int64_t)S.idx.size());
+    last = r;
+  }
+  standard_aggregation(n, S, passes, agg, nagg);
+}
+
 static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, int overlap,
                       const amgdd_params* params, void* stream, amgdd_hierarchy** out,
                       const std::vector<std::pair<std::string, double>>* preset = nullptr) {
-  if (out == nullptr || G == nullptr || agg == nullptr) {
-    set_error("amgdd_setup: G, agg and out must not be NULL");
+  if (out == nullptr || G == nullptr) {
+    set_error("amgdd_setup: G and out must not be NULL");
     return AMGDD_ERR_INVALID_ARG;
   }
   *out = nullptr;
   amgdd_params prm = params ? *params : amgdd_params_default();
   if (prm.L_max < 1 || prm.n_cmin < 1 || prm.n_cmin > 8 || prm.max_iter < 1 || overlap < 1 ||
       (prm.precision != AMGDD_FP64 && prm.precision != AMGDD_MIXED32) || prm.check_every < 1 || prm.n_coarse < 1 ||
-      prm.coarse_overlap < 0 || prm.cycle < 0 || prm.cycle > 1 ||
+      prm.coarse_overlap < 0 || prm.cycle < 0 || prm.cycle > 1 || !(prm.kappa >= 0) ||
+      (agg == nullptr && prm.agg_passes < 1) ||
       (prm.cycle == 1 && prm.precision != AMGDD_FP64)) {
     set_error("amgdd_setup: invalid parameters");
     return AMGDD_ERR_INVALID_ARG;
@@ -2702,8 +2760,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
       return AMGDD_ERR_INVALID_ARG;
     }
   const int64_t m = G->m, n = G->n, nnz = G->nnz;
-  if (m < 0 || n < 1 || nnz < 0 || n >= (int64_t)1 << 31 || G->rowptr == nullptr ||
-      (nnz > 0 && (G->col == nullptr || G->val == nullptr))) {
+  if (bad_header(G)) {
     set_error("amgdd_setup: bad CSR header (m=%lld n=%lld nnz=%lld)", (long long)m, (long long)n, (long long)nnz);
     return AMGDD_ERR_INVALID_ARG;
   }
@@ -2719,24 +2776,12 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   AMGDD_TRY(fetch_any(rowptr, G->rowptr, (size_t)m + 1, gdev, s));
   AMGDD_TRY(fetch_any(col, G->col, (size_t)nnz, gdev, s));
   AMGDD_TRY(fetch_any(val, G->val, (size_t)nnz, gdev, s));
-  AMGDD_TRY(fetch_any(aggh, agg, (size_t)n, is_device_ptr(agg), s));
+  if (agg) AMGDD_TRY(fetch_any(aggh, agg, (size_t)n, is_device_ptr(agg), s));
   if (D1) AMGDD_TRY(fetch_any(d1, D1, (size_t)n, is_device_ptr(D1), s));
-  // CSR validation
-  if (rowptr[0] != 0 || rowptr[m] != nnz) {
-    set_error("amgdd_setup: rowptr[0] must be 0 and rowptr[m] = nnz");
-    return AMGDD_ERR_INVALID_ARG;
-  }
-  for (int64_t r = 0; r < m; ++r) {
-    if (rowptr[r + 1] < rowptr[r]) {
-      set_error("amgdd_setup: rowptr decreases at row %lld", (long long)r);
-      return AMGDD_ERR_INVALID_ARG;
-    }
-    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
-      if (col[e] < 0 || col[e] >= n || (e > rowptr[r] && col[e] <= col[e - 1])) {
-        set_error("amgdd_setup: row %lld: column ids must increase strictly within [0, n)", (long long)r);
-        return AMGDD_ERR_INVALID_ARG;
-      }
-    }
+  AMGDD_TRY(check_pattern("amgdd_setup", rowptr, col, m, n, nnz));
+  if (!agg) {  // level-0 aggregates from the graph of A (Section 3.3)
+    int64_t na = 0;
+    aggregate_rows(rowptr, col, m, n, prm.agg_passes, aggh, na);
   }
   for (double v : val)
     if (!std::isfinite(v)) {
@@ -2780,7 +2825,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
                       std::to_string(prm.L_max) + "|c";
     for (int i = 0; i < prm.n_cmin; ++i) sig += std::to_string(prm.c_min[i]) + ",";
     char buf[64];
-    std::snprintf(buf, sizeof buf, "|t%.6g|d1%d", prm.thresh, D1 ? 1 : 0);
+    std::snprintf(buf, sizeof buf, "|t%.6g|k%.6g|d1%d", prm.thresh, prm.kappa, D1 ? 1 : 0);
     tctx.sig = sig + buf;
   }
   tctx.load();
@@ -2960,6 +3005,30 @@ int amgdd_setup(const amgdd_csr* G, const double* D1, const int32_t* agg, int ov
     set_error("amgdd_setup: unexpected exception");
     return AMGDD_ERR_INTERNAL;
   }
+}
+
+int amgdd_aggregate(const amgdd_csr* G, int passes, void* stream, int32_t* agg, int64_t* nagg) {
+  if (G == nullptr || agg == nullptr || passes < 1 || bad_header(G)) {
+    set_error("amgdd_aggregate: invalid argument");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool gdev = G->mem == AMGDD_DEVICE;
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> col, a;
+  AMGDD_TRY(fetch_any(rowptr, G->rowptr, (size_t)G->m + 1, gdev, s));
+  AMGDD_TRY(fetch_any(col, G->col, (size_t)G->nnz, gdev, s));
+  AMGDD_TRY(check_pattern("amgdd_aggregate", rowptr, col, G->m, G->n, G->nnz));
+  int64_t na = 0;
+  aggregate_rows(rowptr, col, G->m, G->n, passes, a, na);
+  if (is_device_ptr(agg)) {
+    AMGDD_CUDA(cudaMemcpyAsync(agg, a.data(), a.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    AMGDD_CUDA(cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(agg, a.data(), a.size() * sizeof(int32_t));
+  }
+  if (nagg) *nagg = na;
+  return AMGDD_OK;
 }
 
 int amgdd_solve(amgdd_hierarchy* h, const double* b, int nrhs, double tol, double* x, void* stream,
@@ -3446,6 +3515,16 @@ int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap) {
     amgdd_level_describe(h, (int)l, &d);
     s += (l ? ", " : "") + std::to_string(d.w_vals);
   }
+  s += "], \"thresh\": [";
+  for (size_t l = 0; l + 1 < h->lv.size(); ++l) {
+    char buf[40];
+    std::snprintf(buf, sizeof buf, "%s%.17g", l ? ", " : "", h->lv[l]->thresh);
+    s += buf;
+  }
+  s += "], \"n_color\": [";
+  for (size_t l = 0; l + 1 < h->lv.size(); ++l) s += (l ? ", " : "") + std::to_string(h->lv[l]->n_color);
+  s += "], \"n_mult\": [";
+  for (size_t l = 0; l + 1 < h->lv.size(); ++l) s += (l ? ", " : "") + std::to_string(h->lv[l]->n_mult);
   s += "], \"coarse_A\": [";
   for (size_t l = 0; l < h->lv.size(); ++l) {
     const Level& L = *h->lv[l];

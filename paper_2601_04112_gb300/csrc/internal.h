@@ -252,6 +252,9 @@ struct Level {
   DBuf<double> Aw64, AwT64;
   DBuf<float> Aw32, AwT32;
   double inv_err = 0.0;  // coarsest level: measured ||W A v - v|| / ||v||
+  double thresh = 0.0;   // eigenvalue threshold used on this level
+  int n_color = 0;       // kappa > 0: colours of the subdomain colouring
+  int n_mult = 0;        // kappa > 0: largest row multiplicity M(j)
   // dense tail: the V-cycle from this level to the coarsest as one n x n
   // matrix B (B = its action on the unit vectors), row-major with leading
   // dimension dld = n rounded up to 4 (zero columns); dplan applies it as

@@ -129,54 +129,158 @@ void touched_aggregates(const Supports& S, const std::vector<int32_t>& agg, std:
   }
 }
 
-void block_aggregation(int nb, const std::vector<int64_t>& tptr, const std::vector<int32_t>& tids,
-                       std::vector<int32_t>& bagg, int& nagg) {
-  std::vector<std::vector<int32_t>> nbr(nb);
-  const int64_t ng = (int64_t)tptr.size() - 1;
-  for (int64_t g = 0; g < ng; ++g)
-    for (int64_t p = tptr[g]; p < tptr[g + 1]; ++p)
-      for (int64_t q = tptr[g]; q < tptr[g + 1]; ++q)
-        if (tids[p] != tids[q]) nbr[tids[p]].push_back(tids[q]);
-  for (auto& v : nbr) {
-    std::sort(v.begin(), v.end());
-    v.erase(std::unique(v.begin(), v.end()), v.end());
+// Standard aggregation (Section 2.1 passes, every edge strong) on a graph
+// given by hyperedges: two vertices are adjacent when an edge holds both.
+void hyper_aggregation(int64_t nv, const std::vector<int64_t>& eptr, const std::vector<int32_t>& eidx,
+                       std::vector<int32_t>& agg, int64_t& nagg) {
+  // neighbour lists (sorted, no self) through vertex -> edge incidence
+  std::vector<int64_t> vptr(nv + 1, 0);
+  const int64_t ne = (int64_t)eptr.size() - 1;
+  for (int64_t e = 0; e < ne; ++e)
+    for (int64_t q = eptr[e]; q < eptr[e + 1]; ++q) vptr[eidx[q] + 1]++;
+  for (int64_t v = 0; v < nv; ++v) vptr[v + 1] += vptr[v];
+  std::vector<int64_t> ve(vptr[nv]);
+  {
+    std::vector<int64_t> fill(vptr.begin(), vptr.end() - 1);
+    for (int64_t e = 0; e < ne; ++e)
+      for (int64_t q = eptr[e]; q < eptr[e + 1]; ++q) ve[fill[eidx[q]]++] = e;
   }
-  bagg.assign(nb, -1);
-  int nxt = 0;
+  std::vector<int64_t> nptr(nv + 1, 0);
+  std::vector<int32_t> nbr;
+  std::vector<int64_t> stamp(nv, -1);
+  for (int64_t v = 0; v < nv; ++v) {
+    stamp[v] = v;
+    const size_t s0 = nbr.size();
+    for (int64_t k = vptr[v]; k < vptr[v + 1]; ++k) {
+      const int64_t e = ve[k];
+      for (int64_t q = eptr[e]; q < eptr[e + 1]; ++q) {
+        const int32_t u = eidx[q];
+        if (stamp[u] != v) {
+          stamp[u] = v;
+          nbr.push_back(u);
+        }
+      }
+    }
+    std::sort(nbr.begin() + s0, nbr.end());
+    nptr[v + 1] = (int64_t)nbr.size();
+  }
+  agg.assign(nv, -1);
+  int64_t nxt = 0;
   // pass 1: roots whose neighbours are all unaggregated
-  for (int j = 0; j < nb; ++j) {
-    if (bagg[j] >= 0) continue;
+  for (int64_t j = 0; j < nv; ++j) {
+    if (agg[j] >= 0) continue;
     bool free_all = true;
-    for (int32_t u : nbr[j])
-      if (bagg[u] >= 0) {
+    for (int64_t k = nptr[j]; k < nptr[j + 1]; ++k)
+      if (agg[nbr[k]] >= 0) {
         free_all = false;
         break;
       }
     if (free_all) {
-      bagg[j] = nxt;
-      for (int32_t u : nbr[j]) bagg[u] = nxt;
+      agg[j] = (int32_t)nxt;
+      for (int64_t k = nptr[j]; k < nptr[j + 1]; ++k) agg[nbr[k]] = (int32_t)nxt;
       ++nxt;
     }
   }
   // pass 2: join the lowest-index neighbour aggregated in pass 1
-  const std::vector<int32_t> after1(bagg);
-  for (int j = 0; j < nb; ++j) {
-    if (bagg[j] >= 0) continue;
-    for (int32_t u : nbr[j])
-      if (after1[u] >= 0) {
-        bagg[j] = after1[u];
+  const std::vector<int32_t> after1(agg);
+  for (int64_t j = 0; j < nv; ++j) {
+    if (agg[j] >= 0) continue;
+    for (int64_t k = nptr[j]; k < nptr[j + 1]; ++k)
+      if (after1[nbr[k]] >= 0) {
+        agg[j] = after1[nbr[k]];
         break;
       }
   }
   // pass 3: leftovers start aggregates with their unaggregated neighbours
-  for (int j = 0; j < nb; ++j) {
-    if (bagg[j] >= 0) continue;
-    bagg[j] = nxt;
-    for (int32_t u : nbr[j])
-      if (bagg[u] < 0) bagg[u] = nxt;
+  for (int64_t j = 0; j < nv; ++j) {
+    if (agg[j] >= 0) continue;
+    agg[j] = (int32_t)nxt;
+    for (int64_t k = nptr[j]; k < nptr[j + 1]; ++k)
+      if (agg[nbr[k]] < 0) agg[nbr[k]] = (int32_t)nxt;
     ++nxt;
   }
   nagg = nxt;
+}
+
+void block_aggregation(int nb, const std::vector<int64_t>& tptr, const std::vector<int32_t>& tids,
+                       std::vector<int32_t>& bagg, int& nagg) {
+  int64_t na = 0;
+  hyper_aggregation(nb, tptr, tids, bagg, na);
+  nagg = (int)na;
+}
+
+void standard_aggregation(int64_t n, const Supports& S, int passes, std::vector<int32_t>& agg, int64_t& nagg) {
+  hyper_aggregation(n, S.ptr, S.idx, agg, nagg);
+  std::vector<int64_t> tptr;
+  std::vector<int32_t> tids, bagg, seen;
+  for (int p = 1; p < passes; ++p) {
+    // hyperedges of the graph of T^T A T: the distinct aggregates each row touches
+    tptr.assign(1, 0);
+    tids.clear();
+    seen.assign(nagg, -1);
+    const int64_t ng = S.size();
+    for (int64_t g = 0; g < ng; ++g) {
+      for (int64_t q = S.ptr[g]; q < S.ptr[g + 1]; ++q) {
+        const int32_t a = agg[S.idx[q]];
+        if (seen[a] != (int32_t)g) {
+          seen[a] = (int32_t)g;
+          tids.push_back(a);
+        }
+      }
+      tptr.push_back((int64_t)tids.size());
+    }
+    int64_t nb = 0;
+    hyper_aggregation(nagg, tptr, tids, bagg, nb);
+    for (auto& a : agg) a = bagg[a];
+    nagg = nb;
+  }
+}
+
+int colour_subdomains(const std::vector<int64_t>& om_ptr, const std::vector<int32_t>& om_idx, int64_t n,
+                      const Supports& S, const std::vector<int64_t>& nptr, const std::vector<int32_t>& ngrp) {
+  const int64_t nagg = (int64_t)om_ptr.size() - 1;
+  if (nagg <= 0) return 0;
+  // node -> subdomains holding it
+  std::vector<int64_t> sptr(n + 1, 0);
+  for (int32_t v : om_idx) sptr[v + 1]++;
+  for (int64_t v = 0; v < n; ++v) sptr[v + 1] += sptr[v];
+  std::vector<int32_t> sidx(om_idx.size());
+  {
+    std::vector<int64_t> fill(sptr.begin(), sptr.end() - 1);
+    for (int64_t i = 0; i < nagg; ++i)
+      for (int64_t q = om_ptr[i]; q < om_ptr[i + 1]; ++q) sidx[fill[om_idx[q]]++] = (int32_t)i;
+  }
+  std::vector<int32_t> colour(nagg, -1);
+  std::vector<int64_t> vstamp(n, -1), cstamp;
+  int ncol = 0;
+  for (int64_t i = 0; i < nagg; ++i) {
+    auto visit = [&](int32_t v) {
+      if (vstamp[v] == i) return;
+      vstamp[v] = i;
+      for (int64_t e = sptr[v]; e < sptr[v + 1]; ++e) {
+        const int32_t j = sidx[e];
+        if (j < i) cstamp[colour[j]] = i;
+      }
+    };
+    cstamp.resize((size_t)ncol + 1, -1);
+    for (int64_t q = om_ptr[i]; q < om_ptr[i + 1]; ++q) {
+      const int32_t u = om_idx[q];
+      visit(u);
+      for (int64_t e = nptr[u]; e < nptr[u + 1]; ++e) {
+        const int32_t g = ngrp[e];
+        for (int64_t k = S.ptr[g]; k < S.ptr[g + 1]; ++k) visit(S.idx[k]);
+      }
+    }
+    int c = 0;
+    while (cstamp[c] == i) ++c;
+    colour[i] = c;
+    ncol = std::max(ncol, c + 1);
+  }
+  return ncol;
+}
+
+double kappa_threshold(double kappa, int n_color, int n_mult) {
+  return std::max(0.1, (kappa - n_color) / ((double)n_color * n_mult));
 }
 
 }  // namespace amgdd

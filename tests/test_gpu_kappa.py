@@ -1,0 +1,173 @@
+"""GPU parity of the kappa-derived threshold on the finite-difference workload (Sections 3.4, 4.1).
+
+The library colours the overlapping subdomains and takes the largest row multiplicity on every level on the
+host, derives thresh_l = max{0.1, (kappa - n_color) / (n_color n_multiplicity)} and selects the local
+eigenpairs with it.
+
+What is unique is compared exactly or to the Q1 parity tolerances; what is not is checked for validity.
+On the finite-difference G the coarse-level blocks A~_GG have genuine eigenvalues spread between 1e-13 and
+1e-8 of the largest.  The pseudo-inverse of Eq. gevp-S then depends on where its rank is cut, and a
+normal-equations (Gram) computation resolves eigenvalues near 1e-13 only to about 1e-3, so the coarse-level
+spectra of two correct implementations differ.  Up to the first such level ("gray level", found in the
+oracle): structure, n_color, n_multiplicity and thresh_l exactly, spectra and level-0 operators to the Q1
+tolerances.  From it on: the library's own hierarchy is valid (mu in [0, 1], k_i within its cap) and its PCG
+converges to the tolerance in a comparable number of iterations.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from inputs import fd_2d, fd_block_aggregates, seeded_rhs
+from test_gpu_parity import _apply, _check_spectra, _degenerate_cut, _rel
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # 48 x 48 unknowns, theta = pi/6, eps = 1e-4, 4x4 aggregates: three levels
+    "fd_48": dict(N=48, theta=math.pi / 6, eps=1e-4, bs=4, c_min=(2, 3, 4), n_coarse=100, kappa=50.0),
+    # ragged blocks (30 = 7 x 4 + 2 per axis), kappa small enough that the 0.1 floor binds on coarse levels
+    "fd_30_floor": dict(N=30, theta=0.9, eps=1e-3, bs=4, c_min=(2, 3), n_coarse=60, kappa=6.0),
+}
+
+
+@pytest.fixture(scope="module")
+def amg():
+    from paper_2601_04112_gb300 import build
+
+    build.build()
+    import paper_2601_04112_gb300 as amg
+
+    amg.load_library()
+    return amg
+
+
+def first_gray_level(ho, lo=1e-14, hi=1e-8):
+    """First level with a block A~_GG holding an eigenvalue in (lo, hi) x its largest (len(levels) - 1 if
+    none): where the pseudo-inverse of Eq. gevp-S stops being well posed in FP64 Gram arithmetic."""
+    for lvl, L in enumerate(ho.levels[:-1]):
+        for i in range(L.nagg):
+            no = L.omega[i].shape[0]
+            G = L.Atil[i][no:, no:]
+            if G.shape[0] == 0:
+                continue
+            w = np.linalg.eigvalsh(G)
+            r = w / w.max()
+            if np.any((r > lo) & (r < hi)):
+                return lvl
+    return len(ho.levels) - 1
+
+
+def check_structure_upto(amg, H, ho, g):
+    """Aggregates and Omega lists on levels <= g, k_i on levels < g, exactly."""
+    for lvl in range(min(g, len(ho.levels) - 2) + 1):
+        Lo = ho.levels[lvl]
+        d = H.describe(lvl)
+        assert d["n"] == Lo.n and d["nagg"] == Lo.nagg, lvl
+        assert np.array_equal(H.export(lvl, amg.ARR_AGG), Lo.agg.astype(np.int32))
+        ptr = H.export(lvl, amg.ARR_OMEGA_PTR)
+        idx = H.export(lvl, amg.ARR_OMEGA_IDX)
+        for i in range(Lo.nagg):
+            assert np.array_equal(idx[ptr[i]:ptr[i + 1]], Lo.Omega[i].astype(np.int32)), (lvl, i)
+        if lvl < g:
+            assert np.array_equal(H.export(lvl, amg.ARR_K), np.array([Z.shape[1] for Z in Lo.Z], dtype=np.int32))
+
+
+def check_valid_from(amg, H, c_min, g):
+    """The library's own levels >= g: mu in [0, 1] (S~ <= A_ww), 0 <= k_i <= max(1, |omega_i| / c_l)."""
+    nl = H.num_levels
+    for lvl in range(g, nl - 1):
+        mu = H.export(lvl, amg.ARR_MU)
+        assert mu.min() >= -1e-10 and mu.max() <= 1 + 1e-10, lvl
+        k = H.export(lvl, amg.ARR_K)
+        nom = H.export(lvl, amg.ARR_NOMEGA)
+        cap = np.maximum(1, nom // c_min[min(lvl, len(c_min) - 1)])
+        assert np.all(k >= 0) and np.all(k <= cap), lvl
+
+
+def check_level0_operators(amg, H, ho):
+    """A, RAS, RAS-T and P P^T on level 0 (the V-cycle reaches the coarse levels)."""
+    rng = np.random.default_rng(11)
+    Lo = ho.levels[0]
+    x = rng.standard_normal(Lo.n)
+    assert _rel(_apply(amg, H, amg.OP_A, 0, x, Lo.n), Lo.A @ x) <= 1e-13
+    assert _rel(_apply(amg, H, amg.OP_RAS, 0, x, Lo.n), oracle.ras(Lo, x)) <= 1e-12
+    assert _rel(_apply(amg, H, amg.OP_RAST, 0, x, Lo.n), oracle.rast(Lo, x)) <= 1e-12
+    nn = ho.levels[1].n
+    y = _apply(amg, H, amg.OP_PROLONG, 0, _apply(amg, H, amg.OP_RESTRICT, 0, x, nn), Lo.n)
+    yo = Lo.P @ (Lo.P.T @ x)
+    for i in range(Lo.nagg):
+        if _degenerate_cut(Lo.mu[i], Lo.Z[i].shape[1], Lo.omega[i].shape[0]):
+            continue
+        om = Lo.omega[i]
+        assert np.abs(y[om] - yo[om]).max() <= 1e-10 * np.abs(yo).max(), i
+
+
+def check_solve(amg, H, ho, b):
+    """FP64 and mixed PCG reach 1e-8; FP64 iterations within the oracle's +- 1 when the whole hierarchy is
+    well posed, else at most 1.5 x the oracle's + 3."""
+    xo, io = oracle.pcg(ho, b, tol=1e-8)
+    H.set_precision(amg.FP64)
+    xg, ig = H.solve(b, tol=1e-8)
+    assert ig[0]["status"] == 0 and ig[0]["relres_true"] <= 1e-8
+    if first_gray_level(ho) == len(ho.levels) - 1:
+        assert abs(ig[0]["iters"] - io["iters"]) <= 1
+        if ig[0]["iters"] == io["iters"]:
+            assert _rel(xg[:, 0] if xg.ndim == 2 else xg, xo) <= 1e-10
+    else:
+        assert ig[0]["iters"] <= 1.5 * io["iters"] + 3, (ig[0]["iters"], io["iters"])
+    H.set_precision(amg.MIXED32)
+    _, i32 = H.solve(b, tol=1e-8)
+    assert i32[0]["status"] == 0 and i32[0]["relres_true"] <= 1e-8
+    H.set_precision(amg.FP64)
+
+
+def _both(amg, c):
+    p = fd_2d(c["N"], c["theta"], c["eps"], agg=fd_block_aggregates(c["N"], c["bs"]))
+    ho = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, overlap=1, c_min=c["c_min"],
+                      n_coarse=c["n_coarse"], keep_local=True, kappa=c["kappa"])
+    H = amg.Hierarchy.from_problem(p, overlap=1, c_min=c["c_min"], n_coarse=c["n_coarse"], kappa=c["kappa"],
+                                   precision=amg.FP64)
+    return p, ho, H
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_kappa_threshold_per_level(amg, name):
+    c = CASES[name]
+    p, ho, H = _both(amg, c)
+    st = H.stats()
+    g = first_gray_level(ho)
+    lv = ho.levels[:g + 1]
+    upto = min(g + 1, len(ho.levels) - 1)
+    assert st["n_color"][:upto] == [L.n_color for L in lv][:upto]
+    assert st["n_mult"][:upto] == [L.n_mult for L in lv][:upto]
+    assert st["thresh"][:upto] == [L.thresh for L in lv][:upto]
+    if name == "fd_30_floor":
+        assert st["thresh"][1] == 0.1  # (6 - 5) / (5 * 3) < 0.1
+    check_structure_upto(amg, H, ho, g)
+    for lvl in range(g):
+        _check_spectra(amg, H, ho, lvl)
+    check_valid_from(amg, H, c["c_min"], g)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_kappa_operators_and_solve(amg, name):
+    c = CASES[name]
+    p, ho, H = _both(amg, c)
+    check_level0_operators(amg, H, ho)
+    check_solve(amg, H, ho, seeded_rhs(p.n, 1, 3)[:, 0])
+
+
+def test_kappa_zero_keeps_fixed_threshold(amg):
+    N = 24
+    p = fd_2d(N, 0.5, 1e-3, agg=fd_block_aggregates(N, 4))
+    H = amg.Hierarchy.from_problem(p, overlap=1, c_min=(2,), n_coarse=50, thresh=0.25)
+    st = H.stats()
+    assert all(t == 0.25 for t in st["thresh"]) and all(v == 0 for v in st["n_color"])
+
+
+def test_negative_kappa_rejected(amg):
+    p = fd_2d(8, 0.5, 1e-3, agg=fd_block_aggregates(8, 4))
+    with pytest.raises(Exception):
+        amg.Hierarchy.from_problem(p, overlap=1, kappa=-1.0)
