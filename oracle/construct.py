@@ -157,10 +157,19 @@ def local_gep(S, Aww, cap, thresh):
 
 
 def _block_aggregation(prev):
-    """Coarse aggregates on the block graph of the previous level."""
-    nb = prev.nagg
+    """Coarse aggregates on the block graph of the previous level.
+
+    One vertex per previous-level aggregate that kept coarse dofs (k_i > 0;
+    one with k_i = 0 has none on the next level and is left out), in
+    ascending order; an edge where a row of G touches both."""
+    live = np.flatnonzero(prev.k > 0)
+    nb = live.shape[0]
+    new_id = -np.ones(prev.nagg, dtype=np.int64)
+    new_id[live] = np.arange(nb)
     r, c = [], []
     for t in prev.touched:
+        t = new_id[t]
+        t = t[t >= 0]
         if t.shape[0] > 1:
             r.append(np.repeat(t, t.shape[0]))
             c.append(np.tile(t, t.shape[0]))
@@ -173,7 +182,7 @@ def _block_aggregation(prev):
         B = sp.csr_matrix((nb, nb), dtype=np.int8)
     B.sort_indices()
     bagg, nagg = vanek_aggregation(B)
-    agg = np.repeat(bagg, prev.k)
+    agg = np.repeat(bagg, prev.k[live])
     return agg, nagg
 
 
@@ -182,7 +191,8 @@ def _next_groups(level):
 
     A row g of G_l becomes g P_l; its support is the coarse columns of every
     aggregate the row touches, and g^T g becomes P^T (g^T g) P restricted to
-    those columns.
+    those columns.  A row whose touched aggregates all kept k = 0 columns
+    becomes zero and is dropped.
     """
     # row j of P is Z_a(position of j in omega_a, :) in the columns of a
     pos = np.zeros(level.n, dtype=np.int64)
@@ -190,6 +200,8 @@ def _next_groups(level):
         pos[level.omega[i]] = np.arange(level.omega[i].shape[0])
     merged = {}
     for s, H, t in zip(level.sups, level.grams, level.touched):
+        if not np.any(level.k[t] > 0):
+            continue
         cs = np.concatenate([np.arange(level.col0[a], level.col0[a] + level.k[a]) for a in t])
         Pg = np.zeros((s.shape[0], cs.shape[0]))  # P(S_g, S'_g)
         off = np.concatenate([[0], np.cumsum([level.k[a] for a in t])])
@@ -264,6 +276,8 @@ def setup(rowptr, col, val, n, D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=200
         cur.col0 = np.zeros(cur.nagg + 1, dtype=np.int64)
         np.cumsum(ks, out=cur.col0[1:])
         nc = int(cur.col0[-1])
+        if nc == 0:  # no lambda above any level's threshold: nothing to coarsen to
+            raise ValueError(f"level {lvl} produced an empty coarse space")
         r, cc, v = [], [], []
         for i in range(cur.nagg):
             Z = cur.Z[i]

@@ -1356,8 +1356,15 @@ int build_next(amgdd_hierarchy& h, Level& L, Level& N, cudaStream_t s) {
   std::vector<int32_t> tids, M;
   touched_aggregates(S, L.agg, tptr, tids, M);
   const int64_t ng = S.size();
+  // a row whose touched aggregates all kept k = 0 columns becomes zero in
+  // G_{l+1} = G_l P_l and is dropped
+  std::vector<char> live_row(ng, 0);
+  for (int64_t g = 0; g < ng; ++g)
+    for (int64_t t = tptr[g]; t < tptr[g + 1]; ++t)
+      if (L.k[tids[t]] > 0) live_row[g] = 1;
   std::map<std::vector<int32_t>, int64_t> keys;
-  for (int64_t g = 0; g < ng; ++g) keys.emplace(std::vector<int32_t>(tids.begin() + tptr[g], tids.begin() + tptr[g + 1]), 0);
+  for (int64_t g = 0; g < ng; ++g)
+    if (live_row[g]) keys.emplace(std::vector<int32_t>(tids.begin() + tptr[g], tids.begin() + tptr[g + 1]), 0);
   int64_t h_id = 0;
   N.g_ptr.assign(1, 0);
   N.g_idx.clear();
@@ -1376,17 +1383,19 @@ int build_next(amgdd_hierarchy& h, Level& L, Level& N, cudaStream_t s) {
     N.h_off[q + 1] = N.h_off[q] + sn * sn;
   }
   // contributions and per-support-node Z rows
-  std::vector<int64_t> owner(ng);
+  std::vector<int64_t> owner(ng, -1);
   std::vector<int64_t> cnt(nnew + 1, 0);
   for (int64_t g = 0; g < ng; ++g) {
+    if (!live_row[g]) continue;
     owner[g] = keys[std::vector<int32_t>(tids.begin() + tptr[g], tids.begin() + tptr[g + 1])];
     cnt[owner[g] + 1]++;
   }
   for (int64_t q = 0; q < nnew; ++q) cnt[q + 1] += cnt[q];
-  std::vector<int32_t> contrib(ng);
+  std::vector<int32_t> contrib(std::max<int64_t>(cnt[nnew], 1));
   {
     std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
-    for (int64_t g = 0; g < ng; ++g) contrib[fill[owner[g]]++] = (int32_t)g;
+    for (int64_t g = 0; g < ng; ++g)
+      if (owner[g] >= 0) contrib[fill[owner[g]]++] = (int32_t)g;
   }
   std::vector<int32_t> pos(L.n, 0);
   for (int i = 0; i < L.nagg; ++i)
@@ -1432,13 +1441,24 @@ int build_next(amgdd_hierarchy& h, Level& L, Level& N, cudaStream_t s) {
   AMGDD_TRY(N.d_g_ptr.upload(N.g_ptr, s));
   AMGDD_TRY(N.d_g_idx.upload(N.g_idx, s));
   AMGDD_TRY(N.d_h_off.upload(N.h_off, s));
-  // aggregates of level l+1: whole blocks of coarse dofs
+  // aggregates of level l+1: whole blocks of coarse dofs, on the graph of the
+  // blocks that kept coarse dofs (k > 0), in ascending order
+  std::vector<int32_t> live_id(L.nagg, -1), ltids;
+  int nlive = 0;
+  for (int a = 0; a < L.nagg; ++a)
+    if (L.k[a] > 0) live_id[a] = nlive++;
+  std::vector<int64_t> ltptr(1, 0);
+  for (int64_t g = 0; g < ng; ++g) {
+    for (int64_t t = tptr[g]; t < tptr[g + 1]; ++t)
+      if (live_id[tids[t]] >= 0) ltids.push_back(live_id[tids[t]]);
+    ltptr.push_back((int64_t)ltids.size());
+  }
   std::vector<int32_t> bagg;
   int nn = 0;
-  block_aggregation(L.nagg, tptr, tids, bagg, nn);
+  block_aggregation(nlive, ltptr, ltids, bagg, nn);
   N.agg.assign(N.n, 0);
   for (int a = 0; a < L.nagg; ++a)
-    for (int64_t c = L.col0[a]; c < L.col0[a + 1]; ++c) N.agg[c] = bagg[a];
+    for (int64_t c = L.col0[a]; c < L.col0[a + 1]; ++c) N.agg[c] = bagg[live_id[a]];
   N.nagg = nn;
   AMGDD_CUDA(cudaStreamSynchronize(s));
   return AMGDD_OK;

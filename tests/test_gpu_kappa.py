@@ -20,6 +20,7 @@ import pytest
 
 import oracle
 from inputs import fd_2d, fd_block_aggregates, seeded_rhs
+from oracle.construct import row_groups_from_csr
 from test_gpu_parity import _apply, _check_spectra, _degenerate_cut, _rel
 
 pytestmark = pytest.mark.gpu
@@ -29,6 +30,9 @@ CASES = {
     "fd_48": dict(N=48, theta=math.pi / 6, eps=1e-4, bs=4, c_min=(2, 3, 4), n_coarse=100, kappa=50.0),
     # ragged blocks (30 = 7 x 4 + 2 per axis), kappa small enough that the 0.1 floor binds on coarse levels
     "fd_30_floor": dict(N=30, theta=0.9, eps=1e-3, bs=4, c_min=(2, 3), n_coarse=60, kappa=6.0),
+    # isotropic, standard aggregation chosen by each side: aggregates with k_i = 0 on levels 0 and 1 (no
+    # lambda above the threshold), left out of the next level's dofs, rows and block graph
+    "fd_16_iso": dict(N=16, theta=math.pi / 6, eps=1.0, bs=0, c_min=(2, 3, 4), n_coarse=20, kappa=50.0),
 }
 
 
@@ -124,8 +128,12 @@ def check_solve(amg, H, ho, b):
 
 
 def _both(amg, c):
-    p = fd_2d(c["N"], c["theta"], c["eps"], agg=fd_block_aggregates(c["N"], c["bs"]))
-    ho = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, overlap=1, c_min=c["c_min"],
+    p = fd_2d(c["N"], c["theta"], c["eps"], agg=fd_block_aggregates(c["N"], c["bs"]) if c["bs"] else None)
+    agg = p.agg
+    if agg is None:
+        sups, _ = row_groups_from_csr(p.rowptr, p.col, p.val, p.n, p.D1)
+        agg, _ = oracle.standard_aggregation(sups, p.n, 1)
+    ho = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, agg, overlap=1, c_min=c["c_min"],
                       n_coarse=c["n_coarse"], keep_local=True, kappa=c["kappa"])
     H = amg.Hierarchy.from_problem(p, overlap=1, c_min=c["c_min"], n_coarse=c["n_coarse"], kappa=c["kappa"],
                                    precision=amg.FP64)
@@ -165,6 +173,14 @@ def test_kappa_zero_keeps_fixed_threshold(amg):
     H = amg.Hierarchy.from_problem(p, overlap=1, c_min=(2,), n_coarse=50, thresh=0.25)
     st = H.stats()
     assert all(t == 0.25 for t in st["thresh"]) and all(v == 0 for v in st["n_color"])
+
+
+def test_empty_coarse_space_rejected(amg):
+    """Isotropic 20 x 20: every aggregate of a coarse level keeps k_i = 0; setup fails cleanly (the oracle
+    raises on the same level)."""
+    p = fd_2d(20, math.pi / 6, 1.0)
+    with pytest.raises(Exception, match="empty coarse space"):
+        amg.Hierarchy.from_problem(p, overlap=1, c_min=(2, 3, 4), n_coarse=20, kappa=50.0)
 
 
 def test_negative_kappa_rejected(amg):

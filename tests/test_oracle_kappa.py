@@ -71,12 +71,16 @@ def test_fd_blocks_need_four_colours_and_multiplicity_three():
 
 
 def test_single_aggregate():
+    # (setup itself stops there: with one subdomain S~ = A_ww, every lambda = 1 < 19 and k = 0)
+    from oracle.structure import multiplicity_and_nz
+
     N = 6
     p = fd_2d(N, 0.3, 1e-2, agg=fd_block_aggregates(N, N))
-    h = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, overlap=1, c_min=(2,), n_coarse=1, L_max=2,
-                     kappa=20.0)
-    L0 = h.levels[0]
-    assert (L0.n_color, L0.n_mult, L0.thresh) == (1, 1, 19.0)
+    Om, adj = _subdomains(p)
+    _, nc = subdomain_colouring(Om, adj, p.n)
+    sups, _ = row_groups_from_csr(p.rowptr, p.col, p.val, p.n, p.D1)
+    M, _, _ = multiplicity_and_nz(sups, p.agg.astype(np.int64), 1)
+    assert (nc, int(M.max()), kappa_threshold(20.0, nc, int(M.max()))) == (1, 1, 19.0)
 
 
 def test_floor():
@@ -96,3 +100,36 @@ def test_selection_follows_derived_threshold():
         lam = np.where(mu > 0, 1.0 / np.where(mu > 0, mu, 1.0), np.inf)
         want = min(int(np.sum(lam > L0.thresh)), max(1, L0.omega[i].shape[0] // 2))
         assert L0.Z[i].shape[1] == want
+
+
+def test_aggregates_without_coarse_vectors():
+    """Isotropic 16 x 16 with kappa = 50: some aggregates keep k_i = 0 (no lambda above the threshold).
+    They add no coarse dofs, rows touching only them vanish from G_{l+1}, they are left out of the block
+    graph, and A_{l+1} is still P_l^T A_l P_l."""
+    from oracle.structure import standard_aggregation
+    from inputs import seeded_rhs
+
+    p = fd_2d(16, math.pi / 6, 1.0)
+    sups, _ = row_groups_from_csr(p.rowptr, p.col, p.val, p.n, p.D1)
+    agg, _ = standard_aggregation(sups, p.n, 1)
+    h = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=20, kappa=50.0)
+    assert any(np.any(L.k == 0) for L in h.levels[:-1])
+    for lvl in range(len(h.levels) - 1):
+        L, Ln = h.levels[lvl], h.levels[lvl + 1]
+        assert Ln.n == int(L.k.sum()) == L.P.shape[1]
+        ref = (L.P.T @ L.A @ L.P).toarray()
+        assert np.abs(Ln.A.toarray() - ref).max() <= 1e-13 * np.abs(ref).max()
+        for i in np.flatnonzero(L.k == 0):
+            assert L.P[L.omega[i]].nnz == 0
+    x, info = oracle.pcg(h, seeded_rhs(p.n, 1, 1)[:, 0], tol=1e-8)
+    assert info["status"] == 0 and info["relres_true"] <= 1e-8
+
+
+def test_empty_coarse_space_is_an_error():
+    from oracle.structure import standard_aggregation
+
+    p = fd_2d(20, math.pi / 6, 1.0)
+    sups, _ = row_groups_from_csr(p.rowptr, p.col, p.val, p.n, p.D1)
+    agg, _ = standard_aggregation(sups, p.n, 1)
+    with pytest.raises(ValueError, match="empty coarse space"):
+        oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=20, kappa=50.0)
