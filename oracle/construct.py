@@ -69,6 +69,7 @@ class Level:
     Atil: list = field(default_factory=list)  # kept only when keep_local
     S: list = field(default_factory=list)  # kept only when keep_local
     Ai: list = field(default_factory=list)  # kept only when keep_local
+    rows: list | None = None  # schur="rows": per group its rows R_g (R_g^T R_g = grams[g])
     thresh: float = 0.1  # eigenvalue threshold used on this level
     n_color: int = 0  # with kappa: colours of the subdomain colouring
     n_mult: int = 0  # with kappa: largest row multiplicity M(j)
@@ -127,6 +128,39 @@ def schur_complement(Atil, no, rtol):
             Uk = U[:, keep]
             T = Awg @ Uk
             S = Aww - (T / w[keep]) @ T.T
+    return 0.5 * (S + S.T)
+
+
+def local_splitting_rows(Omega_i, nz_i, sups, rows, M):
+    """The rows behind A~_i of the Lemma: the rows of every group in nz_i,
+    scaled by 1/sqrt(M) and embedded in Omega_i, so that Y^T Y = A~_i."""
+    m = Omega_i.shape[0]
+    order = np.argsort(Omega_i)
+    blocks = []
+    for g in nz_i:
+        p = order[np.searchsorted(Omega_i, sups[g], sorter=order)]
+        Yg = np.zeros((rows[g].shape[0], m))
+        Yg[:, p] = rows[g] / np.sqrt(M[g])
+        blocks.append(Yg)
+    return np.vstack(blocks) if blocks else np.zeros((0, m))
+
+
+def schur_complement_rows(Y, no, sv_rtol):
+    """S~ of Eq. gevp-S from the rows Y = [X Y_G] (X on omega_i, Y_G on Gamma_i):
+    A~_ww - A~_wG (A~_GG)^+ A~_Gw = X^T (I - Pi) X with Pi the orthogonal
+    projector onto range(Y_G).  Pi comes from the SVD of Y_G, singular values
+    at or below sv_rtol * (largest) being treated as zero; S~ = Xp^T Xp with
+    Xp = (I - Pi) X, never a difference of Grams."""
+    X = Y[:, :no]
+    YG = Y[:, no:]
+    if YG.shape[1] == 0 or YG.shape[0] == 0:
+        S = X.T @ X
+    else:
+        U, sv, _ = np.linalg.svd(YG, full_matrices=False)
+        keep = sv > sv_rtol * sv.max() if sv.size and sv.max() > 0 else np.zeros(sv.shape, dtype=bool)
+        Uk = U[:, keep]
+        Xp = X - Uk @ (Uk.T @ X)
+        S = Xp.T @ Xp
     return 0.5 * (S + S.T)
 
 
@@ -219,9 +253,49 @@ def _next_groups(level):
     return [merged[k][0] for k in keys], [merged[k][1] for k in keys]
 
 
+def _next_groups_rows(level):
+    """Row groups of G_{l+1} = G_l P_l carried as rows: each group's rows R_g
+    become R_g P(S_g, S'_g); groups with one touched-aggregate set are stacked
+    and compressed to the R factor of their QR decomposition (an orthogonal
+    change of rows that keeps R^T R).  Same groups, supports and order as
+    `_next_groups`."""
+    pos = np.zeros(level.n, dtype=np.int64)
+    for i in range(level.nagg):
+        pos[level.omega[i]] = np.arange(level.omega[i].shape[0])
+    merged = {}
+    for s, R, t in zip(level.sups, level.rows, level.touched):
+        if not np.any(level.k[t] > 0):
+            continue
+        cs = np.concatenate([np.arange(level.col0[a], level.col0[a] + level.k[a]) for a in t])
+        Pg = np.zeros((s.shape[0], cs.shape[0]))
+        off = np.concatenate([[0], np.cumsum([level.k[a] for a in t])])
+        for r, j in enumerate(s):
+            a = int(level.agg[j])
+            c = int(np.searchsorted(t, a))
+            Pg[r, off[c]:off[c + 1]] = level.Z[a][pos[j]]
+        key = tuple(int(a) for a in t)
+        merged.setdefault(key, (cs.astype(np.int64), []))[1].append(R @ Pg)
+    keys = sorted(merged)
+    sups, rows, grams = [], [], []
+    for k in keys:
+        cs, parts = merged[k]
+        Rn = np.linalg.qr(np.vstack(parts), mode="r")
+        sups.append(cs)
+        rows.append(Rn)
+        grams.append(Rn.T @ Rn)
+    return sups, rows, grams
+
+
 def setup(rowptr, col, val, n, D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=2000, L_max=10,
-          thresh=0.1, schur_rtol=1e-12, keep_local=False, coarse_overlap=0, kappa=None):
+          thresh=0.1, schur_rtol=1e-12, keep_local=False, coarse_overlap=0, kappa=None, schur="gram",
+          sv_rtol=1e-10):
     """Build the multilevel hierarchy {A_l, G_l, P_l} of Algorithm 1.
+
+    schur = "gram" forms S~ from the Gram A~_i with an eigenvalue-thresholded
+    pseudo-inverse (`schur_rtol`); "rows" carries the rows of every G_l and
+    forms S~ by an orthogonal projector on them (`sv_rtol` on singular
+    values).  The two agree in exact arithmetic; the rows form resolves the
+    small singular directions the Gram squares away.
 
     With `kappa` given, each level's eigenvalue threshold is derived from it
     (Section 3.4): max{0.1, (kappa - n_color) / (n_color n_multiplicity)}, with
@@ -232,10 +306,12 @@ def setup(rowptr, col, val, n, D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=200
     `overlap` hops of neighbours form Omega_i on level 0; coarse levels use
     `coarse_overlap` hops (0: the same as level 0).  Algorithm 1 itself adds
     one layer of neighbours in A_l on every level."""
-    sups, grams = row_groups_from_csr(rowptr, col, val, n, D1)
+    if schur not in ("gram", "rows"):
+        raise ValueError("schur must be 'gram' or 'rows'")
+    sups, grams, rows = row_groups_from_csr(rowptr, col, val, n, D1, with_rows=True)
     A = assemble_A(sups, grams, n)
     levels = []
-    cur = Level(n=n, sups=sups, grams=grams, A=A)
+    cur = Level(n=n, sups=sups, grams=grams, A=A, rows=rows if schur == "rows" else None)
     lvl = 0
     agg0 = np.asarray(agg)
     while lvl < L_max - 1 and cur.n > n_coarse:
@@ -262,8 +338,13 @@ def setup(rowptr, col, val, n, D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=200
             Ai = Acsr[Om][:, Om].toarray()
             L = np.linalg.cholesky(Ai)  # raises LinAlgError when A_i is not SPD
             cur.chol.append(L)
-            At = local_splitting(Om, cur.nz[i], cur.sups, cur.grams, cur.M)
-            S = schur_complement(At, no, schur_rtol)
+            if schur == "rows":
+                Y = local_splitting_rows(Om, cur.nz[i], cur.sups, cur.rows, cur.M)
+                At = Y.T @ Y
+                S = schur_complement_rows(Y, no, sv_rtol)
+            else:
+                At = local_splitting(Om, cur.nz[i], cur.sups, cur.grams, cur.M)
+                S = schur_complement(At, no, schur_rtol)
             mu, Z = local_gep(S, Ai[:no, :no], max(1, no // c), cur.thresh)
             cur.mu.append(mu)
             cur.Z.append(Z)
@@ -287,13 +368,17 @@ def setup(rowptr, col, val, n, D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=200
         cur.P = sp.csr_matrix((np.concatenate(v), (np.concatenate(r), np.concatenate(cc))), shape=(cur.n, nc))
         cur.P.sort_indices()
         levels.append(cur)
-        nsups, ngrams = _next_groups(cur)
-        cur = Level(n=nc, sups=nsups, grams=ngrams, A=assemble_A(nsups, ngrams, nc))
+        if schur == "rows":
+            nsups, nrows, ngrams = _next_groups_rows(cur)
+        else:
+            nsups, ngrams = _next_groups(cur)
+            nrows = None
+        cur = Level(n=nc, sups=nsups, grams=ngrams, A=assemble_A(nsups, ngrams, nc), rows=nrows)
         lvl += 1
     levels.append(cur)
     AL = cur.A.toarray()
     coarse = np.linalg.cholesky(AL)
     params = dict(overlap=overlap, coarse_overlap=coarse_overlap, c_min=tuple(c_min), n_coarse=n_coarse, L_max=L_max,
                   thresh=thresh, kappa=kappa,
-                  schur_rtol=schur_rtol)
+                  schur_rtol=schur_rtol, schur=schur, sv_rtol=sv_rtol)
     return Hierarchy(levels=levels, coarse_chol=coarse, params=params)

@@ -21,20 +21,21 @@ import numpy as np
 import scipy.sparse as sp
 
 
-def row_groups_from_csr(rowptr, col, val, n, D1=None):
+def row_groups_from_csr(rowptr, col, val, n, D1=None, with_rows=False):
     """Group the rows of G (and the rows sqrt(D1_jj) e_j^T) by support.
 
     Returns (supports, grams): supports[g] is the sorted int64 column list
     shared by every row of group g, grams[g] = sum over those rows of
     g_l^T g_l restricted to the support (dense, symmetric).  Section 1
     writes A = D1 + B^T D2^{-1} B = G^T G with G^T = [sqrt(D1), ...], so the
-    D1 rows are ordinary rows of G with a one-node support.
+    D1 rows are ordinary rows of G with a one-node support.  With_rows adds
+    a third list: the group's rows themselves (count x support size).
     """
     rowptr = np.asarray(rowptr, dtype=np.int64)
     col = np.asarray(col, dtype=np.int64)
     val = np.asarray(val, dtype=np.float64)
     lens = np.diff(rowptr)
-    sups, grams = [], []
+    sups, grams, rws = [], [], []
     # rows of equal length are handled together; identical supports merge
     extra = None
     if D1 is not None:
@@ -54,21 +55,24 @@ def row_groups_from_csr(rowptr, col, val, n, D1=None):
             C = np.concatenate([C, extra[0]])
             V = np.concatenate([V, extra[1]])
             extra = None
-        _append_groups(C, V, sups, grams)
+        _append_groups(C, V, sups, grams, rws)
     if extra is not None:
-        _append_groups(extra[0], extra[1], sups, grams)
-    return sups, grams
+        _append_groups(extra[0], extra[1], sups, grams, rws)
+    return (sups, grams, rws) if with_rows else (sups, grams)
 
 
-def _append_groups(C, V, sups, grams):
+def _append_groups(C, V, sups, grams, rws):
     uniq, inv = np.unique(C, axis=0, return_inverse=True)
     inv = inv.ravel()
     outer = V[:, :, None] * V[:, None, :]
     H = np.zeros((uniq.shape[0],) + outer.shape[1:])
     np.add.at(H, inv, outer)
+    order = np.argsort(inv, kind="stable")
+    starts = np.searchsorted(inv[order], np.arange(uniq.shape[0] + 1))
     for g in range(uniq.shape[0]):
         sups.append(uniq[g].astype(np.int64))
         grams.append(H[g])
+        rws.append(V[order[starts[g]:starts[g + 1]]])
 
 
 def incidence(sups, n):
