@@ -203,8 +203,10 @@ int amgdd_aggregate(const amgdd_csr* G, int passes, void* stream, int32_t* agg, 
  *              to form Omega_i = omega_i u Gamma_i (Section 2.2).
  *   params   : NULL for amgdd_params_default().
  *   out      : receives the hierarchy, freed with amgdd_free.
- * Errors: INVALID_ARG (bad CSR/ids/params), NONFINITE, NOT_SPD (a block
- * A(Omega_i, Omega_i) or the coarsest matrix failed Cholesky), OOM, CUDA. */
+ * Errors: INVALID_ARG (bad CSR/ids/params, or a level where no local
+ * eigenvector passes the threshold: an empty coarse space), NONFINITE,
+ * NOT_SPD (a block A(Omega_i, Omega_i) or the coarsest matrix failed
+ * Cholesky), OOM, CUDA.                                                   */
 int amgdd_setup(const amgdd_csr* G, const double* D1, const int32_t* agg, int overlap,
                 const amgdd_params* params, void* stream, amgdd_hierarchy** out);
 

@@ -2934,6 +2934,10 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
       break;
     }
     AMGDD_TRY(build_level(*H, L, lvl, lvl == 0 ? aggh.data() : nullptr, s));
+    if (L.col0.back() == 0) {  // no local eigenvector passed the threshold anywhere on this level
+      set_error("level %d produced an empty coarse space", lvl);
+      return AMGDD_ERR_INVALID_ARG;
+    }
     AMGDD_TRY(build_plans(*H, L, L.d_om_idx, s));
     if (lvl > 0) {
       Phase ph(9, "block rows", s);
@@ -2972,10 +2976,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     }
     for (double& a : g_timer.acc) a = 0.0;
     L.d_H.release();
-    if (N->n == 0) {
-      set_error("level %d produced an empty coarse space", lvl);
-      return AMGDD_ERR_INTERNAL;
-    }
+
     H->lv.push_back(std::move(N));
     ++lvl;
   }
