@@ -45,6 +45,9 @@ def _dense_coupled(p, Om):
 
 
 @pytest.mark.parametrize("make", [lambda: fd_2d(13, 0.5, 1e-3, agg=fd_block_aggregates(13, 3)),
+                                  # 2x2 blocks: many subdomain pairs are coupled by A without sharing a node
+                                  # (9 colours; a colouring by shared nodes alone needs 4)
+                                  lambda: fd_2d(13, 0.5, 1e-3, agg=fd_block_aggregates(13, 2)),
                                   lambda: q1_2d(12, rotated_sqrtK(0.4, 1e-3), agg=block_aggregates_2d(12, 3))])
 def test_colouring_is_proper_and_greedy(make):
     p = make()
