@@ -136,3 +136,22 @@ def test_empty_coarse_space_is_an_error():
     agg, _ = standard_aggregation(sups, p.n, 1)
     with pytest.raises(ValueError, match="empty coarse space"):
         oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=20, kappa=50.0)
+
+
+def test_two_level_with_threshold_selection_is_size_independent():
+    """With every local eigenvector above the kappa threshold kept (cap |omega_i|, c_min = 1), the two-level
+    method's PCG count does not grow with the grid (the GenEO-type bound behind Section 3.4's formula depends
+    on n_color, n_multiplicity and thresh only): 48^2, 64^2 and 96^2 all take 12 iterations to 1e-8."""
+    from oracle.structure import standard_aggregation
+    from inputs import seeded_rhs
+
+    its = []
+    for N in (48, 64, 96):
+        p = fd_2d(N, math.pi / 6, 1e-5)
+        sups, _ = row_groups_from_csr(p.rowptr, p.col, p.val, p.n, p.D1)
+        agg, _ = standard_aggregation(sups, p.n, 1)
+        h = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, agg, overlap=1, c_min=(1,), L_max=2, n_coarse=1,
+                         kappa=50.0)
+        _, info = oracle.pcg(h, seeded_rhs(p.n, 1, 6)[:, 0], tol=1e-8)
+        its.append(info["iters"])
+    assert max(its) - min(its) <= 1 and max(its) <= 14, its
