@@ -404,6 +404,11 @@ void amgdd_free(amgdd_hierarchy* h);
 const char* amgdd_status_string(int status);
 const char* amgdd_last_error(void);
 
+/* sizeof of the structs a binding mirrors, for a layout check at load time:
+ * which = 0 amgdd_params, 1 amgdd_info, 2 amgdd_level_desc, 3 amgdd_csr,
+ * 4 amgdd_server_params; 0 for any other value.  Host only.              */
+size_t amgdd_struct_size(int which);
+
 #ifdef __cplusplus
 }
 #endif

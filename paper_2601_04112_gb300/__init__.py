@@ -34,7 +34,7 @@ EXPORTED = [
     "amgdd_kernel_launches", "amgdd_apply_noalloc", "amgdd_device_bytes", "amgdd_server_params_default",
     "amgdd_server_create", "amgdd_server_add_operator", "amgdd_server_submit", "amgdd_server_poll",
     "amgdd_server_stats", "amgdd_server_destroy", "amgdd_hierarchy_save", "amgdd_hierarchy_load",
-    "amgdd_selftest_wait_timeouts", "amgdd_aggregate",
+    "amgdd_selftest_wait_timeouts", "amgdd_aggregate", "amgdd_struct_size",
 ]
 AMGDD_PENDING = 1
 
@@ -128,6 +128,12 @@ def load_library(path: str = LIB_PATH):
     for name in ("amgdd_setup", "amgdd_solve", "amgdd_set_precision", "amgdd_apply", "amgdd_num_levels",
                  "amgdd_level_describe", "amgdd_level_export", "amgdd_hierarchy_stats", "amgdd_bytes_model"):
         getattr(lib, name).restype = i32
+    lib.amgdd_struct_size.argtypes = [i32]
+    lib.amgdd_struct_size.restype = ctypes.c_size_t
+    for which, st in enumerate((Params, Info, LevelDesc, Csr, ServerParams)):
+        if lib.amgdd_struct_size(which) != ctypes.sizeof(st):
+            raise RuntimeError(f"{path} was built against another amgdd.h: {st.__name__} is "
+                               f"{lib.amgdd_struct_size(which)} bytes there, {ctypes.sizeof(st)} here; rebuild it")
     _lib = lib
     return lib
 

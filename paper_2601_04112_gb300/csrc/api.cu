@@ -2708,6 +2708,17 @@ const char* amgdd_status_string(int st) {
 
 const char* amgdd_last_error(void) { return g_last_error.c_str(); }
 
+size_t amgdd_struct_size(int which) {
+  switch (which) {
+    case 0: return sizeof(amgdd_params);
+    case 1: return sizeof(amgdd_info);
+    case 2: return sizeof(amgdd_level_desc);
+    case 3: return sizeof(amgdd_csr);
+    case 4: return sizeof(amgdd_server_params);
+    default: return 0;
+  }
+}
+
 // CSR pattern rules shared by setup and aggregation: rowptr[0] = 0,
 // rowptr[m] = nnz, nondecreasing, column ids strictly increasing in [0, n).
 static int check_pattern(const char* who, const std::vector<int64_t>& rowptr, const std::vector<int32_t>& col,
