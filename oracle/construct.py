@@ -145,19 +145,21 @@ def local_splitting_rows(Omega_i, nz_i, sups, rows, M):
     return np.vstack(blocks) if blocks else np.zeros((0, m))
 
 
-def schur_complement_rows(Y, no, sv_rtol):
+def schur_complement_rows(Y, no, sv_rtol=None):
     """S~ of Eq. gevp-S from the rows Y = [X Y_G] (X on omega_i, Y_G on Gamma_i):
     A~_ww - A~_wG (A~_GG)^+ A~_Gw = X^T (I - Pi) X with Pi the orthogonal
     projector onto range(Y_G).  Pi comes from the SVD of Y_G, singular values
-    at or below sv_rtol * (largest) being treated as zero; S~ = Xp^T Xp with
-    Xp = (I - Pi) X, never a difference of Grams."""
+    at or below the rank tolerance being treated as zero: max(shape) * eps *
+    (largest) by default (the numerical rank of Y_G), sv_rtol * (largest) when
+    given; S~ = Xp^T Xp with Xp = (I - Pi) X, never a difference of Grams."""
     X = Y[:, :no]
     YG = Y[:, no:]
     if YG.shape[1] == 0 or YG.shape[0] == 0:
         S = X.T @ X
     else:
         U, sv, _ = np.linalg.svd(YG, full_matrices=False)
-        keep = sv > sv_rtol * sv.max() if sv.size and sv.max() > 0 else np.zeros(sv.shape, dtype=bool)
+        rt = max(YG.shape) * np.finfo(np.float64).eps if sv_rtol is None else sv_rtol
+        keep = sv > rt * sv.max() if sv.size and sv.max() > 0 else np.zeros(sv.shape, dtype=bool)
         Uk = U[:, keep]
         Xp = X - Uk @ (Uk.T @ X)
         S = Xp.T @ Xp
@@ -287,15 +289,16 @@ def _next_groups_rows(level):
 
 
 def setup(rowptr, col, val, n, D1, agg, overlap=1, c_min=(2, 3, 4), n_coarse=2000, L_max=10,
-          thresh=0.1, schur_rtol=1e-12, keep_local=False, coarse_overlap=0, kappa=None, schur="gram",
-          sv_rtol=1e-10):
+          thresh=0.1, schur_rtol=1e-12, keep_local=False, coarse_overlap=0, kappa=None, schur="rows",
+          sv_rtol=None):
     """Build the multilevel hierarchy {A_l, G_l, P_l} of Algorithm 1.
 
-    schur = "gram" forms S~ from the Gram A~_i with an eigenvalue-thresholded
-    pseudo-inverse (`schur_rtol`); "rows" carries the rows of every G_l and
-    forms S~ by an orthogonal projector on them (`sv_rtol` on singular
-    values).  The two agree in exact arithmetic; the rows form resolves the
-    small singular directions the Gram squares away.
+    schur = "rows" (default) carries the rows of every G_l and forms S~ by an
+    orthogonal projector on the Gamma rows, cut at their numerical rank
+    (max(shape) eps of the largest singular value, or `sv_rtol` of it);
+    "gram" forms S~ from the Gram A~_i with an eigenvalue-thresholded
+    pseudo-inverse (`schur_rtol`).  The two agree in exact arithmetic; the
+    row form resolves the small singular directions the Gram squares away.
 
     With `kappa` given, each level's eigenvalue threshold is derived from it
     (Section 3.4): max{0.1, (kappa - n_color) / (n_color n_multiplicity)}, with

@@ -18,7 +18,8 @@ Every check runs the same seeded problem through both sides.  Structures
 The coarse-level A~_GG blocks are exactly singular (hundreds of eigenvalues
 at the rounding floor, none between 1e-14 and 1e-8 of the largest), so the
 pseudo-inverse of Eq. gevp-S is well defined; both sides reveal that null
-space (eigenvalues in the oracle, diagonal pivoting on the GPU).
+space (singular values of the Gamma rows in the oracle, diagonal pivoting of
+the Gram on the GPU).
 """
 import math
 

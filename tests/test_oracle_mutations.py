@@ -40,20 +40,34 @@ def _lemma_error(h):
 def test_dropped_multiplicity_breaks_lemma(monkeypatch):
     p = _prob()
     assert _lemma_error(_h(p)) <= 1e-14
+    orig = osetup.local_splitting_rows
+    monkeypatch.setattr(osetup, "local_splitting_rows",
+                        lambda Om, nz, sups, rows, M: orig(Om, nz, sups, rows, np.ones_like(M)))
+    assert _lemma_error(_h(p)) > 1e-3
+
+
+def test_dropped_multiplicity_breaks_lemma_gram_route(monkeypatch):
+    p = _prob()
+    assert _lemma_error(_h(p, schur="gram")) <= 1e-14
     orig = osetup.local_splitting
     monkeypatch.setattr(osetup, "local_splitting",
                         lambda Om, nz, sups, grams, M: orig(Om, nz, sups, grams, np.ones_like(M)))
-    assert _lemma_error(_h(p)) > 1e-3
+    assert _lemma_error(_h(p, schur="gram")) > 1e-3
 
 
 def test_schur_sign_error_breaks_svd_pin(monkeypatch):
     p = _prob()
 
-    def bad(Atil, no, rtol):
-        Aww, Awg, Agg = Atil[:no, :no], Atil[:no, no:], Atil[no:, no:]
-        return Aww + Awg @ np.linalg.pinv(Agg) @ Awg.T
+    def bad(Y, no, sv_rtol=None):  # the projected part added instead of removed
+        X, YG = Y[:, :no], Y[:, no:]
+        if YG.shape[1] == 0:
+            return X.T @ X
+        U, sv, _ = np.linalg.svd(YG, full_matrices=False)
+        Uk = U[:, sv > 1e-12 * sv.max()]
+        T = Uk.T @ X
+        return X.T @ X + T.T @ T
 
-    monkeypatch.setattr(osetup, "schur_complement", bad)
+    monkeypatch.setattr(osetup, "schur_complement_rows", bad)
     h = _h(p)
     L = h.levels[0]
     G, P = _brute.dense_G(p)
@@ -99,22 +113,24 @@ def test_missing_overlap_hop_breaks_bfs_pin():
 
 def test_permuted_coarse_columns_break_galerkin(monkeypatch):
     p = q1_2d(12, rotated_sqrtK(0.4, 0.05), agg=block_aggregates_2d(12, 3))
-    orig = osetup._next_groups
+    for route, name in (("rows", "_next_groups_rows"), ("gram", "_next_groups")):
+        orig = getattr(osetup, name)
 
-    def permuted(level):
-        # wrong index: coarse columns of every block reversed while propagating G
-        good = level.Z
-        level.Z = [Z[:, ::-1] for Z in good]
-        try:
-            return orig(level)
-        finally:
-            level.Z = good
+        def permuted(level, orig=orig):
+            # wrong index: coarse columns of every block reversed while propagating G
+            good = level.Z
+            level.Z = [Z[:, ::-1] for Z in good]
+            try:
+                return orig(level)
+            finally:
+                level.Z = good
 
-    monkeypatch.setattr(osetup, "_next_groups", permuted)
-    h = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, overlap=1, c_min=(3,), n_coarse=5, L_max=2)
-    P = h.levels[0].P.toarray()
-    gal = P.T @ h.levels[0].A.toarray() @ P
-    assert np.abs(h.levels[1].A.toarray() - gal).max() > 1e-6 * np.abs(gal).max()
+        monkeypatch.setattr(osetup, name, permuted)
+        h = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, overlap=1, c_min=(3,), n_coarse=5, L_max=2,
+                         schur=route)
+        P = h.levels[0].P.toarray()
+        gal = P.T @ h.levels[0].A.toarray() @ P
+        assert np.abs(h.levels[1].A.toarray() - gal).max() > 1e-6 * np.abs(gal).max(), route
 
 
 def test_transposed_local_factor_breaks_exact_single_block(monkeypatch):

@@ -39,7 +39,7 @@ def test_rows_reproduce_grams_and_splitting():
 def test_rows_match_gram_route_on_clean_gap():
     p = q1_2d(23, rotated_sqrtK(0.4, 1e-2), agg=block_aggregates_2d(23, 4))
     kw = dict(overlap=1, c_min=(2, 3), n_coarse=40)
-    hg = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, **kw)
+    hg = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, schur="gram", **kw)
     hr = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, p.agg, schur="rows", **kw)
     assert [L.n for L in hg.levels] == [L.n for L in hr.levels]
     for Lg, Lr in zip(hg.levels, hr.levels):
@@ -56,7 +56,31 @@ def test_rows_route_is_stable_where_gram_route_is_not():
     base = _fd48(schur="rows", sv_rtol=1e-10).levels[1].mu[0]
     for sv in (1e-8, 1e-12, 1e-14):
         assert np.abs(_fd48(schur="rows", sv_rtol=sv).levels[1].mu[0] - base).max() <= 1e-9
-    g12 = _fd48(schur_rtol=1e-12).levels[1].mu[0]
-    g13 = _fd48(schur_rtol=1e-13).levels[1].mu[0]
+    g12 = _fd48(schur="gram", schur_rtol=1e-12).levels[1].mu[0]
+    g13 = _fd48(schur="gram", schur_rtol=1e-13).levels[1].mu[0]
     assert np.abs(g12 - g13).max() > 1e-2
     assert np.abs(g13 - base).max() <= 1e-4  # the Gram route's finer cut lands near the row answer
+
+
+def test_schur_is_the_least_squares_minimum():
+    """u^T S~ u = min_v ||X u + Y_G v||^2 (the shorted operator of A~_i onto omega_i), by a least-squares
+    solve per random u: no projector, no Gram, no pseudo-inverse."""
+    from oracle.construct import local_splitting_rows
+
+    h = _fd48(schur="rows")
+    rng = np.random.default_rng(7)
+    for lvl in (0, 1):
+        L = h.levels[lvl]
+        for i in range(0, L.nagg, 5):
+            no = L.omega[i].shape[0]
+            Y = local_splitting_rows(L.Omega[i], L.nz[i], L.sups, L.rows, L.M)
+            X, YG = Y[:, :no], Y[:, no:]
+            for _ in range(2):
+                u = rng.standard_normal(no)
+                if YG.shape[1]:
+                    v = np.linalg.lstsq(YG, -X @ u, rcond=None)[0]
+                    best = float(np.sum((X @ u + YG @ v) ** 2))
+                else:
+                    best = float(np.sum((X @ u) ** 2))
+                got = float(u @ L.S[i] @ u)
+                assert abs(got - best) <= 1e-9 * float(np.sum((X @ u) ** 2)), (lvl, i, got, best)
