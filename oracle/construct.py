@@ -11,18 +11,20 @@ For each level l (Algorithm 1), while l < L_max - 1 and n_l > n_coarse:
   2. overlapping subdomains and Boolean PoU (Section 2.2, Eq. pou2);
   3. smoother blocks A_i = A_l(Omega_i, Omega_i) and their Cholesky factors
      (Section 2.2; the factors are applied by triangular solves);
-  4. SPSD splitting A~_i = sum_{rows in nz_i} g^T g / M (Lemma);
+  4. SPSD splitting A~_i = sum_{rows in nz_i} g^T g / M (Lemma), kept as its
+     rows Y = [X Y_G] (the rows of nz_i scaled by 1/sqrt(M)), A~_i = Y^T Y;
   5. reduced generalized eigenproblem on omega_i (Eq. gevp-S):
-     A_ww u = lambda S~ u with S~ the Schur complement of A~_i onto omega_i;
-     solved as S~ u = mu A_ww u, mu = 1/lambda ascending, so the largest
-     lambda come first;
+     A_ww u = lambda S~ u with S~ the Schur complement of A~_i onto omega_i,
+     X^T (I - Pi) X with Pi the projector onto the Gamma rows (the
+     pseudo-inverse reading); solved as S~ u = mu A_ww u, mu = 1/lambda
+     ascending, so the largest lambda come first;
   6. selection: all lambda > thresh, at most max(1, floor(|omega_i|/c_l))
      (Section 3.4); Z_i normalised so Z_i^T A_ww Z_i = I and the first entry
      within (1 - 1e-6) of the column's largest magnitude is positive;
   7. P_l = [R_{omega_1}^T Z_1 ... ] (Eq. mg-p), columns ordered by aggregate
      then by ascending mu;
-  8. G_{l+1} = G_l P_l, A_{l+1} = G_{l+1}^T G_{l+1} (Section 3.1,
-     "Multilevel method").
+  8. G_{l+1} = G_l P_l (its rows carried group by group), A_{l+1} =
+     G_{l+1}^T G_{l+1} (Section 3.1, "Multilevel method").
 
 The coarsest level is factored densely (Cholesky).
 """
