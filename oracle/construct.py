@@ -19,7 +19,8 @@ For each level l (Algorithm 1), while l < L_max - 1 and n_l > n_coarse:
      pseudo-inverse reading); solved as S~ u = mu A_ww u, mu = 1/lambda
      ascending, so the largest lambda come first;
   6. selection: all lambda > thresh, at most max(1, floor(|omega_i|/c_l))
-     (Section 3.4); Z_i normalised so Z_i^T A_ww Z_i = I and the first entry
+     (Section 3.4), thresh fixed or derived per level from kappa; an
+     aggregate may keep none (k_i = 0); Z_i normalised so Z_i^T A_ww Z_i = I and the first entry
      within (1 - 1e-6) of the column's largest magnitude is positive;
   7. P_l = [R_{omega_1}^T Z_1 ... ] (Eq. mg-p), columns ordered by aggregate
      then by ascending mu;
