@@ -155,3 +155,20 @@ def test_two_level_with_threshold_selection_is_size_independent():
         _, info = oracle.pcg(h, seeded_rhs(p.n, 1, 6)[:, 0], tol=1e-8)
         its.append(info["iters"])
     assert max(its) - min(its) <= 1 and max(its) <= 14, its
+
+
+def test_two_level_with_threshold_selection_is_angle_robust():
+    """The same two-level method across the anisotropy angle (theta = 0, pi/6, pi/4 on 48^2 at eps = 1e-5): the
+    bound does not see theta, and the PCG counts stay within 10-18 (12-15 here; a Schur complement that ignores
+    the Gamma rows takes 320-1000)."""
+    from oracle.structure import standard_aggregation
+    from inputs import seeded_rhs
+
+    for theta in (0.0, math.pi / 6, math.pi / 4):
+        p = fd_2d(48, theta, 1e-5)
+        sups, _ = row_groups_from_csr(p.rowptr, p.col, p.val, p.n, p.D1)
+        agg, _ = standard_aggregation(sups, p.n, 1)
+        h = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, agg, overlap=1, c_min=(1,), L_max=2, n_coarse=1,
+                         kappa=50.0)
+        _, info = oracle.pcg(h, seeded_rhs(p.n, 1, 6)[:, 0], tol=1e-8)
+        assert 10 <= info["iters"] <= 18, (theta, info["iters"])
