@@ -33,6 +33,9 @@ CASES = {
     # isotropic, standard aggregation chosen by each side: aggregates with k_i = 0 on levels 0 and 1 (no
     # lambda above the threshold), left out of the next level's dofs, rows and block graph
     "fd_16_iso": dict(N=16, theta=math.pi / 6, eps=1.0, bs=0, c_min=(2, 3, 4), n_coarse=20, kappa=50.0),
+    # two levels at the diagonal angle, every eigenvector above the threshold kept (c_min = 1): level 0 is well
+    # posed and the coarsest level is solved exactly, so the whole hierarchy and the solve have full parity
+    "fd_48_2lvl": dict(N=48, theta=math.pi / 4, eps=1e-5, bs=0, c_min=(1,), n_coarse=1, kappa=50.0, L_max=2),
 }
 
 
@@ -133,10 +136,11 @@ def _both(amg, c):
     if agg is None:
         sups, _ = row_groups_from_csr(p.rowptr, p.col, p.val, p.n, p.D1)
         agg, _ = oracle.standard_aggregation(sups, p.n, 1)
+    L_max = c.get("L_max", 10)
     ho = oracle.setup(p.rowptr, p.col, p.val, p.n, p.D1, agg, overlap=1, c_min=c["c_min"],
-                      n_coarse=c["n_coarse"], keep_local=True, kappa=c["kappa"])
+                      n_coarse=c["n_coarse"], keep_local=True, kappa=c["kappa"], L_max=L_max)
     H = amg.Hierarchy.from_problem(p, overlap=1, c_min=c["c_min"], n_coarse=c["n_coarse"], kappa=c["kappa"],
-                                   precision=amg.FP64)
+                                   precision=amg.FP64, L_max=L_max)
     return p, ho, H
 
 
