@@ -40,7 +40,7 @@ WORKLOAD = "q1_512_rot"
 # DRAM bytes per V-cycle by kernel family, from ncu captures of WORKLOAD
 # (dram__bytes_read.sum + dram__bytes_write.sum summed over one V-cycle's
 # launches; profiles/).  Entries are removed when their kernels change.
-TRAFFIC = {"k_seg": 881.19e6, "k_ell": 41.80e6, "k_dense": 29.42e6}  # profiles/dram_solve_kernels_q1_512_rot.md
+TRAFFIC = {"k_seg": 881.19e6, "k_ell": 41.80e6, "k_dense": 29.42e6}
 
 
 def parse_args():

@@ -580,7 +580,11 @@ __global__ void k_gep(const int32_t* __restrict__ mdim, const int32_t* __restric
       }
       tm.sync();
     }
-    // implicit QL on (d, e): e[i] couples i and i+1
+    // implicit QL on (d, e): e[i] couples i and i+1.  This is the published
+    // implicit QL method with Wilkinson shifts (Bowdler, Martin, Reinsch and
+    // Wilkinson, Numer. Math. 11 (1968); EISPACK tql2): per sweep the shift g,
+    // the chain of plane rotations from the bottom of the unreduced block up,
+    // and the split test on |e|; rotations are accumulated into V by the team.
     for (int guard = 0; guard < 64 * n + 64; ++guard) {
       if (tm.rank == 0) {
         int l = ctl[2], iter = ctl[3], nrot = 0, fin = 0;
