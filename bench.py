@@ -40,7 +40,7 @@ WORKLOAD = "q1_512_rot"
 # DRAM bytes per V-cycle by kernel family, from ncu captures of WORKLOAD
 # (dram__bytes_read.sum + dram__bytes_write.sum summed over one V-cycle's
 # launches; profiles/).  Entries are removed when their kernels change.
-TRAFFIC = {"k_seg": 881.19e6, "k_ell": 41.80e6, "k_dense": 29.42e6}
+TRAFFIC = {}
 
 
 def parse_args():
@@ -512,7 +512,7 @@ def run_ours(args):
     n = prob.n
     t0 = time.time()
     H = amg.Hierarchy.from_problem(prob, overlap=cfg["overlap"], c_min=cfg["c_min"], n_coarse=cfg["n_coarse"],
-                                   thresh=cfg["thresh"], kappa=cfg.get("kappa", 0.0), agg_passes=cfg.get("agg_passes", 1), precision=amg.MIXED32, tune_cache=args.tune_cache,
+                                   thresh=cfg["thresh"], kappa=cfg.get("kappa", 0.0), agg_passes=cfg.get("agg_passes", 1), precision=amg.MIXED16, tune_cache=args.tune_cache,
                                    coarse_overlap=cfg.get("coarse_overlap", 0),
                                    tune={"timed": 1, "defaults": 0, "staged": 2, "shifted": 3, "lanes": 4}[args.tune_mode],
                                    deterministic=1 if args.deterministic else 0)
@@ -553,27 +553,30 @@ def run_ours(args):
     def maxrank(v):
         return replica_max(v, world)
 
-    # warm-up (both precisions: graph capture, first-touch)
-    for prec in (amg.FP64, amg.MIXED32):
+    # warm-up (every precision: graph capture, first-touch)
+    for prec in (amg.FP64, amg.MIXED32, amg.MIXED16):
         timed(prec, 0, args.warmup, B, X)
+    HEAD = amg.MIXED16  # the headline precision: FP16 matrices, FP32 vectors, FP64 flexible CG
     if args.profile_only:
-        H.set_precision(amg.MIXED32)
+        H.set_precision(HEAD)
         # the NVTX range lets a profiler select these V-cycles (setup's own
         # tuning launches run the same kernels)
         torch.cuda.nvtx.range_push("vcycle_profile")
-        ms, by = H.profile_vcycle(10)
+        ms, by, _ = H.profile_vcycle(10, graph=True)
         torch.cuda.nvtx.range_pop()
         print(json.dumps({"stats": stats, "profile_ms": ms.tolist(), "profile_bytes": by.tolist()}))
         return
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)  # nvidia-smi's own start-up, so that its samples fall inside the timed region
-    t_mix, w_mix, inf_mix, launches = timed(amg.MIXED32, args.warmup, args.steps, B, X)
+    t_mix, w_mix, inf_mix, launches = timed(HEAD, args.warmup, args.steps, B, X)
     clocks = sampler.stop()
+    t_32, w_32, inf_32, _ = timed(amg.MIXED32, args.warmup, args.steps, B, X)
     t_64, w_64, inf_64, _ = timed(amg.FP64, args.warmup, args.steps, B, X)
     t_mix = maxrank(t_mix)
+    t_32 = maxrank(t_32)
     t_64 = maxrank(t_64)
-    for inf in inf_mix + inf_64:
+    for inf in inf_mix + inf_32 + inf_64:
         assert inf["status"] == 0 and inf["relres_true"] <= 1e-8, inf
     fallbacks = sum(i["fallback"] for i in inf_mix)
     it_mix = [i["iters"] for i in inf_mix]
@@ -581,60 +584,86 @@ def run_ours(args):
     solves = args.steps * world
     value = solves / t_mix
     fp64_value = solves / t_64
+    m32_value = solves / t_32
     vc_mix = sum(i + 1 for i in it_mix) * world / t_mix
     vc_64 = sum(i + 1 for i in it_64) * world / t_64
     lat = sorted(i["solve_ms"] for i in inf_mix)
 
-    # per-step V-cycle profile (CUDA events between launches) -> roofline
-    H.set_precision(amg.MIXED32)
-    ms, by = H.profile_vcycle(10)
+    # per-step V-cycle profile -> roofline.  The primary figures replay the
+    # cycle as a CUDA graph with event record nodes between its kernels (the
+    # solve replays its cycle as a graph too); the eager profile (events
+    # between separately launched kernels, host launch gaps included) is
+    # reported beside it.
+    H.set_precision(HEAD)
+    ms, by, cyc_graph_ms = H.profile_vcycle(10, graph=True)
+    ms_e, by_e = H.profile_vcycle(10)
     # kernel families by profile slot: slot 6 is the persistent tail (one
     # cooperative launch for every level from its first), slot 2 the two
     # residuals (k_seg over block rows or grouped k_apply), slots 1/5 casts
     forms = [c["form"] for c in stats["coarse_A"]]
     dense_l = stats.get("dense_tail", {}).get("mixed", {}).get("from", 0)
-    fam_ms, fam_by, fam_n = {}, {}, {}
-    for l in range(ms.shape[0]):
-        for k in range(ms.shape[1]):
-            if ms[l, k] <= 0:
-                continue
-            if k == 6:
-                fam, nk = "k_persistent", 1
-            elif k == 0 and dense_l > 0 and l == dense_l:
-                fam, nk = "k_dense", 1
-            elif k == 2:
-                fam, nk = {"block rows": "k_seg", "ELL rows": "k_ell"}.get(forms[l], "k_apply"), 2
-            elif k in (1, 5):
-                fam, nk = "k_cast", 1
-            else:
-                fam, nk = "k_seg", 1
-            fam_ms[fam] = fam_ms.get(fam, 0.0) + float(ms[l, k])
-            fam_by[fam] = fam_by.get(fam, 0.0) + float(by[l, k])
-            fam_n[fam] = fam_n.get(fam, 0) + nk
-    vcyc_ms = float(ms.sum())
+
+    def families(ms, by):
+        fam_ms, fam_by, fam_n = {}, {}, {}
+        for l in range(ms.shape[0]):
+            for k in range(ms.shape[1]):
+                if ms[l, k] <= 0:
+                    continue
+                if k == 6:
+                    fam, nk = "k_persistent", 1
+                elif k == 0 and dense_l > 0 and l == dense_l:
+                    fam, nk = "k_dense", 1
+                elif k == 2:
+                    fam, nk = {"block rows": "k_seg", "ELL rows": "k_ell"}.get(forms[l], "k_apply"), 2
+                elif k in (1, 5):
+                    fam, nk = "k_cast", 1
+                else:
+                    fam, nk = "k_seg", 1
+                fam_ms[fam] = fam_ms.get(fam, 0.0) + float(ms[l, k])
+                fam_by[fam] = fam_by.get(fam, 0.0) + float(by[l, k])
+                fam_n[fam] = fam_n.get(fam, 0) + nk
+        return fam_ms, fam_by, fam_n
+
+    fam_ms, fam_by, fam_n = families(ms, by)
+    fam_ms_e, fam_by_e, _ = families(ms_e, by_e)
     peak, peak_kind = hbm_peak()
     top = max(fam_ms, key=fam_ms.get)
-    kdesc = {"k_seg": "k_seg (batched gather-GEMV-scatter: RAS, RAS-T, P, R, block-row residuals; FP32)",
+    kdesc = {"k_seg": "k_seg (batched gather-GEMV-scatter: RAS, RAS-T, P, R, block-row residuals; FP16 matrices "
+                      "where setup timed them faster, else FP32; FP32 vectors)",
              "k_apply": "k_apply (grouped G then G^T residual; FP32)",
              "k_persistent": "k_persistent (cooperative V-cycle tail: every phase of the coarse levels; FP32)",
              "k_dense": "k_dense (dense V-cycle tail GEMV; FP32)",
              "k_ell": "k_ell (level-0 residual by ELL rows of A; FP32)",
              "k_cast": "k_cast"}
-    kms, kby = fam_ms[top], fam_by[top]
+    # the event record nodes of the marked graph add their own gaps, so the
+    # family's time inside the plain graph is taken as its share of the
+    # marked cycle applied to the plain cycle's replay time
+    kby = fam_by[top]
+    share = fam_ms[top] / float(ms.sum())
+    kms = cyc_graph_ms * share
     achieved = kby / (kms * 1e-3) / 1e9
     # DRAM bytes per V-cycle of a kernel family from an ncu capture of this
     # workload (profiles/); valid only while those kernels are unchanged
     traffic = (TRAFFIC.get(top) if args.workload == WORKLOAD and args.N is None and not args.deterministic
                and args.tune_mode == "timed" else None)
+    cyc_bytes = float(by.sum())
+    kms_e = fam_ms_e.get(top, 0.0)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per V-cycle (kernel family)",
                 "kernel": kdesc.get(top, top), "launches_per_vcycle": fam_n[top],
                 "bytes_per_vcycle": kby, "ms_per_vcycle": kms,
+                "timing": ("V-cycle replayed as a CUDA graph (CUDA events around the replay); the family's time is "
+                           "its share of the same cycle replayed with event record nodes between its kernels"),
+                "share_of_vcycle": share,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
                 "families": {f: {"ms": round(fam_ms[f], 4), "gbs": round(fam_by[f] / (fam_ms[f] * 1e-3) / 1e9, 1),
                                  "launches": fam_n[f]} for f in fam_ms},
-                "vcycle": {"ms": vcyc_ms, "bytes": float(by.sum()),
-                           "achieved_gbs": float(by.sum()) / (vcyc_ms * 1e-3) / 1e9}}
+                "eager": {"ms": round(kms_e, 4),
+                          "frac": (fam_by_e.get(top, 0.0) / (kms_e * 1e-3) / 1e9 / peak) if kms_e > 0 else None,
+                          "timing": "separate launches, CUDA events between them (host launch gaps included)"},
+                "vcycle": {"ms_graph": cyc_graph_ms, "ms_marked_graph": float(ms.sum()), "bytes": cyc_bytes,
+                           "achieved_gbs": cyc_bytes / (cyc_graph_ms * 1e-3) / 1e9,
+                           "frac": cyc_bytes / (cyc_graph_ms * 1e-3) / 1e9 / peak}}
     slot_names = {0: "ras_coarse_or_dense", 1: "cast_in", 2: "residual_applies", 3: "restrict", 4: "prolong",
                   5: "cast_out", 6: "persistent_tail", 7: "rast"}
     vprof = []
@@ -647,7 +676,7 @@ def run_ours(args):
     Bp = torch.empty((nsol, n), dtype=torch.float64, pin_memory=True)
     Bp.copy_(B.cpu())
     Xp = torch.zeros_like(Bp).pin_memory()
-    t_e2e, w_e2e, inf_e2e, _ = timed(amg.MIXED32, args.warmup, args.steps, Bp, Xp)
+    t_e2e, w_e2e, inf_e2e, _ = timed(HEAD, args.warmup, args.steps, Bp, Xp)
     t_e2e = maxrank(max(t_e2e, w_e2e))
     e2e = {"value": solves / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
 
@@ -706,13 +735,17 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_mix / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": workload_desc(cfg), "precision": "FP32 V-cycle, FP64 flexible CG",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32+f64", "data": "synthetic",
+        "config": {"workload": workload_desc(cfg),
+                   "precision": "MIXED16: FP16 smoother rows, basis and coarse block rows, FP32 vectors and sums, "
+                                "FP64 flexible CG",
                    "l2": "inputs larger than L2: one V-cycle moves %.2f GB" % (float(by.sum()) / 1e9),
                    "parallelism": f"replicas x{world}",
                    "mode": "deterministic (no atomics)" if args.deterministic else "default"},
         "fp64": {"value": fp64_value, "unit": "solves/s", "ms_per_step": t_64 / args.steps * 1e3,
                  "iters": it_64},
+        "mixed32": {"value": m32_value, "unit": "solves/s", "ms_per_step": t_32 / args.steps * 1e3,
+                    "iters": [i["iters"] for i in inf_32]},
         "mixed_over_fp64": value / fp64_value,
         "vcycles_per_s": {"mixed": vc_mix, "fp64": vc_64},
         "iters": it_mix, "mixed_fp64_fallbacks": fallbacks, "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},

@@ -59,6 +59,15 @@ extern "C" {
  * and fine-level A-apply stay FP64; the coarsest solve stays FP64.         */
 #define AMGDD_FP64 0
 #define AMGDD_MIXED32 1
+/* MIXED16: MIXED32 with the smoother rows, the basis (P and P^T) and the
+ * block rows of coarse A read from FP16 copies (round to nearest, widened
+ * to FP32 and summed in FP32): half the bytes of those matrices per
+ * V-cycle.  A level holding an entry beyond the FP16 range keeps FP32.
+ * The flexible FP64 CG wins the accuracy back (the same stall guard as
+ * MIXED32).  Batched solves (nrhs > 1) and the persistent V-cycle tail read
+ * the FP32 copies.  The FP16 copies are built at setup (precision =
+ * MIXED16) or at the first amgdd_set_precision(MIXED16).                  */
+#define AMGDD_MIXED16 2
 
 /* ---- inputs ----------------------------------------------------------- */
 /* G in CSR form.  rowptr has m+1 entries (rowptr[0] = 0, nondecreasing,
@@ -230,6 +239,12 @@ int amgdd_solve(amgdd_hierarchy* h, const double* b, int nrhs, double tol, doubl
 /* Switches the precision used by later solves (the hierarchy stores both). */
 int amgdd_set_precision(amgdd_hierarchy* h, int precision);
 
+/* Sets the CG iteration limit of later solves (params.max_iter at setup);
+ * with tol = 0 a solve then runs exactly max_iter iterations, which lets a
+ * caller compare iterates at a fixed count.  Errors: INVALID_ARG for
+ * max_iter < 1.                                                            */
+int amgdd_set_max_iter(amgdd_hierarchy* h, int max_iter);
+
 /* ---- single steps of the cycle (device FP64 vectors; for testing) ---- */
 #define AMGDD_OP_A 0        /* y = A_l x                    (Eq. 1)       */
 #define AMGDD_OP_RAS 1      /* y = M_RAS^{-1} x             (Eq. ras)     */
@@ -257,8 +272,11 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
  * the library holds that array until the process exits.  Levels whose
  * input or output vector has more than 131072 entries are rejected with
  * AMGDD_ERR_INVALID_ARG in MIXED32 (FP64 needs no staging and has no limit).
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  All
+ * The hierarchy's device must be the current device (AMGDD_ERR_INVALID_ARG
+ * otherwise).  The first call on a device looks up the array's device
+ * address with that device current and keeps it for the process; make that
+ * first call before any stream capture (a cudaDeviceReset invalidates the
+ * kept address, as it invalidates every hierarchy on that device).  All
  * calls share the array: calls that overlap on the GPU (other streams,
  * other host threads) race on it.  The call synchronises `stream` before
  * returning, as amgdd_apply does.                                          */
@@ -276,6 +294,9 @@ typedef struct {
   int64_t g_vals;      /* stored values of G_l (rows x support)           */
   int64_t w_vals;      /* stored values of the smoother, sum |omega||Omega| */
   int is_coarsest;
+  int64_t g_sup_len;   /* sum over row groups of |S_g| (AMGDD_ARR_G_IDX)  */
+  int64_t a_nnz;       /* structural nonzeros of A_l (AMGDD_ARR_A_IDX)    */
+  int64_t p_nnz;       /* structural nonzeros of P_l, sum |omega_i| k_i   */
 } amgdd_level_desc;
 
 int amgdd_num_levels(const amgdd_hierarchy* h);
@@ -298,10 +319,31 @@ int amgdd_level_describe(const amgdd_hierarchy* h, int level, amgdd_level_desc* 
 #define AMGDD_ARR_K 4
 #define AMGDD_ARR_Z 5
 #define AMGDD_ARR_MU 6
+/* Structural patterns (Section 3.1: G_{l+1} = G_l P_l, A_l = G_l^T G_l;
+ * Eq. mg-p for P), every level:
+ *   G_PTR int64[ngroups+1], G_IDX int32[g_sup_len]: the support S_g of each
+ *              row group of G_l (rows with one structural support; ascending
+ *              node ids; groups in the library's order, and rows with
+ *              one support may fall in several groups).  Rows that carry
+ *              D1 (level 0) are one-node supports.  Compression changes
+ *              the rows a group stores, never its support.
+ *   A_PTR int64[n+1], A_IDX int32[a_nnz]: CSR pattern of A_l, j ~ k iff a
+ *              support holds both (ascending columns).
+ *   P_PTR int64[n+1], P_IDX int32[p_nnz]: CSR pattern of P_l (not on the
+ *              coarsest level): row j spans the k_a columns of its
+ *              aggregate a, numbered by aggregate, then ascending mu.     */
+#define AMGDD_ARR_G_PTR 7
+#define AMGDD_ARR_G_IDX 8
+#define AMGDD_ARR_A_PTR 9
+#define AMGDD_ARR_A_IDX 10
+#define AMGDD_ARR_P_PTR 11
+#define AMGDD_ARR_P_IDX 12
 int amgdd_level_export(const amgdd_hierarchy* h, int level, int which, void* dst, size_t cap);
 
 /* JSON summary (levels, n_l, row groups, stored values, operator
- * complexity, algorithmic bytes per V-cycle, setup time) into json[cap].  */
+ * complexity, algorithmic bytes per V-cycle, setup time) into json[cap].
+ * "process_device_allocs" counts the device allocations the library has
+ * made in this process so far (all hierarchies and threads).             */
 int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap);
 
 /* Algorithmic bytes one V-cycle must move in the current precision, and
@@ -316,9 +358,14 @@ int amgdd_bytes_model(const amgdd_hierarchy* h, double* vcycle_bytes, double* ap
  * (bytes[l*8 + slot]: stored matrix values, index arrays, and one pass over
  * each input and output vector).  Slots: 0 RAS (or the coarsest solve),
  * 1 residual copies (casts on the coarsest level), 2 residual A-applies,
- * 3 restriction, 4 prolongation, 5 cast back (coarsest level), 7 RAS-T.
- * cap >= 8 * amgdd_num_levels(h).                                        */
-int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes, int cap);
+ * 3 restriction, 4 prolongation, 5 cast back (coarsest level), 6 the
+ * persistent tail, 7 RAS-T.  graph = 0: the launches run eagerly, so a step's
+ * time includes host launch gaps; graph != 0: the marked cycle is captured
+ * once in a CUDA graph (the marks become event record nodes) and replayed,
+ * as the solve replays its cycle, and when cap > 8 * levels, ms[8 * levels]
+ * receives the mean time of one replay of the same cycle captured without
+ * marks.  cap >= 8 * amgdd_num_levels(h).                                 */
+int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, int graph, double* ms, double* bytes, int cap);
 
 /* Kernels this library has launched in the process so far (a replay of a
  * captured CUDA graph counts every kernel in it).                         */

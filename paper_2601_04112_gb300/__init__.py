@@ -23,12 +23,13 @@ AMGDD_OK = 0
 STATUS = {0: "ok", -1: "invalid argument", -2: "not SPD", -3: "non-finite", -4: "CG breakdown",
           -5: "no convergence", -6: "out of device memory", -7: "CUDA error", -8: "internal error"}
 HOST, DEVICE = 0, 1
-FP64, MIXED32 = 0, 1
+FP64, MIXED32, MIXED16 = 0, 1, 2
 OP_A, OP_RAS, OP_RAST, OP_RESTRICT, OP_PROLONG, OP_VCYCLE, OP_COARSE, OP_M2 = range(8)
 ARR_AGG, ARR_OMEGA_PTR, ARR_OMEGA_IDX, ARR_NOMEGA, ARR_K, ARR_Z, ARR_MU = range(7)
+ARR_G_PTR, ARR_G_IDX, ARR_A_PTR, ARR_A_IDX, ARR_P_PTR, ARR_P_IDX = range(7, 13)
 
 EXPORTED = [
-    "amgdd_params_default", "amgdd_setup", "amgdd_solve", "amgdd_set_precision", "amgdd_apply",
+    "amgdd_params_default", "amgdd_setup", "amgdd_solve", "amgdd_set_precision", "amgdd_set_max_iter", "amgdd_apply",
     "amgdd_num_levels", "amgdd_level_describe", "amgdd_level_export", "amgdd_hierarchy_stats",
     "amgdd_bytes_model", "amgdd_free", "amgdd_status_string", "amgdd_last_error", "amgdd_profile_vcycle",
     "amgdd_kernel_launches", "amgdd_apply_noalloc", "amgdd_device_bytes", "amgdd_server_params_default",
@@ -70,7 +71,8 @@ class LevelDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nagg", ctypes.c_int64), ("n_next", ctypes.c_int64),
                 ("omega_len", ctypes.c_int64), ("z_len", ctypes.c_int64), ("ngroups", ctypes.c_int64),
                 ("g_rows", ctypes.c_int64), ("g_vals", ctypes.c_int64), ("w_vals", ctypes.c_int64),
-                ("is_coarsest", ctypes.c_int)]
+                ("is_coarsest", ctypes.c_int), ("g_sup_len", ctypes.c_int64), ("a_nnz", ctypes.c_int64),
+                ("p_nnz", ctypes.c_int64)]
 
 
 _lib = None
@@ -90,6 +92,7 @@ def load_library(path: str = LIB_PATH):
     lib.amgdd_setup.argtypes = [ctypes.POINTER(Csr), vp, vp, i32, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]
     lib.amgdd_solve.argtypes = [vp, vp, i32, dbl, vp, vp, ctypes.POINTER(Info)]
     lib.amgdd_set_precision.argtypes = [vp, i32]
+    lib.amgdd_set_max_iter.argtypes = [vp, i32]
     lib.amgdd_apply.argtypes = [vp, i32, i32, vp, vp, vp]
     lib.amgdd_apply_noalloc.argtypes = [vp, i32, i32, vp, vp, vp]
     lib.amgdd_apply_noalloc.restype = i32
@@ -107,7 +110,7 @@ def load_library(path: str = LIB_PATH):
     lib.amgdd_status_string.argtypes = [i32]
     lib.amgdd_status_string.restype = ctypes.c_char_p
     lib.amgdd_last_error.restype = ctypes.c_char_p
-    lib.amgdd_profile_vcycle.argtypes = [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl), i32]
+    lib.amgdd_profile_vcycle.argtypes = [vp, i32, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl), i32]
     lib.amgdd_profile_vcycle.restype = i32
     lib.amgdd_kernel_launches.restype = ctypes.c_int64
     lib.amgdd_device_bytes.argtypes = [vp, i32]
@@ -125,7 +128,8 @@ def load_library(path: str = LIB_PATH):
     for name in ("amgdd_server_create", "amgdd_server_add_operator", "amgdd_server_submit", "amgdd_server_poll",
                  "amgdd_server_stats"):
         getattr(lib, name).restype = i32
-    for name in ("amgdd_setup", "amgdd_solve", "amgdd_set_precision", "amgdd_apply", "amgdd_num_levels",
+    for name in ("amgdd_setup", "amgdd_solve", "amgdd_set_precision", "amgdd_set_max_iter", "amgdd_apply",
+                 "amgdd_num_levels",
                  "amgdd_level_describe", "amgdd_level_export", "amgdd_hierarchy_stats", "amgdd_bytes_model"):
         getattr(lib, name).restype = i32
     lib.amgdd_struct_size.argtypes = [i32]
@@ -274,6 +278,9 @@ class Hierarchy:
     def set_precision(self, precision: int):
         _check(self._lib.amgdd_set_precision(self._h, int(precision)))
 
+    def set_max_iter(self, max_iter: int):
+        _check(self._lib.amgdd_set_max_iter(self._h, int(max_iter)))
+
     def solve(self, b, x=None, tol=1e-8, stream=None):
         """Solve A x = b (b: n or n x nrhs, column-major); returns (x, infos)."""
         nrhs = 1 if b.ndim == 1 else b.shape[1]
@@ -329,7 +336,10 @@ class Hierarchy:
         nag = d["nagg"]
         size = {ARR_AGG: (d["n"], np.int32), ARR_OMEGA_PTR: (nag + 1, np.int64),
                 ARR_OMEGA_IDX: (d["omega_len"], np.int32), ARR_NOMEGA: (nag, np.int32), ARR_K: (nag, np.int32),
-                ARR_Z: (d["z_len"], np.float64)}
+                ARR_Z: (d["z_len"], np.float64), ARR_G_PTR: (d["ngroups"] + 1, np.int64),
+                ARR_G_IDX: (d["g_sup_len"], np.int32), ARR_A_PTR: (d["n"] + 1, np.int64),
+                ARR_A_IDX: (d["a_nnz"], np.int32), ARR_P_PTR: (d["n"] + 1, np.int64),
+                ARR_P_IDX: (d["p_nnz"], np.int32)}
         if which == ARR_MU:
             cnt = int(self.export(level, ARR_NOMEGA).sum())
             size[ARR_MU] = (cnt, np.float64)
@@ -343,13 +353,19 @@ class Hierarchy:
         _check(self._lib.amgdd_hierarchy_stats(self._h, buf, len(buf)))
         return json.loads(buf.value.decode())
 
-    def profile_vcycle(self, reps: int = 10):
-        """Per (level, slot) mean device ms and algorithmic bytes of one V-cycle."""
+    def profile_vcycle(self, reps: int = 10, graph: bool = False):
+        """Per (level, slot) mean device ms and algorithmic bytes of one V-cycle.
+
+        graph=False: eager launches with events between them.  graph=True: the
+        marked cycle replayed as a CUDA graph; also returns the mean ms of one
+        replay of the unmarked cycle graph as a third value."""
         nl = self.num_levels
-        ms = (ctypes.c_double * (8 * nl))()
-        by = (ctypes.c_double * (8 * nl))()
-        _check(self._lib.amgdd_profile_vcycle(self._h, int(reps), ms, by, 8 * nl))
-        return np.array(ms).reshape(nl, 8), np.array(by).reshape(nl, 8)
+        cap = 8 * nl + 1
+        ms = (ctypes.c_double * cap)()
+        by = (ctypes.c_double * cap)()
+        _check(self._lib.amgdd_profile_vcycle(self._h, int(reps), 1 if graph else 0, ms, by, cap))
+        out = np.array(ms)[:8 * nl].reshape(nl, 8), np.array(by)[:8 * nl].reshape(nl, 8)
+        return (*out, float(ms[8 * nl])) if graph else out
 
     def bytes_model(self):
         v, a = ctypes.c_double(), ctypes.c_double()

@@ -32,6 +32,9 @@ namespace amgdd {
 static thread_local std::string g_last_error;
 thread_local int* g_err_word = nullptr;
 thread_local int64_t g_alloc_bytes = 0;
+static std::atomic<int64_t> g_alloc_calls{0};
+int64_t device_alloc_count() { return g_alloc_calls.load(); }
+void note_device_alloc() { g_alloc_calls.fetch_add(1); }
 thread_local bool g_pdl = false;
 
 // Setup-time tuning context: whether to time alternatives, the problem/GPU
@@ -987,6 +990,13 @@ struct amgdd_hierarchy {
 
 namespace {
 
+// MIXED32 and MIXED16 run the V-cycle on FP32 vectors under the flexible FP64
+// CG; MIXED16 reads the gather-GEMV matrices in FP16 where a level has them.
+bool mixed(const amgdd_hierarchy& h) { return h.precision != AMGDD_FP64; }
+bool use16(const amgdd_hierarchy& h, const Level& L, bool f32) {
+  return f32 && h.precision == AMGDD_MIXED16 && L.h16;
+}
+
 // ---------------------------------------------------------------------------
 // Compression of the row groups of one level: pivoted Cholesky of each Gram.
 int compress(Level& L, cudaStream_t s) {
@@ -1571,17 +1581,19 @@ int build_coarsest(amgdd_hierarchy& h, Level& L, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Algorithmic bytes: stored matrix values, index arrays, and one pass over
 // each input and output vector (two for read-modify-write outputs).
-static double seg_bytes(const SegPlan& p, int64_t nin, int64_t nout, bool rmw, size_t esz) {
-  return (double)p.mat_len * esz + (double)(p.in_len + p.out_len) * 4.0 + (double)nin * esz +
+// esz: bytes of a vector entry; msz: of a stored matrix entry (0: esz; 2
+// for the FP16 copies of MIXED16).
+static double seg_bytes(const SegPlan& p, int64_t nin, int64_t nout, bool rmw, size_t esz, size_t msz = 0) {
+  return (double)p.mat_len * (msz ? msz : esz) + (double)(p.in_len + p.out_len) * 4.0 + (double)nin * esz +
          (double)nout * esz * (rmw ? 2.0 : 1.0);
 }
 
 // One RAS-T: the scatter-add form, or the stored products plus the per-node
 // gather (positions, pointers, the stored values and x read and written).
-static double rast_bytes(const Level& L, size_t esz) {
-  if (L.yd64.p == nullptr) return seg_bytes(L.rast, L.n, L.n, true, esz);
+static double rast_bytes(const Level& L, size_t esz, size_t msz = 0) {
+  if (L.yd64.p == nullptr) return seg_bytes(L.rast, L.n, L.n, true, esz, msz);
   const double tot = (double)L.om_ptr.back();
-  return seg_bytes(L.rast_det, L.n, (int64_t)tot, false, esz) + tot * (4.0 + esz) + (L.n + 1) * 8.0 +
+  return seg_bytes(L.rast_det, L.n, (int64_t)tot, false, esz, msz) + tot * (4.0 + esz) + (L.n + 1) * 8.0 +
          2.0 * L.n * esz;
 }
 
@@ -1598,19 +1610,31 @@ static double apply_bytes(const Level& L, size_t esz) {
 
 // One residual s = r - A x of a non-coarsest level, with the copy of r that
 // the matrix-free form needs.
-static double resid_bytes(const Level& L, size_t esz) {
+static double resid_bytes(const Level& L, size_t esz, size_t msz = 0) {
   if (L.use_ell) return (double)L.n * L.ell_w * (esz + 4.0) + 3.0 * L.n * esz;
-  if (L.has_blk) return seg_bytes(L.ablk, L.n, L.n, true, esz);
+  if (L.has_blk) return seg_bytes(L.ablk, L.n, L.n, true, esz, msz);
   return apply_bytes(L, esz) + (double)L.n * esz;
 }
 
 // y = A_l x (Eq. 1) in the level's working precision: block rows when stored,
 // else G then G^T by row groups.
-static int level_apply_A(const Level& L, bool f32, const void* x, void* y, cudaStream_t s) {
+// One gather-GEMV of a level's operator pair (M and its block transpose) in
+// the working precision: FP64, FP32, or the FP16 copies under MIXED16.
+static int seg_op(bool h16, bool f32, const SegPlan& p, const DBuf<double>& M64, const DBuf<float>& M32,
+                  const DBuf<__half>& M16, const DBuf<double>& T64, const DBuf<float>& T32, const DBuf<__half>& T16,
+                  const void* x, void* y, SegMode mode, const int* skip, cudaStream_t s, const void* csrc = nullptr,
+                  void* cdst = nullptr) {
+  if (h16 && p.lanes16 > 0)  // plans where setup timed the FP16 form faster
+    return launch_seg16(p, M16.p, T16.p, (const float*)x, (float*)y, mode, skip, s, (const float*)csrc,
+                        (float*)cdst);
+  return launch_seg(p, f32 ? (const void*)M32.p : (const void*)M64.p, f32, x, y, f32, mode, skip, s, csrc, cdst,
+                    f32 ? (const void*)T32.p : (const void*)T64.p);
+}
+
+static int level_apply_A(const Level& L, bool f32, const void* x, void* y, cudaStream_t s, bool h16 = false) {
   if (L.use_ell) return launch_ell(L, f32, x, y, nullptr, nullptr, s);
   if (L.has_blk)
-    return launch_seg(L.ablk, f32 ? (const void*)L.A32.p : (const void*)L.A64.p, f32, x, y, f32, SEG_STORE, nullptr,
-                      s, nullptr, nullptr, f32 ? (const void*)L.At32.p : (const void*)L.At64.p);
+    return seg_op(h16, f32, L.ablk, L.A64, L.A32, L.A16, L.At64, L.At32, L.At16, x, y, SEG_STORE, nullptr, s);
   AMGDD_CUDA(cudaMemsetAsync(y, 0, L.n * (f32 ? sizeof(float) : sizeof(double)), s));
   return launch_apply(L.aplan, L, f32, x, y, +1, nullptr, s);
 }
@@ -1618,11 +1642,10 @@ static int level_apply_A(const Level& L, bool f32, const void* x, void* y, cudaS
 // s = r - A_l x.  The matrix-free form subtracts A x from s in place, so the
 // launch before it must have copied r into s (`rcopy` tells those launches).
 static int level_residual(const Level& L, bool f32, const void* x, const void* r, void* sv, const int* skip,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool h16 = false) {
   if (L.use_ell) return launch_ell(L, f32, x, sv, r, skip, s);
   if (L.has_blk)
-    return launch_seg(L.ablk, f32 ? (const void*)L.A32.p : (const void*)L.A64.p, f32, x, sv, f32, SEG_RESID, skip,
-                      s, r, nullptr, f32 ? (const void*)L.At32.p : (const void*)L.At64.p);
+    return seg_op(h16, f32, L.ablk, L.A64, L.A32, L.A16, L.At64, L.At32, L.At16, x, sv, SEG_RESID, skip, s, r);
   return launch_apply(L.aplan, L, f32, x, sv, -1, skip, s);
 }
 static bool rcopy(const Level& L) { return !L.has_blk && !L.use_ell; }
@@ -1630,16 +1653,19 @@ static bool rcopy(const Level& L) { return !L.has_blk && !L.use_ell; }
 // x(Omega_i) += W_i^T s(omega_i) for all i (Eq. ras-t): atomic scatter-add,
 // or (deterministic hierarchies) stored per Omega-list position and summed
 // per node in a fixed order.  K > 1: K interleaved columns.
-static int apply_rast(const Level& L, bool f32, const void* sv, void* x, const int* skip, cudaStream_t s, int K = 1) {
+static int apply_rast(const Level& L, bool f32, const void* sv, void* x, const int* skip, cudaStream_t s, int K = 1,
+                      bool h16 = false) {
   const void* Wt = f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p;
   const void* W = f32 ? (const void*)L.W32.p : (const void*)L.W64.p;
+  h16 = h16 && K == 1;
   if (L.yd64.p == nullptr) {
-    if (K == 1) return launch_seg(L.rast, Wt, f32, sv, x, f32, SEG_ATOMIC_ADD, skip, s, nullptr, nullptr, W);
+    if (K == 1)
+      return seg_op(h16, f32, L.rast, L.Wt64, L.Wt32, L.Wt16, L.W64, L.W32, L.W16, sv, x, SEG_ATOMIC_ADD, skip, s);
     return launch_seg_multi(L.rast, Wt, W, f32, sv, x, SEG_ATOMIC_ADD, nullptr, K, skip, s);
   }
   void* Y = K == 1 ? (f32 ? (void*)L.yd32.p : (void*)L.yd64.p) : (f32 ? (void*)L.myd32.p : (void*)L.myd64.p);
   if (K == 1)
-    AMGDD_TRY(launch_seg(L.rast_det, Wt, f32, sv, Y, f32, SEG_STORE, skip, s, nullptr, nullptr, W));
+    AMGDD_TRY(seg_op(h16, f32, L.rast_det, L.Wt64, L.Wt32, L.Wt16, L.W64, L.W32, L.W16, sv, Y, SEG_STORE, skip, s));
   else
     AMGDD_TRY(launch_seg_multi(L.rast_det, Wt, W, f32, sv, Y, SEG_STORE, nullptr, K, skip, s));
   return launch_gather_add(L.det_ptr.p, L.det_pos.p, Y, x, L.n, K, f32, skip, s);
@@ -1661,7 +1687,9 @@ struct VProf {
       tag.push_back(0);
     }
     tag[used] = level < 0 ? -1 : level * kSlots + slot;
-    AMGDD_CUDA(cudaEventRecord(ev[used], s));
+    // External: under stream capture the mark becomes an event record node
+    // of the graph (a plain record would only carry a capture dependency)
+    AMGDD_CUDA(cudaEventRecordWithFlags(ev[used], s, cudaEventRecordExternal));
     ++used;
     return AMGDD_OK;
   }
@@ -1715,33 +1743,30 @@ static int vcycle(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, c
     return coarse_solve(h, L, r, x, L.s64.p, skip, s);
   }
   Level& N = *h.lv[l + 1];
-  const void* W = f32 ? (const void*)L.W32.p : (const void*)L.W64.p;
-  const void* Wt = f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p;
-  const void* Z = f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p;
-  const void* Zt = f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p;
+  const bool h16 = use16(h, L, f32);
   void* sv = f32 ? (void*)L.s32.p : (void*)L.s64.p;
   void* rn = f32 ? (void*)N.r32.p : (void*)N.r64.p;
   void* xn = f32 ? (void*)N.x32.p : (void*)N.x64.p;
   // pre-smoothing from x = 0: x = M_RAS^{-1} r  (Eq. ras); the same launch
   // copies s(omega_i) = r(omega_i) for the residual
   AMGDD_MARK(0);
-  AMGDD_TRY(launch_seg(L.ras, W, f32, r, x, f32, SEG_STORE, skip, s, rcopy(L) ? r : nullptr, rcopy(L) ? sv : nullptr,
-                       Wt));
+  AMGDD_TRY(seg_op(h16, f32, L.ras, L.W64, L.W32, L.W16, L.Wt64, L.Wt32, L.Wt16, r, x, SEG_STORE, skip, s,
+                   rcopy(L) ? r : nullptr, rcopy(L) ? sv : nullptr));
   // s = r - A x ; r_c = P^T s
   AMGDD_MARK(2);
-  AMGDD_TRY(level_residual(L, f32, x, r, sv, skip, s));
+  AMGDD_TRY(level_residual(L, f32, x, r, sv, skip, s, h16));
   AMGDD_MARK(3);
-  AMGDD_TRY(launch_seg(L.restr, Zt, f32, sv, rn, f32, SEG_STORE, skip, s, nullptr, nullptr, Z));
+  AMGDD_TRY(seg_op(h16, f32, L.restr, L.Zt64, L.Zt32, L.Zt16, L.Z64, L.Z32, L.Z16, sv, rn, SEG_STORE, skip, s));
   // x_c = B_{l+1} r_c ; x += P x_c  (Eq. cgc)
   AMGDD_TRY(vcycle(h, l + 1, f32, rn, xn, skip, s, prof));
   AMGDD_MARK(4);
-  AMGDD_TRY(launch_seg(L.prol, Z, f32, xn, x, f32, SEG_ADD, skip, s, rcopy(L) ? r : nullptr, rcopy(L) ? sv : nullptr,
-                       Zt));
+  AMGDD_TRY(seg_op(h16, f32, L.prol, L.Z64, L.Z32, L.Z16, L.Zt64, L.Zt32, L.Zt16, xn, x, SEG_ADD, skip, s,
+                   rcopy(L) ? r : nullptr, rcopy(L) ? sv : nullptr));
   // post-smoothing: x += M_RAS-T^{-1} (r - A x)  (Eq. ras-t)
   AMGDD_MARK(2);
-  AMGDD_TRY(level_residual(L, f32, x, r, sv, skip, s));
+  AMGDD_TRY(level_residual(L, f32, x, r, sv, skip, s, h16));
   AMGDD_MARK(7);
-  return apply_rast(L, f32, sv, x, skip, s);
+  return apply_rast(L, f32, sv, x, skip, s, 1, h16);
 }
 
 // Phases of the V-cycle from level `from` >= 1 to the coarsest and back, in
@@ -1917,6 +1942,116 @@ static void drop_dense(Level& L) {
 constexpr int64_t kDenseMaxN = 12288;
 constexpr double kHbmBytesPerUs = 6.8e6;
 
+// MIXED16 storage: FP16 copies (round to nearest) of every level's smoother
+// rows W_i and W_i^T, basis Z_i and Z_i^T and block rows of A.  FP16 holds
+// magnitudes up to 65504 with 11 significant bits; a level whose FP32 copies
+// hold a larger or non-finite entry keeps FP32 (the V-cycle then reads FP32
+// there).  Entries below 2^-24 round to 0 or to subnormals: their absolute
+// error, at most 2^-25, is far below the rounding of the row's largest
+// entries.  Built once; the FP32 copies stay for MIXED32 and batched solves.
+// FP16 form of one plan under MIXED16: the FP32 launch as setup chose it,
+// against the FP16 shifted kernel with 4, 8, 16 or 32 lanes per row over
+// the same chunks, on scratch vectors; the fastest is kept (lanes16 = 0:
+// the plan reads its FP32 copy).  The choice is cached like the others.
+static int tune16(SegPlan& p, const std::string& key, const float* M32, const float* T32, const __half* M16,
+                  const __half* T16, int64_t nin, int64_t nout, SegMode mode, cudaStream_t s) {
+  p.lanes16 = 0;
+  if (p.nchunks == 0 || M16 == nullptr) return AMGDD_OK;
+  double cached = 0.0;
+  if (g_tune && g_tune->get(key, cached)) {
+    const int l = (int)cached;
+    p.lanes16 = (l == 4 || l == 8 || l == 16 || l == 32) ? l : 0;
+    return AMGDD_OK;
+  }
+  if (g_tune && !g_tune->on) {  // no timing: the FP16 kernel with the plan's lanes
+    p.lanes16 = p.lanes;
+    return AMGDD_OK;
+  }
+  DBuf<float> xin, yout, cin;
+  AMGDD_TRY(xin.alloc(std::max<int64_t>(nin, 1)));
+  AMGDD_TRY(yout.alloc(std::max<int64_t>(nout, 1)));
+  AMGDD_TRY(cin.alloc(std::max<int64_t>(nout, 1)));
+  AMGDD_TRY(xin.zero(s));
+  AMGDD_TRY(yout.zero(s));
+  AMGDD_TRY(cin.zero(s));
+  cudaEvent_t e[2];
+  for (auto& v : e) AMGDD_CUDA(cudaEventCreate(&v));
+  constexpr int kReps = 8;
+  int rc = AMGDD_OK;
+  float best_t = 0.f;
+  int best = 0;
+  for (int l : {0, 4, 8, 16, 32}) {
+    p.lanes16 = l;
+    for (int rep = 0; rep < kReps + 2 && rc == AMGDD_OK; ++rep) {
+      if (rep == 2) cudaEventRecord(e[0], s);
+      rc = l == 0 ? launch_seg(p, M32, true, xin.p, yout.p, true, mode, nullptr, s,
+                               mode == SEG_RESID ? cin.p : nullptr, nullptr, T32)
+                  : launch_seg16(p, M16, T16, xin.p, yout.p, mode, nullptr, s, mode == SEG_RESID ? cin.p : nullptr,
+                                 nullptr);
+    }
+    cudaEventRecord(e[1], s);
+    float ms = 0.f;
+    if (rc == AMGDD_OK &&
+        (cudaEventSynchronize(e[1]) != cudaSuccess || cudaEventElapsedTime(&ms, e[0], e[1]) != cudaSuccess))
+      rc = AMGDD_ERR_CUDA;
+    if (rc != AMGDD_OK) break;
+    if (l == 0 || ms < best_t) {
+      best_t = ms;
+      best = l;
+    }
+  }
+  for (auto& v : e) cudaEventDestroy(v);
+  AMGDD_TRY(rc);
+  p.lanes16 = best;
+  if (g_tune) g_tune->put(key, (double)best);
+  return AMGDD_OK;
+}
+
+static int build_half(amgdd_hierarchy& h) {
+  cudaStream_t s = h.work;
+  for (size_t lvl = 0; lvl < h.lv.size(); ++lvl) {
+    Level& L = *h.lv[lvl];
+    if (L.coarsest || L.h16) continue;
+    struct Pair {
+      const DBuf<float>* src;
+      DBuf<__half>* dst;
+    } pairs[6] = {{&L.W32, &L.W16}, {&L.Wt32, &L.Wt16}, {&L.Z32, &L.Z16},
+                  {&L.Zt32, &L.Zt16}, {&L.A32, &L.A16}, {&L.At32, &L.At16}};
+    bool ok = true;
+    std::vector<float> hv;
+    for (auto& pr : pairs) {
+      if (pr.src->p == nullptr || pr.src->n == 0) continue;
+      AMGDD_TRY(download(hv, pr.src->p, pr.src->n, s));
+      for (float v : hv)
+        if (!(std::fabs(v) <= 65000.0f)) {
+          ok = false;
+          break;
+        }
+      if (!ok) break;
+    }
+    if (!ok) continue;  // this level keeps FP32
+    for (auto& pr : pairs) {
+      if (pr.src->p == nullptr || pr.src->n == 0) continue;
+      AMGDD_TRY(pr.dst->alloc(pr.src->n));
+      AMGDD_TRY(launch_to_half(pr.src->p, pr.dst->p, (int64_t)pr.src->n, s));
+    }
+    L.h16 = true;
+    const std::string k = "L" + std::to_string(lvl) + "|h16|";
+    const int64_t nn = L.col0.back();
+    AMGDD_TRY(tune16(L.ras, k + "ras", L.W32.p, L.Wt32.p, L.W16.p, L.Wt16.p, L.n, L.n, SEG_STORE, s));
+    AMGDD_TRY(tune16(L.rast, k + "rast", L.Wt32.p, L.W32.p, L.Wt16.p, L.W16.p, L.n, L.n, SEG_ATOMIC_ADD, s));
+    if (L.yd32.p)
+      AMGDD_TRY(tune16(L.rast_det, k + "rastd", L.Wt32.p, L.W32.p, L.Wt16.p, L.W16.p, L.n, L.om_ptr.back(),
+                       SEG_STORE, s));
+    AMGDD_TRY(tune16(L.restr, k + "restrict", L.Zt32.p, L.Z32.p, L.Zt16.p, L.Z16.p, L.n, nn, SEG_STORE, s));
+    AMGDD_TRY(tune16(L.prol, k + "prolong", L.Z32.p, L.Zt32.p, L.Z16.p, L.Zt16.p, nn, L.n, SEG_ADD, s));
+    if (L.has_blk)
+      AMGDD_TRY(tune16(L.ablk, k + "ablk", L.A32.p, L.At32.p, L.A16.p, L.At16.p, L.n, L.n, SEG_RESID, s));
+  }
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  return AMGDD_OK;
+}
+
 static int tune_dense(amgdd_hierarchy& h) {
   cudaStream_t s = h.work;
   const int nl = (int)h.lv.size();
@@ -2069,7 +2204,7 @@ static int precondition_additive(amgdd_hierarchy& h, const double* r, double* z,
 static int precondition(amgdd_hierarchy& h, const double* r, double* z, const int* skip, cudaStream_t s) {
   Level& L0 = *h.lv[0];
   if (h.prm.cycle == 1) return precondition_additive(h, r, z, skip, s);
-  if (h.precision == AMGDD_MIXED32) {
+  if (mixed(h)) {
     AMGDD_TRY(launch_cast(r, false, L0.r32.p, true, L0.n, skip, s));
     AMGDD_TRY(vcycle(h, 0, true, L0.r32.p, L0.x32.p, skip, s));
     return launch_cast(L0.x32.p, true, z, false, L0.n, skip, s);
@@ -2090,7 +2225,7 @@ static int pcg_iteration(amgdd_hierarchy& h, cudaStream_t s, cudaGraphConditiona
   const int64_t n = h.n;
   PcgState* st = h.st.p;
   const int* done = &st->done;
-  const bool flex = h.precision == AMGDD_MIXED32;
+  const bool flex = mixed(h);
   Level& L0 = *h.lv[0];
   if (L0.use_ell) {
     // fused: four launches besides the V-cycle, each reducing its own dot
@@ -2131,7 +2266,7 @@ static int pcg_start(amgdd_hierarchy& h, cudaStream_t s) {
   AMGDD_TRY(launch_pcg_scalar(4, st, h.partials.p, s));
   AMGDD_TRY(precondition(h, h.r.p, h.z.p, done, s));
   AMGDD_TRY(launch_copy_vec(h.z.p, h.p.p, false, n, done, s));
-  if (h.precision == AMGDD_MIXED32) AMGDD_TRY(launch_copy_vec(h.z.p, h.zold.p, false, n, done, s));
+  if (mixed(h)) AMGDD_TRY(launch_copy_vec(h.z.p, h.zold.p, false, n, done, s));
   AMGDD_TRY(launch_dot_partial(h.r.p, h.z.p, nullptr, n, h.partials.p, done, s));
   AMGDD_TRY(launch_pcg_scalar(0, st, h.partials.p, s));
   return AMGDD_OK;
@@ -2202,7 +2337,7 @@ static int solve_one(amgdd_hierarchy& h, const double* bsrc, bool bdev, double t
                      cudaStream_t s, amgdd_info* info) {
   amgdd_info first{};
   int st = AMGDD_OK;
-  if (h.precision == AMGDD_MIXED32 && h.mixed_stalled) {
+  if (mixed(h) && h.mixed_stalled) {
     // this hierarchy's FP32 cycle stalled before: go straight to FP64
     first = amgdd_info{};
     st = kStallStatus;
@@ -2214,10 +2349,11 @@ static int solve_one(amgdd_hierarchy& h, const double* bsrc, bool bdev, double t
     return st;
   }
   h.mixed_stalled = true;
+  const int prec = h.precision;
   h.precision = AMGDD_FP64;
   amgdd_info second{};
   st = solve_once(h, bsrc, bdev, tol, xdst, xdev, s, &second);
-  h.precision = AMGDD_MIXED32;
+  h.precision = prec;
   second.fallback = 1;
   second.iters_mixed = first.iters;
   second.iters += first.iters;
@@ -2238,10 +2374,10 @@ static int solve_once(amgdd_hierarchy& h, const double* bsrc, bool bdev, double 
   PcgState init{};
   init.tol2 = tol * tol;
   init.max_iter = h.prm.max_iter;
-  init.flexible = h.precision == AMGDD_MIXED32 ? 1 : 0;
+  init.flexible = mixed(h) ? 1 : 0;
   *h.st_host = init;
   AMGDD_CUDA(cudaMemcpyAsync(h.st.p, h.st_host, sizeof(PcgState), cudaMemcpyHostToDevice, s));
-  const int pi = h.precision == AMGDD_MIXED32 ? 1 : 0;
+  const int pi = mixed(h) ? 1 : 0;
   if (h.prm.use_graph) {
     if (h.gloop[pi] == nullptr) AMGDD_TRY(build_solve_graphs(h, pi, s));
     AMGDD_CUDA(cudaGraphLaunch(h.ginit[pi], s));
@@ -2292,7 +2428,7 @@ static int solve_once(amgdd_hierarchy& h, const double* bsrc, bool bdev, double 
     const int* done = &h.st.p->done;
     AMGDD_TRY(precondition(h, h.r.p, h.z.p, done, s));
     AMGDD_TRY(launch_copy_vec(h.z.p, h.p.p, false, n, done, s));
-    if (h.precision == AMGDD_MIXED32) AMGDD_TRY(launch_copy_vec(h.z.p, h.zold.p, false, n, done, s));
+    if (mixed(h)) AMGDD_TRY(launch_copy_vec(h.z.p, h.zold.p, false, n, done, s));
     AMGDD_TRY(launch_dot_partial(h.r.p, h.z.p, nullptr, n, h.partials.p, done, s));
     AMGDD_TRY(launch_pcg_scalar(0, h.st.p, h.partials.p, s));
     if (h.prm.use_graph) {
@@ -2441,7 +2577,7 @@ static int vcycle_multi(amgdd_hierarchy& h, int l, bool f32, int K, const void* 
 static int precondition_multi(amgdd_hierarchy& h, int K, const double* r, double* z, const int* skip,
                               cudaStream_t s) {
   Level& L0 = *h.lv[0];
-  if (h.precision == AMGDD_MIXED32) {
+  if (mixed(h)) {
     AMGDD_TRY(launch_cast(r, false, L0.mr32.p, true, h.n * K, skip, s));
     AMGDD_TRY(vcycle_multi(h, 0, true, K, L0.mr32.p, L0.mx32.p, skip, s));
     return launch_cast(L0.mx32.p, true, z, false, h.n * K, skip, s);
@@ -2459,7 +2595,7 @@ static int pcg_start_multi(amgdd_hierarchy& h, int K, cudaStream_t s) {
   AMGDD_TRY(launch_pcg_scalar_multi(4, M.st.p, M.grp.p, M.partials.p, K, s));
   AMGDD_TRY(precondition_multi(h, K, M.r.p, M.z.p, skip, s));
   AMGDD_TRY(launch_copy_vec(M.z.p, M.p.p, false, nk, skip, s));
-  if (h.precision == AMGDD_MIXED32) AMGDD_TRY(launch_copy_vec(M.z.p, M.zold.p, false, nk, skip, s));
+  if (mixed(h)) AMGDD_TRY(launch_copy_vec(M.z.p, M.zold.p, false, nk, skip, s));
   AMGDD_TRY(launch_dot_multi(M.r.p, M.z.p, nullptr, n, K, M.partials.p, skip, s));
   return launch_pcg_scalar_multi(0, M.st.p, M.grp.p, M.partials.p, K, s);
 }
@@ -2480,7 +2616,7 @@ static int pcg_iteration_multi(amgdd_hierarchy& h, int K, cudaStream_t s, cudaGr
   AMGDD_TRY(launch_dot_multi(M.r.p, M.r.p, nullptr, n, K, M.partials.p, skip, s));
   AMGDD_TRY(launch_pcg_scalar_multi(2, M.st.p, M.grp.p, M.partials.p, K, s));
   AMGDD_TRY(precondition_multi(h, K, M.r.p, M.z.p, skip, s));
-  const bool flex = h.precision == AMGDD_MIXED32;
+  const bool flex = mixed(h);
   AMGDD_TRY(launch_dot_multi(M.r.p, M.z.p, flex ? M.zold.p : nullptr, n, K, M.partials.p, skip, s));
   AMGDD_TRY(launch_pcg_scalar_multi(3, M.st.p, M.grp.p, M.partials.p, K, s, cond, use_cond));
   return launch_update_p_multi(M.st.p, M.grp.p, M.p.p, M.z.p, flex ? M.zold.p : nullptr, n, K, s);
@@ -2543,12 +2679,12 @@ static int solve_group(amgdd_hierarchy& h, const double* b, bool bdev, int ncols
     PcgState init{};
     init.tol2 = tol * tol;
     init.max_iter = h.prm.max_iter;
-    init.flexible = h.precision == AMGDD_MIXED32 ? 1 : 0;
+    init.flexible = mixed(h) ? 1 : 0;
     M.st_host[k] = init;
   }
   AMGDD_CUDA(cudaMemcpyAsync(M.st.p, M.st_host, K * sizeof(PcgState), cudaMemcpyHostToDevice, s));
   AMGDD_CUDA(cudaMemsetAsync(M.grp.p, 0, sizeof(int), s));
-  const int pi = h.precision == AMGDD_MIXED32 ? 1 : 0, ki = kidx(K);
+  const int pi = mixed(h) ? 1 : 0, ki = kidx(K);
   if (M.gloop[pi][ki] == nullptr) AMGDD_TRY(build_multi_graphs(h, pi, K, s));
   AMGDD_CUDA(cudaGraphLaunch(M.ginit[pi][ki], s));
   count_graph_launch(M.ginit_kernels[pi][ki]);
@@ -2585,7 +2721,7 @@ static int solve_group(amgdd_hierarchy& h, const double* b, bool bdev, int ncols
     AMGDD_CUDA(cudaMemcpyAsync(M.r.p, M.q.p, nk * sizeof(double), cudaMemcpyDeviceToDevice, s));
     AMGDD_TRY(precondition_multi(h, K, M.r.p, M.z.p, M.grp.p, s));
     AMGDD_TRY(launch_copy_vec(M.z.p, M.p.p, false, nk, M.grp.p, s));
-    if (h.precision == AMGDD_MIXED32) AMGDD_TRY(launch_copy_vec(M.z.p, M.zold.p, false, nk, M.grp.p, s));
+    if (mixed(h)) AMGDD_TRY(launch_copy_vec(M.z.p, M.zold.p, false, nk, M.grp.p, s));
     AMGDD_TRY(launch_dot_multi(M.r.p, M.z.p, nullptr, n, K, M.partials.p, M.grp.p, s));
     AMGDD_TRY(launch_pcg_scalar_multi(0, M.st.p, M.grp.p, M.partials.p, K, s));
     AMGDD_CUDA(cudaGraphLaunch(M.gloop[pi][ki], s));
@@ -2778,7 +2914,8 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   *out = nullptr;
   amgdd_params prm = params ? *params : amgdd_params_default();
   if (prm.L_max < 1 || prm.n_cmin < 1 || prm.n_cmin > 8 || prm.max_iter < 1 || overlap < 1 ||
-      (prm.precision != AMGDD_FP64 && prm.precision != AMGDD_MIXED32) || prm.check_every < 1 || prm.n_coarse < 1 ||
+      (prm.precision != AMGDD_FP64 && prm.precision != AMGDD_MIXED32 && prm.precision != AMGDD_MIXED16) ||
+      prm.check_every < 1 || prm.n_coarse < 1 ||
       prm.coarse_overlap < 0 || prm.cycle < 0 || prm.cycle > 1 || !(prm.kappa >= 0) ||
       (agg == nullptr && prm.agg_passes < 1) ||
       (prm.cycle == 1 && prm.precision != AMGDD_FP64)) {
@@ -3015,6 +3152,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   AMGDD_CUDA(cudaEventCreateWithFlags(&H->join[0], cudaEventDisableTiming));
   AMGDD_CUDA(cudaEventCreateWithFlags(&H->join[1], cudaEventDisableTiming));
   AMGDD_CUDA(cudaStreamSynchronize(s));
+  if (H->precision == AMGDD_MIXED16) AMGDD_TRY(build_half(*H));
   AMGDD_TRY(tune_dense(*H));
   AMGDD_TRY(tune_tail(*H));
   tctx.save();
@@ -3084,11 +3222,12 @@ int amgdd_solve(amgdd_hierarchy* h, const double* b, int nrhs, double tol, doubl
         const int K = g <= 2 ? 2 : (g <= 4 ? 4 : 8);
         std::vector<amgdd_info> tmp(g);
         amgdd_info* inf = info ? info + j0 : tmp.data();
-        const bool sticky = h->precision == AMGDD_MIXED32 && h->mixed_stalled;
+        const int prec = h->precision;
+        const bool sticky = mixed(*h) && h->mixed_stalled;
         if (sticky) h->precision = AMGDD_FP64;  // the FP32 cycle stalled on this hierarchy before
         const int st = solve_group(*h, b + (int64_t)j0 * h->n, bdev, g, K, tol, x + (int64_t)j0 * h->n, xdev, s, inf);
         if (sticky) {
-          h->precision = AMGDD_MIXED32;
+          h->precision = prec;
           for (int k = 0; k < g; ++k) inf[k].fallback = 1;
         }
         const bool per_rhs = st == AMGDD_OK || st == AMGDD_ERR_BREAKDOWN || st == AMGDD_ERR_NO_CONVERGENCE ||
@@ -3119,7 +3258,7 @@ int amgdd_solve(amgdd_hierarchy* h, const double* b, int nrhs, double tol, doubl
 }
 
 int amgdd_set_precision(amgdd_hierarchy* h, int precision) {
-  if (h == nullptr || (precision != AMGDD_FP64 && precision != AMGDD_MIXED32)) {
+  if (h == nullptr || (precision != AMGDD_FP64 && precision != AMGDD_MIXED32 && precision != AMGDD_MIXED16)) {
     set_error("amgdd_set_precision: invalid argument");
     return AMGDD_ERR_INVALID_ARG;
   }
@@ -3127,8 +3266,26 @@ int amgdd_set_precision(amgdd_hierarchy* h, int precision) {
     set_error("amgdd_set_precision: the additive two-level method runs in FP64 only");
     return AMGDD_ERR_INVALID_ARG;
   }
+  if (precision == AMGDD_MIXED16) AMGDD_TRY(build_half(*h));
+  if ((precision == AMGDD_MIXED16) != (h->precision == AMGDD_MIXED16)) {
+    // the FP32-vector solve graphs read the other matrix copies: recapture
+    for (auto* ge : {&h->ginit[1], &h->gloop[1]})
+      if (*ge) {
+        cudaGraphExecDestroy(*ge);
+        *ge = nullptr;
+      }
+  }
   h->precision = precision;
   h->mixed_stalled = false;  // give the FP32 cycle a fresh chance
+  return AMGDD_OK;
+}
+
+int amgdd_set_max_iter(amgdd_hierarchy* h, int max_iter) {
+  if (h == nullptr || max_iter < 1) {
+    set_error("amgdd_set_max_iter: invalid argument");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  h->prm.max_iter = max_iter;
   return AMGDD_OK;
 }
 
@@ -3141,7 +3298,7 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
   PdlScope pdl_scope(h->prm.pdl != 0);
   cudaStream_t s = (cudaStream_t)stream;
   Level& L = *h->lv[level];
-  const bool f32 = h->precision == AMGDD_MIXED32;
+  const bool f32 = mixed(*h);
   if (op == AMGDD_OP_M2) {
     if (h->prm.cycle != 1 || level != 0) {
       set_error("amgdd_apply: M2 needs level 0 of a hierarchy built with cycle = 1");
@@ -3181,26 +3338,25 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
     yout = yout32.p;
   }
   const size_t esz = f32 ? sizeof(float) : sizeof(double);
+  const bool h16 = use16(*h, L, f32);
   switch (op) {
     case AMGDD_OP_A:
-      AMGDD_TRY(level_apply_A(L, f32, xin, yout, s));
+      AMGDD_TRY(level_apply_A(L, f32, xin, yout, s, h16));
       break;
     case AMGDD_OP_RAS:
-      AMGDD_TRY(launch_seg(L.ras, f32 ? (const void*)L.W32.p : (const void*)L.W64.p, f32, xin, yout, f32, SEG_STORE,
-                           nullptr, s, nullptr, nullptr, f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p));
+      AMGDD_TRY(seg_op(h16, f32, L.ras, L.W64, L.W32, L.W16, L.Wt64, L.Wt32, L.Wt16, xin, yout, SEG_STORE, nullptr, s));
       break;
     case AMGDD_OP_RAST:
       AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
-      AMGDD_TRY(apply_rast(L, f32, xin, yout, nullptr, s));
+      AMGDD_TRY(apply_rast(L, f32, xin, yout, nullptr, s, 1, h16));
       break;
     case AMGDD_OP_RESTRICT:
-      AMGDD_TRY(launch_seg(L.restr, f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p, f32, xin, yout, f32,
-                           SEG_STORE, nullptr, s, nullptr, nullptr, f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p));
+      AMGDD_TRY(
+          seg_op(h16, f32, L.restr, L.Zt64, L.Zt32, L.Zt16, L.Z64, L.Z32, L.Z16, xin, yout, SEG_STORE, nullptr, s));
       break;
     case AMGDD_OP_PROLONG:
       AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
-      AMGDD_TRY(launch_seg(L.prol, f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p, f32, xin, yout, f32, SEG_ADD,
-                           nullptr, s, nullptr, nullptr, f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p));
+      AMGDD_TRY(seg_op(h16, f32, L.prol, L.Z64, L.Z32, L.Z16, L.Zt64, L.Zt32, L.Zt16, xin, yout, SEG_ADD, nullptr, s));
       break;
     case AMGDD_OP_VCYCLE:
       AMGDD_TRY(vcycle(*h, level, f32, xin, yout, nullptr, s));
@@ -3227,12 +3383,22 @@ constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 float* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
 
-// Device address of the staging array on the current device.  Host code
-// may not use the symbol itself: it names a host-side stand-in.  The
-// address is looked up once per device, with that device current.
-int noalloc_stage(float** out) {
-  int dev = 0;
-  AMGDD_CUDA(cudaGetDevice(&dev));
+// Device address of the staging array on device `dev`, which must be the
+// current device: the hierarchy's kernels run there, and the array of
+// another device is another allocation.  Host code may not use the symbol
+// itself: it names a host-side stand-in.  The address is looked up once per
+// device, with that device current, and kept for the life of the process
+// (a cudaDeviceReset would invalidate it, as it invalidates every
+// hierarchy built on that device).
+int noalloc_stage(int dev, float** out) {
+  int cur = 0;
+  AMGDD_CUDA(cudaGetDevice(&cur));
+  if (cur != dev) {
+    set_error("amgdd_apply_noalloc: the current device is %d but the hierarchy lives on device %d; make the "
+              "hierarchy's device current",
+              cur, dev);
+    return AMGDD_ERR_INVALID_ARG;
+  }
   if (dev < 0 || dev >= kNoAllocMaxDevices) {
     set_error("amgdd_apply_noalloc: device id %d out of range", dev);
     return AMGDD_ERR_INVALID_ARG;
@@ -3253,11 +3419,20 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
     set_error("amgdd_apply_noalloc: invalid argument");
     return AMGDD_ERR_INVALID_ARG;
   }
+  {
+    int cur = 0;
+    AMGDD_CUDA(cudaGetDevice(&cur));
+    if (cur != h->device) {
+      set_error("amgdd_apply_noalloc: the current device is %d but the hierarchy lives on device %d", cur,
+                h->device);
+      return AMGDD_ERR_INVALID_ARG;
+    }
+  }
   ErrScope err_scope(&h->st.p->vc_err);
   PdlScope pdl_scope(h->prm.pdl != 0);
   cudaStream_t s = (cudaStream_t)stream;
   Level& L = *h->lv[level];
-  const bool f32 = h->precision == AMGDD_MIXED32;
+  const bool f32 = mixed(*h);
   if (op == AMGDD_OP_M2) {
     if (h->prm.cycle != 1 || level != 0) {
       set_error("amgdd_apply: M2 needs level 0 of a hierarchy built with cycle = 1");
@@ -3299,32 +3474,31 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
                 (long long)nin, (long long)nout, (long long)kNoAllocMaxN);
       return AMGDD_ERR_INVALID_ARG;
     }
-    AMGDD_TRY(noalloc_stage(&stage));
+    AMGDD_TRY(noalloc_stage(h->device, &stage));
     AMGDD_TRY(launch_cast(x, false, stage, true, nin, nullptr, s));
     xin = stage;
     yout = stage + kNoAllocMaxN;
   }
   const size_t esz = f32 ? sizeof(float) : sizeof(double);
+  const bool h16 = use16(*h, L, f32);
   switch (op) {
     case AMGDD_OP_A:
-      AMGDD_TRY(level_apply_A(L, f32, xin, yout, s));
+      AMGDD_TRY(level_apply_A(L, f32, xin, yout, s, h16));
       break;
     case AMGDD_OP_RAS:
-      AMGDD_TRY(launch_seg(L.ras, f32 ? (const void*)L.W32.p : (const void*)L.W64.p, f32, xin, yout, f32, SEG_STORE,
-                           nullptr, s, nullptr, nullptr, f32 ? (const void*)L.Wt32.p : (const void*)L.Wt64.p));
+      AMGDD_TRY(seg_op(h16, f32, L.ras, L.W64, L.W32, L.W16, L.Wt64, L.Wt32, L.Wt16, xin, yout, SEG_STORE, nullptr, s));
       break;
     case AMGDD_OP_RAST:
       AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
-      AMGDD_TRY(apply_rast(L, f32, xin, yout, nullptr, s));
+      AMGDD_TRY(apply_rast(L, f32, xin, yout, nullptr, s, 1, h16));
       break;
     case AMGDD_OP_RESTRICT:
-      AMGDD_TRY(launch_seg(L.restr, f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p, f32, xin, yout, f32,
-                           SEG_STORE, nullptr, s, nullptr, nullptr, f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p));
+      AMGDD_TRY(
+          seg_op(h16, f32, L.restr, L.Zt64, L.Zt32, L.Zt16, L.Z64, L.Z32, L.Z16, xin, yout, SEG_STORE, nullptr, s));
       break;
     case AMGDD_OP_PROLONG:
       AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
-      AMGDD_TRY(launch_seg(L.prol, f32 ? (const void*)L.Z32.p : (const void*)L.Z64.p, f32, xin, yout, f32, SEG_ADD,
-                           nullptr, s, nullptr, nullptr, f32 ? (const void*)L.Zt32.p : (const void*)L.Zt64.p));
+      AMGDD_TRY(seg_op(h16, f32, L.prol, L.Z64, L.Z32, L.Z16, L.Zt64, L.Zt32, L.Zt16, xin, yout, SEG_ADD, nullptr, s));
       break;
     case AMGDD_OP_VCYCLE:
       AMGDD_TRY(vcycle(*h, level, f32, xin, yout, nullptr, s));
@@ -3337,7 +3511,7 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
   return take_err_word(*h, s);
 }
 
-int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes, int cap) {
+int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, int graph, double* ms, double* bytes, int cap) {
   if (h == nullptr || ms == nullptr || bytes == nullptr || reps < 1 ||
       cap < (int)h->lv.size() * VProf::kSlots) {
     set_error("amgdd_profile_vcycle: invalid argument (cap must be >= levels * %d)", VProf::kSlots);
@@ -3346,9 +3520,9 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes
   ErrScope err_scope(&h->st.p->vc_err);
   PdlScope pdl_scope(h->prm.pdl != 0);
   const int nl = (int)h->lv.size();
-  for (int i = 0; i < nl * VProf::kSlots; ++i) ms[i] = bytes[i] = 0.0;
+  for (int i = 0; i < std::min(cap, nl * VProf::kSlots + 1); ++i) ms[i] = bytes[i] = 0.0;
   cudaStream_t s = h->work;
-  const bool f32 = h->precision == AMGDD_MIXED32;
+  const bool f32 = mixed(*h);
   Level& L0 = *h->lv[0];
   const void* r = f32 ? (const void*)L0.s32.p : (const void*)L0.s64.p;
   void* x = f32 ? (void*)L0.r32.p : (void*)L0.r64.p;
@@ -3357,15 +3531,55 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes
   AMGDD_CUDA(cudaMemsetAsync((void*)r, 0, L0.n * (f32 ? 4 : 8), s));
   VProf prof;
   std::vector<double> acc(nl * VProf::kSlots, 0.0);
-  for (int rep = 0; rep < reps; ++rep) {
-    prof.used = 0;
-    AMGDD_TRY(vcycle(*h, 0, f32, r, x, nullptr, s, &prof));
-    AMGDD_TRY(prof.mark(s, -1, 0));
-    AMGDD_CUDA(cudaStreamSynchronize(s));
+  auto collect = [&]() -> int {
     for (size_t i = 0; i + 1 < prof.used; ++i) {
       float t = 0.f;
       AMGDD_CUDA(cudaEventElapsedTime(&t, prof.ev[i], prof.ev[i + 1]));
       if (prof.tag[i] >= 0) acc[prof.tag[i]] += t;
+    }
+    return AMGDD_OK;
+  };
+  if (!graph) {
+    for (int rep = 0; rep < reps; ++rep) {
+      prof.used = 0;
+      AMGDD_TRY(vcycle(*h, 0, f32, r, x, nullptr, s, &prof));
+      AMGDD_TRY(prof.mark(s, -1, 0));
+      AMGDD_CUDA(cudaStreamSynchronize(s));
+      AMGDD_TRY(collect());
+    }
+  } else {
+    // the marked cycle as one CUDA graph (event record nodes between its
+    // kernels), replayed: the per-step times then hold the in-graph gaps
+    // between dependent kernels and no host launch overhead
+    prof.used = 0;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    capture_begin();
+    AMGDD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int rc = vcycle(*h, 0, f32, r, x, nullptr, s, &prof);
+    if (rc == AMGDD_OK) rc = prof.mark(s, -1, 0);
+    const cudaError_t ce = cudaStreamEndCapture(s, &g);
+    const int64_t nk = capture_end();
+    if (rc == AMGDD_OK && (ce != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess)) {
+      set_error("amgdd_profile_vcycle: capture of the marked V-cycle failed");
+      rc = AMGDD_ERR_CUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+    for (int rep = 0; rep < reps + 2 && rc == AMGDD_OK; ++rep) {  // two warm-up replays
+      if (cudaGraphLaunch(ge, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("amgdd_profile_vcycle: graph replay failed");
+        rc = AMGDD_ERR_CUDA;
+        break;
+      }
+      count_graph_launch(nk);
+      if (rep >= 2) rc = collect();
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    AMGDD_TRY(rc);
+    if (cap > nl * VProf::kSlots) {  // the same cycle without marks
+      double us = 0.0;
+      AMGDD_TRY(time_vcycle_graph(*h, 0, f32, r, x, &us));
+      ms[nl * VProf::kSlots] = us * 1e-3;
     }
   }
   const size_t esz = f32 ? 4 : 8;
@@ -3382,12 +3596,16 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, double* ms, double* bytes
       if (f32) b[1] = b[5] = (double)L.n * 12.0;
     } else {
       const int64_t nn = L.col0.back();
+      const int pf1 = h->persist_from[f32 ? 1 : 0];
+      // FP16 entries where MIXED16 reads them (per plan; the persistent tail reads FP32)
+      const bool h16 = use16(*h, L, f32) && !(pf1 > 0 && l >= pf1);
+      auto msz = [&](const SegPlan& p) -> size_t { return h16 && p.lanes16 > 0 ? 2 : esz; };
       const double cp = rcopy(L) ? (double)L.n * esz : 0.0;  // fused copy r -> s
-      b[0] = seg_bytes(L.ras, L.n, L.n, false, esz) + cp;
-      b[2] = 2.0 * (resid_bytes(L, esz) - cp);  // two residuals
-      b[3] = seg_bytes(L.restr, L.n, nn, false, esz);
-      b[4] = seg_bytes(L.prol, nn, L.n, true, esz) + cp;
-      b[7] = rast_bytes(L, esz);
+      b[0] = seg_bytes(L.ras, L.n, L.n, false, esz, msz(L.ras)) + cp;
+      b[2] = 2.0 * (resid_bytes(L, esz, msz(L.ablk)) - cp);  // two residuals
+      b[3] = seg_bytes(L.restr, L.n, nn, false, esz, msz(L.restr));
+      b[4] = seg_bytes(L.prol, nn, L.n, true, esz, msz(L.prol)) + cp;
+      b[7] = rast_bytes(L, esz, msz(L.yd64.p ? L.rast_det : L.rast));
     }
   }
   const int pf = h->persist_from[f32 ? 1 : 0];
@@ -3414,6 +3632,27 @@ int64_t amgdd_device_bytes(const amgdd_hierarchy* h, int with_batched) {
 
 int amgdd_num_levels(const amgdd_hierarchy* h) { return h ? (int)h->lv.size() : 0; }
 
+// Structural pattern of A_l = G_l^T G_l (+ D1 on level 0, carried as rows of
+// G): j ~ k iff some row group's support holds both (CSR, ascending columns).
+static void level_A_pattern(const Level& L, std::vector<int64_t>& ptr, std::vector<int32_t>& idx) {
+  std::vector<std::vector<int32_t>> rows((size_t)L.n);
+  for (size_t g = 0; g + 1 < L.g_ptr.size(); ++g)
+    for (int64_t a = L.g_ptr[g]; a < L.g_ptr[g + 1]; ++a) {
+      auto& r = rows[(size_t)L.g_idx[a]];
+      r.insert(r.end(), L.g_idx.begin() + L.g_ptr[g], L.g_idx.begin() + L.g_ptr[g + 1]);
+    }
+  ptr.assign((size_t)L.n + 1, 0);
+  idx.clear();
+  for (int64_t j = 0; j < L.n; ++j) {
+    auto& r = rows[(size_t)j];
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+    idx.insert(idx.end(), r.begin(), r.end());
+    ptr[j + 1] = (int64_t)idx.size();
+    std::vector<int32_t>().swap(r);
+  }
+}
+
 int amgdd_level_describe(const amgdd_hierarchy* h, int level, amgdd_level_desc* out) {
   if (h == nullptr || out == nullptr || level < 0 || level >= (int)h->lv.size()) {
     set_error("amgdd_level_describe: invalid argument");
@@ -3428,7 +3667,10 @@ int amgdd_level_describe(const amgdd_hierarchy* h, int level, amgdd_level_desc* 
     out->g_rows += L.g_rank[g];
     out->g_vals += (int64_t)L.g_rank[g] * (L.g_ptr[g + 1] - L.g_ptr[g]);
   }
+  out->g_sup_len = L.g_ptr.empty() ? 0 : L.g_ptr.back();
+  out->a_nnz = level < (int)h->nnzA.size() ? h->nnzA[level] : 0;
   if (!L.coarsest) {
+    for (int i = 0; i < L.nagg; ++i) out->p_nnz += (int64_t)L.nomega[i] * L.k[i];
     out->nagg = L.nagg;
     out->n_next = L.col0.empty() ? 0 : L.col0.back();
     out->omega_len = (int64_t)L.om_idx.size();
@@ -3454,11 +3696,39 @@ int amgdd_level_export(const amgdd_hierarchy* h, int level, int which, void* dst
     std::memcpy(dst, src, bytes);
     return AMGDD_OK;
   };
+  switch (which) {
+    case AMGDD_ARR_G_PTR: return put(L.g_ptr.data(), L.g_ptr.size() * sizeof(int64_t));
+    case AMGDD_ARR_G_IDX: return put(L.g_idx.data(), L.g_idx.size() * sizeof(int32_t));
+    case AMGDD_ARR_A_PTR:
+    case AMGDD_ARR_A_IDX: {
+      std::vector<int64_t> ptr;
+      std::vector<int32_t> idx;
+      level_A_pattern(L, ptr, idx);
+      return which == AMGDD_ARR_A_PTR ? put(ptr.data(), ptr.size() * sizeof(int64_t))
+                                      : put(idx.data(), idx.size() * sizeof(int32_t));
+    }
+    default:
+      break;
+  }
   if (L.coarsest && which != AMGDD_ARR_AGG) {
     set_error("amgdd_level_export: the coarsest level has no aggregates");
     return AMGDD_ERR_INVALID_ARG;
   }
   switch (which) {
+    case AMGDD_ARR_P_PTR:
+    case AMGDD_ARR_P_IDX: {
+      // row j of P_l spans the k_a columns of its aggregate a (Eq. mg-p);
+      // columns are numbered by aggregate, then by ascending mu
+      std::vector<int64_t> c0(L.nagg + 1, 0);
+      for (int a = 0; a < L.nagg; ++a) c0[a + 1] = c0[a] + L.k[a];
+      std::vector<int64_t> ptr(L.n + 1, 0);
+      for (int64_t j = 0; j < L.n; ++j) ptr[j + 1] = ptr[j] + L.k[L.agg[j]];
+      if (which == AMGDD_ARR_P_PTR) return put(ptr.data(), ptr.size() * sizeof(int64_t));
+      std::vector<int32_t> idx((size_t)ptr[L.n]);
+      for (int64_t j = 0; j < L.n; ++j)
+        for (int64_t c = 0; c < ptr[j + 1] - ptr[j]; ++c) idx[ptr[j] + c] = (int32_t)(c0[L.agg[j]] + c);
+      return put(idx.data(), idx.size() * sizeof(int32_t));
+    }
     case AMGDD_ARR_AGG:
       if (L.agg.empty()) {
         set_error("amgdd_level_export: no aggregates on this level");
@@ -3489,21 +3759,24 @@ int amgdd_level_export(const amgdd_hierarchy* h, int level, int which, void* dst
   }
 }
 
-static void level_bytes(const amgdd_hierarchy& h, const Level& L, size_t esz, double& cyc) {
+static void level_bytes(const amgdd_hierarchy& h, const Level& L, size_t esz, double& cyc, bool tail = false) {
   if (L.coarsest) {
     cyc += ((double)L.n * L.n * 8.0 + 2.0 * L.n * 8.0) * (h.prm.coarse_refine && L.Aw64.p ? 3.0 : 1.0);
     return;
   }
   const int64_t nn = L.col0.back();
-  cyc += seg_bytes(L.ras, L.n, L.n, false, esz) + rast_bytes(L, esz) +
-         seg_bytes(L.restr, L.n, nn, false, esz) + seg_bytes(L.prol, nn, L.n, true, esz) +
-         2.0 * resid_bytes(L, esz);
-  (void)h;
+  // FP16 entries where MIXED16 reads them (per plan; the persistent tail reads FP32)
+  const bool h16 = use16(h, L, esz == 4) && !tail;
+  auto msz = [&](const SegPlan& p) -> size_t { return h16 && p.lanes16 > 0 ? 2 : esz; };
+  cyc += seg_bytes(L.ras, L.n, L.n, false, esz, msz(L.ras)) +
+         rast_bytes(L, esz, msz(L.yd64.p ? L.rast_det : L.rast)) +
+         seg_bytes(L.restr, L.n, nn, false, esz, msz(L.restr)) + seg_bytes(L.prol, nn, L.n, true, esz, msz(L.prol)) +
+         2.0 * resid_bytes(L, esz, msz(L.ablk));
 }
 
 int amgdd_bytes_model(const amgdd_hierarchy* h, double* vcycle_bytes, double* apply_out) {
   if (h == nullptr) return AMGDD_ERR_INVALID_ARG;
-  const size_t esz = h->precision == AMGDD_MIXED32 ? 4 : 8;
+  const size_t esz = mixed(*h) ? 4 : 8;
   const int df = h->dense_from[esz == 4 ? 1 : 0];
   double cyc = 0.0;
   for (size_t l = 0; l < h->lv.size(); ++l) {
@@ -3512,7 +3785,8 @@ int amgdd_bytes_model(const amgdd_hierarchy* h, double* vcycle_bytes, double* ap
       cyc += ((double)L.n * L.dld + 2.0 * L.n) * esz;
       break;
     }
-    level_bytes(*h, L, esz, cyc);
+    const int pf = h->persist_from[esz == 4 ? 1 : 0];
+    level_bytes(*h, L, esz, cyc, pf > 0 && (int)l >= pf);
   }
   const Level& L0 = *h->lv[0];
   const double ap = L0.use_ell ? (double)L0.n * L0.ell_w * 12.0 + 2.0 * L0.n * 8.0 : apply_bytes(L0, 8);
@@ -3531,6 +3805,7 @@ int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap) {
   for (int64_t v : h->nnzA) oc += (double)v;
   oc /= h->nnzA.empty() ? 1.0 : (double)h->nnzA[0];
   s += "], \"op_complexity\": " + std::to_string(oc);
+  s += ", \"process_device_allocs\": " + std::to_string(device_alloc_count());
   s += ", \"nagg\": [";
   for (size_t l = 0; l < h->lv.size(); ++l) s += (l ? ", " : "") + std::to_string(h->lv[l]->nagg);
   s += "], \"g_vals\": [";
@@ -3557,6 +3832,15 @@ int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap) {
   for (size_t l = 0; l + 1 < h->lv.size(); ++l) s += (l ? ", " : "") + std::to_string(h->lv[l]->n_color);
   s += "], \"n_mult\": [";
   for (size_t l = 0; l + 1 < h->lv.size(); ++l) s += (l ? ", " : "") + std::to_string(h->lv[l]->n_mult);
+  s += "], \"fp16_levels\": [";
+  for (size_t l = 0; l < h->lv.size(); ++l) s += std::string(l ? ", " : "") + (h->lv[l]->h16 ? "true" : "false");
+  s += "], \"fp16_lanes\": [";  // per level: ras, rast, restrict, prolong, block rows (0: FP32 copy)
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    const Level& L = *h->lv[l];
+    s += std::string(l ? ", [" : "[") + std::to_string(L.ras.lanes16) + ", " + std::to_string(L.rast.lanes16) +
+         ", " + std::to_string(L.restr.lanes16) + ", " + std::to_string(L.prol.lanes16) + ", " +
+         std::to_string(L.ablk.lanes16) + "]";
+  }
   s += "], \"coarse_A\": [";
   for (size_t l = 0; l < h->lv.size(); ++l) {
     const Level& L = *h->lv[l];

@@ -13,6 +13,7 @@
 // All kernels take an optional device flag `skip`; when it is set (the CG
 // iteration has converged) they return at once, so a captured batch of
 // iterations is a no-op after convergence.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,6 +57,52 @@ __device__ __forceinline__ float vdot(const float4& a, const float4& b) {
 }
 __device__ __forceinline__ double vdot(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
 
+// Matrix entries of type TM against vector entries of type T: V is the
+// 16-byte load of W = 16 / sizeof(TM) matrix entries, dot() its product with
+// W consecutive entries of x (aligned: x + c W is a multiple of W elements).
+// 16-bit matrices (the MIXED16 storage) are widened to FP32 and summed in
+// FP32.
+template <class T, class TM>
+struct MV;
+template <>
+struct MV<float, float> {
+  using V = float4;
+  static constexpr int W = 4;
+  static __device__ __forceinline__ float dot(const V& m, const float* x) {
+    return vdot(m, *reinterpret_cast<const float4*>(x));
+  }
+};
+template <>
+struct MV<double, double> {
+  using V = double2;
+  static constexpr int W = 2;
+  static __device__ __forceinline__ double dot(const V& m, const double* x) {
+    return vdot(m, *reinterpret_cast<const double2*>(x));
+  }
+};
+template <>
+struct MV<float, __half> {
+  using V = uint4;
+  static constexpr int W = 8;
+  static __device__ __forceinline__ float dot(const V& m, const float* x) {
+    const float4 a = *reinterpret_cast<const float4*>(x);
+    const float4 b = *reinterpret_cast<const float4*>(x + 4);
+    const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&m.x));
+    const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&m.y));
+    const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&m.z));
+    const float2 f3 = __half22float2(*reinterpret_cast<const __half2*>(&m.w));
+    return f0.x * a.x + f0.y * a.y + f1.x * a.z + f1.y * a.w + f2.x * b.x + f2.y * b.y + f3.x * b.z + f3.y * b.w;
+  }
+};
+template <class T, class TM>
+__device__ __forceinline__ T mval(TM v) {
+  return T(v);
+}
+template <>
+__device__ __forceinline__ float mval<float, __half>(__half v) {
+  return __half2float(v);
+}
+
 // VK (vector kind) 0: scalar loads.  VK 1: every row of every block starts on
 // a 16-byte boundary and has a multiple of the vector width W entries (checked
 // when the plan is built); rows and the staged x are read 16 bytes per lane.
@@ -68,27 +115,27 @@ __device__ __forceinline__ double vdot(const double2& a, const double2& b) { ret
 // matrix (m_len entries) is read element by element up to that end.
 // U = 4 (plans with long rows only): the gather and the row loop keep four
 // independent loads per thread in flight.
-template <class T, int VK>
+template <class T, int VK, int W>
 __device__ __forceinline__ void seg_stage(T* xs, int S, int c, T v) {
   if constexpr (VK == 2) {
 #pragma unroll
-    for (int k = 0; k < Vec2<T>::width; ++k) xs[k * S + c + k] = v;
+    for (int k = 0; k < W; ++k) xs[k * S + c + k] = v;
   } else {
     xs[c] = v;
   }
 }
 
-template <class T, int L, int MODE, int VK, int U = 1>
+template <class T, class TM, int L, int MODE, int VK, int U = 1>
 __global__ void __launch_bounds__(kSegThreads) k_seg(const SegDesc* __restrict__ desc,
                                                      const int32_t* __restrict__ in_idx,
-                                                     const int32_t* __restrict__ out_idx, const T* __restrict__ M,
+                                                     const int32_t* __restrict__ out_idx, const TM* __restrict__ M,
                                                      const T* __restrict__ x, T* __restrict__ y, const int* skip,
                                                      const T* __restrict__ csrc, T* __restrict__ cdst, int64_t m_len) {
   pdl_prologue();
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  using V = typename Vec2<T>::type;
-  constexpr int W = Vec2<T>::width;
+  using V = typename MV<T, TM>::V;
+  constexpr int W = MV<T, TM>::W;
   T* xs = reinterpret_cast<T*>(smem_raw);
   const SegDesc dsc = desc[blockIdx.x];  // the chunk's block, in one dependent step
   const int r0 = dsc.r0;
@@ -136,7 +183,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const SegDesc* __restrict__
     }
   }
   if constexpr (U == 1) {
-    for (int c = threadIdx.x; c < ncb; c += blockDim.x) seg_stage<T, VK>(xs, S, c, x[ii[c]]);
+    for (int c = threadIdx.x; c < ncb; c += blockDim.x) seg_stage<T, VK, W>(xs, S, c, x[ii[c]]);
   } else {
     const int step = (int)blockDim.x;
     int c = threadIdx.x;
@@ -148,9 +195,9 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const SegDesc* __restrict__
 #pragma unroll
       for (int u = 0; u < U; ++u) v[u] = x[id[u]];
 #pragma unroll
-      for (int u = 0; u < U; ++u) seg_stage<T, VK>(xs, S, c + u * step, v[u]);
+      for (int u = 0; u < U; ++u) seg_stage<T, VK, W>(xs, S, c + u * step, v[u]);
     }
-    for (; c < ncb; c += step) seg_stage<T, VK>(xs, S, c, x[ii[c]]);
+    for (; c < ncb; c += step) seg_stage<T, VK, W>(xs, S, c, x[ii[c]]);
   }
   __syncthreads();
   const unsigned mask = group_mask<L>();
@@ -163,7 +210,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const SegDesc* __restrict__
       const int a = (int)(e0 & (W - 1));
       const int64_t base = e0 - a;
       const V* rv = reinterpret_cast<const V*>(M + base);
-      const V* xv = reinterpret_cast<const V*>(xs + a * S);
+      const T* xa = xs + a * S;
       int nv = (ncb + a + W - 1) / W;
       const bool cut = base + (int64_t)nv * W > m_len;  // last row of the matrix: one vector crosses its end
       if (cut) --nv;
@@ -191,12 +238,11 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const SegDesc* __restrict__
       }
       T acc = T(0);
       if (cut && lane == 0) {
-        const T* xa = xs + a * S;
-        for (int j = nv * W; base + j < m_len; ++j) acc += M[base + j] * xa[j];
+        for (int j = nv * W; base + j < m_len; ++j) acc += mval<T, TM>(M[base + j]) * xa[j];
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (lane + u * L < nv) acc += vdot(pre[u], xv[lane + u * L]);
+        if (lane + u * L < nv) acc += MV<T, TM>::dot(pre[u], xa + (lane + u * L) * W);
       int c = lane + U * L;
       {
         T q[U];
@@ -207,12 +253,12 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const SegDesc* __restrict__
 #pragma unroll
           for (int u = 0; u < U; ++u) m[u] = rv[c + u * L];
 #pragma unroll
-          for (int u = 0; u < U; ++u) q[u] += vdot(m[u], xv[c + u * L]);
+          for (int u = 0; u < U; ++u) q[u] += MV<T, TM>::dot(m[u], xa + (c + u * L) * W);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) acc += q[u];
       }
-      for (; c < nv; c += L) acc += vdot(rv[c], xv[c]);
+      for (; c < nv; c += L) acc += MV<T, TM>::dot(rv[c], xa + c * W);
       acc = group_sum<L>(acc, mask);
       if (lane == 0) {
         T* dst = y + po;
@@ -238,12 +284,8 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const SegDesc* __restrict__
     for (int r = r0 + grp; r < r1; r += ngrp) {
       T acc = T(0);
       if constexpr (VK != 0) {
-        const V* rv;
-        const V* xv;
-        int nv;
-        rv = reinterpret_cast<const V*>(M + mob + (int64_t)r * ncb);  // VK 1: aligned rows
-        xv = reinterpret_cast<const V*>(xs);
-        nv = ncb / W;
+        const V* rv = reinterpret_cast<const V*>(M + mob + (int64_t)r * ncb);  // VK 1: aligned rows
+        const int nv = ncb / W;
         int c = lane;
         if constexpr (U > 1) {
           T a[U];
@@ -254,14 +296,14 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const SegDesc* __restrict__
   #pragma unroll
             for (int u = 0; u < U; ++u) m[u] = rv[c + u * L];
   #pragma unroll
-            for (int u = 0; u < U; ++u) a[u] += vdot(m[u], xv[c + u * L]);
+            for (int u = 0; u < U; ++u) a[u] += MV<T, TM>::dot(m[u], xs + (c + u * L) * W);
           }
   #pragma unroll
           for (int u = 0; u < U; ++u) acc += a[u];
         }
-        for (; c < nv; c += L) acc += vdot(rv[c], xv[c]);
+        for (; c < nv; c += L) acc += MV<T, TM>::dot(rv[c], xs + c * W);
       } else {
-        const T* row = M + mob + (int64_t)r * ncb;
+        const TM* row = M + mob + (int64_t)r * ncb;
         int c = lane;
         if constexpr (U > 1) {
           T a[U];
@@ -270,14 +312,14 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const SegDesc* __restrict__
           for (; c + (U - 1) * L < ncb; c += U * L) {
             T m[U];
   #pragma unroll
-            for (int u = 0; u < U; ++u) m[u] = row[c + u * L];
+            for (int u = 0; u < U; ++u) m[u] = mval<T, TM>(row[c + u * L]);
   #pragma unroll
             for (int u = 0; u < U; ++u) a[u] += m[u] * xs[c + u * L];
           }
   #pragma unroll
           for (int u = 0; u < U; ++u) acc += a[u];
         }
-        for (; c < ncb; c += L) acc += row[c] * xs[c];
+        for (; c < ncb; c += L) acc += mval<T, TM>(row[c]) * xs[c];
       }
       acc = group_sum<L>(acc, mask);
       if (lane == 0) {
@@ -304,10 +346,10 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const SegDesc* __restrict__
 // block's transposed copy MT (nc x nr, row-major), so the L lanes read L
 // consecutive values.  x(in_idx) is staged once per task in shared memory.
 // Outputs, atomics and the fused copy are issued by all lanes at once.
-template <class T, int L, int MODE>
+template <class T, class TM, int L, int MODE>
 __global__ void __launch_bounds__(128) k_seg_rows(const SegDesc* __restrict__ desc, int ntasks, int max_nc,
                                                   const int32_t* __restrict__ in_idx,
-                                                  const int32_t* __restrict__ out_idx, const T* __restrict__ MT,
+                                                  const int32_t* __restrict__ out_idx, const TM* __restrict__ MT,
                                                   const T* __restrict__ x, T* __restrict__ y, const int* skip,
                                                   const T* __restrict__ csrc, T* __restrict__ cdst) {
   pdl_prologue();
@@ -329,10 +371,10 @@ __global__ void __launch_bounds__(128) k_seg_rows(const SegDesc* __restrict__ de
   constexpr int kPre = 16;
   const bool act = lane < rows;
   const int r = r0 + lane;
-  const T* col = MT + dsc.m_off + r;
+  const TM* col = MT + dsc.m_off + r;
   T pre[kPre];
 #pragma unroll
-  for (int c = 0; c < kPre; ++c) pre[c] = (act && c < ncb) ? col[(int64_t)c * nrb] : T(0);
+  for (int c = 0; c < kPre; ++c) pre[c] = (act && c < ncb) ? mval<T, TM>(col[(int64_t)c * nrb]) : T(0);
   const int o = act ? out_idx[dsc.out_off + r] : 0;
   const bool need_c = MODE == SEG_RESID || cdst != nullptr;
   const T cv = (act && need_c) ? csrc[o] : T(0);
@@ -343,7 +385,7 @@ __global__ void __launch_bounds__(128) k_seg_rows(const SegDesc* __restrict__ de
 #pragma unroll
   for (int c = 0; c < kPre; ++c)
     if (c < ncb) acc += pre[c] * xs[c];
-  for (int c = kPre; c < ncb; ++c) acc += col[(int64_t)c * nrb] * xs[c];
+  for (int c = kPre; c < ncb; ++c) acc += mval<T, TM>(col[(int64_t)c * nrb]) * xs[c];
   T* dst = y + o;
   if (MODE == SEG_STORE)
     *dst = acc;
@@ -540,13 +582,13 @@ __global__ void __launch_bounds__(kItemThreads) k_seg_staged(const __grid_consta
   (void)item_run<T, L>(P, blockIdx.x, smem_raw, bar, use, err);
 }
 
-template <class T, int L, int MODE>
-int seg_rows_launch(const SegPlan& p, const T* MT, const T* x, T* y, const int* skip, cudaStream_t s, const T* csrc,
+template <class T, class TM, int L, int MODE>
+int seg_rows_launch(const SegPlan& p, const TM* MT, const T* x, T* y, const int* skip, cudaStream_t s, const T* csrc,
                     T* cdst) {
   const int per = 128 / L;
   const int grid = (p.ntasks + per - 1) / per;
   const size_t smem = (size_t)per * p.max_nc * sizeof(T);
-  auto kern = k_seg_rows<T, L, MODE>;
+  auto kern = k_seg_rows<T, TM, L, MODE>;
   if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   AMGDD_CUDA(launch_k(g_pdl, kern, grid, 128, smem, s, (const SegDesc*)p.task_desc.p, p.ntasks, p.max_nc,
                       p.in_idx_ext, p.out_idx_ext, MT, x, y, skip, csrc, cdst));
@@ -555,20 +597,20 @@ int seg_rows_launch(const SegPlan& p, const T* MT, const T* x, T* y, const int* 
   return AMGDD_OK;
 }
 
-template <class T, int L>
-int seg_rows_mode(const SegPlan& p, const T* MT, const T* x, T* y, SegMode mode, const int* skip, cudaStream_t s,
+template <class T, class TM, int L>
+int seg_rows_mode(const SegPlan& p, const TM* MT, const T* x, T* y, SegMode mode, const int* skip, cudaStream_t s,
                   const T* csrc, T* cdst) {
   switch (mode) {
-    case SEG_STORE: return seg_rows_launch<T, L, SEG_STORE>(p, MT, x, y, skip, s, csrc, cdst);
-    case SEG_ADD: return seg_rows_launch<T, L, SEG_ADD>(p, MT, x, y, skip, s, csrc, cdst);
-    case SEG_ATOMIC_ADD: return seg_rows_launch<T, L, SEG_ATOMIC_ADD>(p, MT, x, y, skip, s, csrc, cdst);
-    case SEG_ATOMIC_SUB: return seg_rows_launch<T, L, SEG_ATOMIC_SUB>(p, MT, x, y, skip, s, csrc, cdst);
-    default: return seg_rows_launch<T, L, SEG_RESID>(p, MT, x, y, skip, s, csrc, cdst);
+    case SEG_STORE: return seg_rows_launch<T, TM, L, SEG_STORE>(p, MT, x, y, skip, s, csrc, cdst);
+    case SEG_ADD: return seg_rows_launch<T, TM, L, SEG_ADD>(p, MT, x, y, skip, s, csrc, cdst);
+    case SEG_ATOMIC_ADD: return seg_rows_launch<T, TM, L, SEG_ATOMIC_ADD>(p, MT, x, y, skip, s, csrc, cdst);
+    case SEG_ATOMIC_SUB: return seg_rows_launch<T, TM, L, SEG_ATOMIC_SUB>(p, MT, x, y, skip, s, csrc, cdst);
+    default: return seg_rows_launch<T, TM, L, SEG_RESID>(p, MT, x, y, skip, s, csrc, cdst);
   }
 }
 
-template <class T, int L, int VK, int U>
-int seg_launch_kind(const SegPlan& p, const T* M, const T* x, T* y, SegMode mode, const int* skip, cudaStream_t s,
+template <class T, class TM, int L, int VK, int U>
+int seg_launch_kind(const SegPlan& p, const TM* M, const T* x, T* y, SegMode mode, const int* skip, cudaStream_t s,
                     const T* csrc, T* cdst, size_t smem) {
   auto launch = [&](auto kern) -> int {
     if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -579,18 +621,18 @@ int seg_launch_kind(const SegPlan& p, const T* M, const T* x, T* y, SegMode mode
     return AMGDD_OK;
   };
   switch (mode) {
-    case SEG_STORE: return launch(k_seg<T, L, SEG_STORE, VK, U>);
-    case SEG_ADD: return launch(k_seg<T, L, SEG_ADD, VK, U>);
-    case SEG_ATOMIC_ADD: return launch(k_seg<T, L, SEG_ATOMIC_ADD, VK, U>);
-    case SEG_ATOMIC_SUB: return launch(k_seg<T, L, SEG_ATOMIC_SUB, VK, U>);
-    default: return launch(k_seg<T, L, SEG_RESID, VK, U>);
+    case SEG_STORE: return launch(k_seg<T, TM, L, SEG_STORE, VK, U>);
+    case SEG_ADD: return launch(k_seg<T, TM, L, SEG_ADD, VK, U>);
+    case SEG_ATOMIC_ADD: return launch(k_seg<T, TM, L, SEG_ATOMIC_ADD, VK, U>);
+    case SEG_ATOMIC_SUB: return launch(k_seg<T, TM, L, SEG_ATOMIC_SUB, VK, U>);
+    default: return launch(k_seg<T, TM, L, SEG_RESID, VK, U>);
   }
 }
 
 // Shared memory of the shifted-vector form (W copies of the staged input).
-template <class T>
+template <class T, class TM>
 size_t seg_shift_smem(const SegPlan& p) {
-  constexpr int W = Vec2<T>::width;
+  constexpr int W = MV<T, TM>::W;
   return (size_t)W * (size_t)(((p.max_nc + W - 1) / W) * W + W) * sizeof(T);
 }
 
@@ -601,14 +643,14 @@ int seg_dispatch_mode(const SegPlan& p, const T* M, const T* x, T* y, SegMode mo
   // the shifted form (always with the 4-way unrolled gather and row loops)
   // needs a 16-byte aligned base (device allocations are)
   if ((sizeof(T) == 4 ? p.shift : p.shift64) && !p.vec && ((uintptr_t)M & 15) == 0)
-    return seg_launch_kind<T, L, 2, 4>(p, M, x, y, mode, skip, s, csrc, cdst, seg_shift_smem<T>(p));
+    return seg_launch_kind<T, T, L, 2, 4>(p, M, x, y, mode, skip, s, csrc, cdst, seg_shift_smem<T, T>(p));
   if constexpr (L == 32) {
     if (p.unroll)
-      return p.vec ? seg_launch_kind<T, L, 1, 4>(p, M, x, y, mode, skip, s, csrc, cdst, smem)
-                   : seg_launch_kind<T, L, 0, 4>(p, M, x, y, mode, skip, s, csrc, cdst, smem);
+      return p.vec ? seg_launch_kind<T, T, L, 1, 4>(p, M, x, y, mode, skip, s, csrc, cdst, smem)
+                   : seg_launch_kind<T, T, L, 0, 4>(p, M, x, y, mode, skip, s, csrc, cdst, smem);
   }
-  return p.vec ? seg_launch_kind<T, L, 1, 1>(p, M, x, y, mode, skip, s, csrc, cdst, smem)
-               : seg_launch_kind<T, L, 0, 1>(p, M, x, y, mode, skip, s, csrc, cdst, smem);
+  return p.vec ? seg_launch_kind<T, T, L, 1, 1>(p, M, x, y, mode, skip, s, csrc, cdst, smem)
+               : seg_launch_kind<T, T, L, 0, 1>(p, M, x, y, mode, skip, s, csrc, cdst, smem);
 }
 
 template <class T>
@@ -620,9 +662,9 @@ int seg_dispatch(const SegPlan& p, const T* M, const T* MT, const T* x, T* y, Se
       return AMGDD_ERR_INTERNAL;
     }
     switch (p.kind) {
-      case 8: return seg_rows_mode<T, 8>(p, MT, x, y, mode, skip, s, csrc, cdst);
-      case 16: return seg_rows_mode<T, 16>(p, MT, x, y, mode, skip, s, csrc, cdst);
-      default: return seg_rows_mode<T, 32>(p, MT, x, y, mode, skip, s, csrc, cdst);
+      case 8: return seg_rows_mode<T, T, 8>(p, MT, x, y, mode, skip, s, csrc, cdst);
+      case 16: return seg_rows_mode<T, T, 16>(p, MT, x, y, mode, skip, s, csrc, cdst);
+      default: return seg_rows_mode<T, T, 32>(p, MT, x, y, mode, skip, s, csrc, cdst);
     }
   }
   switch (p.lanes) {
@@ -631,6 +673,16 @@ int seg_dispatch(const SegPlan& p, const T* M, const T* MT, const T* x, T* y, Se
     case 16: return seg_dispatch_mode<T, 16>(p, M, x, y, mode, skip, s, csrc, cdst);
     default: return seg_dispatch_mode<T, 32>(p, M, x, y, mode, skip, s, csrc, cdst);
   }
+}
+
+// FP16 matrices (MIXED16 storage) against FP32 vectors: the row-per-lane
+// plans read the transposed copy; every other plan takes the shifted
+// 16-byte loads (8 entries each) at any row alignment.
+template <int L>
+int seg16_lanes(const SegPlan& p, const __half* M, const float* x, float* y, SegMode mode, const int* skip,
+                cudaStream_t s, const float* csrc, float* cdst) {
+  return seg_launch_kind<float, __half, L, 2, 4>(p, M, x, y, mode, skip, s, csrc, cdst,
+                                                 seg_shift_smem<float, __half>(p));
 }
 
 // ---------------------------------------------------------------------------
@@ -1236,6 +1288,37 @@ int launch_seg(const SegPlan& p, const void* M, bool m_fp32, const void* x, void
                               (const double*)csrc, (double*)cdst);
 }
 
+int launch_seg16(const SegPlan& p, const __half* M, const __half* MT, const float* x, float* y, SegMode mode,
+                 const int* skip, cudaStream_t s, const float* csrc, float* cdst) {
+  if (p.rows_mode ? p.ntasks == 0 : p.nchunks == 0) return AMGDD_OK;
+  if (mode == SEG_RESID && csrc == nullptr) {
+    set_error("launch_seg16: the residual mode needs the right-hand side");
+    return AMGDD_ERR_INTERNAL;
+  }
+  const int lanes = p.lanes16 > 0 && p.nchunks > 0 ? p.lanes16 : (p.rows_mode ? 0 : p.lanes);
+  if (lanes == 0) {
+    if (MT == nullptr) {
+      set_error("launch_seg16: row-per-lane plan needs the transposed operator");
+      return AMGDD_ERR_INTERNAL;
+    }
+    switch (p.kind) {
+      case 8: return seg_rows_mode<float, __half, 8>(p, MT, x, y, mode, skip, s, csrc, cdst);
+      case 16: return seg_rows_mode<float, __half, 16>(p, MT, x, y, mode, skip, s, csrc, cdst);
+      default: return seg_rows_mode<float, __half, 32>(p, MT, x, y, mode, skip, s, csrc, cdst);
+    }
+  }
+  if (M == nullptr || ((uintptr_t)M & 15) != 0) {
+    set_error("launch_seg16: the matrix must be 16-byte aligned");
+    return AMGDD_ERR_INTERNAL;
+  }
+  switch (lanes) {
+    case 4: return seg16_lanes<4>(p, M, x, y, mode, skip, s, csrc, cdst);
+    case 8: return seg16_lanes<8>(p, M, x, y, mode, skip, s, csrc, cdst);
+    case 16: return seg16_lanes<16>(p, M, x, y, mode, skip, s, csrc, cdst);
+    default: return seg16_lanes<32>(p, M, x, y, mode, skip, s, csrc, cdst);
+  }
+}
+
 int launch_apply(const ApplyPlan& p, const Level& L, bool fp32, const void* x, void* y, int sign, const int* skip,
                  cudaStream_t s) {
   // buckets are ordered by kind: kinds 0-3 run in the narrow kernel, 4-7 in the wide one
@@ -1364,6 +1447,20 @@ int launch_dense(const void* B, int64_t ld, int n, bool fp32, const void* x, voi
     case 2: return go(k_dense<float, 2>, k_dense<double, 2>);
     default: return go(k_dense<float, 1>, k_dense<double, 1>);
   }
+}
+
+__global__ void k_to_half(const float* __restrict__ src, __half* __restrict__ dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __float2half_rn(src[i]);
+}
+
+int launch_to_half(const float* src, __half* dst, int64_t n, cudaStream_t s) {
+  if (n <= 0) return AMGDD_OK;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_to_half<<<grid, 256, 0, s>>>(src, dst, n);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
 }
 
 int launch_cast(const void* src, bool src32, void* dst, bool dst32, int64_t n, const int* skip, cudaStream_t s) {

@@ -2,6 +2,7 @@
 // launch wrappers.  Nothing here is part of the C ABI (include/amgdd.h).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -33,6 +34,11 @@ void set_error(const char* fmt, ...);
 // Net device bytes allocated through DBuf by the calling thread (setup
 // measures a hierarchy's footprint as the change over its build).
 extern thread_local int64_t g_alloc_bytes;
+// Device allocations made through DBuf in this process (all threads); the
+// hierarchy's JSON summary reports it, so a caller can check that a call
+// allocated nothing.
+int64_t device_alloc_count();
+void note_device_alloc();
 
 // Solve-phase kernels are launched with programmatic dependent launch while
 // set (per thread: each hierarchy call sets it from its parameters).
@@ -68,6 +74,7 @@ struct DBuf {
     }
     n = count;
     g_alloc_bytes += (int64_t)(count * sizeof(T) + 16);
+    note_device_alloc();
     return AMGDD_OK;
   }
   int upload(const std::vector<T>& h, cudaStream_t s) {
@@ -122,6 +129,7 @@ struct SegPlan {
   bool shift = false;   // 32 lanes, rows at any alignment: aligned vector loads against shifted copies of x
   bool shift64 = false; // the same for the FP64 copies (chosen separately)
   bool unroll = false;  // long rows (32 lanes, >= 512 entries on average): 4-way unrolled loops
+  int lanes16 = 0;      // MIXED16: lanes per row of the FP16 shifted kernel; 0 = read the FP32 copy
   int max_nc = 0;       // longest row (shared-memory staging of the gathered x)
   int64_t mat_len = 0;  // total stored matrix entries
   int64_t in_len = 0, out_len = 0;
@@ -247,6 +255,11 @@ struct Level {
   DBuf<float> myd32;
   DBuf<double> W64, Wt64, Z64, Zt64, mu;
   DBuf<float> W32, Wt32, Z32, Zt32;
+  // MIXED16 storage: FP16 copies of the smoother rows, the basis and the
+  // block rows of A (built on demand; h16 once every copy of the level is
+  // in range)
+  bool h16 = false;
+  DBuf<__half> W16, Wt16, Z16, Zt16, A16, At16;
   // rows omega_i of A over Omega_i (layout of W_i; the residual of the
   // batched solver where A has no block rows), applied with the RAS plan
   DBuf<double> Aw64, AwT64;
@@ -283,6 +296,12 @@ struct Level {
 int launch_seg(const SegPlan& p, const void* M, bool m_fp32, const void* x, void* y, bool v_fp32, SegMode mode,
                const int* skip, cudaStream_t s, const void* csrc = nullptr, void* cdst = nullptr,
                const void* MT = nullptr);
+// The same with FP16 matrix entries (MIXED16 storage) and FP32 vectors:
+// entries are widened to FP32 and summed in FP32.
+int launch_seg16(const SegPlan& p, const __half* M, const __half* MT, const float* x, float* y, SegMode mode,
+                 const int* skip, cudaStream_t s, const float* csrc = nullptr, float* cdst = nullptr);
+// dst[i] = FP16 round-to-nearest of src[i] (setup: the MIXED16 copies).
+int launch_to_half(const float* src, __half* dst, int64_t n, cudaStream_t s);
 int launch_apply(const ApplyPlan& p, const Level& L, bool fp32, const void* x, void* y, int sign, const int* skip,
                  cudaStream_t s);
 int launch_cast(const void* src, bool src32, void* dst, bool dst32, int64_t n, const int* skip, cudaStream_t s);

@@ -50,8 +50,11 @@ def test_additive_two_level_matches_oracle(amg, tau, N, bs):
     xg, ig = H.solve(b, tol=1e-8)
     assert ig[0]["status"] == 0 and ig[0]["relres_true"] <= 1e-8
     assert abs(ig[0]["iters"] - io["iters"]) <= 1
-    if ig[0]["iters"] == io["iters"]:
-        assert _rel(np.asarray(xg).ravel(), xo) <= 1e-10
+    H.set_max_iter(io["iters"])  # the iterate at the oracle's count, not only at stop
+    xk, ik = H.solve(b, tol=0.0)
+    H.set_max_iter(1000)
+    assert ik[0]["iters"] == io["iters"]
+    assert _rel(np.asarray(xk).ravel(), xo) <= 1e-10
     # several right-hand sides (solved column by column) agree with single solves
     B = seeded_rhs(p.n, 3, 4)
     X, infos = H.solve(B, tol=1e-8)

@@ -51,8 +51,13 @@ def test_batched_fp64_matches_single_and_oracle(amg, name):
         assert abs(infos[j]["iters"] - isg[0]["iters"]) <= 1
         assert _rel(X[:, j], _cols(xs)[:, 0]) <= 1e-9
         xo, io = oracle.pcg(ho, B[:, j], tol=1e-8)
-        if infos[j]["iters"] == io["iters"]:
-            assert _rel(X[:, j], xo) <= 1e-9
+        # the batch's column j after exactly the oracle's iteration count (tol = 0 runs every column to the
+        # limit), not only at stop
+        H.set_max_iter(io["iters"])
+        Xk, ik = H.solve(B, tol=0.0)
+        H.set_max_iter(1000)
+        assert ik[j]["iters"] == io["iters"]
+        assert _rel(_cols(np.asarray(Xk))[:, j], xo) <= 1e-9
 
 
 @pytest.mark.parametrize("name", ["q1_64", "overlap2_d1"])

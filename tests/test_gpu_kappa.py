@@ -21,7 +21,7 @@ import pytest
 import oracle
 from inputs import fd_2d, fd_block_aggregates, seeded_rhs
 from oracle.construct import row_groups_from_csr
-from test_gpu_parity import _apply, _check_spectra, _degenerate_cut, _rel
+from test_gpu_parity import _apply, _check_patterns, _check_spectra, _degenerate_cut, _rel, _x_at_iters
 
 pytestmark = pytest.mark.gpu
 
@@ -67,7 +67,8 @@ def first_gray_level(ho, lo=1e-14, hi=1e-8):
 
 
 def check_structure_upto(amg, H, ho, g):
-    """Aggregates and Omega lists on levels <= g, k_i on levels < g, exactly."""
+    """Aggregates, Omega lists and the G_l / A_l patterns on levels <= g, k_i and the P_l pattern on levels < g,
+    exactly."""
     for lvl in range(min(g, len(ho.levels) - 2) + 1):
         Lo = ho.levels[lvl]
         d = H.describe(lvl)
@@ -79,6 +80,8 @@ def check_structure_upto(amg, H, ho, g):
             assert np.array_equal(idx[ptr[i]:ptr[i + 1]], Lo.Omega[i].astype(np.int32)), (lvl, i)
         if lvl < g:
             assert np.array_equal(H.export(lvl, amg.ARR_K), np.array([Z.shape[1] for Z in Lo.Z], dtype=np.int32))
+        # G_l and A_l patterns follow from the k_i above this level; P_l's from this level's k_i
+        _check_patterns(amg, H, Lo, lvl, coarsest=lvl >= g)
 
 
 def check_valid_from(amg, H, c_min, g):
@@ -120,8 +123,7 @@ def check_solve(amg, H, ho, b):
     assert ig[0]["status"] == 0 and ig[0]["relres_true"] <= 1e-8
     if first_gray_level(ho) == len(ho.levels) - 1:
         assert abs(ig[0]["iters"] - io["iters"]) <= 1
-        if ig[0]["iters"] == io["iters"]:
-            assert _rel(xg[:, 0] if xg.ndim == 2 else xg, xo) <= 1e-10
+        assert _rel(_x_at_iters(H, b, io["iters"]), xo) <= 1e-10
     else:
         assert ig[0]["iters"] <= 1.5 * io["iters"] + 3, (ig[0]["iters"], io["iters"])
     H.set_precision(amg.MIXED32)
