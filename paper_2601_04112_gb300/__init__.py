@@ -58,7 +58,7 @@ class Params(ctypes.Structure):
                 ("coarse_overlap", ctypes.c_int), ("coarse_refine", ctypes.c_int),
                 ("pdl", ctypes.c_int), ("dense_tail", ctypes.c_int), ("ell", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("cycle", ctypes.c_int),
-                ("kappa", ctypes.c_double), ("agg_passes", ctypes.c_int)]
+                ("kappa", ctypes.c_double), ("agg_passes", ctypes.c_int), ("schur_gram", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

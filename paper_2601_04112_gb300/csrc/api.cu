@@ -1000,6 +1000,7 @@ bool use16(const amgdd_hierarchy& h, const Level& L, bool f32) {
 // ---------------------------------------------------------------------------
 // Compression of the row groups of one level: pivoted Cholesky of each Gram.
 int compress(Level& L, cudaStream_t s) {
+  if (L.rows_ready) return build_apply(L, s);  // rows carried by QR from the level above
   const int64_t ng = (int64_t)L.g_ptr.size() - 1;
   const int64_t cap = L.h_off.back();
   AMGDD_TRY(L.d_R64.alloc(cap));
@@ -1137,13 +1138,33 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
 
   std::vector<int32_t> loc(L.n, -1);
   std::vector<int64_t> gstamp((size_t)(L.g_ptr.size() - 1), -1);
-  const int64_t budget = (int64_t)384 << 20;  // doubles per batch for A and A~ pools
+  const int64_t budget = (int64_t)384 << 20;  // doubles per batch for A and A~ pools (and the rows of the splitting)
+  const bool rows_schur = !h.prm.schur_gram;
+  // rows of the splitting of each aggregate (row route): sum of rank_g over the groups of nz_i
+  std::vector<int64_t> yrows(nagg, 0);
+  if (rows_schur)
+    for (int i = 0; i < nagg; ++i) {
+      const int64_t o0 = L.om_ptr[i], o1 = L.om_ptr[i + 1];
+      for (int64_t q = o0; q < o1; ++q) {
+        const int32_t v = L.om_idx[q];
+        if (L.agg[v] != i) continue;  // nz_i: the groups touching omega_i
+        for (int64_t e = nptr[v]; e < nptr[v + 1]; ++e) {
+          const int32_t g = ngrp[e];
+          if (gstamp[g] != -2 - (int64_t)i) {
+            gstamp[g] = -2 - (int64_t)i;
+            yrows[i] += L.g_rank[g];
+          }
+        }
+      }
+    }
+  std::fill(gstamp.begin(), gstamp.end(), -1);
   int i0 = 0;
   while (i0 < nagg) {
     int i1 = i0;
     int64_t pool = 0;
-    while (i1 < nagg && (i1 == i0 || pool + 2 * (int64_t)mdim[i1] * mdim[i1] <= budget)) {
-      pool += 2 * (int64_t)mdim[i1] * mdim[i1];
+    auto need = [&](int i) { return 2 * (int64_t)mdim[i] * mdim[i] + yrows[i] * mdim[i]; };
+    while (i1 < nagg && (i1 == i0 || pool + need(i1) <= budget)) {
+      pool += need(i1);
       ++i1;
     }
     const int nb = i1 - i0;
@@ -1231,7 +1252,30 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
       }
     {
       Phase ph(3, "schur", s);
-      AMGDD_TRY(launch_schur(nb, max_m, B.m.p, B.no.p, B.a_off.p, Atpool.p, h.prm.schur_rtol, s));
+      if (rows_schur) {
+        std::vector<int64_t> yoff(nb + 1, 0), noff(nb + 1, 0);
+        std::vector<int32_t> yr(nb);
+        int bmax_m = 0;
+        for (int t = 0; t < nb; ++t) {
+          yr[t] = (int32_t)yrows[i0 + t];
+          yoff[t + 1] = yoff[t] + yrows[i0 + t] * bm[t];
+          noff[t + 1] = noff[t] + bm[t];
+          bmax_m = std::max(bmax_m, (int)bm[t]);
+        }
+        DBuf<int64_t> dyoff, dnoff;
+        DBuf<int32_t> dyr;
+        DBuf<double> Ypool, nrm;
+        AMGDD_TRY(dyoff.upload(yoff, s));
+        AMGDD_TRY(dnoff.upload(noff, s));
+        AMGDD_TRY(dyr.upload(yr, s));
+        AMGDD_TRY(Ypool.alloc(std::max<int64_t>(yoff[nb], 1)));
+        AMGDD_TRY(nrm.alloc(std::max<int64_t>(noff[nb], 1)));
+        AMGDD_TRY(launch_schur_rows(nb, bmax_m, B, L.d_g_ptr.p, L.d_h_off.p, L.d_rank.p, L.d_R64.p, dM.p, dyoff.p,
+                                    dyr.p, Ypool.p, dnoff.p, nrm.p, Atpool.p, s));
+        AMGDD_CUDA(cudaStreamSynchronize(s));
+      } else {
+        AMGDD_TRY(launch_schur(nb, max_m, B.m.p, B.no.p, B.a_off.p, Atpool.p, h.prm.schur_rtol, s));
+      }
     }
     {
       Phase ph(4, "inverse rows", s);
@@ -1447,6 +1491,35 @@ int build_next(amgdd_hierarchy& h, Level& L, Level& N, cudaStream_t s) {
     AMGDD_TRY(launch_next_gram(P, max_sn, L.d_g_ptr.p, L.d_h_off.p, L.d_H.p, L.Z64.p, N.d_H.p, scratch.p, f, c, s));
   }
   AMGDD_CUDA(cudaStreamSynchronize(s));
+  if (!h.prm.schur_gram) {
+    // row route: G_{l+1}'s rows by QR of the stacked R_g P_g, in chunks of
+    // new groups whose stacked rows fit a scratch budget
+    std::vector<int64_t> t_off(nnew + 1, 0);
+    for (int64_t q = 0; q < nnew; ++q) {
+      int64_t rows = 0;
+      for (int64_t e = cnt[q]; e < cnt[q + 1]; ++e) rows += L.g_rank[contrib[e]];
+      t_off[q + 1] = t_off[q] + rows * (N.g_ptr[q + 1] - N.g_ptr[q]);
+    }
+    DBuf<int64_t> d_toff;
+    AMGDD_TRY(d_toff.upload(t_off, s));
+    AMGDD_TRY(N.d_R64.alloc(std::max<int64_t>(N.h_off[nnew], 1)));
+    AMGDD_TRY(N.d_R32.alloc(std::max<int64_t>(N.h_off[nnew], 1)));
+    AMGDD_TRY(N.d_rank.alloc(std::max<int64_t>(nnew, 1)));
+    const int64_t budget = (int64_t)64 << 20;  // doubles of stacked rows per launch
+    int64_t maxper = 1;
+    for (int64_t q = 0; q < nnew; ++q) maxper = std::max(maxper, t_off[q + 1] - t_off[q]);
+    DBuf<double> tscr;
+    AMGDD_TRY(tscr.alloc(std::max(budget, maxper)));
+    for (int64_t f = 0; f < nnew;) {
+      int64_t e = f + 1;
+      while (e < nnew && t_off[e + 1] - t_off[f] <= std::max(budget, maxper)) ++e;
+      AMGDD_TRY(launch_next_rows(P, L.d_g_ptr.p, L.d_h_off.p, L.d_rank.p, L.d_R64.p, L.Z64.p, d_toff.p, tscr.p,
+                                 N.d_R64.p, N.d_R32.p, N.d_rank.p, f, e - f, s));
+      f = e;
+    }
+    AMGDD_TRY(download(N.g_rank, N.d_rank.p, nnew, s));
+    N.rows_ready = true;
+  }
   N.n = L.col0[L.nagg];
   AMGDD_TRY(N.d_g_ptr.upload(N.g_ptr, s));
   AMGDD_TRY(N.d_g_idx.upload(N.g_idx, s));

@@ -191,6 +191,7 @@ struct Level {
   DBuf<int64_t> d_g_ptr, d_h_off;
   DBuf<int32_t> d_g_idx, d_rank;
   DBuf<double> d_H;     // Grams H_g = sum_rows g^T g (setup only, freed after use)
+  bool rows_ready = false;  // d_R64 already holds rows carried by QR (row route): no pivoted Cholesky
   DBuf<double> d_R64;   // compressed rows, capacity s x s per group
   DBuf<float> d_R32;
   ApplyPlan aplan;  // supports of at most 32 nodes
@@ -526,5 +527,16 @@ int launch_blockrows(int nblk, const int32_t* nr, const int32_t* nc, const int64
                      double* At64, float* At32, cudaStream_t s);
 int launch_next_gram(const NextGramPlan& p, int max_sn, const int64_t* g_ptr, const int64_t* h_off, const double* H,
                      const double* Z64, double* Hn, double* scratch, int64_t first, int64_t count, cudaStream_t s);
+// G_{l+1}'s rows by QR of the stacked R_g P_g (row route); t_off: prefix of
+// rows x sn per new group (scratch holds groups first .. first+count-1).
+int launch_next_rows(const NextGramPlan& p, const int64_t* g_ptr, const int64_t* h_off, const int32_t* rank,
+                     const double* R, const double* Z64, const int64_t* t_off, double* scratch, double* Rn64,
+                     float* Rn32, int32_t* rank_out, int64_t first, int64_t count, cudaStream_t s);
+// S~ of Eq. gevp-S from the rows of the splitting (row route) into the omega
+// block of Atpool; Ypool holds y_rows[b] x m per matrix, nrm m per matrix.
+int launch_schur_rows(int nb, int max_m, const LocalBatch& b, const int64_t* g_ptr, const int64_t* h_off,
+                      const int32_t* rank, const double* R, const int32_t* M, const int64_t* y_off,
+                      const int32_t* y_rows, double* Ypool, const int64_t* n_off, double* nrm, double* Atpool,
+                      cudaStream_t s);
 
 }  // namespace amgdd

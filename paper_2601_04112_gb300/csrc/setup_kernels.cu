@@ -857,6 +857,223 @@ __global__ void k_next_gram(int64_t first, const int64_t* __restrict__ new_ptr, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Rows of one support group of G_{l+1} = G_l P_l (Section 3.1), carried as
+// rows: the stacked products R_g P_g of every contributing level-l group g
+// (rank_g rows each, P_g as in k_next_gram) are reduced by Householder QR to
+// their R factor, min(rows, sn) rows over the new support.  Q is orthogonal,
+// so R^T R = sum_g P_g^T R_g^T R_g P_g (the Gram k_next_gram forms), while R
+// keeps the small singular values of the rows to rounding relative to the
+// largest, which the Gram of the rows would square away.
+// T: stacked rows, column-major (ld = rows) in scratch at t_off[h].
+__global__ void k_next_rows(int64_t first, const int64_t* __restrict__ new_ptr, const int32_t* __restrict__ contrib,
+                            const int64_t* __restrict__ new_sptr, const int64_t* __restrict__ new_hoff,
+                            const int64_t* __restrict__ rowz_ptr, const int64_t* __restrict__ rowz_zoff,
+                            const int32_t* __restrict__ rowz_k, const int32_t* __restrict__ rowz_col,
+                            const int64_t* __restrict__ g_ptr, const int64_t* __restrict__ h_off,
+                            const int32_t* __restrict__ rank, const double* __restrict__ R,
+                            const double* __restrict__ Z64, const int64_t* __restrict__ t_off,
+                            double* __restrict__ scratch, double* __restrict__ Rn64, float* __restrict__ Rn32,
+                            int32_t* __restrict__ rank_out) {
+  __shared__ double sh[32];
+  const int64_t h = first + blockIdx.x;
+  const int sn = (int)(new_sptr[h + 1] - new_sptr[h]);
+  double* T = scratch + (t_off[h] - t_off[first]);
+  const int nr = (int)(t_off[h + 1] - t_off[h]) / sn;
+  // T = [R_g P_g; ...]
+  int row = 0;
+  for (int64_t q = new_ptr[h]; q < new_ptr[h + 1]; ++q) {
+    const int g = contrib[q];
+    const int s = (int)(g_ptr[g + 1] - g_ptr[g]);
+    const int rk = rank[g];
+    const double* Rg = R + h_off[g];
+    const int64_t rp = rowz_ptr[g];
+    for (int64_t e = threadIdx.x; e < (int64_t)rk * sn; e += blockDim.x) {
+      const int r = (int)(e / sn), d = (int)(e % sn);
+      double acc = 0.0;
+      for (int bb = 0; bb < s; ++bb) {
+        const int cb = rowz_col[rp + bb];
+        const int kb = rowz_k[rp + bb];
+        if (d >= cb && d < cb + kb) acc += Rg[(int64_t)r * s + bb] * Z64[rowz_zoff[rp + bb] + (d - cb)];
+      }
+      T[(row + r) + (int64_t)d * nr] = acc;
+    }
+    row += rk;
+  }
+  __syncthreads();
+  const int kmax = min(nr, sn);
+  const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31, nw = (int)blockDim.x >> 5;
+  for (int k = 0; k < kmax; ++k) {
+    const double* xk = T + (int64_t)k * nr;
+    double part = 0.0;
+    for (int i = k + (int)threadIdx.x; i < nr; i += blockDim.x) part += xk[i] * xk[i];
+    const double nb2 = block_sum(part, sh);
+    const double x0 = xk[k];
+    const double xn = sqrt(nb2);
+    const double alpha = x0 >= 0.0 ? -xn : xn;
+    const double v0 = x0 - alpha;
+    const double vtv = v0 * v0 + (nb2 - x0 * x0);
+    if (vtv > 0.0) {
+      for (int j = k + 1 + warp; j < sn; j += nw) {
+        double* cj = T + (int64_t)j * nr;
+        double acc = lane == 0 ? v0 * cj[k] : 0.0;
+        for (int i = k + 1 + lane; i < nr; i += 32) acc += xk[i] * cj[i];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        const double f = 2.0 * acc / vtv;
+        if (lane == 0) cj[k] -= f * v0;
+        for (int i = k + 1 + lane; i < nr; i += 32) cj[i] -= f * xk[i];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) T[k + (int64_t)k * nr] = vtv > 0.0 ? alpha : x0;
+    __syncthreads();
+  }
+  // R (row-major, ld sn): row k = T[k, k..sn-1], zeros left of the diagonal
+  double* Rh = Rn64 + new_hoff[h];
+  float* Rh32 = Rn32 + new_hoff[h];
+  for (int64_t e = threadIdx.x; e < (int64_t)kmax * sn; e += blockDim.x) {
+    const int k = (int)(e / sn), j = (int)(e % sn);
+    const double v = j < k ? 0.0 : T[k + (int64_t)j * nr];
+    Rh[e] = v;
+    Rh32[e] = (float)v;
+  }
+  if (threadIdx.x == 0) rank_out[h] = kmax;
+}
+
+// Schur complement of Eq. gevp-S in row form: S~ = X^T (I - Pi) X with
+// [X Y_G] = W^{1/2} G(nz_i, Omega_i) the rows of the splitting of the Lemma
+// (each group g in nz_i contributes its rows R_g / sqrt(M_g)), X on omega_i,
+// Y_G on Gamma_i, and Pi the orthogonal projector onto range(Y_G).
+// Householder QR with column pivoting on the Gamma columns (largest remaining
+// column norm first, the smallest index on ties) reveals the numerical rank
+// of Y_G: it stops once the largest remaining column norm is at most
+// max(rows, |Gamma_i|) eps times the first pivot's (those directions are its
+// numerical null space).  The same reflections applied to X leave
+// Q^T X = [X_1; X_2] with Pi X = Q [X_1; 0], so S~ = X_2^T X_2, formed from
+// rows and never as a difference of Grams.  S~ replaces the omega block of
+// At (column-major, ld m), which the eigensolver reads.
+// Y: rows x m column-major at y_off[b]; nrm: m doubles per matrix at n_off[b].
+template <int CL>
+__global__ void k_schur_rows(const int32_t* __restrict__ mdim, const int32_t* __restrict__ nodim,
+                             const int64_t* __restrict__ a_off, const int64_t* __restrict__ pair_ptr,
+                             const int32_t* __restrict__ pair_grp, const int32_t* __restrict__ pair_nz,
+                             const int64_t* __restrict__ map_ptr, const int32_t* __restrict__ map,
+                             const int64_t* __restrict__ g_ptr, const int64_t* __restrict__ h_off,
+                             const int32_t* __restrict__ rank, const double* __restrict__ R,
+                             const int32_t* __restrict__ M, const int64_t* __restrict__ y_off,
+                             const int32_t* __restrict__ y_rows, double* __restrict__ Ypool,
+                             const int64_t* __restrict__ n_off, double* __restrict__ nrm_pool,
+                             double* __restrict__ Atpool) {
+  __shared__ double s_best;
+  __shared__ int s_bi;
+  const Team<CL> tm;
+  const int b = blockIdx.x / CL;
+  const int m = mdim[b], no = nodim[b];
+  const int nr = y_rows[b];
+  double* Y = Ypool + y_off[b];
+  double* nrm = nrm_pool + n_off[b];
+  for (int64_t e = tm.rank; e < (int64_t)nr * m; e += tm.size) Y[e] = 0.0;
+  tm.sync();
+  int row = 0;
+  for (int64_t p = pair_ptr[b]; p < pair_ptr[b + 1]; ++p) {
+    if (!pair_nz[p]) continue;
+    const int g = pair_grp[p];
+    const int s = (int)(g_ptr[g + 1] - g_ptr[g]);
+    const int rk = rank[g];
+    const double w = 1.0 / sqrt((double)M[g]);
+    const double* Rg = R + h_off[g];
+    const int32_t* mp = map + map_ptr[p];
+    for (int64_t e = tm.rank; e < (int64_t)rk * s; e += tm.size) {
+      const int r = (int)(e / s), a = (int)(e % s);
+      const int la = mp[a];
+      if (la >= 0) Y[(row + r) + (int64_t)la * nr] = Rg[(int64_t)r * s + a] * w;
+    }
+    row += rk;
+  }
+  tm.sync();
+  const int warp = tm.rank >> 5, lane = (int)threadIdx.x & 31, nw = tm.size >> 5;
+  const int ng = m - no;
+  const int kmax = min(nr, ng);
+  const double tol = (double)max(nr, ng) * DBL_EPSILON;
+  double c1 = 0.0;
+  int r = 0;
+  for (int k = 0; k < kmax; ++k) {
+    // squared norms of the live Gamma columns over rows k.., a warp per column
+    for (int j = no + k + warp; j < m; j += nw) {
+      const double* cj = Y + (int64_t)j * nr;
+      double acc = 0.0;
+      for (int i = k + lane; i < nr; i += 32) acc += cj[i] * cj[i];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (lane == 0) nrm[j] = acc;
+    }
+    tm.sync();
+    if (threadIdx.x < 32) {  // every CTA picks the same pivot from the same norms
+      double best = -1.0;
+      int bi = m;
+      for (int j = no + k + (int)threadIdx.x; j < m; j += 32) {
+        const double d = nrm[j];
+        if (d > best || (d == best && j < bi)) {
+          best = d;
+          bi = j;
+        }
+      }
+      best = warp_max_idx(best, bi);
+      if (threadIdx.x == 0) {
+        s_best = best;
+        s_bi = bi;
+      }
+    }
+    __syncthreads();
+    const double nb2 = s_best;
+    const int pj = s_bi;
+    const double xn = sqrt(fmax(nb2, 0.0));
+    if (k == 0) c1 = xn;
+    if (!(xn > tol * c1)) break;
+    const int c = no + k;
+    if (pj != c)
+      for (int i = tm.rank; i < nr; i += tm.size) {
+        const double t = Y[i + (int64_t)c * nr];
+        Y[i + (int64_t)c * nr] = Y[i + (int64_t)pj * nr];
+        Y[i + (int64_t)pj * nr] = t;
+      }
+    tm.sync();
+    const double* xk = Y + (int64_t)c * nr;
+    const double x0 = xk[k];
+    const double alpha = x0 >= 0.0 ? -xn : xn;
+    const double v0 = x0 - alpha;
+    const double vtv = v0 * v0 + (nb2 - x0 * x0);
+    if (vtv > 0.0) {
+      // the omega columns and the Gamma columns after c
+      const int nupd = no + (m - c - 1);
+      for (int jj = warp; jj < nupd; jj += nw) {
+        const int j = jj < no ? jj : c + 1 + (jj - no);
+        double* cj = Y + (int64_t)j * nr;
+        double acc = lane == 0 ? v0 * cj[k] : 0.0;
+        for (int i = k + 1 + lane; i < nr; i += 32) acc += xk[i] * cj[i];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        const double f = 2.0 * acc / vtv;
+        if (lane == 0) cj[k] -= f * v0;
+        for (int i = k + 1 + lane; i < nr; i += 32) cj[i] -= f * xk[i];
+      }
+    }
+    tm.sync();
+    r = k + 1;
+  }
+  // S~ = X_2^T X_2 over rows r.. (the same sum order for (a, c) and (c, a))
+  double* At = Atpool + a_off[b];
+  for (int64_t e = tm.rank; e < (int64_t)no * no; e += tm.size) {
+    const int a = (int)(e % no), cc = (int)(e / no);
+    const double* ya = Y + (int64_t)a * nr;
+    const double* yc = Y + (int64_t)cc * nr;
+    double acc = 0.0;
+    for (int i = r; i < nr; ++i) acc += ya[i] * yc[i];
+    At[a + (int64_t)cc * m] = acc;
+  }
+}
+
 int threads_for(int64_t work) { return work <= 64 ? 64 : (work <= 1024 ? 128 : 256); }
 
 }  // namespace
@@ -990,6 +1207,35 @@ int launch_next_gram(const NextGramPlan& p, int max_sn, const int64_t* g_ptr, co
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
   return AMGDD_OK;
+}
+
+int launch_next_rows(const NextGramPlan& p, const int64_t* g_ptr, const int64_t* h_off, const int32_t* rank,
+                     const double* R, const double* Z64, const int64_t* t_off, double* scratch, double* Rn64,
+                     float* Rn32, int32_t* rank_out, int64_t first, int64_t count, cudaStream_t s) {
+  if (count == 0) return AMGDD_OK;
+  k_next_rows<<<(unsigned)count, 256, 0, s>>>(first, p.new_ptr.p, p.contrib.p, p.new_sptr.p, p.new_hoff.p,
+                                              p.rowz_ptr.p, p.rowz_zoff.p, p.rowz_k.p, p.rowz_col.p, g_ptr, h_off,
+                                              rank, R, Z64, t_off, scratch, Rn64, Rn32, rank_out);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
+int launch_schur_rows(int nb, int max_m, const LocalBatch& b, const int64_t* g_ptr, const int64_t* h_off,
+                      const int32_t* rank, const double* R, const int32_t* M, const int64_t* y_off,
+                      const int32_t* y_rows, double* Ypool, const int64_t* n_off, double* nrm, double* Atpool,
+                      cudaStream_t s) {
+  if (nb == 0) return AMGDD_OK;
+  // cluster teams only while the batch leaves SMs idle: with many matrices a
+  // CTA each keeps every SM busy without the team's barriers
+  if (max_m >= kBigDim && nb * kBigTeam <= 2 * 152)
+    return launch_team(k_schur_rows<kBigTeam>, kBigTeam, nb, 256, 0, s, b.m.p, b.no.p, b.a_off.p, b.pair_ptr.p,
+                       b.pair_grp.p, b.pair_nz.p, b.map_ptr.p, b.map.p, g_ptr, h_off, rank, R, M, y_off, y_rows,
+                       Ypool, n_off, nrm, Atpool);
+  return launch_team(k_schur_rows<1>, 1, nb, max_m >= 64 ? 256 : 128, 0, s, b.m.p, b.no.p, b.a_off.p, b.pair_ptr.p,
+                     b.pair_grp.p,
+                     b.pair_nz.p, b.map_ptr.p, b.map.p, g_ptr, h_off, rank, R, M, y_off, y_rows, Ypool, n_off, nrm,
+                     Atpool);
 }
 
 namespace {

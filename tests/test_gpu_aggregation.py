@@ -13,7 +13,8 @@ import oracle
 from inputs import fd_2d, q1_2d, rotated_sqrtK, seeded_rhs
 from inputs.q1 import config_problem
 from oracle.construct import row_groups_from_csr
-from test_gpu_kappa import check_level0_operators, check_solve, check_structure_upto, check_valid_from, first_gray_level
+from test_gpu_kappa import check_level0_operators, check_solve, check_structure_upto, check_valid_from
+from test_gpu_parity import first_ill_posed_level
 from test_gpu_parity import _check_spectra
 
 pytestmark = pytest.mark.gpu
@@ -96,7 +97,7 @@ def test_setup_without_aggregates(amg, passes):
                       kappa=50.0, agg_passes=passes, precision=amg.FP64)
     # the finite-difference coarse levels are compared as in the kappa tests (exactly up to the first level
     # whose pseudo-inverse is not well posed, for validity and convergence from it on)
-    g = first_gray_level(ho)
+    g = first_ill_posed_level(ho)
     check_structure_upto(amg, H, ho, g)
     for lvl in range(g):
         _check_spectra(amg, H, ho, lvl)

@@ -91,6 +91,63 @@ def _x_at_iters(H, b, iters):
     return x[:, 0] if x.ndim == 2 else x
 
 
+EPS = np.finfo(np.float64).eps
+
+
+def row_conditioning(ho):
+    """Per level l (below the coarsest): (c_l, gap_l) from the oracle's rows of the splitting.
+
+    The Schur complement of Eq. gevp-S in row form, S~ = X^T (I - Pi) X, depends on the projector Pi onto
+    the Gamma rows Y_G, cut at their numerical rank (max(shape) eps of the largest singular value).  A
+    rounding perturbation dY ~ eps ||Y|| moves Pi by ||dY|| / sigma_min (first-order perturbation of an
+    orthogonal projector, sigma_min the smallest kept singular value), so no FP64 computation of this
+    level is accurate beyond c_l = max_i eps ||Y_G|| / sigma_min(Y_G): the parity bar on a level is
+    max(bar, 8 c) with c the largest c_j of this and the finer levels.  gap_l = min over aggregates of
+    the distance of the kept and dropped singular values from the cut (as a factor); below 10 the rank
+    itself is not determined by FP64 data and parity is not posed (the rounding noise of the rows, the
+    dropped values of a clean level, sits about 100 below the cut)."""
+    if getattr(ho, "_rowcond", None) is not None:
+        return ho._rowcond
+    from oracle.construct import local_splitting_rows
+
+    out = []
+    for L in ho.levels[:-1]:
+        c, gap = 0.0, np.inf
+        for i in range(L.nagg):
+            no = L.omega[i].shape[0]
+            Y = local_splitting_rows(L.Omega[i], L.nz[i], L.sups, L.rows, L.M)
+            YG = Y[:, no:]
+            if YG.size == 0:
+                continue
+            sv = np.linalg.svd(YG, compute_uv=False)
+            if sv.max() <= 0:
+                continue
+            cut = max(YG.shape) * EPS * sv.max()
+            kept, dropped = sv[sv > cut], sv[sv <= cut]
+            c = max(c, EPS * sv.max() / kept.min())
+            gap = min(gap, kept.min() / cut, cut / dropped.max() if dropped.size and dropped.max() > 0 else np.inf)
+        out.append((c, gap))
+    ho._rowcond = out
+    return out
+
+
+def level_bar(ho, lvl, bar):
+    """max(bar, 8 c) with c the row conditioning of levels <= lvl (row_conditioning)."""
+    rc = row_conditioning(ho)
+    c = max([0.0] + [rc[j][0] for j in range(min(lvl + 1, len(rc)))])
+    return max(bar, 8.0 * c)
+
+
+def first_ill_posed_level(ho):
+    """First level whose Gamma rows have singular values within a factor 10 of the rank cut (its rank is not
+    fixed by FP64 data), or whose conditioning c_l exceeds 1e-6 (beyond that the first-order bound 8 c no
+    longer holds: second-order terms and the finer levels' errors take over); len(levels) - 1 if none."""
+    for lvl, (c, gap) in enumerate(row_conditioning(ho)):
+        if gap <= 10.0 or c > 1e-6:
+            return lvl
+    return len(ho.levels) - 1
+
+
 def _check_patterns(amg, H, Lo, lvl, coarsest):
     """Structural patterns, bit-exact: the row-group supports of G_l, A_l and P_l."""
     # the distinct row supports of G_l (how rows with one support are grouped is each side's own choice)
@@ -144,8 +201,8 @@ def _degenerate_cut(mu, k, no):
 
 
 def _check_spectra(amg, H, ho, lvl, tol_mu=None, tol_angle=None):
-    tol_mu = tol_mu if tol_mu is not None else (1e-11 if lvl == 0 else 1e-10)
-    tol_angle = tol_angle if tol_angle is not None else (1e-10 if lvl == 0 else 1e-9)
+    tol_mu = tol_mu if tol_mu is not None else level_bar(ho, lvl, 1e-11 if lvl == 0 else 1e-10)
+    tol_angle = tol_angle if tol_angle is not None else level_bar(ho, lvl, 1e-10 if lvl == 0 else 1e-9)
     Lo = ho.levels[lvl]
     mu = H.export(lvl, amg.ARR_MU)
     Z = H.export(lvl, amg.ARR_Z)
@@ -293,7 +350,7 @@ def test_level0_forms_match_oracle(amg, name, ell):
     xg, ig = H.solve(b, tol=1e-8)
     assert ig[0]["status"] == 0 and ig[0]["relres_true"] <= 1e-8
     assert abs(ig[0]["iters"] - io["iters"]) <= 1
-    assert _rel(_x_at_iters(H, b, io["iters"]), xo) <= 1e-10
+    assert _rel(_x_at_iters(H, b, io["iters"]), xo) <= level_bar(ho, len(ho.levels), 1e-10)
     H.set_precision(amg.MIXED32)
     _, im = H.solve(b, tol=1e-8)
     assert im[0]["status"] == 0 and im[0]["relres_true"] <= 1e-8
@@ -326,7 +383,7 @@ def test_deterministic_repeats_bitwise(amg, name):
     xo, io = oracle.pcg(ho, b, tol=1e-8)
     xg, ig = H.solve(b, tol=1e-8)
     assert abs(ig[0]["iters"] - io["iters"]) <= 1
-    assert _rel(_x_at_iters(H, b, io["iters"]), xo) <= 1e-10
+    assert _rel(_x_at_iters(H, b, io["iters"]), xo) <= level_bar(ho, len(ho.levels), 1e-10)
 
 
 def test_saved_hierarchy_reloads(amg, tmp_path):
@@ -363,8 +420,8 @@ def _check_level_operators(amg, c, H, ho, upto=None):
         if upto is not None and upto < last and lvl > upto:
             return
         x = rng.standard_normal(Lo.n)
-        tA = 1e-13 if lvl == 0 else 1e-10
-        tS = 1e-12 if lvl == 0 else 1e-10
+        tA = 1e-13 if lvl == 0 else level_bar(ho, lvl - 1, 1e-10)
+        tS = 1e-12 if lvl == 0 else level_bar(ho, lvl - 1, 1e-10)
         assert _rel(_apply(amg, H, amg.OP_A, lvl, x, Lo.n), Lo.A @ x) <= tA
         assert _rel(_apply(amg, H, amg.OP_RAS, lvl, x, Lo.n), oracle.ras(Lo, x)) <= tS
         assert _rel(_apply(amg, H, amg.OP_RAST, lvl, x, Lo.n), oracle.rast(Lo, x)) <= tS
@@ -376,7 +433,7 @@ def _check_level_operators(amg, c, H, ho, upto=None):
         rc = _apply(amg, H, amg.OP_RESTRICT, lvl, x, nn)
         y = _apply(amg, H, amg.OP_PROLONG, lvl, rc, Lo.n)
         yo = Lo.P @ (Lo.P.T @ x)
-        tP = 1e-10 if lvl == 0 else 1e-9
+        tP = level_bar(ho, lvl, 1e-10 if lvl == 0 else 1e-9)
         for i in range(Lo.nagg):
             if _degenerate_cut(Lo.mu[i], Lo.Z[i].shape[1], Lo.omega[i].shape[0]):
                 continue
@@ -388,13 +445,13 @@ def _check_level_operators(amg, c, H, ho, upto=None):
         # the V-cycle from level 0 (the preconditioner) is basis-independent;
         # from a coarse level it is written in the basis the level above
         # selected, like A_l and the smoothers there
-        tV = c.get("tol_vcycle", 1e-12) if lvl == 0 else 1e-10
+        tV = level_bar(ho, len(ho.levels), c.get("tol_vcycle", 1e-12) if lvl == 0 else 1e-10)
         assert _rel(v, oracle.vcycle(ho, x, lvl)) <= tV, (lvl, _rel(v, oracle.vcycle(ho, x, lvl)))
     Lc = ho.levels[-1]
     xc = rng.standard_normal(Lc.n)
     ref = np.linalg.solve(Lc.A.toarray(), xc)
     # A_L is written in the basis of level L-1
-    tC = 1e-11 if len(ho.levels) == 2 else 1e-9
+    tC = level_bar(ho, len(ho.levels), 1e-11 if len(ho.levels) == 2 else 1e-9)
     assert _rel(_apply(amg, H, amg.OP_COARSE, len(ho.levels) - 1, xc, Lc.n), ref) <= tC
 
 
@@ -436,7 +493,7 @@ def test_pcg_fp64_matches_oracle(amg, name):
     xg, ig = H.solve(b, tol=1e-8)
     assert ig[0]["status"] == 0 and ig[0]["relres_true"] <= 1e-8
     assert abs(ig[0]["iters"] - io["iters"]) <= 1
-    assert _rel(_x_at_iters(H, b, io["iters"]), xo) <= 1e-10
+    assert _rel(_x_at_iters(H, b, io["iters"]), xo) <= level_bar(ho, len(ho.levels), 1e-10)
 
 
 @pytest.fixture(scope="module")
@@ -447,55 +504,30 @@ def case_256():
     return p, cfg, ho
 
 
-def first_gray_level(ho, lo=1e-14, hi=1e-8):
-    """First level with a block A~_GG holding an eigenvalue in (lo, hi) x its largest (len(levels) - 1 if
-    none): from there the pseudo-inverse of Eq. gevp-S formed from Grams in FP64 is no longer well posed,
-    and the oracle's own Gram route departs from its row route."""
-    for lvl, L in enumerate(ho.levels[:-1]):
-        for i in range(L.nagg):
-            no = L.omega[i].shape[0]
-            G = L.Atil[i][no:, no:]
-            if G.shape[0] == 0:
-                continue
-            w = np.linalg.eigvalsh(G)
-            r = w / w.max()
-            if np.any((r > lo) & (r < hi)):
-                return lvl
-    return len(ho.levels) - 1
-
-
 def test_timed_plans_at_256(amg, case_256):
     """The benchmark workload (theta = pi/6, eps = 1e-4, 4 x 4 aggregates, LS_{2,3,4}, n_coarse 2000) at
     256 x 256 cells: 65,025 unknowns on five levels, with every kernel form chosen by setup timing (tune = 1,
     the default), so that multi-chunk blocks, many rows per CTA, block-row coarse A and whatever dense tail
-    the timing picks run under the parity bar: structure and patterns, spectra and every operator on each
-    level up to the first whose Schur complement is ill posed in Gram form (reading 3 of the design notes;
-    level 3 here), and from there a valid hierarchy and the same PCG iteration count."""
+    the timing picks run under the full parity bar: structure and patterns, spectra, every operator of
+    every level, and the PCG iterate at the oracle's iteration count.  Level 3's Gamma rows have singular
+    values down to 9e-10 of their largest (with a clean gap above the rank cut), so no FP64 computation of
+    that level is accurate beyond about 2.4e-7 (row_conditioning): the bars there are scaled by it."""
     p, cfg, ho = case_256
     assert len(ho.levels) == 5
     H = amg.Hierarchy.from_problem(p, overlap=cfg["overlap"], c_min=cfg["c_min"], n_coarse=cfg["n_coarse"], tune=1)
-    g = first_gray_level(ho)
-    for lvl in range(g + 1):
-        Lo = ho.levels[lvl]
-        assert H.describe(lvl)["n"] == Lo.n
-        _check_patterns(amg, H, Lo, lvl, lvl >= g)
-        assert np.array_equal(H.export(lvl, amg.ARR_AGG), Lo.agg.astype(np.int32))
-        if lvl < g:
-            assert np.array_equal(H.export(lvl, amg.ARR_K), np.array([Z.shape[1] for Z in Lo.Z], dtype=np.int32))
-            _check_spectra(amg, H, ho, lvl)
-    _check_level_operators(amg, {}, H, ho, upto=g)
-    for lvl in range(g, H.num_levels - 1):  # the library's own levels: mu in [0, 1], k_i within its cap
-        mu = H.export(lvl, amg.ARR_MU)
-        assert mu.min() >= -1e-10 and mu.max() <= 1 + 1e-10, lvl
+    assert first_ill_posed_level(ho) == len(ho.levels) - 1
+    _check_structure(amg, H, ho)
+    for lvl in range(len(ho.levels) - 1):
+        _check_spectra(amg, H, ho, lvl)
+    _check_level_operators(amg, {}, H, ho)
     b = seeded_rhs(p.n, 1, 1)[:, 0]
     xo, io = oracle.pcg(ho, b, tol=1e-8)
     xg, ig = H.solve(b, tol=1e-8)
     assert ig[0]["status"] == 0 and ig[0]["relres_true"] <= 1e-8
     assert abs(ig[0]["iters"] - io["iters"]) <= 1
-    if g == len(ho.levels) - 1:
-        assert _rel(_x_at_iters(H, b, io["iters"]), xo) <= 1e-10
+    assert _rel(_x_at_iters(H, b, io["iters"]), xo) <= level_bar(ho, len(ho.levels), 1e-10)
     H.set_precision(amg.MIXED32)
-    _check_level_operators_mixed(amg, H, ho, upto=g)
+    _check_level_operators_mixed(amg, H, ho)
     x32, i32 = H.solve(b, tol=1e-8)
     assert i32[0]["status"] == 0 and i32[0]["relres_true"] <= 1e-8
     assert i32[0]["iters"] <= ig[0]["iters"] + 2
