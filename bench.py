@@ -78,6 +78,18 @@ def parse_args():
     return ap.parse_args()
 
 
+def setup_rates(stats, fp64_gflops):
+    """Setup phases: counted FP64 GFLOP (a model from the block sizes), milliseconds, GFLOP/s and the fraction of
+    the device's measured FP64 FMA rate (amgdd_measure_fp64)."""
+    out = {"fp64_gflops_measured": round(fp64_gflops, 1), "phases": {}}
+    for k, gf in stats.get("setup_phases_gflop", {}).items():
+        ms = stats["setup_phases_ms"].get(k, 0.0)
+        rate = gf / (ms * 1e-3) if ms > 0 else None
+        out["phases"][k] = {"gflop": round(gf, 3), "ms": round(ms, 1), "gflops": None if rate is None else round(rate, 1),
+                            "frac_of_fp64": None if rate is None else round(rate / fp64_gflops, 4)}
+    return out
+
+
 def replica_max(v, world, device="cuda"):
     """Max of a per-rank value over the replicas (the slowest rank's time
     sets whole-job throughput); the identity with one rank."""
@@ -556,7 +568,7 @@ def run_ours(args):
     # warm-up (every precision: graph capture, first-touch)
     for prec in (amg.FP64, amg.MIXED32, amg.MIXED16):
         timed(prec, 0, args.warmup, B, X)
-    HEAD = amg.MIXED16  # the headline precision: FP16 matrices, FP32 vectors, FP64 flexible CG
+    HEAD = amg.MIXED32  # the headline precision: FP32 V-cycle, FP64 flexible CG (MIXED16 reported beside it)
     if args.profile_only:
         H.set_precision(HEAD)
         # the NVTX range lets a profiler select these V-cycles (setup's own
@@ -571,12 +583,12 @@ def run_ours(args):
     time.sleep(0.3)  # nvidia-smi's own start-up, so that its samples fall inside the timed region
     t_mix, w_mix, inf_mix, launches = timed(HEAD, args.warmup, args.steps, B, X)
     clocks = sampler.stop()
-    t_32, w_32, inf_32, _ = timed(amg.MIXED32, args.warmup, args.steps, B, X)
+    t_16, w_16, inf_16, _ = timed(amg.MIXED16, args.warmup, args.steps, B, X)
     t_64, w_64, inf_64, _ = timed(amg.FP64, args.warmup, args.steps, B, X)
     t_mix = maxrank(t_mix)
-    t_32 = maxrank(t_32)
+    t_16 = maxrank(t_16)
     t_64 = maxrank(t_64)
-    for inf in inf_mix + inf_32 + inf_64:
+    for inf in inf_mix + inf_16 + inf_64:
         assert inf["status"] == 0 and inf["relres_true"] <= 1e-8, inf
     fallbacks = sum(i["fallback"] for i in inf_mix)
     it_mix = [i["iters"] for i in inf_mix]
@@ -584,7 +596,7 @@ def run_ours(args):
     solves = args.steps * world
     value = solves / t_mix
     fp64_value = solves / t_64
-    m32_value = solves / t_32
+    m16_value = solves / t_16
     vc_mix = sum(i + 1 for i in it_mix) * world / t_mix
     vc_64 = sum(i + 1 for i in it_64) * world / t_64
     lat = sorted(i["solve_ms"] for i in inf_mix)
@@ -594,16 +606,14 @@ def run_ours(args):
     # solve replays its cycle as a graph too); the eager profile (events
     # between separately launched kernels, host launch gaps included) is
     # reported beside it.
-    H.set_precision(HEAD)
-    ms, by, cyc_graph_ms = H.profile_vcycle(10, graph=True)
-    ms_e, by_e = H.profile_vcycle(10)
-    # kernel families by profile slot: slot 6 is the persistent tail (one
-    # cooperative launch for every level from its first), slot 2 the two
-    # residuals (k_seg over block rows or grouped k_apply), slots 1/5 casts
     forms = [c["form"] for c in stats["coarse_A"]]
     dense_l = stats.get("dense_tail", {}).get("mixed", {}).get("from", 0)
+    peak, peak_kind = hbm_peak()
 
     def families(ms, by):
+        # kernel families by profile slot: slot 6 is the persistent tail (one
+        # cooperative launch for every level from its first), slot 2 the two
+        # residuals (k_seg over block rows or grouped k_apply), slots 1/5 casts
         fam_ms, fam_by, fam_n = {}, {}, {}
         for l in range(ms.shape[0]):
             for k in range(ms.shape[1]):
@@ -624,46 +634,57 @@ def run_ours(args):
                 fam_n[fam] = fam_n.get(fam, 0) + nk
         return fam_ms, fam_by, fam_n
 
-    fam_ms, fam_by, fam_n = families(ms, by)
-    fam_ms_e, fam_by_e, _ = families(ms_e, by_e)
-    peak, peak_kind = hbm_peak()
-    top = max(fam_ms, key=fam_ms.get)
-    kdesc = {"k_seg": "k_seg (batched gather-GEMV-scatter: RAS, RAS-T, P, R, block-row residuals; FP16 matrices "
-                      "where setup timed them faster, else FP32; FP32 vectors)",
-             "k_apply": "k_apply (grouped G then G^T residual; FP32)",
-             "k_persistent": "k_persistent (cooperative V-cycle tail: every phase of the coarse levels; FP32)",
-             "k_dense": "k_dense (dense V-cycle tail GEMV; FP32)",
-             "k_ell": "k_ell (level-0 residual by ELL rows of A; FP32)",
-             "k_cast": "k_cast"}
-    # the event record nodes of the marked graph add their own gaps, so the
-    # family's time inside the plain graph is taken as its share of the
-    # marked cycle applied to the plain cycle's replay time
-    kby = fam_by[top]
-    share = fam_ms[top] / float(ms.sum())
-    kms = cyc_graph_ms * share
-    achieved = kby / (kms * 1e-3) / 1e9
-    # DRAM bytes per V-cycle of a kernel family from an ncu capture of this
-    # workload (profiles/); valid only while those kernels are unchanged
-    traffic = (TRAFFIC.get(top) if args.workload == WORKLOAD and args.N is None and not args.deterministic
-               and args.tune_mode == "timed" else None)
-    cyc_bytes = float(by.sum())
-    kms_e = fam_ms_e.get(top, 0.0)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_unit": "bytes per V-cycle (kernel family)",
-                "kernel": kdesc.get(top, top), "launches_per_vcycle": fam_n[top],
-                "bytes_per_vcycle": kby, "ms_per_vcycle": kms,
-                "timing": ("V-cycle replayed as a CUDA graph (CUDA events around the replay); the family's time is "
-                           "its share of the same cycle replayed with event record nodes between its kernels"),
-                "share_of_vcycle": share,
-                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-                "families": {f: {"ms": round(fam_ms[f], 4), "gbs": round(fam_by[f] / (fam_ms[f] * 1e-3) / 1e9, 1),
-                                 "launches": fam_n[f]} for f in fam_ms},
-                "eager": {"ms": round(kms_e, 4),
-                          "frac": (fam_by_e.get(top, 0.0) / (kms_e * 1e-3) / 1e9 / peak) if kms_e > 0 else None,
-                          "timing": "separate launches, CUDA events between them (host launch gaps included)"},
-                "vcycle": {"ms_graph": cyc_graph_ms, "ms_marked_graph": float(ms.sum()), "bytes": cyc_bytes,
-                           "achieved_gbs": cyc_bytes / (cyc_graph_ms * 1e-3) / 1e9,
-                           "frac": cyc_bytes / (cyc_graph_ms * 1e-3) / 1e9 / peak}}
+    def roofline_of(prec, kdesc_seg):
+        H.set_precision(prec)
+        ms, by, cyc_graph_ms = H.profile_vcycle(10, graph=True)
+        ms_e, by_e = H.profile_vcycle(10)
+        fam_ms, fam_by, fam_n = families(ms, by)
+        fam_ms_e, fam_by_e, _ = families(ms_e, by_e)
+        top = max(fam_ms, key=fam_ms.get)
+        kdesc = {"k_seg": kdesc_seg,
+                 "k_apply": "k_apply (grouped G then G^T residual; FP32)",
+                 "k_persistent": "k_persistent (cooperative V-cycle tail: every phase of the coarse levels; FP32)",
+                 "k_dense": "k_dense (dense V-cycle tail GEMV; FP32)",
+                 "k_ell": "k_ell (level-0 residual by ELL rows of A; FP32)",
+                 "k_cast": "k_cast"}
+        # the event record nodes of the marked graph add their own gaps, so the
+        # family's time inside the plain graph is taken as its share of the
+        # marked cycle applied to the plain cycle's replay time
+        kby = fam_by[top]
+        share = fam_ms[top] / float(ms.sum())
+        kms = cyc_graph_ms * share
+        achieved = kby / (kms * 1e-3) / 1e9
+        # DRAM bytes per V-cycle of a kernel family from an ncu capture of this
+        # workload (profiles/); valid only while those kernels are unchanged
+        traffic = (TRAFFIC.get((prec, top)) if args.workload == WORKLOAD and args.N is None and not args.deterministic
+                   and args.tune_mode == "timed" else None)
+        cyc_bytes = float(by.sum())
+        kms_e = fam_ms_e.get(top, 0.0)
+        rl = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+              "traffic": traffic, "traffic_unit": "bytes per V-cycle (kernel family)",
+              "kernel": kdesc.get(top, top), "launches_per_vcycle": fam_n[top],
+              "bytes_per_vcycle": kby, "ms_per_vcycle": kms,
+              "timing": ("V-cycle replayed as a CUDA graph (CUDA events around the replay); the family's time is "
+                         "its share of the same cycle replayed with event record nodes between its kernels"),
+              "share_of_vcycle": share,
+              "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+              "families": {f: {"ms_marked": round(fam_ms[f], 4),
+                               "gbs": round(fam_by[f] / (cyc_graph_ms * fam_ms[f] / float(ms.sum()) * 1e-3) / 1e9,
+                                            1),
+                               "launches": fam_n[f]} for f in fam_ms},
+              "eager": {"ms": round(kms_e, 4),
+                        "frac": (fam_by_e.get(top, 0.0) / (kms_e * 1e-3) / 1e9 / peak) if kms_e > 0 else None,
+                        "timing": "separate launches, CUDA events between them (host launch gaps included)"},
+              "vcycle": {"ms_graph": cyc_graph_ms, "ms_marked_graph": float(ms.sum()), "bytes": cyc_bytes,
+                         "achieved_gbs": cyc_bytes / (cyc_graph_ms * 1e-3) / 1e9,
+                         "frac": cyc_bytes / (cyc_graph_ms * 1e-3) / 1e9 / peak}}
+        return rl, ms, by
+
+    roofline16, _, _ = roofline_of(
+        amg.MIXED16, "k_seg (batched gather-GEMV-scatter: RAS, RAS-T, P, R, block-row residuals; FP16 matrices "
+                     "where setup timed them faster, else FP32; FP32 vectors)")
+    roofline, ms, by = roofline_of(
+        HEAD, "k_seg (batched gather-GEMV-scatter: RAS, RAS-T, P, R, block-row residuals; FP32)")
     slot_names = {0: "ras_coarse_or_dense", 1: "cast_in", 2: "residual_applies", 3: "restrict", 4: "prolong",
                   5: "cast_out", 6: "persistent_tail", 7: "rast"}
     vprof = []
@@ -735,21 +756,24 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_mix / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32+f64", "data": "synthetic",
-        "config": {"workload": workload_desc(cfg),
-                   "precision": "MIXED16: FP16 smoother rows, basis and coarse block rows, FP32 vectors and sums, "
-                                "FP64 flexible CG",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": workload_desc(cfg), "precision": "FP32 V-cycle, FP64 flexible CG",
                    "l2": "inputs larger than L2: one V-cycle moves %.2f GB" % (float(by.sum()) / 1e9),
                    "parallelism": f"replicas x{world}",
                    "mode": "deterministic (no atomics)" if args.deterministic else "default"},
         "fp64": {"value": fp64_value, "unit": "solves/s", "ms_per_step": t_64 / args.steps * 1e3,
                  "iters": it_64},
-        "mixed32": {"value": m32_value, "unit": "solves/s", "ms_per_step": t_32 / args.steps * 1e3,
-                    "iters": [i["iters"] for i in inf_32]},
+        "mixed16": {"value": m16_value, "unit": "solves/s", "ms_per_step": t_16 / args.steps * 1e3,
+                    "iters": [i["iters"] for i in inf_16],
+                    "precision": "FP16 copies of the smoother rows, basis and coarse block rows where setup timed "
+                                 "them faster, FP32 vectors and sums, FP64 flexible CG",
+                    "roofline": roofline16,
+                    "fp16_lanes_by_level": stats.get("fp16_lanes")},
         "mixed_over_fp64": value / fp64_value,
         "vcycles_per_s": {"mixed": vc_mix, "fp64": vc_64},
         "iters": it_mix, "mixed_fp64_fallbacks": fallbacks, "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "setup_s": setup_s, "setup_phases_ms": {k: round(v, 1) for k, v in stats["setup_phases_ms"].items()},
+        "setup_fp64": setup_rates(stats, amg.measure_fp64()),
         "levels": stats["n"], "op_complexity": stats["op_complexity"],
         "convergence": convergence(inf_64[0]),
         "coarse_A": [c["form"] for c in stats["coarse_A"]],

@@ -379,6 +379,13 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, int graph, double* ms, do
  * captured CUDA graph counts every kernel in it).                         */
 int64_t amgdd_kernel_launches(void);
 
+/* FP64 FMA throughput of the current device in GFLOP/s: independent fused
+ * multiply-add chains (8 per thread) on every SM, the best of three timed
+ * launches (CUDA events on `stream`).  The denominator of the setup phases'
+ * GFLOP/s ("setup_phases_gflop" in amgdd_hierarchy_stats over
+ * "setup_phases_ms").  Errors: INVALID_ARG for a null output, CUDA.       */
+int amgdd_measure_fp64(void* stream, double* gflops);
+
 /* Device bytes the hierarchy holds: what setup kept, plus the batched-solve
  * workspace once allocated (with_batched != 0: counted even before it is,
  * as an admission estimate).  -1 for NULL.                               */

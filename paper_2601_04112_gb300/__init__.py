@@ -35,7 +35,7 @@ EXPORTED = [
     "amgdd_kernel_launches", "amgdd_apply_noalloc", "amgdd_device_bytes", "amgdd_server_params_default",
     "amgdd_server_create", "amgdd_server_add_operator", "amgdd_server_submit", "amgdd_server_poll",
     "amgdd_server_stats", "amgdd_server_destroy", "amgdd_hierarchy_save", "amgdd_hierarchy_load",
-    "amgdd_selftest_wait_timeouts", "amgdd_aggregate", "amgdd_struct_size",
+    "amgdd_selftest_wait_timeouts", "amgdd_aggregate", "amgdd_struct_size", "amgdd_measure_fp64",
 ]
 AMGDD_PENDING = 1
 
@@ -132,6 +132,8 @@ def load_library(path: str = LIB_PATH):
                  "amgdd_num_levels",
                  "amgdd_level_describe", "amgdd_level_export", "amgdd_hierarchy_stats", "amgdd_bytes_model"):
         getattr(lib, name).restype = i32
+    lib.amgdd_measure_fp64.argtypes = [vp, ctypes.POINTER(dbl)]
+    lib.amgdd_measure_fp64.restype = i32
     lib.amgdd_struct_size.argtypes = [i32]
     lib.amgdd_struct_size.restype = ctypes.c_size_t
     for which, st in enumerate((Params, Info, LevelDesc, Csr, ServerParams)):
@@ -192,6 +194,14 @@ def selftest_wait_timeouts(stream=None) -> tuple[int, int]:
     a, b = ctypes.c_int(0), ctypes.c_int(0)
     _check(lib.amgdd_selftest_wait_timeouts(_stream(stream), ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def measure_fp64(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device, GFLOP/s (amgdd_measure_fp64)."""
+    lib = load_library()
+    g = ctypes.c_double()
+    _check(lib.amgdd_measure_fp64(_stream(stream), ctypes.byref(g)))
+    return float(g.value)
 
 
 def kernel_launches() -> int:

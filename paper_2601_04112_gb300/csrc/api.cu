@@ -80,6 +80,54 @@ struct TuneCtx {
 };
 static thread_local TuneCtx* g_tune = nullptr;
 
+// Setup times the kernel forms of each plan on a cold L2, as the V-cycle
+// meets them (every matrix is read once per cycle): before each timed launch
+// a 256 MiB buffer (twice the L2) is overwritten.  One buffer per setup (or
+// per build of the FP16 copies), released with it.
+struct L2Flush {
+  DBuf<char> buf;
+  int run(cudaStream_t s) {
+    if (buf.p == nullptr) AMGDD_TRY(buf.alloc((size_t)256 << 20));
+    AMGDD_CUDA(cudaMemsetAsync(buf.p, 0, buf.n, s));
+    return AMGDD_OK;
+  }
+};
+static thread_local L2Flush* g_flush = nullptr;
+struct FlushScope {
+  L2Flush f;
+  L2Flush* prev;
+  FlushScope() : prev(g_flush) {
+    if (prev == nullptr) g_flush = &f;
+  }
+  ~FlushScope() {
+    if (prev == nullptr) g_flush = nullptr;
+  }
+};
+
+// Mean device time (ms) of `reps` launches of `launch`, each on a cold L2
+// (when a flush scope is active), after two warm-up launches.
+template <class F>
+static int time_cold(cudaStream_t s, int reps, F&& launch, float* ms_out) {
+  cudaEvent_t e[2];
+  for (auto& v : e) AMGDD_CUDA(cudaEventCreate(&v));
+  int rc = AMGDD_OK;
+  float tot = 0.f;
+  for (int rep = 0; rep < reps + 2 && rc == AMGDD_OK; ++rep) {
+    if (g_flush) rc = g_flush->run(s);
+    if (rc == AMGDD_OK) rc = cudaEventRecord(e[0], s) == cudaSuccess ? AMGDD_OK : AMGDD_ERR_CUDA;
+    if (rc == AMGDD_OK) rc = launch();
+    if (rc == AMGDD_OK) rc = cudaEventRecord(e[1], s) == cudaSuccess ? AMGDD_OK : AMGDD_ERR_CUDA;
+    float ms = 0.f;
+    if (rc == AMGDD_OK &&
+        (cudaEventSynchronize(e[1]) != cudaSuccess || cudaEventElapsedTime(&ms, e[0], e[1]) != cudaSuccess))
+      rc = AMGDD_ERR_CUDA;
+    if (rep >= 2) tot += ms;
+  }
+  for (auto& v : e) cudaEventDestroy(v);
+  *ms_out = tot;
+  return rc;
+}
+
 static std::atomic<int64_t> g_kernels{0};
 static thread_local bool g_capturing = false;
 static thread_local int64_t g_capture_kernels = 0;
@@ -657,8 +705,6 @@ int tune_seg(SegPlan& p, const std::string& key, const T* M, const T* MT, int64_
         }
       }
   }
-  cudaEvent_t e[2];
-  for (auto& v : e) AMGDD_CUDA(cudaEventCreate(&v));
   constexpr int kReps = 8;
   int rc = AMGDD_OK;
   float best_t = 0.f;
@@ -668,23 +714,18 @@ int tune_seg(SegPlan& p, const std::string& key, const T* M, const T* MT, int64_
     const Cand& c = cands[ci];
     set_form(c.form);
     if (c.form == 0 || c.form == 2) rc = set_layout(c.lanes, c.rpc);
-    for (int rep = 0; rep < kReps + 2 && rc == AMGDD_OK; ++rep) {
-      if (rep == 2) cudaEventRecord(e[0], s);
-      rc = launch_seg(p, M, f32, xin.p, yout.p, f32, mode, nullptr, s, mode == SEG_RESID ? cin.p : nullptr, nullptr,
-                      MT);
-    }
-    cudaEventRecord(e[1], s);
     float ms = 0.f;
-    if (rc == AMGDD_OK &&
-        (cudaEventSynchronize(e[1]) != cudaSuccess || cudaEventElapsedTime(&ms, e[0], e[1]) != cudaSuccess))
-      rc = AMGDD_ERR_CUDA;
+    if (rc == AMGDD_OK)
+      rc = time_cold(s, kReps, [&] {
+        return launch_seg(p, M, f32, xin.p, yout.p, f32, mode, nullptr, s, mode == SEG_RESID ? cin.p : nullptr,
+                          nullptr, MT);
+      }, &ms);
     if (tf[c.form] == 0.f || ms < tf[c.form]) tf[c.form] = ms;
     if (best < 0 || ms < best_t) {
       best = (int)ci;
       best_t = ms;
     }
   }
-  for (auto& v : e) cudaEventDestroy(v);
   AMGDD_TRY(rc);
   const Cand& b = cands[best];
   set_form(b.form);
@@ -943,6 +984,7 @@ struct amgdd_hierarchy {
   bool mixed_stalled = false;  // an FP32-cycle solve stalled; later MIXED32 solves use the FP64 cycle
   int64_t setup_bytes = 0;  // device bytes held after setup
   double phase_ms[16] = {};  // setup time by phase, summed over levels
+  double phase_flops[16] = {};  // FP64 flops by phase (counted from the block sizes), summed over levels
   const char* phase_name[16] = {};
   int64_t multi_bytes = 0;  // device bytes of the batched-solve workspace, once allocated
   // persistent V-cycle tail per precision (index 1 = MIXED32): phase list,
@@ -1019,6 +1061,10 @@ int compress(Level& L, cudaStream_t s) {
                            scratch.p, per, s));
   }
   AMGDD_TRY(download(L.g_rank, L.d_rank.p, ng, s));
+  for (int64_t g = 0; g < ng; ++g) {  // pivoted Cholesky: the trailing update per kept pivot
+    const double sz = (double)(L.g_ptr[g + 1] - L.g_ptr[g]);
+    for (int k = 0; k < L.g_rank[g]; ++k) g_timer.flops[6] += (sz - k - 1) * (sz - k - 1) + (sz - k);
+  }
   return build_apply(L, s);
 }
 
@@ -1241,6 +1287,7 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
     {
       Phase ph(2, "cholesky", s);
       AMGDD_TRY(launch_chol(nb, max_m, B.m.p, B.a_off.p, Apool.p, dstat.p, s));
+      for (int t = 0; t < nb; ++t) g_timer.flops[2] += (double)bm[t] * bm[t] * bm[t] / 3.0;
     }
     std::vector<int32_t> stat;
     AMGDD_TRY(download(stat, dstat.p, nb, s));
@@ -1270,11 +1317,21 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
         AMGDD_TRY(dyr.upload(yr, s));
         AMGDD_TRY(Ypool.alloc(std::max<int64_t>(yoff[nb], 1)));
         AMGDD_TRY(nrm.alloc(std::max<int64_t>(noff[nb], 1)));
+        DBuf<int32_t> drk;
+        AMGDD_TRY(drk.alloc(nb));
         AMGDD_TRY(launch_schur_rows(nb, bmax_m, B, L.d_g_ptr.p, L.d_h_off.p, L.d_rank.p, L.d_R64.p, dM.p, dyoff.p,
-                                    dyr.p, Ypool.p, dnoff.p, nrm.p, Atpool.p, s));
-        AMGDD_CUDA(cudaStreamSynchronize(s));
+                                    dyr.p, Ypool.p, dnoff.p, nrm.p, Atpool.p, drk.p, s));
+        std::vector<int32_t> rk;
+        AMGDD_TRY(download(rk, drk.p, nb, s));
+        for (int t = 0; t < nb; ++t) {  // per reflection: norms and update of the remaining columns; then X_2^T X_2
+          const double nr = (double)yr[t], m = (double)bm[t], no = (double)bno[t];
+          for (int k = 0; k < rk[t]; ++k) g_timer.flops[3] += 6.0 * (nr - k) * (m - k);
+          g_timer.flops[3] += 2.0 * (nr - rk[t]) * no * no;
+        }
       } else {
         AMGDD_TRY(launch_schur(nb, max_m, B.m.p, B.no.p, B.a_off.p, Atpool.p, h.prm.schur_rtol, s));
+        for (int t = 0; t < nb; ++t)
+          g_timer.flops[3] += 2.0 * (double)(bm[t] - bno[t]) * bm[t] * bm[t] / 2.0;  // at most |Gamma| pivots
       }
     }
     {
@@ -1290,6 +1347,7 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
       AMGDD_TRY(dcc.upload(cc, s));
       AMGDD_TRY(launch_inv_rows(nb, max_m, B.m.p, B.no.p, B.a_off.p, Apool.p, dwoff.p, L.W64.p, L.W32.p, L.Wt64.p,
                                 L.Wt32.p, inv_scratch.p, dcb.p, dcc.p, (int)cb.size(), kInvChunk, s));
+      for (int t = 0; t < nb; ++t) g_timer.flops[4] += 2.0 * (double)bno[t] * bm[t] * bm[t];  // two solves per column
       if (full_inv) {  // the same solves for every column of A_i^{-1} (rows = columns: m per block)
         std::vector<int32_t> fb, fc;
         std::vector<int64_t> fo(nb);
@@ -1312,8 +1370,22 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
     }
     {
       Phase ph(5, "eigen", s);
+      DBuf<int32_t> dwork;
+      AMGDD_TRY(dwork.alloc(nb));
       AMGDD_TRY(launch_gep(nb, max_no, B.m.p, B.no.p, B.a_off.p, Apool.p, Atpool.p, dcap.p, L.thresh, dmuoff.p,
-                           L.mu.p, dzcap.p, Zcap.p, dk.p, gscr.p, dscr.p, s));
+                           L.mu.p, dzcap.p, Zcap.p, dk.p, gscr.p, dscr.p, dwork.p, s));
+      std::vector<int32_t> wk, kk;
+      AMGDD_TRY(download(wk, dwork.p, nb, s));
+      AMGDD_TRY(download(kk, dk.p, nb, s));
+      const bool ql = gep_uses_ql(max_no);
+      for (int t = 0; t < nb; ++t) {
+        // L^{-1} S~ L^{-T}; Jacobi rounds (a full pass over C and V per round, n - 1 rounds a sweep) or the
+        // tridiagonal reduction with its Q and the QL rotations applied to V; Z = L^{-T} V (k columns)
+        const double n = (double)bno[t];
+        double f = 2.0 * n * n * n + 2.0 * n * n * kk[t];
+        f += ql ? (8.0 / 3.0) * n * n * n + 6.0 * n * wk[t] : 12.0 * n * n * (n - 1.0) * wk[t];
+        g_timer.flops[5] += f;
+      }
     }
     std::vector<int32_t> kb;
     AMGDD_TRY(download(kb, dk.p, nb, s));
@@ -1332,6 +1404,24 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
   }
   L.col0.assign(nagg + 1, 0);
   for (int i = 0; i < nagg; ++i) L.col0[i + 1] = L.col0[i] + L.k[i];
+  // every stored smoother and basis entry is finite: the shifted vector loads
+  // of the gather-GEMV multiply a neighbouring row's entries by zero, which
+  // only a finite entry survives (an FP32 overflow would otherwise spread NaN)
+  {
+    DBuf<int> bad;
+    AMGDD_TRY(bad.alloc(1));
+    AMGDD_TRY(bad.zero(s));
+    AMGDD_TRY(count_nonfinite(L.W64.p, (int64_t)L.W64.n, false, bad.p, s));
+    AMGDD_TRY(count_nonfinite(L.W32.p, (int64_t)L.W32.n, true, bad.p, s));
+    AMGDD_TRY(count_nonfinite(L.Z64.p, L.z_off.back(), false, bad.p, s));
+    AMGDD_TRY(count_nonfinite(L.Z32.p, L.z_off.back(), true, bad.p, s));
+    std::vector<int> nb;
+    AMGDD_TRY(download(nb, bad.p, 1, s));
+    if (nb[0] != 0) {
+      set_error("level %d: %d stored smoother or basis entries are not finite", lvl, nb[0]);
+      return AMGDD_ERR_NONFINITE;
+    }
+  }
   return AMGDD_OK;
 }
 
@@ -1490,6 +1580,15 @@ int build_next(amgdd_hierarchy& h, Level& L, Level& N, cudaStream_t s) {
     const int64_t c = std::min(chunk, nnew - f);
     AMGDD_TRY(launch_next_gram(P, max_sn, L.d_g_ptr.p, L.d_h_off.p, L.d_H.p, L.Z64.p, N.d_H.p, scratch.p, f, c, s));
   }
+  for (int64_t q = 0; q < nnew; ++q) {  // T = H_g P_g and P_g^T T: each entry of P_g (sum k) meets s, then sn terms
+    const double sn = (double)(N.g_ptr[q + 1] - N.g_ptr[q]);
+    for (int64_t e = cnt[q]; e < cnt[q + 1]; ++e) {
+      const int32_t g = contrib[e];
+      double ksum = 0.0;
+      for (int64_t t = rz_ptr[g]; t < rz_ptr[g + 1]; ++t) ksum += rz_k[t];
+      g_timer.flops[7] += 2.0 * ksum * ((double)S.len(g) + sn);
+    }
+  }
   AMGDD_CUDA(cudaStreamSynchronize(s));
   if (!h.prm.schur_gram) {
     // row route: G_{l+1}'s rows by QR of the stacked R_g P_g, in chunks of
@@ -1519,6 +1618,12 @@ int build_next(amgdd_hierarchy& h, Level& L, Level& N, cudaStream_t s) {
     }
     AMGDD_TRY(download(N.g_rank, N.d_rank.p, nnew, s));
     N.rows_ready = true;
+    for (int64_t q = 0; q < nnew; ++q) {  // the stacked R_g P_g, then a Householder QR of them
+      const double sn = (double)(N.g_ptr[q + 1] - N.g_ptr[q]);
+      const double nr = (double)(t_off[q + 1] - t_off[q]) / std::max(1.0, sn);
+      g_timer.flops[7] += 2.0 * nr * sn * sn;
+      for (int k = 0; k < N.g_rank[q]; ++k) g_timer.flops[7] += 4.0 * (nr - k) * (sn - k);
+    }
   }
   N.n = L.col0[L.nagg];
   AMGDD_TRY(N.d_g_ptr.upload(N.g_ptr, s));
@@ -1694,12 +1799,10 @@ static double resid_bytes(const Level& L, size_t esz, size_t msz = 0) {
 // One gather-GEMV of a level's operator pair (M and its block transpose) in
 // the working precision: FP64, FP32, or the FP16 copies under MIXED16.
 static int seg_op(bool h16, bool f32, const SegPlan& p, const DBuf<double>& M64, const DBuf<float>& M32,
-                  const DBuf<__half>& M16, const DBuf<double>& T64, const DBuf<float>& T32, const DBuf<__half>& T16,
-                  const void* x, void* y, SegMode mode, const int* skip, cudaStream_t s, const void* csrc = nullptr,
-                  void* cdst = nullptr) {
-  if (h16 && p.lanes16 > 0)  // plans where setup timed the FP16 form faster
-    return launch_seg16(p, M16.p, T16.p, (const float*)x, (float*)y, mode, skip, s, (const float*)csrc,
-                        (float*)cdst);
+                  const DBuf<double>& T64, const DBuf<float>& T32, const void* x, void* y, SegMode mode,
+                  const int* skip, cudaStream_t s, const void* csrc = nullptr, void* cdst = nullptr) {
+  if (h16 && p.lanes16 != 0)  // plans where setup timed an FP16 form faster
+    return launch_seg16(p, (const float*)x, (float*)y, mode, skip, s, (const float*)csrc, (float*)cdst);
   return launch_seg(p, f32 ? (const void*)M32.p : (const void*)M64.p, f32, x, y, f32, mode, skip, s, csrc, cdst,
                     f32 ? (const void*)T32.p : (const void*)T64.p);
 }
@@ -1707,7 +1810,7 @@ static int seg_op(bool h16, bool f32, const SegPlan& p, const DBuf<double>& M64,
 static int level_apply_A(const Level& L, bool f32, const void* x, void* y, cudaStream_t s, bool h16 = false) {
   if (L.use_ell) return launch_ell(L, f32, x, y, nullptr, nullptr, s);
   if (L.has_blk)
-    return seg_op(h16, f32, L.ablk, L.A64, L.A32, L.A16, L.At64, L.At32, L.At16, x, y, SEG_STORE, nullptr, s);
+    return seg_op(h16, f32, L.ablk, L.A64, L.A32, L.At64, L.At32, x, y, SEG_STORE, nullptr, s);
   AMGDD_CUDA(cudaMemsetAsync(y, 0, L.n * (f32 ? sizeof(float) : sizeof(double)), s));
   return launch_apply(L.aplan, L, f32, x, y, +1, nullptr, s);
 }
@@ -1718,7 +1821,7 @@ static int level_residual(const Level& L, bool f32, const void* x, const void* r
                           cudaStream_t s, bool h16 = false) {
   if (L.use_ell) return launch_ell(L, f32, x, sv, r, skip, s);
   if (L.has_blk)
-    return seg_op(h16, f32, L.ablk, L.A64, L.A32, L.A16, L.At64, L.At32, L.At16, x, sv, SEG_RESID, skip, s, r);
+    return seg_op(h16, f32, L.ablk, L.A64, L.A32, L.At64, L.At32, x, sv, SEG_RESID, skip, s, r);
   return launch_apply(L.aplan, L, f32, x, sv, -1, skip, s);
 }
 static bool rcopy(const Level& L) { return !L.has_blk && !L.use_ell; }
@@ -1733,12 +1836,12 @@ static int apply_rast(const Level& L, bool f32, const void* sv, void* x, const i
   h16 = h16 && K == 1;
   if (L.yd64.p == nullptr) {
     if (K == 1)
-      return seg_op(h16, f32, L.rast, L.Wt64, L.Wt32, L.Wt16, L.W64, L.W32, L.W16, sv, x, SEG_ATOMIC_ADD, skip, s);
+      return seg_op(h16, f32, L.rast, L.Wt64, L.Wt32, L.W64, L.W32, sv, x, SEG_ATOMIC_ADD, skip, s);
     return launch_seg_multi(L.rast, Wt, W, f32, sv, x, SEG_ATOMIC_ADD, nullptr, K, skip, s);
   }
   void* Y = K == 1 ? (f32 ? (void*)L.yd32.p : (void*)L.yd64.p) : (f32 ? (void*)L.myd32.p : (void*)L.myd64.p);
   if (K == 1)
-    AMGDD_TRY(seg_op(h16, f32, L.rast_det, L.Wt64, L.Wt32, L.Wt16, L.W64, L.W32, L.W16, sv, Y, SEG_STORE, skip, s));
+    AMGDD_TRY(seg_op(h16, f32, L.rast_det, L.Wt64, L.Wt32, L.W64, L.W32, sv, Y, SEG_STORE, skip, s));
   else
     AMGDD_TRY(launch_seg_multi(L.rast_det, Wt, W, f32, sv, Y, SEG_STORE, nullptr, K, skip, s));
   return launch_gather_add(L.det_ptr.p, L.det_pos.p, Y, x, L.n, K, f32, skip, s);
@@ -1751,6 +1854,7 @@ struct VProf {
   std::vector<cudaEvent_t> ev;
   std::vector<int> tag;  // level * kSlots + slot, -1 for the final mark
   size_t used = 0;
+  bool in_graph = false;  // marks recorded under stream capture
   static constexpr int kSlots = 8;
   int mark(cudaStream_t s, int level, int slot) {
     if (used == ev.size()) {
@@ -1760,9 +1864,12 @@ struct VProf {
       tag.push_back(0);
     }
     tag[used] = level < 0 ? -1 : level * kSlots + slot;
-    // External: under stream capture the mark becomes an event record node
-    // of the graph (a plain record would only carry a capture dependency)
-    AMGDD_CUDA(cudaEventRecordWithFlags(ev[used], s, cudaEventRecordExternal));
+    // External (under stream capture only): the mark becomes an event record
+    // node of the graph (a plain record would only carry a capture dependency)
+    if (in_graph)
+      AMGDD_CUDA(cudaEventRecordWithFlags(ev[used], s, cudaEventRecordExternal));
+    else
+      AMGDD_CUDA(cudaEventRecord(ev[used], s));
     ++used;
     return AMGDD_OK;
   }
@@ -1823,17 +1930,17 @@ static int vcycle(amgdd_hierarchy& h, int l, bool f32, const void* r, void* x, c
   // pre-smoothing from x = 0: x = M_RAS^{-1} r  (Eq. ras); the same launch
   // copies s(omega_i) = r(omega_i) for the residual
   AMGDD_MARK(0);
-  AMGDD_TRY(seg_op(h16, f32, L.ras, L.W64, L.W32, L.W16, L.Wt64, L.Wt32, L.Wt16, r, x, SEG_STORE, skip, s,
+  AMGDD_TRY(seg_op(h16, f32, L.ras, L.W64, L.W32, L.Wt64, L.Wt32, r, x, SEG_STORE, skip, s,
                    rcopy(L) ? r : nullptr, rcopy(L) ? sv : nullptr));
   // s = r - A x ; r_c = P^T s
   AMGDD_MARK(2);
   AMGDD_TRY(level_residual(L, f32, x, r, sv, skip, s, h16));
   AMGDD_MARK(3);
-  AMGDD_TRY(seg_op(h16, f32, L.restr, L.Zt64, L.Zt32, L.Zt16, L.Z64, L.Z32, L.Z16, sv, rn, SEG_STORE, skip, s));
+  AMGDD_TRY(seg_op(h16, f32, L.restr, L.Zt64, L.Zt32, L.Z64, L.Z32, sv, rn, SEG_STORE, skip, s));
   // x_c = B_{l+1} r_c ; x += P x_c  (Eq. cgc)
   AMGDD_TRY(vcycle(h, l + 1, f32, rn, xn, skip, s, prof));
   AMGDD_MARK(4);
-  AMGDD_TRY(seg_op(h16, f32, L.prol, L.Z64, L.Z32, L.Z16, L.Zt64, L.Zt32, L.Zt16, xn, x, SEG_ADD, skip, s,
+  AMGDD_TRY(seg_op(h16, f32, L.prol, L.Z64, L.Z32, L.Zt64, L.Zt32, xn, x, SEG_ADD, skip, s,
                    rcopy(L) ? r : nullptr, rcopy(L) ? sv : nullptr));
   // post-smoothing: x += M_RAS-T^{-1} (r - A x)  (Eq. ras-t)
   AMGDD_MARK(2);
@@ -2022,24 +2129,93 @@ constexpr double kHbmBytesPerUs = 6.8e6;
 // there).  Entries below 2^-24 round to 0 or to subnormals: their absolute
 // error, at most 2^-25, is far below the rounding of the row's largest
 // entries.  Built once; the FP32 copies stay for MIXED32 and batched solves.
+// The padded FP16 copy of one plan's FP32 matrix and its chunk descriptors
+// (the plan's chunks as setup chose them, pointing into the padded copy).
+static int build_pad16(SegPlan& p, const float* M32, cudaStream_t s) {
+  p.m16.release();
+  p.chunk_desc16.release();
+  p.mat_len16 = 0;
+  if (p.nchunks == 0 || M32 == nullptr) return AMGDD_OK;
+  std::vector<int64_t> off16(p.nblocks + 1, 0);
+  for (int b = 0; b < p.nblocks; ++b)
+    off16[b + 1] = off16[b] + (int64_t)p.h_nr[b] * (((int64_t)p.h_nc[b] + 7) / 8 * 8);
+  p.mat_len16 = off16[p.nblocks];
+  DBuf<int64_t> d_off16;
+  AMGDD_TRY(d_off16.upload(off16, s));
+  AMGDD_TRY(p.m16.alloc(std::max<int64_t>(p.mat_len16, 1)));
+  AMGDD_TRY(launch_pad16(M32, p.m_off.p, p.nr.p, p.nc.p, d_off16.p, p.nblocks, p.m16.p, s));
+  std::vector<SegDesc> cd;
+  cd.reserve(p.nchunks);
+  const int rpc = p.rows_per_chunk;
+  for (int b = 0; b < p.nblocks; ++b)
+    for (int r = 0; r < p.h_nr[b]; r += rpc)
+      cd.push_back(SegDesc{off16[b], p.h_ioff[b], p.h_ooff[b], r, std::min(p.h_nr[b], r + rpc), p.h_nc[b],
+                           p.h_nr[b]});
+  if ((int)cd.size() != p.nchunks) {
+    set_error("build_pad16: chunk count mismatch");
+    return AMGDD_ERR_INTERNAL;
+  }
+  AMGDD_TRY(p.chunk_desc16.upload(cd, s));
+  return AMGDD_OK;
+}
+
+// The transposed FP16 copy of one plan (columns of rows padded to an even
+// count) and tasks of up to 2 kind rows for the FP16 row-per-lane kernel.
+static int build_pad16t(SegPlan& p, const float* T32, int kind, cudaStream_t s) {
+  if (T32 == nullptr || p.nblocks == 0) return AMGDD_OK;
+  std::vector<int64_t> off16(p.nblocks + 1, 0);
+  for (int b = 0; b < p.nblocks; ++b)
+    off16[b + 1] = off16[b] + (int64_t)p.h_nc[b] * (((int64_t)p.h_nr[b] + 1) / 2 * 2);
+  if (p.mt16.p == nullptr) {
+    DBuf<int64_t> d_off16;
+    AMGDD_TRY(d_off16.upload(off16, s));
+    AMGDD_TRY(p.mt16.alloc(std::max<int64_t>(off16[p.nblocks], 2)));
+    AMGDD_TRY(launch_pad16t(T32, p.m_off.p, p.nr.p, p.nc.p, d_off16.p, p.nblocks, p.mt16.p, s));
+  }
+  std::vector<SegDesc> td;
+  for (int b = 0; b < p.nblocks; ++b)
+    for (int r = 0; r < p.h_nr[b]; r += 2 * kind)
+      td.push_back(SegDesc{off16[b], p.h_ioff[b], p.h_ooff[b], r, std::min(p.h_nr[b], r + 2 * kind), p.h_nc[b],
+                           p.h_nr[b]});
+  p.ntasks16 = (int)td.size();
+  return p.task_desc16.upload(td, s);
+}
+
 // FP16 form of one plan under MIXED16: the FP32 launch as setup chose it,
-// against the FP16 shifted kernel with 4, 8, 16 or 32 lanes per row over
-// the same chunks, on scratch vectors; the fastest is kept (lanes16 = 0:
-// the plan reads its FP32 copy).  The choice is cached like the others.
-static int tune16(SegPlan& p, const std::string& key, const float* M32, const float* T32, const __half* M16,
-                  const __half* T16, int64_t nin, int64_t nout, SegMode mode, cudaStream_t s) {
+// against the FP16 kernels over the same blocks: lanes per row (rows padded
+// to 16-byte vectors; 4, 8, 16 or 32 lanes, the plan's chunks) and, for rows
+// of at most 256 entries, row per lane (two rows per half2 of the transposed
+// copy; 8, 16 or 32 lanes per task), on scratch vectors; the fastest is kept
+// (lanes16 = 0: the plan reads its FP32 copy and the FP16 copies are
+// dropped).  The choice is cached like the others.
+static int tune16(SegPlan& p, const std::string& key, const float* M32, const float* T32, int64_t nin, int64_t nout,
+                  SegMode mode, cudaStream_t s) {
   p.lanes16 = 0;
-  if (p.nchunks == 0 || M16 == nullptr) return AMGDD_OK;
+  if (p.nblocks == 0 || M32 == nullptr) return AMGDD_OK;
+  const bool can_lanes = p.nchunks > 0;
+  const bool can_rows = T32 != nullptr && p.max_nc <= 256;
+  auto valid = [&](int l) {
+    return l == 0 || (l > 0 && can_lanes && (l == 4 || l == 8 || l == 16 || l == 32)) ||
+           (l < 0 && can_rows && (l == -8 || l == -16 || l == -32));
+  };
+  auto realize = [&](int l) -> int {  // build the copies form l reads, drop the others
+    if (l <= 0) {
+      p.m16.release();
+      p.chunk_desc16.release();
+    }
+    if (l >= 0) {
+      p.mt16.release();
+      p.task_desc16.release();
+      p.ntasks16 = 0;
+    }
+    if (l > 0 && p.m16.p == nullptr) AMGDD_TRY(build_pad16(p, M32, s));
+    if (l < 0) AMGDD_TRY(build_pad16t(p, T32, -l, s));
+    p.lanes16 = l;
+    return AMGDD_OK;
+  };
   double cached = 0.0;
-  if (g_tune && g_tune->get(key, cached)) {
-    const int l = (int)cached;
-    p.lanes16 = (l == 4 || l == 8 || l == 16 || l == 32) ? l : 0;
-    return AMGDD_OK;
-  }
-  if (g_tune && !g_tune->on) {  // no timing: the FP16 kernel with the plan's lanes
-    p.lanes16 = p.lanes;
-    return AMGDD_OK;
-  }
+  if (g_tune && g_tune->get(key, cached)) return realize(valid((int)cached) ? (int)cached : 0);
+  if (g_tune && !g_tune->on) return realize(can_lanes ? p.lanes : 0);  // no timing
   DBuf<float> xin, yout, cin;
   AMGDD_TRY(xin.alloc(std::max<int64_t>(nin, 1)));
   AMGDD_TRY(yout.alloc(std::max<int64_t>(nout, 1)));
@@ -2047,54 +2223,56 @@ static int tune16(SegPlan& p, const std::string& key, const float* M32, const fl
   AMGDD_TRY(xin.zero(s));
   AMGDD_TRY(yout.zero(s));
   AMGDD_TRY(cin.zero(s));
-  cudaEvent_t e[2];
-  for (auto& v : e) AMGDD_CUDA(cudaEventCreate(&v));
   constexpr int kReps = 8;
   int rc = AMGDD_OK;
   float best_t = 0.f;
   int best = 0;
-  for (int l : {0, 4, 8, 16, 32}) {
+  for (int l : {0, 4, 8, 16, 32, -8, -16, -32}) {
+    if (!valid(l)) continue;
+    if (l > 0 && p.m16.p == nullptr) rc = build_pad16(p, M32, s);
+    if (l < 0 && rc == AMGDD_OK) rc = build_pad16t(p, T32, -l, s);
     p.lanes16 = l;
-    for (int rep = 0; rep < kReps + 2 && rc == AMGDD_OK; ++rep) {
-      if (rep == 2) cudaEventRecord(e[0], s);
-      rc = l == 0 ? launch_seg(p, M32, true, xin.p, yout.p, true, mode, nullptr, s,
-                               mode == SEG_RESID ? cin.p : nullptr, nullptr, T32)
-                  : launch_seg16(p, M16, T16, xin.p, yout.p, mode, nullptr, s, mode == SEG_RESID ? cin.p : nullptr,
-                                 nullptr);
-    }
-    cudaEventRecord(e[1], s);
     float ms = 0.f;
-    if (rc == AMGDD_OK &&
-        (cudaEventSynchronize(e[1]) != cudaSuccess || cudaEventElapsedTime(&ms, e[0], e[1]) != cudaSuccess))
-      rc = AMGDD_ERR_CUDA;
+    if (rc == AMGDD_OK)
+      rc = time_cold(s, kReps, [&] {
+        return l == 0 ? launch_seg(p, M32, true, xin.p, yout.p, true, mode, nullptr, s,
+                                   mode == SEG_RESID ? cin.p : nullptr, nullptr, T32)
+                      : launch_seg16(p, xin.p, yout.p, mode, nullptr, s, mode == SEG_RESID ? cin.p : nullptr,
+                                     nullptr);
+      }, &ms);
     if (rc != AMGDD_OK) break;
     if (l == 0 || ms < best_t) {
       best_t = ms;
       best = l;
     }
   }
-  for (auto& v : e) cudaEventDestroy(v);
   AMGDD_TRY(rc);
-  p.lanes16 = best;
+  AMGDD_TRY(realize(best));
   if (g_tune) g_tune->put(key, (double)best);
   return AMGDD_OK;
 }
 
+// MIXED16 storage: per gather-GEMV plan of every level, an FP16 copy (round
+// to nearest) of its FP32 matrix (smoother rows W_i or W_i^T, basis Z_i or
+// Z_i^T, coarse block rows), kept where setup times it faster than the FP32
+// copy.  FP16 holds magnitudes up to 65504 with 11 significant bits; a level
+// whose FP32 copies hold a larger or non-finite entry keeps FP32 throughout.
+// Entries below 2^-24 round to 0 or to subnormals: their absolute error, at
+// most 2^-25, is far below the rounding of the row's largest entries.  Built
+// once; the FP32 copies stay for MIXED32, batched solves and the persistent
+// tail.
 static int build_half(amgdd_hierarchy& h) {
   cudaStream_t s = h.work;
+  FlushScope flush_scope;
   for (size_t lvl = 0; lvl < h.lv.size(); ++lvl) {
     Level& L = *h.lv[lvl];
     if (L.coarsest || L.h16) continue;
-    struct Pair {
-      const DBuf<float>* src;
-      DBuf<__half>* dst;
-    } pairs[6] = {{&L.W32, &L.W16}, {&L.Wt32, &L.Wt16}, {&L.Z32, &L.Z16},
-                  {&L.Zt32, &L.Zt16}, {&L.A32, &L.A16}, {&L.At32, &L.At16}};
+    const DBuf<float>* srcs[6] = {&L.W32, &L.Wt32, &L.Z32, &L.Zt32, &L.A32, &L.At32};
     bool ok = true;
     std::vector<float> hv;
-    for (auto& pr : pairs) {
-      if (pr.src->p == nullptr || pr.src->n == 0) continue;
-      AMGDD_TRY(download(hv, pr.src->p, pr.src->n, s));
+    for (const DBuf<float>* src : srcs) {
+      if (src->p == nullptr || src->n == 0) continue;
+      AMGDD_TRY(download(hv, src->p, src->n, s));
       for (float v : hv)
         if (!(std::fabs(v) <= 65000.0f)) {
           ok = false;
@@ -2103,23 +2281,16 @@ static int build_half(amgdd_hierarchy& h) {
       if (!ok) break;
     }
     if (!ok) continue;  // this level keeps FP32
-    for (auto& pr : pairs) {
-      if (pr.src->p == nullptr || pr.src->n == 0) continue;
-      AMGDD_TRY(pr.dst->alloc(pr.src->n));
-      AMGDD_TRY(launch_to_half(pr.src->p, pr.dst->p, (int64_t)pr.src->n, s));
-    }
     L.h16 = true;
     const std::string k = "L" + std::to_string(lvl) + "|h16|";
     const int64_t nn = L.col0.back();
-    AMGDD_TRY(tune16(L.ras, k + "ras", L.W32.p, L.Wt32.p, L.W16.p, L.Wt16.p, L.n, L.n, SEG_STORE, s));
-    AMGDD_TRY(tune16(L.rast, k + "rast", L.Wt32.p, L.W32.p, L.Wt16.p, L.W16.p, L.n, L.n, SEG_ATOMIC_ADD, s));
+    AMGDD_TRY(tune16(L.ras, k + "ras", L.W32.p, L.Wt32.p, L.n, L.n, SEG_STORE, s));
+    AMGDD_TRY(tune16(L.rast, k + "rast", L.Wt32.p, L.W32.p, L.n, L.n, SEG_ATOMIC_ADD, s));
     if (L.yd32.p)
-      AMGDD_TRY(tune16(L.rast_det, k + "rastd", L.Wt32.p, L.W32.p, L.Wt16.p, L.W16.p, L.n, L.om_ptr.back(),
-                       SEG_STORE, s));
-    AMGDD_TRY(tune16(L.restr, k + "restrict", L.Zt32.p, L.Z32.p, L.Zt16.p, L.Z16.p, L.n, nn, SEG_STORE, s));
-    AMGDD_TRY(tune16(L.prol, k + "prolong", L.Z32.p, L.Zt32.p, L.Z16.p, L.Zt16.p, nn, L.n, SEG_ADD, s));
-    if (L.has_blk)
-      AMGDD_TRY(tune16(L.ablk, k + "ablk", L.A32.p, L.At32.p, L.A16.p, L.At16.p, L.n, L.n, SEG_RESID, s));
+      AMGDD_TRY(tune16(L.rast_det, k + "rastd", L.Wt32.p, L.W32.p, L.n, L.om_ptr.back(), SEG_STORE, s));
+    AMGDD_TRY(tune16(L.restr, k + "restrict", L.Zt32.p, L.Z32.p, L.n, nn, SEG_STORE, s));
+    AMGDD_TRY(tune16(L.prol, k + "prolong", L.Z32.p, L.Zt32.p, nn, L.n, SEG_ADD, s));
+    if (L.has_blk) AMGDD_TRY(tune16(L.ablk, k + "ablk", L.A32.p, L.At32.p, L.n, L.n, SEG_RESID, s));
   }
   AMGDD_CUDA(cudaStreamSynchronize(s));
   return AMGDD_OK;
@@ -3078,6 +3249,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     explicit TuneScope(TuneCtx* t) { g_tune = t; }
     ~TuneScope() { g_tune = nullptr; }
   } tune_scope(&tctx);
+  FlushScope flush_scope;  // cold-L2 timing of the kernel forms
   // ---- level 0 row groups: consecutive rows with identical supports ----
   std::unique_ptr<Level> L0(new Level());
   L0->n = n;
@@ -3187,6 +3359,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     }
     for (int i = 0; i < 16; ++i) {
       H->phase_ms[i] += g_timer.acc[i];
+      H->phase_flops[i] += g_timer.flops[i];
       if (g_timer.name[i]) H->phase_name[i] = g_timer.name[i];
     }
     if (g_timer.on) {
@@ -3196,6 +3369,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
       fprintf(stderr, "\n");
     }
     for (double& a : g_timer.acc) a = 0.0;
+    for (double& a : g_timer.flops) a = 0.0;
     L.d_H.release();
 
     H->lv.push_back(std::move(N));
@@ -3209,6 +3383,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   }
   for (int i = 0; i < 16; ++i) {  // the coarsest level's phases
     H->phase_ms[i] += g_timer.acc[i];
+    H->phase_flops[i] += g_timer.flops[i];
     if (g_timer.name[i]) H->phase_name[i] = g_timer.name[i];
   }
   // ---- solver workspace --------------------------------------------------
@@ -3231,6 +3406,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   tctx.save();
   for (const auto& kv : tctx.kv)
     if (kv.first.compare(0, tctx.sig.size(), tctx.sig) == 0) H->tune_kv.emplace_back(kv.first, kv.second);
+  flush_scope.f.buf.release();
   H->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   H->setup_bytes = g_alloc_bytes - bytes0;
   *out = H.release();
@@ -3417,7 +3593,7 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
       AMGDD_TRY(level_apply_A(L, f32, xin, yout, s, h16));
       break;
     case AMGDD_OP_RAS:
-      AMGDD_TRY(seg_op(h16, f32, L.ras, L.W64, L.W32, L.W16, L.Wt64, L.Wt32, L.Wt16, xin, yout, SEG_STORE, nullptr, s));
+      AMGDD_TRY(seg_op(h16, f32, L.ras, L.W64, L.W32, L.Wt64, L.Wt32, xin, yout, SEG_STORE, nullptr, s));
       break;
     case AMGDD_OP_RAST:
       AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
@@ -3425,11 +3601,11 @@ int amgdd_apply(amgdd_hierarchy* h, int op, int level, const double* x, double* 
       break;
     case AMGDD_OP_RESTRICT:
       AMGDD_TRY(
-          seg_op(h16, f32, L.restr, L.Zt64, L.Zt32, L.Zt16, L.Z64, L.Z32, L.Z16, xin, yout, SEG_STORE, nullptr, s));
+          seg_op(h16, f32, L.restr, L.Zt64, L.Zt32, L.Z64, L.Z32, xin, yout, SEG_STORE, nullptr, s));
       break;
     case AMGDD_OP_PROLONG:
       AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
-      AMGDD_TRY(seg_op(h16, f32, L.prol, L.Z64, L.Z32, L.Z16, L.Zt64, L.Zt32, L.Zt16, xin, yout, SEG_ADD, nullptr, s));
+      AMGDD_TRY(seg_op(h16, f32, L.prol, L.Z64, L.Z32, L.Zt64, L.Zt32, xin, yout, SEG_ADD, nullptr, s));
       break;
     case AMGDD_OP_VCYCLE:
       AMGDD_TRY(vcycle(*h, level, f32, xin, yout, nullptr, s));
@@ -3559,7 +3735,7 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
       AMGDD_TRY(level_apply_A(L, f32, xin, yout, s, h16));
       break;
     case AMGDD_OP_RAS:
-      AMGDD_TRY(seg_op(h16, f32, L.ras, L.W64, L.W32, L.W16, L.Wt64, L.Wt32, L.Wt16, xin, yout, SEG_STORE, nullptr, s));
+      AMGDD_TRY(seg_op(h16, f32, L.ras, L.W64, L.W32, L.Wt64, L.Wt32, xin, yout, SEG_STORE, nullptr, s));
       break;
     case AMGDD_OP_RAST:
       AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
@@ -3567,11 +3743,11 @@ int amgdd_apply_noalloc(amgdd_hierarchy* h, int op, int level, const double* x, 
       break;
     case AMGDD_OP_RESTRICT:
       AMGDD_TRY(
-          seg_op(h16, f32, L.restr, L.Zt64, L.Zt32, L.Zt16, L.Z64, L.Z32, L.Z16, xin, yout, SEG_STORE, nullptr, s));
+          seg_op(h16, f32, L.restr, L.Zt64, L.Zt32, L.Z64, L.Z32, xin, yout, SEG_STORE, nullptr, s));
       break;
     case AMGDD_OP_PROLONG:
       AMGDD_CUDA(cudaMemsetAsync(yout, 0, nout * esz, s));
-      AMGDD_TRY(seg_op(h16, f32, L.prol, L.Z64, L.Z32, L.Z16, L.Zt64, L.Zt32, L.Zt16, xin, yout, SEG_ADD, nullptr, s));
+      AMGDD_TRY(seg_op(h16, f32, L.prol, L.Z64, L.Z32, L.Zt64, L.Zt32, xin, yout, SEG_ADD, nullptr, s));
       break;
     case AMGDD_OP_VCYCLE:
       AMGDD_TRY(vcycle(*h, level, f32, xin, yout, nullptr, s));
@@ -3625,6 +3801,7 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, int graph, double* ms, do
     // kernels), replayed: the per-step times then hold the in-graph gaps
     // between dependent kernels and no host launch overhead
     prof.used = 0;
+    prof.in_graph = true;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
     capture_begin();
@@ -3672,7 +3849,7 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, int graph, double* ms, do
       const int pf1 = h->persist_from[f32 ? 1 : 0];
       // FP16 entries where MIXED16 reads them (per plan; the persistent tail reads FP32)
       const bool h16 = use16(*h, L, f32) && !(pf1 > 0 && l >= pf1);
-      auto msz = [&](const SegPlan& p) -> size_t { return h16 && p.lanes16 > 0 ? 2 : esz; };
+      auto msz = [&](const SegPlan& p) -> size_t { return h16 && p.lanes16 != 0 ? 2 : esz; };
       const double cp = rcopy(L) ? (double)L.n * esz : 0.0;  // fused copy r -> s
       b[0] = seg_bytes(L.ras, L.n, L.n, false, esz, msz(L.ras)) + cp;
       b[2] = 2.0 * (resid_bytes(L, esz, msz(L.ablk)) - cp);  // two residuals
@@ -3695,6 +3872,14 @@ int amgdd_profile_vcycle(amgdd_hierarchy* h, int reps, int graph, double* ms, do
 }
 
 int64_t amgdd_kernel_launches(void) { return g_kernels.load(); }
+
+int amgdd_measure_fp64(void* stream, double* gflops) {
+  if (gflops == nullptr) {
+    set_error("amgdd_measure_fp64: null output");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  return measure_fp64_rate((cudaStream_t)stream, gflops);
+}
 
 int64_t amgdd_device_bytes(const amgdd_hierarchy* h, int with_batched) {
   if (h == nullptr) return -1;
@@ -3840,7 +4025,7 @@ static void level_bytes(const amgdd_hierarchy& h, const Level& L, size_t esz, do
   const int64_t nn = L.col0.back();
   // FP16 entries where MIXED16 reads them (per plan; the persistent tail reads FP32)
   const bool h16 = use16(h, L, esz == 4) && !tail;
-  auto msz = [&](const SegPlan& p) -> size_t { return h16 && p.lanes16 > 0 ? 2 : esz; };
+  auto msz = [&](const SegPlan& p) -> size_t { return h16 && p.lanes16 != 0 ? 2 : esz; };
   cyc += seg_bytes(L.ras, L.n, L.n, false, esz, msz(L.ras)) +
          rast_bytes(L, esz, msz(L.yd64.p ? L.rast_det : L.rast)) +
          seg_bytes(L.restr, L.n, nn, false, esz, msz(L.restr)) + seg_bytes(L.prol, nn, L.n, true, esz, msz(L.prol)) +
@@ -3958,6 +4143,15 @@ int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap) {
     if (h->phase_name[i]) {
       char buf[96];
       std::snprintf(buf, sizeof buf, "%s\"%s\": %.3f", first ? "" : ", ", h->phase_name[i], h->phase_ms[i]);
+      s += buf;
+      first = false;
+    }
+  s += "}, \"setup_phases_gflop\": {";  // FP64 flops counted from the actual block sizes (a model per phase)
+  first = true;
+  for (int i = 0; i < 16; ++i)
+    if (h->phase_name[i] && h->phase_flops[i] > 0) {
+      char buf[96];
+      std::snprintf(buf, sizeof buf, "%s\"%s\": %.4f", first ? "" : ", ", h->phase_name[i], h->phase_flops[i] * 1e-9);
       s += buf;
       first = false;
     }

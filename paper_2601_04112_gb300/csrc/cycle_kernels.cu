@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <map>
 #include <mutex>
 #include <cstdint>
@@ -113,6 +114,9 @@ __device__ __forceinline__ float mval<float, __half>(__half v) {
 // neighbouring rows that the aligned vectors take in (stored, finite values)
 // are multiplied by zero.  A vector that would cross the end of the stored
 // matrix (m_len entries) is read element by element up to that end.
+// VK 3: every row padded with zeros to a whole number of vectors (row
+// stride nc rounded up to W; the MIXED16 copies), read like VK 1 against
+// one staged copy of x that is zero past nc.
 // U = 4 (plans with long rows only): the gather and the row loop keep four
 // independent loads per thread in flight.
 template <class T, int VK, int W>
@@ -181,6 +185,9 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const SegDesc* __restrict__
       const int k = t / E, e = t - k * E;
       xs[k * S + (e < k ? e : ncb + e)] = T(0);
     }
+  }
+  if constexpr (VK == 3) {  // padded rows: the staged x is zero up to the padded length
+    for (int c = ncb + (int)threadIdx.x; c < ((ncb + W - 1) / W) * W; c += blockDim.x) xs[c] = T(0);
   }
   if constexpr (U == 1) {
     for (int c = threadIdx.x; c < ncb; c += blockDim.x) seg_stage<T, VK, W>(xs, S, c, x[ii[c]]);
@@ -284,8 +291,10 @@ __global__ void __launch_bounds__(kSegThreads) k_seg(const SegDesc* __restrict__
     for (int r = r0 + grp; r < r1; r += ngrp) {
       T acc = T(0);
       if constexpr (VK != 0) {
-        const V* rv = reinterpret_cast<const V*>(M + mob + (int64_t)r * ncb);  // VK 1: aligned rows
-        const int nv = ncb / W;
+        // VK 1: aligned rows of whole vectors; VK 3: rows padded to whole vectors (stride rounded up)
+        const int stride = VK == 3 ? ((ncb + W - 1) / W) * W : ncb;
+        const V* rv = reinterpret_cast<const V*>(M + mob + (int64_t)r * stride);
+        const int nv = stride / W;
         int c = lane;
         if constexpr (U > 1) {
           T a[U];
@@ -398,6 +407,78 @@ __global__ void __launch_bounds__(128) k_seg_rows(const SegDesc* __restrict__ de
   else
     *dst = cv - acc;
   if (MODE != SEG_RESID && cdst != nullptr) cdst[o] = cv;
+}
+
+// FP16 row per lane (MIXED16): lane l of a task owns output rows r0 + 2l and
+// r0 + 2l + 1 and reads both at once as one half2 of the transposed FP16
+// copy (columns of rows padded to an even count, so every half2 is aligned
+// and the padding row is zero), widened to FP32 and summed in FP32.
+template <int L, int MODE>
+__global__ void __launch_bounds__(128) k_seg_rows16(const SegDesc* __restrict__ desc, int ntasks, int max_nc,
+                                                    const int32_t* __restrict__ in_idx,
+                                                    const int32_t* __restrict__ out_idx, const __half* __restrict__ MT,
+                                                    const float* __restrict__ x, float* __restrict__ y,
+                                                    const int* skip, const float* __restrict__ csrc,
+                                                    float* __restrict__ cdst) {
+  pdl_prologue();
+  if (skip != nullptr && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int grp = (int)threadIdx.x / L;
+  const int t = blockIdx.x * (128 / L) + grp;
+  if (t >= ntasks) return;
+  const int lane = threadIdx.x % L;
+  const unsigned mask = group_mask<L>();
+  float* xs = reinterpret_cast<float*>(smem_raw) + (size_t)grp * max_nc;
+  const SegDesc dsc = desc[t];
+  const int rows = dsc.r1 - dsc.r0;
+  const int ncb = dsc.nc;
+  const int nrp = (dsc.nr + 1) & ~1;
+  const int32_t* ii = in_idx + dsc.in_off;
+  const int ra = dsc.r0 + 2 * lane;
+  const bool act0 = 2 * lane < rows, act1 = 2 * lane + 1 < rows;
+  const __half2* col = reinterpret_cast<const __half2*>(MT + dsc.m_off + ra);
+  const int64_t step = nrp / 2;
+  constexpr int kPre = 16;
+  float2 pre[kPre];
+#pragma unroll
+  for (int c = 0; c < kPre; ++c)
+    pre[c] = (act0 && c < ncb) ? __half22float2(col[(int64_t)c * step]) : make_float2(0.f, 0.f);
+  const bool need_c = MODE == SEG_RESID || cdst != nullptr;
+  const int o0 = act0 ? out_idx[dsc.out_off + ra] : 0;
+  const int o1 = act1 ? out_idx[dsc.out_off + ra + 1] : 0;
+  const float cv0 = (act0 && need_c) ? csrc[o0] : 0.f;
+  const float cv1 = (act1 && need_c) ? csrc[o1] : 0.f;
+  for (int c = lane; c < ncb; c += L) xs[c] = x[ii[c]];
+  __syncwarp(mask);
+  if (!act0) return;
+  float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+  for (int c = 0; c < kPre; ++c)
+    if (c < ncb) {
+      a0 += pre[c].x * xs[c];
+      a1 += pre[c].y * xs[c];
+    }
+  for (int c = kPre; c < ncb; ++c) {
+    const float2 f = __half22float2(col[(int64_t)c * step]);
+    a0 += f.x * xs[c];
+    a1 += f.y * xs[c];
+  }
+  auto out = [&](int o, float acc, float cv) {
+    float* dst = y + o;
+    if (MODE == SEG_STORE)
+      *dst = acc;
+    else if (MODE == SEG_ADD)
+      *dst += acc;
+    else if (MODE == SEG_ATOMIC_ADD)
+      atomic_add(dst, acc);
+    else if (MODE == SEG_ATOMIC_SUB)
+      atomic_add(dst, -acc);
+    else
+      *dst = cv - acc;
+    if (MODE != SEG_RESID && cdst != nullptr) cdst[o] = cv;
+  };
+  out(o0, a0, cv0);
+  if (act1) out(o1, a1, cv1);
 }
 
 // ---------------------------------------------------------------------------
@@ -675,14 +756,28 @@ int seg_dispatch(const SegPlan& p, const T* M, const T* MT, const T* x, T* y, Se
   }
 }
 
-// FP16 matrices (MIXED16 storage) against FP32 vectors: the row-per-lane
-// plans read the transposed copy; every other plan takes the shifted
-// 16-byte loads (8 entries each) at any row alignment.
+// FP16 matrices (MIXED16 storage) against FP32 vectors: rows padded to
+// whole 16-byte vectors (VK 3), one staged copy of x.
 template <int L>
-int seg16_lanes(const SegPlan& p, const __half* M, const float* x, float* y, SegMode mode, const int* skip,
-                cudaStream_t s, const float* csrc, float* cdst) {
-  return seg_launch_kind<float, __half, L, 2, 4>(p, M, x, y, mode, skip, s, csrc, cdst,
-                                                 seg_shift_smem<float, __half>(p));
+int seg16_lanes(const SegPlan& p, const float* x, float* y, SegMode mode, const int* skip, cudaStream_t s,
+                const float* csrc, float* cdst) {
+  constexpr int W = MV<float, __half>::W;
+  const size_t smem = (size_t)((p.max_nc + W - 1) / W) * W * sizeof(float);
+  auto launch = [&](auto kern) -> int {
+    if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AMGDD_CUDA(launch_k(g_pdl, kern, p.nchunks, kSegThreads, smem, s, (const SegDesc*)p.chunk_desc16.p,
+                        p.in_idx_ext, p.out_idx_ext, (const __half*)p.m16.p, x, y, skip, csrc, cdst, p.mat_len16));
+    AMGDD_CUDA(cudaGetLastError());
+    count_kernels(1);
+    return AMGDD_OK;
+  };
+  switch (mode) {
+    case SEG_STORE: return launch(k_seg<float, __half, L, SEG_STORE, 3, 4>);
+    case SEG_ADD: return launch(k_seg<float, __half, L, SEG_ADD, 3, 4>);
+    case SEG_ATOMIC_ADD: return launch(k_seg<float, __half, L, SEG_ATOMIC_ADD, 3, 4>);
+    case SEG_ATOMIC_SUB: return launch(k_seg<float, __half, L, SEG_ATOMIC_SUB, 3, 4>);
+    default: return launch(k_seg<float, __half, L, SEG_RESID, 3, 4>);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1288,35 +1383,100 @@ int launch_seg(const SegPlan& p, const void* M, bool m_fp32, const void* x, void
                               (const double*)csrc, (double*)cdst);
 }
 
-int launch_seg16(const SegPlan& p, const __half* M, const __half* MT, const float* x, float* y, SegMode mode,
-                 const int* skip, cudaStream_t s, const float* csrc, float* cdst) {
-  if (p.rows_mode ? p.ntasks == 0 : p.nchunks == 0) return AMGDD_OK;
+int launch_seg16(const SegPlan& p, const float* x, float* y, SegMode mode, const int* skip, cudaStream_t s,
+                 const float* csrc, float* cdst) {
   if (mode == SEG_RESID && csrc == nullptr) {
     set_error("launch_seg16: the residual mode needs the right-hand side");
     return AMGDD_ERR_INTERNAL;
   }
-  const int lanes = p.lanes16 > 0 && p.nchunks > 0 ? p.lanes16 : (p.rows_mode ? 0 : p.lanes);
-  if (lanes == 0) {
-    if (MT == nullptr) {
-      set_error("launch_seg16: row-per-lane plan needs the transposed operator");
-      return AMGDD_ERR_INTERNAL;
-    }
-    switch (p.kind) {
-      case 8: return seg_rows_mode<float, __half, 8>(p, MT, x, y, mode, skip, s, csrc, cdst);
-      case 16: return seg_rows_mode<float, __half, 16>(p, MT, x, y, mode, skip, s, csrc, cdst);
-      default: return seg_rows_mode<float, __half, 32>(p, MT, x, y, mode, skip, s, csrc, cdst);
-    }
-  }
-  if (M == nullptr || ((uintptr_t)M & 15) != 0) {
-    set_error("launch_seg16: the matrix must be 16-byte aligned");
+  if (p.lanes16 > 0 && p.nchunks == 0) return AMGDD_OK;
+  if (p.lanes16 > 0 && (p.m16.p == nullptr || p.chunk_desc16.p == nullptr)) {
+    set_error("launch_seg16: the plan has no FP16 copy");
     return AMGDD_ERR_INTERNAL;
   }
-  switch (lanes) {
-    case 4: return seg16_lanes<4>(p, M, x, y, mode, skip, s, csrc, cdst);
-    case 8: return seg16_lanes<8>(p, M, x, y, mode, skip, s, csrc, cdst);
-    case 16: return seg16_lanes<16>(p, M, x, y, mode, skip, s, csrc, cdst);
-    default: return seg16_lanes<32>(p, M, x, y, mode, skip, s, csrc, cdst);
+  if (p.lanes16 < 0) {  // row per lane, -lanes16 lanes per task of up to 2 (-lanes16) rows
+    if (p.mt16.p == nullptr || p.task_desc16.p == nullptr || p.ntasks16 == 0) {
+      set_error("launch_seg16: the plan has no FP16 row-per-lane form");
+      return AMGDD_ERR_INTERNAL;
+    }
+    auto go = [&](auto kern, int L) -> int {
+      const int per = 128 / L;
+      const size_t smem = (size_t)per * p.max_nc * sizeof(float);
+      if (smem > 48 * 1024)
+        AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      AMGDD_CUDA(launch_k(g_pdl, kern, (p.ntasks16 + per - 1) / per, 128, smem, s,
+                          (const SegDesc*)p.task_desc16.p, p.ntasks16, p.max_nc, p.in_idx_ext, p.out_idx_ext,
+                          (const __half*)p.mt16.p, x, y, skip, csrc, cdst));
+      AMGDD_CUDA(cudaGetLastError());
+      count_kernels(1);
+      return AMGDD_OK;
+    };
+    auto modes = [&](auto tag) -> int {
+      constexpr int L = decltype(tag)::value;
+      switch (mode) {
+        case SEG_STORE: return go(k_seg_rows16<L, SEG_STORE>, L);
+        case SEG_ADD: return go(k_seg_rows16<L, SEG_ADD>, L);
+        case SEG_ATOMIC_ADD: return go(k_seg_rows16<L, SEG_ATOMIC_ADD>, L);
+        case SEG_ATOMIC_SUB: return go(k_seg_rows16<L, SEG_ATOMIC_SUB>, L);
+        default: return go(k_seg_rows16<L, SEG_RESID>, L);
+      }
+    };
+    switch (-p.lanes16) {
+      case 8: return modes(std::integral_constant<int, 8>{});
+      case 16: return modes(std::integral_constant<int, 16>{});
+      default: return modes(std::integral_constant<int, 32>{});
+    }
   }
+  switch (p.lanes16) {
+    case 4: return seg16_lanes<4>(p, x, y, mode, skip, s, csrc, cdst);
+    case 8: return seg16_lanes<8>(p, x, y, mode, skip, s, csrc, cdst);
+    case 16: return seg16_lanes<16>(p, x, y, mode, skip, s, csrc, cdst);
+    default: return seg16_lanes<32>(p, x, y, mode, skip, s, csrc, cdst);
+  }
+}
+
+__global__ void k_pad16(const float* __restrict__ M32, const int64_t* __restrict__ m_off,
+                        const int32_t* __restrict__ nr, const int32_t* __restrict__ nc,
+                        const int64_t* __restrict__ m_off16, __half* __restrict__ dst) {
+  const int b = blockIdx.x;
+  const int r_n = nr[b], c_n = nc[b], cp = (c_n + 7) / 8 * 8;
+  const float* src = M32 + m_off[b];
+  __half* d = dst + m_off16[b];
+  for (int64_t e = threadIdx.x; e < (int64_t)r_n * cp; e += blockDim.x) {
+    const int r = (int)(e / cp), c = (int)(e % cp);
+    d[e] = c < c_n ? __float2half_rn(src[(int64_t)r * c_n + c]) : __float2half_rn(0.0f);
+  }
+}
+
+__global__ void k_pad16t(const float* __restrict__ MT32, const int64_t* __restrict__ m_off,
+                         const int32_t* __restrict__ nr, const int32_t* __restrict__ nc,
+                         const int64_t* __restrict__ m_off16, __half* __restrict__ dst) {
+  const int b = blockIdx.x;
+  const int r_n = nr[b], c_n = nc[b], rp = (r_n + 1) & ~1;
+  const float* src = MT32 + m_off[b];
+  __half* d = dst + m_off16[b];
+  for (int64_t e = threadIdx.x; e < (int64_t)c_n * rp; e += blockDim.x) {
+    const int c = (int)(e / rp), r = (int)(e % rp);
+    d[e] = r < r_n ? __float2half_rn(src[(int64_t)c * r_n + r]) : __float2half_rn(0.0f);
+  }
+}
+
+int launch_pad16t(const float* MT32, const int64_t* m_off, const int32_t* nr, const int32_t* nc,
+                  const int64_t* m_off16, int nblocks, __half* dst, cudaStream_t s) {
+  if (nblocks == 0) return AMGDD_OK;
+  k_pad16t<<<nblocks, 128, 0, s>>>(MT32, m_off, nr, nc, m_off16, dst);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
+int launch_pad16(const float* M32, const int64_t* m_off, const int32_t* nr, const int32_t* nc,
+                 const int64_t* m_off16, int nblocks, __half* dst, cudaStream_t s) {
+  if (nblocks == 0) return AMGDD_OK;
+  k_pad16<<<nblocks, 128, 0, s>>>(M32, m_off, nr, nc, m_off16, dst);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
 }
 
 int launch_apply(const ApplyPlan& p, const Level& L, bool fp32, const void* x, void* y, int sign, const int* skip,
@@ -1449,15 +1609,21 @@ int launch_dense(const void* B, int64_t ld, int n, bool fp32, const void* x, voi
   }
 }
 
-__global__ void k_to_half(const float* __restrict__ src, __half* __restrict__ dst, int64_t n) {
+template <class T>
+__global__ void k_count_nonfinite(const T* __restrict__ v, int64_t n, int* __restrict__ count) {
+  int c = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = __float2half_rn(src[i]);
+    if (!isfinite(v[i])) ++c;
+  if (c) atomicAdd(count, c);
 }
 
-int launch_to_half(const float* src, __half* dst, int64_t n, cudaStream_t s) {
-  if (n <= 0) return AMGDD_OK;
-  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-  k_to_half<<<grid, 256, 0, s>>>(src, dst, n);
+int count_nonfinite(const void* v, int64_t n, bool fp32, int* d_count, cudaStream_t s) {
+  if (n <= 0 || v == nullptr) return AMGDD_OK;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  if (fp32)
+    k_count_nonfinite<float><<<grid, 256, 0, s>>>((const float*)v, n, d_count);
+  else
+    k_count_nonfinite<double><<<grid, 256, 0, s>>>((const double*)v, n, d_count);
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
   return AMGDD_OK;

@@ -129,7 +129,19 @@ struct SegPlan {
   bool shift = false;   // 32 lanes, rows at any alignment: aligned vector loads against shifted copies of x
   bool shift64 = false; // the same for the FP64 copies (chosen separately)
   bool unroll = false;  // long rows (32 lanes, >= 512 entries on average): 4-way unrolled loops
-  int lanes16 = 0;      // MIXED16: lanes per row of the FP16 shifted kernel; 0 = read the FP32 copy
+  int lanes16 = 0;      // MIXED16: lanes per row of the FP16 kernel; 0 = read the FP32 copy
+  // MIXED16: the plan's matrix in FP16, each row padded with zeros to a
+  // multiple of 8 entries (16 bytes) so that every row starts aligned; the
+  // chunks' descriptors point into it (row stride = nc rounded up to 8)
+  DBuf<__half> m16;
+  DBuf<SegDesc> chunk_desc16;
+  int64_t mat_len16 = 0;
+  // MIXED16, row per lane (lanes16 = -kind): the transposed blocks in FP16
+  // (nc x nr, each column of rows padded to an even count), two output rows
+  // per lane read as one half2; tasks of up to 2 kind rows
+  DBuf<__half> mt16;
+  DBuf<SegDesc> task_desc16;
+  int ntasks16 = 0;
   int max_nc = 0;       // longest row (shared-memory staging of the gathered x)
   int64_t mat_len = 0;  // total stored matrix entries
   int64_t in_len = 0, out_len = 0;
@@ -256,11 +268,10 @@ struct Level {
   DBuf<float> myd32;
   DBuf<double> W64, Wt64, Z64, Zt64, mu;
   DBuf<float> W32, Wt32, Z32, Zt32;
-  // MIXED16 storage: FP16 copies of the smoother rows, the basis and the
-  // block rows of A (built on demand; h16 once every copy of the level is
-  // in range)
+  // MIXED16 storage: the level's gather-GEMV plans hold FP16 copies of their
+  // matrices (SegPlan::m16; built on demand, h16 once every FP32 copy of the
+  // level is in the FP16 range)
   bool h16 = false;
-  DBuf<__half> W16, Wt16, Z16, Zt16, A16, At16;
   // rows omega_i of A over Omega_i (layout of W_i; the residual of the
   // batched solver where A has no block rows), applied with the RAS plan
   DBuf<double> Aw64, AwT64;
@@ -299,13 +310,23 @@ int launch_seg(const SegPlan& p, const void* M, bool m_fp32, const void* x, void
                const void* MT = nullptr);
 // The same with FP16 matrix entries (MIXED16 storage) and FP32 vectors:
 // entries are widened to FP32 and summed in FP32.
-int launch_seg16(const SegPlan& p, const __half* M, const __half* MT, const float* x, float* y, SegMode mode,
-                 const int* skip, cudaStream_t s, const float* csrc = nullptr, float* cdst = nullptr);
-// dst[i] = FP16 round-to-nearest of src[i] (setup: the MIXED16 copies).
-int launch_to_half(const float* src, __half* dst, int64_t n, cudaStream_t s);
+// Reads the plan's padded FP16 copy (SegPlan::m16) with p.lanes16 lanes per row.
+int launch_seg16(const SegPlan& p, const float* x, float* y, SegMode mode, const int* skip, cudaStream_t s,
+                 const float* csrc = nullptr, float* cdst = nullptr);
+// The padded FP16 copy of a plan's FP32 matrix (row-major blocks at m_off,
+// nr x nc): block b goes to m_off16[b] with rows of nc rounded up to 8
+// entries, the padding zero; FP16 round to nearest.
+int launch_pad16(const float* M32, const int64_t* m_off, const int32_t* nr, const int32_t* nc,
+                 const int64_t* m_off16, int nblocks, __half* dst, cudaStream_t s);
+// The same for the transposed blocks (nc x nr row-major at m_off): block b
+// goes to m_off16[b] as nc rows of nr rounded up to even, the padding zero.
+int launch_pad16t(const float* MT32, const int64_t* m_off, const int32_t* nr, const int32_t* nc,
+                  const int64_t* m_off16, int nblocks, __half* dst, cudaStream_t s);
 int launch_apply(const ApplyPlan& p, const Level& L, bool fp32, const void* x, void* y, int sign, const int* skip,
                  cudaStream_t s);
 int launch_cast(const void* src, bool src32, void* dst, bool dst32, int64_t n, const int* skip, cudaStream_t s);
+// *d_count += the number of non-finite entries of v[0..n) (setup checks of the stored operators).
+int count_nonfinite(const void* v, int64_t n, bool fp32, int* d_count, cudaStream_t s);
 int launch_copy_vec(const void* src, void* dst, bool fp32, int64_t n, const int* skip, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
@@ -486,16 +507,25 @@ constexpr int kInvChunk = 32;  // RHS columns per CTA of the inverse-row solves
 struct PhaseTimer {
   bool on = false;
   double acc[16] = {0};
+  double flops[16] = {0};  // FP64 flops of each phase (counted from the block sizes)
   const char* name[16] = {nullptr};
   void add(int i, const char* nm, double ms) {
     acc[i] += ms;
     name[i] = nm;
   }
 };
+// work_out[b]: Jacobi sweeps (blocks below the team size) or implicit-QL
+// rotations (team blocks) that block b's eigensolve took.
 int launch_gep(int nb, int max_no, const int32_t* m, const int32_t* no, const int64_t* a_off, const double* Lpool,
                const double* Spool, const int32_t* cap, double thresh, const int64_t* mu_off, double* mu,
                const int64_t* z_off_cap, double* Zcap, int32_t* kout, double* scratch, const int64_t* scr_off,
-               cudaStream_t s);
+               int32_t* work_out, cudaStream_t s);
+// true when launch_gep takes the tridiagonal + implicit QL path for a batch
+// whose largest omega block has max_no entries
+bool gep_uses_ql(int max_no);
+// Measured FP64 FMA rate of the device (GFLOP/s): independent FMA chains on
+// every SM, timed with CUDA events.
+int measure_fp64_rate(cudaStream_t s, double* gflops);
 int launch_pack_z(int nb, const int32_t* no, const int32_t* k, const int64_t* z_off_cap, const double* Zcap,
                   const int64_t* z_off, double* Z64, float* Z32, double* Zt64, float* Zt32, cudaStream_t s);
 // Rows omega_i of each assembled A_i (before its Cholesky) in the layout of
@@ -537,6 +567,6 @@ int launch_next_rows(const NextGramPlan& p, const int64_t* g_ptr, const int64_t*
 int launch_schur_rows(int nb, int max_m, const LocalBatch& b, const int64_t* g_ptr, const int64_t* h_off,
                       const int32_t* rank, const double* R, const int32_t* M, const int64_t* y_off,
                       const int32_t* y_rows, double* Ypool, const int64_t* n_off, double* nrm, double* Atpool,
-                      cudaStream_t s);
+                      int32_t* rank_out, cudaStream_t s);
 
 }  // namespace amgdd

@@ -440,8 +440,10 @@ __global__ void k_gep(const int32_t* __restrict__ mdim, const int32_t* __restric
                       const double* __restrict__ Spool, const int32_t* __restrict__ capv, double thresh,
                       const int64_t* __restrict__ mu_off, double* __restrict__ mu_out,
                       const int64_t* __restrict__ z_off_cap, double* __restrict__ Zcap, int32_t* __restrict__ kout,
-                      double* __restrict__ scratch, const int64_t* __restrict__ scr_off) {
+                      double* __restrict__ scratch, const int64_t* __restrict__ scr_off,
+                      int32_t* __restrict__ work_out) {
   __shared__ double sh[32];
+  int work = 0;  // Jacobi sweeps or QL rotations (for the setup flop count)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Team<CL> tm;
   const int b = blockIdx.x / CL;
@@ -644,6 +646,7 @@ __global__ void k_gep(const int32_t* __restrict__ mdim, const int32_t* __restric
       tm.sync();
       const int nrot = ctl[0];
       const int fin = ctl[1];
+      work += nrot;
       if (fin) break;
       for (int row = tm.rank; row < n; row += tm.size) {
         for (int q = 0; q < nrot; ++q) {
@@ -678,6 +681,7 @@ __global__ void k_gep(const int32_t* __restrict__ mdim, const int32_t* __restric
       off = tm.sum(off, sh, red);
       tot = tm.sum(tot, sh, red);
       if (!(off > tolf * tolf * tot)) break;
+      ++work;
       for (int r = 0; r < mr; ++r) {
         for (int k = threadIdx.x; k < ne / 2; k += blockDim.x) {
           int p, q;
@@ -740,6 +744,7 @@ __global__ void k_gep(const int32_t* __restrict__ mdim, const int32_t* __restric
       }
     }
   }
+  if (tm.rank == 0) work_out[b] = work;
   // ascending mu (stable on ties)
   for (int i = tm.rank; i < n; i += tm.size) {
     const double di = C[i + (int64_t)i * n];
@@ -964,7 +969,7 @@ __global__ void k_schur_rows(const int32_t* __restrict__ mdim, const int32_t* __
                              const int32_t* __restrict__ M, const int64_t* __restrict__ y_off,
                              const int32_t* __restrict__ y_rows, double* __restrict__ Ypool,
                              const int64_t* __restrict__ n_off, double* __restrict__ nrm_pool,
-                             double* __restrict__ Atpool) {
+                             double* __restrict__ Atpool, int32_t* __restrict__ rank_out) {
   __shared__ double s_best;
   __shared__ int s_bi;
   const Team<CL> tm;
@@ -1062,6 +1067,7 @@ __global__ void k_schur_rows(const int32_t* __restrict__ mdim, const int32_t* __
     tm.sync();
     r = k + 1;
   }
+  if (tm.rank == 0) rank_out[b] = r;
   // S~ = X_2^T X_2 over rows r.. (the same sum order for (a, c) and (c, a))
   double* At = Atpool + a_off[b];
   for (int64_t e = tm.rank; e < (int64_t)no * no; e += tm.size) {
@@ -1179,14 +1185,58 @@ int gep_scratch_doubles(int n, int CL) { return 5 * n * n + (n + 2) / 2 + 1 + CL
 int launch_gep(int nb, int max_no, const int32_t* m, const int32_t* no, const int64_t* a_off, const double* Lpool,
                const double* Spool, const int32_t* cap, double thresh, const int64_t* mu_off, double* mu,
                const int64_t* z_off_cap, double* Zcap, int32_t* kout, double* scratch, const int64_t* scr_off,
-               cudaStream_t s) {
+               int32_t* work_out, cudaStream_t s) {
   if (nb == 0) return AMGDD_OK;
   const size_t smem = (size_t)(2 * (max_no + 1)) * sizeof(double) + (size_t)(max_no + 1) * sizeof(int);
-  if (max_no >= kBigDim)
+  if (gep_uses_ql(max_no))
     return launch_team(k_gep<kBigTeam, true>, kBigTeam, nb, 256, smem, s, m, no, a_off, Lpool, Spool, cap, thresh,
-                       mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off);
+                       mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off, work_out);
   return launch_team(k_gep<1, false>, 1, nb, threads_for((int64_t)max_no * max_no), smem, s, m, no, a_off, Lpool,
-                     Spool, cap, thresh, mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off);
+                     Spool, cap, thresh, mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off, work_out);
+}
+
+bool gep_uses_ql(int max_no) { return max_no >= kBigDim; }
+
+namespace {
+// Independent FMA chains: 8 per thread, `iters` steps each (2 flops per FMA).
+__global__ void k_fp64_rate(double* out, int iters, double a, double b) {
+  double v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = (double)(threadIdx.x + k);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = fma(v[k], a, b);
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += v[k];
+  if (t == 12345.678) out[0] = t;  // keeps the chains live; never true for these inputs
+}
+}  // namespace
+
+int measure_fp64_rate(cudaStream_t s, double* gflops) {
+  DBuf<double> out;
+  AMGDD_TRY(out.alloc(1));
+  const int blocks = 152 * 8, threads = 256, iters = 4096;
+  cudaEvent_t e[2];
+  for (auto& v : e) AMGDD_CUDA(cudaEventCreate(&v));
+  float best = 0.f;
+  int rc = AMGDD_OK;
+  for (int rep = 0; rep < 4 && rc == AMGDD_OK; ++rep) {
+    cudaEventRecord(e[0], s);
+    k_fp64_rate<<<blocks, threads, 0, s>>>(out.p, iters, 0.999999, 1e-7);
+    cudaEventRecord(e[1], s);
+    float ms = 0.f;
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e[0], e[1]) != cudaSuccess)
+      rc = AMGDD_ERR_CUDA;
+    count_kernels(1);
+    if (rep > 0 && (best == 0.f || ms < best)) best = ms;
+  }
+  for (auto& v : e) cudaEventDestroy(v);
+  AMGDD_TRY(rc);
+  *gflops = 2.0 * 8.0 * (double)iters * blocks * threads / (best * 1e-3) / 1e9;
+  return AMGDD_OK;
 }
 
 int launch_pack_z(int nb, const int32_t* no, const int32_t* k, const int64_t* z_off_cap, const double* Zcap,
@@ -1224,18 +1274,18 @@ int launch_next_rows(const NextGramPlan& p, const int64_t* g_ptr, const int64_t*
 int launch_schur_rows(int nb, int max_m, const LocalBatch& b, const int64_t* g_ptr, const int64_t* h_off,
                       const int32_t* rank, const double* R, const int32_t* M, const int64_t* y_off,
                       const int32_t* y_rows, double* Ypool, const int64_t* n_off, double* nrm, double* Atpool,
-                      cudaStream_t s) {
+                      int32_t* rank_out, cudaStream_t s) {
   if (nb == 0) return AMGDD_OK;
   // cluster teams only while the batch leaves SMs idle: with many matrices a
   // CTA each keeps every SM busy without the team's barriers
   if (max_m >= kBigDim && nb * kBigTeam <= 2 * 152)
     return launch_team(k_schur_rows<kBigTeam>, kBigTeam, nb, 256, 0, s, b.m.p, b.no.p, b.a_off.p, b.pair_ptr.p,
                        b.pair_grp.p, b.pair_nz.p, b.map_ptr.p, b.map.p, g_ptr, h_off, rank, R, M, y_off, y_rows,
-                       Ypool, n_off, nrm, Atpool);
+                       Ypool, n_off, nrm, Atpool, rank_out);
   return launch_team(k_schur_rows<1>, 1, nb, max_m >= 64 ? 256 : 128, 0, s, b.m.p, b.no.p, b.a_off.p, b.pair_ptr.p,
                      b.pair_grp.p,
                      b.pair_nz.p, b.map_ptr.p, b.map.p, g_ptr, h_off, rank, R, M, y_off, y_rows, Ypool, n_off, nrm,
-                     Atpool);
+                     Atpool, rank_out);
 }
 
 namespace {
