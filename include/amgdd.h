@@ -152,14 +152,17 @@ typedef struct {
   int agg_passes;      /* amgdd_setup with agg = NULL: level-0 aggregates */
                        /*   by this many passes of standard aggregation   */
                        /*   (see amgdd_aggregate); >= 1, default 1        */
-  int schur_gram;      /* Schur complement of Eq. gevp-S: 0 (default) in  */
-                       /*   row form, S~ = X^T (I - Pi) X with Pi the     */
-                       /*   projector onto the Gamma rows (pivoted        */
-                       /*   Householder QR, cut at the numerical rank),   */
-                       /*   and the rows of G_{l+1} = G_l P_l carried by  */
-                       /*   QR; 1: from the Gram A~_i with diagonally     */
-                       /*   pivoted elimination (cut at schur_rtol) and   */
-                       /*   the rows of G_{l+1} from its Gram             */
+  int schur_gram;      /* Schur complement of Eq. gevp-S.  Row form:      */
+                       /*   S~ = X^T (I - Pi) X with Pi the projector     */
+                       /*   onto the Gamma rows (pivoted Householder QR,  */
+                       /*   cut at the numerical rank), and the rows of   */
+                       /*   G_{l+1} = G_l P_l carried by QR.  Gram form:  */
+                       /*   from A~_i with diagonally pivoted elimination */
+                       /*   (cut at schur_rtol), rows of G_{l+1} from its */
+                       /*   Gram.  0 (default): per level, rows unless    */
+                       /*   their QR would cost more than 8 times the     */
+                       /*   Gram elimination (3D coarse levels); 1: Gram  */
+                       /*   on every level; 2: rows on every level        */
 } amgdd_params;
 
 typedef struct amgdd_hierarchy amgdd_hierarchy; /* opaque, library-owned */

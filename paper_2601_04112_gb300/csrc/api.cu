@@ -1185,10 +1185,9 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
   std::vector<int32_t> loc(L.n, -1);
   std::vector<int64_t> gstamp((size_t)(L.g_ptr.size() - 1), -1);
   const int64_t budget = (int64_t)384 << 20;  // doubles per batch for A and A~ pools (and the rows of the splitting)
-  const bool rows_schur = !h.prm.schur_gram;
   // rows of the splitting of each aggregate (row route): sum of rank_g over the groups of nz_i
   std::vector<int64_t> yrows(nagg, 0);
-  if (rows_schur)
+  if (h.prm.schur_gram != 1)
     for (int i = 0; i < nagg; ++i) {
       const int64_t o0 = L.om_ptr[i], o1 = L.om_ptr[i + 1];
       for (int64_t q = o0; q < o1; ++q) {
@@ -1204,11 +1203,25 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
       }
     }
   std::fill(gstamp.begin(), gstamp.end(), -1);
+  // the route of this level (schur_gram = 0): rows unless their Householder
+  // QR would cost more than 8 times the Gram elimination (3D coarse levels,
+  // whose splitting holds many more rows than columns)
+  bool rows_schur = h.prm.schur_gram == 2;
+  if (h.prm.schur_gram == 0) {
+    double fr = 0.0, fg = 0.0;
+    for (int i = 0; i < nagg; ++i) {
+      const double m = mdim[i], ng = m - L.nomega[i], nr = (double)yrows[i];
+      fr += 4.0 * nr * m * std::min(nr, ng);
+      fg += m * m * m;
+    }
+    rows_schur = fr <= 8.0 * fg;
+  }
+  L.schur_rows = rows_schur;
   int i0 = 0;
   while (i0 < nagg) {
     int i1 = i0;
     int64_t pool = 0;
-    auto need = [&](int i) { return 2 * (int64_t)mdim[i] * mdim[i] + yrows[i] * mdim[i]; };
+    auto need = [&](int i) { return 2 * (int64_t)mdim[i] * mdim[i] + (rows_schur ? yrows[i] * mdim[i] : 0); };
     while (i1 < nagg && (i1 == i0 || pool + need(i1) <= budget)) {
       pool += need(i1);
       ++i1;
@@ -1319,8 +1332,10 @@ int build_level(amgdd_hierarchy& h, Level& L, int lvl, const int32_t* agg_in, cu
         AMGDD_TRY(nrm.alloc(std::max<int64_t>(noff[nb], 1)));
         DBuf<int32_t> drk;
         AMGDD_TRY(drk.alloc(nb));
+        // cluster teams once the mean row block holds a million entries (8 MB)
+        const bool team = yoff[nb] >= (int64_t)nb << 20;
         AMGDD_TRY(launch_schur_rows(nb, bmax_m, B, L.d_g_ptr.p, L.d_h_off.p, L.d_rank.p, L.d_R64.p, dM.p, dyoff.p,
-                                    dyr.p, Ypool.p, dnoff.p, nrm.p, Atpool.p, drk.p, s));
+                                    dyr.p, Ypool.p, dnoff.p, nrm.p, Atpool.p, drk.p, team, s));
         std::vector<int32_t> rk;
         AMGDD_TRY(download(rk, drk.p, nb, s));
         for (int t = 0; t < nb; ++t) {  // per reflection: norms and update of the remaining columns; then X_2^T X_2
@@ -1590,8 +1605,9 @@ int build_next(amgdd_hierarchy& h, Level& L, Level& N, cudaStream_t s) {
     }
   }
   AMGDD_CUDA(cudaStreamSynchronize(s));
-  if (!h.prm.schur_gram) {
-    // row route: G_{l+1}'s rows by QR of the stacked R_g P_g, in chunks of
+  if (L.schur_rows) {
+    // row route (this level formed its Schur complements from rows; the next
+    // level most likely will too): G_{l+1}'s rows by QR of the stacked R_g P_g, in chunks of
     // new groups whose stacked rows fit a scratch budget
     std::vector<int64_t> t_off(nnew + 1, 0);
     for (int64_t q = 0; q < nnew; ++q) {
@@ -1612,8 +1628,10 @@ int build_next(amgdd_hierarchy& h, Level& L, Level& N, cudaStream_t s) {
     for (int64_t f = 0; f < nnew;) {
       int64_t e = f + 1;
       while (e < nnew && t_off[e + 1] - t_off[f] <= std::max(budget, maxper)) ++e;
+      // cluster teams once the mean stacked block holds a million entries
+      const bool team = t_off[e] - t_off[f] >= (e - f) << 20;
       AMGDD_TRY(launch_next_rows(P, L.d_g_ptr.p, L.d_h_off.p, L.d_rank.p, L.d_R64.p, L.Z64.p, d_toff.p, tscr.p,
-                                 N.d_R64.p, N.d_R32.p, N.d_rank.p, f, e - f, s));
+                                 N.d_R64.p, N.d_R32.p, N.d_rank.p, f, e - f, team, s));
       f = e;
     }
     AMGDD_TRY(download(N.g_rank, N.d_rank.p, nnew, s));
@@ -3159,6 +3177,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   amgdd_params prm = params ? *params : amgdd_params_default();
   if (prm.L_max < 1 || prm.n_cmin < 1 || prm.n_cmin > 8 || prm.max_iter < 1 || overlap < 1 ||
       (prm.precision != AMGDD_FP64 && prm.precision != AMGDD_MIXED32 && prm.precision != AMGDD_MIXED16) ||
+      prm.schur_gram < 0 || prm.schur_gram > 2 ||
       prm.check_every < 1 || prm.n_coarse < 1 ||
       prm.coarse_overlap < 0 || prm.cycle < 0 || prm.cycle > 1 || !(prm.kappa >= 0) ||
       (agg == nullptr && prm.agg_passes < 1) ||
@@ -4090,6 +4109,8 @@ int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap) {
   for (size_t l = 0; l + 1 < h->lv.size(); ++l) s += (l ? ", " : "") + std::to_string(h->lv[l]->n_color);
   s += "], \"n_mult\": [";
   for (size_t l = 0; l + 1 < h->lv.size(); ++l) s += (l ? ", " : "") + std::to_string(h->lv[l]->n_mult);
+  s += "], \"schur_route\": [";
+  for (size_t l = 0; l + 1 < h->lv.size(); ++l) s += std::string(l ? ", " : "") + (h->lv[l]->schur_rows ? "\"rows\"" : "\"gram\"");
   s += "], \"fp16_levels\": [";
   for (size_t l = 0; l < h->lv.size(); ++l) s += std::string(l ? ", " : "") + (h->lv[l]->h16 ? "true" : "false");
   s += "], \"fp16_lanes\": [";  // per level: ras, rast, restrict, prolong, block rows (0: FP32 copy)

@@ -204,6 +204,7 @@ struct Level {
   DBuf<int32_t> d_g_idx, d_rank;
   DBuf<double> d_H;     // Grams H_g = sum_rows g^T g (setup only, freed after use)
   bool rows_ready = false;  // d_R64 already holds rows carried by QR (row route): no pivoted Cholesky
+  bool schur_rows = false;  // this level's Schur complements were formed from rows (else from Grams)
   DBuf<double> d_R64;   // compressed rows, capacity s x s per group
   DBuf<float> d_R32;
   ApplyPlan aplan;  // supports of at most 32 nodes
@@ -561,12 +562,12 @@ int launch_next_gram(const NextGramPlan& p, int max_sn, const int64_t* g_ptr, co
 // rows x sn per new group (scratch holds groups first .. first+count-1).
 int launch_next_rows(const NextGramPlan& p, const int64_t* g_ptr, const int64_t* h_off, const int32_t* rank,
                      const double* R, const double* Z64, const int64_t* t_off, double* scratch, double* Rn64,
-                     float* Rn32, int32_t* rank_out, int64_t first, int64_t count, cudaStream_t s);
+                     float* Rn32, int32_t* rank_out, int64_t first, int64_t count, bool team, cudaStream_t s);
 // S~ of Eq. gevp-S from the rows of the splitting (row route) into the omega
 // block of Atpool; Ypool holds y_rows[b] x m per matrix, nrm m per matrix.
 int launch_schur_rows(int nb, int max_m, const LocalBatch& b, const int64_t* g_ptr, const int64_t* h_off,
                       const int32_t* rank, const double* R, const int32_t* M, const int64_t* y_off,
                       const int32_t* y_rows, double* Ypool, const int64_t* n_off, double* nrm, double* Atpool,
-                      int32_t* rank_out, cudaStream_t s);
+                      int32_t* rank_out, bool team, cudaStream_t s);
 
 }  // namespace amgdd

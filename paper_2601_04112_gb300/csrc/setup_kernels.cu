@@ -871,6 +871,7 @@ __global__ void k_next_gram(int64_t first, const int64_t* __restrict__ new_ptr, 
 // keeps the small singular values of the rows to rounding relative to the
 // largest, which the Gram of the rows would square away.
 // T: stacked rows, column-major (ld = rows) in scratch at t_off[h].
+template <int CL>
 __global__ void k_next_rows(int64_t first, const int64_t* __restrict__ new_ptr, const int32_t* __restrict__ contrib,
                             const int64_t* __restrict__ new_sptr, const int64_t* __restrict__ new_hoff,
                             const int64_t* __restrict__ rowz_ptr, const int64_t* __restrict__ rowz_zoff,
@@ -879,11 +880,13 @@ __global__ void k_next_rows(int64_t first, const int64_t* __restrict__ new_ptr, 
                             const int32_t* __restrict__ rank, const double* __restrict__ R,
                             const double* __restrict__ Z64, const int64_t* __restrict__ t_off,
                             double* __restrict__ scratch, double* __restrict__ Rn64, float* __restrict__ Rn32,
-                            int32_t* __restrict__ rank_out) {
+                            int32_t* __restrict__ rank_out, double* __restrict__ red_pool) {
   __shared__ double sh[32];
-  const int64_t h = first + blockIdx.x;
+  const Team<CL> tm;
+  const int64_t h = first + blockIdx.x / CL;
   const int sn = (int)(new_sptr[h + 1] - new_sptr[h]);
   double* T = scratch + (t_off[h] - t_off[first]);
+  double* red = red_pool + (h - first) * CL;
   const int nr = (int)(t_off[h + 1] - t_off[h]) / sn;
   // T = [R_g P_g; ...]
   int row = 0;
@@ -893,7 +896,7 @@ __global__ void k_next_rows(int64_t first, const int64_t* __restrict__ new_ptr, 
     const int rk = rank[g];
     const double* Rg = R + h_off[g];
     const int64_t rp = rowz_ptr[g];
-    for (int64_t e = threadIdx.x; e < (int64_t)rk * sn; e += blockDim.x) {
+    for (int64_t e = tm.rank; e < (int64_t)rk * sn; e += tm.size) {
       const int r = (int)(e / sn), d = (int)(e % sn);
       double acc = 0.0;
       for (int bb = 0; bb < s; ++bb) {
@@ -905,14 +908,14 @@ __global__ void k_next_rows(int64_t first, const int64_t* __restrict__ new_ptr, 
     }
     row += rk;
   }
-  __syncthreads();
+  tm.sync();
   const int kmax = min(nr, sn);
-  const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31, nw = (int)blockDim.x >> 5;
+  const int warp = tm.rank >> 5, lane = (int)threadIdx.x & 31, nw = tm.size >> 5;
   for (int k = 0; k < kmax; ++k) {
     const double* xk = T + (int64_t)k * nr;
     double part = 0.0;
-    for (int i = k + (int)threadIdx.x; i < nr; i += blockDim.x) part += xk[i] * xk[i];
-    const double nb2 = block_sum(part, sh);
+    for (int i = k + tm.rank; i < nr; i += tm.size) part += xk[i] * xk[i];
+    const double nb2 = tm.sum(part, sh, red);
     const double x0 = xk[k];
     const double xn = sqrt(nb2);
     const double alpha = x0 >= 0.0 ? -xn : xn;
@@ -930,20 +933,20 @@ __global__ void k_next_rows(int64_t first, const int64_t* __restrict__ new_ptr, 
         for (int i = k + 1 + lane; i < nr; i += 32) cj[i] -= f * xk[i];
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) T[k + (int64_t)k * nr] = vtv > 0.0 ? alpha : x0;
-    __syncthreads();
+    tm.sync();
+    if (tm.rank == 0) T[k + (int64_t)k * nr] = vtv > 0.0 ? alpha : x0;
+    tm.sync();
   }
   // R (row-major, ld sn): row k = T[k, k..sn-1], zeros left of the diagonal
   double* Rh = Rn64 + new_hoff[h];
   float* Rh32 = Rn32 + new_hoff[h];
-  for (int64_t e = threadIdx.x; e < (int64_t)kmax * sn; e += blockDim.x) {
+  for (int64_t e = tm.rank; e < (int64_t)kmax * sn; e += tm.size) {
     const int k = (int)(e / sn), j = (int)(e % sn);
     const double v = j < k ? 0.0 : T[k + (int64_t)j * nr];
     Rh[e] = v;
     Rh32[e] = (float)v;
   }
-  if (threadIdx.x == 0) rank_out[h] = kmax;
+  if (tm.rank == 0) rank_out[h] = kmax;
 }
 
 // Schur complement of Eq. gevp-S in row form: S~ = X^T (I - Pi) X with
@@ -1261,24 +1264,30 @@ int launch_next_gram(const NextGramPlan& p, int max_sn, const int64_t* g_ptr, co
 
 int launch_next_rows(const NextGramPlan& p, const int64_t* g_ptr, const int64_t* h_off, const int32_t* rank,
                      const double* R, const double* Z64, const int64_t* t_off, double* scratch, double* Rn64,
-                     float* Rn32, int32_t* rank_out, int64_t first, int64_t count, cudaStream_t s) {
+                     float* Rn32, int32_t* rank_out, int64_t first, int64_t count, bool team, cudaStream_t s) {
   if (count == 0) return AMGDD_OK;
-  k_next_rows<<<(unsigned)count, 256, 0, s>>>(first, p.new_ptr.p, p.contrib.p, p.new_sptr.p, p.new_hoff.p,
-                                              p.rowz_ptr.p, p.rowz_zoff.p, p.rowz_k.p, p.rowz_col.p, g_ptr, h_off,
-                                              rank, R, Z64, t_off, scratch, Rn64, Rn32, rank_out);
-  AMGDD_CUDA(cudaGetLastError());
-  count_kernels(1);
-  return AMGDD_OK;
+  DBuf<double> red;
+  AMGDD_TRY(red.alloc(count * kBigTeam));
+  // cluster teams for large stacked blocks (3D coarse levels), a CTA each otherwise
+  if (team)
+    return launch_team(k_next_rows<kBigTeam>, kBigTeam, (int)count, 256, 0, s, first, p.new_ptr.p, p.contrib.p,
+                       p.new_sptr.p, p.new_hoff.p, p.rowz_ptr.p, p.rowz_zoff.p, p.rowz_k.p, p.rowz_col.p, g_ptr,
+                       h_off, rank, R, Z64, t_off, scratch, Rn64, Rn32, rank_out, red.p);
+  return launch_team(k_next_rows<1>, 1, (int)count, 256, 0, s, first, p.new_ptr.p, p.contrib.p, p.new_sptr.p,
+                     p.new_hoff.p, p.rowz_ptr.p, p.rowz_zoff.p, p.rowz_k.p, p.rowz_col.p, g_ptr, h_off, rank, R, Z64,
+                     t_off, scratch, Rn64, Rn32, rank_out, red.p);
 }
 
 int launch_schur_rows(int nb, int max_m, const LocalBatch& b, const int64_t* g_ptr, const int64_t* h_off,
                       const int32_t* rank, const double* R, const int32_t* M, const int64_t* y_off,
                       const int32_t* y_rows, double* Ypool, const int64_t* n_off, double* nrm, double* Atpool,
-                      int32_t* rank_out, cudaStream_t s) {
+                      int32_t* rank_out, bool team, cudaStream_t s) {
   if (nb == 0) return AMGDD_OK;
-  // cluster teams only while the batch leaves SMs idle: with many matrices a
-  // CTA each keeps every SM busy without the team's barriers
-  if (max_m >= kBigDim && nb * kBigTeam <= 2 * 152)
+  // cluster teams for large row blocks (each reflection streams the whole
+  // block; a CTA alone would take seconds on a 3D coarse level) or while the
+  // batch leaves SMs idle; with many small matrices a CTA each keeps every
+  // SM busy without the team's barriers
+  if (max_m >= kBigDim && (team || nb * kBigTeam <= 2 * 152))
     return launch_team(k_schur_rows<kBigTeam>, kBigTeam, nb, 256, 0, s, b.m.p, b.no.p, b.a_off.p, b.pair_ptr.p,
                        b.pair_grp.p, b.pair_nz.p, b.map_ptr.p, b.map.p, g_ptr, h_off, rank, R, M, y_off, y_rows,
                        Ypool, n_off, nrm, Atpool, rank_out);
