@@ -58,6 +58,9 @@ def parse_args():
     ap.add_argument("--serve", action="store_true",
                     help="run the serving workload (many operators and right-hand-side counts) instead")
     ap.add_argument("--no-serving", action="store_true", help="skip the small serving run of the default line")
+    ap.add_argument("--serve-mix", action="store_true",
+                    help="run the serving mix with setup on the request path (operators carried by the requests; "
+                         "sides 32..256, 1..64 right-hand sides; a one-at-a-time FP64 loop beside it) instead")
     ap.add_argument("--additive", action="store_true",
                     help="time PCG with the additive two-level method (cycle = 1) beside the multiplicative two-level "
                          "cycle, FP64, on the 64x64 workload's two-level hierarchy, instead")
@@ -382,6 +385,91 @@ def serving_run(amg, seed, sides, nops, nreq, max_rhs, rate_frac=0.8, slots=4):
             "precision": "mixed", "data": "synthetic, seeded"}
 
 
+def serving_mix_run(amg, seed, sides, nreq, max_rhs, pool=None, rate_fracs=(0.5, 0.8, 1.0), slots=4):
+    """The serving mix with setup on the request path: every request carries its operator, a 2D Q1 problem with
+    side drawn uniformly from `sides`, theta ~ U[0, pi), eps log-uniform in [1e-6, 1], 4x4 aggregates, LS_{2,3,4},
+    mixed precision, and 1..max_rhs N(0,1) right-hand sides.  pool = None: a new operator per request (no
+    reuse); pool = P: operators drawn from a seeded pool of P.  Latency is arrival -> result.  Reported: the
+    saturated rate (everything arrives at once), open-loop Poisson arrivals at rate_fracs of it (each run with
+    operators keyed afresh, so that setup stays on the request path), and a one-at-a-time FP64 loop over the same
+    requests (setup and solve per request, nothing overlapped, each operator built once).  Both build with the
+    fixed kernel choices (tune = 0)."""
+    import numpy as np
+    import torch
+    from inputs import block_aggregates_2d, q1_2d, rotated_sqrtK, seeded_rhs
+
+    rng = np.random.default_rng(seed)
+    nops = nreq if pool is None else pool
+    opdefs = []
+    for j in range(nops):
+        N = int(sides[int(rng.integers(len(sides)))])
+        theta, eps = float(rng.uniform(0.0, math.pi)), float(10.0 ** rng.uniform(-6.0, 0.0))
+        opdefs.append(q1_2d(N, rotated_sqrtK(theta, eps), agg=block_aggregates_2d(N, 4)))
+    reqs = []
+    for i in range(nreq):
+        k = i if pool is None else int(rng.integers(nops))
+        reqs.append((k, seeded_rhs(opdefs[k].n, int(rng.integers(1, max_rhs + 1)), seed * 100000 + i)))
+    cols = sum(B.shape[1] for _, B in reqs)
+    # setup on the request path takes the fixed kernel choices (tune = 0): timing the forms of every new
+    # operator costs more than it saves on a request's few solves, and builds overlap other work on the GPU
+    kw = dict(c_min=(2, 3, 4), n_coarse=2000, precision=amg.MIXED32, tune=0)
+
+    def run(key0, rate):
+        srv = amg.Server(slots=slots)
+        gaps = rng.exponential(1.0 / rate, nreq) if rate else np.zeros(nreq)
+        t0 = time.perf_counter()
+        due = t0
+        sub = []
+        for (k, B), g in zip(reqs, gaps):
+            due += g
+            while time.perf_counter() < due:
+                time.sleep(0)
+            sub.append(srv.submit_problem(opdefs[k], key=key0 + k, b=B, **kw)[0])
+        lats = []
+        for rid in sub:
+            x, infos, lat, st = srv.poll(rid)
+            assert st == 0 and all(i["relres_true"] <= 1e-8 for i in infos), infos
+            lats.append(lat)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        lats.sort()
+        pct = lambda q: lats[min(len(lats) - 1, int(q * len(lats)))]
+        return {"requests_per_s": nreq / wall, "solves_per_s": cols / wall, "p50_ms": pct(0.5),
+                "p99_ms": pct(0.99), "builds": st["builds"], "setup_ms_total": st["build_ms_total"],
+                "cache_hits": st["cache_hits"], "mean_batch_columns": st["mean_batch_columns"],
+                "evictions": st["evictions"], "waits_for_memory": st["waits_for_memory"]}
+
+    sat = run(1 << 40, None)
+    open_loop = []
+    for j, f in enumerate(rate_fracs):
+        r = run((j + 2) << 40, f * sat["requests_per_s"])
+        r["rate_frac_of_saturation"] = f
+        open_loop.append(r)
+    # one request at a time, FP64, no server: setup and solve of each request in turn
+    t0 = time.perf_counter()
+    built = {}
+    lat1 = []
+    for k, B in reqs:
+        t1 = time.perf_counter()
+        if k not in built:  # the loop keeps what it built (a pool reuses its operators)
+            built[k] = amg.Hierarchy.from_problem(opdefs[k], overlap=1, c_min=(2, 3, 4), n_coarse=2000, tune=0)
+        H = built[k]
+        _, inf = H.solve(B, tol=1e-8)
+        assert all(i["relres_true"] <= 1e-8 for i in inf)
+        lat1.append((time.perf_counter() - t1) * 1e3)
+    torch.cuda.synchronize()
+    loop_s = time.perf_counter() - t0
+    lat1.sort()
+    return {"requests": nreq, "rhs_columns": cols, "sides": list(sides), "max_rhs": max_rhs,
+            "operators": "one per request" if pool is None else f"pool of {pool}", "slots": slots,
+            "saturated": sat, "open_loop": open_loop,
+            "fp64_one_at_a_time": {"requests_per_s": nreq / loop_s, "solves_per_s": cols / loop_s,
+                                   "service_p50_ms": lat1[len(lat1) // 2],
+                                   "service_p99_ms": lat1[min(len(lat1) - 1, int(0.99 * len(lat1)))]},
+            "precision": "mixed (FP32 V-cycle, FP64 flexible CG) in the server", "data": "synthetic, seeded"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -502,6 +590,16 @@ def run_ours(args):
             print(json.dumps({"metric": f"LS variants over {args.ls_study} (FP64 PCG to 1e-8)", "impl": "ours",
                               "workload": workload_desc(config_problem("fd_500_rot")[1]), "points": rows}),
                   flush=True)
+        return
+
+    if args.serve_mix:
+        # the serving mix with setup on the request path (literal: a new operator per request; and a pool of 16)
+        out = {"metric": "serving with setup on the request path: solves/s and p50/p99 latency (mixed)",
+               "impl": "ours", "n_gpus": world,
+               "literal": serving_mix_run(amg, seed=5, sides=(32, 64, 128, 256), nreq=48, max_rhs=64),
+               "pool": serving_mix_run(amg, seed=6, sides=(32, 64, 128, 256), nreq=192, max_rhs=64, pool=16)}
+        if rank == 0:
+            print(json.dumps(out), flush=True)
         return
 
     if args.serve:

@@ -431,6 +431,20 @@ int amgdd_server_add_operator(amgdd_server* s, int64_t key, const amgdd_csr* G, 
  * once with the request id.  INVALID_ARG for an unknown operator or device
  * pointers.                                                               */
 int amgdd_server_submit(amgdd_server* s, int64_t op, const double* b, int nrhs, double tol, double* x, int64_t* req);
+/* Queues a solve whose operator comes with the request (setup on the request
+ * path): if `key` is resident (or already queued for setup) the request joins
+ * it (*cached = 1); otherwise the operator (G, D1, agg, overlap, params as in
+ * amgdd_setup; the caller keeps them valid until the request is polled to
+ * completion) is built by a worker once admission allows: its expected
+ * device bytes (bytes per unknown of the operators built so far, x 1.25)
+ * fit the budget after evicting idle operators and the device's free memory
+ * at that moment.  Meanwhile the request waits and other requests proceed;
+ * a setup error completes the operator's requests with that error, and an
+ * operator that cannot fit even with nothing else resident fails with
+ * AMGDD_ERR_OOM.  b and x as in amgdd_server_submit.                       */
+int amgdd_server_submit_problem(amgdd_server* s, int64_t key, const amgdd_csr* G, const double* D1,
+                                const int32_t* agg, int overlap, const amgdd_params* params, const double* b,
+                                int nrhs, double tol, double* x, int64_t* req, int* cached);
 /* AMGDD_PENDING while queued or running (waits up to wait_ms first; < 0:
  * until done); else the request's status, with info (nrhs entries, may be
  * NULL) and the latency from submit to completion, and the request is
@@ -438,7 +452,9 @@ int amgdd_server_submit(amgdd_server* s, int64_t op, const double* b, int nrhs, 
 int amgdd_server_poll(amgdd_server* s, int64_t req, int wait_ms, amgdd_info* info, double* latency_ms);
 /* JSON: completed requests, batches, mean columns per batch, latency
  * p50/p99/max (ms, over every completed request), resident operators and
- * bytes, evictions, cache hits, queue length, seconds since creation.    */
+ * bytes, evictions, cache hits, queue length, operators built on the request
+ * path and their total setup ms, admission waits, bytes per unknown, seconds
+ * since creation.                                                         */
 int amgdd_server_stats(amgdd_server* s, char* json, size_t cap);
 /* Stops the workers after their current batches and frees every operator. */
 void amgdd_server_destroy(amgdd_server* s);

@@ -36,6 +36,7 @@ EXPORTED = [
     "amgdd_server_create", "amgdd_server_add_operator", "amgdd_server_submit", "amgdd_server_poll",
     "amgdd_server_stats", "amgdd_server_destroy", "amgdd_hierarchy_save", "amgdd_hierarchy_load",
     "amgdd_selftest_wait_timeouts", "amgdd_aggregate", "amgdd_struct_size", "amgdd_measure_fp64",
+    "amgdd_server_submit_problem",
 ]
 AMGDD_PENDING = 1
 
@@ -122,6 +123,10 @@ def load_library(path: str = LIB_PATH):
                                               ctypes.POINTER(i32)]
     lib.amgdd_server_submit.argtypes = [vp, ctypes.c_int64, vp, i32, dbl, vp, ctypes.POINTER(ctypes.c_int64)]
     lib.amgdd_server_poll.argtypes = [vp, ctypes.c_int64, i32, ctypes.POINTER(Info), ctypes.POINTER(dbl)]
+    lib.amgdd_server_submit_problem.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(Csr), vp, vp, i32,
+                                                ctypes.POINTER(Params), vp, i32, dbl, vp, ctypes.POINTER(ctypes.c_int64),
+                                                ctypes.POINTER(i32)]
+    lib.amgdd_server_submit_problem.restype = i32
     lib.amgdd_server_stats.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.amgdd_server_destroy.argtypes = [vp]
     lib.amgdd_server_destroy.restype = None
@@ -429,9 +434,31 @@ class Server:
         self._bufs[rid.value] = (b, x, nrhs)
         return rid.value
 
+    def submit_problem(self, prob, key: int, b: np.ndarray, tol: float = 1e-8, overlap: int = 1, **kw):
+        """Queue a solve that carries its operator (setup on the request path when `key` is not resident);
+        returns (request id, cached)."""
+        rowptr = np.ascontiguousarray(prob.rowptr, dtype=np.int64)
+        col = np.ascontiguousarray(prob.col, dtype=np.int32)
+        val = np.ascontiguousarray(prob.val, dtype=np.float64)
+        agg = np.ascontiguousarray(prob.agg, dtype=np.int32)
+        d1 = None if prob.D1 is None else np.ascontiguousarray(prob.D1, dtype=np.float64)
+        csr = Csr(len(rowptr) - 1, prob.n, len(col), rowptr.ctypes.data, col.ctypes.data, val.ctypes.data, 0)
+        prm = params(**kw)
+        b = np.asfortranarray(b, dtype=np.float64)
+        nrhs = 1 if b.ndim == 1 else b.shape[1]
+        x = np.zeros_like(b, order="F")
+        rid, cached = ctypes.c_int64(), ctypes.c_int()
+        _check(self._lib.amgdd_server_submit_problem(self._s, int(key), ctypes.byref(csr), _ptr(d1)[0],
+                                                     agg.ctypes.data, int(overlap), ctypes.byref(prm), b.ctypes.data,
+                                                     nrhs, float(tol), x.ctypes.data, ctypes.byref(rid),
+                                                     ctypes.byref(cached)))
+        # the operator's inputs stay alive with the request (the library builds from them later)
+        self._bufs[rid.value] = (b, x, nrhs, (rowptr, col, val, agg, d1, csr, prm))
+        return rid.value, bool(cached.value)
+
     def poll(self, rid: int, wait_ms: int = -1):
         """None while pending; else (x, infos, latency_ms, status)."""
-        b, x, nrhs = self._bufs[rid]
+        b, x, nrhs = self._bufs[rid][:3]
         infos = (Info * nrhs)()
         lat = ctypes.c_double()
         st = self._lib.amgdd_server_poll(self._s, int(rid), int(wait_ms), infos, ctypes.byref(lat))

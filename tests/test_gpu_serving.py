@@ -104,3 +104,55 @@ def test_mixed_precision_operators(amg):
         x, infos, lat, st = srv.poll(rid)
         assert st == 0 and all(i["relres_true"] <= 1e-8 for i in infos)
     srv.close()
+
+
+def test_operators_built_on_the_request_path(amg):
+    """Requests that carry their operator: one setup per distinct key, run by a worker; every result equals a
+    solve of the same right-hand sides on a hierarchy built alone, to the batched solver's rounding."""
+    probs = _probs()
+    kw = dict(KW, tune=0)
+    reqs = _requests(probs, 18, 11)
+    refs = {}
+    for k, p in enumerate(probs):
+        H = amg.Hierarchy.from_problem(p, overlap=1, **kw)
+        refs[k] = H
+    expect = [np.asarray(refs[k].solve(B, tol=1e-8)[0]) for k, B in reqs]
+    srv = amg.Server(slots=3)
+    sub = [srv.submit_problem(probs[k], key=100 + k, b=B, **kw) for k, B in reqs]
+    assert sum(not cached for _, cached in sub) == len({k for k, _ in reqs})
+    for (rid, _), (k, B), xe in zip(sub, reqs, expect):
+        x, infos, lat, st = srv.poll(rid)
+        assert st == 0 and all(i["status"] == 0 and i["relres_true"] <= 1e-8 for i in infos)
+        assert _rel(np.asarray(x).reshape(xe.shape), xe) <= 1e-9
+    s = srv.stats()
+    assert s["builds"] == len({k for k, _ in reqs}) and s["build_ms_total"] > 0.0
+    assert s["bytes_per_unknown"] > 0.0
+    srv.close()
+
+
+def test_request_path_admission_waits_and_refuses(amg):
+    """A budget that holds one operator at a time: requests of three operators built on the request path all
+    complete, the idle operators being evicted between them; an operator larger than the whole budget fails
+    its request with AMGDD_ERR_OOM instead of waiting forever."""
+    probs = _probs()
+    kw = dict(KW, tune=0)
+    sizes = []
+    for p in probs:
+        H = amg.Hierarchy.from_problem(p, overlap=1, **kw)
+        sizes.append(H.device_bytes(with_batched=True))
+        del H
+    srv = amg.Server(hbm_budget=int(max(sizes) * 1.6), slots=2)
+    reqs = _requests(probs, 12, 13)
+    sub = [srv.submit_problem(probs[k], key=200 + k, b=B, **kw) for k, B in reqs]
+    for rid, _ in sub:
+        x, infos, lat, st = srv.poll(rid)
+        assert st == 0 and all(i["relres_true"] <= 1e-8 for i in infos)
+    s = srv.stats()
+    assert s["evictions"] >= 1 and s["device_bytes"] <= s["budget_bytes"]
+    srv.close()
+    tiny = amg.Server(hbm_budget=1 << 20, slots=1)
+    rid, _ = tiny.submit_problem(probs[0], key=300, b=seeded_rhs(probs[0].n, 1, 1), **kw)
+    with pytest.raises(amg.AmgddError) as e:
+        tiny.poll(rid)
+    assert e.value.status == -6
+    tiny.close()
