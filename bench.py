@@ -37,10 +37,11 @@ if ROOT not in sys.path:
 
 METRIC = "V-cycles/s & solves/s to 1e-8 rel. residual (mixed vs FP64); p50/p99 latency"
 WORKLOAD = "q1_512_rot"
-# DRAM bytes per V-cycle by kernel family, from ncu captures of WORKLOAD
-# (dram__bytes_read.sum + dram__bytes_write.sum summed over one V-cycle's
-# launches; profiles/).  Entries are removed when their kernels change.
-TRAFFIC = {}
+# DRAM bytes per V-cycle by (precision, kernel family), from an ncu capture
+# of WORKLOAD (dram__bytes_read.sum + dram__bytes_write.sum summed over one
+# V-cycle's launches, FP32 cycle; profiles/).  Entries are removed when their
+# kernels change.
+TRAFFIC = {(1, "k_seg"): 881.04e6, (1, "k_ell"): 41.80e6, (1, "k_dense"): 29.42e6}
 
 
 def parse_args():
