@@ -653,7 +653,7 @@ def run_ours(args):
                                    thresh=cfg["thresh"], kappa=cfg.get("kappa", 0.0), agg_passes=cfg.get("agg_passes", 1), precision=amg.MIXED16, tune_cache=args.tune_cache,
                                    coarse_overlap=cfg.get("coarse_overlap", 0),
                                    tune={"timed": 1, "defaults": 0, "staged": 2, "shifted": 3, "lanes": 4}[args.tune_mode],
-                                   deterministic=1 if args.deterministic else 0)
+                                   deterministic=1 if args.deterministic else 0, batch_cols=32)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     stats = H.stats()
@@ -853,9 +853,8 @@ def run_ours(args):
                "mixed": 8 * nbatch * world / tb_mix, "fp64": 8 * nbatch * world / tb_64,
                "max_iters_per_batch": {"mixed": itb_mix[0], "fp64": itb_64[0]}}
 
-    # 64 right-hand sides at once: one call (two batches of 32 columns that
-    # read every matrix once per iteration for 32 columns) against eight calls
-    # of 8 columns (the matrices read eight times per iteration of the 64)
+    # 64 right-hand sides in calls of 8, 16 or 32 columns (batches of that
+    # width: the matrices are read once per iteration for each batch)
     def timed_wide(prec, reps, width):
         H.set_precision(prec)
         B64 = torch.from_numpy(np.ascontiguousarray(seeded_rhs(n, 64, cfg["seed"] * 1000 + 700 + rank))).cuda()
@@ -877,14 +876,12 @@ def run_ours(args):
         return 64 * reps * world / maxrank(e0.elapsed_time(e1) / 1e3), its
 
     wreps = max(2, args.steps // 20)
-    w64, w64_it = timed_wide(amg.MIXED32, wreps, 64)
-    w8, w8_it = timed_wide(amg.MIXED32, wreps, 8)
-    f64w, _ = timed_wide(amg.FP64, wreps, 64)
-    f8w, _ = timed_wide(amg.FP64, wreps, 8)
-    batched["rhs64"] = {"unit": "solves/s", "calls": wreps * world,
-                        "mixed": {"one_call_2x32": w64, "eight_calls_8": w8, "ratio": w64 / w8},
-                        "fp64": {"one_call_2x32": f64w, "eight_calls_8": f8w, "ratio": f64w / f8w},
-                        "max_iters": {"2x32": w64_it, "8x8": w8_it}}
+    rhs64 = {"unit": "solves/s", "reps": wreps * world, "by_batch_width": {}}
+    for prec, key in ((amg.MIXED32, "mixed"), (amg.FP64, "fp64")):
+        for width in (8, 16, 32):
+            v, it = timed_wide(prec, wreps, width)
+            rhs64["by_batch_width"].setdefault(key, {})[str(width)] = {"solves_per_s": v, "max_iters": it}
+    batched["rhs64"] = rhs64
     H.set_precision(HEAD)
 
     serving = None

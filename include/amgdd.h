@@ -163,6 +163,12 @@ typedef struct {
                        /*   their QR would cost more than 8 times the     */
                        /*   Gram elimination (3D coarse levels); 1: Gram  */
                        /*   on every level; 2: rows on every level        */
+  int batch_cols;      /* amgdd_solve with nrhs > 1: columns per batch,   */
+                       /*   2, 4, 8, 16 or 32 (default 8).  Wider batches */
+                       /*   read the matrices once for more columns but   */
+                       /*   move more vector bytes per launch and hold    */
+                       /*   more registers; on the 512^2 Q1 workload 8 is */
+                       /*   fastest in mixed precision, on 3D 32^3 16     */
 } amgdd_params;
 
 typedef struct amgdd_hierarchy amgdd_hierarchy; /* opaque, library-owned */
@@ -186,7 +192,7 @@ typedef struct {
 
 /* Defaults: L_max 10, n_coarse 2000, thresh 0.1 (kappa 0), c_min = {2,3,4} (LS_{2,3,4}),
  * FP64, max_iter 1000, schur_rtol 1e-12, graphs on, check_every 4, tune 1,
- * no tune cache, agg_passes 1.                                            */
+ * no tune cache, agg_passes 1, batch_cols 8.                              */
 amgdd_params amgdd_params_default(void);
 
 /* ---- level-0 aggregation (Section 3.3) ------------------------------- */
@@ -205,8 +211,13 @@ amgdd_params amgdd_params_default(void);
  *   agg    : receives n aggregate ids 0..nagg-1 (creation order of the last
  *            pass); host or device buffer owned by the caller.
  *   nagg   : receives the number of aggregates (may be NULL).
- * Host computation (the passes are sequential by definition); `stream`
- * orders the copies of device buffers.  Errors: INVALID_ARG.             */
+ * Runs on the device, on `stream`: the visiting order fixes the result,
+ * yet each pass is an order-independent rule (pass 1's roots are the first
+ * maximal independent set, in ascending order, of the graph joining
+ * unknowns within distance 2; pass 3's that of the graph on the leftovers),
+ * so the unknowns decide in parallel rounds and the ids equal those of the
+ * sequential passes.  The row supports are grouped on the host.  Errors:
+ * INVALID_ARG, OOM, CUDA.                                                 */
 int amgdd_aggregate(const amgdd_csr* G, int passes, void* stream, int32_t* agg, int64_t* nagg);
 
 /* ---- setup: Algorithm 1 ---------------------------------------------- */
@@ -238,11 +249,17 @@ int amgdd_setup(const amgdd_csr* G, const double* D1, const int32_t* agg, int ov
  * every params.check_every iterations; iterations after convergence leave x
  * unchanged).  info (host, nrhs entries) may be NULL.
  * With nrhs > 1 (and CUDA graphs on) the right-hand sides are solved in
- * batches of up to 8 that share every V-cycle and A-apply launch: each
+ * batches of up to params.batch_cols (<= 32) that share every V-cycle and
+ * A-apply launch: each
  * column is its own CG (own scalars and stopping test, x frozen once it has
  * converged), so a batch reads the hierarchy's matrices once per iteration
- * for all of its columns.  Per-column results agree with single solves to
- * rounding (the batched kernels sum in another order).
+ * for all of its columns (a gather-GEMV whose staged input would not fit
+ * shared memory at the batch's width reads them once per column tile).  A
+ * batch runs at 2, 4, 8, 16 or 32 columns, the next at or above its count
+ * (padding columns are zero and finish at once); its workspace is allocated
+ * at the first batched solve and grown for a wider one.  Per-column results
+ * agree with single solves to rounding (the batched kernels sum in another
+ * order).
  * Returns the first non-OK per-RHS status, or an error code.             */
 int amgdd_solve(amgdd_hierarchy* h, const double* b, int nrhs, double tol, double* x, void* stream,
                 amgdd_info* info);
@@ -390,8 +407,10 @@ int64_t amgdd_kernel_launches(void);
 int amgdd_measure_fp64(void* stream, double* gflops);
 
 /* Device bytes the hierarchy holds: what setup kept, plus the batched-solve
- * workspace once allocated (with_batched != 0: counted even before it is,
- * as an admission estimate).  -1 for NULL.                               */
+ * workspace once allocated.  with_batched > 0 counts, as an admission
+ * estimate, the workspace a batched solve would grow it to: 1 for a batch
+ * of params.batch_cols columns, 2..32 for a batch of that many columns
+ * (rounded up to 2, 4, 8, 16 or 32).  -1 for NULL.                        */
 int64_t amgdd_device_bytes(const amgdd_hierarchy* h, int with_batched);
 
 /* ---- serving: continuous batching over cached hierarchies ------------ */
@@ -400,7 +419,7 @@ int64_t amgdd_device_bytes(const amgdd_hierarchy* h, int with_batched);
  * and solves queued requests with `slots` worker threads, each on its own
  * stream.  A worker takes the oldest request whose operator is idle and
  * merges the other queued requests for that operator and tolerance into one
- * batched amgdd_solve of at most max_batch (<= 8) columns; requests that
+ * batched amgdd_solve of at most max_batch (<= 32) columns; requests that
  * arrive meanwhile join later batches as slots free, and batches of
  * different operators overlap on the device.  The serving workload of many
  * grid sizes and right-hand-side counts is beyond the paper (which solves
@@ -410,7 +429,7 @@ typedef struct amgdd_server amgdd_server; /* opaque */
 typedef struct {
   int64_t hbm_budget;  /* device bytes for resident operators             */
   int slots;           /* concurrent batches (worker threads)             */
-  int max_batch;       /* columns per batched solve, 1..8                 */
+  int max_batch;       /* columns per batched solve, 1..32                */
 } amgdd_server_params;
 
 #define AMGDD_PENDING 1 /* amgdd_server_poll: not finished yet            */
@@ -459,14 +478,24 @@ int amgdd_server_stats(amgdd_server* s, char* json, size_t cap);
 /* Stops the workers after their current batches and frees every operator. */
 void amgdd_server_destroy(amgdd_server* s);
 
-/* Save a hierarchy to `path`: its setup inputs (G, D1, aggregates, overlap),
- * parameters and setup-time kernel choices (a binary file of this library
- * version).  Load runs the setup (Algorithm 1) again from the file with
- * those choices replayed instead of timed, on `stream`, so the loaded
- * hierarchy applies the same arithmetic with the same kernels on a GPU of
- * the same model.  Errors: AMGDD_ERR_INVALID_ARG for a path that cannot be
- * written or read or a file of another format or version; setup's errors.
- * The caller frees the loaded hierarchy with amgdd_free.                 */
+/* Save a hierarchy to `path` (a binary file of this library version): its
+ * setup inputs (G, D1, aggregates, overlap), parameters and setup-time
+ * kernel choices, and what Algorithm 1 computed on every level: the
+ * compressed rows of G_l's row groups, the aggregates and Omega lists, the
+ * rows omega_i of A_i^{-1} (and of A over Omega_i), the local spectra and
+ * bases Z_i, the coarse block rows where setup kept them, every row of
+ * A_i^{-1} for the additive form, and the coarsest inverse, all in FP64.
+ * Load restores them on `stream` without solving any local problem again:
+ * it rebuilds the index plans, derives the FP32 and transposed copies (and
+ * the FP16 copies under MIXED16), replays the kernel choices instead of
+ * timing them, and builds the dense tail and solve graphs; with the
+ * deterministic kernels the loaded hierarchy applies the same operator bit
+ * for bit.  Every size and index of the file is checked against the others
+ * before use.  Files of the earlier format (inputs and choices only) load by
+ * running the setup again with the choices replayed.  Errors:
+ * AMGDD_ERR_INVALID_ARG for a path that cannot be written or read, a file of
+ * another format or version, or one whose levels are inconsistent; OOM,
+ * CUDA.  The caller frees the loaded hierarchy with amgdd_free.          */
 int amgdd_hierarchy_save(const amgdd_hierarchy* h, const char* path);
 int amgdd_hierarchy_load(const char* path, void* stream, amgdd_hierarchy** out);
 

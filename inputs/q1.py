@@ -173,6 +173,16 @@ CONFIGS = {
     # the same structure on 512 x 512 cells
     "q1_512_circ": dict(N=512, field="circ", theta=0.0, eps=1e-6, d1=1e-8, bs=8, overlap=2, coarse_overlap=1,
                         seed=3, c_min=(4, 5), n_coarse=2000, thresh=0.1, nrhs=1),
+    # the closed-field-line workload with two layers of overlap on every level
+    # (one layer above level 0 loses convergence as the grid grows)
+    "q1_2048_circ_ov2": dict(N=2048, field="circ", theta=0.0, eps=1e-6, d1=1e-8, bs=8, overlap=2, coarse_overlap=2,
+                             seed=3, c_min=(4, 5), n_coarse=2000, thresh=0.1, nrhs=1),
+    "q1_512_circ_ov2": dict(N=512, field="circ", theta=0.0, eps=1e-6, d1=1e-8, bs=8, overlap=2, coarse_overlap=2,
+                            seed=3, c_min=(4, 5), n_coarse=2000, thresh=0.1, nrhs=1),
+    # the closed-field-line workload with the kappa-derived threshold of
+    # Section 3.4 (kappa = 50) and no cap on the kept eigenvectors
+    "q1_2048_circ_kappa": dict(N=2048, field="circ", theta=0.0, eps=1e-6, d1=1e-8, bs=8, overlap=2,
+                               coarse_overlap=1, seed=3, c_min=(1,), n_coarse=2000, thresh=0.1, kappa=50.0, nrhs=1),
     # the paper's own finite-difference discretization (Section 4.1): 500 x 500
     # unknowns, theta = pi/6, 4x4 aggregates, the threshold from kappa = 50
     # (level-0 aggregates from one pass of standard aggregation, chosen by each solver itself)

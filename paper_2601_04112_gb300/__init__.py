@@ -59,7 +59,8 @@ class Params(ctypes.Structure):
                 ("coarse_overlap", ctypes.c_int), ("coarse_refine", ctypes.c_int),
                 ("pdl", ctypes.c_int), ("dense_tail", ctypes.c_int), ("ell", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("cycle", ctypes.c_int),
-                ("kappa", ctypes.c_double), ("agg_passes", ctypes.c_int), ("schur_gram", ctypes.c_int)]
+                ("kappa", ctypes.c_double), ("agg_passes", ctypes.c_int), ("schur_gram", ctypes.c_int),
+                ("batch_cols", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -258,12 +259,12 @@ class Hierarchy:
         return cls(prob.rowptr, prob.col, prob.val, prob.n, D1=prob.D1, agg=prob.agg, overlap=overlap, **kw)
 
     def save(self, path):
-        """Write the setup inputs, parameters and kernel choices (amgdd_hierarchy_save)."""
+        """Write the setup inputs, parameters, kernel choices and every level's computed operators (amgdd_hierarchy_save)."""
         _check(self._lib.amgdd_hierarchy_save(self._h, str(path).encode()))
 
     @classmethod
     def load(cls, path, stream=None):
-        """Rebuild a saved hierarchy with its kernel choices replayed (amgdd_hierarchy_load)."""
+        """Restore a saved hierarchy: its levels as setup computed them, kernel choices replayed (amgdd_hierarchy_load)."""
         lib = load_library()
         h = ctypes.c_void_p()
         import torch
@@ -387,8 +388,9 @@ class Hierarchy:
         _check(self._lib.amgdd_bytes_model(self._h, ctypes.byref(v), ctypes.byref(a)))
         return v.value, a.value
 
-    def device_bytes(self, with_batched: bool = False) -> int:
-        return int(self._lib.amgdd_device_bytes(self._h, int(bool(with_batched))))
+    def device_bytes(self, with_batched=False) -> int:
+        """Device bytes held; with_batched: True for a batch of the hierarchy's batch_cols, or a column count."""
+        return int(self._lib.amgdd_device_bytes(self._h, int(with_batched)))
 
 
 class Server:

@@ -16,7 +16,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SOURCES = ["csrc/api.cu", "csrc/cycle_kernels.cu", "csrc/multi_kernels.cu", "csrc/setup_kernels.cu",
-           "csrc/server.cu", "csrc/structure.cpp"]
+           "csrc/aggregate_kernels.cu", "csrc/server.cu", "csrc/structure.cpp"]
 HEADERS = ["csrc/internal.h", "csrc/structure.h"]
 LIB = os.path.join(HERE, "libamgdd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

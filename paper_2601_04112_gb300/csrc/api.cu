@@ -509,7 +509,7 @@ int build_apply(Level& L, cudaStream_t s) {
 // row touches whole blocks of coarse dofs (the columns of one Z_i), so a
 // block's rows share the support in_b and A(D_b, in_b) is dense.  Used when
 // it moves no more bytes than the matrix-free form.
-int build_blockrows(Level& L, cudaStream_t s) {
+int build_blockrows(Level& L, cudaStream_t s, const std::vector<double>* saved = nullptr) {
   Supports S;
   S.ptr = L.g_ptr;
   S.idx = L.g_idx;
@@ -575,7 +575,38 @@ int build_blockrows(Level& L, cudaStream_t s) {
   const double mf_bytes = apply_bytes(L, 4);
   L.blk_mb = blk_bytes / 1e6;
   L.mf_mb = mf_bytes / 1e6;
-  if (nblk * 2 > n) return AMGDD_OK;  // (near-)singleton blocks: nothing to gain
+  if (nblk * 2 > n) {  // (near-)singleton blocks: nothing to gain
+    if (saved && !saved->empty()) {
+      set_error("saved hierarchy: block rows stored for a level that has none");
+      return AMGDD_ERR_INVALID_ARG;
+    }
+    return AMGDD_OK;
+  }
+  if (saved) {  // a loaded hierarchy: the stored FP64 block rows, or none (the row groups won at setup)
+    if (saved->empty()) return AMGDD_OK;
+    if ((int64_t)saved->size() != mat) {
+      set_error("saved hierarchy: %zu block-row entries, the structure has %lld", saved->size(), (long long)mat);
+      return AMGDD_ERR_INVALID_ARG;
+    }
+    DBuf<int32_t> dnr, dnc;
+    DBuf<int64_t> dmoff;
+    AMGDD_TRY(dnr.upload(nr, s));
+    AMGDD_TRY(dnc.upload(nc, s));
+    AMGDD_TRY(dmoff.upload(moff, s));
+    AMGDD_TRY(L.A64.upload(*saved, s));
+    AMGDD_TRY(L.At64.alloc(mat));
+    AMGDD_TRY(L.A32.alloc(mat));
+    AMGDD_TRY(L.At32.alloc(mat));
+    AMGDD_TRY(launch_block_copies(nblk, dnr.p, dnc.p, dmoff.p, L.A64.p, L.A32.p, L.At64.p, L.At32.p, s));
+    AMGDD_TRY(L.d_blk_in.upload(blk_in, s));
+    std::vector<int32_t> io(n);
+    std::iota(io.begin(), io.end(), 0);
+    AMGDD_TRY(L.d_blk_out.upload(io, s));
+    AMGDD_TRY(build_seg(L.ablk, nr, nc, moff, ioff, ooff, L.d_blk_in.p, L.d_blk_out.p, s));
+    AMGDD_CUDA(cudaStreamSynchronize(s));
+    L.has_blk = true;
+    return AMGDD_OK;
+  }
   DBuf<int32_t> dnr, dnc, dpgrp, dpp0, dmap;
   DBuf<int64_t> dmoff, dpptr, dpmap;
   AMGDD_TRY(dnr.upload(nr, s));
@@ -953,6 +984,21 @@ int tune_level_A(Level& L, int lvl, cudaStream_t s) {
 }
 
 }  // namespace
+
+// What setup computed for one level, as a saved hierarchy stores it: the
+// structure (row groups of G_l, aggregates, Omega lists, k_i and offsets)
+// and the FP64 matrices (compressed rows R_g, smoother rows W_i, rows of A
+// over Omega_i, spectra, bases Z_i, the additive form's A_i^{-1}, coarse
+// block rows, the coarsest inverse).  The FP32 and transposed copies are
+// derived again on load.
+struct LevelSnap {
+  int64_t n = 0, nnzA = 0;
+  int32_t nagg = 0, coarsest = 0, schur_rows = 0, n_color = 0, n_mult = 0;
+  double thresh = 0.0, inv_err = 0.0;
+  std::vector<int64_t> g_ptr, h_off, om_ptr, z_off, mu_off, col0, wf_off;
+  std::vector<int32_t> g_idx, g_rank, agg, om_idx, nomega, k;
+  std::vector<double> R64, W64, Aw64, mu, Z64, Wf64, A64;
+};
 }  // namespace amgdd
 
 using namespace amgdd;
@@ -1000,17 +1046,27 @@ struct amgdd_hierarchy {
   int dense_from[2] = {0, 0};
   double dense_us[2][16] = {};  // setup-time V-cycle timings by dense level (0 = none)
   DBuf<unsigned> bar;
-  // batched right-hand sides: CG vectors (n x kMaxRhs, interleaved), K
-  // states, graphs per precision and K in {2, 4, 8}; allocated at the first
-  // batched solve
+  // batched right-hand sides: CG vectors (n x cap, interleaved), cap
+  // states, graphs per precision and K in {2, 4, 8, 16, 32}; allocated at
+  // the first batched solve for its width and grown (graphs rebuilt) when a
+  // wider batch comes
   struct Multi {
     bool ready = false;
+    int cap = 0;
     DBuf<double> x, r, z, zold, p, q, b, stage, partials;
     DBuf<PcgState> st;
     DBuf<int> grp;
     PcgState* st_host = nullptr;
-    cudaGraphExec_t ginit[2][3] = {}, gloop[2][3] = {};
-    int64_t ginit_kernels[2][3] = {}, gloop_kernels[2][3] = {};
+    cudaGraphExec_t ginit[2][5] = {}, gloop[2][5] = {};
+    int64_t ginit_kernels[2][5] = {}, gloop_kernels[2][5] = {};
+    void drop_graphs() {
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 5; ++j) {
+          if (ginit[i][j]) cudaGraphExecDestroy(ginit[i][j]);
+          if (gloop[i][j]) cudaGraphExecDestroy(gloop[i][j]);
+          ginit[i][j] = gloop[i][j] = nullptr;
+        }
+    }
   } mw;
   ~amgdd_hierarchy() {
     for (int i = 0; i < 2; ++i) {
@@ -1018,11 +1074,7 @@ struct amgdd_hierarchy {
       if (gloop[i]) cudaGraphExecDestroy(gloop[i]);
     }
     if (st_host) cudaFreeHost(st_host);
-    for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 3; ++j) {
-        if (mw.ginit[i][j]) cudaGraphExecDestroy(mw.ginit[i][j]);
-        if (mw.gloop[i][j]) cudaGraphExecDestroy(mw.gloop[i][j]);
-      }
+    mw.drop_graphs();
     if (mw.st_host) cudaFreeHost(mw.st_host);
     for (auto& e : join)
       if (e) cudaEventDestroy(e);
@@ -1661,7 +1713,17 @@ int build_next(amgdd_hierarchy& h, Level& L, Level& N, cudaStream_t s) {
   }
   std::vector<int32_t> bagg;
   int nn = 0;
-  block_aggregation(nlive, ltptr, ltids, bagg, nn);
+  {
+    DBuf<int64_t> d_lptr;
+    DBuf<int32_t> d_lids, d_bagg;
+    AMGDD_TRY(d_lptr.upload(ltptr, s));
+    AMGDD_TRY(d_lids.upload(ltids, s));
+    AMGDD_TRY(d_bagg.alloc(std::max(nlive, 1)));
+    int64_t nb = 0;
+    AMGDD_TRY(device_hyper_aggregation(nlive, (int64_t)ltptr.size() - 1, d_lptr.p, d_lids.p, d_bagg.p, &nb, s));
+    AMGDD_TRY(download(bagg, d_bagg.p, (size_t)nlive, s));
+    nn = (int)nb;
+  }
   N.agg.assign(N.n, 0);
   for (int a = 0; a < L.nagg; ++a)
     for (int64_t c = L.col0[a]; c < L.col0[a + 1]; ++c) N.agg[c] = bagg[live_id[a]];
@@ -1768,6 +1830,115 @@ int build_coarsest(amgdd_hierarchy& h, Level& L, cudaStream_t s) {
     const bool keep = h.prm.coarse_refine == 2 || (h.prm.coarse_refine == 1 && L.inv_err > 1e-13);
     if (!keep && &L != h.lv[0].get()) L.Aw64.release();
   }
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  return AMGDD_OK;
+}
+
+// ---- loaded hierarchies: what setup computed, restored from a snapshot ----
+// Uploads the FP64 blocks (rows[b] x cols[b] at off[b]) and derives their
+// FP32 rounding and transposes.
+int restore_blocks(const std::vector<double>& src, const std::vector<int32_t>& rows, const std::vector<int32_t>& cols,
+                   const std::vector<int64_t>& off, DBuf<double>& m64, DBuf<float>& m32, DBuf<double>& t64,
+                   DBuf<float>& t32, cudaStream_t s) {
+  AMGDD_TRY(m64.upload(src, s));
+  AMGDD_TRY(m32.alloc(src.size()));
+  AMGDD_TRY(t64.alloc(src.size()));
+  AMGDD_TRY(t32.alloc(src.size()));
+  DBuf<int32_t> dr, dc;
+  DBuf<int64_t> doff;
+  AMGDD_TRY(dr.upload(rows, s));
+  AMGDD_TRY(dc.upload(cols, s));
+  AMGDD_TRY(doff.upload(off, s));
+  AMGDD_TRY(launch_block_copies((int)rows.size(), dr.p, dc.p, doff.p, m64.p, m32.p, t64.p, t32.p, s));
+  AMGDD_CUDA(cudaStreamSynchronize(s));
+  return AMGDD_OK;
+}
+
+// The compressed rows of G_l (ranks and FP64 rows; FP32 rows derived).
+int restore_rows(Level& L, const LevelSnap& S, cudaStream_t s) {
+  if (S.R64.empty()) return AMGDD_OK;  // a coarsest level below level 0 keeps no rows
+  L.g_rank = S.g_rank;
+  AMGDD_TRY(L.d_rank.upload(L.g_rank, s));
+  AMGDD_TRY(L.d_R64.upload(S.R64, s));
+  AMGDD_TRY(L.d_R32.alloc(S.R64.size()));
+  AMGDD_TRY(launch_cast(L.d_R64.p, false, L.d_R32.p, true, (int64_t)S.R64.size(), nullptr, s));
+  L.rows_ready = true;
+  return AMGDD_OK;
+}
+
+// The local problems of one level (build_level's results).
+int restore_level(amgdd_hierarchy& h, Level& L, const LevelSnap& S, cudaStream_t s) {
+  h.nnzA.push_back(S.nnzA);
+  L.agg = S.agg;
+  L.nagg = S.nagg;
+  L.om_ptr = S.om_ptr;
+  L.om_idx = S.om_idx;
+  L.nomega = S.nomega;
+  L.thresh = S.thresh;
+  L.n_color = S.n_color;
+  L.n_mult = S.n_mult;
+  L.k = S.k;
+  L.col0 = S.col0;
+  L.z_off = S.z_off;
+  L.mu_off = S.mu_off;
+  L.wf_off = S.wf_off;
+  L.schur_rows = S.schur_rows != 0;
+  const int nagg = L.nagg;
+  std::vector<int32_t> rows(nagg), cols(nagg);
+  std::vector<int64_t> off(nagg);
+  int64_t w = 0;
+  for (int i = 0; i < nagg; ++i) {
+    rows[i] = L.nomega[i];
+    cols[i] = (int32_t)(L.om_ptr[i + 1] - L.om_ptr[i]);
+    off[i] = w;
+    w += (int64_t)rows[i] * cols[i];
+  }
+  AMGDD_TRY(restore_blocks(S.W64, rows, cols, off, L.W64, L.W32, L.Wt64, L.Wt32, s));
+  if (!S.Aw64.empty()) AMGDD_TRY(restore_blocks(S.Aw64, rows, cols, off, L.Aw64, L.Aw32, L.AwT64, L.AwT32, s));
+  AMGDD_TRY(L.mu.upload(S.mu, s));
+  for (int i = 0; i < nagg; ++i) {
+    cols[i] = L.k[i];
+    off[i] = L.z_off[i];
+  }
+  AMGDD_TRY(restore_blocks(S.Z64, rows, cols, off, L.Z64, L.Z32, L.Zt64, L.Zt32, s));
+  if (!S.Wf64.empty()) {
+    for (int i = 0; i < nagg; ++i) {
+      rows[i] = cols[i] = (int32_t)(L.om_ptr[i + 1] - L.om_ptr[i]);
+      off[i] = L.wf_off[i];
+    }
+    AMGDD_TRY(restore_blocks(S.Wf64, rows, cols, off, L.Wf64, L.Wf32, L.Wft64, L.Wft32, s));
+  }
+  return AMGDD_OK;
+}
+
+// The structure of level l+1 (build_next's results; its rows come with the
+// level's own snapshot).
+int restore_next(Level& N, const LevelSnap& S, cudaStream_t s) {
+  N.n = S.n;
+  N.g_ptr = S.g_ptr;
+  N.g_idx = S.g_idx;
+  N.h_off = S.h_off;
+  AMGDD_TRY(N.d_g_ptr.upload(N.g_ptr, s));
+  AMGDD_TRY(N.d_g_idx.upload(N.g_idx, s));
+  AMGDD_TRY(N.d_h_off.upload(N.h_off, s));
+  N.agg = S.agg;
+  N.nagg = S.nagg;
+  return AMGDD_OK;
+}
+
+// The coarsest level (build_coarsest's results).
+int restore_coarsest(amgdd_hierarchy& h, Level& L, const LevelSnap& S, cudaStream_t s) {
+  const int64_t m = L.n;
+  L.coarsest = true;
+  h.nnzA.push_back(S.nnzA);
+  const std::vector<int32_t> rows{(int32_t)m};
+  const std::vector<int64_t> off{0};
+  AMGDD_TRY(restore_blocks(S.W64, rows, rows, off, L.W64, L.W32, L.Wt64, L.Wt32, s));
+  if (!S.Aw64.empty()) AMGDD_TRY(L.Aw64.upload(S.Aw64, s));
+  L.inv_err = S.inv_err;
+  std::vector<int32_t> nr{(int32_t)m}, nc{(int32_t)m};
+  std::vector<int64_t> moff{0}, ioff{0}, ooff{0};
+  AMGDD_TRY(build_seg(L.ras, nr, nc, moff, ioff, ooff, h.iota.p, h.iota.p, s));
   AMGDD_CUDA(cudaStreamSynchronize(s));
   return AMGDD_OK;
 }
@@ -2741,24 +2912,44 @@ static int take_err_word(amgdd_hierarchy& h, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Batched right-hand sides: K in {2, 4, 8} independent CGs that share every
-// V-cycle and A-apply launch (multi_kernels.cu).
-constexpr int kMaxRhs = 8;
-static int kidx(int K) { return K == 2 ? 0 : (K == 4 ? 1 : 2); }
+// Batched right-hand sides: K in {2, 4, 8, 16, 32} independent CGs that
+// share every V-cycle and A-apply launch (multi_kernels.cu).
+constexpr int kMaxRhs = 32;
+static int kidx(int K) { return K == 2 ? 0 : (K == 4 ? 1 : (K == 8 ? 2 : (K == 16 ? 3 : 4))); }
+static int kclass(int g) { return g <= 2 ? 2 : (g <= 4 ? 4 : (g <= 8 ? 8 : (g <= 16 ? 16 : 32))); }
 
-static int ensure_multi(amgdd_hierarchy& h) {
+// Device bytes of the batched-solve workspace for `cap` columns (allocated
+// or not): the eight CG vectors, the dot partials and states, and per level
+// three FP64 and three FP32 vectors (plus the stored RAS-T products of the
+// deterministic form).
+static int64_t multi_bytes_estimate(const amgdd_hierarchy& h, int cap) {
+  int64_t b = (int64_t)8 * h.n * cap * 8 + (int64_t)kDotBlocks * 2 * cap * 8 + (int64_t)cap * sizeof(PcgState) + 16;
+  for (const auto& L : h.lv) {
+    b += L->n * cap * (3 * 8 + 3 * 4);
+    if (L->yd64.p) b += (int64_t)L->om_ptr.back() * cap * (8 + 4);
+  }
+  return b;
+}
+
+static int ensure_multi(amgdd_hierarchy& h, int K) {
   auto& M = h.mw;
-  if (M.ready) return AMGDD_OK;
-  const int64_t bytes0 = g_alloc_bytes;
-  const int64_t nk = h.n * kMaxRhs;
+  if (M.ready && M.cap >= K) return AMGDD_OK;
+  // (re)allocate for K columns: the captured graphs hold the old pointers
+  M.drop_graphs();
+  M.ready = false;
+  if (M.st_host) {
+    cudaFreeHost(M.st_host);
+    M.st_host = nullptr;
+  }
+  const int64_t nk = h.n * K;
   for (auto* v : {&M.x, &M.r, &M.z, &M.zold, &M.p, &M.q, &M.b, &M.stage}) AMGDD_TRY(v->alloc(nk));
-  AMGDD_TRY(M.partials.alloc((int64_t)kDotBlocks * 2 * kMaxRhs));
-  AMGDD_TRY(M.st.alloc(kMaxRhs));
+  AMGDD_TRY(M.partials.alloc((int64_t)kDotBlocks * 2 * K));
+  AMGDD_TRY(M.st.alloc(K));
   AMGDD_TRY(M.grp.alloc(4));
-  AMGDD_CUDA(cudaMallocHost((void**)&M.st_host, kMaxRhs * sizeof(PcgState)));
+  AMGDD_CUDA(cudaMallocHost((void**)&M.st_host, K * sizeof(PcgState)));
   for (auto& Lp : h.lv) {
     Level& L = *Lp;
-    const int64_t lk = L.n * kMaxRhs;
+    const int64_t lk = L.n * K;
     AMGDD_TRY(L.mr64.alloc(lk));
     AMGDD_TRY(L.mx64.alloc(lk));
     AMGDD_TRY(L.ms64.alloc(lk));
@@ -2766,20 +2957,14 @@ static int ensure_multi(amgdd_hierarchy& h) {
     AMGDD_TRY(L.mx32.alloc(lk));
     AMGDD_TRY(L.ms32.alloc(lk));
     if (L.yd64.p) {
-      AMGDD_TRY(L.myd64.alloc((size_t)L.om_ptr.back() * kMaxRhs));
-      AMGDD_TRY(L.myd32.alloc((size_t)L.om_ptr.back() * kMaxRhs));
+      AMGDD_TRY(L.myd64.alloc((size_t)L.om_ptr.back() * K));
+      AMGDD_TRY(L.myd32.alloc((size_t)L.om_ptr.back() * K));
     }
   }
+  M.cap = K;
   M.ready = true;
-  h.multi_bytes = g_alloc_bytes - bytes0;
+  h.multi_bytes = multi_bytes_estimate(h, K);
   return AMGDD_OK;
-}
-
-// Device bytes of the batched-solve workspace (allocated or not).
-static int64_t multi_bytes_estimate(const amgdd_hierarchy& h) {
-  int64_t b = (int64_t)8 * h.n * kMaxRhs * 8 + (int64_t)kDotBlocks * 2 * kMaxRhs * 8;
-  for (const auto& L : h.lv) b += L->n * kMaxRhs * (3 * 8 + 3 * 4);
-  return b;
 }
 
 // s = r - A x for K columns: block rows where stored, else the rows omega_i
@@ -2929,7 +3114,7 @@ static int solve_group(amgdd_hierarchy& h, const double* b, bool bdev, int ncols
                        bool xdev, cudaStream_t s, amgdd_info* info) {
   auto& M = h.mw;
   const int64_t n = h.n;
-  AMGDD_TRY(ensure_multi(h));
+  AMGDD_TRY(ensure_multi(h, K));
   cudaEvent_t e0, e1;
   AMGDD_CUDA(cudaEventCreate(&e0));
   AMGDD_CUDA(cudaEventCreate(&e1));
@@ -3047,7 +3232,10 @@ static int solve_group(amgdd_hierarchy& h, const double* b, bool bdev, int ncols
 
 // Binary helpers of the saved-hierarchy format.
 namespace {
-constexpr char kSaveMagic[8] = {'A', 'M', 'G', 'D', 'D', 'H', 'v', '1'};
+// v1: setup inputs, parameters and kernel choices; v2 adds the level
+// snapshots (what setup computed), so loading skips the local problems.
+constexpr char kSaveMagicV1[8] = {'A', 'M', 'G', 'D', 'D', 'H', 'v', '1'};
+constexpr char kSaveMagic[8] = {'A', 'M', 'G', 'D', 'D', 'H', 'v', '2'};
 
 template <class T>
 bool put_vec(FILE* f, const std::vector<T>& v) {
@@ -3060,6 +3248,107 @@ bool get_vec(FILE* f, std::vector<T>& v, uint64_t max_count) {
   if (std::fread(&c, sizeof c, 1, f) != 1 || c > max_count) return false;
   v.resize(c);
   return c == 0 || std::fread(v.data(), sizeof(T), c, f) == c;
+}
+
+struct SnapScalars {
+  int64_t n, nnzA;
+  int32_t nagg, coarsest, schur_rows, n_color, n_mult, pad;
+  double thresh, inv_err;
+};
+
+bool put_snap(FILE* f, const LevelSnap& S) {
+  const SnapScalars c{S.n, S.nnzA, S.nagg, S.coarsest, S.schur_rows, S.n_color, S.n_mult, 0, S.thresh, S.inv_err};
+  return std::fwrite(&c, sizeof c, 1, f) == 1 && put_vec(f, S.g_ptr) && put_vec(f, S.h_off) &&
+         put_vec(f, S.om_ptr) && put_vec(f, S.z_off) && put_vec(f, S.mu_off) && put_vec(f, S.col0) &&
+         put_vec(f, S.wf_off) && put_vec(f, S.g_idx) && put_vec(f, S.g_rank) && put_vec(f, S.agg) &&
+         put_vec(f, S.om_idx) && put_vec(f, S.nomega) && put_vec(f, S.k) && put_vec(f, S.R64) && put_vec(f, S.W64) &&
+         put_vec(f, S.Aw64) && put_vec(f, S.mu) && put_vec(f, S.Z64) && put_vec(f, S.Wf64) && put_vec(f, S.A64);
+}
+
+bool get_snap(FILE* f, LevelSnap& S, uint64_t mx) {
+  SnapScalars c{};
+  if (std::fread(&c, sizeof c, 1, f) != 1) return false;
+  S.n = c.n;
+  S.nnzA = c.nnzA;
+  S.nagg = c.nagg;
+  S.coarsest = c.coarsest;
+  S.schur_rows = c.schur_rows;
+  S.n_color = c.n_color;
+  S.n_mult = c.n_mult;
+  S.thresh = c.thresh;
+  S.inv_err = c.inv_err;
+  return get_vec(f, S.g_ptr, mx) && get_vec(f, S.h_off, mx) && get_vec(f, S.om_ptr, mx) && get_vec(f, S.z_off, mx) &&
+         get_vec(f, S.mu_off, mx) && get_vec(f, S.col0, mx) && get_vec(f, S.wf_off, mx) && get_vec(f, S.g_idx, mx) &&
+         get_vec(f, S.g_rank, mx) && get_vec(f, S.agg, mx) && get_vec(f, S.om_idx, mx) && get_vec(f, S.nomega, mx) &&
+         get_vec(f, S.k, mx) && get_vec(f, S.R64, mx) && get_vec(f, S.W64, mx) && get_vec(f, S.Aw64, mx) &&
+         get_vec(f, S.mu, mx) && get_vec(f, S.Z64, mx) && get_vec(f, S.Wf64, mx) && get_vec(f, S.A64, mx);
+}
+
+// Every size and index of the snapshots consistent (they drive the device
+// index lists of the loaded hierarchy): level sizes chain through the
+// coarse column counts, supports and Omega lists stay inside their level,
+// offsets are the prefix sums of the block sizes, and each stored matrix has
+// its blocks' size.
+bool snaps_valid(const std::vector<LevelSnap>& v, int64_t n0) {
+  if (v.empty()) return false;
+  for (size_t l = 0; l < v.size(); ++l) {
+    const LevelSnap& S = v[l];
+    const int64_t n = S.n;
+    if (n != (l == 0 ? n0 : v[l - 1].col0.empty() ? -1 : v[l - 1].col0.back()) || n <= 0) return false;
+    if (S.coarsest != (l + 1 == v.size() ? 1 : 0)) return false;
+    const int64_t ng = (int64_t)S.g_ptr.size() - 1;
+    if (ng < 0 || S.g_ptr[0] != 0 || S.h_off.size() != S.g_ptr.size() || S.h_off[0] != 0) return false;
+    for (int64_t g = 0; g < ng; ++g) {
+      const int64_t len = S.g_ptr[g + 1] - S.g_ptr[g];
+      if (len < 0 || S.h_off[g + 1] - S.h_off[g] != len * len) return false;
+    }
+    if (S.g_ptr.back() != (int64_t)S.g_idx.size()) return false;
+    for (int32_t c : S.g_idx)
+      if (c < 0 || c >= n) return false;
+    if (!S.R64.empty()) {
+      if ((int64_t)S.R64.size() != S.h_off.back() || (int64_t)S.g_rank.size() != ng) return false;
+      for (int64_t g = 0; g < ng; ++g)
+        if (S.g_rank[g] < 0 || S.g_rank[g] > S.g_ptr[g + 1] - S.g_ptr[g]) return false;
+    } else if (!S.coarsest || l == 0) {
+      return false;  // every level that applies its G keeps the rows
+    }
+    if (S.coarsest) {
+      if ((int64_t)S.W64.size() != n * n || !(S.Aw64.empty() || (int64_t)S.Aw64.size() == n * n)) return false;
+      continue;
+    }
+    const int64_t na = S.nagg;
+    if (na < 1 || (int64_t)S.agg.size() != n || (int64_t)S.om_ptr.size() != na + 1 ||
+        (int64_t)S.nomega.size() != na || (int64_t)S.k.size() != na || (int64_t)S.col0.size() != na + 1 ||
+        (int64_t)S.z_off.size() != na + 1 || (int64_t)S.mu_off.size() != na + 1)
+      return false;
+    for (int32_t a : S.agg)
+      if (a < 0 || a >= na) return false;
+    if (S.om_ptr[0] != 0 || S.om_ptr.back() != (int64_t)S.om_idx.size()) return false;
+    for (int32_t c : S.om_idx)
+      if (c < 0 || c >= n) return false;
+    int64_t w = 0, wf = 0;
+    if (S.col0[0] != 0 || S.z_off[0] != 0 || S.mu_off[0] != 0) return false;
+    for (int64_t i = 0; i < na; ++i) {
+      const int64_t m = S.om_ptr[i + 1] - S.om_ptr[i], no = S.nomega[i], k = S.k[i];
+      if (m < 1 || no < 1 || no > m || k < 0 || k > no) return false;
+      if (S.col0[i + 1] != S.col0[i] + k || S.z_off[i + 1] != S.z_off[i] + no * k ||
+          S.mu_off[i + 1] != S.mu_off[i] + no)
+        return false;
+      w += no * m;
+      wf += m * m;
+    }
+    if ((int64_t)S.W64.size() != w || !(S.Aw64.empty() || (int64_t)S.Aw64.size() == w) ||
+        (int64_t)S.mu.size() != S.mu_off.back() || (int64_t)S.Z64.size() != S.z_off.back())
+      return false;
+    if (!S.Wf64.empty()) {
+      if ((int64_t)S.wf_off.size() != na + 1 || S.wf_off[0] != 0 || (int64_t)S.Wf64.size() != wf) return false;
+      for (int64_t i = 0; i < na; ++i) {
+        const int64_t m = S.om_ptr[i + 1] - S.om_ptr[i];
+        if (S.wf_off[i + 1] != S.wf_off[i] + m * m) return false;
+      }
+    }
+  }
+  return true;
 }
 }  // namespace
 
@@ -3086,6 +3375,7 @@ amgdd_params amgdd_params_default(void) {
   p.coarse_refine = 1;
   p.pdl = 0;
   p.agg_passes = 1;
+  p.batch_cols = 8;
   return p;
 }
 
@@ -3147,8 +3437,11 @@ static bool bad_header(const amgdd_csr* G) {
 
 // Level-0 aggregates by `passes` passes of standard aggregation on the graph
 // of A (rows of G as hyperedges; consecutive rows with one support counted once).
-static void aggregate_rows(const std::vector<int64_t>& rowptr, const std::vector<int32_t>& col, int64_t m,
-                           int64_t n, int passes, std::vector<int32_t>& agg, int64_t& nagg) {
+// Level-0 aggregates of the graph of A = G^T G (rows of G as hyperedges,
+// consecutive rows with one support merged) by `passes` passes of standard
+// aggregation on the device; d_agg (n, device) receives the ids.
+static int aggregate_rows(const std::vector<int64_t>& rowptr, const std::vector<int32_t>& col, int64_t m, int64_t n,
+                          int passes, int32_t* d_agg, int64_t& nagg, cudaStream_t s, int64_t* rounds = nullptr) {
   Supports S;
   S.ptr.assign(1, 0);
   S.idx.reserve(col.size());
@@ -3163,12 +3456,17 @@ static void aggregate_rows(const std::vector<int64_t>& rowptr, const std::vector
     S.ptr.push_back((int64_t)S.idx.size());
     last = r;
   }
-  standard_aggregation(n, S, passes, agg, nagg);
+  DBuf<int64_t> eptr;
+  DBuf<int32_t> eidx;
+  AMGDD_TRY(eptr.upload(S.ptr, s));
+  AMGDD_TRY(eidx.upload(S.idx, s));
+  return device_standard_aggregation(n, S.size(), eptr.p, eidx.p, passes, d_agg, &nagg, s, rounds);
 }
 
 static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, int overlap,
                       const amgdd_params* params, void* stream, amgdd_hierarchy** out,
-                      const std::vector<std::pair<std::string, double>>* preset = nullptr) {
+                      const std::vector<std::pair<std::string, double>>* preset = nullptr,
+                      const std::vector<LevelSnap>* snap = nullptr) {
   if (out == nullptr || G == nullptr) {
     set_error("amgdd_setup: G and out must not be NULL");
     return AMGDD_ERR_INVALID_ARG;
@@ -3178,6 +3476,8 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   if (prm.L_max < 1 || prm.n_cmin < 1 || prm.n_cmin > 8 || prm.max_iter < 1 || overlap < 1 ||
       (prm.precision != AMGDD_FP64 && prm.precision != AMGDD_MIXED32 && prm.precision != AMGDD_MIXED16) ||
       prm.schur_gram < 0 || prm.schur_gram > 2 ||
+      (prm.batch_cols != 2 && prm.batch_cols != 4 && prm.batch_cols != 8 && prm.batch_cols != 16 &&
+       prm.batch_cols != 32) ||
       prm.check_every < 1 || prm.n_coarse < 1 ||
       prm.coarse_overlap < 0 || prm.cycle < 0 || prm.cycle > 1 || !(prm.kappa >= 0) ||
       (agg == nullptr && prm.agg_passes < 1) ||
@@ -3210,9 +3510,12 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   if (agg) AMGDD_TRY(fetch_any(aggh, agg, (size_t)n, is_device_ptr(agg), s));
   if (D1) AMGDD_TRY(fetch_any(d1, D1, (size_t)n, is_device_ptr(D1), s));
   AMGDD_TRY(check_pattern("amgdd_setup", rowptr, col, m, n, nnz));
-  if (!agg) {  // level-0 aggregates from the graph of A (Section 3.3)
+  if (!agg) {  // level-0 aggregates from the graph of A (Section 3.3), on the device
     int64_t na = 0;
-    aggregate_rows(rowptr, col, m, n, prm.agg_passes, aggh, na);
+    DBuf<int32_t> dagg;
+    AMGDD_TRY(dagg.alloc(std::max<int64_t>(n, 1)));
+    AMGDD_TRY(aggregate_rows(rowptr, col, m, n, prm.agg_passes, dagg.p, na, s));
+    AMGDD_TRY(download(aggh, dagg.p, (size_t)n, s));
   }
   for (double v : val)
     if (!std::isfinite(v)) {
@@ -3260,10 +3563,8 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     tctx.sig = sig + buf;
   }
   tctx.load();
-  if (preset) {  // choices saved with a hierarchy: replayed, not re-timed
+  if (preset)  // choices saved with a hierarchy: replayed, not re-timed (tune = 0 keeps its fixed defaults)
     for (const auto& kv : *preset) tctx.kv[kv.first] = kv.second;
-    tctx.on = true;
-  }
   struct TuneScope {
     explicit TuneScope(TuneCtx* t) { g_tune = t; }
     ~TuneScope() { g_tune = nullptr; }
@@ -3307,8 +3608,12 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   AMGDD_TRY(L0->d_g_ptr.upload(L0->g_ptr, s));
   AMGDD_TRY(L0->d_g_idx.upload(L0->g_idx, s));
   AMGDD_TRY(L0->d_h_off.upload(L0->h_off, s));
-  AMGDD_TRY(L0->d_H.alloc(std::max<int64_t>(L0->h_off[ng0], 1)));
-  {
+  if (snap && ((*snap)[0].g_ptr != L0->g_ptr || (*snap)[0].g_idx != L0->g_idx)) {
+    set_error("saved hierarchy: level-0 row groups differ from those of the saved G");
+    return AMGDD_ERR_INVALID_ARG;
+  }
+  if (!snap) {  // the Grams of level 0 (a loaded hierarchy has its rows already)
+    AMGDD_TRY(L0->d_H.alloc(std::max<int64_t>(L0->h_off[ng0], 1)));
     DBuf<int64_t> d_rowptr, d_r0, d_r1;
     DBuf<double> d_val, d_d1;
     AMGDD_TRY(d_rowptr.upload(rowptr, s));
@@ -3334,6 +3639,13 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
   for (;;) {
     Level& L = *H->lv[lvl];
     const bool coarsest = !(lvl < prm.L_max - 1 && L.n > prm.n_coarse);
+    if (snap) {
+      if (lvl >= (int)snap->size() || ((*snap)[lvl].coarsest != 0) != coarsest) {
+        set_error("saved hierarchy: level %d does not match the saved parameters", lvl);
+        return AMGDD_ERR_INVALID_ARG;
+      }
+      AMGDD_TRY(restore_rows(L, (*snap)[lvl], s));
+    }
     if (!coarsest || lvl == 0) {
       Phase ph(6, "compress", s);
       AMGDD_TRY(compress(L, s));
@@ -3341,11 +3653,12 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     AMGDD_TRY(alloc_vectors(L));
     if (coarsest) {
       Phase ph(8, "coarsest", s);
-      AMGDD_TRY(build_coarsest(*H, L, s));
+      AMGDD_TRY(snap ? restore_coarsest(*H, L, (*snap)[lvl], s) : build_coarsest(*H, L, s));
       AMGDD_TRY(tune_level_plans(L, lvl, 0, s));
       break;
     }
-    AMGDD_TRY(build_level(*H, L, lvl, lvl == 0 ? aggh.data() : nullptr, s));
+    AMGDD_TRY(snap ? restore_level(*H, L, (*snap)[lvl], s)
+                   : build_level(*H, L, lvl, lvl == 0 ? aggh.data() : nullptr, s));
     if (L.col0.back() == 0) {  // no local eigenvector passed the threshold anywhere on this level
       set_error("level %d produced an empty coarse space", lvl);
       return AMGDD_ERR_INVALID_ARG;
@@ -3353,7 +3666,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     AMGDD_TRY(build_plans(*H, L, L.d_om_idx, s));
     if (lvl > 0) {
       Phase ph(9, "block rows", s);
-      AMGDD_TRY(build_blockrows(L, s));
+      AMGDD_TRY(build_blockrows(L, s, snap ? &(*snap)[lvl].A64 : nullptr));
     }
     {
       Phase ph(10, "tune", s);
@@ -3374,7 +3687,7 @@ static int setup_impl(const amgdd_csr* G, const double* D1, const int32_t* agg, 
     std::unique_ptr<Level> N(new Level());
     {
       Phase ph(7, "next level", s);
-      AMGDD_TRY(build_next(*H, L, *N, s));
+      AMGDD_TRY(snap ? restore_next(*N, (*snap)[lvl + 1], s) : build_next(*H, L, *N, s));
     }
     for (int i = 0; i < 16; ++i) {
       H->phase_ms[i] += g_timer.acc[i];
@@ -3453,18 +3766,17 @@ int amgdd_aggregate(const amgdd_csr* G, int passes, void* stream, int32_t* agg, 
   cudaStream_t s = (cudaStream_t)stream;
   const bool gdev = G->mem == AMGDD_DEVICE;
   std::vector<int64_t> rowptr;
-  std::vector<int32_t> col, a;
+  std::vector<int32_t> col;
   AMGDD_TRY(fetch_any(rowptr, G->rowptr, (size_t)G->m + 1, gdev, s));
   AMGDD_TRY(fetch_any(col, G->col, (size_t)G->nnz, gdev, s));
   AMGDD_TRY(check_pattern("amgdd_aggregate", rowptr, col, G->m, G->n, G->nnz));
   int64_t na = 0;
-  aggregate_rows(rowptr, col, G->m, G->n, passes, a, na);
-  if (is_device_ptr(agg)) {
-    AMGDD_CUDA(cudaMemcpyAsync(agg, a.data(), a.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    AMGDD_CUDA(cudaStreamSynchronize(s));
-  } else {
-    std::memcpy(agg, a.data(), a.size() * sizeof(int32_t));
-  }
+  DBuf<int32_t> dagg;
+  AMGDD_TRY(dagg.alloc(std::max<int64_t>(G->n, 1)));
+  AMGDD_TRY(aggregate_rows(rowptr, col, G->m, G->n, passes, dagg.p, na, s));
+  AMGDD_CUDA(cudaMemcpyAsync(agg, dagg.p, (size_t)G->n * sizeof(int32_t),
+                             is_device_ptr(agg) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  AMGDD_CUDA(cudaStreamSynchronize(s));
   if (nagg) *nagg = na;
   return AMGDD_OK;
 }
@@ -3485,9 +3797,10 @@ int amgdd_solve(amgdd_hierarchy* h, const double* b, int nrhs, double tol, doubl
     const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
     int first_bad = AMGDD_OK;
     if (nrhs > 1 && h->prm.use_graph && h->lv[0]->Aw64.p != nullptr && h->prm.cycle == 0) {
-      for (int j0 = 0; j0 < nrhs; j0 += kMaxRhs) {
-        const int g = std::min(kMaxRhs, nrhs - j0);
-        const int K = g <= 2 ? 2 : (g <= 4 ? 4 : 8);
+      const int bc = std::min(h->prm.batch_cols, kMaxRhs);
+      for (int j0 = 0; j0 < nrhs; j0 += bc) {
+        const int g = std::min(bc, nrhs - j0);
+        const int K = kclass(g);
         std::vector<amgdd_info> tmp(g);
         amgdd_info* inf = info ? info + j0 : tmp.data();
         const int prec = h->precision;
@@ -3903,7 +4216,10 @@ int amgdd_measure_fp64(void* stream, double* gflops) {
 int64_t amgdd_device_bytes(const amgdd_hierarchy* h, int with_batched) {
   if (h == nullptr) return -1;
   int64_t b = h->setup_bytes + h->multi_bytes;
-  if (with_batched && !h->mw.ready) b += multi_bytes_estimate(*h);
+  if (with_batched > 0) {  // 1: the hierarchy's batch width; 2..32: a batch of that many columns
+    const int want = kclass(std::min(with_batched == 1 ? h->prm.batch_cols : with_batched, kMaxRhs));
+    if (h->mw.cap < want) b += multi_bytes_estimate(*h, want) - h->multi_bytes;
+  }
   return b;
 }
 
@@ -4192,6 +4508,54 @@ int amgdd_hierarchy_stats(const amgdd_hierarchy* h, char* json, size_t cap) {
 // again with those choices replayed instead of timed, so the loaded
 // hierarchy applies the same arithmetic with the same kernels (on a GPU of
 // the same model; elsewhere the choices are timed anew).
+// What setup computed for level l, downloaded (FP64 matrices only; unused
+// entries of the compressed-row capacity are written as zeros).
+static int snapshot_level(const amgdd_hierarchy& h, int l, LevelSnap& S) {
+  const Level& L = *h.lv[l];
+  cudaStream_t s = h.work;
+  S.n = L.n;
+  S.nnzA = l < (int)h.nnzA.size() ? h.nnzA[l] : 0;
+  S.nagg = L.nagg;
+  S.coarsest = L.coarsest ? 1 : 0;
+  S.schur_rows = L.schur_rows ? 1 : 0;
+  S.n_color = L.n_color;
+  S.n_mult = L.n_mult;
+  S.thresh = L.thresh;
+  S.inv_err = L.inv_err;
+  S.g_ptr = L.g_ptr;
+  S.g_idx = L.g_idx;
+  S.h_off = L.h_off;
+  if (L.d_R64.p) {
+    S.g_rank = L.g_rank;
+    AMGDD_TRY(download(S.R64, L.d_R64.p, (size_t)L.h_off.back(), s));
+    for (size_t g = 0; g + 1 < L.g_ptr.size(); ++g) {
+      const int64_t sz = L.g_ptr[g + 1] - L.g_ptr[g];
+      for (int64_t e = L.h_off[g] + (int64_t)L.g_rank[g] * sz; e < L.h_off[g + 1]; ++e) S.R64[e] = 0.0;
+    }
+  }
+  if (L.coarsest) {
+    AMGDD_TRY(download(S.W64, L.W64.p, L.W64.n, s));
+    if (L.Aw64.p) AMGDD_TRY(download(S.Aw64, L.Aw64.p, L.Aw64.n, s));
+    return AMGDD_OK;
+  }
+  S.agg = L.agg;
+  S.om_ptr = L.om_ptr;
+  S.om_idx = L.om_idx;
+  S.nomega = L.nomega;
+  S.k = L.k;
+  S.col0 = L.col0;
+  S.z_off = L.z_off;
+  S.mu_off = L.mu_off;
+  S.wf_off = L.wf_off;
+  AMGDD_TRY(download(S.W64, L.W64.p, L.W64.n, s));
+  if (L.Aw64.p) AMGDD_TRY(download(S.Aw64, L.Aw64.p, L.Aw64.n, s));
+  AMGDD_TRY(download(S.mu, L.mu.p, (size_t)L.mu_off.back(), s));
+  AMGDD_TRY(download(S.Z64, L.Z64.p, (size_t)L.z_off.back(), s));
+  if (L.Wf64.p) AMGDD_TRY(download(S.Wf64, L.Wf64.p, L.Wf64.n, s));
+  if (L.has_blk && L.A64.p) AMGDD_TRY(download(S.A64, L.A64.p, L.A64.n, s));
+  return AMGDD_OK;
+}
+
 int amgdd_hierarchy_save(const amgdd_hierarchy* h, const char* path) {
   if (h == nullptr || path == nullptr) {
     set_error("amgdd_hierarchy_save: invalid argument");
@@ -4218,6 +4582,18 @@ int amgdd_hierarchy_save(const amgdd_hierarchy* h, const char* path) {
     const uint32_t len = (uint32_t)kv.first.size();
     ok = ok && std::fwrite(&len, sizeof len, 1, f) == 1 && std::fwrite(kv.first.data(), 1, len, f) == len &&
          std::fwrite(&kv.second, sizeof(double), 1, f) == 1;
+  }
+  // the level snapshots, one at a time
+  const uint64_t nl = h->lv.size();
+  ok = ok && std::fwrite(&nl, sizeof nl, 1, f) == 1;
+  for (size_t l = 0; ok && l < h->lv.size(); ++l) {
+    LevelSnap S;
+    const int rc = snapshot_level(*h, (int)l, S);
+    if (rc != AMGDD_OK) {
+      std::fclose(f);
+      return rc;
+    }
+    ok = put_snap(f, S);
   }
   ok = (std::fclose(f) == 0) && ok;
   if (!ok) {
@@ -4248,7 +4624,8 @@ int amgdd_hierarchy_load(const char* path, void* stream, amgdd_hierarchy** out) 
   std::vector<double> val, d1;
   std::vector<std::pair<std::string, double>> kv;
   constexpr uint64_t kMax = (uint64_t)1 << 40;
-  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kSaveMagic, 8) == 0 &&
+  bool ok = std::fread(magic, 1, 8, f) == 8 &&
+            (std::memcmp(magic, kSaveMagic, 8) == 0 || std::memcmp(magic, kSaveMagicV1, 8) == 0) &&
             std::fread(&psz, sizeof psz, 1, f) == 1 && psz == sizeof(amgdd_params) &&
             std::fread(&prm, psz, 1, f) == 1 && std::fread(&ov, sizeof ov, 1, f) == 1 &&
             std::fread(&hd, sizeof hd, 1, f) == 1 && std::fread(&n, sizeof n, 1, f) == 1 && get_vec(f, rowptr, kMax) &&
@@ -4262,6 +4639,15 @@ int amgdd_hierarchy_load(const char* path, void* stream, amgdd_hierarchy** out) 
     std::string k(ok ? len : 0, '\0');
     ok = ok && std::fread(&k[0], 1, len, f) == len && std::fread(&v, sizeof v, 1, f) == 1;
     if (ok) kv.emplace_back(std::move(k), v);
+  }
+  std::vector<LevelSnap> snaps;
+  const bool v2 = ok && std::memcmp(magic, kSaveMagic, 8) == 0;
+  if (v2) {
+    uint64_t nl = 0;
+    ok = std::fread(&nl, sizeof nl, 1, f) == 1 && nl >= 1 && nl <= 64;
+    snaps.resize(ok ? nl : 0);
+    for (auto& S : snaps) ok = ok && get_snap(f, S, kMax);
+    ok = ok && snaps_valid(snaps, n);
   }
   std::fclose(f);
   if (!ok || rowptr.empty() || col.size() != val.size() || (int64_t)agg.size() != n ||
@@ -4279,7 +4665,7 @@ int amgdd_hierarchy_load(const char* path, void* stream, amgdd_hierarchy** out) 
   G.val = val.data();
   G.mem = AMGDD_HOST;
   try {
-    return setup_impl(&G, hd ? d1.data() : nullptr, agg.data(), ov, &prm, stream, out, &kv);
+    return setup_impl(&G, hd ? d1.data() : nullptr, agg.data(), ov, &prm, stream, out, &kv, v2 ? &snaps : nullptr);
   } catch (const std::bad_alloc&) {
     set_error("amgdd_hierarchy_load: host allocation failed");
     return AMGDD_ERR_OOM;

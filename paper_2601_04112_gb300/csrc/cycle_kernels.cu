@@ -1548,8 +1548,10 @@ int launch_gather_add(const int64_t* ptr, const int32_t* pos, const void* Y, voi
     case 2: return go(k_gather_add<float, 2>, k_gather_add<double, 2>);
     case 4: return go(k_gather_add<float, 4>, k_gather_add<double, 4>);
     case 8: return go(k_gather_add<float, 8>, k_gather_add<double, 8>);
+    case 16: return go(k_gather_add<float, 16>, k_gather_add<double, 16>);
+    case 32: return go(k_gather_add<float, 32>, k_gather_add<double, 32>);
     default:
-      set_error("launch_gather_add: K must be 1, 2, 4 or 8");
+      set_error("launch_gather_add: K must be 1, 2, 4, 8, 16 or 32");
       return AMGDD_ERR_INVALID_ARG;
   }
 }
@@ -1709,38 +1711,6 @@ int launch_cg_zdot(PcgState* st, const float* x32, double* z, const double* r, c
 // index arrays are read-only for the whole launch.
 namespace {
 
-constexpr long long kBarrierCycles = 4000000000LL;  // about 2 s at 2 GHz
-
-// Grid barrier for a cooperative launch (all CTAs resident).  bar[0] counts
-// arrivals, bar[1] is the generation.  The wait is bounded: on timeout, or if
-// another CTA already reported one, it sets *err and returns, and every later
-// barrier of the launch returns at once.
-__device__ __forceinline__ void grid_barrier(unsigned* bar, int* err) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    volatile int* verr = err;
-    const unsigned gen = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == gen) {
-        if (*verr != 0 || clock64() - t0 > kBarrierCycles) {
-          atomicExch(err, 1);
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-}
 
 // Failure-detection probe of the bounded waits: which 0, a grid barrier that
 // the last CTA never reaches; which 1, an mbarrier phase that no copy or

@@ -55,6 +55,39 @@ inline cudaError_t launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 bl
   return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
+constexpr long long kBarrierCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+// Grid barrier for a cooperative launch (all CTAs resident).  bar[0] counts
+// arrivals, bar[1] is the generation.  The wait is bounded: on timeout, or if
+// another CTA already reported one, it sets *err and returns, and every later
+// barrier of the launch returns at once.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    volatile int* verr = err;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (*verr != 0 || clock64() - t0 > kBarrierCycles) {
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);

@@ -328,6 +328,19 @@ int launch_apply(const ApplyPlan& p, const Level& L, bool fp32, const void* x, v
 int launch_cast(const void* src, bool src32, void* dst, bool dst32, int64_t n, const int* skip, cudaStream_t s);
 // *d_count += the number of non-finite entries of v[0..n) (setup checks of the stored operators).
 int count_nonfinite(const void* v, int64_t n, bool fp32, int* d_count, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Standard aggregation on the device (aggregate_kernels.cu): the graph whose
+// vertices 0..nv-1 are adjacent when a hyperedge (d_eptr: ne + 1 offsets,
+// d_eidx: members, device memory) holds both; d_agg (nv, device) receives
+// the ids of the sequential three passes in creation order, *nagg their
+// count; *rounds (optional) accumulates the parallel rounds taken.
+int device_hyper_aggregation(int64_t nv, int64_t ne, const int64_t* d_eptr, const int32_t* d_eidx, int32_t* d_agg,
+                             int64_t* nagg, cudaStream_t s, int64_t* rounds = nullptr);
+// The same with `passes` passes, each on the graph of the aggregates so far
+// (the aggregates a hyperedge touches): ids of the last pass, composed.
+int device_standard_aggregation(int64_t n, int64_t ne, const int64_t* d_eptr, const int32_t* d_eidx, int passes,
+                                int32_t* d_agg, int64_t* nagg, cudaStream_t s, int64_t* rounds = nullptr);
 int launch_copy_vec(const void* src, void* dst, bool fp32, int64_t n, const int* skip, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
@@ -548,6 +561,11 @@ int launch_dense_pack(const double* C, int n, int64_t ld, double* B64, float* B3
 // multiple of 4; x and y 16-byte aligned)
 int launch_dense(const void* B, int64_t ld, int n, bool fp32, const void* x, void* y, const int* skip,
                  cudaStream_t s);
+// FP32 rounding and block transposes (FP64, FP32) of row-major blocks
+// rows[b] x cols[b] at off[b] of src (the copies a loaded hierarchy derives
+// from its stored FP64 matrices); null outputs are skipped.
+int launch_block_copies(int nb, const int32_t* rows, const int32_t* cols, const int64_t* off, const double* src,
+                        float* dst32, double* dstT64, float* dstT32, cudaStream_t s);
 int launch_copy_wrows(int nb, const int32_t* m, const int32_t* no, const int64_t* a_off, const double* Apool,
                       const int64_t* w_off, double* Aw64, float* Aw32, double* AwT64, float* AwT32, cudaStream_t s);
 // Block rows of A_l = sum_g H_g: for block b, rows p0 .. p0+nr_b-1 of each

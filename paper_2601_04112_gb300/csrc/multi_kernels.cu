@@ -1,9 +1,13 @@
-// Solve-phase kernels for K right-hand sides at once (K = 2, 4 or 8).
+// Solve-phase kernels for K right-hand sides at once (K = 2, 4, 8, 16 or 32).
 //
 // Vectors hold the K columns interleaved by node: v[i * K + k].  Every
-// matrix entry a gather-GEMV reads is applied to all K columns, so the
-// matrices of a V-cycle (the smoother rows W_i, the coarse bases Z_i, the
-// rows of A) stream once per K solves.  The CG of each column is the same
+// matrix entry a gather-GEMV reads is applied to all the columns of its
+// launch, so the matrices of a V-cycle (the smoother rows W_i, the coarse
+// bases Z_i, the rows of A) stream once per K solves.  A gather-GEMV whose
+// staged input would not fit shared memory at K columns takes the columns in
+// tiles inside the launch (leading dimension K, tile t at column t * KT):
+// each CTA stages one tile, applies its block rows, then the next tile, so
+// the block's rows come again from L2 rather than DRAM.  The CG of each column is the same
 // recurrence as the single right-hand-side solver, with its own scalars and
 // convergence flag; a column that has converged keeps its iterate.
 #include <cuda_runtime.h>
@@ -20,16 +24,17 @@ namespace {
 constexpr int kMultiThreads = 128;
 
 template <class T, int K>
-__device__ __forceinline__ void multi_out(SegMode mode, T* y, const T* c, int o, const T (&acc)[K]) {
+__device__ __forceinline__ void multi_out(SegMode mode, T* y, const T* c, int o, const T (&acc)[K], int ld, int k0) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    T* d = y + (int64_t)o * K + k;
+    const int64_t at = (int64_t)o * ld + k0 + k;
+    T* d = y + at;
     switch (mode) {
       case SEG_STORE: *d = acc[k]; break;
       case SEG_ADD: *d += acc[k]; break;
       case SEG_ATOMIC_ADD: atomicAdd(d, acc[k]); break;
       case SEG_ATOMIC_SUB: atomicAdd(d, -acc[k]); break;
-      default: *d = c[(int64_t)o * K + k] - acc[k]; break;
+      default: *d = c[at] - acc[k]; break;
     }
   }
 }
@@ -42,7 +47,7 @@ __global__ void __launch_bounds__(kMultiThreads) k_seg_multi(const SegDesc* __re
                                                              const int32_t* __restrict__ out_idx,
                                                              const T* __restrict__ M, const T* __restrict__ x,
                                                              T* __restrict__ y, const T* __restrict__ c, int mode,
-                                                             const int* skip) {
+                                                             const int* skip, int ld, int ntile) {
   pdl_prologue();
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -52,40 +57,44 @@ __global__ void __launch_bounds__(kMultiThreads) k_seg_multi(const SegDesc* __re
   const int ncb = dsc.nc;
   const int r1 = dsc.r1;
   const int32_t* ii = in_idx + dsc.in_off;
-  for (int e = threadIdx.x; e < ncb * K; e += blockDim.x) {
-    const int cc = e / K, k = e - cc * K;
-    xs[e] = x[(int64_t)ii[cc] * K + k];
-  }
-  __syncthreads();
   const int lane = threadIdx.x % L;
   const int grp = threadIdx.x / L;
   const int ngrp = blockDim.x / L;
   const unsigned mask = group_mask<L>();
   const T* Mb = M + dsc.m_off;
   const int32_t* oo = out_idx + dsc.out_off;
-  for (int r = r0 + grp; r < r1; r += ngrp) {
-    const T* row = Mb + (int64_t)r * ncb;
-    T acc[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = T(0);
-    int cc = lane;
-    for (; cc + 3 * L < ncb; cc += 4 * L) {  // four row entries per lane in flight
-      T m[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) m[u] = row[cc + u * L];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] += m[u] * xs[(cc + u * L) * K + k];
+  for (int tile = 0; tile < ntile; ++tile) {
+    const int k0 = tile * K;
+    if (tile > 0) __syncthreads();  // every row of the previous tile has read xs
+    for (int e = threadIdx.x; e < ncb * K; e += blockDim.x) {
+      const int cc = e / K, k = e - cc * K;
+      xs[e] = x[(int64_t)ii[cc] * ld + k0 + k];
     }
-    for (; cc < ncb; cc += L) {
-      const T m = row[cc];
+    __syncthreads();
+    for (int r = r0 + grp; r < r1; r += ngrp) {
+      const T* row = Mb + (int64_t)r * ncb;
+      T acc[K];
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc[k] += m * xs[cc * K + k];
+      for (int k = 0; k < K; ++k) acc[k] = T(0);
+      int cc = lane;
+      for (; cc + 3 * L < ncb; cc += 4 * L) {  // four row entries per lane in flight
+        T m[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) m[u] = row[cc + u * L];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int k = 0; k < K; ++k) acc[k] += m[u] * xs[(cc + u * L) * K + k];
+      }
+      for (; cc < ncb; cc += L) {
+        const T m = row[cc];
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] += m * xs[cc * K + k];
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] = group_sum<L>(acc[k], mask);
+      if (lane == 0) multi_out<T, K>((SegMode)mode, y, c, oo[r], acc, ld, k0);
     }
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = group_sum<L>(acc[k], mask);
-    if (lane == 0) multi_out<T, K>((SegMode)mode, y, c, oo[r], acc);
   }
 }
 
@@ -126,7 +135,7 @@ __global__ void __launch_bounds__(256) k_ell_multi(const T* __restrict__ val, co
 template <class T, int L, int K>
 __global__ void __launch_bounds__(kMultiThreads) k_seg_rows_multi(
     const SegDesc* __restrict__ desc, int ntasks, int max_nc, const int32_t* __restrict__ in_idx, const int32_t* __restrict__ out_idx, const T* __restrict__ MT,
-    const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ c, int mode, const int* skip) {
+    const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ c, int mode, const int* skip, int ld, int ntile) {
   pdl_prologue();
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -141,23 +150,28 @@ __global__ void __launch_bounds__(kMultiThreads) k_seg_rows_multi(
   const int rows = dsc.r1 - dsc.r0;
   const int ncb = dsc.nc, nrb = dsc.nr;
   const int32_t* ii = in_idx + dsc.in_off;
-  for (int e = lane; e < ncb * K; e += L) {
-    const int cc = e / K, k = e - cc * K;
-    xs[e] = x[(int64_t)ii[cc] * K + k];
-  }
-  __syncwarp(mask);
-  if (lane >= rows) return;
   const int r = r0 + lane;
   const T* col = MT + dsc.m_off + r;
-  T acc[K];
+  for (int tile = 0; tile < ntile; ++tile) {
+    const int k0 = tile * K;
+    if (tile > 0) __syncwarp(mask);  // every lane of the group has read the previous tile
+    for (int e = lane; e < ncb * K; e += L) {
+      const int cc = e / K, k = e - cc * K;
+      xs[e] = x[(int64_t)ii[cc] * ld + k0 + k];
+    }
+    __syncwarp(mask);
+    if (lane < rows) {
+      T acc[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) acc[k] = T(0);
-  for (int cc = 0; cc < ncb; ++cc) {
-    const T m = col[(int64_t)cc * nrb];
+      for (int k = 0; k < K; ++k) acc[k] = T(0);
+      for (int cc = 0; cc < ncb; ++cc) {
+        const T m = col[(int64_t)cc * nrb];
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] += m * xs[cc * K + k];
+        for (int k = 0; k < K; ++k) acc[k] += m * xs[cc * K + k];
+      }
+      multi_out<T, K>((SegMode)mode, y, c, out_idx[dsc.out_off + r], acc, ld, k0);
+    }
   }
-  multi_out<T, K>((SegMode)mode, y, c, out_idx[dsc.out_off + r], acc);
 }
 
 // K dot products a_k . b_k (and a_k . c_k) per CTA; the grid stride is a
@@ -334,9 +348,15 @@ int grid_of(int64_t len, int threads) {
   return (int)std::min<int64_t>(std::max<int64_t>(g, 1), 152 * 16);
 }
 
+// Shared memory of one launch over KT columns.
+size_t seg_multi_smem(const SegPlan& p, int KT, size_t esz) {
+  const int per = p.rows_mode ? kMultiThreads / (p.kind == 8 ? 8 : (p.kind == 16 ? 16 : 32)) : 1;
+  return (size_t)per * p.max_nc * KT * esz;
+}
+
 template <class T, int K>
 int seg_multi_k(const SegPlan& p, const T* M, const T* MT, const T* x, T* y, SegMode mode, const T* c,
-                const int* skip, cudaStream_t s) {
+                const int* skip, cudaStream_t s, int ld, int ntile) {
   if (p.rows_mode) {
     if (MT == nullptr) {
       set_error("launch_seg_multi: row-per-lane plan needs the transposed operator");
@@ -348,7 +368,7 @@ int seg_multi_k(const SegPlan& p, const T* M, const T* MT, const T* x, T* y, Seg
       if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       AMGDD_CUDA(launch_k(g_pdl, kern, (p.ntasks + per - 1) / per, kMultiThreads, smem, s,
                           (const SegDesc*)p.task_desc.p, p.ntasks, p.max_nc, p.in_idx_ext, p.out_idx_ext, MT, x, y,
-                          c, (int)mode, skip));
+                          c, (int)mode, skip, ld, ntile));
       AMGDD_CUDA(cudaGetLastError());
       count_kernels(1);
       return AMGDD_OK;
@@ -363,7 +383,7 @@ int seg_multi_k(const SegPlan& p, const T* M, const T* MT, const T* x, T* y, Seg
     const size_t smem = (size_t)p.max_nc * K * sizeof(T);
     if (smem > 48 * 1024) AMGDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     AMGDD_CUDA(launch_k(g_pdl, kern, p.nchunks, kMultiThreads, smem, s, (const SegDesc*)p.chunk_desc.p,
-                        p.in_idx_ext, p.out_idx_ext, M, x, y, c, (int)mode, skip));
+                        p.in_idx_ext, p.out_idx_ext, M, x, y, c, (int)mode, skip, ld, ntile));
     AMGDD_CUDA(cudaGetLastError());
     count_kernels(1);
     return AMGDD_OK;
@@ -376,16 +396,31 @@ int seg_multi_k(const SegPlan& p, const T* M, const T* MT, const T* x, T* y, Seg
   }
 }
 
+// The columns of one staged tile: all K while the staged input stays within
+// 64 KiB (wider tiles only where they leave room for several CTAs per SM),
+// and within 200 KiB for K <= 8; the launch then walks K / KT tiles.
+int seg_multi_tile(const SegPlan& p, int K, size_t esz) {
+  int KT = K;
+  while (KT > 8 && seg_multi_smem(p, KT, esz) > (size_t)64 * 1024) KT /= 2;
+  while (KT > 2 && seg_multi_smem(p, KT, esz) > (size_t)200 * 1024) KT /= 2;
+  return KT;
+}
+
 template <class T>
 int seg_multi(const SegPlan& p, const T* M, const T* MT, const T* x, T* y, SegMode mode, const T* c, int K,
               const int* skip, cudaStream_t s) {
-  switch (K) {
-    case 2: return seg_multi_k<T, 2>(p, M, MT, x, y, mode, c, skip, s);
-    case 4: return seg_multi_k<T, 4>(p, M, MT, x, y, mode, c, skip, s);
-    case 8: return seg_multi_k<T, 8>(p, M, MT, x, y, mode, c, skip, s);
-    default:
-      set_error("launch_seg_multi: K must be 2, 4 or 8 (got %d)", K);
-      return AMGDD_ERR_INTERNAL;
+  if (K != 2 && K != 4 && K != 8 && K != 16 && K != 32) {
+    set_error("launch_seg_multi: K must be 2, 4, 8, 16 or 32 (got %d)", K);
+    return AMGDD_ERR_INTERNAL;
+  }
+  const int KT = seg_multi_tile(p, K, sizeof(T));
+  const int nt = K / KT;
+  switch (KT) {
+    case 2: return seg_multi_k<T, 2>(p, M, MT, x, y, mode, c, skip, s, K, nt);
+    case 4: return seg_multi_k<T, 4>(p, M, MT, x, y, mode, c, skip, s, K, nt);
+    case 8: return seg_multi_k<T, 8>(p, M, MT, x, y, mode, c, skip, s, K, nt);
+    case 16: return seg_multi_k<T, 16>(p, M, MT, x, y, mode, c, skip, s, K, nt);
+    default: return seg_multi_k<T, 32>(p, M, MT, x, y, mode, c, skip, s, K, nt);
   }
 }
 
@@ -412,7 +447,9 @@ int launch_dot_multi(const double* a, const double* b, const double* c, int64_t 
     case 2: AMGDD_CUDA(launch_k(g_pdl, k_dot_multi<2>, kDotBlocks, 256, 0, s, a, b, c, len, partials, skip)); break;
     case 4: AMGDD_CUDA(launch_k(g_pdl, k_dot_multi<4>, kDotBlocks, 256, 0, s, a, b, c, len, partials, skip)); break;
     case 8: AMGDD_CUDA(launch_k(g_pdl, k_dot_multi<8>, kDotBlocks, 256, 0, s, a, b, c, len, partials, skip)); break;
-    default: set_error("launch_dot_multi: K must be 2, 4 or 8"); return AMGDD_ERR_INTERNAL;
+    case 16: AMGDD_CUDA(launch_k(g_pdl, k_dot_multi<16>, kDotBlocks, 256, 0, s, a, b, c, len, partials, skip)); break;
+    case 32: AMGDD_CUDA(launch_k(g_pdl, k_dot_multi<32>, kDotBlocks, 256, 0, s, a, b, c, len, partials, skip)); break;
+    default: set_error("launch_dot_multi: K must be 2, 4, 8, 16 or 32"); return AMGDD_ERR_INTERNAL;
   }
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
@@ -425,7 +462,9 @@ int launch_pcg_scalar_multi(int which, PcgState* st, int* grp, const double* par
     case 2: AMGDD_CUDA(launch_k(g_pdl, k_pcg_scalar_multi<2>, 1, 64, 0, s, which, st, grp, partials, kDotBlocks, cond, use_cond)); break;
     case 4: AMGDD_CUDA(launch_k(g_pdl, k_pcg_scalar_multi<4>, 1, 128, 0, s, which, st, grp, partials, kDotBlocks, cond, use_cond)); break;
     case 8: AMGDD_CUDA(launch_k(g_pdl, k_pcg_scalar_multi<8>, 1, 256, 0, s, which, st, grp, partials, kDotBlocks, cond, use_cond)); break;
-    default: set_error("launch_pcg_scalar_multi: K must be 2, 4 or 8"); return AMGDD_ERR_INTERNAL;
+    case 16: AMGDD_CUDA(launch_k(g_pdl, k_pcg_scalar_multi<16>, 1, 512, 0, s, which, st, grp, partials, kDotBlocks, cond, use_cond)); break;
+    case 32: AMGDD_CUDA(launch_k(g_pdl, k_pcg_scalar_multi<32>, 1, 1024, 0, s, which, st, grp, partials, kDotBlocks, cond, use_cond)); break;
+    default: set_error("launch_pcg_scalar_multi: K must be 2, 4, 8, 16 or 32"); return AMGDD_ERR_INTERNAL;
   }
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
@@ -439,7 +478,10 @@ int launch_update_xr_multi(const PcgState* st, const int* grp, double* x, double
   switch (K) {
     case 2: AMGDD_CUDA(launch_k(g_pdl, k_update_xr_multi<2>, g, 256, 0, s, st, grp, x, r, p, q, len)); break;
     case 4: AMGDD_CUDA(launch_k(g_pdl, k_update_xr_multi<4>, g, 256, 0, s, st, grp, x, r, p, q, len)); break;
-    default: AMGDD_CUDA(launch_k(g_pdl, k_update_xr_multi<8>, g, 256, 0, s, st, grp, x, r, p, q, len)); break;
+    case 8: AMGDD_CUDA(launch_k(g_pdl, k_update_xr_multi<8>, g, 256, 0, s, st, grp, x, r, p, q, len)); break;
+    case 16: AMGDD_CUDA(launch_k(g_pdl, k_update_xr_multi<16>, g, 256, 0, s, st, grp, x, r, p, q, len)); break;
+    case 32: AMGDD_CUDA(launch_k(g_pdl, k_update_xr_multi<32>, g, 256, 0, s, st, grp, x, r, p, q, len)); break;
+    default: set_error("launch_update_xr_multi: K must be 2, 4, 8, 16 or 32"); return AMGDD_ERR_INTERNAL;
   }
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
@@ -453,7 +495,10 @@ int launch_update_p_multi(const PcgState* st, const int* grp, double* p, const d
   switch (K) {
     case 2: AMGDD_CUDA(launch_k(g_pdl, k_update_p_multi<2>, g, 256, 0, s, st, grp, p, z, zold, len)); break;
     case 4: AMGDD_CUDA(launch_k(g_pdl, k_update_p_multi<4>, g, 256, 0, s, st, grp, p, z, zold, len)); break;
-    default: AMGDD_CUDA(launch_k(g_pdl, k_update_p_multi<8>, g, 256, 0, s, st, grp, p, z, zold, len)); break;
+    case 8: AMGDD_CUDA(launch_k(g_pdl, k_update_p_multi<8>, g, 256, 0, s, st, grp, p, z, zold, len)); break;
+    case 16: AMGDD_CUDA(launch_k(g_pdl, k_update_p_multi<16>, g, 256, 0, s, st, grp, p, z, zold, len)); break;
+    case 32: AMGDD_CUDA(launch_k(g_pdl, k_update_p_multi<32>, g, 256, 0, s, st, grp, p, z, zold, len)); break;
+    default: set_error("launch_update_p_multi: K must be 2, 4, 8, 16 or 32"); return AMGDD_ERR_INTERNAL;
   }
   AMGDD_CUDA(cudaGetLastError());
   count_kernels(1);
@@ -499,8 +544,14 @@ int launch_ell_multi(const Level& L, bool fp32, const void* x, void* y, const vo
     case 8:
       return res ? go(k_ell_multi<float, 8, true>, k_ell_multi<double, 8, true>)
                  : go(k_ell_multi<float, 8, false>, k_ell_multi<double, 8, false>);
+    case 16:
+      return res ? go(k_ell_multi<float, 16, true>, k_ell_multi<double, 16, true>)
+                 : go(k_ell_multi<float, 16, false>, k_ell_multi<double, 16, false>);
+    case 32:
+      return res ? go(k_ell_multi<float, 32, true>, k_ell_multi<double, 32, true>)
+                 : go(k_ell_multi<float, 32, false>, k_ell_multi<double, 32, false>);
     default:
-      set_error("launch_ell_multi: K must be 2, 4 or 8");
+      set_error("launch_ell_multi: K must be 2, 4, 8, 16 or 32");
       return AMGDD_ERR_INVALID_ARG;
   }
 }

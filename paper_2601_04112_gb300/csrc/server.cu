@@ -335,7 +335,7 @@ int amgdd_server_create(const amgdd_server_params* params, amgdd_server** out) {
   *out = nullptr;
   amgdd_server_params p = params ? *params : amgdd_server_params_default();
   if (p.slots < 1 || p.slots > 64 || p.max_batch < 1 || p.hbm_budget <= 0) return AMGDD_ERR_INVALID_ARG;
-  p.max_batch = std::min(p.max_batch, 8);
+  p.max_batch = std::min(p.max_batch, 32);
   std::unique_ptr<amgdd_server> s(new amgdd_server());
   s->prm = p;
   if (cudaGetDevice(&s->device) != cudaSuccess) return AMGDD_ERR_CUDA;

@@ -1428,6 +1428,34 @@ int launch_dense_pack(const double* C, int n, int64_t ld, double* B64, float* B3
   return AMGDD_OK;
 }
 
+// The derived copies of stored blocks (a loaded hierarchy): block b is
+// rows[b] x cols[b], row-major at off[b] in src; dst32 receives its FP32
+// rounding, dstT64 / dstT32 its transpose (cols x rows, row-major, same
+// offset) in FP64 / FP32.  Null outputs are skipped.
+__global__ void k_block_copies(const int32_t* __restrict__ rows, const int32_t* __restrict__ cols,
+                               const int64_t* __restrict__ off, const double* __restrict__ src,
+                               float* __restrict__ dst32, double* __restrict__ dstT64, float* __restrict__ dstT32) {
+  const int b = blockIdx.x;
+  const int nr = rows[b], nc = cols[b];
+  const int64_t o = off[b];
+  for (int64_t e = threadIdx.x; e < (int64_t)nr * nc; e += blockDim.x) {
+    const int r = (int)(e / nc), c = (int)(e - (int64_t)r * nc);
+    const double v = src[o + e];
+    if (dst32) dst32[o + e] = (float)v;
+    if (dstT64) dstT64[o + (int64_t)c * nr + r] = v;
+    if (dstT32) dstT32[o + (int64_t)c * nr + r] = (float)v;
+  }
+}
+
+int launch_block_copies(int nb, const int32_t* rows, const int32_t* cols, const int64_t* off, const double* src,
+                        float* dst32, double* dstT64, float* dstT32, cudaStream_t s) {
+  if (nb == 0) return AMGDD_OK;
+  k_block_copies<<<nb, 256, 0, s>>>(rows, cols, off, src, dst32, dstT64, dstT32);
+  AMGDD_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return AMGDD_OK;
+}
+
 int launch_copy_wrows(int nb, const int32_t* m, const int32_t* no, const int64_t* a_off, const double* Apool,
                       const int64_t* w_off, double* Aw64, float* Aw32, double* AwT64, float* AwT32, cudaStream_t s) {
   if (nb == 0) return AMGDD_OK;

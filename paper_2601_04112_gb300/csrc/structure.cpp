@@ -1,10 +1,9 @@
 // Host-side structural setup: graph of A through shared row supports,
 // cleanup of unaggregated nodes (Section 3.3), overlapping subdomains
 // Omega_i = omega_i u Gamma_i (Section 2.2), touched aggregates and the row
-// multiplicity M of the Lemma (Section 3.1), and standard aggregation of the
-// coarse block graph (Section 2.1 passes; the coarse-level rule of
-// Algorithm 1 is left open by the paper and is read as aggregating whole
-// blocks of coarse dofs).
+// multiplicity M of the Lemma (Section 3.1), the subdomain colouring of
+// Section 3.4.  Standard aggregation itself (level 0, and the coarse block
+// graph) runs on the device (aggregate_kernels.cu).
 #include "structure.h"
 
 #include <algorithm>
@@ -126,113 +125,6 @@ void touched_aggregates(const Supports& S, const std::vector<int32_t>& agg, std:
     tids.insert(tids.end(), t.begin(), t.end());
     tptr[g + 1] = (int64_t)tids.size();
     M[g] = (int32_t)t.size();
-  }
-}
-
-// Standard aggregation (Section 2.1 passes, every edge strong) on a graph
-// given by hyperedges: two vertices are adjacent when an edge holds both.
-void hyper_aggregation(int64_t nv, const std::vector<int64_t>& eptr, const std::vector<int32_t>& eidx,
-                       std::vector<int32_t>& agg, int64_t& nagg) {
-  // neighbour lists (sorted, no self) through vertex -> edge incidence
-  std::vector<int64_t> vptr(nv + 1, 0);
-  const int64_t ne = (int64_t)eptr.size() - 1;
-  for (int64_t e = 0; e < ne; ++e)
-    for (int64_t q = eptr[e]; q < eptr[e + 1]; ++q) vptr[eidx[q] + 1]++;
-  for (int64_t v = 0; v < nv; ++v) vptr[v + 1] += vptr[v];
-  std::vector<int64_t> ve(vptr[nv]);
-  {
-    std::vector<int64_t> fill(vptr.begin(), vptr.end() - 1);
-    for (int64_t e = 0; e < ne; ++e)
-      for (int64_t q = eptr[e]; q < eptr[e + 1]; ++q) ve[fill[eidx[q]]++] = e;
-  }
-  std::vector<int64_t> nptr(nv + 1, 0);
-  std::vector<int32_t> nbr;
-  std::vector<int64_t> stamp(nv, -1);
-  for (int64_t v = 0; v < nv; ++v) {
-    stamp[v] = v;
-    const size_t s0 = nbr.size();
-    for (int64_t k = vptr[v]; k < vptr[v + 1]; ++k) {
-      const int64_t e = ve[k];
-      for (int64_t q = eptr[e]; q < eptr[e + 1]; ++q) {
-        const int32_t u = eidx[q];
-        if (stamp[u] != v) {
-          stamp[u] = v;
-          nbr.push_back(u);
-        }
-      }
-    }
-    std::sort(nbr.begin() + s0, nbr.end());
-    nptr[v + 1] = (int64_t)nbr.size();
-  }
-  agg.assign(nv, -1);
-  int64_t nxt = 0;
-  // pass 1: roots whose neighbours are all unaggregated
-  for (int64_t j = 0; j < nv; ++j) {
-    if (agg[j] >= 0) continue;
-    bool free_all = true;
-    for (int64_t k = nptr[j]; k < nptr[j + 1]; ++k)
-      if (agg[nbr[k]] >= 0) {
-        free_all = false;
-        break;
-      }
-    if (free_all) {
-      agg[j] = (int32_t)nxt;
-      for (int64_t k = nptr[j]; k < nptr[j + 1]; ++k) agg[nbr[k]] = (int32_t)nxt;
-      ++nxt;
-    }
-  }
-  // pass 2: join the lowest-index neighbour aggregated in pass 1
-  const std::vector<int32_t> after1(agg);
-  for (int64_t j = 0; j < nv; ++j) {
-    if (agg[j] >= 0) continue;
-    for (int64_t k = nptr[j]; k < nptr[j + 1]; ++k)
-      if (after1[nbr[k]] >= 0) {
-        agg[j] = after1[nbr[k]];
-        break;
-      }
-  }
-  // pass 3: leftovers start aggregates with their unaggregated neighbours
-  for (int64_t j = 0; j < nv; ++j) {
-    if (agg[j] >= 0) continue;
-    agg[j] = (int32_t)nxt;
-    for (int64_t k = nptr[j]; k < nptr[j + 1]; ++k)
-      if (agg[nbr[k]] < 0) agg[nbr[k]] = (int32_t)nxt;
-    ++nxt;
-  }
-  nagg = nxt;
-}
-
-void block_aggregation(int nb, const std::vector<int64_t>& tptr, const std::vector<int32_t>& tids,
-                       std::vector<int32_t>& bagg, int& nagg) {
-  int64_t na = 0;
-  hyper_aggregation(nb, tptr, tids, bagg, na);
-  nagg = (int)na;
-}
-
-void standard_aggregation(int64_t n, const Supports& S, int passes, std::vector<int32_t>& agg, int64_t& nagg) {
-  hyper_aggregation(n, S.ptr, S.idx, agg, nagg);
-  std::vector<int64_t> tptr;
-  std::vector<int32_t> tids, bagg, seen;
-  for (int p = 1; p < passes; ++p) {
-    // hyperedges of the graph of T^T A T: the distinct aggregates each row touches
-    tptr.assign(1, 0);
-    tids.clear();
-    seen.assign(nagg, -1);
-    const int64_t ng = S.size();
-    for (int64_t g = 0; g < ng; ++g) {
-      for (int64_t q = S.ptr[g]; q < S.ptr[g + 1]; ++q) {
-        const int32_t a = agg[S.idx[q]];
-        if (seen[a] != (int32_t)g) {
-          seen[a] = (int32_t)g;
-          tids.push_back(a);
-        }
-      }
-      tptr.push_back((int64_t)tids.size());
-    }
-    int64_t nb = 0;
-    hyper_aggregation(nagg, tptr, tids, bagg, nb);
-    for (auto& a : agg) a = bagg[a];
-    nagg = nb;
   }
 }
 

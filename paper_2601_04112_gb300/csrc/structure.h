@@ -45,20 +45,4 @@ int colour_subdomains(const std::vector<int64_t>& om_ptr, const std::vector<int3
 // 3.4): max{0.1, (kappa - n_color) / (n_color n_multiplicity)}.
 double kappa_threshold(double kappa, int n_color, int n_mult);
 
-// Standard aggregation (Section 2.1 passes, every edge strong) on the graph
-// whose vertices are adjacent when a hyperedge (eptr/eidx lists) holds both;
-// ids in creation order.
-void hyper_aggregation(int64_t nv, const std::vector<int64_t>& eptr, const std::vector<int32_t>& eidx,
-                       std::vector<int32_t>& agg, int64_t& nagg);
-
-// Level-0 aggregates on the graph of A = D1 + G^T G (rows of G as
-// hyperedges), with `passes` passes of aggregating aggregates: pass p + 1
-// aggregates the graph of T_p^T A T_p (Section 3.3).
-void standard_aggregation(int64_t n, const Supports& S, int passes, std::vector<int32_t>& agg, int64_t& nagg);
-
-// Standard aggregation with all edges strong on the graph of aggregates
-// that share a row (block graph); returns block -> coarse aggregate.
-void block_aggregation(int nblocks, const std::vector<int64_t>& tptr, const std::vector<int32_t>& tids,
-                       std::vector<int32_t>& bagg, int& nagg);
-
 }  // namespace amgdd

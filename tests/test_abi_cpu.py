@@ -1,6 +1,6 @@
 """The C-ABI library builds for sm_103a and exports every symbol that
-include/amgdd.h declares; its host-only logic (defaults, file checks, level-0
-aggregation) runs here too.  No device call: this runs without a GPU."""
+include/amgdd.h declares; its host-only logic (defaults, file checks) runs
+here too.  No device call: this runs without a GPU."""
 import ctypes
 import os
 import re
@@ -41,7 +41,7 @@ def test_params_default_without_gpu():
     p = amg.params(c_min=(2, 3, 4))
     assert p.L_max == 10 and p.n_coarse == 2000 and abs(p.thresh - 0.1) < 1e-15
     assert list(p.c_min)[:3] == [2, 3, 4] and p.n_cmin == 3
-    assert p.kappa == 0.0 and p.agg_passes == 1
+    assert p.kappa == 0.0 and p.agg_passes == 1 and p.batch_cols == 8
 
 
 
@@ -59,24 +59,3 @@ def test_hierarchy_load_rejects_bad_files(tmp_path):
             assert e.status == -1
         else:
             raise AssertionError("load accepted " + str(path))
-
-
-def test_host_aggregation_matches_oracle():
-    """Level-0 aggregation is host logic of the library (sequential passes, host buffers in and out): it
-    runs without a GPU and must equal the oracle's standard aggregation id for id."""
-    import math
-
-    import numpy as np
-
-    import oracle
-    import paper_2601_04112_gb300 as amg
-    from inputs import fd_2d, q1_2d, rotated_sqrtK
-    from oracle.construct import row_groups_from_csr
-
-    amg.load_library()
-    for p in (fd_2d(30, math.pi / 6, 1e-4), q1_2d(21, rotated_sqrtK(0.4, 1e-3))):
-        sups, _ = row_groups_from_csr(p.rowptr, p.col, p.val, p.n, p.D1)
-        for passes in (1, 2):
-            ao, no = oracle.standard_aggregation(sups, p.n, passes)
-            ag, ng = amg.aggregate(p.rowptr, p.col, p.n, passes)
-            assert ng == no and np.array_equal(ag, ao.astype(np.int32))

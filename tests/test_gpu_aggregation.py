@@ -1,7 +1,12 @@
 """Level-0 aggregation through the C ABI (amgdd_aggregate, and amgdd_setup with agg = NULL) against the
 oracle's standard aggregation with repeated passes (Section 3.3).
 
-Aggregate ids are integers: bit-exact.  The hierarchy built from library-chosen aggregates then matches the
+The library runs the passes on the device in parallel rounds (pass 1's roots as the first maximal
+independent set of the distance-2 graph, pass 3's as that of the graph on the leftovers); the oracle
+visits the unknowns one by one.  Aggregate ids are integers: bit-exact, on structured grids, on
+random patterns with isolated unknowns and many pass-2 joins, and on grids large enough for hundreds
+of rounds.  (With every edge strong, pass 3 never has work: an unknown that is not a root had a
+neighbour aggregated at its visit, so pass 2 places it.)  The hierarchy built from library-chosen aggregates then matches the
 oracle's hierarchy on the same aggregates (structure, spectra, level operators, PCG).
 """
 import math
@@ -23,6 +28,8 @@ PROBLEMS = {
     "fd_40": lambda: fd_2d(40, math.pi / 6, 1e-4),
     "q1_33": lambda: q1_2d(33, rotated_sqrtK(0.4, 1e-3)),
     "q1_3d_10": lambda: config_problem("q1_3d_32", N=10)[0],
+    "q1_129": lambda: q1_2d(129, rotated_sqrtK(0.4, 1e-3)),
+    "q1_3d_18": lambda: config_problem("q1_3d_32", N=18)[0],
 }
 
 
@@ -48,6 +55,29 @@ def test_aggregate_matches_oracle(amg, name, passes):
     p = PROBLEMS[name]()
     ao, no = _oracle_agg(p, passes)
     ag, ng = amg.aggregate(p.rowptr, p.col, p.n, passes)
+    assert ng == no and np.array_equal(ag, ao.astype(np.int32))
+
+
+def _random_pattern(seed, n, m):
+    """Rows of 1-4 distinct random columns; some columns in no row (isolated unknowns)."""
+    rng = np.random.default_rng(seed)
+    used = rng.permutation(n)[: int(0.9 * n)]
+    rp, cl = [0], []
+    for _ in range(m):
+        k = int(rng.integers(1, 5))
+        cl.extend(sorted(set(rng.choice(used, size=k).tolist())))
+        rp.append(len(cl))
+    return np.array(rp, dtype=np.int64), np.array(cl, dtype=np.int32)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("passes", [1, 2])
+def test_aggregate_random_patterns_match_oracle(amg, seed, passes):
+    n = 3000
+    rp, cl = _random_pattern(seed, n, 2200)
+    sups, _ = row_groups_from_csr(rp, cl, np.ones(len(cl)), n)
+    ao, no = oracle.standard_aggregation(sups, n, passes)
+    ag, ng = amg.aggregate(rp, cl, n, passes)
     assert ng == no and np.array_equal(ag, ao.astype(np.int32))
 
 

@@ -386,27 +386,81 @@ def test_deterministic_repeats_bitwise(amg, name):
     assert _rel(_x_at_iters(H, b, io["iters"]), xo) <= level_bar(ho, len(ho.levels), 1e-10)
 
 
-def test_saved_hierarchy_reloads(amg, tmp_path):
-    """amgdd_hierarchy_save / _load: the reloaded hierarchy has the same
-    levels, aggregates and kernel choices, and solves to the same x."""
-    c = CASES["ragged_3lvl"]
+RELOAD_CASES = {  # name: (parity case, parameter overrides)
+    "ragged_3lvl": ("ragged_3lvl", {}),
+    "large_blocks": ("large_blocks", {}),  # coarse block rows kept by timing or not
+    "overlap2_d1": ("overlap2_d1", {}),  # D1 rows among the row groups
+    "q1_3d_12": ("q1_3d_12", {}),
+    "one_level": ("ragged_3lvl", dict(n_coarse=100000)),  # the coarsest level is level 0
+    "additive": ("ragged_3lvl", dict(cycle=1, L_max=2, c_min=(1,), n_coarse=1, thresh=2.0)),  # all of A_i^{-1}
+}
+
+
+@pytest.mark.parametrize("name", list(RELOAD_CASES))
+def test_saved_hierarchy_reloads(amg, tmp_path, name):
+    """amgdd_hierarchy_save / _load: the file holds what setup computed (the
+    row groups' compressed rows, the local inverses' rows, the bases and
+    spectra, the coarse block rows, the coarsest inverse) with the kernel
+    choices, and loading runs none of the local problems again.  With the
+    deterministic kernels the reloaded hierarchy is the same operator bit for
+    bit: equal levels, aggregates, bases and spectra, and FP64 and FP32-cycle
+    solves with the same iterates (fixed kernel choices, tune = 0: a timed
+    setup builds its dense tail while trying others, which reorders sums at
+    rounding level; the timed case is checked to 1e-12).  A truncated file
+    is refused."""
+    base, over = RELOAD_CASES[name]
+    c = CASES[base]
     p = _problem(c)
-    H = amg.Hierarchy.from_problem(p, overlap=c["overlap"], c_min=c["c_min"], n_coarse=c["n_coarse"],
-                                   deterministic=1)
+    kw = dict(overlap=c["overlap"], c_min=c["c_min"], n_coarse=c["n_coarse"],
+              coarse_overlap=c.get("coarse_overlap", 0), deterministic=1, tune=0)
+    kw.update(over)
+    if "cycle" in over:
+        kw.pop("deterministic")
+    H = amg.Hierarchy.from_problem(p, **kw)
     path = tmp_path / "h.amgdd"
     H.save(path)
     H2 = amg.Hierarchy.load(path)
     assert H2.num_levels == H.num_levels and H2.n == H.n
-    for lvl in range(H.num_levels - 1):
-        assert np.array_equal(H.export(lvl, amg.ARR_AGG), H2.export(lvl, amg.ARR_AGG))
     s1, s2 = H.stats(), H2.stats()
+    # loading skips the local problems: no eigensolve or Schur time
+    ph = s2["setup_phases_ms"]
+    assert ph.get("eigen", 0.0) == 0.0 and ph.get("schur", 0.0) == 0.0 and ph.get("cholesky", 0.0) == 0.0, ph
+    for lvl in range(H.num_levels - 1):
+        for arr in (amg.ARR_AGG, amg.ARR_OMEGA_PTR, amg.ARR_OMEGA_IDX, amg.ARR_K, amg.ARR_Z, amg.ARR_MU,
+                    amg.ARR_G_PTR, amg.ARR_G_IDX, amg.ARR_A_PTR, amg.ARR_A_IDX):
+            assert np.array_equal(H.export(lvl, arr), H2.export(lvl, arr)), (lvl, arr)
+    assert s1["n"] == s2["n"] and s1["op_complexity"] == s2["op_complexity"]
     assert [d["form"] for d in s1["coarse_A"]] == [d["form"] for d in s2["coarse_A"]]
     assert s1["dense_tail"]["fp64"]["from"] == s2["dense_tail"]["fp64"]["from"]
     b = seeded_rhs(p.n, 1, 9)[:, 0]
-    x1, i1 = H.solve(b, tol=1e-8)
-    x2, i2 = H2.solve(b, tol=1e-8)
-    assert i1[0]["iters"] == i2[0]["iters"]
-    assert _rel(np.asarray(x2), np.asarray(x1)) <= 1e-12
+    precs = (amg.FP64,) if "cycle" in over else (amg.FP64, amg.MIXED32)
+    for prec in precs:
+        H.set_precision(prec)
+        H2.set_precision(prec)
+        x1, i1 = H.solve(b, tol=1e-8)
+        x2, i2 = H2.solve(b, tol=1e-8)
+        assert i1[0]["iters"] == i2[0]["iters"] and i2[0]["status"] == 0
+        if "cycle" in over:
+            assert _rel(np.asarray(x2), np.asarray(x1)) <= 1e-12
+        else:
+            assert np.array_equal(np.asarray(x2), np.asarray(x1)), prec
+    if name == "ragged_3lvl":  # a timed setup (dense tail, kernel forms by timing) reloads to rounding
+        kw.pop("tune")
+        Ht = amg.Hierarchy.from_problem(p, **kw)
+        Ht.save(tmp_path / "t.amgdd")
+        Ht2 = amg.Hierarchy.load(tmp_path / "t.amgdd")
+        for prec in (amg.FP64, amg.MIXED32):
+            Ht.set_precision(prec)
+            Ht2.set_precision(prec)
+            x1, i1 = Ht.solve(b, tol=1e-8)
+            x2, i2 = Ht2.solve(b, tol=1e-8)
+            assert i1[0]["iters"] == i2[0]["iters"] and _rel(np.asarray(x2), np.asarray(x1)) <= 1e-12
+    # a truncated file is refused (no partial hierarchy)
+    data = path.read_bytes()
+    cut = tmp_path / "cut.amgdd"
+    cut.write_bytes(data[: len(data) - 1000])
+    with pytest.raises(RuntimeError):
+        amg.Hierarchy.load(cut)
     with pytest.raises(RuntimeError):
         amg.Hierarchy.load(tmp_path / "missing.amgdd")
 
