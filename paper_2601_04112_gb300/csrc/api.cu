@@ -2646,9 +2646,19 @@ static int precondition(amgdd_hierarchy& h, const double* r, double* z, const in
 }
 
 // q = A p in FP64 on level 0.
+// A one-level hierarchy keeps its dense A (the coarsest level's Aw64, symmetric):
+// in deterministic mode its A-apply is that GEMV instead of the row groups'
+// scatter with atomics (level 0 has no ELL rows without aggregates).
+static bool dense_level0(const amgdd_hierarchy& h) {
+  const Level& L0 = *h.lv[0];
+  return h.prm.deterministic && L0.coarsest && L0.Aw64.p != nullptr;
+}
+
 static int apply_fine64(amgdd_hierarchy& h, const double* p, double* q, const int* skip, cudaStream_t s) {
   Level& L0 = *h.lv[0];
   if (L0.use_ell) return launch_ell(L0, false, p, q, nullptr, skip, s);
+  if (dense_level0(h))
+    return launch_seg(L0.ras, L0.Aw64.p, false, p, q, false, SEG_STORE, skip, s, nullptr, nullptr, L0.Aw64.p);
   AMGDD_CUDA(cudaMemsetAsync(q, 0, L0.n * sizeof(double), s));
   return launch_apply(L0.aplan, L0, false, p, q, +1, skip, s);
 }
@@ -2836,6 +2846,9 @@ static int solve_once(amgdd_hierarchy& h, const double* bsrc, bool bdev, double 
   for (int restarts = 0;; ++restarts) {
     if (h.lv[0]->use_ell) {
       AMGDD_TRY(launch_ell(*h.lv[0], false, h.x.p, h.q.p, h.b.p, nullptr, s));
+    } else if (dense_level0(h)) {
+      AMGDD_TRY(launch_seg(h.lv[0]->ras, h.lv[0]->Aw64.p, false, h.x.p, h.q.p, false, SEG_RESID, nullptr, s, h.b.p,
+                           nullptr, h.lv[0]->Aw64.p));
     } else {
       AMGDD_CUDA(cudaMemcpyAsync(h.q.p, h.b.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
       AMGDD_TRY(launch_apply(h.lv[0]->aplan, *h.lv[0], false, h.x.p, h.q.p, -1, nullptr, s));
@@ -3056,7 +3069,8 @@ static int pcg_iteration_multi(amgdd_hierarchy& h, int K, cudaStream_t s, cudaGr
   if (L0.use_ell)
     AMGDD_TRY(launch_ell_multi(L0, false, M.p.p, M.q.p, nullptr, K, skip, s));
   else
-    AMGDD_TRY(launch_seg_multi(L0.ras, L0.Aw64.p, L0.AwT64.p, false, M.p.p, M.q.p, SEG_STORE, nullptr, K, skip, s));
+    AMGDD_TRY(launch_seg_multi(L0.ras, L0.Aw64.p, L0.AwT64.p ? L0.AwT64.p : L0.Aw64.p, false, M.p.p, M.q.p, SEG_STORE,
+                               nullptr, K, skip, s));
   AMGDD_TRY(launch_dot_multi(M.p.p, M.q.p, nullptr, n, K, M.partials.p, skip, s));
   AMGDD_TRY(launch_pcg_scalar_multi(1, M.st.p, M.grp.p, M.partials.p, K, s));
   AMGDD_TRY(launch_update_xr_multi(M.st.p, M.grp.p, M.x.p, M.r.p, M.p.p, M.q.p, n, K, s));
@@ -3146,7 +3160,7 @@ static int solve_group(amgdd_hierarchy& h, const double* b, bool bdev, int ncols
     if (L0.use_ell)
       AMGDD_TRY(launch_ell_multi(L0, false, M.x.p, M.q.p, M.b.p, K, nullptr, s));
     else
-      AMGDD_TRY(launch_seg_multi(L0.ras, L0.Aw64.p, L0.AwT64.p, false, M.x.p, M.q.p, SEG_RESID, M.b.p, K, nullptr,
+      AMGDD_TRY(launch_seg_multi(L0.ras, L0.Aw64.p, L0.AwT64.p ? L0.AwT64.p : L0.Aw64.p, false, M.x.p, M.q.p, SEG_RESID, M.b.p, K, nullptr,
                                  s));
     AMGDD_TRY(launch_dot_multi(M.q.p, M.q.p, nullptr, n, K, M.partials.p, nullptr, s));
     AMGDD_TRY(download(part, M.partials.p, (size_t)kDotBlocks * 2 * K, s));
