@@ -648,14 +648,23 @@ __global__ void k_gep(const int32_t* __restrict__ mdim, const int32_t* __restric
       const int fin = ctl[1];
       work += nrot;
       if (fin) break;
-      for (int row = tm.rank; row < n; row += tm.size) {
-        for (int q = 0; q < nrot; ++q) {
-          const int i = ri[q];
-          const double cs = rc[q], sn = rs[q];
-          double* vi = V + row + (int64_t)i * n;
-          const double a0 = vi[0], a1 = vi[n];
-          vi[n] = sn * a0 + cs * a1;
-          vi[0] = cs * a0 - sn * a1;
+      // The chain's rotations act on consecutive pairs (i, i + 1), i = ri[0],
+      // ri[0] - 1, ...: rotation q finishes element i + 1 of a row and hands
+      // its new element i to rotation q + 1, so that element stays in a
+      // register and only the independent loads of element i touch memory.
+      if (nrot > 0) {
+        for (int row = tm.rank; row < n; row += tm.size) {
+          double* vr = V + row;
+          double hi = vr[(int64_t)(ri[0] + 1) * n];
+#pragma unroll 4
+          for (int q = 0; q < nrot; ++q) {
+            const int i = ri[q];
+            const double cs = rc[q], sn = rs[q];
+            const double a0 = vr[(int64_t)i * n];
+            vr[(int64_t)(i + 1) * n] = sn * a0 + cs * hi;
+            hi = cs * a0 - sn * hi;
+          }
+          vr[(int64_t)ri[nrot - 1] * n] = hi;
         }
       }
       tm.sync();
@@ -1154,11 +1163,53 @@ int launch_team(K kern, int CL, int nb, int threads, size_t smem, cudaStream_t s
 
 constexpr int kBigTeam = 8;   // CTAs per large matrix (portable cluster size)
 constexpr int kBigDim = 160;  // matrices at least this large use a cluster team
+constexpr int kHugeTeam = 16;  // CTAs per large matrix when a batch has too few to fill the GPU with teams of 8
+
+// A batch of nb large matrices takes teams of 16 (a non-portable cluster
+// size) when nb teams of 16 still fit the SMs and the device can place a
+// 16-CTA cluster of this kernel; else teams of 8.
+template <class K>
+bool huge_team(K kern, int nb, int threads, size_t smem) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return false;
+  if (nb * kHugeTeam > sms) return false;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)kHugeTeam);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)kHugeTeam;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return clusters >= 1;
+}
 
 int launch_chol(int nb, int max_m, const int32_t* m, const int64_t* a_off, double* Apool, int32_t* status,
                 cudaStream_t s) {
   if (nb == 0) return AMGDD_OK;
-  if (max_m >= kBigDim) return launch_team(k_chol<kBigTeam>, kBigTeam, nb, 256, 0, s, m, a_off, Apool, status);
+  if (max_m >= kBigDim) {
+    if (huge_team(k_chol<kHugeTeam>, nb, 256, 0))
+      return launch_team(k_chol<kHugeTeam>, kHugeTeam, nb, 256, 0, s, m, a_off, Apool, status);
+    return launch_team(k_chol<kBigTeam>, kBigTeam, nb, 256, 0, s, m, a_off, Apool, status);
+  }
   return launch_team(k_chol<1>, 1, nb, threads_for((int64_t)max_m * max_m), 0, s, m, a_off, Apool, status);
 }
 
@@ -1166,8 +1217,11 @@ int launch_schur(int nb, int max_m, const int32_t* m, const int32_t* no, const i
                  double rtol, cudaStream_t s) {
   if (nb == 0) return AMGDD_OK;
   const size_t smem = (size_t)max_m * sizeof(int);
-  if (max_m >= kBigDim)
+  if (max_m >= kBigDim) {
+    if (huge_team(k_schur<kHugeTeam>, nb, 256, smem))
+      return launch_team(k_schur<kHugeTeam>, kHugeTeam, nb, 256, smem, s, m, no, a_off, Atpool, rtol);
     return launch_team(k_schur<kBigTeam>, kBigTeam, nb, 256, smem, s, m, no, a_off, Atpool, rtol);
+  }
   return launch_team(k_schur<1>, 1, nb, threads_for((int64_t)max_m * max_m), smem, s, m, no, a_off, Atpool, rtol);
 }
 
@@ -1191,9 +1245,13 @@ int launch_gep(int nb, int max_no, const int32_t* m, const int32_t* no, const in
                int32_t* work_out, cudaStream_t s) {
   if (nb == 0) return AMGDD_OK;
   const size_t smem = (size_t)(2 * (max_no + 1)) * sizeof(double) + (size_t)(max_no + 1) * sizeof(int);
-  if (gep_uses_ql(max_no))
+  if (gep_uses_ql(max_no)) {
+    if (huge_team(k_gep<kHugeTeam, true>, nb, 256, smem))
+      return launch_team(k_gep<kHugeTeam, true>, kHugeTeam, nb, 256, smem, s, m, no, a_off, Lpool, Spool, cap,
+                         thresh, mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off, work_out);
     return launch_team(k_gep<kBigTeam, true>, kBigTeam, nb, 256, smem, s, m, no, a_off, Lpool, Spool, cap, thresh,
                        mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off, work_out);
+  }
   return launch_team(k_gep<1, false>, 1, nb, threads_for((int64_t)max_no * max_no), smem, s, m, no, a_off, Lpool,
                      Spool, cap, thresh, mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off, work_out);
 }
@@ -1267,8 +1325,12 @@ int launch_next_rows(const NextGramPlan& p, const int64_t* g_ptr, const int64_t*
                      float* Rn32, int32_t* rank_out, int64_t first, int64_t count, bool team, cudaStream_t s) {
   if (count == 0) return AMGDD_OK;
   DBuf<double> red;
-  AMGDD_TRY(red.alloc(count * kBigTeam));
+  AMGDD_TRY(red.alloc(count * kHugeTeam));
   // cluster teams for large stacked blocks (3D coarse levels), a CTA each otherwise
+  if (team && huge_team(k_next_rows<kHugeTeam>, (int)count, 256, 0))
+    return launch_team(k_next_rows<kHugeTeam>, kHugeTeam, (int)count, 256, 0, s, first, p.new_ptr.p, p.contrib.p,
+                       p.new_sptr.p, p.new_hoff.p, p.rowz_ptr.p, p.rowz_zoff.p, p.rowz_k.p, p.rowz_col.p, g_ptr,
+                       h_off, rank, R, Z64, t_off, scratch, Rn64, Rn32, rank_out, red.p);
   if (team)
     return launch_team(k_next_rows<kBigTeam>, kBigTeam, (int)count, 256, 0, s, first, p.new_ptr.p, p.contrib.p,
                        p.new_sptr.p, p.new_hoff.p, p.rowz_ptr.p, p.rowz_zoff.p, p.rowz_k.p, p.rowz_col.p, g_ptr,
@@ -1287,6 +1349,10 @@ int launch_schur_rows(int nb, int max_m, const LocalBatch& b, const int64_t* g_p
   // block; a CTA alone would take seconds on a 3D coarse level) or while the
   // batch leaves SMs idle; with many small matrices a CTA each keeps every
   // SM busy without the team's barriers
+  if (max_m >= kBigDim && (team || nb * kBigTeam <= 2 * 152) && huge_team(k_schur_rows<kHugeTeam>, nb, 256, 0))
+    return launch_team(k_schur_rows<kHugeTeam>, kHugeTeam, nb, 256, 0, s, b.m.p, b.no.p, b.a_off.p, b.pair_ptr.p,
+                       b.pair_grp.p, b.pair_nz.p, b.map_ptr.p, b.map.p, g_ptr, h_off, rank, R, M, y_off, y_rows,
+                       Ypool, n_off, nrm, Atpool, rank_out);
   if (max_m >= kBigDim && (team || nb * kBigTeam <= 2 * 152))
     return launch_team(k_schur_rows<kBigTeam>, kBigTeam, nb, 256, 0, s, b.m.p, b.no.p, b.a_off.p, b.pair_ptr.p,
                        b.pair_grp.p, b.pair_nz.p, b.map_ptr.p, b.map.p, g_ptr, h_off, rank, R, M, y_off, y_rows,
