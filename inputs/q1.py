@@ -166,6 +166,10 @@ CONFIGS = {
     # 512 x 512 cells, one point of the (eps, theta) sweep
     "q1_512_rot": dict(N=512, field="rot", theta=math.pi / 6, eps=1e-4, d1=0.0, bs=4, overlap=1, seed=2,
                        c_min=(2, 3, 4), n_coarse=2000, thresh=0.1, nrhs=1),
+    # the same with the kappa-derived threshold of Section 3.4 (kappa = 50)
+    # and no cap on the kept eigenvectors
+    "q1_512_rot_kappa": dict(N=512, field="rot", theta=math.pi / 6, eps=1e-4, d1=0.0, bs=4, overlap=1, seed=2,
+                             c_min=(1,), n_coarse=2000, thresh=0.1, kappa=50.0, nrhs=1),
     # 2048 x 2048 cells, closed circular field lines, D1 = 1e-8 h^2; two
     # layers of overlap on level 0, one on coarse levels
     "q1_2048_circ": dict(N=2048, field="circ", theta=0.0, eps=1e-6, d1=1e-8, bs=8, overlap=2, coarse_overlap=1,
