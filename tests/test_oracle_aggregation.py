@@ -60,3 +60,67 @@ def test_invariants(make, passes):
         prev, _ = standard_aggregation(sups, p.n, passes - 1)
         for a in np.unique(prev):
             assert np.unique(agg[prev == a]).shape[0] == 1
+
+
+def _lexicographic_mis_of_square(adj):
+    """The first maximal independent set, in ascending order, of the graph joining vertices within distance 2."""
+    A = (adj != 0).astype(np.int64)
+    A.setdiag(1)
+    A2 = (A @ A).tocsr()
+    chosen, blocked = [], np.zeros(adj.shape[0], dtype=bool)
+    for v in range(adj.shape[0]):
+        if not blocked[v]:
+            chosen.append(v)
+            blocked[A2.indices[A2.indptr[v]:A2.indptr[v + 1]]] = True
+    return chosen
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pass_one_roots_are_the_first_independent_set_of_the_squared_graph(seed):
+    """A characterisation of pass 1 independent of its loop: a vertex roots an aggregate exactly when no
+    lower-index root lies within distance 2 (a vertex is aggregated only by an adjacent root), so the roots
+    are the ascending-order maximal independent set of the distance-2 graph; and with every edge strong no
+    vertex is left for pass 3 (a vertex that is no root had an aggregated neighbour at its visit).  Pass 1
+    creates id t at its t-th root, so the t-th vertex of that set must carry id t, with its neighbours, and
+    the count of aggregates must equal the set's size."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(40, 400))
+    sups = [np.unique(rng.integers(0, n, size=int(rng.integers(1, 5)))) for _ in range(int(rng.integers(n // 2, 2 * n)))]
+    adj = structural_adjacency(sups, n).tocsr()
+    adj.setdiag(0)
+    adj.eliminate_zeros()
+    roots = _lexicographic_mis_of_square(adj)
+    agg, nagg = standard_aggregation(sups, n, 1)
+    # pass 1 made exactly len(roots) aggregates (pass 3 none): each root's id is its rank, and it holds its root
+    assert nagg == len(roots)
+    for t, r in enumerate(roots):
+        assert agg[r] == t
+    # each root's neighbours share its aggregate (pass 1 takes the whole closed neighbourhood)
+    for r in roots:
+        nb = adj.indices[adj.indptr[r]:adj.indptr[r + 1]]
+        assert np.all(agg[nb] == agg[r])
+
+
+def test_planted_pass_one_mistake_is_caught(monkeypatch):
+    """A pass 1 that roots an aggregate whenever the node itself is free (ignoring its neighbours) breaks the
+    characterisation above."""
+    import oracle.structure as ostruct
+
+    def greedy_free_only(adj_nodiag):
+        A = adj_nodiag.tocsr()
+        n = A.shape[0]
+        agg = -np.ones(n, dtype=np.int64)
+        nxt = 0
+        for j in range(n):
+            if agg[j] >= 0:
+                continue
+            nb = A.indices[A.indptr[j]:A.indptr[j + 1]]
+            agg[j] = nxt
+            agg[nb[agg[nb] < 0]] = nxt
+            nxt += 1
+        return agg, nxt
+
+    monkeypatch.setattr(ostruct, "vanek_aggregation", greedy_free_only)
+    with pytest.raises(AssertionError):
+        for seed in range(6):
+            test_pass_one_roots_are_the_first_independent_set_of_the_squared_graph(seed)
