@@ -265,7 +265,7 @@ struct Level {
   DBuf<int32_t> det_pos;
   DBuf<double> yd64;
   DBuf<float> yd32;
-  DBuf<double> myd64;  // the same for kMaxRhs interleaved columns (batched)
+  DBuf<double> myd64;  // the same for the batched solves' interleaved columns
   DBuf<float> myd32;
   DBuf<double> W64, Wt64, Z64, Zt64, mu;
   DBuf<float> W32, Wt32, Z32, Zt32;
@@ -295,8 +295,8 @@ struct Level {
   // ---- work vectors of the V-cycle ----------------------------------------
   DBuf<double> r64, x64, s64;
   DBuf<float> r32, x32, s32;
-  // the same for up to kMaxRhs right-hand sides (interleaved; allocated at
-  // the first batched solve)
+  // the same for the batched solves' columns (interleaved; allocated at the
+  // first batched solve for its width, grown for a wider one)
   DBuf<double> mr64, mx64, ms64;
   DBuf<float> mr32, mx32, ms32;
 };
@@ -452,7 +452,7 @@ int launch_cg_zdot(PcgState* st, const float* x32, double* z, const double* r, c
 
 // ---------------------------------------------------------------------------
 // K right-hand sides at once (multi_kernels.cu): vectors interleaved by node
-// (v[i * K + k]), K in {2, 4, 8}.  Modes as launch_seg (SEG_RESID reads c).
+// (v[i * K + k]), K in {2, 4, 8, 16, 32}.  Modes as launch_seg (SEG_RESID reads c).
 int launch_seg_multi(const SegPlan& p, const void* M, const void* MT, bool fp32, const void* x, void* y, SegMode mode,
                      const void* csrc, int K, const int* skip, cudaStream_t s);
 // partials: kDotBlocks x 2K (a.b then a.c per column)
@@ -553,7 +553,7 @@ int launch_ell_fill(int64_t total, const int64_t* src, const double* Aw64, doubl
                     cudaStream_t s);
 // y = A x (csrc null) or y = csrc - A x over the ELL rows of L
 int launch_ell(const Level& L, bool fp32, const void* x, void* y, const void* csrc, const int* skip, cudaStream_t s);
-// the same for K in {2, 4, 8} interleaved columns
+// the same for K in {2, 4, 8, 16, 32} interleaved columns
 int launch_ell_multi(const Level& L, bool fp32, const void* x, void* y, const void* c, int K, const int* skip,
                      cudaStream_t s);
 int launch_dense_pack(const double* C, int n, int64_t ld, double* B64, float* B32, cudaStream_t s);
