@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--serve", action="store_true",
                     help="run the serving workload (many operators and right-hand-side counts) instead")
     ap.add_argument("--no-serving", action="store_true", help="skip the small serving run of the default line")
+    ap.add_argument("--serve-kappa", action="store_true",
+                    help="with --serve-mix: operators by the kappa threshold (Section 3.4) instead of LS_{2,3,4}")
     ap.add_argument("--serve-mix", action="store_true",
                     help="run the serving mix with setup on the request path (operators carried by the requests; "
                          "sides 32..256, 1..64 right-hand sides; a one-at-a-time FP64 loop beside it) instead")
@@ -413,7 +415,7 @@ def serving_run(amg, seed, sides, nops, nreq, max_rhs, rate_frac=0.8, slots=4):
             "precision": "mixed", "data": "synthetic, seeded"}
 
 
-def serving_mix_run(amg, seed, sides, nreq, max_rhs, pool=None, rate_fracs=(0.5, 0.8, 1.0), slots=4):
+def serving_mix_run(amg, seed, sides, nreq, max_rhs, pool=None, rate_fracs=(0.5, 0.8, 1.0), slots=4, kappa=False):
     """The serving mix with setup on the request path: every request carries its operator, a 2D Q1 problem with
     side drawn uniformly from `sides`, theta ~ U[0, pi), eps log-uniform in [1e-6, 1], 4x4 aggregates, LS_{2,3,4},
     mixed precision, and 1..max_rhs N(0,1) right-hand sides.  pool = None: a new operator per request (no
@@ -421,7 +423,8 @@ def serving_mix_run(amg, seed, sides, nreq, max_rhs, pool=None, rate_fracs=(0.5,
     saturated rate (everything arrives at once), open-loop Poisson arrivals at rate_fracs of it (each run with
     operators keyed afresh, so that setup stays on the request path), and a one-at-a-time FP64 loop over the same
     requests (setup and solve per request, nothing overlapped, each operator built once).  Both build with the
-    fixed kernel choices (tune = 0)."""
+    fixed kernel choices (tune = 0).  kappa: every operator takes the kappa-derived threshold of Section 3.4
+    (kappa = 50) with no cap on the kept eigenvectors instead of LS_{2,3,4}."""
     import numpy as np
     import torch
     from inputs import block_aggregates_2d, q1_2d, rotated_sqrtK, seeded_rhs
@@ -440,7 +443,8 @@ def serving_mix_run(amg, seed, sides, nreq, max_rhs, pool=None, rate_fracs=(0.5,
     cols = sum(B.shape[1] for _, B in reqs)
     # setup on the request path takes the fixed kernel choices (tune = 0): timing the forms of every new
     # operator costs more than it saves on a request's few solves, and builds overlap other work on the GPU
-    kw = dict(c_min=(2, 3, 4), n_coarse=2000, precision=amg.MIXED32, tune=0)
+    lsk = dict(c_min=(1,), kappa=50.0) if kappa else dict(c_min=(2, 3, 4))
+    kw = dict(n_coarse=2000, precision=amg.MIXED32, tune=0, **lsk)
 
     def run(key0, rate):
         srv = amg.Server(slots=slots)
@@ -481,7 +485,7 @@ def serving_mix_run(amg, seed, sides, nreq, max_rhs, pool=None, rate_fracs=(0.5,
     for k, B in reqs:
         t1 = time.perf_counter()
         if k not in built:  # the loop keeps what it built (a pool reuses its operators)
-            built[k] = amg.Hierarchy.from_problem(opdefs[k], overlap=1, c_min=(2, 3, 4), n_coarse=2000, tune=0)
+            built[k] = amg.Hierarchy.from_problem(opdefs[k], overlap=1, n_coarse=2000, tune=0, **lsk)
         H = built[k]
         _, inf = H.solve(B, tol=1e-8)
         assert all(i["relres_true"] <= 1e-8 for i in inf)
@@ -495,7 +499,8 @@ def serving_mix_run(amg, seed, sides, nreq, max_rhs, pool=None, rate_fracs=(0.5,
             "fp64_one_at_a_time": {"requests_per_s": nreq / loop_s, "solves_per_s": cols / loop_s,
                                    "service_p50_ms": lat1[len(lat1) // 2],
                                    "service_p99_ms": lat1[min(len(lat1) - 1, int(0.99 * len(lat1)))]},
-            "precision": "mixed (FP32 V-cycle, FP64 flexible CG) in the server", "data": "synthetic, seeded"}
+            "precision": "mixed (FP32 V-cycle, FP64 flexible CG) in the server", "data": "synthetic, seeded",
+            "coarsening": "kappa = 50, no cap" if kappa else "LS_{2,3,4}"}
 
 
 def run_ours(args):
@@ -624,8 +629,10 @@ def run_ours(args):
         # the serving mix with setup on the request path (literal: a new operator per request; and a pool of 16)
         out = {"metric": "serving with setup on the request path: solves/s and p50/p99 latency (mixed)",
                "impl": "ours", "n_gpus": world,
-               "literal": serving_mix_run(amg, seed=5, sides=(32, 64, 128, 256), nreq=48, max_rhs=64),
-               "pool": serving_mix_run(amg, seed=6, sides=(32, 64, 128, 256), nreq=192, max_rhs=64, pool=16)}
+               "literal": serving_mix_run(amg, seed=5, sides=(32, 64, 128, 256), nreq=48, max_rhs=64,
+                                          kappa=args.serve_kappa)}
+        if not args.serve_kappa:
+            out["pool"] = serving_mix_run(amg, seed=6, sides=(32, 64, 128, 256), nreq=192, max_rhs=64, pool=16)
         if rank == 0:
             print(json.dumps(out), flush=True)
         return
