@@ -29,6 +29,13 @@
 // walked through the vertex -> edge incidence, and every test is an "any"
 // or a "min", so repeated members and repeated edges change nothing.  The
 // ids equal those of the sequential passes, vertex for vertex.
+//
+// Pass 1 takes one full round over every vertex, then rounds over the
+// frontier only (the vertices whose inputs a change of the previous round
+// touched), all of them in one cooperative launch with a bounded grid
+// barrier between the two phases of a round.  The visiting order makes the
+// rounds a dependent chain (about 2N of them on an N x N grid), each short
+// and latency-bound.
 #include <cuda_runtime.h>
 
 #include <climits>
