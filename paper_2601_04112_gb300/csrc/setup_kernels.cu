@@ -441,7 +441,7 @@ __global__ void k_gep(const int32_t* __restrict__ mdim, const int32_t* __restric
                       const int64_t* __restrict__ mu_off, double* __restrict__ mu_out,
                       const int64_t* __restrict__ z_off_cap, double* __restrict__ Zcap, int32_t* __restrict__ kout,
                       double* __restrict__ scratch, const int64_t* __restrict__ scr_off,
-                      int32_t* __restrict__ work_out) {
+                      int32_t* __restrict__ work_out, int ql_smem) {
   __shared__ double sh[32];
   int work = 0;  // Jacobi sweeps or QL rotations (for the setup flop count)
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -512,7 +512,7 @@ __global__ void k_gep(const int32_t* __restrict__ mdim, const int32_t* __restric
     double* rc = pv + n;
     double* rs = rc + n;
     int* ri = reinterpret_cast<int*>(rs + n);
-    int* ctl = ri + n;  // [0] rotations in the sweep, [1] finished, [2] l, [3] iterations at l
+    int* ctl = ri + n;  // [0] rotations in the sweep, [1] finished
     for (int k = 0; k + 2 < n; ++k) {
       const int mm = n - k - 1;
       double* x = C + (k + 1) + (int64_t)k * n;  // column k below the diagonal
@@ -559,8 +559,6 @@ __global__ void k_gep(const int32_t* __restrict__ mdim, const int32_t* __restric
       }
       d[n - 1] = C[(n - 1) + (int64_t)(n - 1) * n];
       e[n - 1] = 0.0;
-      ctl[2] = 0;
-      ctl[3] = 0;
     }
     tm.sync();
     // V = H_0 H_1 ... H_{n-3}, accumulated backwards
@@ -587,61 +585,102 @@ __global__ void k_gep(const int32_t* __restrict__ mdim, const int32_t* __restric
     // Wilkinson, Numer. Math. 11 (1968); EISPACK tql2): per sweep the shift g,
     // the chain of plane rotations from the bottom of the unreduced block up,
     // and the split test on |e|; rotations are accumulated into V by the team.
+    // The chain is serial: warp 0 of the team's first CTA runs it (the split
+    // test by the whole warp, 32 entries per ballot; the rotations by lane 0)
+    // on copies of d and e in that CTA's shared memory when they fit
+    // (ql_smem), then publishes the sweep's rotations for the team.
+    const bool lead = tm.cta == 0;
+    const bool shq = ql_smem != 0;
+    double* sd = shq ? reinterpret_cast<double*>(smem_raw) : d;
+    double* se = shq ? sd + n : e;
+    double* qc = shq ? se + n : rc;
+    double* qs = shq ? qc + n : rs;
+    int* qi = shq ? reinterpret_cast<int*>(qs + n) : ri;
+    if (shq && lead) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        sd[i] = d[i];
+        se[i] = e[i];
+      }
+      __syncthreads();
+    }
+    int l = 0, iter = 0;  // kept by warp 0 of the first CTA (the same in every lane)
     for (int guard = 0; guard < 64 * n + 64; ++guard) {
-      if (tm.rank == 0) {
-        int l = ctl[2], iter = ctl[3], nrot = 0, fin = 0;
+      if (lead && threadIdx.x < 32) {
+        const int lane = (int)threadIdx.x;
+        int nrot = 0, fin = 0;
         for (;;) {
           if (l >= n) {
             fin = 1;
             break;
           }
-          int mm = l;
-          for (; mm < n - 1; ++mm)
-            if (fabs(e[mm]) <= DBL_EPSILON * (fabs(d[mm]) + fabs(d[mm + 1]))) break;
+          int mm = n - 1;  // the first small e[mm] at or after l
+          for (int base = l; base < n - 1; base += 32) {
+            const int idx = base + lane;
+            const bool small =
+                idx < n - 1 && fabs(se[idx]) <= DBL_EPSILON * (fabs(sd[idx]) + fabs(sd[idx + 1]));
+            const unsigned bal = __ballot_sync(0xffffffffu, small);
+            if (bal) {
+              mm = base + __ffs(bal) - 1;
+              break;
+            }
+          }
           if (mm == l || iter >= 60) {  // d[l] converged (or the iteration budget is spent)
             ++l;
             iter = 0;
             continue;
           }
           ++iter;
-          double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-          double r = hypot(g, 1.0);
-          g = d[mm] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
-          double sn = 1.0, cs = 1.0, p = 0.0;
-          bool split = false;
-          for (int i = mm - 1; i >= l; --i) {
-            const double f = sn * e[i], bb = cs * e[i];
-            r = hypot(f, g);
-            e[i + 1] = r;
-            if (r == 0.0) {  // the chain split: recheck convergence before finishing
-              d[i + 1] -= p;
-              e[mm] = 0.0;
-              split = true;
-              break;
+          if (lane == 0) {
+            double g = (sd[l + 1] - sd[l]) / (2.0 * se[l]);
+            double r = hypot(g, 1.0);
+            g = sd[mm] - sd[l] + se[l] / (g + (g >= 0.0 ? r : -r));
+            double sn = 1.0, cs = 1.0, p = 0.0;
+            bool split = false;
+            for (int i = mm - 1; i >= l; --i) {
+              const double f = sn * se[i], bb = cs * se[i];
+              r = hypot(f, g);
+              se[i + 1] = r;
+              if (r == 0.0) {  // the chain split: recheck convergence before finishing
+                sd[i + 1] -= p;
+                se[mm] = 0.0;
+                split = true;
+                break;
+              }
+              sn = f / r;
+              cs = g / r;
+              g = sd[i + 1] - p;
+              r = (sd[i] - g) * sn + 2.0 * cs * bb;
+              p = sn * r;
+              sd[i + 1] = g + p;
+              g = cs * r - bb;
+              qc[nrot] = cs;
+              qs[nrot] = sn;
+              qi[nrot] = i;
+              ++nrot;
             }
-            sn = f / r;
-            cs = g / r;
-            g = d[i + 1] - p;
-            r = (d[i] - g) * sn + 2.0 * cs * bb;
-            p = sn * r;
-            d[i + 1] = g + p;
-            g = cs * r - bb;
-            rc[nrot] = cs;
-            rs[nrot] = sn;
-            ri[nrot] = i;
-            ++nrot;
+            if (!split) {
+              sd[l] -= p;
+              se[l] = g;
+              se[mm] = 0.0;
+            }
           }
-          if (!split) {
-            d[l] -= p;
-            e[l] = g;
-            e[mm] = 0.0;
-          }
+          nrot = __shfl_sync(0xffffffffu, nrot, 0);
+          __syncwarp();
           break;
         }
-        ctl[0] = nrot;
-        ctl[1] = fin;
-        ctl[2] = l;
-        ctl[3] = iter;
+        if (lane == 0) {
+          ctl[0] = nrot;
+          ctl[1] = fin;
+        }
+      }
+      if (shq && lead) {  // publish the sweep's rotations for the other CTAs
+        __syncthreads();
+        const int nr = ctl[0];
+        for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+          rc[q] = qc[q];
+          rs[q] = qs[q];
+          ri[q] = qi[q];
+        }
       }
       tm.sync();
       const int nrot = ctl[0];
@@ -669,6 +708,10 @@ __global__ void k_gep(const int32_t* __restrict__ mdim, const int32_t* __restric
       }
       tm.sync();
     }
+    if (shq && lead) {  // the eigenvalues back to d for the team
+      for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = sd[i];
+    }
+    tm.sync();
     for (int i = tm.rank; i < n; i += tm.size) C[i + (int64_t)i * n] = d[i];
     tm.sync();
   } else {
@@ -1246,14 +1289,18 @@ int launch_gep(int nb, int max_no, const int32_t* m, const int32_t* no, const in
   if (nb == 0) return AMGDD_OK;
   const size_t smem = (size_t)(2 * (max_no + 1)) * sizeof(double) + (size_t)(max_no + 1) * sizeof(int);
   if (gep_uses_ql(max_no)) {
-    if (huge_team(k_gep<kHugeTeam, true>, nb, 256, smem))
-      return launch_team(k_gep<kHugeTeam, true>, kHugeTeam, nb, 256, smem, s, m, no, a_off, Lpool, Spool, cap,
-                         thresh, mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off, work_out);
-    return launch_team(k_gep<kBigTeam, true>, kBigTeam, nb, 256, smem, s, m, no, a_off, Lpool, Spool, cap, thresh,
-                       mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off, work_out);
+    // QL: shared copies of d, e and one sweep's rotations (4 doubles and an int per row) when they fit
+    const size_t smem_q = (size_t)max_no * (4 * sizeof(double) + sizeof(int)) + 64;
+    const int shq = smem_q <= (size_t)200 * 1024 ? 1 : 0;
+    const size_t sm = shq ? std::max(smem, smem_q) : smem;
+    if (huge_team(k_gep<kHugeTeam, true>, nb, 256, sm))
+      return launch_team(k_gep<kHugeTeam, true>, kHugeTeam, nb, 256, sm, s, m, no, a_off, Lpool, Spool, cap,
+                         thresh, mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off, work_out, shq);
+    return launch_team(k_gep<kBigTeam, true>, kBigTeam, nb, 256, sm, s, m, no, a_off, Lpool, Spool, cap, thresh,
+                       mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off, work_out, shq);
   }
   return launch_team(k_gep<1, false>, 1, nb, threads_for((int64_t)max_no * max_no), smem, s, m, no, a_off, Lpool,
-                     Spool, cap, thresh, mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off, work_out);
+                     Spool, cap, thresh, mu_off, mu, z_off_cap, Zcap, kout, scratch, scr_off, work_out, 0);
 }
 
 bool gep_uses_ql(int max_no) { return max_no >= kBigDim; }
