@@ -1280,7 +1280,6 @@ int launch_inv_rows(int nb, int max_m, const int32_t* m, const int32_t* no, cons
   return AMGDD_OK;
 }
 
-int gep_scratch_doubles(int n, int CL) { return 5 * n * n + (n + 2) / 2 + 1 + CL + 2; }
 
 int launch_gep(int nb, int max_no, const int32_t* m, const int32_t* no, const int64_t* a_off, const double* Lpool,
                const double* Spool, const int32_t* cap, double thresh, const int64_t* mu_off, double* mu,
